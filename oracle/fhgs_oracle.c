@@ -1,0 +1,820 @@
+/*
+ * FHGS oracle: a plain, slow, FP64 CPU implementation of the feature-splatting
+ * hot path (arXiv 2505.19154).  TEST INFRASTRUCTURE ONLY: it is used by the
+ * tests, by the smoke check and by the CPU-baseline leg of the benchmark.  The
+ * product path never links, loads or calls it, and it shares no code, header
+ * or constant table with the CUDA library.
+ *
+ * What each function follows:
+ *   - orc_project / orc_project_bwd: the screen-space footprint of a 3-D
+ *     Gaussian (EWA: Sigma' = J W Sigma W^T J^T + dilation I) and its inverse
+ *     (the conic), which the paper takes over from the 3DGS rasterizer it
+ *     builds on (Sec. 2.1, App. A); SH colour (Sec. 2.1, 3DGS background).
+ *   - orc_bin_f32: the FP32 binning specification (pixel/tile rectangle and
+ *     depth key, App. A "CreateTiles / DuplicateWithKeys"); a plain C float
+ *     transcription, compiled with -ffp-contract=off so every operation is a
+ *     single IEEE rounding in the written order.
+ *   - orc_render: Eq. 4, c(x) = sum_i c_i w_i, w_i = alpha_i T_i,
+ *     T_i = prod_{j<i} (1 - alpha_j), evaluated front to back (nearest first)
+ *     over each 16x16 tile's depth-sorted list (App. A), and the same weights
+ *     applied to the per-primitive feature f_i (the DRF path of Sec. 3.2).
+ *   - orc_render_bwd: the exact derivative of Eq. 4, whose core is the
+ *     App. A.2 identity dL/dalpha_k = T_k dL/dw_k - (1/(1-alpha_k))
+ *     sum_{i>k} w_i dL/dw_i, plus the background term.
+ *   - orc_render_brute: Eq. 4 per pixel over ALL primitives, sorted by depth,
+ *     with no tiles (the brute-force definition).
+ *   - orc_fuse: the compositing-weight-normalised feature fusion
+ *     f_g = sum_{v,p} w_g(v,p) F_v(p) / sum_{v,p} w_g(v,p) (Sec. 3.1).
+ *
+ * Layouts (all row-major, caller-owned):
+ *   camera  double[18]: width, height, fx, fy, cx, cy, then the 3x4
+ *           world-to-camera matrix [R|t] row by row (OpenCV axes).
+ *   params  double[12]: znear, dilation, alpha_min, alpha_max, t_eps,
+ *           cutoff_sq, fov_clamp, bg_r, bg_g, bg_b, tile (16), sh_degree.
+ *   means/scales double[n][3], quats double[n][4] (w,x,y,z), opac double[n],
+ *   sh double[n][K][3] with K = (sh_degree+1)^2.
+ *   projection record double[n][ORC_REC]: see the ORC_* indices below.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_REC 24
+enum {
+    R_MX = 0, R_MY, R_A, R_B, R_C, R_DEPTH, R_R, R_G, R_BL, R_RAW_R, R_RAW_G,
+    R_RAW_B, R_VALID, R_OP, R_SIG_A, R_SIG_B, R_SIG_C, R_EXT_X, R_EXT_Y
+};
+
+enum { P_ZNEAR = 0, P_DIL, P_AMIN, P_AMAX, P_TEPS, P_CUT, P_FOV, P_BG0, P_BG1,
+       P_BG2, P_TILE, P_SHDEG };
+
+static double cam_R(const double *cam, int i, int j) { return cam[6 + 4 * i + j]; }
+static double cam_t(const double *cam, int i) { return cam[6 + 4 * i + 3]; }
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ---------------------------------------------------------------- SH ---- */
+/* Real spherical harmonics up to degree 3 in the 3DGS-family ordering and
+ * sign convention.  Normalisation constants are the closed forms
+ * sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the Legendre polynomial
+ * prefactors, written out per basis function. */
+static void sh_basis(const double d[3], double Y[16], double dY[16][3])
+{
+    const double x = d[0], y = d[1], z = d[2];
+    const double PI = 3.14159265358979323846;
+    const double c0 = 0.5 * sqrt(1.0 / PI);
+    const double c1 = sqrt(3.0 / (4.0 * PI));
+    const double c2a = 0.5 * sqrt(15.0 / PI);
+    const double c2b = 0.25 * sqrt(5.0 / PI);
+    const double c2c = 0.25 * sqrt(15.0 / PI);
+    const double c3a = 0.25 * sqrt(35.0 / (2.0 * PI));
+    const double c3b = 0.5 * sqrt(105.0 / PI);
+    const double c3c = 0.25 * sqrt(21.0 / (2.0 * PI));
+    const double c3d = 0.25 * sqrt(7.0 / PI);
+    const double c3e = 0.25 * sqrt(105.0 / PI);
+    double xx = x * x, yy = y * y, zz = z * z;
+
+    Y[0] = c0;
+    Y[1] = -c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = -c1 * x;
+    Y[4] = c2a * x * y;
+    Y[5] = -c2a * y * z;
+    Y[6] = c2b * (2.0 * zz - xx - yy);
+    Y[7] = -c2a * x * z;
+    Y[8] = c2c * (xx - yy);
+    Y[9] = -c3a * y * (3.0 * xx - yy);
+    Y[10] = c3b * x * y * z;
+    Y[11] = -c3c * y * (4.0 * zz - xx - yy);
+    Y[12] = c3d * z * (2.0 * zz - 3.0 * xx - 3.0 * yy);
+    Y[13] = -c3c * x * (4.0 * zz - xx - yy);
+    Y[14] = c3e * z * (xx - yy);
+    Y[15] = -c3a * x * (xx - 3.0 * yy);
+    if (!dY) return;
+    memset(dY, 0, sizeof(double) * 48);
+    dY[1][1] = -c1;
+    dY[2][2] = c1;
+    dY[3][0] = -c1;
+    dY[4][0] = c2a * y;           dY[4][1] = c2a * x;
+    dY[5][1] = -c2a * z;          dY[5][2] = -c2a * y;
+    dY[6][0] = -2.0 * c2b * x;    dY[6][1] = -2.0 * c2b * y;   dY[6][2] = 4.0 * c2b * z;
+    dY[7][0] = -c2a * z;          dY[7][2] = -c2a * x;
+    dY[8][0] = 2.0 * c2c * x;     dY[8][1] = -2.0 * c2c * y;
+    dY[9][0] = -c3a * 6.0 * x * y;
+    dY[9][1] = -c3a * (3.0 * xx - 3.0 * yy);
+    dY[10][0] = c3b * y * z;      dY[10][1] = c3b * x * z;     dY[10][2] = c3b * x * y;
+    dY[11][0] = c3c * 2.0 * x * y;
+    dY[11][1] = -c3c * (4.0 * zz - xx - 3.0 * yy);
+    dY[11][2] = -c3c * 8.0 * y * z;
+    dY[12][0] = -c3d * 6.0 * x * z;
+    dY[12][1] = -c3d * 6.0 * y * z;
+    dY[12][2] = c3d * (6.0 * zz - 3.0 * xx - 3.0 * yy);
+    dY[13][0] = -c3c * (4.0 * zz - 3.0 * xx - yy);
+    dY[13][1] = c3c * 2.0 * x * y;
+    dY[13][2] = -c3c * 8.0 * x * z;
+    dY[14][0] = c3e * 2.0 * x * z;
+    dY[14][1] = -c3e * 2.0 * y * z;
+    dY[14][2] = c3e * (xx - yy);
+    dY[15][0] = -c3a * (3.0 * xx - 3.0 * yy);
+    dY[15][1] = c3a * 6.0 * x * y;
+}
+
+/* Exported for the SH pins: Y (n x 16) and dY (n x 16 x 3) at unit dirs. */
+void orc_sh_basis(int64_t n, const double *dirs, double *Y, double *dY)
+{
+    for (int64_t i = 0; i < n; ++i)
+        sh_basis(dirs + 3 * i, Y + 16 * i, dY ? (double (*)[3])(dY + 48 * i) : NULL);
+}
+
+/* ------------------------------------------------------- rotations ---- */
+static void quat_to_rot(const double qn[4], double R[3][3])
+{
+    const double w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    R[0][1] = 2.0 * (x * y - w * z);
+    R[0][2] = 2.0 * (x * z + w * y);
+    R[1][0] = 2.0 * (x * y + w * z);
+    R[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    R[1][2] = 2.0 * (y * z - w * x);
+    R[2][0] = 2.0 * (x * z - w * y);
+    R[2][1] = 2.0 * (y * z + w * x);
+    R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+void orc_quat_to_rot(int64_t n, const double *q, double *R)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double nq = sqrt(q[4 * i] * q[4 * i] + q[4 * i + 1] * q[4 * i + 1] +
+                         q[4 * i + 2] * q[4 * i + 2] + q[4 * i + 3] * q[4 * i + 3]);
+        double qn[4] = {q[4 * i] / nq, q[4 * i + 1] / nq, q[4 * i + 2] / nq, q[4 * i + 3] / nq};
+        quat_to_rot(qn, (double (*)[3])(R + 9 * i));
+    }
+}
+
+/* ------------------------------------------------------- projection --- */
+/* Per Gaussian, FP64.  Fills the ORC_REC record; R_VALID = 0 when culled
+ * (depth <= znear, non-positive determinant, or a non-finite value). */
+static void project_one(const double *mu, const double *s, const double *q,
+                        const double *sh, int K, const double *cam,
+                        const double *prm, double *out)
+{
+    memset(out, 0, sizeof(double) * ORC_REC);
+    const double W = cam[0], H = cam[1], fx = cam[2], fy = cam[3], cx = cam[4], cy = cam[5];
+    double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (!(nq > 0.0) || !isfinite(nq)) return;
+    double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
+    double R[3][3];
+    quat_to_rot(qn, R);
+    double M[3][3], S[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[i][j] = R[i][j] * s[j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            S[i][j] = M[i][0] * M[j][0] + M[i][1] * M[j][1] + M[i][2] * M[j][2];
+    double t[3];
+    for (int i = 0; i < 3; ++i)
+        t[i] = cam_R(cam, i, 0) * mu[0] + cam_R(cam, i, 1) * mu[1] + cam_R(cam, i, 2) * mu[2] + cam_t(cam, i);
+    if (!(t[2] > prm[P_ZNEAR])) return;
+    double limx = prm[P_FOV] * (0.5 * W / fx), limy = prm[P_FOV] * (0.5 * H / fy);
+    double ux = t[0] / t[2], uy = t[1] / t[2];
+    double xh = ux > limx ? limx : (ux < -limx ? -limx : ux);
+    double yh = uy > limy ? limy : (uy < -limy ? -limy : uy);
+    double J[2][3] = {{fx / t[2], 0.0, -fx * xh / t[2]}, {0.0, fy / t[2], -fy * yh / t[2]}};
+    double Tm[2][3];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j)
+            Tm[i][j] = J[i][0] * cam_R(cam, 0, j) + J[i][1] * cam_R(cam, 1, j) + J[i][2] * cam_R(cam, 2, j);
+    double S2[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) acc += Tm[i][k] * S[k][l] * Tm[j][l];
+            S2[i][j] = acc;
+        }
+    double a = S2[0][0] + prm[P_DIL], b = S2[0][1], c = S2[1][1] + prm[P_DIL];
+    double det = a * c - b * b;
+    if (!(det > 0.0)) return;
+    double mx = fx * t[0] / t[2] + cx, my = fy * t[1] / t[2] + cy;
+    if (!isfinite(mx) || !isfinite(my)) return;
+    out[R_MX] = mx;
+    out[R_MY] = my;
+    out[R_A] = c / det;
+    out[R_B] = -b / det;
+    out[R_C] = a / det;
+    out[R_DEPTH] = t[2];
+    out[R_SIG_A] = a;
+    out[R_SIG_B] = b;
+    out[R_SIG_C] = c;
+    out[R_EXT_X] = sqrt(prm[P_CUT] * a);
+    out[R_EXT_Y] = sqrt(prm[P_CUT] * c);
+    /* SH colour: direction from the camera centre (-R^T t) to the mean. */
+    double cpos[3], v[3];
+    for (int i = 0; i < 3; ++i)
+        cpos[i] = -(cam_R(cam, 0, i) * cam_t(cam, 0) + cam_R(cam, 1, i) * cam_t(cam, 1) + cam_R(cam, 2, i) * cam_t(cam, 2));
+    for (int i = 0; i < 3; ++i) v[i] = mu[i] - cpos[i];
+    double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double d[3] = {v[0] / nv, v[1] / nv, v[2] / nv};
+    double Y[16];
+    sh_basis(d, Y, NULL);
+    for (int ch = 0; ch < 3; ++ch) {
+        double acc = 0.0;
+        for (int k = 0; k < K; ++k) acc += sh[3 * k + ch] * Y[k];
+        double raw = acc + 0.5;
+        out[R_RAW_R + ch] = raw;
+        out[R_R + ch] = raw > 0.0 ? raw : 0.0;
+    }
+    out[R_VALID] = 1.0;
+}
+
+void orc_project(int64_t n, const double *means, const double *scales, const double *quats,
+                 const double *opac, const double *sh, int K, const double *cam,
+                 const double *prm, double *rec)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < n; ++g) {
+        project_one(means + 3 * g, scales + 3 * g, quats + 4 * g, sh + (int64_t)3 * K * g, K, cam, prm,
+                    rec + (int64_t)ORC_REC * g);
+        rec[(int64_t)ORC_REC * g + R_OP] = opac[g];
+    }
+}
+
+/* ------------------------------------------------ FP32 binning spec --- */
+/* Single-precision, contraction-free transcription of the binning rules:
+ * every line is one IEEE-754 binary32 operation (or a fixed left-to-right
+ * chain of them), sqrt and division correctly rounded.  Outputs per
+ * Gaussian: pixel rectangle and tile rectangle (inclusive), tile count,
+ * the raw bits of the view-space depth, and the FP32 footprint
+ * (mean2d, conic) that the binning decisions were made from. */
+static int bin_one_f32(const float *mu, const float *s, const float *q, const float *cam,
+                       const float *prm, int32_t *pix, int32_t *tile, uint32_t *ntiles,
+                       uint32_t *dbits, float *fp)
+{
+    const float W = cam[0], H = cam[1], fx = cam[2], fy = cam[3], cx = cam[4], cy = cam[5];
+    const int tsz = (int)prm[P_TILE];
+    float n2 = q[0] * q[0];
+    n2 = n2 + q[1] * q[1];
+    n2 = n2 + q[2] * q[2];
+    n2 = n2 + q[3] * q[3];
+    if (!(n2 > 0.0f) || !isfinite(n2)) return 0;
+    float inv = 1.0f / sqrtf(n2);
+    float w = q[0] * inv, x = q[1] * inv, y = q[2] * inv, z = q[3] * inv;
+    float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+    float wx = w * x, wy = w * y, wz = w * z;
+    float R[3][3];
+    R[0][0] = 1.0f - 2.0f * (yy + zz);
+    R[0][1] = 2.0f * (xy - wz);
+    R[0][2] = 2.0f * (xz + wy);
+    R[1][0] = 2.0f * (xy + wz);
+    R[1][1] = 1.0f - 2.0f * (xx + zz);
+    R[1][2] = 2.0f * (yz - wx);
+    R[2][0] = 2.0f * (xz - wy);
+    R[2][1] = 2.0f * (yz + wx);
+    R[2][2] = 1.0f - 2.0f * (xx + yy);
+    float M[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[i][j] = R[i][j] * s[j];
+    float Sg[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+            float acc = M[i][0] * M[j][0];
+            acc = acc + M[i][1] * M[j][1];
+            acc = acc + M[i][2] * M[j][2];
+            Sg[i][j] = acc;
+            Sg[j][i] = acc;
+        }
+    float t[3];
+    for (int i = 0; i < 3; ++i) {
+        float acc = cam[6 + 4 * i + 0] * mu[0];
+        acc = acc + cam[6 + 4 * i + 1] * mu[1];
+        acc = acc + cam[6 + 4 * i + 2] * mu[2];
+        t[i] = acc + cam[6 + 4 * i + 3];
+    }
+    if (!(t[2] > prm[P_ZNEAR])) return 0;
+    float limx = prm[P_FOV] * ((0.5f * W) / fx);
+    float limy = prm[P_FOV] * ((0.5f * H) / fy);
+    float ux = t[0] / t[2], uy = t[1] / t[2];
+    float xh = fminf(limx, fmaxf(-limx, ux));
+    float yh = fminf(limy, fmaxf(-limy, uy));
+    float J00 = fx / t[2], J02 = -((fx * xh) / t[2]);
+    float J11 = fy / t[2], J12 = -((fy * yh) / t[2]);
+    float Tm[2][3];
+    for (int j = 0; j < 3; ++j) {
+        Tm[0][j] = J00 * cam[6 + 0 * 4 + j] + J02 * cam[6 + 2 * 4 + j];
+        Tm[1][j] = J11 * cam[6 + 1 * 4 + j] + J12 * cam[6 + 2 * 4 + j];
+    }
+    float U[2][3];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float acc = Tm[i][0] * Sg[0][j];
+            acc = acc + Tm[i][1] * Sg[1][j];
+            acc = acc + Tm[i][2] * Sg[2][j];
+            U[i][j] = acc;
+        }
+    float a = U[0][0] * Tm[0][0];
+    a = a + U[0][1] * Tm[0][1];
+    a = a + U[0][2] * Tm[0][2];
+    a = a + prm[P_DIL];
+    float b = U[0][0] * Tm[1][0];
+    b = b + U[0][1] * Tm[1][1];
+    b = b + U[0][2] * Tm[1][2];
+    float c = U[1][0] * Tm[1][0];
+    c = c + U[1][1] * Tm[1][1];
+    c = c + U[1][2] * Tm[1][2];
+    c = c + prm[P_DIL];
+    float ac = a * c;
+    float det = ac - b * b;
+    float A, B, C;
+    if (det < 1e-6f * ac) {
+        /* near-degenerate: determinant and inverse in binary64 */
+        double dd = (double)a * (double)c - (double)b * (double)b;
+        det = (float)dd;
+        if (!(det > 0.0f)) return 0;
+        A = (float)((double)c / dd);
+        B = (float)(-(double)b / dd);
+        C = (float)((double)a / dd);
+    } else {
+        if (!(det > 0.0f)) return 0;
+        A = c / det;
+        B = -(b / det);
+        C = a / det;
+    }
+    float mx = (fx * t[0]) / t[2] + cx;
+    float my = (fy * t[1]) / t[2] + cy;
+    float ex = sqrtf(prm[P_CUT] * a);
+    float ey = sqrtf(prm[P_CUT] * c);
+    if (!isfinite(mx) || !isfinite(my) || !isfinite(ex) || !isfinite(ey)) return 0;
+    float xlo = ceilf((mx - ex) - 0.5f), xhi = floorf((mx + ex) - 0.5f);
+    float ylo = ceilf((my - ey) - 0.5f), yhi = floorf((my + ey) - 0.5f);
+    xlo = fmaxf(xlo, 0.0f);
+    ylo = fmaxf(ylo, 0.0f);
+    xhi = fminf(xhi, W - 1.0f);
+    yhi = fminf(yhi, H - 1.0f);
+    if (xlo > xhi || ylo > yhi) return 0;
+    int ix0 = (int)xlo, ix1 = (int)xhi, iy0 = (int)ylo, iy1 = (int)yhi;
+    pix[0] = ix0; pix[1] = iy0; pix[2] = ix1; pix[3] = iy1;
+    tile[0] = ix0 / tsz; tile[1] = iy0 / tsz; tile[2] = ix1 / tsz; tile[3] = iy1 / tsz;
+    *ntiles = (uint32_t)((tile[2] - tile[0] + 1) * (tile[3] - tile[1] + 1));
+    memcpy(dbits, &t[2], 4);
+    fp[0] = mx; fp[1] = my; fp[2] = A; fp[3] = B; fp[4] = C; fp[5] = t[2];
+    return 1;
+}
+
+void orc_bin_f32(int64_t n, const float *means, const float *scales, const float *quats,
+                 const float *cam, const float *prm, int32_t *pix, int32_t *tile,
+                 uint32_t *ntiles, uint32_t *dbits, float *fp)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < n; ++g) {
+        int ok = bin_one_f32(means + 3 * g, scales + 3 * g, quats + 4 * g, cam, prm, pix + 4 * g,
+                             tile + 4 * g, ntiles + g, dbits + g, fp + 6 * g);
+        if (!ok) {
+            for (int k = 0; k < 4; ++k) { pix[4 * g + k] = -1; tile[4 * g + k] = -1; }
+            ntiles[g] = 0;
+            dbits[g] = 0xFFFFFFFFu;
+            for (int k = 0; k < 6; ++k) fp[6 * g + k] = 0.0f;
+        }
+    }
+}
+
+/* --------------------------------------------------------- render ----- */
+/* One pixel, Eq. 4 front to back over an ordered candidate list.  Records
+ * the contributors (index into the list, alpha, T before, weight) when
+ * `rec_*` are given.  Returns the number of contributors. */
+typedef struct {
+    double T;
+    double rgb[3];
+    int32_t last;       /* (position of the last contributor in the list) + 1 */
+    double margin;      /* min relative distance of any threshold decision */
+    uint64_t sig;       /* hash of the contributor set and clamp flags */
+} pix_state;
+
+static double rel(double v, double thr) { return fabs(v - thr) / thr; }
+
+static int composite_pixel(double px, double py, const uint32_t *list, int64_t len,
+                           const double *rec, const double *feat, int D, const double *prm,
+                           pix_state *st, double *F, int64_t *ci, double *calpha, double *cT,
+                           double *cG, int64_t cap)
+{
+    const double cut = prm[P_CUT], amin = prm[P_AMIN], amax = prm[P_AMAX], teps = prm[P_TEPS];
+    double T = 1.0;
+    int nc = 0;
+    st->rgb[0] = st->rgb[1] = st->rgb[2] = 0.0;
+    st->last = 0;
+    st->margin = INFINITY;
+    st->sig = 1469598103934665603ull;
+    if (F)
+        for (int k = 0; k < D; ++k) F[k] = 0.0;
+    for (int64_t k = 0; k < len; ++k) {
+        const uint32_t g = list[k];
+        const double *r = rec + (int64_t)ORC_REC * g;
+        if (r[R_VALID] == 0.0) continue;
+        double dx = px - r[R_MX], dy = py - r[R_MY];
+        double q2 = r[R_A] * dx * dx + 2.0 * r[R_B] * dx * dy + r[R_C] * dy * dy;
+        double m = rel(q2, cut);
+        if (m < st->margin) st->margin = m;
+        if (q2 > cut) continue;
+        double G = exp(-0.5 * q2);
+        double rho = r[R_OP] * G;
+        m = rel(rho, amax);
+        if (m < st->margin) st->margin = m;
+        double alpha = rho > amax ? amax : rho;
+        m = rel(alpha, amin);
+        if (m < st->margin) st->margin = m;
+        if (alpha < amin) continue;
+        double Tn = T * (1.0 - alpha);
+        m = rel(Tn, teps);
+        if (m < st->margin) st->margin = m;
+        if (Tn < teps) break;
+        double w = alpha * T;
+        st->rgb[0] += w * r[R_R];
+        st->rgb[1] += w * r[R_G];
+        st->rgb[2] += w * r[R_BL];
+        if (F && D > 0) {
+            const double *f = feat + (int64_t)D * g;
+            for (int c = 0; c < D; ++c) F[c] += w * f[c];
+        }
+        if (ci && nc < cap) {
+            ci[nc] = k;
+            calpha[nc] = alpha;
+            cT[nc] = T;
+            cG[nc] = G;
+        }
+        st->sig = (st->sig ^ ((uint64_t)g * 2u + (rho > amax ? 1u : 0u))) * 1099511628211ull;
+        ++nc;
+        T = Tn;
+        st->last = (int32_t)(k + 1);
+    }
+    st->T = T;
+    return nc;
+}
+
+/* Tiled render of the pixels in [x0,x1) x [y0,y1) of one camera.
+ * gids/ranges: the camera's depth-sorted per-tile lists (ranges[2*tile]).
+ * Outputs are indexed by region pixel (row-major in the region). */
+void orc_render(const double *rec, const double *feat, int D, const uint32_t *gids,
+                const uint32_t *ranges, const double *cam, const double *prm, int x0, int y0,
+                int x1, int y1, double *out_rgb, double *out_feat, double *out_T,
+                int32_t *out_last, double *out_margin, int32_t *out_ncontrib)
+{
+    const int W = (int)cam[0], tsz = (int)prm[P_TILE];
+    const int tiles_x = (W + tsz - 1) / tsz;
+    const int rw = x1 - x0, rh = y1 - y0;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+        int px = x0 + (int)(idx % rw), py = y0 + (int)(idx / rw);
+        int tile = (py / tsz) * tiles_x + px / tsz;
+        uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+        pix_state st;
+        int nc = composite_pixel(px + 0.5, py + 0.5, gids + s, (int64_t)e - s, rec, feat, D, prm, &st,
+                                 out_feat ? out_feat + (int64_t)D * idx : NULL, NULL, NULL, NULL, NULL, 0);
+        for (int c = 0; c < 3; ++c) out_rgb[3 * idx + c] = st.rgb[c] + st.T * prm[P_BG0 + c];
+        out_T[idx] = st.T;
+        out_last[idx] = st.last;
+        out_margin[idx] = st.margin;
+        out_ncontrib[idx] = nc;
+    }
+}
+
+/* Brute-force render: every pixel in the region composites ALL valid
+ * Gaussians whose ellipse covers it, sorted by (depth_key, index) with no
+ * tiles.  depth_key is supplied by the caller (FP32 depth bits or FP64
+ * depth).  Also returns a per-pixel decision signature. */
+typedef struct { double key; uint32_t g; } kd_pair;
+static int kd_cmp(const void *a, const void *b)
+{
+    const kd_pair *x = (const kd_pair *)a, *y = (const kd_pair *)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return x->g < y->g ? -1 : (x->g > y->g ? 1 : 0);
+}
+
+void orc_render_brute(int64_t n, const double *rec, const double *depth_key, const double *feat,
+                      int D, const double *cam, const double *prm, int x0, int y0, int x1, int y1,
+                      double *out_rgb, double *out_feat, double *out_T, double *out_margin,
+                      uint64_t *out_sig)
+{
+    /* global depth order once, then per-pixel filtering keeps that order */
+    kd_pair *order = (kd_pair *)malloc(sizeof(kd_pair) * (size_t)(n > 0 ? n : 1));
+    int64_t m = 0;
+    for (int64_t g = 0; g < n; ++g)
+        if (rec[(int64_t)ORC_REC * g + R_VALID] != 0.0) {
+            order[m].key = depth_key[g];
+            order[m].g = (uint32_t)g;
+            ++m;
+        }
+    qsort(order, (size_t)m, sizeof(kd_pair), kd_cmp);
+    uint32_t *sorted = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1));
+    for (int64_t i = 0; i < m; ++i) sorted[i] = order[i].g;
+    free(order);
+    const int rw = x1 - x0, rh = y1 - y0;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+        int px = x0 + (int)(idx % rw), py = y0 + (int)(idx / rw);
+        pix_state st;
+        composite_pixel(px + 0.5, py + 0.5, sorted, m, rec, feat, D, prm, &st,
+                        out_feat ? out_feat + (int64_t)D * idx : NULL, NULL, NULL, NULL, NULL, 0);
+        for (int c = 0; c < 3; ++c) out_rgb[3 * idx + c] = st.rgb[c] + st.T * prm[P_BG0 + c];
+        out_T[idx] = st.T;
+        out_margin[idx] = st.margin;
+        out_sig[idx] = st.sig;
+    }
+    free(sorted);
+}
+
+/* ---------------------------------------------------- render backward -- */
+/* Gradient of L = sum_p dC_p . rgb_p + dF_p . feat_p over the region with
+ * respect to each Gaussian's screen footprint and appearance.  Accumulates
+ * (+=) into g_mean2d[n][2], g_conic[n][3] (A, B, C of q2 = A dx^2 +
+ * 2 B dx dy + C dy^2), g_op[n], g_rgb[n][3] and, when non-NULL, g_feat[n][D].
+ * The contributors are recovered by replaying the forward (exact T_i). */
+#define ORC_MAXC 65536
+void orc_render_bwd(const double *rec, const double *feat, int D, const uint32_t *gids,
+                    const uint32_t *ranges, const double *cam, const double *prm, int x0, int y0,
+                    int x1, int y1, const double *dC, const double *dF, double *g_mean2d,
+                    double *g_conic, double *g_op, double *g_rgb, double *g_feat)
+{
+    const int W = (int)cam[0], tsz = (int)prm[P_TILE];
+    const int tiles_x = (W + tsz - 1) / tsz;
+    const int rw = x1 - x0, rh = y1 - y0;
+    const double amax = prm[P_AMAX];
+#pragma omp parallel
+    {
+        int64_t *ci = (int64_t *)malloc(sizeof(int64_t) * ORC_MAXC);
+        double *ca = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *cT = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *cG = (double *)malloc(sizeof(double) * ORC_MAXC);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+            int px = x0 + (int)(idx % rw), py = y0 + (int)(idx / rw);
+            int tile = (py / tsz) * tiles_x + px / tsz;
+            uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+            const uint32_t *list = gids + s;
+            pix_state st;
+            int nc = composite_pixel(px + 0.5, py + 0.5, list, (int64_t)e - s, rec, feat, D, prm, &st,
+                                     NULL, ci, ca, cT, cG, ORC_MAXC);
+            if (nc > ORC_MAXC) nc = ORC_MAXC; /* never reached for the scenes used */
+            const double *dc = dC + 3 * idx;
+            const double *df = dF ? dF + (int64_t)D * idx : NULL;
+            double S = st.T * (dc[0] * prm[P_BG0] + dc[1] * prm[P_BG1] + dc[2] * prm[P_BG2]);
+            for (int j = nc - 1; j >= 0; --j) {
+                const uint32_t g = list[ci[j]];
+                const double *r = rec + (int64_t)ORC_REC * g;
+                const double alpha = ca[j], T = cT[j], G = cG[j], w = alpha * T;
+                double gw = dc[0] * r[R_R] + dc[1] * r[R_G] + dc[2] * r[R_BL];
+                if (df) {
+                    const double *f = feat + (int64_t)D * g;
+                    for (int c = 0; c < D; ++c) gw += df[c] * f[c];
+                }
+                const double dalpha = T * gw - S / (1.0 - alpha);
+                S += w * gw;
+                for (int c = 0; c < 3; ++c) {
+#pragma omp atomic
+                    g_rgb[3 * g + c] += w * dc[c];
+                }
+                if (df && g_feat) {
+                    double *gf = g_feat + (int64_t)D * g;
+                    for (int c = 0; c < D; ++c) {
+#pragma omp atomic
+                        gf[c] += w * df[c];
+                    }
+                }
+                const double rho = r[R_OP] * G;
+                const double drho = rho > amax ? 0.0 : dalpha;
+#pragma omp atomic
+                g_op[g] += G * drho;
+                const double dq2 = -0.5 * r[R_OP] * G * drho;
+                const double dx = px + 0.5 - r[R_MX], dy = py + 0.5 - r[R_MY];
+#pragma omp atomic
+                g_conic[3 * g + 0] += dx * dx * dq2;
+#pragma omp atomic
+                g_conic[3 * g + 1] += 2.0 * dx * dy * dq2;
+#pragma omp atomic
+                g_conic[3 * g + 2] += dy * dy * dq2;
+                const double ddx = (2.0 * r[R_A] * dx + 2.0 * r[R_B] * dy) * dq2;
+                const double ddy = (2.0 * r[R_B] * dx + 2.0 * r[R_C] * dy) * dq2;
+#pragma omp atomic
+                g_mean2d[2 * g + 0] -= ddx;
+#pragma omp atomic
+                g_mean2d[2 * g + 1] -= ddy;
+            }
+        }
+        free(ci); free(ca); free(cT); free(cG);
+    }
+}
+
+/* ------------------------------------------------ projection backward -- */
+/* Chain rule from (mean2d, conic, rgb) of one camera to the Gaussian
+ * parameters; accumulates (+=) into g_means[n][3], g_scales[n][3],
+ * g_quats[n][4], g_sh[n][K][3]. */
+static void project_bwd_one(const double *mu, const double *s, const double *q, const double *sh,
+                            int K, const double *cam, const double *prm, const double *rec,
+                            const double *gm2, const double *gcon, const double *grgb,
+                            double *gmu, double *gs, double *gq, double *gsh)
+{
+    if (rec[R_VALID] == 0.0) return;
+    const double W = cam[0], H = cam[1], fx = cam[2], fy = cam[3];
+    double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
+    double R[3][3];
+    quat_to_rot(qn, R);
+    double M[3][3], S[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[i][j] = R[i][j] * s[j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            S[i][j] = M[i][0] * M[j][0] + M[i][1] * M[j][1] + M[i][2] * M[j][2];
+    double Rw[3][3], t[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) Rw[i][j] = cam_R(cam, i, j);
+        t[i] = Rw[i][0] * mu[0] + Rw[i][1] * mu[1] + Rw[i][2] * mu[2] + cam_t(cam, i);
+    }
+    const double tz = t[2];
+    double limx = prm[P_FOV] * (0.5 * W / fx), limy = prm[P_FOV] * (0.5 * H / fy);
+    double ux = t[0] / tz, uy = t[1] / tz;
+    int clx = (ux > limx) || (ux < -limx), cly = (uy > limy) || (uy < -limy);
+    double xh = ux > limx ? limx : (ux < -limx ? -limx : ux);
+    double yh = uy > limy ? limy : (uy < -limy ? -limy : uy);
+    double J[2][3] = {{fx / tz, 0.0, -fx * xh / tz}, {0.0, fy / tz, -fy * yh / tz}};
+    double Tm[2][3];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j)
+            Tm[i][j] = J[i][0] * Rw[0][j] + J[i][1] * Rw[1][j] + J[i][2] * Rw[2][j];
+
+    /* conic = inverse of Sigma2; symmetric matrix gradient G_K */
+    double Kc[2][2] = {{rec[R_A], rec[R_B]}, {rec[R_B], rec[R_C]}};
+    double GK[2][2] = {{gcon[0], 0.5 * gcon[1]}, {0.5 * gcon[1], gcon[2]}};
+    double tmp[2][2], G2[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) tmp[i][j] = Kc[i][0] * GK[0][j] + Kc[i][1] * GK[1][j];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) G2[i][j] = -(tmp[i][0] * Kc[0][j] + tmp[i][1] * Kc[1][j]);
+    /* Sigma2 = Tm Sigma Tm^T + dil I */
+    double GS[3][3], GT[2][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 2; ++k)
+                for (int l = 0; l < 2; ++l) acc += Tm[k][i] * G2[k][l] * Tm[l][j];
+            GS[i][j] = acc;
+        }
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 2; ++k)
+                for (int l = 0; l < 3; ++l) acc += G2[i][k] * Tm[k][l] * S[l][j];
+            GT[i][j] = 2.0 * acc;
+        }
+    /* Tm = J Rw */
+    double GJ[2][3];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j)
+            GJ[i][j] = GT[i][0] * Rw[j][0] + GT[i][1] * Rw[j][1] + GT[i][2] * Rw[j][2];
+    double gt[3] = {0.0, 0.0, 0.0};
+    gt[2] += GJ[0][0] * (-fx / (tz * tz)) + GJ[1][1] * (-fy / (tz * tz));
+    gt[2] += GJ[0][2] * (fx * xh / (tz * tz)) + GJ[1][2] * (fy * yh / (tz * tz));
+    double gxh = GJ[0][2] * (-fx / tz), gyh = GJ[1][2] * (-fy / tz);
+    if (!clx) { gt[0] += gxh / tz; gt[2] += gxh * (-t[0] / (tz * tz)); }
+    if (!cly) { gt[1] += gyh / tz; gt[2] += gyh * (-t[1] / (tz * tz)); }
+    /* mean2d */
+    gt[0] += gm2[0] * fx / tz;
+    gt[2] += gm2[0] * (-fx * t[0] / (tz * tz));
+    gt[1] += gm2[1] * fy / tz;
+    gt[2] += gm2[1] * (-fy * t[1] / (tz * tz));
+    for (int j = 0; j < 3; ++j) gmu[j] += Rw[0][j] * gt[0] + Rw[1][j] * gt[1] + Rw[2][j] * gt[2];
+    /* Sigma = M M^T, M = R diag(s) */
+    double GM[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            GM[i][j] = 2.0 * (GS[i][0] * M[0][j] + GS[i][1] * M[1][j] + GS[i][2] * M[2][j]);
+    double GR[3][3];
+    for (int j = 0; j < 3; ++j) {
+        double acc = 0.0;
+        for (int i = 0; i < 3; ++i) { acc += GM[i][j] * R[i][j]; GR[i][j] = GM[i][j] * s[j]; }
+        gs[j] += acc;
+    }
+    const double w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    double gqn[4];
+    gqn[0] = 2.0 * (-z * GR[0][1] + y * GR[0][2] + z * GR[1][0] - x * GR[1][2] - y * GR[2][0] + x * GR[2][1]);
+    gqn[1] = 2.0 * (y * GR[0][1] + z * GR[0][2] + y * GR[1][0] - 2.0 * x * GR[1][1] - w * GR[1][2] +
+                    z * GR[2][0] + w * GR[2][1] - 2.0 * x * GR[2][2]);
+    gqn[2] = 2.0 * (-2.0 * y * GR[0][0] + x * GR[0][1] + w * GR[0][2] + x * GR[1][0] + z * GR[1][2] -
+                    w * GR[2][0] + z * GR[2][1] - 2.0 * y * GR[2][2]);
+    gqn[3] = 2.0 * (-2.0 * z * GR[0][0] - w * GR[0][1] + x * GR[0][2] + w * GR[1][0] - 2.0 * z * GR[1][1] +
+                    y * GR[1][2] + x * GR[2][0] + y * GR[2][1]);
+    double dot = qn[0] * gqn[0] + qn[1] * gqn[1] + qn[2] * gqn[2] + qn[3] * gqn[3];
+    for (int k = 0; k < 4; ++k) gq[k] += (gqn[k] - qn[k] * dot) / nq;
+    /* SH colour */
+    double cpos[3], v[3];
+    for (int i = 0; i < 3; ++i)
+        cpos[i] = -(Rw[0][i] * cam_t(cam, 0) + Rw[1][i] * cam_t(cam, 1) + Rw[2][i] * cam_t(cam, 2));
+    for (int i = 0; i < 3; ++i) v[i] = mu[i] - cpos[i];
+    double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double d[3] = {v[0] / nv, v[1] / nv, v[2] / nv};
+    double Y[16], dY[16][3];
+    sh_basis(d, Y, dY);
+    double graw[3];
+    for (int c = 0; c < 3; ++c) graw[c] = rec[R_RAW_R + c] > 0.0 ? grgb[c] : 0.0;
+    double gd[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < K; ++k) {
+        double sk = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            gsh[3 * k + c] += Y[k] * graw[c];
+            sk += sh[3 * k + c] * graw[c];
+        }
+        for (int i = 0; i < 3; ++i) gd[i] += sk * dY[k][i];
+    }
+    double dd = d[0] * gd[0] + d[1] * gd[1] + d[2] * gd[2];
+    for (int i = 0; i < 3; ++i) gmu[i] += (gd[i] - d[i] * dd) / nv;
+}
+
+void orc_project_bwd(int64_t n, const double *means, const double *scales, const double *quats,
+                     const double *sh, int K, const double *cam, const double *prm, const double *rec,
+                     const double *g_mean2d, const double *g_conic, const double *g_rgb,
+                     double *g_means, double *g_scales, double *g_quats, double *g_sh)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < n; ++g)
+        project_bwd_one(means + 3 * g, scales + 3 * g, quats + 4 * g, sh + (int64_t)3 * K * g, K, cam,
+                        prm, rec + (int64_t)ORC_REC * g, g_mean2d + 2 * g, g_conic + 3 * g,
+                        g_rgb + 3 * g, g_means + 3 * g, g_scales + 3 * g, g_quats + 4 * g,
+                        g_sh + (int64_t)3 * K * g);
+}
+
+/* ------------------------------------------------------------ fusion -- */
+/* Accumulates, for one view, num[g][c] += w_g(p) F(p)[c] and
+ * den[g] += w_g(p) over the region's pixels, with w the Eq. 4 weights of
+ * the tiled forward.  fmap is indexed by region pixel (row-major), D wide. */
+void orc_fuse_view(const double *rec, const uint32_t *gids, const uint32_t *ranges,
+                   const double *cam, const double *prm, int x0, int y0, int x1, int y1,
+                   const double *fmap, int D, double *num, double *den)
+{
+    const int W = (int)cam[0], tsz = (int)prm[P_TILE];
+    const int tiles_x = (W + tsz - 1) / tsz;
+    const int rw = x1 - x0, rh = y1 - y0;
+#pragma omp parallel
+    {
+        int64_t *ci = (int64_t *)malloc(sizeof(int64_t) * ORC_MAXC);
+        double *ca = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *cT = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *cG = (double *)malloc(sizeof(double) * ORC_MAXC);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+            int px = x0 + (int)(idx % rw), py = y0 + (int)(idx / rw);
+            int tile = (py / tsz) * tiles_x + px / tsz;
+            uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+            const uint32_t *list = gids + s;
+            pix_state st;
+            int nc = composite_pixel(px + 0.5, py + 0.5, list, (int64_t)e - s, rec, NULL, 0, prm, &st,
+                                     NULL, ci, ca, cT, cG, ORC_MAXC);
+            if (nc > ORC_MAXC) nc = ORC_MAXC;
+            const double *f = fmap + (int64_t)D * idx;
+            for (int j = 0; j < nc; ++j) {
+                const uint32_t g = list[ci[j]];
+                const double w = ca[j] * cT[j];
+#pragma omp atomic
+                den[g] += w;
+                for (int c = 0; c < D; ++c) {
+#pragma omp atomic
+                    num[(int64_t)D * g + c] += w * f[c];
+                }
+            }
+        }
+        free(ci); free(ca); free(cT); free(cG);
+    }
+}
+
+/* f_g = num_g / den_g where den_g > 0, else 0 (and flag[g] = 1). */
+void orc_fuse_finalize(int64_t n, int D, const double *num, const double *den, double *out,
+                       int32_t *flag)
+{
+    for (int64_t g = 0; g < n; ++g) {
+        if (den[g] > 0.0) {
+            for (int c = 0; c < D; ++c) out[(int64_t)D * g + c] = num[(int64_t)D * g + c] / den[g];
+            flag[g] = 0;
+        } else {
+            for (int c = 0; c < D; ++c) out[(int64_t)D * g + c] = 0.0;
+            flag[g] = 1;
+        }
+    }
+}
