@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""fwd+bwd throughput of the FHGS feature-splatting hot path on GB300.
+
+Workload (one step = the whole hot path on one synthetic view):
+  1M Gaussians (means N(0, 0.6^2) clipped to [-2,2]^3, log-scales U[-5,-2],
+  SH degree 3, opacity sigmoid(N(0,1))), 512-dim BF16 features ~N(0,1),
+  one 1920x1080 pinhole camera at distance 4 (60 deg horizontal FoV),
+  upstream gradients N(0,1) on the RGB and feature images.
+  step = project (EWA + SH) -> bin + sort -> render forward (RGB + feature
+  blend) -> render backward -> projection backward.
+
+Prints one JSON line.  `value` is device-resident fwd+bwd Mpix/s of the
+tensor-core path (the FP32 CUDA-core path is reported beside it), `e2e` the
+same through the C ABI with host buffers and every copy inside the timed
+region, `roofline` the dominant kernel against the measured HBM peak, and
+`cpu_baseline` the FP64 oracle on the host cores on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpix/s at 1M Gaussians, D=512, BF16-TC vs FP32 path; % of roofline"
+UNIT = "Mpix/s"
+WORKLOAD = "1M Gaussians, 1920x1080 view, SH degree 3, D=512 BF16 features, fwd+bwd"
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--D", type=int, default=512)
+    ap.add_argument("--path", choices=["tc", "fp32", "auto"], default="auto")
+    ap.add_argument("--fp32-steps", type=int, default=3, help="timed steps of the FP32 comparison path (0 = skip)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="warm-up + one step, no JSON (for ncu)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
+                    bf16_sus=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), src="measured")
+    return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------- workload
+def make_workload(seed, n, D, dev):
+    import numpy as np
+    import torch
+    from paper_2505_19154_gb300 import synth
+    scene, cams = synth.config3(seed, n=n, D=D)
+    t = {k: torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).to(dev)
+         for k in ("means", "scales", "quats", "opacities", "sh")}
+    t["features"] = torch.from_numpy(scene["features"]).to(dev).to(torch.bfloat16)
+    P = cams[0]["width"] * cams[0]["height"]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1000 + seed)
+    t["dC"] = torch.randn((P, 3), generator=gen, device=dev)
+    t["dF"] = torch.randn((P, D), generator=gen, device=dev)
+    return scene, cams, t, P
+
+
+def algorithmic_bytes(P, N, D, I):
+    """Bytes each kernel group must move at minimum (see the roofline notes
+    in the design doc): images once, features/records once per pass, gradients
+    written once, tile instances written and read once."""
+    return {
+        "project": N * (12 + 12 + 16 + 4 + 192) + N * (48 + 16 + 8),
+        "bin_sort": 24 * I,
+        "render_fwd": P * (4 * D + 20) + N * (2 * D + 48),
+        "render_bwd": P * (4 * D + 20) + N * (2 * D + 48) + N * (4 * D + 48),
+        "project_bwd": N * (236 + 48) + N * (48 + 236),
+    }
+
+
+def run_ours(args):
+    import torch
+    from paper_2505_19154_gb300 import api
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, cams, t, P = make_workload(rank, args.n, args.D, dev)
+    path = {"tc": api.PATH_TC, "fp32": api.PATH_FP32, "auto": api.PATH_AUTO}[args.path]
+    rast = api.Rasterizer(local, sh_degree=3, path=path)
+    g = (t["means"], t["scales"], t["quats"], t["opacities"], t["sh"])
+    st0 = rast.prepare(*g, cams)                      # sizes the instance buffer
+    I = st0["n_instances"]
+    rast.capacity = int(I * 1.05) + 1024
+    del st0
+
+    def step(rr):
+        st = rr.prepare(*g, cams, check=False)
+        rgb, feat = rr.forward(st, t["features"])
+        grads = rr.backward(st, t["dC"], t["dF"])
+        return st, rgb, feat, grads
+
+    for _ in range(max(args.warmup, 1)):
+        step(rast)
+    torch.cuda.synchronize()
+    status = rast.ctx.sync_status()
+    if status != api.OK:
+        raise RuntimeError(f"device status {status} after warm-up")
+    if args.profile_only:
+        step(rast)
+        torch.cuda.synchronize()
+        return
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(rr, K, with_profile):
+        clocks = ClockSampler(local)
+        if with_profile:
+            rr.ctx.profile(True)
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        n0 = api.Context.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            step(rr)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        launches = api.Context.launch_count() - n0
+        ck = clocks.stop()
+        ms = e0.elapsed_time(e1) / K
+        prof = rr.ctx.profile_read() if with_profile else {}
+        if with_profile:
+            rr.ctx.profile(False)
+        if world > 1:
+            x = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+            ms = float(x.item())
+        return ms, prof, launches, ck
+
+    K = args.steps
+    ms, prof, launches, clocks = timed(rast, K, True)
+    if rast.ctx.sync_status() != api.OK:
+        raise RuntimeError("device status after timed region")
+    value = P * world / (ms * 1e-3) / 1e6
+    used_tc = any(k.endswith("_tc") for k in prof)
+
+    # kernel-level roofline: the dominant kernel group, algorithmic bytes / its mean duration
+    peaks = load_peaks()
+    N, D = args.n, args.D
+    algo = algorithmic_bytes(P, N, D, I)
+    per = {}
+    for name, (cnt, tot) in prof.items():
+        base = name.replace("_tc", "").replace("_fp32", "")
+        per[name] = dict(launches=cnt, ms=tot / max(cnt, 1), share=tot / max(1e-9, sum(v[1] for v in prof.values())),
+                         bytes=algo.get(base))
+    dom = max(per, key=lambda k: per[k]["ms"] * per[k]["launches"]) if per else None
+    roof = None
+    if dom and per[dom]["bytes"]:
+        ach = per[dom]["bytes"] / (per[dom]["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peaks["hbm"], "unit": "GB/s",
+                "frac": round(ach / peaks["hbm"], 4), "traffic": None,
+                "peak_source": peaks["src"] + " (MEASURED_PEAKS.json hbm_gbs)" if peaks["src"] == "measured" else "fallback"}
+
+    # FP32 CUDA-core path on the same inputs (the baseline the TC path must beat)
+    fp32 = None
+    if args.fp32_steps > 0 and used_tc:
+        r32 = api.Rasterizer(local, sh_degree=3, path=api.PATH_FP32)
+        r32.capacity = rast.capacity
+        step(r32)
+        torch.cuda.synchronize()
+        ms32, prof32, _, _ = timed(r32, args.fp32_steps, True)
+        fp32 = {"value": round(P * world / (ms32 * 1e-3) / 1e6, 2), "ms_per_step": round(ms32, 3),
+                "kernels_ms": {k: round(v[1] / max(v[0], 1), 3) for k, v in prof32.items()}}
+        del r32
+
+    # end to end through the C ABI with host buffers: H2D of every input and
+    # D2H of every output inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        names_in = ["means", "scales", "quats", "opacities", "sh", "features", "dC", "dF"]
+        h_in = {k: t[k].cpu().pin_memory() for k in names_in}
+        d_in = {k: torch.empty_like(t[k]) for k in names_in}
+        st, rgb, feat, grads = step(rast)
+        outs = [rgb, feat] + [v for v in grads.values() if v is not None]
+        h_out = [o.cpu().pin_memory() for o in outs]
+        bi = sum(v.numel() * v.element_size() for v in h_in.values())
+        bo = sum(v.numel() * v.element_size() for v in h_out)
+
+        def e2e_step():
+            for k in names_in:
+                d_in[k].copy_(h_in[k], non_blocking=True)
+            gg = (d_in["means"], d_in["scales"], d_in["quats"], d_in["opacities"], d_in["sh"])
+            s2 = rast.prepare(*gg, cams, check=False)
+            rg, ft = rast.forward(s2, d_in["features"])
+            gr = rast.backward(s2, d_in["dC"], d_in["dF"])
+            for o, ho in zip([rg, ft] + [v for v in gr.values() if v is not None], h_out):
+                ho.copy_(o, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        Ke = max(3, min(K, 10))
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(Ke):
+            e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        mse = e0.elapsed_time(e1) / Ke
+        if world > 1:
+            x = torch.tensor([mse], device=dev)
+            torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+            mse = float(x.item())
+        e2e = {"value": round(P * world / (mse * 1e-3) / 1e6, 2), "unit": UNIT, "ms_per_step": round(mse, 3),
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(scene, cams, args.D, max_seconds=25.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if used_tc else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": N, "width": 1920, "height": 1080, "feature_dim": D,
+                       "sh_degree": 3, "path": "tc" if used_tc else "fp32", "tile_instances": I,
+                       "l2": "inputs larger than L2 (features 1 GB, dL/dfeat 4.2 GB)",
+                       "parallelism": f"independent views, {world} GPU(s)"},
+            "roofline": roof, "kernels": per, "fp32_path": fp32, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clocks, "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(scene, cams, D, seed=0):
+    """One bounded oracle sample of the same workload: projection and FP32
+    binning of every Gaussian, per-tile lists of the 64x64 crop's tiles,
+    FP64 forward + backward of the crop's 4096 pixels."""
+    import numpy as np
+    import oracle
+    from paper_2505_19154_gb300 import synth
+    x0, y0, x1, y1 = synth.CROP3
+    prm = dict(sh_degree=3)
+    dC, dF = synth.upstream(seed, (x1 - x0) * (y1 - y0), D)
+    prep = oracle.prepare(scene, cams, prm, tile_rect=(x0 // 16, y0 // 16, (x1 - 1) // 16, (y1 - 1) // 16))
+    oracle.forward(scene, cams, prm, scene["features"], region=synth.CROP3, prep=prep)
+    oracle.backward(scene, cams, prm, scene["features"], [dC], [dF], region=synth.CROP3, prep=prep)
+    return (x1 - x0) * (y1 - y0)
+
+
+def cpu_baseline(scene, cams, D, max_seconds=25.0, reps_max=3):
+    import oracle
+    t0 = time.time()
+    reps, px = 0, 0
+    while reps < reps_max and (reps == 0 or time.time() - t0 < max_seconds / 2):
+        px += oracle_sample(scene, cams, D)
+        reps += 1
+    dt = time.time() - t0
+    return {"value": round(px / dt / 1e6, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{reps} x (project + FP32-spec binning of all {len(scene['means'])} Gaussians, "
+                      f"lists of the 64x64 crop's tiles, FP64 fwd+bwd of its 4096 pixels, D={D})",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2505_19154_gb300 import synth
+    scene, cams = synth.config3(0, n=args.n, D=args.D)
+    import oracle
+    for _ in range(args.warmup):
+        oracle_sample(scene, cams, args.D)
+    t0 = time.time()
+    px = 0
+    for _ in range(args.steps):
+        px += oracle_sample(scene, cams, args.D)
+    dt = time.time() - t0
+    v = px / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / max(args.steps, 1), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": args.n, "width": 1920, "height": 1080,
+                       "feature_dim": args.D, "sample": "64x64 crop per step"},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": round(v, 6),
+                             "sample": "each step: project + FP32-spec binning of all Gaussians, lists of the "
+                                       "64x64 crop's tiles, FP64 fwd+bwd of its 4096 pixels"},
+            "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

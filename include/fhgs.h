@@ -1,0 +1,225 @@
+/*
+ * fhgs.h -- C ABI of libfhgs.so, the GB300 (sm_103a) hot path of FHGS
+ * feature splatting (arXiv 2505.19154).
+ *
+ * The library renders 3-D Gaussians that each carry an RGB colour (SH) and a
+ * D-dimensional feature, with the tile-based depth-sorted rasterizer the
+ * paper builds on (App. A), the front-to-back compositing of Eq. 4 applied to
+ * colour and feature (the DRF path of Sec. 3.2), its hand-written derivative
+ * (App. A.2), and the compositing-weight-normalised fusion of 2-D feature
+ * maps into per-Gaussian features (Sec. 3.1).
+ *
+ * Conventions shared by every call
+ *   - Every pointer marked "device" is caller-owned CUDA device memory; the
+ *     library never allocates, frees or retains caller buffers.  Scratch that
+ *     the library needs is owned by the context (fhgs_ctx) and grows on
+ *     demand; fhgs_reserve() pre-sizes it (required before stream capture).
+ *   - Host arrays (cameras, params, the fusion map pointer table) are read
+ *     during the call only.
+ *   - Every call is asynchronous on the given CUDA stream (cudaStream_t,
+ *     passed as void*; NULL = legacy default stream) and returns an
+ *     fhgs_status.  Errors that the host can see (bad sizes, NULL pointers,
+ *     unsupported options, misaligned pointers) return immediately and
+ *     launch nothing.  Errors found on the device (instance-buffer overflow,
+ *     a bounded wait that ran out, non-finite inputs) latch into the
+ *     context's device status word; fhgs_sync_status() synchronises the
+ *     stream and reports them.  fhgs_last_error() gives a message.
+ *   - Arrays are dense and row-major.  Images of several cameras are packed
+ *     one after the other: camera c's pixel (x, y) is row
+ *     pix_offset(c) + y * width(c) + x, pix_offset(c) = sum_{c'<c} W*H.
+ *   - Tiles are 16 x 16 pixels (App. A).  The global tile id of camera c's
+ *     tile (tx, ty) is tile_offset(c) + ty * ceil(W/16) + tx,
+ *     tile_offset(c) = sum_{c'<c} ceil(W/16) * ceil(H/16).
+ */
+#ifndef FHGS_H
+#define FHGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FHGS_ABI_VERSION 1
+#define FHGS_MAX_CAMS 32 /* cameras per call */
+#define FHGS_MAX_SH_DEGREE 3
+
+typedef enum fhgs_status {
+    FHGS_OK = 0,
+    FHGS_ERR_INVALID_ARG = 1,  /* NULL pointer, negative size, bad camera */
+    FHGS_ERR_UNSUPPORTED = 2,  /* D % 8 != 0, sh_degree > 3, tile != 16x16, too many cameras */
+    FHGS_ERR_ALIGNMENT = 3,    /* a pointer that needs 16-byte alignment is not */
+    FHGS_ERR_CUDA = 4,         /* a CUDA runtime call failed (see fhgs_last_error) */
+    FHGS_ERR_CAPACITY = 5,     /* more tile instances than the buffer holds */
+    FHGS_ERR_TIMEOUT = 6,      /* a bounded device-side wait ran out */
+    FHGS_ERR_NUMERIC = 7,      /* non-finite input values were found (and culled) */
+    FHGS_ERR_NO_DEVICE = 8     /* no CUDA device, or not an sm_103 GPU */
+} fhgs_status;
+
+typedef struct fhgs_ctx fhgs_ctx;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  world_to_cam is
+ * the 3x4 matrix [R|t] row by row: x_cam = R x_world + t (the matrix W of
+ * Eq. 3).  width, height >= 1; fx, fy > 0. */
+typedef struct fhgs_camera {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float world_to_cam[12];
+} fhgs_camera;
+
+/* Rasterizer parameters.  The paper fixes the tile size (16x16, App. A); it
+ * gives no value for the others, which take the 3DGS-family defaults set by
+ * fhgs_default_params(). */
+typedef struct fhgs_params {
+    int32_t tile_w, tile_h;  /* must be 16, 16 */
+    int32_t sh_degree;       /* 0..3; sh holds (sh_degree+1)^2 coefficients per channel */
+    int32_t path;            /* FHGS_PATH_* : which render kernels run */
+    int32_t batch;           /* Gaussians per batch in the tensor-core kernels; 0 = auto */
+    int32_t d_split;         /* feature columns per CTA in the tensor-core kernels; 0 = auto */
+    float znear;             /* cull if view depth <= znear (0.2) */
+    float dilation;          /* added to the screen covariance diagonal (0.3 px^2) */
+    float alpha_min;         /* skip a Gaussian at a pixel if alpha < alpha_min (1/255) */
+    float alpha_max;         /* alpha = min(alpha_max, op * G) (0.99) */
+    float t_eps;             /* stop before a Gaussian that takes T below t_eps (1e-4) */
+    float cutoff_sq;         /* skip a pixel outside the ellipse q2 > cutoff_sq (9) */
+    float fov_clamp;         /* Jacobian uses x/z clamped to +-fov_clamp*W/(2 fx) (1.3) */
+    float bg[3];             /* background colour behind the remaining transmittance */
+} fhgs_params;
+
+enum {
+    FHGS_PATH_AUTO = 0, /* tensor-core feature blend when D > 0 and features are BF16 */
+    FHGS_PATH_FP32 = 1, /* plain FP32 per-pixel loop on the CUDA cores */
+    FHGS_PATH_TC = 2    /* BF16 x BF16 -> FP32 blend on tcgen05 tensor cores (BF16 only) */
+};
+
+typedef enum fhgs_dtype { FHGS_F32 = 0, FHGS_BF16 = 1 } fhgs_dtype;
+
+/* The Gaussian parameters of Eq. 1 in their 3-D (EWA) form; all device,
+ * float32, n rows.  means [n][3]; scales [n][3] (linear, > 0); quats [n][4]
+ * (w, x, y, z), normalised inside; opacities [n] in [0, 1] (already
+ * activated); sh [n][(sh_degree+1)^2][3]. */
+typedef struct fhgs_gaussians {
+    const float *means, *scales, *quats, *opacities, *sh;
+    int64_t n;
+} fhgs_gaussians;
+
+/* Depth-sorted per-tile lists produced by fhgs_bin_sort (App. A: Duplicate-
+ * WithKeys, SortByKeys, IdentifyTileRanges).  All device, caller-owned.
+ *   gids      [capacity]      Gaussian index of each tile instance, sorted by
+ *                             (global tile id, depth, Gaussian index).
+ *   keys      [capacity]      nullable; the 64-bit sort key of each instance:
+ *                             global tile id << 32 | IEEE bits of the view
+ *                             depth (positive, so the bits order like depth).
+ *   ranges    [total_tiles][2] [start, end) of each tile's run in gids.
+ *   n_instances [1]            number of instances emitted (may exceed
+ *                             capacity; then FHGS_ERR_CAPACITY is latched). */
+typedef struct fhgs_bins {
+    uint32_t *gids;
+    uint64_t *keys;
+    uint32_t *ranges;
+    int64_t *n_instances;
+    int64_t capacity;
+} fhgs_bins;
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on CUDA device `device` (made current for the call).
+ * Fails with FHGS_ERR_NO_DEVICE if the device is absent or not sm_103. */
+fhgs_status fhgs_create(fhgs_ctx **ctx, int device);
+void fhgs_destroy(fhgs_ctx *ctx);
+const char *fhgs_last_error(const fhgs_ctx *ctx);
+const char *fhgs_status_string(fhgs_status s);
+int fhgs_abi_version(void);
+void fhgs_default_params(fhgs_params *p);
+
+/* Bytes of the per-(camera, Gaussian) projection buffer that fhgs_project
+ * fills; the caller allocates it (16-byte aligned) and passes it on. */
+int64_t fhgs_proj_bytes(int64_t n, int n_cams);
+/* Number of tiles over all cameras (rows of fhgs_bins.ranges). */
+int64_t fhgs_total_tiles(const fhgs_camera *cams, int n_cams);
+/* Pre-size the context's scratch for up to max_n Gaussians x n_cams cameras
+ * and max_instances tile instances, so later calls allocate nothing. */
+fhgs_status fhgs_reserve(fhgs_ctx *ctx, int64_t max_n, int n_cams, int64_t max_instances);
+/* Synchronise `stream`, then read and clear the context's device status
+ * word.  Returns the first latched device-side error, or FHGS_OK. */
+fhgs_status fhgs_sync_status(fhgs_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------------ hot path ---- */
+/* EWA projection of every Gaussian into every camera and its SH
+ * colour (Sec. 2.1 / App. A "Homogenization, 2DScreenGaussians").  Writes
+ * the opaque projection buffer `proj` (fhgs_proj_bytes(n, n_cams) bytes):
+ * screen mean, conic, opacity, colour, tile rectangle and depth key per
+ * (camera, Gaussian).  Binning decisions follow the FP32 binning
+ * specification exactly (single-rounded binary32 operations in a fixed
+ * order).  Non-finite inputs are culled and latch FHGS_ERR_NUMERIC. */
+fhgs_status fhgs_project(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhgs_camera *cams, int n_cams,
+                         const fhgs_params *p, void *proj, void *stream);
+
+/* Duplicate each projected Gaussian into every 16x16 tile its
+ * rectangle overlaps, sort the instances by (global tile id, depth,
+ * Gaussian index) and find each tile's range (App. A).  Fills `bins`;
+ * bins->keys may be NULL.  Uses context scratch. */
+fhgs_status fhgs_bin_sort(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_camera *cams, int n_cams,
+                          const fhgs_params *p, const fhgs_bins *bins, void *stream);
+
+/* Front-to-back compositing (Eq. 4) per tile of colour and features.
+ *   features [n][D] device, FHGS_F32 or FHGS_BF16 (D % 8 == 0; D may be 0 and
+ *            features NULL for colour only).  FHGS_PATH_TC needs BF16.
+ *   rgb      [P][3]  out: sum_i w_i c_i + T_final * bg
+ *   feat     [P][D]  out, nullable: sum_i w_i f_i (no background)
+ *   T_final  [P]     out: transmittance after the last contributor
+ *   last     [P]     out: (position in the tile's list of the last
+ *                    contributor) + 1, 0 if none
+ * P = total pixels of all cameras.  The tensor-core path rounds w_i to
+ * BF16 for the feature blend and accumulates in FP32. */
+fhgs_status fhgs_render_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_bins *bins,
+                            const void *features, fhgs_dtype ftype, int D, const fhgs_camera *cams,
+                            int n_cams, const fhgs_params *p, float *rgb, float *feat, float *T_final,
+                            int32_t *last, void *stream);
+
+/* Derivative of L = sum_p grad_rgb[p] . rgb[p] + grad_feat[p] . feat[p]
+ * (App. A.2: dL/dalpha_k = T_k dL/dw_k - (1/(1-alpha_k)) sum_{i>k} w_i
+ * dL/dw_i, plus the background term), walking each tile back to front and
+ * recovering T by division from T_final.  All gradient outputs are
+ * OVERWRITTEN (not accumulated), device float32 with the shapes of the
+ * inputs: grad_means [n][3], grad_scales [n][3], grad_quats [n][4],
+ * grad_opac [n], grad_sh [n][K][3], grad_features [n][D] (nullable: skips
+ * that contraction).  grad_feat may be NULL (treated as zero). */
+fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *proj, const fhgs_bins *bins,
+                            const void *features, fhgs_dtype ftype, int D, const fhgs_camera *cams,
+                            int n_cams, const fhgs_params *p, const float *T_final, const int32_t *last,
+                            const float *grad_rgb, const float *grad_feat, float *grad_means,
+                            float *grad_scales, float *grad_quats, float *grad_opac, float *grad_sh,
+                            float *grad_features, void *stream);
+
+/* Non-differentiable feature fusion (Sec. 3.1, with the per-primitive
+ * feature defined as the compositing-weight-normalised scatter over views):
+ *   num[g][c] += sum_{v,p} w_g(v,p) maps[v][p][c],  den[g] += sum w_g(v,p),
+ * with w the Eq. 4 weights of the forward render of view v.  maps is a HOST
+ * array of n_views DEVICE pointers, each [H_v*W_v][D] float32.
+ * flags: FHGS_FUSE_ACCUMULATE keeps num/den (else they are zeroed first);
+ * FHGS_FUSE_FINALIZE then writes out[g][c] = num/den where den > 0, else 0;
+ * FHGS_FUSE_NORMALIZE additionally L2-normalises each non-zero out row.
+ * out may be NULL unless FINALIZE is set.  Uses context scratch; views are
+ * processed one at a time. */
+enum { FHGS_FUSE_ACCUMULATE = 1, FHGS_FUSE_FINALIZE = 2, FHGS_FUSE_NORMALIZE = 4 };
+fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhgs_camera *views, int n_views,
+                               const float *const *maps, int D, const fhgs_params *p, float *num,
+                               float *den, float *out, uint32_t flags, void *stream);
+
+/* ----------------------------------------------------- instrumentation -- */
+/* Kernel timing: while enabled, every kernel group the context launches is
+ * bracketed by CUDA events recorded on the launch stream (a pool of 8192
+ * events, created when first enabled).  fhgs_profile_read synchronises on
+ * the recorded events, writes a JSON object {"name": [launches, total_ms],
+ * ...} into buf (NUL-terminated, truncated to len) and clears the records.
+ * Timing adds one event record before and after each launch. */
+fhgs_status fhgs_profile_enable(fhgs_ctx *ctx, int enable);
+fhgs_status fhgs_profile_read(fhgs_ctx *ctx, char *buf, int64_t len);
+/* Number of kernels this library has launched in this process. */
+int64_t fhgs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHGS_H */

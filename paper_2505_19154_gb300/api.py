@@ -1,0 +1,349 @@
+"""Python binding of libfhgs.so (include/fhgs.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch supplies device memory, streams and autograd wiring.
+If the library is missing the calls raise; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+import torch
+
+from . import _build
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_ALIGNMENT, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NUMERIC, \
+    ERR_NO_DEVICE = range(9)
+PATH_AUTO, PATH_FP32, PATH_TC = 0, 1, 2
+F32, BF16 = 0, 1
+FUSE_ACCUMULATE, FUSE_FINALIZE, FUSE_NORMALIZE = 1, 2, 4
+MAX_CAMS = 32
+
+EXPORTS = ["fhgs_create", "fhgs_destroy", "fhgs_last_error", "fhgs_status_string", "fhgs_abi_version",
+           "fhgs_default_params", "fhgs_proj_bytes", "fhgs_total_tiles", "fhgs_reserve", "fhgs_sync_status",
+           "fhgs_project", "fhgs_bin_sort", "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features",
+           "fhgs_profile_enable", "fhgs_profile_read", "fhgs_launch_count"]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("world_to_cam", ctypes.c_float * 12)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("batch", ctypes.c_int32), ("d_split", ctypes.c_int32),
+                ("znear", ctypes.c_float), ("dilation", ctypes.c_float), ("alpha_min", ctypes.c_float),
+                ("alpha_max", ctypes.c_float), ("t_eps", ctypes.c_float), ("cutoff_sq", ctypes.c_float),
+                ("fov_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3)]
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class Bins(ctypes.Structure):
+    _fields_ = [("gids", ctypes.c_void_p), ("keys", ctypes.c_void_p), ("ranges", ctypes.c_void_p),
+                ("n_instances", ctypes.c_void_p), ("capacity", ctypes.c_int64)]
+
+
+class FhgsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fhgs status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libfhgs.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libfhgs.so is not built ({_build.LIB}); run __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        vp, i32, i64, f32p = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+        L.fhgs_create.argtypes = [ctypes.POINTER(vp), i32]
+        L.fhgs_destroy.argtypes = [vp]
+        L.fhgs_destroy.restype = None
+        L.fhgs_last_error.argtypes = [vp]
+        L.fhgs_last_error.restype = ctypes.c_char_p
+        L.fhgs_status_string.argtypes = [i32]
+        L.fhgs_status_string.restype = ctypes.c_char_p
+        L.fhgs_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.fhgs_default_params.restype = None
+        L.fhgs_proj_bytes.argtypes = [i64, i32]
+        L.fhgs_proj_bytes.restype = i64
+        L.fhgs_total_tiles.argtypes = [ctypes.POINTER(Camera), i32]
+        L.fhgs_total_tiles.restype = i64
+        L.fhgs_reserve.argtypes = [vp, i64, i32, i64]
+        L.fhgs_sync_status.argtypes = [vp, vp]
+        L.fhgs_project.argtypes = [vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), i32,
+                                   ctypes.POINTER(Params), vp, vp]
+        L.fhgs_bin_sort.argtypes = [vp, i64, vp, ctypes.POINTER(Camera), i32, ctypes.POINTER(Params),
+                                    ctypes.POINTER(Bins), vp]
+        L.fhgs_render_fwd.argtypes = [vp, i64, vp, ctypes.POINTER(Bins), vp, i32, i32, ctypes.POINTER(Camera), i32,
+                                      ctypes.POINTER(Params), f32p, f32p, f32p, vp, vp]
+        L.fhgs_render_bwd.argtypes = [vp, ctypes.POINTER(Gaussians), vp, ctypes.POINTER(Bins), vp, i32, i32,
+                                      ctypes.POINTER(Camera), i32, ctypes.POINTER(Params), f32p, vp, f32p, f32p,
+                                      f32p, f32p, f32p, f32p, f32p, f32p, vp]
+        L.fhgs_fuse_features.argtypes = [vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), i32,
+                                         ctypes.POINTER(ctypes.c_void_p), i32, ctypes.POINTER(Params), f32p, f32p,
+                                         f32p, ctypes.c_uint32, vp]
+        L.fhgs_profile_enable.argtypes = [vp, i32]
+        L.fhgs_profile_read.argtypes = [vp, ctypes.c_char_p, i64]
+        L.fhgs_launch_count.argtypes = []
+        L.fhgs_launch_count.restype = i64
+        for name in ("fhgs_create", "fhgs_reserve", "fhgs_sync_status", "fhgs_project", "fhgs_bin_sort",
+                     "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features", "fhgs_profile_enable",
+                     "fhgs_profile_read"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def make_params(sh_degree: int = 0, path: int = PATH_AUTO, bg=(0.0, 0.0, 0.0), **kw) -> Params:
+    p = Params()
+    lib().fhgs_default_params(ctypes.byref(p))
+    p.sh_degree = int(sh_degree)
+    p.path = int(path)
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    p.bg[0], p.bg[1], p.bg[2] = (float(b) for b in bg)
+    return p
+
+
+def make_cameras(cams: Sequence[dict]):
+    """Camera dicts (width, height, fx, fy, cx, cy, w2c 3x4) to a C array.
+    Values are rounded to float32 exactly as the oracle's FP32 spec does."""
+    arr = (Camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i].width, arr[i].height = int(c["width"]), int(c["height"])
+        arr[i].fx, arr[i].fy = float(np.float32(c["fx"])), float(np.float32(c["fy"]))
+        arr[i].cx, arr[i].cy = float(np.float32(c["cx"])), float(np.float32(c["cy"]))
+        w = np.asarray(c["w2c"], np.float64).reshape(-1).astype(np.float32)
+        for k in range(12):
+            arr[i].world_to_cam[k] = float(w[k])
+    return arr
+
+
+class Context:
+    """An fhgs_ctx on one CUDA device, with thin wrappers of every ABI call."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        s = lib().fhgs_create(ctypes.byref(h), self.device)
+        if s != OK:
+            raise FhgsError(s, lib().fhgs_status_string(s).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fhgs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, s: int):
+        if s != OK:
+            raise FhgsError(s, lib().fhgs_last_error(self.h).decode())
+
+    @staticmethod
+    def stream_ptr(stream=None):
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return ctypes.c_void_p(st.cuda_stream)
+
+    # --------------------------------------------------------- instrumentation
+    def profile(self, enable: bool = True):
+        self.check(lib().fhgs_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self.check(lib().fhgs_profile_read(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    @staticmethod
+    def launch_count() -> int:
+        return int(lib().fhgs_launch_count())
+
+    # --------------------------------------------------------------- calls
+    def reserve(self, max_n: int, n_cams: int, max_instances: int):
+        self.check(lib().fhgs_reserve(self.h, int(max_n), int(n_cams), int(max_instances)))
+
+    def sync_status(self, stream=None) -> int:
+        return lib().fhgs_sync_status(self.h, self.stream_ptr(stream))
+
+    def project(self, g: Gaussians, cams, params: Params, proj: torch.Tensor, stream=None):
+        self.check(lib().fhgs_project(self.h, ctypes.byref(g), cams, len(cams), ctypes.byref(params), _ptr(proj),
+                                      self.stream_ptr(stream)))
+
+    def bin_sort(self, n: int, proj, cams, params, bins: Bins, stream=None):
+        self.check(lib().fhgs_bin_sort(self.h, int(n), _ptr(proj), cams, len(cams), ctypes.byref(params),
+                                       ctypes.byref(bins), self.stream_ptr(stream)))
+
+    def render_fwd(self, n, proj, bins, features, D, cams, params, rgb, feat, T, last, stream=None):
+        ft = BF16 if (features is not None and features.dtype == torch.bfloat16) else F32
+        self.check(lib().fhgs_render_fwd(self.h, int(n), _ptr(proj), ctypes.byref(bins), _ptr(features), ft, int(D),
+                                         cams, len(cams), ctypes.byref(params), _ptr(rgb), _ptr(feat), _ptr(T),
+                                         _ptr(last), self.stream_ptr(stream)))
+
+    def render_bwd(self, g, proj, bins, features, D, cams, params, T, last, grgb, gfeat, out: dict, stream=None):
+        ft = BF16 if (features is not None and features.dtype == torch.bfloat16) else F32
+        self.check(lib().fhgs_render_bwd(self.h, ctypes.byref(g), _ptr(proj), ctypes.byref(bins), _ptr(features),
+                                         ft, int(D), cams, len(cams), ctypes.byref(params), _ptr(T), _ptr(last),
+                                         _ptr(grgb), _ptr(gfeat), _ptr(out["means"]), _ptr(out["scales"]),
+                                         _ptr(out["quats"]), _ptr(out["opacities"]), _ptr(out["sh"]),
+                                         _ptr(out.get("features")), self.stream_ptr(stream)))
+
+    def fuse(self, g, views, maps: Sequence[torch.Tensor], D, params, num, den, out, flags, stream=None):
+        ptrs = (ctypes.c_void_p * max(1, len(maps)))(*[m.data_ptr() for m in maps])
+        self.check(lib().fhgs_fuse_features(self.h, ctypes.byref(g), views, len(views), ptrs, int(D),
+                                            ctypes.byref(params), _ptr(num), _ptr(den), _ptr(out), int(flags),
+                                            self.stream_ptr(stream)))
+
+
+def gaussians_struct(means, scales, quats, opacities, sh) -> Gaussians:
+    g = Gaussians()
+    g.means, g.scales, g.quats = means.data_ptr(), scales.data_ptr(), quats.data_ptr()
+    g.opacities, g.sh, g.n = opacities.data_ptr(), sh.data_ptr(), means.shape[0]
+    return g
+
+
+def _contig(t, dtype=torch.float32):
+    return t.detach().to(dtype).contiguous()
+
+
+class Rasterizer:
+    """Forward/backward of the hot path on one device, keeping the buffers
+    (projection, tile lists, instance capacity) between calls."""
+
+    def __init__(self, device: int = 0, sh_degree: int = 0, path: int = PATH_AUTO, bg=(0.0, 0.0, 0.0),
+                 keep_keys: bool = False, **params):
+        self.ctx = Context(device)
+        self.dev = torch.device("cuda", device)
+        self.params = make_params(sh_degree=sh_degree, path=path, bg=bg, **params)
+        self.keep_keys = keep_keys
+        self.capacity = 0
+
+    def set_path(self, path: int):
+        self.params.path = int(path)
+
+    # --------------------------------------------------------------- steps
+    def prepare(self, means, scales, quats, opacities, sh, cams: Sequence[dict], capacity: int | None = None,
+                check: bool = True) -> dict:
+        """Projection + binning.  Returns the state the render calls use."""
+        ccams = make_cameras(cams)
+        n = int(means.shape[0])
+        g = gaussians_struct(means, scales, quats, opacities, sh)
+        total_tiles = int(lib().fhgs_total_tiles(ccams, len(cams)))
+        proj = torch.empty(int(lib().fhgs_proj_bytes(n, len(cams))), dtype=torch.uint8, device=self.dev)
+        self.ctx.project(g, ccams, self.params, proj)
+        if capacity is not None:
+            self.capacity = max(self.capacity, int(capacity))
+        if self.capacity == 0:
+            self.capacity = max(1024, 16 * n * len(cams))
+        while True:
+            st = dict(n=n, g=g, cams=ccams, ncam=len(cams), proj=proj, total_tiles=total_tiles,
+                      gids=torch.empty(self.capacity, dtype=torch.int32, device=self.dev),
+                      keys=torch.empty(self.capacity, dtype=torch.int64, device=self.dev) if self.keep_keys else None,
+                      ranges=torch.empty((total_tiles, 2), dtype=torch.int32, device=self.dev),
+                      count=torch.zeros(1, dtype=torch.int64, device=self.dev))
+            st["bins"] = Bins(st["gids"].data_ptr(), _ptr(st["keys"]).value if st["keys"] is not None else None,
+                              st["ranges"].data_ptr(), st["count"].data_ptr(), self.capacity)
+            self.ctx.bin_sort(n, proj, ccams, self.params, st["bins"])
+            if not check:
+                return st
+            cnt = int(st["count"].item())
+            if cnt <= self.capacity:
+                self.ctx.sync_status()  # clears a latched overflow from an earlier try
+                st["n_instances"] = cnt
+                return st
+            self.capacity = int(cnt * 1.25) + 1024
+
+    def forward(self, st: dict, features, cams: Sequence[dict] | None = None, want_feat: bool = True):
+        P = sum(int(c.width) * int(c.height) for c in st["cams"])
+        D = 0 if features is None else int(features.shape[1])
+        rgb = torch.empty((P, 3), dtype=torch.float32, device=self.dev)
+        feat = torch.empty((P, D), dtype=torch.float32, device=self.dev) if (D and want_feat) else None
+        T = torch.empty(P, dtype=torch.float32, device=self.dev)
+        last = torch.empty(P, dtype=torch.int32, device=self.dev)
+        self.ctx.render_fwd(st["n"], st["proj"], st["bins"], features, D if feat is not None else 0, st["cams"],
+                            self.params, rgb, feat, T, last)
+        st.update(T=T, last=last, features=features, D=D)
+        return rgb, feat
+
+    def backward(self, st: dict, grad_rgb, grad_feat, want_feat_grad: bool = True) -> dict:
+        n, D = st["n"], st["D"]
+        K = (self.params.sh_degree + 1) ** 2
+        out = dict(means=torch.empty((n, 3), device=self.dev), scales=torch.empty((n, 3), device=self.dev),
+                   quats=torch.empty((n, 4), device=self.dev), opacities=torch.empty(n, device=self.dev),
+                   sh=torch.empty((n, K, 3), device=self.dev),
+                   features=torch.empty((n, D), device=self.dev) if (D and want_feat_grad) else None)
+        self.ctx.render_bwd(st["g"], st["proj"], st["bins"], st["features"], D, st["cams"], self.params, st["T"],
+                            st["last"], grad_rgb.contiguous(),
+                            None if grad_feat is None else grad_feat.contiguous(), out)
+        return out
+
+    def fuse(self, means, scales, quats, opacities, sh, views: Sequence[dict], maps: Sequence[torch.Tensor],
+             normalize: bool = False, num=None, den=None, accumulate: bool = False):
+        n = int(means.shape[0])
+        D = int(maps[0].shape[-1])
+        g = gaussians_struct(means, scales, quats, opacities, sh)
+        num = torch.zeros((n, D), device=self.dev) if num is None else num
+        den = torch.zeros(n, device=self.dev) if den is None else den
+        out = torch.empty((n, D), device=self.dev)
+        flags = FUSE_FINALIZE | (FUSE_NORMALIZE if normalize else 0) | (FUSE_ACCUMULATE if accumulate else 0)
+        self.ctx.fuse(g, make_cameras(views), [m.contiguous() for m in maps], D, self.params, num, den, out, flags)
+        return out, num, den
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacities, sh, features, rast, cams):
+        m, s, q, o, h = (_contig(t) for t in (means, scales, quats, opacities, sh))
+        f = None if features is None else features.detach().contiguous()
+        st = rast.prepare(m, s, q, o, h, cams)
+        rgb, feat = rast.forward(st, f)
+        ctx.rast, ctx.st = rast, st
+        ctx.keep = (m, s, q, o, h, f)
+        ctx.has_feat = f is not None
+        return rgb, feat if feat is not None else torch.zeros(0, device=rgb.device)
+
+    @staticmethod
+    def backward(ctx, grad_rgb, grad_feat):
+        rast, st = ctx.rast, ctx.st
+        gf = grad_feat if (ctx.has_feat and grad_feat is not None and grad_feat.numel()) else None
+        out = rast.backward(st, grad_rgb.float(), None if gf is None else gf.float(),
+                            want_feat_grad=ctx.needs_input_grad[5])
+        gfeat = out.get("features")
+        if gfeat is not None and ctx.keep[5] is not None:
+            gfeat = gfeat.to(ctx.keep[5].dtype)
+        return out["means"], out["scales"], out["quats"], out["opacities"], out["sh"], gfeat, None, None
+
+
+def render(means, scales, quats, opacities, sh, features, cams: Sequence[dict], rast: Rasterizer):
+    """Differentiable render: returns rgb [P,3] and feat [P,D] (packed over
+    cameras).  Gradients flow to every input, features included."""
+    return _RenderFn.apply(means, scales, quats, opacities, sh, features, rast, list(cams))

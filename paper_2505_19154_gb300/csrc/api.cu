@@ -1,0 +1,563 @@
+// C ABI of libfhgs.so (declared in include/fhgs.h): argument checks, context
+// scratch, camera/parameter marshalling and kernel dispatch.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fhgs_internal.cuh"
+
+using namespace fhgs;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+
+struct fhgs_ctx {
+    int device = 0;
+    bool prof = false;
+    std::vector<cudaEvent_t> pool;  // profiling events, created on first enable
+    size_t pool_next = 0;
+    std::vector<ProfRec> recs;
+    int sm_count = 0;
+    std::string err;
+    unsigned *status = nullptr;  // device status word
+    DevBuf bin;                  // binning scratch
+    DevBuf g2d;                  // per (camera, Gaussian) render gradients
+    DevBuf fuse_proj, fuse_gids, fuse_ranges, fuse_count;  // fusion view scratch
+    long long bin_cn = 0, bin_cap = 0;
+};
+
+static std::atomic<long long> g_launches{0};
+
+namespace fhgs {
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace fhgs
+
+namespace {
+
+constexpr int kRadixBlocksPerSM = 2;
+constexpr size_t kProfEvents = 8192;
+
+// Brackets one kernel group with CUDA events on its stream while profiling.
+struct Prof {
+    fhgs_ctx *ctx;
+    cudaStream_t st;
+    ProfRec *rec = nullptr;
+    Prof(fhgs_ctx *c, const char *name, cudaStream_t s) : ctx(c), st(s) {
+        if (!ctx->prof || ctx->pool_next + 2 > ctx->pool.size()) return;
+        ctx->recs.push_back({name, ctx->pool[ctx->pool_next], ctx->pool[ctx->pool_next + 1]});
+        ctx->pool_next += 2;
+        rec = &ctx->recs.back();
+        cudaEventRecord(rec->a, st);
+    }
+    ~Prof() {
+        if (rec) cudaEventRecord(rec->b, st);
+    }
+};
+
+fhgs_status fail(fhgs_ctx *ctx, fhgs_status s, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+fhgs_status cuda_fail(fhgs_ctx *ctx, cudaError_t e, const char *what) {
+    if (ctx) ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return FHGS_ERR_CUDA;
+}
+
+#define FHGS_CUDA(ctx, call)                                      \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+fhgs_status ensure(fhgs_ctx *ctx, DevBuf &b, size_t bytes) {
+    if (b.bytes >= bytes) return FHGS_OK;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree");
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    b.p = p;
+    b.bytes = bytes;
+    return FHGS_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+fhgs_status check_params(fhgs_ctx *ctx, const fhgs_params *p) {
+    if (!p) return fail(ctx, FHGS_ERR_INVALID_ARG, "params is NULL");
+    if (p->tile_w != kTile || p->tile_h != kTile)
+        return fail(ctx, FHGS_ERR_UNSUPPORTED, "only 16x16 tiles are supported");
+    if (p->sh_degree < 0 || p->sh_degree > FHGS_MAX_SH_DEGREE)
+        return fail(ctx, FHGS_ERR_UNSUPPORTED, "sh_degree must be 0..3");
+    if (!(p->alpha_max > 0.f && p->alpha_max < 1.f) || !(p->alpha_min >= 0.f) || !(p->t_eps > 0.f) ||
+        !(p->cutoff_sq > 0.f) || !(p->znear > 0.f) || !(p->dilation >= 0.f))
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "parameter out of range");
+    if (p->path < FHGS_PATH_AUTO || p->path > FHGS_PATH_TC)
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "unknown path");
+    return FHGS_OK;
+}
+
+fhgs_status make_cams(fhgs_ctx *ctx, const fhgs_camera *cams, int n_cams, CamSet &cs) {
+    if (!cams) return fail(ctx, FHGS_ERR_INVALID_ARG, "cams is NULL");
+    if (n_cams < 1) return fail(ctx, FHGS_ERR_INVALID_ARG, "n_cams must be >= 1, got " + std::to_string(n_cams));
+    if (n_cams > FHGS_MAX_CAMS) return fail(ctx, FHGS_ERR_UNSUPPORTED, "at most 32 cameras per call");
+    memset(&cs, 0, sizeof(cs));
+    cs.n = n_cams;
+    long long tiles = 0, pix = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        const fhgs_camera &c = cams[i];
+        if (c.width < 1 || c.height < 1 || !(c.fx > 0.f) || !(c.fy > 0.f) || !std::isfinite(c.cx) ||
+            !std::isfinite(c.cy))
+            return fail(ctx, FHGS_ERR_INVALID_ARG, "camera " + std::to_string(i) + " is invalid");
+        for (int k = 0; k < 12; ++k)
+            if (!std::isfinite(c.world_to_cam[k]))
+                return fail(ctx, FHGS_ERR_INVALID_ARG, "camera " + std::to_string(i) + " has a non-finite pose");
+        DevCam &d = cs.c[i];
+        d.W = c.width;
+        d.H = c.height;
+        d.tiles_x = (c.width + kTile - 1) / kTile;
+        d.tiles_y = (c.height + kTile - 1) / kTile;
+        d.tile_off = (int)tiles;
+        d.pix_off = pix;
+        d.fx = c.fx;
+        d.fy = c.fy;
+        d.cx = c.cx;
+        d.cy = c.cy;
+        for (int r = 0; r < 3; ++r) {
+            for (int k = 0; k < 3; ++k) d.R[3 * r + k] = c.world_to_cam[4 * r + k];
+            d.t[r] = c.world_to_cam[4 * r + 3];
+        }
+        for (int k = 0; k < 3; ++k) {
+            double acc = 0.0;
+            for (int r = 0; r < 3; ++r) acc += (double)d.R[3 * r + k] * (double)d.t[r];
+            d.campos[k] = (float)(-acc);
+        }
+        tiles += (long long)d.tiles_x * d.tiles_y;
+        pix += (long long)c.width * c.height;
+    }
+    if (tiles >= (1ll << 31)) return fail(ctx, FHGS_ERR_UNSUPPORTED, "too many tiles");
+    cs.total_tiles = (int)tiles;
+    cs.total_pix = pix;
+    return FHGS_OK;
+}
+
+Params make_params(const fhgs_params *p) {
+    Params q;
+    q.znear = p->znear;
+    q.dil = p->dilation;
+    q.amin = p->alpha_min;
+    q.amax = p->alpha_max;
+    q.teps = p->t_eps;
+    q.cut = p->cutoff_sq;
+    q.fov = p->fov_clamp;
+    q.bg0 = p->bg[0];
+    q.bg1 = p->bg[1];
+    q.bg2 = p->bg[2];
+    q.sh_deg = p->sh_degree;
+    q.K = (p->sh_degree + 1) * (p->sh_degree + 1);
+    return q;
+}
+
+fhgs_status check_gaussians(fhgs_ctx *ctx, const fhgs_gaussians *g, bool need_sh) {
+    if (!g) return fail(ctx, FHGS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0 || g->n >= (1ll << 31)) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad Gaussian count");
+    if (g->n == 0) return FHGS_OK;
+    if (!g->means || !g->scales || !g->quats || !g->opacities || (need_sh && !g->sh))
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "a Gaussian parameter pointer is NULL");
+    if (!aligned16(g->quats)) return fail(ctx, FHGS_ERR_ALIGNMENT, "quats must be 16-byte aligned");
+    return FHGS_OK;
+}
+
+fhgs_status check_bins(fhgs_ctx *ctx, const fhgs_bins *b) {
+    if (!b || !b->gids || !b->ranges || !b->n_instances)
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "bins has a NULL buffer");
+    if (b->capacity < 0 || b->capacity > 0xFFFFFFFFll)
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "bins capacity out of range");
+    return FHGS_OK;
+}
+
+fhgs_status check_features(fhgs_ctx *ctx, const void *features, fhgs_dtype ft, int D, long long n) {
+    if (D < 0) return fail(ctx, FHGS_ERR_INVALID_ARG, "D must be >= 0");
+    if (D % 8) return fail(ctx, FHGS_ERR_UNSUPPORTED, "D must be a multiple of 8");
+    if (ft != FHGS_F32 && ft != FHGS_BF16) return fail(ctx, FHGS_ERR_INVALID_ARG, "unknown feature dtype");
+    if (n == 0) return FHGS_OK;  // no rows: the pointer is never read
+    if (D > 0 && !features) return fail(ctx, FHGS_ERR_INVALID_ARG, "features is NULL with D > 0");
+    if (D > 0 && !aligned16(features)) return fail(ctx, FHGS_ERR_ALIGNMENT, "features must be 16-byte aligned");
+    return FHGS_OK;
+}
+
+fhgs_status ensure_bin_scratch(fhgs_ctx *ctx, long long cn, long long capacity) {
+    const int G = ctx->sm_count * kRadixBlocksPerSM;
+    const long long want_cn = cn > ctx->bin_cn ? cn : ctx->bin_cn;
+    const long long want_cap = capacity > ctx->bin_cap ? capacity : ctx->bin_cap;
+    const size_t bytes = bin_scratch_bytes(want_cn, want_cap, G);
+    if (bytes > ctx->bin.bytes) {
+        fhgs_status s = ensure(ctx, ctx->bin, bytes);
+        if (s != FHGS_OK) return s;
+    }
+    ctx->bin_cn = want_cn;
+    ctx->bin_cap = want_cap;
+    return FHGS_OK;
+}
+
+bool use_tc(const fhgs_params *p, fhgs_dtype ft, int D) {
+    if (D == 0) return false;
+    if (p->path == FHGS_PATH_FP32) return false;
+    if (ft != FHGS_BF16) return false;
+    return tc_supported(D, p->d_split) != 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fhgs_abi_version(void) { return FHGS_ABI_VERSION; }
+
+const char *fhgs_status_string(fhgs_status s) {
+    switch (s) {
+        case FHGS_OK: return "ok";
+        case FHGS_ERR_INVALID_ARG: return "invalid argument";
+        case FHGS_ERR_UNSUPPORTED: return "unsupported";
+        case FHGS_ERR_ALIGNMENT: return "misaligned pointer";
+        case FHGS_ERR_CUDA: return "CUDA error";
+        case FHGS_ERR_CAPACITY: return "instance buffer overflow";
+        case FHGS_ERR_TIMEOUT: return "device wait timed out";
+        case FHGS_ERR_NUMERIC: return "non-finite input";
+        case FHGS_ERR_NO_DEVICE: return "no sm_103 device";
+    }
+    return "unknown status";
+}
+
+void fhgs_default_params(fhgs_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->tile_w = p->tile_h = kTile;
+    p->sh_degree = 0;
+    p->path = FHGS_PATH_AUTO;
+    p->batch = 0;
+    p->d_split = 0;
+    p->znear = 0.2f;
+    p->dilation = 0.3f;
+    p->alpha_min = 1.0f / 255.0f;
+    p->alpha_max = 0.99f;
+    p->t_eps = 1e-4f;
+    p->cutoff_sq = 9.0f;
+    p->fov_clamp = 1.3f;
+}
+
+fhgs_status fhgs_create(fhgs_ctx **out, int device) {
+    if (!out) return FHGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return FHGS_ERR_NO_DEVICE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return FHGS_ERR_NO_DEVICE;
+    if (prop.major != 10 || prop.minor != 3) return FHGS_ERR_NO_DEVICE;
+    if (cudaSetDevice(device) != cudaSuccess) return FHGS_ERR_NO_DEVICE;
+    fhgs_ctx *ctx = new fhgs_ctx();
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    if (cudaMalloc(&ctx->status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess) {
+        delete ctx;
+        return FHGS_ERR_CUDA;
+    }
+    *out = ctx;
+    return FHGS_OK;
+}
+
+void fhgs_destroy(fhgs_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    for (DevBuf *b : {&ctx->bin, &ctx->g2d, &ctx->fuse_proj, &ctx->fuse_gids, &ctx->fuse_ranges, &ctx->fuse_count})
+        if (b->p) cudaFree(b->p);
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    if (ctx->status) cudaFree(ctx->status);
+    delete ctx;
+}
+
+const char *fhgs_last_error(const fhgs_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int64_t fhgs_proj_bytes(int64_t n, int n_cams) {
+    if (n < 0 || n_cams < 1) return -1;
+    return (int64_t)proj_bytes((long long)n * n_cams);
+}
+
+int64_t fhgs_total_tiles(const fhgs_camera *cams, int n_cams) {
+    if (!cams || n_cams < 1) return -1;
+    int64_t t = 0;
+    for (int i = 0; i < n_cams; ++i)
+        t += (int64_t)((cams[i].width + kTile - 1) / kTile) * ((cams[i].height + kTile - 1) / kTile);
+    return t;
+}
+
+fhgs_status fhgs_reserve(fhgs_ctx *ctx, int64_t max_n, int n_cams, int64_t max_instances) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    if (max_n < 0 || n_cams < 1 || max_instances < 0) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad reserve size");
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    fhgs_status s = ensure_bin_scratch(ctx, (long long)max_n * n_cams, max_instances);
+    if (s != FHGS_OK) return s;
+    return ensure(ctx, ctx->g2d, sizeof(float) * 12 * (size_t)max_n * n_cams + 256);
+}
+
+fhgs_status fhgs_sync_status(fhgs_ctx *ctx, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    FHGS_CUDA(ctx, cudaStreamSynchronize(st));
+    unsigned h = 0;
+    FHGS_CUDA(ctx, cudaMemcpy(&h, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    FHGS_CUDA(ctx, cudaMemset(ctx->status, 0, sizeof(unsigned)));
+    if (h & ST_CAPACITY) return fail(ctx, FHGS_ERR_CAPACITY, "tile instance buffer overflow");
+    if (h & ST_TIMEOUT) return fail(ctx, FHGS_ERR_TIMEOUT, "a device-side wait ran out");
+    if (h & ST_NUMERIC) return fail(ctx, FHGS_ERR_NUMERIC, "non-finite inputs were culled");
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_project(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhgs_camera *cams, int n_cams,
+                         const fhgs_params *p, void *proj, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    fhgs_status s = check_params(ctx, p);
+    if (s == FHGS_OK) s = check_gaussians(ctx, g, true);
+    if (s != FHGS_OK) return s;
+    CamSet cs;
+    if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
+    if (!proj) return fail(ctx, FHGS_ERR_INVALID_ARG, "proj is NULL");
+    if (!aligned16(proj)) return fail(ctx, FHGS_ERR_ALIGNMENT, "proj must be 16-byte aligned");
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    const Params q = make_params(p);
+    {
+        Prof pr(ctx, "project", (cudaStream_t)stream);
+        launch_project(*g, cs, q, proj_view(proj, (long long)g->n * n_cams), ctx->status, (cudaStream_t)stream);
+    }
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_bin_sort(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_camera *cams, int n_cams,
+                          const fhgs_params *p, const fhgs_bins *bins, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    fhgs_status s = check_params(ctx, p);
+    if (s == FHGS_OK) s = check_bins(ctx, bins);
+    if (s != FHGS_OK) return s;
+    if (n < 0 || n >= (1ll << 31)) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad Gaussian count");
+    if (!proj) return fail(ctx, FHGS_ERR_INVALID_ARG, "proj is NULL");
+    CamSet cs;
+    if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
+    if ((long long)n * n_cams >= (1ll << 32)) return fail(ctx, FHGS_ERR_UNSUPPORTED, "too many entries");
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    const long long cn = (long long)n * n_cams;
+    if ((s = ensure_bin_scratch(ctx, cn, bins->capacity)) != FHGS_OK) return s;
+    BinScratch sc = bin_scratch_view(ctx->bin.p, ctx->bin_cn, ctx->bin_cap, ctx->sm_count * kRadixBlocksPerSM);
+    {
+        Prof pr(ctx, "bin_sort", (cudaStream_t)stream);
+        launch_bin_sort(n, n_cams, cs, proj_view(const_cast<void *>(proj), cn), *bins, sc, ctx->status, ctx->sm_count,
+                        (cudaStream_t)stream);
+    }
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_render_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_bins *bins, const void *features,
+                            fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams, const fhgs_params *p,
+                            float *rgb, float *feat, float *T_final, int32_t *last, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    fhgs_status s = check_params(ctx, p);
+    if (s == FHGS_OK) s = check_bins(ctx, bins);
+    if (s == FHGS_OK) s = check_features(ctx, features, ftype, D, n);
+    if (s != FHGS_OK) return s;
+    if (n < 0 || !proj || !rgb || !T_final || !last)
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL output or projection buffer");
+    if (feat && !aligned16(feat)) return fail(ctx, FHGS_ERR_ALIGNMENT, "feat must be 16-byte aligned");
+    if (p->path == FHGS_PATH_TC && D > 0 && !use_tc(p, ftype, D))
+        return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core path needs BF16 features and a supported D");
+    CamSet cs;
+    if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    const Params q = make_params(p);
+    ProjView pv = proj_view(const_cast<void *>(proj), (long long)n * n_cams);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int Df = feat ? D : 0;
+    const bool tc = Df > 0 && use_tc(p, ftype, D);
+    Prof pr(ctx, tc ? "render_fwd_tc" : "render_fwd_fp32", st);
+    if (tc)
+        launch_render_fwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, D, p->d_split, rgb, feat, T_final,
+                             last, ctx->status, st);
+    else
+        launch_render_fwd_fp32(n, cs, q, pv, *bins, features, ftype == FHGS_BF16, Df, rgb, feat, T_final, last, st);
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *proj, const fhgs_bins *bins,
+                            const void *features, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
+                            const fhgs_params *p, const float *T_final, const int32_t *last, const float *grad_rgb,
+                            const float *grad_feat, float *grad_means, float *grad_scales, float *grad_quats,
+                            float *grad_opac, float *grad_sh, float *grad_features, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    fhgs_status s = check_params(ctx, p);
+    if (s == FHGS_OK) s = check_gaussians(ctx, g, true);
+    if (s == FHGS_OK) s = check_bins(ctx, bins);
+    if (s == FHGS_OK) s = check_features(ctx, features, ftype, D, g ? g->n : 0);
+    if (s != FHGS_OK) return s;
+    if (!proj || !T_final || !last || !grad_rgb)
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL input buffer");
+    if (g->n > 0 && (!grad_means || !grad_scales || !grad_quats || !grad_opac || !grad_sh))
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL gradient buffer");
+    if (!aligned16(grad_quats)) return fail(ctx, FHGS_ERR_ALIGNMENT, "grad_quats must be 16-byte aligned");
+    if ((grad_feat && !aligned16(grad_feat)) || (grad_features && !aligned16(grad_features)))
+        return fail(ctx, FHGS_ERR_ALIGNMENT, "feature gradients must be 16-byte aligned");
+    if (p->path == FHGS_PATH_TC && D > 0 && !use_tc(p, ftype, D))
+        return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core path needs BF16 features and a supported D");
+    CamSet cs;
+    if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    const long long n = g->n, cn = n * n_cams;
+    if ((s = ensure(ctx, ctx->g2d, sizeof(float) * 12 * (size_t)cn + 256)) != FHGS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *g2d = (float *)ctx->g2d.p;
+    FHGS_CUDA(ctx, cudaMemsetAsync(g2d, 0, sizeof(float) * 12 * (size_t)cn, st));
+    if (grad_features && D > 0) FHGS_CUDA(ctx, cudaMemsetAsync(grad_features, 0, sizeof(float) * (size_t)n * D, st));
+    const Params q = make_params(p);
+    ProjView pv = proj_view(const_cast<void *>(proj), cn);
+    const bool tc = D > 0 && use_tc(p, ftype, D) && (grad_feat || grad_features);
+    {
+        Prof pr(ctx, tc ? "render_bwd_tc" : "render_bwd_fp32", st);
+        if (tc)
+            launch_render_bwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, D, p->d_split, T_final, last,
+                                 grad_rgb, grad_feat, g2d, grad_features, ctx->status, st);
+        else
+            launch_render_bwd_fp32(n, cs, q, pv, *bins, features, ftype == FHGS_BF16, D, T_final, last, grad_rgb,
+                                   grad_feat, g2d, D > 0 ? grad_features : nullptr, st);
+    }
+    {
+        Prof pb(ctx, "project_bwd", st);
+        launch_project_bwd(*g, cs, q, pv, g2d, grad_means, grad_scales, grad_quats, grad_opac, grad_sh, st);
+    }
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhgs_camera *views, int n_views,
+                               const float *const *maps, int D, const fhgs_params *p, float *num, float *den,
+                               float *out, uint32_t flags, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    fhgs_status s = check_params(ctx, p);
+    if (s == FHGS_OK) s = check_gaussians(ctx, g, true);
+    if (s != FHGS_OK) return s;
+    if (!views || n_views < 0) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad views");
+    if (n_views > 0 && !maps) return fail(ctx, FHGS_ERR_INVALID_ARG, "maps is NULL");
+    if (D <= 0 || D % 8) return fail(ctx, FHGS_ERR_UNSUPPORTED, "D must be a positive multiple of 8");
+    if (!num || !den) return fail(ctx, FHGS_ERR_INVALID_ARG, "num/den is NULL");
+    if ((flags & FHGS_FUSE_FINALIZE) && !out) return fail(ctx, FHGS_ERR_INVALID_ARG, "out is NULL with FINALIZE");
+    if (!aligned16(num) || (out && !aligned16(out))) return fail(ctx, FHGS_ERR_ALIGNMENT, "num/out must be 16-byte aligned");
+    for (int v = 0; v < n_views; ++v) {
+        if (!maps[v]) return fail(ctx, FHGS_ERR_INVALID_ARG, "map " + std::to_string(v) + " is NULL");
+        if (!aligned16(maps[v])) return fail(ctx, FHGS_ERR_ALIGNMENT, "map " + std::to_string(v) + " is not 16-byte aligned");
+        CamSet tmp;
+        if ((s = make_cams(ctx, views + v, 1, tmp)) != FHGS_OK) return s;
+    }
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long n = g->n;
+    if (!(flags & FHGS_FUSE_ACCUMULATE)) {
+        FHGS_CUDA(ctx, cudaMemsetAsync(num, 0, sizeof(float) * (size_t)n * D, st));
+        FHGS_CUDA(ctx, cudaMemsetAsync(den, 0, sizeof(float) * (size_t)n, st));
+    }
+    const Params q = make_params(p);
+    if ((s = ensure(ctx, ctx->fuse_proj, proj_bytes(n))) != FHGS_OK) return s;
+    if ((s = ensure(ctx, ctx->fuse_count, 256)) != FHGS_OK) return s;
+    for (int v = 0; v < n_views && n > 0; ++v) {
+        CamSet cs;
+        make_cams(ctx, views + v, 1, cs);
+        if ((s = ensure(ctx, ctx->fuse_ranges, sizeof(uint32_t) * 2 * (size_t)cs.total_tiles)) != FHGS_OK) return s;
+        ProjView pv = proj_view(ctx->fuse_proj.p, n);
+        launch_project(*g, cs, q, pv, ctx->status, st);
+        // instance capacity: grow until this view's instances fit (reads the
+        // count on the host, so fusion is not meant for stream capture)
+        for (int tries = 0;; ++tries) {
+            if (tries > 3) return fail(ctx, FHGS_ERR_CAPACITY, "instance buffer did not converge");
+            if ((s = ensure(ctx, ctx->fuse_gids, sizeof(uint32_t) * 1024)) != FHGS_OK) return s;
+            fhgs_bins b;
+            b.gids = (uint32_t *)ctx->fuse_gids.p;
+            b.keys = nullptr;
+            b.ranges = (uint32_t *)ctx->fuse_ranges.p;
+            b.n_instances = (int64_t *)ctx->fuse_count.p;
+            b.capacity = (long long)(ctx->fuse_gids.bytes / sizeof(uint32_t));
+            if ((s = ensure_bin_scratch(ctx, n, b.capacity)) != FHGS_OK) return s;
+            BinScratch sc = bin_scratch_view(ctx->bin.p, ctx->bin_cn, ctx->bin_cap, ctx->sm_count * kRadixBlocksPerSM);
+            launch_bin_sort(n, 1, cs, pv, b, sc, nullptr, ctx->sm_count, st);
+            int64_t count = 0;
+            FHGS_CUDA(ctx, cudaMemcpyAsync(&count, b.n_instances, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            FHGS_CUDA(ctx, cudaStreamSynchronize(st));
+            if (count <= b.capacity) {
+                launch_fuse_fp32(n, cs, q, pv, b, maps[v], D, num, den, st);
+                break;
+            }
+            if (count > 0xFFFFFFFFll) return fail(ctx, FHGS_ERR_CAPACITY, "too many instances in one view");
+            if ((s = ensure(ctx, ctx->fuse_gids, sizeof(uint32_t) * (size_t)(count + count / 8 + 1024))) != FHGS_OK)
+                return s;
+        }
+        FHGS_CUDA(ctx, cudaGetLastError());
+    }
+    if (flags & FHGS_FUSE_FINALIZE) launch_fuse_finalize(n, D, num, den, out, (flags & FHGS_FUSE_NORMALIZE) != 0, st);
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_profile_enable(fhgs_ctx *ctx, int enable) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (enable && ctx->pool.empty()) {
+        ctx->pool.resize(kProfEvents);
+        for (size_t i = 0; i < kProfEvents; ++i) FHGS_CUDA(ctx, cudaEventCreate(&ctx->pool[i]));
+    }
+    ctx->prof = enable != 0;
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_profile_read(fhgs_ctx *ctx, char *buf, int64_t len) {
+    if (!ctx || !buf || len < 3) return FHGS_ERR_INVALID_ARG;
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    std::map<std::string, std::pair<long long, double>> agg;
+    for (const ProfRec &r : ctx->recs) {
+        FHGS_CUDA(ctx, cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        FHGS_CUDA(ctx, cudaEventElapsedTime(&ms, r.a, r.b));
+        auto &e = agg[r.name];
+        e.first += 1;
+        e.second += ms;
+    }
+    ctx->recs.clear();
+    ctx->pool_next = 0;
+    std::string out = "{";
+    for (auto &kv : agg) {
+        char tmp[160];
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": [%lld, %.6f]", out.size() > 1 ? ", " : "", kv.first.c_str(),
+                 kv.second.first, kv.second.second);
+        out += tmp;
+    }
+    out += "}";
+    strncpy(buf, out.c_str(), (size_t)len - 1);
+    buf[len - 1] = 0;
+    return FHGS_OK;
+}
+
+int64_t fhgs_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

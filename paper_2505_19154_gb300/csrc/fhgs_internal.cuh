@@ -1,0 +1,149 @@
+// Internal declarations shared by the CUDA translation units of libfhgs.so.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fhgs.h"
+
+namespace fhgs {
+
+constexpr int kTile = 16;          // tile edge in pixels (App. A)
+constexpr int kTilePix = kTile * kTile;
+
+// Device status word bits (latched by kernels, read by fhgs_sync_status).
+enum : unsigned { ST_CAPACITY = 1u, ST_TIMEOUT = 2u, ST_NUMERIC = 4u };
+
+// One camera as the kernels see it (passed by value inside CamSet).
+struct DevCam {
+    int W, H, tiles_x, tiles_y;
+    int tile_off;       // first global tile id of this camera
+    int pad0;
+    long long pix_off;  // first packed pixel row of this camera
+    float fx, fy, cx, cy;
+    float R[9];         // world-to-camera rotation, row-major
+    float t[3];         // world-to-camera translation
+    float campos[3];    // camera centre in world space, -R^T t
+    float pad1;
+};
+
+struct CamSet {
+    int n;
+    int total_tiles;
+    long long total_pix;
+    DevCam c[FHGS_MAX_CAMS];
+};
+
+struct Params {
+    float znear, dil, amin, amax, teps, cut, fov;
+    float bg0, bg1, bg2;
+    int sh_deg, K;
+};
+
+// Per (camera, Gaussian) screen-space record used by the render kernels.
+//   a = (mean_x, mean_y, conic_A, conic_B)   q2 = A dx^2 + 2 B dx dy + C dy^2
+//   b = (conic_C, opacity, r, g)
+//   c = (b, view depth, bits of the colour clamp mask, 0)
+struct __align__(16) GRec {
+    float4 a, b, c;
+};
+
+// Layout of the caller's projection buffer (fhgs_proj_bytes).
+struct ProjView {
+    GRec *rec;        // [C*N]
+    int4 *trect;      // [C*N] tile rectangle (tx0, ty0, tx1, ty1), inclusive
+    uint32_t *ntiles; // [C*N] tiles in the rectangle, 0 if culled
+    uint32_t *dkey;   // [C*N] IEEE bits of the view depth, 0xFFFFFFFF if culled
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline size_t proj_bytes(long long cn) {
+    return align_up(sizeof(GRec) * cn, 256) + align_up(sizeof(int4) * cn, 256) +
+           2 * align_up(sizeof(uint32_t) * cn, 256) + 256;
+}
+
+inline ProjView proj_view(void *base, long long cn) {
+    char *p = (char *)align_up((size_t)base, 256);
+    ProjView v;
+    v.rec = (GRec *)p;
+    p += align_up(sizeof(GRec) * cn, 256);
+    v.trect = (int4 *)p;
+    p += align_up(sizeof(int4) * cn, 256);
+    v.ntiles = (uint32_t *)p;
+    p += align_up(sizeof(uint32_t) * cn, 256);
+    v.dkey = (uint32_t *)p;
+    return v;
+}
+
+// Camera index of a global tile id (cameras are few; linear scan).
+__device__ __forceinline__ int cam_of_tile(const CamSet &cs, int tile) {
+    int ci = 0;
+#pragma unroll 1
+    while (ci + 1 < cs.n && tile >= cs.c[ci + 1].tile_off) ++ci;
+    return ci;
+}
+
+// Eq. 4's alpha at a pixel: q2 = A dx^2 + 2 B dx dy + C dy^2 with
+// (dx, dy) = pixel centre - mean, G = exp(-q2/2), alpha = min(alpha_max,
+// op G).  Written with explicit fused multiply-adds so the forward, backward
+// and fusion kernels all take bit-identical per-pixel decisions.
+__device__ __forceinline__ float eval_q2(float dx, float dy, float A, float B, float C) {
+    const float t = __fmaf_rn(2.f * B, dy, __fmul_rn(A, dx));
+    return __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(C, dy), dy));
+}
+
+__device__ __forceinline__ void latch(unsigned *status, unsigned bit) {
+    if (status) atomicOr(status, bit);
+}
+
+// Counts kernel launches (fhgs_launch_count); defined in api.cu.
+void note_launch(int k);
+
+// ---------------------------------------------------------------- launches
+// projection (project.cu)
+void launch_project(const fhgs_gaussians &g, const CamSet &cs, const Params &p, ProjView pv,
+                    unsigned *status, cudaStream_t st);
+void launch_project_bwd(const fhgs_gaussians &g, const CamSet &cs, const Params &p, ProjView pv,
+                        const float *g2d, float *gmeans, float *gscales, float *gquats, float *gop,
+                        float *gsh, cudaStream_t st);
+
+// binning (binning.cu)
+struct BinScratch {
+    uint32_t *dk_a, *dv_a, *dk_b, *dv_b;  // depth sort [C*N]
+    uint32_t *offsets;                    // [C*N]
+    uint32_t *partials;                   // scan partials
+    uint32_t *hist;                       // radix histogram [256][G]
+    uint32_t *tk_a, *tk_b, *tv_a;         // tile sort [capacity]
+    int radix_blocks;
+};
+size_t bin_scratch_bytes(long long cn, long long capacity, int radix_blocks);
+BinScratch bin_scratch_view(void *base, long long cn, long long capacity, int radix_blocks);
+void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, const fhgs_bins &bins,
+                     BinScratch sc, unsigned *status, int sm_count, cudaStream_t st);
+
+// render, FP32 CUDA-core path (render_fp32.cu)
+void launch_render_fwd_fp32(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                            const void *feats, int bf16, int D, float *rgb, float *feat, float *T,
+                            int32_t *last, cudaStream_t st);
+void launch_render_bwd_fp32(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                            const void *feats, int bf16, int D, const float *T, const int32_t *last,
+                            const float *grgb, const float *gfeat, float *g2d, float *gfeatures,
+                            cudaStream_t st);
+void launch_fuse_fp32(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                      const float *fmap, int D, float *num, float *den, cudaStream_t st);
+void launch_fuse_finalize(long long N, int D, const float *num, const float *den, float *out, int normalize,
+                          cudaStream_t st);
+
+// render, tcgen05 tensor-core path (render_tc.cu)
+int tc_supported(int D, int d_split);
+void launch_render_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                          const __nv_bfloat16 *feats, int D, int d_split, float *rgb, float *feat, float *T,
+                          int32_t *last, unsigned *status, cudaStream_t st);
+void launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                          const __nv_bfloat16 *feats, int D, int d_split, const float *T, const int32_t *last,
+                          const float *grgb, const float *gfeat, float *g2d, float *gfeatures, unsigned *status,
+                          cudaStream_t st);
+
+}  // namespace fhgs
