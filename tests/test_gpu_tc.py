@@ -1,0 +1,101 @@
+"""Parity of the tcgen05 tensor-core path against the FP64 oracle.
+
+Bars: RGB within 1e-5 max abs and `last` exact (the weights are the FP32
+ones); features within 1e-2 of max|F| (the BF16 feature path: weights are
+rounded to BF16, relative error <= 2^-9 per term); footprint gradients
+(means, scales, quats, opacities, SH) within 1e-3 relative L2 (dL/dF enters
+the dF.Fe^T contraction as BF16 hi + lo, ~16 mantissa bits); feature
+gradients within 1e-2 relative L2 (BF16 weights).  Features are BF16 inputs,
+so the oracle uses exactly the same feature values.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_19154_gb300 import api, synth
+from tests.helpers import small_random_scene
+from tests.test_gpu_parity import _t, check_grads, check_image
+
+pytestmark = pytest.mark.gpu
+
+
+def run_tc(scene, cams, prm, d_split=0, dC=None, dF=None):
+    rast = api.Rasterizer(0, sh_degree=prm.get("sh_degree", 0), path=api.PATH_TC,
+                          bg=prm.get("bg", (0.0, 0.0, 0.0)), d_split=d_split)
+    t = {k: _t(scene[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    feats = _t(scene["features"], torch.bfloat16)
+    rast.ctx.profile(True)
+    st = rast.prepare(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams)
+    rgb, feat = rast.forward(st, feats)
+    out = dict(rgb=rgb.cpu().numpy(), feat=feat.cpu().numpy(), T=st["T"].cpu().numpy(),
+               last=st["last"].cpu().numpy())
+    if dC is not None:
+        g = rast.backward(st, _t(dC), None if dF is None else _t(dF))
+        out["grads"] = {k: (None if v is None else v.cpu().numpy()) for k, v in g.items()}
+    torch.cuda.synchronize()
+    assert rast.ctx.sync_status() == api.OK
+    prof = rast.ctx.profile_read()
+    assert "render_fwd_tc" in prof, prof
+    if dC is not None:
+        assert "render_bwd_tc" in prof, prof
+    return out
+
+
+def bf16_scene(n, seed, D, sh_degree=1, spread=0.5):
+    sc = small_random_scene(n, seed=seed, sh_degree=sh_degree, D=D, spread=spread)
+    sc = {k: (np.asarray(v, np.float32) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+    sc["features"] = synth.to_bf16(sc["features"])
+    return sc
+
+
+@pytest.mark.parametrize("d_split", [64, 128])
+def test_tc_forward_small(d_split):
+    sc = bf16_scene(600, seed=41, D=128)
+    cams = [synth.look_at_camera(synth.ring_position(3.0, 10, 5), 48, 40)]
+    prm = dict(sh_degree=1)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_tc(sc, cams, prm, d_split=d_split)
+    refs = oracle.forward(sc, cams, prm, sc["features"], prep=prep)
+    check_image(out, refs, cams, feat_tol=1e-2)
+
+
+def test_tc_forward_multicamera_ragged_dsplit256():
+    sc = bf16_scene(4000, seed=42, D=256, sh_degree=2)
+    cams = [synth.look_at_camera(synth.ring_position(3.0, a, e), w, h)
+            for a, e, w, h in [(0, 0, 70, 50), (130, 20, 33, 47), (250, -25, 96, 64)]]
+    prm = dict(sh_degree=2, bg=(0.1, 0.2, 0.3))
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_tc(sc, cams, prm, d_split=256)
+    refs = oracle.forward(sc, cams, prm, sc["features"], prep=prep)
+    check_image(out, refs, cams, feat_tol=1e-2)
+
+
+@pytest.mark.parametrize("d_split", [64, 128, 256])
+def test_tc_backward_small(d_split):
+    sc = bf16_scene(1500, seed=43, D=256, sh_degree=3)
+    cams = [synth.look_at_camera(synth.ring_position(3.0, 30, 10), 64, 48)]
+    prm = dict(sh_degree=3, bg=(0.2, 0.1, 0.3))
+    dC, dF = synth.upstream(9, 64 * 48, 256)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_tc(sc, cams, prm, d_split=d_split, dC=dC, dF=dF)
+    refs = oracle.forward(sc, cams, prm, sc["features"], prep=prep)
+    check_image(out, refs, cams, feat_tol=1e-2)
+    ref = oracle.backward(sc, cams, prm, sc["features"], [dC], [dF], prep=prep)
+    check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities", "sh"), tol=1e-3)
+    check_grads(out["grads"], ref, keys=("features",), tol=1e-2)
+
+
+@pytest.mark.slow
+def test_tc_config2_forward_backward():
+    scene, cams = synth.config2(0)
+    scene["features"] = synth.to_bf16(scene["features"])
+    prm = dict(sh_degree=3)
+    dC, dF = synth.upstream(2, 512 * 512, 128)
+    prep = oracle.prepare(scene, cams, prm)
+    out = run_tc(scene, cams, prm, dC=dC, dF=dF)
+    refs = oracle.forward(scene, cams, prm, scene["features"], prep=prep)
+    check_image(out, refs, cams, feat_tol=1e-2)
+    ref = oracle.backward(scene, cams, prm, scene["features"], [dC], [dF], prep=prep)
+    check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities", "sh"), tol=1e-3)
+    check_grads(out["grads"], ref, keys=("features",), tol=1e-2)
