@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--D", type=int, default=512)
+    ap.add_argument("--width", type=int, default=1920, help="profiling only: smaller view, same scene")
+    ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--path", choices=["tc", "fp32", "auto"], default="auto")
     ap.add_argument("--fp32-steps", type=int, default=3, help="timed steps of the FP32 comparison path (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -112,11 +114,13 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- workload
-def make_workload(seed, n, D, dev):
+def make_workload(seed, n, D, dev, width=1920, height=1080):
     import numpy as np
     import torch
     from paper_2505_19154_gb300 import synth
     scene, cams = synth.config3(seed, n=n, D=D)
+    if (width, height) != (1920, 1080):  # centre crop of the same view: same focal length
+        cams = [dict(cams[0], width=width, height=height, cx=width / 2.0, cy=height / 2.0)]
     t = {k: torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).to(dev)
          for k in ("means", "scales", "quats", "opacities", "sh")}
     t["features"] = torch.from_numpy(scene["features"]).to(dev).to(torch.bfloat16)
@@ -150,7 +154,7 @@ def run_ours(args):
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    scene, cams, t, P = make_workload(rank, args.n, args.D, dev)
+    scene, cams, t, P = make_workload(rank, args.n, args.D, dev, args.width, args.height)
     path = {"tc": api.PATH_TC, "fp32": api.PATH_FP32, "auto": api.PATH_AUTO}[args.path]
     rast = api.Rasterizer(local, sh_degree=3, path=path)
     g = (t["means"], t["scales"], t["quats"], t["opacities"], t["sh"])

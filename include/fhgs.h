@@ -137,9 +137,10 @@ void fhgs_default_params(fhgs_params *p);
 int64_t fhgs_proj_bytes(int64_t n, int n_cams);
 /* Number of tiles over all cameras (rows of fhgs_bins.ranges). */
 int64_t fhgs_total_tiles(const fhgs_camera *cams, int n_cams);
-/* Pre-size the context's scratch for up to max_n Gaussians x n_cams cameras
- * and max_instances tile instances, so later calls allocate nothing. */
-fhgs_status fhgs_reserve(fhgs_ctx *ctx, int64_t max_n, int n_cams, int64_t max_instances);
+/* Pre-size the context's scratch for up to max_n Gaussians seen by these
+ * cameras, so later calls with at most that many Gaussians and the same
+ * camera resolutions allocate nothing (required before stream capture). */
+fhgs_status fhgs_reserve(fhgs_ctx *ctx, int64_t max_n, const fhgs_camera *cams, int n_cams);
 /* Synchronise `stream`, then read and clear the context's device status
  * word.  Returns the first latched device-side error, or FHGS_OK. */
 fhgs_status fhgs_sync_status(fhgs_ctx *ctx, void *stream);

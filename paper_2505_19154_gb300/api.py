@@ -86,7 +86,7 @@ def lib():
         L.fhgs_proj_bytes.restype = i64
         L.fhgs_total_tiles.argtypes = [ctypes.POINTER(Camera), i32]
         L.fhgs_total_tiles.restype = i64
-        L.fhgs_reserve.argtypes = [vp, i64, i32, i64]
+        L.fhgs_reserve.argtypes = [vp, i64, ctypes.POINTER(Camera), i32]
         L.fhgs_sync_status.argtypes = [vp, vp]
         L.fhgs_project.argtypes = [vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), i32,
                                    ctypes.POINTER(Params), vp, vp]
@@ -189,8 +189,8 @@ class Context:
         return int(lib().fhgs_launch_count())
 
     # --------------------------------------------------------------- calls
-    def reserve(self, max_n: int, n_cams: int, max_instances: int):
-        self.check(lib().fhgs_reserve(self.h, int(max_n), int(n_cams), int(max_instances)))
+    def reserve(self, max_n: int, cams):
+        self.check(lib().fhgs_reserve(self.h, int(max_n), cams, len(cams)))
 
     def sync_status(self, stream=None) -> int:
         return lib().fhgs_sync_status(self.h, self.stream_ptr(stream))

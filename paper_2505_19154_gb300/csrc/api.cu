@@ -34,7 +34,6 @@ struct fhgs_ctx {
     DevBuf bin;                  // binning scratch
     DevBuf g2d;                  // per (camera, Gaussian) render gradients
     DevBuf fuse_proj, fuse_gids, fuse_ranges, fuse_count;  // fusion view scratch
-    long long bin_cn = 0, bin_cap = 0;
 };
 
 static std::atomic<long long> g_launches{0};
@@ -45,7 +44,6 @@ void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 namespace {
 
-constexpr int kRadixBlocksPerSM = 2;
 constexpr size_t kProfEvents = 8192;
 
 // Brackets one kernel group with CUDA events on its stream while profiling.
@@ -202,18 +200,9 @@ fhgs_status check_features(fhgs_ctx *ctx, const void *features, fhgs_dtype ft, i
     return FHGS_OK;
 }
 
-fhgs_status ensure_bin_scratch(fhgs_ctx *ctx, long long cn, long long capacity) {
-    const int G = ctx->sm_count * kRadixBlocksPerSM;
-    const long long want_cn = cn > ctx->bin_cn ? cn : ctx->bin_cn;
-    const long long want_cap = capacity > ctx->bin_cap ? capacity : ctx->bin_cap;
-    const size_t bytes = bin_scratch_bytes(want_cn, want_cap, G);
-    if (bytes > ctx->bin.bytes) {
-        fhgs_status s = ensure(ctx, ctx->bin, bytes);
-        if (s != FHGS_OK) return s;
-    }
-    ctx->bin_cn = want_cn;
-    ctx->bin_cap = want_cap;
-    return FHGS_OK;
+fhgs_status ensure_bin_scratch(fhgs_ctx *ctx, long long N, int n_cams, int total_tiles) {
+    const size_t bytes = bin_scratch_bytes(N, n_cams, total_tiles, ctx->sm_count);
+    return bytes > ctx->bin.bytes ? ensure(ctx, ctx->bin, bytes) : FHGS_OK;
 }
 
 bool use_tc(const fhgs_params *p, fhgs_dtype ft, int D) {
@@ -307,12 +296,14 @@ int64_t fhgs_total_tiles(const fhgs_camera *cams, int n_cams) {
     return t;
 }
 
-fhgs_status fhgs_reserve(fhgs_ctx *ctx, int64_t max_n, int n_cams, int64_t max_instances) {
+fhgs_status fhgs_reserve(fhgs_ctx *ctx, int64_t max_n, const fhgs_camera *cams, int n_cams) {
     if (!ctx) return FHGS_ERR_INVALID_ARG;
-    if (max_n < 0 || n_cams < 1 || max_instances < 0) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad reserve size");
-    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
-    fhgs_status s = ensure_bin_scratch(ctx, (long long)max_n * n_cams, max_instances);
+    if (max_n < 0 || max_n >= (1ll << 31)) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad reserve size");
+    CamSet cs;
+    fhgs_status s = make_cams(ctx, cams, n_cams, cs);
     if (s != FHGS_OK) return s;
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    if ((s = ensure_bin_scratch(ctx, max_n, n_cams, cs.total_tiles)) != FHGS_OK) return s;
     return ensure(ctx, ctx->g2d, sizeof(float) * 12 * (size_t)max_n * n_cams + 256);
 }
 
@@ -362,11 +353,11 @@ fhgs_status fhgs_bin_sort(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs
     if ((long long)n * n_cams >= (1ll << 32)) return fail(ctx, FHGS_ERR_UNSUPPORTED, "too many entries");
     FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
     const long long cn = (long long)n * n_cams;
-    if ((s = ensure_bin_scratch(ctx, cn, bins->capacity)) != FHGS_OK) return s;
-    BinScratch sc = bin_scratch_view(ctx->bin.p, ctx->bin_cn, ctx->bin_cap, ctx->sm_count * kRadixBlocksPerSM);
+    if ((s = ensure_bin_scratch(ctx, n, n_cams, cs.total_tiles)) != FHGS_OK) return s;
+    BinScratch sc = bin_scratch_view(ctx->bin.p, n, n_cams, cs.total_tiles, ctx->sm_count);
     {
         Prof pr(ctx, "bin_sort", (cudaStream_t)stream);
-        launch_bin_sort(n, n_cams, cs, proj_view(const_cast<void *>(proj), cn), *bins, sc, ctx->status, ctx->sm_count,
+        launch_bin_sort(n, n_cams, cs, proj_view(const_cast<void *>(proj), cn), *bins, sc, ctx->status,
                         (cudaStream_t)stream);
     }
     FHGS_CUDA(ctx, cudaGetLastError());
@@ -499,9 +490,9 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
             b.ranges = (uint32_t *)ctx->fuse_ranges.p;
             b.n_instances = (int64_t *)ctx->fuse_count.p;
             b.capacity = (long long)(ctx->fuse_gids.bytes / sizeof(uint32_t));
-            if ((s = ensure_bin_scratch(ctx, n, b.capacity)) != FHGS_OK) return s;
-            BinScratch sc = bin_scratch_view(ctx->bin.p, ctx->bin_cn, ctx->bin_cap, ctx->sm_count * kRadixBlocksPerSM);
-            launch_bin_sort(n, 1, cs, pv, b, sc, nullptr, ctx->sm_count, st);
+            if ((s = ensure_bin_scratch(ctx, n, 1, cs.total_tiles)) != FHGS_OK) return s;
+            BinScratch sc = bin_scratch_view(ctx->bin.p, n, 1, cs.total_tiles, ctx->sm_count);
+            launch_bin_sort(n, 1, cs, pv, b, sc, nullptr, st);
             int64_t count = 0;
             FHGS_CUDA(ctx, cudaMemcpyAsync(&count, b.n_instances, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
             FHGS_CUDA(ctx, cudaStreamSynchronize(st));

@@ -1,187 +1,49 @@
 // Tile binning (App. A: DuplicateWithKeys, SortByKeys, IdentifyTileRanges).
 //
 // The paper sorts one 64-bit key per tile instance, (tile id << 32 | depth
-// bits).  Here the same order is reached in two stable stages, because every
-// instance of one Gaussian shares its depth:
-//   1. sort the C*N (camera, Gaussian) entries by their 32-bit depth bits
-//      (stable LSD radix sort; ties stay in (camera, index) order);
-//   2. emit the tile instances in that depth order and stable-sort them by
-//      their 32-bit global tile id alone (only ceil(log2 tiles) bits).
-// The result equals the ascending sort of (tile << 32 | depth, gid) while
-// moving 8 bytes per instance per pass over a few passes instead of 12 bytes
-// over six or more.  No kernel waits on another block: each radix pass is
-// histogram -> scan -> scatter, all grids fixed, counts read on the device,
-// so the sequence can be captured in a CUDA graph.
+// bits), with ties left to the sort.  Every instance of a Gaussian shares its
+// depth, and a view has only a few thousand tiles, so the same order is built
+// here without sorting instances at all:
+//   1. stable LSD radix sort of the C*N (camera, Gaussian) entries by the
+//      32-bit depth bits (culled entries carry 0xFFFFFFFF and sort last), then
+//      one stable pass by camera: entries are grouped by camera, in depth
+//      order, ties by Gaussian index;
+//   2. each camera's depth-ordered entries are cut into segments of SEG; per
+//      segment the number of its Gaussians covering each tile comes from a 2-D
+//      difference array over the tile grid in shared memory (4 corner updates
+//      per rectangle, then row and column prefix sums);
+//   3. one exclusive scan over the (tile, segment) count table gives, for each
+//      tile, where each segment's run starts; the tile ranges are the
+//      segment-0 offsets;
+//   4. one warp per segment walks its Gaussians in depth order and writes each
+//      one's Gaussian index into every tile of its rectangle at the tile's
+//      running offset (kept in shared memory).
+// The result equals the ascending sort of (tile << 32 | depth bits, index).
+// Instances are written once, 4 bytes each; no kernel waits on another
+// block, grids are fixed and counts live on the device, so the sequence can
+// be captured in a CUDA graph.
 #include "fhgs_internal.cuh"
 
 namespace fhgs {
 namespace {
 
+constexpr int kRadixThreads = 256;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixRounds = 8;
+constexpr int kRadixTile = kRadixThreads * kRadixRounds;  // 2048
+constexpr int kBuckets = 256;
+
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;  // 2048
 
-constexpr int kRadixThreads = 256;
-constexpr int kRadixWarps = kRadixThreads / 32;
-constexpr int kRadixRounds = 8;                                   // items per thread per tile
-constexpr int kRadixTile = kRadixThreads * kRadixRounds;          // 2048
-constexpr int kBuckets = 256;
-
-// ---------------------------------------------------------------- scan
-// offsets[j] = sum_{j' < j} ntiles[order[j']] (exclusive), total -> *n_out.
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ ntiles,
-                                                              const uint32_t *__restrict__ order, long long n,
-                                                              uint32_t *partials) {
-    const long long base = (long long)blockIdx.x * kScanTile;
-    unsigned long long sum = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        const long long j = base + i * kScanThreads + threadIdx.x;
-        if (j < n) sum += ntiles[order[j]];
-    }
-    __shared__ unsigned long long red[kScanThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long s = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) s += red[w];
-        partials[blockIdx.x] = (uint32_t)min(s, 0xFFFFFFFFull);
-    }
-}
-
-// Exclusive scan of the block partials in place (one block); writes the total.
-__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partials, int nblocks, int64_t *n_out) {
-    __shared__ unsigned long long carry;
-    __shared__ unsigned long long wsum[32];
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < nblocks; base += 1024) {
-        const int i = base + threadIdx.x;
-        unsigned long long v = i < nblocks ? partials[i] : 0;
-        unsigned long long x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if ((threadIdx.x & 31) >= o) x += y;
-        }
-        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            unsigned long long w = wsum[threadIdx.x];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-                if (threadIdx.x >= o) w += y;
-            }
-            wsum[threadIdx.x] = w;
-        }
-        __syncthreads();
-        const unsigned long long wpre = (threadIdx.x >= 32) ? wsum[(threadIdx.x >> 5) - 1] : 0;
-        const unsigned long long excl = carry + wpre + x - v;
-        if (i < nblocks) partials[i] = (uint32_t)min(excl, 0xFFFFFFFFull);
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + v;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *n_out = (int64_t)carry;
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *__restrict__ ntiles,
-                                                            const uint32_t *__restrict__ order, long long n,
-                                                            const uint32_t *__restrict__ partials,
-                                                            uint32_t *offsets) {
-    // each thread owns kScanItems consecutive entries (blocked), so a warp
-    // scan over per-thread sums gives every entry's exclusive prefix
-    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
-    uint32_t v[kScanItems];
-    uint32_t tsum = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        v[i] = (base + i < n) ? ntiles[order[base + i]] : 0u;
-        tsum += v[i];
-    }
-    uint32_t x = tsum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) >= o) x += y;
-    }
-    __shared__ uint32_t wsum[kScanThreads / 32];
-    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
-    __syncthreads();
-    uint32_t wpre = 0;
-    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) wpre += wsum[w];
-    uint32_t run = partials[blockIdx.x] + wpre + x - tsum;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        if (base + i < n) offsets[base + i] = run;
-        run += v[i];
-    }
-}
-
-// ---------------------------------------------------------------- emit
-// Warp-cooperative duplication: each warp takes 32 depth-ordered entries and
-// writes the tile instances of each one with all 32 lanes (coalesced).
-__global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ order, const uint32_t *__restrict__ offsets,
-                                              ProjView pv, long long N, long long n_entries, CamSet cs,
-                                              uint32_t *tkey, uint32_t *tval, long long capacity,
-                                              const int64_t *n_total, unsigned *status) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    uint32_t nt = 0, off = 0, g = 0;
-    int4 tr = make_int4(0, 0, 0, 0);
-    int tile_off = 0, tiles_x = 0;
-    if (j < n_entries) {
-        const uint32_t e = order[j];
-        nt = pv.ntiles[e];
-        if (nt) {
-            const int ci = (int)(e / N);
-            g = (uint32_t)(e - (long long)ci * N);
-            tr = pv.trect[e];
-            off = offsets[j];
-            tile_off = cs.c[ci].tile_off;
-            tiles_x = cs.c[ci].tiles_x;
-        }
-    }
-    if (lane == 0 && blockIdx.x == 0 && threadIdx.x == 0 && *n_total > capacity) latch(status, ST_CAPACITY);
-    for (int k = 0; k < 32; ++k) {
-        const uint32_t n_k = __shfl_sync(0xffffffffu, nt, k);
-        if (n_k == 0) continue;
-        const uint32_t off_k = __shfl_sync(0xffffffffu, off, k);
-        const uint32_t g_k = __shfl_sync(0xffffffffu, g, k);
-        const int x0 = __shfl_sync(0xffffffffu, tr.x, k);
-        const int y0 = __shfl_sync(0xffffffffu, tr.y, k);
-        const int x1 = __shfl_sync(0xffffffffu, tr.z, k);
-        const int to = __shfl_sync(0xffffffffu, tile_off, k);
-        const int tx_n = __shfl_sync(0xffffffffu, tiles_x, k);
-        const int w = x1 - x0 + 1;
-        for (uint32_t t = lane; t < n_k; t += 32) {
-            const long long pos = (long long)off_k + t;
-            if (pos >= capacity) break;
-            const int ly = (int)(t / (uint32_t)w), lx = (int)(t - (uint32_t)ly * w);
-            tkey[pos] = (uint32_t)(to + (y0 + ly) * tx_n + x0 + lx);
-            tval[pos] = g_k;
-        }
-    }
-}
-
 // ---------------------------------------------------------------- radix
-__device__ __forceinline__ long long clamp_n(const int64_t *n_dev, long long n_host, long long cap) {
-    long long n = n_dev ? (long long)*n_dev : n_host;
-    return n < cap ? n : cap;
-}
-
 // Per-block digit histogram of the block's contiguous segment.
-__global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
-                                                                 const int64_t *n_dev, long long n_host,
-                                                                 long long cap, int shift, uint32_t mask,
-                                                                 uint32_t *hist) {
+__global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t *__restrict__ keys, long long n,
+                                                                 int shift, uint32_t mask, uint32_t *hist) {
     __shared__ uint32_t h[kRadixWarps][kBuckets];
     for (int i = threadIdx.x; i < kRadixWarps * kBuckets; i += kRadixThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    const long long n = clamp_n(n_dev, n_host, cap);
     const long long G = gridDim.x;
     const long long seg = (n + G - 1) / G;
     const long long s = blockIdx.x * seg, e = min(n, s + seg);
@@ -190,8 +52,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t 
     for (long long i0 = s; i0 < e; i0 += kRadixThreads) {
         const long long i = i0 + threadIdx.x;
         const int d = i < e ? (int)((keys[i] >> shift) & mask) : (kBuckets + (int)(threadIdx.x & 31));
-        // warp-aggregated: one shared-memory add per distinct digit
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);  // one shared add per distinct digit
         if (d < kBuckets && (peers & lt) == 0) atomicAdd(&h[w][d], (uint32_t)__popc(peers));
     }
     __syncthreads();
@@ -203,19 +64,25 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t 
     }
 }
 
-// Exclusive scan of hist (digit-major, block-minor) in place, one block.
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int total) {
+// In-place exclusive scan of a u32 array with one 1024-thread block, four
+// values per thread per step.  Optionally writes the total.
+__global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, int total, int64_t *total_out) {
     __shared__ uint32_t carry;
     __shared__ uint32_t wsum[32];
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int base = 0; base < total; base += 1024) {
-        const int i = base + threadIdx.x;
-        const uint32_t v = i < total ? hist[i] : 0u;
-        uint32_t x = v;
+    for (int base = 0; base < total; base += 4096) {
+        const int i0 = base + threadIdx.x * 4;
+        uint32_t v[4], tsum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = (i0 + k < total) ? a[i0 + k] : 0u;
+            tsum += v[k];
+        }
+        uint32_t x = tsum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if ((threadIdx.x & 31) >= o) x += y;
         }
         if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
@@ -224,19 +91,23 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int total) 
             uint32_t wv = wsum[threadIdx.x];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, wv, o);
+                const uint32_t y = __shfl_up_sync(0xffffffffu, wv, o);
                 if (threadIdx.x >= o) wv += y;
             }
             wsum[threadIdx.x] = wv;
         }
         __syncthreads();
-        const uint32_t wpre = threadIdx.x >= 32 ? wsum[(threadIdx.x >> 5) - 1] : 0u;
-        const uint32_t excl = carry + wpre + x - v;
-        if (i < total) hist[i] = excl;
+        uint32_t run = carry + (threadIdx.x >= 32 ? wsum[(threadIdx.x >> 5) - 1] : 0u) + x - tsum;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < total) a[i0 + k] = run;
+            run += v[k];
+        }
         __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + v;
+        if (threadIdx.x == 1023) carry = run;
         __syncthreads();
     }
+    if (total_out && threadIdx.x == 0) *total_out = (int64_t)carry;
 }
 
 // Stable scatter.  The block walks its segment in tiles of kRadixTile items;
@@ -245,12 +116,10 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int total) 
 // computed in that order keep the sort stable.
 __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, const int64_t *n_dev, long long n_host, long long cap, int shift, uint32_t mask,
-    const uint32_t *__restrict__ hist) {
-    __shared__ uint32_t run[kBuckets];                 // next output slot per digit
-    __shared__ uint32_t tot[kBuckets];                 // this tile's count per digit
-    __shared__ uint32_t wcnt[kRadixWarps][kBuckets];   // per-warp counts, then prefixes
-    const long long n = clamp_n(n_dev, n_host, cap);
+    uint32_t *__restrict__ vout, long long n, int shift, uint32_t mask, const uint32_t *__restrict__ hist) {
+    __shared__ uint32_t run[kBuckets];                // next output slot per digit
+    __shared__ uint32_t tot[kBuckets];                // this tile's count per digit
+    __shared__ uint32_t wcnt[kRadixWarps][kBuckets];  // per-warp counts, then prefixes
     const long long G = gridDim.x;
     const long long seg = (n + G - 1) / G;
     const long long s = blockIdx.x * seg, e = min(n, s + seg);
@@ -259,15 +128,19 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
     const unsigned lt = (1u << lane) - 1u;
     for (long long t0 = s; t0 < e; t0 += kRadixTile) {
         for (int d = lane; d < kBuckets; d += 32) wcnt[w][d] = 0;
-        __syncwarp();
         uint32_t key[kRadixRounds], val[kRadixRounds], rank[kRadixRounds];
         int dig[kRadixRounds];
+#pragma unroll
+        for (int r = 0; r < kRadixRounds; ++r) {  // loads first: all in flight together
+            const long long i = t0 + w * (32 * kRadixRounds) + r * 32 + lane;
+            key[r] = i < e ? kin[i] : 0u;
+            val[r] = i < e ? vin[i] : 0u;
+        }
+        __syncwarp();
 #pragma unroll
         for (int r = 0; r < kRadixRounds; ++r) {
             const long long i = t0 + w * (32 * kRadixRounds) + r * 32 + lane;
             const bool valid = i < e;
-            key[r] = valid ? kin[i] : 0u;
-            val[r] = valid ? vin[i] : 0u;
             // invalid lanes get a private out-of-range digit: they match no one
             dig[r] = valid ? (int)((key[r] >> shift) & mask) : (kBuckets + lane);
             const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
@@ -278,7 +151,6 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
             rank[r] = before + __popc(peers & lt);
         }
         __syncthreads();
-        // exclusive prefix over warps per digit; the sum is the tile total
         for (int d = threadIdx.x; d < kBuckets; d += kRadixThreads) {
             uint32_t acc = 0;
 #pragma unroll
@@ -304,31 +176,29 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
     }
 }
 
-// ---------------------------------------------------------------- ranges
-__global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ tkey, const int64_t *n_dev, long long cap,
-                                                uint32_t *ranges) {
-    const long long n = clamp_n(n_dev, 0, cap);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const uint32_t t = tkey[i];
-        if (i == 0 || tkey[i - 1] != t) ranges[2 * (long long)t] = (uint32_t)i;
-        if (i == n - 1 || tkey[i + 1] != t) ranges[2 * (long long)t + 1] = (uint32_t)(i + 1);
+__global__ void k_iota_keys(const uint32_t *__restrict__ dkey, long long n, uint32_t *k, uint32_t *v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        k[i] = dkey[i];
+        v[i] = (uint32_t)i;
     }
 }
 
-__global__ void __launch_bounds__(256) k_keys64(const uint32_t *__restrict__ tkey, const uint32_t *__restrict__ gid,
-                                                const int64_t *n_dev, long long cap, ProjView pv, long long N,
-                                                CamSet cs, uint64_t *keys) {
-    const long long n = clamp_n(n_dev, 0, cap);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const uint32_t t = tkey[i];
-        const int ci = cam_of_tile(cs, (int)t);
-        keys[i] = ((uint64_t)t << 32) | pv.dkey[(long long)ci * N + gid[i]];
-    }
+__global__ void k_cam_keys(const uint32_t *__restrict__ order, long long n, long long N, uint32_t *k) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) k[i] = (uint32_t)(order[i] / N);
 }
 
-void radix_sort_pairs(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, const int64_t *n_dev, long long n_host,
-                      long long cap, int bits, uint32_t *hist, int G, cudaStream_t st) {
-    // data starts in (kA, vA); passes alternate A->B, B->A
+int radix_blocks(long long n, int sm_count) {
+    long long g = (n + 4095) / 4096;
+    if (g > 2ll * sm_count) g = 2ll * sm_count;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// Sorts (kA, vA) by the low `bits` bits of kA; returns true if the result is
+// in (kB, vB) (odd number of passes), false if back in (kA, vA).
+bool radix_sort_pairs(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, long long n, int bits,
+                      uint32_t *hist, int G, cudaStream_t st) {
     int shift = 0;
     bool a_to_b = true;
     while (shift < bits) {
@@ -339,27 +209,219 @@ void radix_sort_pairs(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, co
         uint32_t *ko = a_to_b ? kB : kA;
         uint32_t *vo = a_to_b ? vB : vA;
         note_launch(3);
-        k_radix_upsweep<<<G, kRadixThreads, 0, st>>>(ki, n_dev, n_host, cap, shift, mask, hist);
-        k_radix_scan<<<1, 1024, 0, st>>>(hist, kBuckets * G);
-        k_radix_downsweep<<<G, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n_dev, n_host, cap, shift, mask, hist);
+        k_radix_upsweep<<<G, kRadixThreads, 0, st>>>(ki, n, shift, mask, hist);
+        k_scan_small<<<1, 1024, 0, st>>>(hist, kBuckets * G, nullptr);
+        k_radix_downsweep<<<G, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n, shift, mask, hist);
         shift += nb;
         a_to_b = !a_to_b;
     }
+    return !a_to_b;
 }
 
-int radix_passes(int bits) { return (bits + 7) / 8; }
+// ------------------------------------------------------- tile counting
+// One block per (segment, camera): per-tile counts of the segment's Gaussians
+// via a 2-D difference array of the camera's tile grid.  Writes
+// table[(tile_off + tile) * S + seg].
+__global__ void __launch_bounds__(256) k_seg_count(const uint32_t *__restrict__ order, ProjView pv, long long N,
+                                                   int SEG, int S, CamSet cs, uint32_t *table) {
+    extern __shared__ int diff[];
+    const int seg = blockIdx.x, ci = blockIdx.y;
+    const DevCam &cam = cs.c[ci];
+    const int tx = cam.tiles_x, ty = cam.tiles_y, pitch = tx + 1;
+    const int cells = pitch * (ty + 1);
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) diff[i] = 0;
+    __syncthreads();
+    const long long b0 = (long long)ci * N + (long long)seg * SEG;
+    const long long b1 = min((long long)(ci + 1) * N, b0 + SEG);
+    for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        const uint32_t e = order[i];
+        if (pv.ntiles[e] == 0) continue;
+        const int4 r = pv.trect[e];
+        atomicAdd(&diff[r.y * pitch + r.x], 1);
+        atomicAdd(&diff[r.y * pitch + r.z + 1], -1);
+        atomicAdd(&diff[(r.w + 1) * pitch + r.x], -1);
+        atomicAdd(&diff[(r.w + 1) * pitch + r.z + 1], 1);
+    }
+    __syncthreads();
+    for (int y = threadIdx.x; y < ty; y += blockDim.x) {  // prefix along x
+        int acc = 0;
+        for (int x = 0; x < tx; ++x) {
+            acc += diff[y * pitch + x];
+            diff[y * pitch + x] = acc;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < tx; x += blockDim.x) {  // prefix along y
+        int acc = 0;
+        for (int y = 0; y < ty; ++y) {
+            acc += diff[y * pitch + x];
+            diff[y * pitch + x] = acc;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tx * ty; t += blockDim.x) {
+        const int y = t / tx, x = t - y * tx;
+        table[(long long)(cam.tile_off + t) * S + seg] = (uint32_t)diff[y * pitch + x];
+    }
+}
+
+// ------------------------------------------------------------- big scan
+// Exclusive scan of a long u32 array: block sums, scan of the sums, then a
+// block-local rescan with the offsets.
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ a, long long n,
+                                                              uint32_t *partials) {
+    const long long base = (long long)blockIdx.x * kScanTile;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const long long j = base + i * kScanThreads + threadIdx.x;
+        if (j < n) sum += a[j];
+    }
+    __shared__ uint32_t red[kScanThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) s += red[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t *a, long long n,
+                                                            const uint32_t *__restrict__ partials) {
+    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? a[base + i] : 0u;
+        tsum += v[i];
+    }
+    uint32_t x = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) >= o) x += y;
+    }
+    __shared__ uint32_t wsum[kScanThreads / 32];
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) wpre += wsum[w];
+    uint32_t run = partials[blockIdx.x] + wpre + x - tsum;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) a[base + i] = run;
+        run += v[i];
+    }
+}
+
+// ------------------------------------------------------------- scatter
+constexpr int kScatterWarps = 2;
+constexpr int kStage = 128;  // entries staged in shared memory per step
+
+// One warp per (segment, camera): walks the segment's Gaussians in depth
+// order, writing each one into every tile of its rectangle at the tile's
+// running offset.  Within one Gaussian all tiles differ, so the 32 lanes
+// update distinct counters; Gaussians follow one another in order.
+__global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32_t *__restrict__ order, ProjView pv,
+                                                                     long long N, int SEG, int S, CamSet cs,
+                                                                     const uint32_t *__restrict__ table,
+                                                                     int max_tiles, uint32_t *gids,
+                                                                     long long capacity) {
+    extern __shared__ uint32_t sh[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = blockIdx.x * kScatterWarps + warp, ci = blockIdx.y;
+    if (seg >= S) return;  // warp-uniform; the kernel uses no block barrier
+    const int stride = (max_tiles + kStage * 6 + 3) & ~3;  // per-warp words, 16-byte multiple
+    uint32_t *ctr = sh + warp * stride;
+    int4 *st_r = reinterpret_cast<int4 *>(ctr + ((max_tiles + 3) & ~3));  // staged rectangles
+    uint32_t *st_g = reinterpret_cast<uint32_t *>(st_r + kStage);        // staged Gaussian index
+    uint32_t *st_n = st_g + kStage;                                      // staged tile count
+    const DevCam &cam = cs.c[ci];
+    const int tx = cam.tiles_x, T = cam.tiles_x * cam.tiles_y;
+    for (int t = lane; t < T; t += 32) ctr[t] = table[(long long)(cam.tile_off + t) * S + seg];
+    const long long b0 = (long long)ci * N + (long long)seg * SEG;
+    const long long b1 = min((long long)(ci + 1) * N, b0 + SEG);
+    for (long long c0 = b0; c0 < b1; c0 += kStage) {
+        const int m = (int)min((long long)kStage, b1 - c0);
+        __syncwarp();
+        for (int k = lane; k < m; k += 32) {
+            const uint32_t e = order[c0 + k];
+            const uint32_t nt = pv.ntiles[e];
+            st_g[k] = (uint32_t)(e - (long long)ci * N);
+            st_n[k] = nt;
+            if (nt) st_r[k] = pv.trect[e];
+        }
+        __syncwarp();
+        for (int k = 0; k < m; ++k) {
+            const uint32_t nt = st_n[k];
+            if (nt == 0) continue;
+            const int4 r = st_r[k];
+            const uint32_t g = st_g[k];
+            const int w = r.z - r.x + 1;
+            for (uint32_t q = lane; q < nt; q += 32) {
+                const int qy = (int)(q / (uint32_t)w), qx = (int)(q - (uint32_t)qy * w);
+                const int t = (r.y + qy) * tx + r.x + qx;
+                const uint32_t pos = ctr[t];
+                if (pos < capacity) gids[pos] = g;
+                ctr[t] = pos + 1;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_table_ranges(const uint32_t *__restrict__ table, int S, int total_tiles,
+                                                      const int64_t *total, long long capacity, uint32_t *ranges,
+                                                      unsigned *status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = *total;
+    if (t == 0 && tot > capacity) latch(status, ST_CAPACITY);
+    if (t >= total_tiles) return;
+    const long long s = table[(long long)t * S];
+    const long long e = (t + 1 < total_tiles) ? (long long)table[(long long)(t + 1) * S] : tot;
+    const bool empty = e <= s;  // empty tiles read (0, 0)
+    ranges[2 * (long long)t] = empty ? 0u : (uint32_t)min(s, capacity);
+    ranges[2 * (long long)t + 1] = empty ? 0u : (uint32_t)min(e, capacity);
+}
+
+// 64-bit sort keys of the sorted instances (optional output).
+__global__ void __launch_bounds__(256) k_keys64(const uint32_t *__restrict__ ranges, const uint32_t *__restrict__ gids,
+                                                ProjView pv, long long N, CamSet cs, uint64_t *keys) {
+    const int t = blockIdx.x;
+    const int ci = cam_of_tile(cs, t);
+    const uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+    for (uint32_t i = s + threadIdx.x; i < e; i += blockDim.x)
+        keys[i] = ((uint64_t)t << 32) | pv.dkey[(long long)ci * N + gids[i]];
+}
+
+int seg_size(long long N, int total_tiles) {
+    int seg = 512;
+    while ((long long)total_tiles * ((N + seg - 1) / seg) > (32ll << 20) && seg < (1 << 20)) seg <<= 1;
+    return seg;
+}
 
 }  // namespace
 
-size_t bin_scratch_bytes(long long cn, long long capacity, int radix_blocks) {
-    const long long nparts = (cn + kScanTile - 1) / kScanTile + 1;
-    return 5 * align_up(sizeof(uint32_t) * (cn + 1), 256) + align_up(sizeof(uint32_t) * nparts, 256) +
-           align_up(sizeof(uint32_t) * kBuckets * (size_t)radix_blocks, 256) +
-           3 * align_up(sizeof(uint32_t) * (capacity + 1), 256) + 256;
+size_t bin_scratch_bytes(long long N, int n_cams, int total_tiles, int sm_count) {
+    const long long cn = N * n_cams;
+    const int SEG = seg_size(N, total_tiles);
+    const long long S = (N + SEG - 1) / SEG;
+    const long long tab = (long long)total_tiles * (S > 0 ? S : 1);
+    const int G = 2 * sm_count;
+    return 4 * align_up(sizeof(uint32_t) * (cn + 1), 256) + align_up(sizeof(uint32_t) * (tab + 1), 256) +
+           align_up(sizeof(uint32_t) * ((tab + kScanTile - 1) / kScanTile + 1), 256) +
+           align_up(sizeof(uint32_t) * kBuckets * (size_t)G, 256) + 256;
 }
 
-BinScratch bin_scratch_view(void *base, long long cn, long long capacity, int radix_blocks) {
-    const long long nparts = (cn + kScanTile - 1) / kScanTile + 1;
+BinScratch bin_scratch_view(void *base, long long N, int n_cams, int total_tiles, int sm_count) {
+    const long long cn = N * n_cams;
+    const int SEG = seg_size(N, total_tiles);
+    const long long S = (N + SEG - 1) / SEG;
+    const long long tab = (long long)total_tiles * (S > 0 ? S : 1);
     char *p = (char *)align_up((size_t)base, 256);
     BinScratch s;
     auto take = [&](size_t bytes) {
@@ -371,64 +433,68 @@ BinScratch bin_scratch_view(void *base, long long cn, long long capacity, int ra
     s.dv_a = take(sizeof(uint32_t) * (cn + 1));
     s.dk_b = take(sizeof(uint32_t) * (cn + 1));
     s.dv_b = take(sizeof(uint32_t) * (cn + 1));
-    s.offsets = take(sizeof(uint32_t) * (cn + 1));
-    s.partials = take(sizeof(uint32_t) * nparts);
-    s.hist = take(sizeof(uint32_t) * kBuckets * (size_t)radix_blocks);
-    s.tk_a = take(sizeof(uint32_t) * (capacity + 1));
-    s.tk_b = take(sizeof(uint32_t) * (capacity + 1));
-    s.tv_a = take(sizeof(uint32_t) * (capacity + 1));
-    s.radix_blocks = radix_blocks;
+    s.table = take(sizeof(uint32_t) * (tab + 1));
+    s.partials = take(sizeof(uint32_t) * ((tab + kScanTile - 1) / kScanTile + 1));
+    s.hist = take(sizeof(uint32_t) * kBuckets * (size_t)(2 * sm_count));
+    s.seg = SEG;
+    s.nseg = (int)S;
+    s.sm_count = sm_count;
     return s;
 }
 
-__global__ void k_iota_keys(const uint32_t *__restrict__ dkey, long long n, uint32_t *k, uint32_t *v) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        k[i] = dkey[i];
-        v[i] = (uint32_t)i;
-    }
-}
-
 void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, const fhgs_bins &bins, BinScratch sc,
-                     unsigned *status, int sm_count, cudaStream_t st) {
+                     unsigned *status, cudaStream_t st) {
     const long long cn = (long long)n_cams * N;
-    const int G = sc.radix_blocks;
     cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)cs.total_tiles, st);
-    if (cn == 0) {
-        cudaMemsetAsync(bins.n_instances, 0, sizeof(int64_t), st);
-        return;
-    }
-    // 1. depth order of all (camera, Gaussian) entries (culled ones last)
+    cudaMemsetAsync(bins.n_instances, 0, sizeof(int64_t), st);
+    if (cn == 0) return;
+    // 1. depth order of all (camera, Gaussian) entries, then grouped by camera
+    const int G = radix_blocks(cn, sc.sm_count);
     note_launch(1);
     k_iota_keys<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(pv.dkey, cn, sc.dk_a, sc.dv_a);
-    radix_sort_pairs(sc.dk_a, sc.dv_a, sc.dk_b, sc.dv_b, nullptr, cn, cn, 32, sc.hist, G, st);
-    const uint32_t *order = sc.dv_a;  // 4 passes: result back in A
-    // 2. instance offsets in depth order
-    const unsigned nparts = (unsigned)((cn + kScanTile - 1) / kScanTile);
+    const bool in_b = radix_sort_pairs(sc.dk_a, sc.dv_a, sc.dk_b, sc.dv_b, cn, 32, sc.hist, G, st);
+    uint32_t *order = in_b ? sc.dv_b : sc.dv_a;
+    if (n_cams > 1) {
+        uint32_t *ck = in_b ? sc.dk_b : sc.dk_a;  // reuse the key buffer for camera ids
+        note_launch(1);
+        k_cam_keys<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(order, cn, N, ck);
+        uint32_t *ok2 = in_b ? sc.dk_a : sc.dk_b, *ov2 = in_b ? sc.dv_a : sc.dv_b;
+        int bits = 1;
+        while ((1 << bits) < n_cams) ++bits;
+        if (radix_sort_pairs(ck, order, ok2, ov2, cn, bits, sc.hist, G, st)) order = ov2;
+    }
+    // 2. per-segment tile counts
+    const int SEG = sc.seg, S = sc.nseg;
+    int max_cells = 0, max_tiles = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        max_cells = max(max_cells, (cs.c[c].tiles_x + 1) * (cs.c[c].tiles_y + 1));
+        max_tiles = max(max_tiles, cs.c[c].tiles_x * cs.c[c].tiles_y);
+    }
+    const int count_smem = max_cells * (int)sizeof(int);
+    cudaFuncSetAttribute(k_seg_count, cudaFuncAttributeMaxDynamicSharedMemorySize, count_smem);
+    note_launch(1);
+    k_seg_count<<<dim3(S, n_cams), 256, count_smem, st>>>(order, pv, N, SEG, S, cs, sc.table);
+    // 3. scan of the (tile, segment) table: segment offsets and the total
+    const long long tab = (long long)cs.total_tiles * S;
+    const unsigned nparts = (unsigned)((tab + kScanTile - 1) / kScanTile);
     note_launch(3);
-    k_scan_reduce<<<nparts, kScanThreads, 0, st>>>(pv.ntiles, order, cn, sc.partials);
-    k_scan_partials<<<1, 1024, 0, st>>>(sc.partials, (int)nparts, bins.n_instances);
-    k_scan_down<<<nparts, kScanThreads, 0, st>>>(pv.ntiles, order, cn, sc.partials, sc.offsets);
-    // 3. emit, then stable sort by global tile id into bins.gids
-    int bits = 1;
-    while ((1ll << bits) < (long long)cs.total_tiles) ++bits;
-    const int passes = radix_passes(bits);
-    uint32_t *k0 = (passes % 2 == 0) ? sc.tk_a : sc.tk_b;
-    uint32_t *v0 = (passes % 2 == 0) ? bins.gids : sc.tv_a;
-    uint32_t *k1 = (passes % 2 == 0) ? sc.tk_b : sc.tk_a;
-    uint32_t *v1 = (passes % 2 == 0) ? sc.tv_a : bins.gids;
+    k_scan_reduce<<<nparts, kScanThreads, 0, st>>>(sc.table, tab, sc.partials);
+    k_scan_small<<<1, 1024, 0, st>>>(sc.partials, (int)nparts, bins.n_instances);
+    k_scan_down<<<nparts, kScanThreads, 0, st>>>(sc.table, tab, sc.partials);
+    // 4. tile ranges, then the scatter of Gaussian indices
     note_launch(1);
-    k_emit<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(order, sc.offsets, pv, N, cn, cs, k0, v0, bins.capacity,
-                                                         bins.n_instances, status);
-    radix_sort_pairs(k0, v0, k1, v1, bins.n_instances, 0, bins.capacity, bits, sc.hist, G, st);
-    // final data is in (k0, v0) when passes is even, (k1, v1) when odd; both
-    // choices put the values in bins.gids
-    const uint32_t *tk = (passes % 2 == 0) ? k0 : k1;
-    const int grid = sm_count * 8;
+    k_table_ranges<<<(cs.total_tiles + 255) / 256, 256, 0, st>>>(sc.table, S, cs.total_tiles, bins.n_instances,
+                                                                 bins.capacity, bins.ranges, status);
+    const int stride_words = (((max_tiles + 3) & ~3) + kStage * 6 + 3) & ~3;
+    const int scat_smem = kScatterWarps * stride_words * (int)sizeof(uint32_t);
+    cudaFuncSetAttribute(k_seg_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, scat_smem);
     note_launch(1);
-    k_ranges<<<grid, 256, 0, st>>>(tk, bins.n_instances, bins.capacity, bins.ranges);
-    if (bins.keys) note_launch(1);
-    if (bins.keys) k_keys64<<<grid, 256, 0, st>>>(tk, bins.gids, bins.n_instances, bins.capacity, pv, N, cs, bins.keys);
+    k_seg_scatter<<<dim3((S + kScatterWarps - 1) / kScatterWarps, n_cams), kScatterWarps * 32, scat_smem, st>>>(
+        order, pv, N, SEG, S, cs, sc.table, max_tiles, bins.gids, bins.capacity);
+    if (bins.keys) {
+        note_launch(1);
+        k_keys64<<<cs.total_tiles, 256, 0, st>>>(bins.ranges, bins.gids, pv, N, cs, bins.keys);
+    }
 }
 
 }  // namespace fhgs

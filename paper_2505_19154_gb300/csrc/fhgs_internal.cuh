@@ -112,16 +112,15 @@ void launch_project_bwd(const fhgs_gaussians &g, const CamSet &cs, const Params 
 // binning (binning.cu)
 struct BinScratch {
     uint32_t *dk_a, *dv_a, *dk_b, *dv_b;  // depth sort [C*N]
-    uint32_t *offsets;                    // [C*N]
-    uint32_t *partials;                   // scan partials
+    uint32_t *table;                      // per (tile, segment) counts, then offsets
+    uint32_t *partials;                   // scan partials of the table
     uint32_t *hist;                       // radix histogram [256][G]
-    uint32_t *tk_a, *tk_b, *tv_a;         // tile sort [capacity]
-    int radix_blocks;
+    int seg, nseg, sm_count;              // segment size, segments per camera
 };
-size_t bin_scratch_bytes(long long cn, long long capacity, int radix_blocks);
-BinScratch bin_scratch_view(void *base, long long cn, long long capacity, int radix_blocks);
+size_t bin_scratch_bytes(long long N, int n_cams, int total_tiles, int sm_count);
+BinScratch bin_scratch_view(void *base, long long N, int n_cams, int total_tiles, int sm_count);
 void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, const fhgs_bins &bins,
-                     BinScratch sc, unsigned *status, int sm_count, cudaStream_t st);
+                     BinScratch sc, unsigned *status, cudaStream_t st);
 
 // render, FP32 CUDA-core path (render_fp32.cu)
 void launch_render_fwd_fp32(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,

@@ -134,6 +134,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive TMEM columns of this warp's 32 lanes -> 16 floats per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, bool valid) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(valid ? 16 : 0)
                  : "memory");
@@ -154,27 +168,29 @@ __device__ __forceinline__ uint8_t *align_smem_1024(uint8_t *raw) {
     return raw + ((1024u - (smem_u32(raw) & 1023u)) & 1023u);
 }
 
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
 // ------------------------------------------------------------- forward
 constexpr int kFB = 64;  // Gaussians per forward batch (MMA K)
 
+// 256 threads: two groups of 4 warps share the half tile's 128 pixels; group g
+// weighs Gaussians [32 g, 32 g + 32) of each batch.  Both groups evaluate
+// their alphas at once; group 0 then runs the transmittance chain over its 32
+// and hands (T, done, last) to group 1 through shared memory.
 template <int DN>
 struct FwdCfg {
     static constexpr int kWBytes = 128 * 128;            // 128 px x 64 BF16 weights
     static constexpr int kFBytes = kFB * DN * 2;         // 64 rows x DN BF16 features
     static constexpr int kNSub = DN > 256 ? DN / 256 : 1;
     static constexpr int kMmaN = DN > 256 ? 256 : DN;
-    static constexpr int kRecBytes = kFB * (16 + 16 + 4 + 4);
-    static constexpr int kSmem = 1024 + 2 * kWBytes + 2 * kFBytes + 2 * kRecBytes + 64;
+    static constexpr int kRecBytes = kFB * 48 + kFB * 4;
+    static constexpr int kOffF = 2 * kWBytes;
+    static constexpr int kOffRec = kOffF + 2 * kFBytes;
+    static constexpr int kOffX = kOffRec + 2 * kRecBytes;   // per-pixel exchange: T, done, last, rgb
+    static constexpr int kOffBar = kOffX + 128 * 24;
+    static constexpr int kSmem = 1024 + kOffBar + 64;
 };
 
 template <int DN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     k_render_fwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                     const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats, int D,
                     float *rgb, float *feat, float *Tout, int32_t *last_out, unsigned *status) {
@@ -182,21 +198,24 @@ __global__ void __launch_bounds__(128, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
     uint8_t *sW = sm;                                   // [2][128 rows][128 B]
-    uint8_t *sF = sm + 2 * C::kWBytes;                  // [2][DN/64 blocks][64 rows][128 B]
-    float4 *sA = reinterpret_cast<float4 *>(sF + 2 * C::kFBytes);  // [2][64]
-    float4 *sB = sA + 2 * kFB;                          // [2][64]
-    float *sBl = reinterpret_cast<float *>(sB + 2 * kFB);          // [2][64]
-    uint32_t *sGid = reinterpret_cast<uint32_t *>(sBl + 2 * kFB);  // [2][64]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sGid + 2 * kFB);  // [2]
+    float *xT = reinterpret_cast<float *>(sm + C::kOffX);        // [128]
+    int *xDone = reinterpret_cast<int *>(xT + 128);               // [128]
+    int *xLast = xDone + 128;                                     // [128]
+    float *xRgb = reinterpret_cast<float *>(xLast + 128);        // [128][3]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + C::kOffBar);  // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    auto srec = [&](int stg) { return reinterpret_cast<GRec *>(sm + C::kOffRec + stg * C::kRecBytes); };
+    auto sgid = [&](int stg) {
+        return reinterpret_cast<uint32_t *>(sm + C::kOffRec + stg * C::kRecBytes + kFB * 48);
+    };
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, grp = tid >> 7, pidx = tid & 127;
     const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, chunk = blockIdx.y;
     const int ci = cam_of_tile(cs, tile);
     const DevCam &cam = cs.c[ci];
     const int lt = tile - cam.tile_off;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    const int px = tx * kTile + (tid & 15), py = ty * kTile + half * 8 + (tid >> 4);
+    const int px = tx * kTile + (pidx & 15), py = ty * kTile + half * 8 + (pidx >> 4);
     const bool inside = px < cam.W && py < cam.H;
     const long long pix = cam.pix_off + (long long)py * cam.W + px;
     const uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
@@ -209,99 +228,134 @@ __global__ void __launch_bounds__(128, 1)
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
+    if (grp == 0) {
+        xT[pidx] = 1.f;
+        xDone[pidx] = inside ? 0 : 1;
+        xLast[pidx] = 0;
+    }
+    const uint32_t sW_s = smem_u32(sW), sF_s = smem_u32(sm + C::kOffF);
+    constexpr uint32_t idesc = idesc_bf16(128, C::kMmaN, false, true);
+
+    auto load_rec = [&](uint32_t base, int stg) {  // group A: Gaussian ids + records
+        const int nb = (int)min((uint32_t)kFB, e - base);
+        if (tid < kFB) sgid(stg)[tid] = tid < nb ? __ldg(gids + base + tid) : 0u;
+        if (tid < nb) {
+            const uint32_t gid = sgid(stg)[tid];
+            const uint32_t dst = smem_u32(srec(stg) + tid);
+            const GRec *src = rec + gid;
+            cp_async16(dst, &src->a, true);
+            cp_async16(dst + 16, &src->b, true);
+            cp_async16(dst + 32, &src->c, true);
+        }
+        cp_async_commit();
+    };
+    auto load_feat = [&](uint32_t base, int stg) {  // group B: feature rows, zero-filled past the end
+        // reads the ids that load_rec stored for this stage (a barrier lies between)
+        const int nb = (int)min((uint32_t)kFB, e - base);
+        constexpr int kCPR = DN / 8;
+        const uint32_t fb = sF_s + stg * C::kFBytes;
+        const uint32_t *ids = sgid(stg);
+#pragma unroll 4
+        for (int q = tid; q < kFB * kCPR; q += 256) {
+            const int g = q / kCPR, c = q - g * kCPR;
+            const bool valid = g < nb;
+            const uint32_t gid = ids[g];
+            cp_async16(fb + (c >> 3) * (kFB * 128) + swz(g, c & 7), feats + (size_t)gid * D + d0 + c * 8, valid);
+        }
+        cp_async_commit();
+    };
+
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t taddr = *tslot;
-    const uint32_t sW_s = smem_u32(sW), sF_s = smem_u32(sF);
-    constexpr uint32_t idesc = idesc_bf16(128, C::kMmaN, false, true);
 
     const float fpx = px + 0.5f, fpy = py + 0.5f;
-    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
-    int last = 0;
-    bool done = !inside;
-    uint32_t phase0 = 0, phase1 = 0;
+    float cr = 0.f, cg = 0.f, cb = 0.f;  // this group's share of the colour
+    uint32_t ph[2] = {0u, 0u};
     int nbatch = 0;
     bool timeout = false;
-
+    if (s < e) load_rec(s, 0);
+    __syncthreads();
+    if (s < e) load_feat(s, 0);
     for (uint32_t base = s; base < e; base += kFB) {
         const int stg = nbatch & 1;
         const int nb = (int)min((uint32_t)kFB, e - base);
-        if (nbatch >= 2) {  // the MMA of batch nbatch-2 must be done reading this stage
-            const bool ok = mbar_wait(&bar[stg], stg ? phase1 : phase0);
-            if (stg) phase1 ^= 1u; else phase0 ^= 1u;
+        const bool more = base + kFB < e;
+        if (more) load_rec(base + kFB, stg ^ 1);
+        else cp_async_commit();
+        asm volatile("cp.async.wait_group 2;" ::: "memory");  // this batch's records
+        __syncthreads();
+        // alphas of this group's 32 Gaussians (no dependence on T)
+        const GRec *R = srec(stg);
+        float a[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+            const int j = grp * 32 + jj;
+            const float4 A4 = R[j].a, B4 = R[j].b;
+            const float dx = fpx - A4.x, dy = fpy - A4.y;
+            const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
+            const float al = fminf(p.amax, B4.y * __expf(-0.5f * q2));
+            a[jj] = (j < nb && q2 <= p.cut && al >= p.amin) ? al : 0.f;
+        }
+        // transmittance chain: group 0 first, then group 1 from group 0's state
+        uint8_t *wb = sW + stg * C::kWBytes;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            if (grp == g) {
+                float T = xT[pidx];
+                bool done = xDone[pidx] != 0;
+                int last = xLast[pidx];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float w8[8];
+#pragma unroll
+                    for (int h = 0; h < 8; ++h) {
+                        const int jj = 8 * q + h, j = grp * 32 + jj;
+                        bool ok = a[jj] > 0.f && !done;
+                        const float Tn = T * (1.f - a[jj]);
+                        const bool stop = ok && Tn < p.teps;
+                        done = done || stop;
+                        ok = ok && !stop;
+                        const float w = ok ? a[jj] * T : 0.f;
+                        w8[h] = w;
+                        if (ok) {
+                            const float4 B4 = R[j].b;
+                            cr += w * B4.z;
+                            cg += w * B4.w;
+                            cb += w * R[j].c.x;
+                            T = Tn;
+                            last = (int)(base - s) + j + 1;
+                        }
+                    }
+                    uint4 pk;
+                    pk.x = pack_bf16(w8[0], w8[1]);
+                    pk.y = pack_bf16(w8[2], w8[3]);
+                    pk.z = pack_bf16(w8[4], w8[5]);
+                    pk.w = pack_bf16(w8[6], w8[7]);
+                    *reinterpret_cast<uint4 *>(wb + swz(pidx, grp * 4 + q)) = pk;
+                }
+                xT[pidx] = T;
+                xDone[pidx] = done ? 1 : 0;
+                xLast[pidx] = last;
+            }
+            __syncthreads();
+        }
+        // the feature stage of batch k+1 is free once the MMA of batch k-1 is done
+        if (nbatch >= 1) {
+            const int ps = stg ^ 1;
+            const bool ok = mbar_wait(&bar[ps], ph[ps]);
+            ph[ps] ^= 1u;
             if (__syncthreads_or(!ok)) {
                 timeout = true;
                 break;
             }
         }
-        if (tid < kFB) sGid[stg * kFB + tid] = tid < nb ? gids[base + tid] : 0u;
-        __syncthreads();
-        {   // feature rows of the batch -> sF[stg]; rows >= nb are zero-filled
-            constexpr int kCPR = DN / 8;
-            const uint32_t fb = sF_s + stg * C::kFBytes;
-#pragma unroll 4
-            for (int q = tid; q < kFB * kCPR; q += 128) {
-                const int g = q / kCPR, c = q - g * kCPR;
-                const bool valid = g < nb;
-                const __nv_bfloat16 *src = feats + (size_t)sGid[stg * kFB + (valid ? g : 0)] * D + d0 + c * 8;
-                cp_async16(fb + (c >> 3) * (kFB * 128) + swz(g, c & 7), src, valid);
-            }
-            cp_async_commit();
-        }
-        if (tid < nb) {
-            const GRec r = rec[sGid[stg * kFB + tid]];
-            sA[stg * kFB + tid] = r.a;
-            sB[stg * kFB + tid] = r.b;
-            sBl[stg * kFB + tid] = r.c.x;
-        }
-        __syncthreads();
-        {   // compositing weights of this pixel -> row `tid` of W[stg]
-            const float4 *A4 = sA + stg * kFB;
-            const float4 *B4 = sB + stg * kFB;
-            const float *Bl = sBl + stg * kFB;
-            uint8_t *wb = sW + stg * C::kWBytes;
-#pragma unroll 1
-            for (int j0 = 0; j0 < kFB; j0 += 8) {
-                float w8[8];
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const int j = j0 + jj;
-                    float w = 0.f;
-                    if (!done && j < nb) {
-                        const float4 a = A4[j], b = B4[j];
-                        const float dx = fpx - a.x, dy = fpy - a.y;
-                        const float q2 = eval_q2(dx, dy, a.z, a.w, b.x);
-                        if (q2 <= p.cut) {
-                            const float al = fminf(p.amax, b.y * __expf(-0.5f * q2));
-                            if (al >= p.amin) {
-                                const float Tn = T * (1.f - al);
-                                if (Tn < p.teps) {
-                                    done = true;
-                                } else {
-                                    w = al * T;
-                                    cr += w * b.z;
-                                    cg += w * b.w;
-                                    cb += w * Bl[j];
-                                    T = Tn;
-                                    last = (int)(base - s) + j + 1;
-                                }
-                            }
-                        }
-                    }
-                    w8[jj] = w;
-                }
-                uint4 pk;
-                pk.x = pack_bf16(w8[0], w8[1]);
-                pk.y = pack_bf16(w8[2], w8[3]);
-                pk.z = pack_bf16(w8[4], w8[5]);
-                pk.w = pack_bf16(w8[6], w8[7]);
-                *reinterpret_cast<uint4 *>(wb + swz(tid, j0 >> 3)) = pk;
-            }
-        }
-        cp_async_wait_all();
+        if (more) load_feat(base + kFB, stg ^ 1);
+        else cp_async_commit();
+        asm volatile("cp.async.wait_group 2;" ::: "memory");  // this batch's features
         fence_async_smem();
-        const int all_done = __syncthreads_and(done);
+        const int all_done = __syncthreads_and(xDone[pidx] != 0);
         if (tid == 0) {
             tc_after();
             const uint32_t wa = sW_s + stg * C::kWBytes, fb = sF_s + stg * C::kFBytes;
@@ -319,26 +373,30 @@ __global__ void __launch_bounds__(128, 1)
         ++nbatch;
         if (all_done) break;
     }
+    cp_async_wait_all();
 
     if (nbatch > 0 && !timeout) {  // the last commit covers every MMA issued before it
-        const int stg = (nbatch - 1) & 1;
-        const bool ok = mbar_wait(&bar[stg], stg ? phase1 : phase0);
+        const int ls = (nbatch - 1) & 1;
+        const bool ok = mbar_wait(&bar[ls], ph[ls]);
         if (__syncthreads_or(!ok)) timeout = true;
     }
     if (timeout) {
         if (tid == 0) latch(status, ST_TIMEOUT);
         if (nbatch > 0) {
-            const int stg = (nbatch - 1) & 1;
-            mbar_wait(&bar[stg], stg ? phase1 : phase0);
+            const int ls = (nbatch - 1) & 1;
+            mbar_wait(&bar[ls], ph[ls]);
         }
     } else {
         tc_after();
-        float *fo = feat + pix * D + d0;
+        // 8 warps drain the accumulator: warp w reads lanes 32 (w % 4).., columns
+        // [(w / 4) DN/2, (w / 4 + 1) DN/2)
+        const int cbase = grp * (DN / 2);
+        float *fo = feat + pix * D + d0 + cbase;
 #pragma unroll 1
-        for (int cc = 0; cc < DN / 32; ++cc) {
+        for (int cc = 0; cc < DN / 64; ++cc) {
             float v[32];
             if (nbatch > 0) {
-                tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + cc * 32, v);
+                tmem_ld32(taddr + ((uint32_t)((warp & 3) * 32) << 16) + cbase + cc * 32, v);
             } else {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = 0.f;
@@ -349,12 +407,21 @@ __global__ void __launch_bounds__(128, 1)
                 for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             }
         }
-        if (chunk == 0 && inside) {
-            rgb[3 * pix + 0] = cr + T * p.bg0;
-            rgb[3 * pix + 1] = cg + T * p.bg1;
-            rgb[3 * pix + 2] = cb + T * p.bg2;
-            Tout[pix] = T;
-            last_out[pix] = last;
+        if (chunk == 0) {
+            if (grp == 1) {
+                xRgb[3 * pidx] = cr;
+                xRgb[3 * pidx + 1] = cg;
+                xRgb[3 * pidx + 2] = cb;
+            }
+            __syncthreads();
+            if (grp == 0 && inside) {
+                const float T = xT[pidx];
+                rgb[3 * pix + 0] = cr + xRgb[3 * pidx] + T * p.bg0;
+                rgb[3 * pix + 1] = cg + xRgb[3 * pidx + 1] + T * p.bg1;
+                rgb[3 * pix + 2] = cb + xRgb[3 * pidx + 2] + T * p.bg2;
+                Tout[pix] = T;
+                last_out[pix] = xLast[pidx];
+            }
         }
     }
     tc_before();
@@ -365,16 +432,57 @@ __global__ void __launch_bounds__(128, 1)
 // ------------------------------------------------------------- backward
 constexpr int kBB = 64;  // Gaussians per backward batch
 
+// One step of a warp reduce-scatter: lanes with bit `off` set keep the upper
+// H values, the others the lower H, each adding its partner's copy.
+template <int H>
+__device__ __forceinline__ void rs_step(float *v, int lane, int off) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float send = up ? v[i] : v[i + H];
+        const float keep = up ? v[i + H] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+}
+
+// Warp sums of 4 per-lane values: lane l returns the total of value (l >> 3) & 3.
+__device__ __forceinline__ float warp_rs4(float *v, int lane) {
+    rs_step<2>(v, lane, 16);
+    rs_step<1>(v, lane, 8);
+    float r = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 4);
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    return r + __shfl_xor_sync(0xffffffffu, r, 1);
+}
+
+// Shared-memory plan of the backward CTA (byte offsets; atoms 1024-aligned):
+//   W   [128 px][64 g] BF16 weights            (A of dFe, MN-major; A of nothing else)
+//   Dh  [DN/64][128 px][64] BF16 dF hi           (A of G, K-major; B of dFe, MN-major)
+//   Dl  same, dF lo = bf16(dF - hi)
+//   Th  [128 px][64 g] BF16 t = G dL/drho, hi    (A of the moments, MN-major)
+//   Tl  same, lo
+//   X   [2 K-blocks][16 rows][64 px] BF16       (B of the moments, K-major): rows 1, i, j, i^2, i j, j^2
+//   F   [DN/64][64 g][64] BF16 feature rows      (B of G, K-major)
+// W is followed by Dh and Th by Tl: the M=128 MMAs with only 64 real rows
+// read their second M block from the next buffer and those rows are unused.
 template <int DN>
 struct BwdCfg {
-    static constexpr int kNBlk = DN / 64;                 // 64-feature blocks
-    static constexpr int kDBytes = kNBlk * 128 * 128;     // 128 px x DN BF16 (one of hi / lo)
-    static constexpr int kFBytes = kNBlk * kBB * 128;     // 64 rows x DN BF16
-    static constexpr int kWBytes = 2 * 128 * 128;         // two M blocks: weights, zeros
-    static constexpr int kRecBytes = kBB * (16 + 16 + 4 + 4 + 4 + 9 * 4);
-    static constexpr int kSmem = 1024 + 2 * kDBytes + kFBytes + kWBytes + kRecBytes + 64;
-    static constexpr int kTmemCols = (64 + DN) <= 256 ? 256 : 512;
-    static constexpr int kFCol = DN <= 128 ? 128 : 256;  // column of the dFe accumulator
+    static constexpr int kNBlk = DN / 64;
+    static constexpr int kOffW = 0;
+    static constexpr int kOffDh = kOffW + 128 * 128;
+    static constexpr int kOffDl = kOffDh + kNBlk * 128 * 128;
+    static constexpr int kOffTh = kOffDl + kNBlk * 128 * 128;
+    static constexpr int kOffTl = kOffTh + 128 * 128;
+    static constexpr int kOffX = kOffTl + 128 * 128;
+    static constexpr int kOffF = kOffX + 2 * 16 * 128;
+    static constexpr int kOffRec = kOffF + kNBlk * kBB * 128;
+    static constexpr int kRecBytes = kBB * 48 + kBB * 4;
+    static constexpr int kOffRgb = kOffRec + 2 * kRecBytes;
+    static constexpr int kOffFlag = kOffRgb + kBB * 3 * 4;
+    static constexpr int kOffBar = kOffFlag + kBB * 4;
+    static constexpr int kSmem = 1024 + kOffBar + 64;
+    static constexpr int kTmemCols = DN <= 128 ? 256 : 512;
+    static constexpr int kColM = 64;                      // moments, 16 columns
+    static constexpr int kColF = DN <= 128 ? 128 : 256;   // dFe, DN columns
 };
 
 template <int DN>
@@ -387,19 +495,21 @@ __global__ void __launch_bounds__(128, 1)
     using C = BwdCfg<DN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
-    uint8_t *sDh = sm;                                  // [DN/64][128 px][128 B]
-    uint8_t *sDl = sm + C::kDBytes;
-    uint8_t *sF = sm + 2 * C::kDBytes;                  // [DN/64][64 g][128 B]
-    uint8_t *sW = sF + C::kFBytes;                      // [2][128 px][128 B]
-    float4 *sA = reinterpret_cast<float4 *>(sW + C::kWBytes);
-    float4 *sB = sA + kBB;
-    float *sBl = reinterpret_cast<float *>(sB + kBB);
-    uint32_t *sGid = reinterpret_cast<uint32_t *>(sBl + kBB);
-    int *sFlag = reinterpret_cast<int *>(sGid + kBB);
-    float *sAcc = reinterpret_cast<float *>(sFlag + kBB);  // [64][9]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sAcc + kBB * 9);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    uint8_t *sW = sm + C::kOffW;
+    uint8_t *sDh = sm + C::kOffDh;
+    uint8_t *sDl = sm + C::kOffDl;
+    uint8_t *sTh = sm + C::kOffTh;
+    uint8_t *sTl = sm + C::kOffTl;
+    uint8_t *sX = sm + C::kOffX;
+    float *sRgb = reinterpret_cast<float *>(sm + C::kOffRgb);  // [64][3]
+    int *sFlag = reinterpret_cast<int *>(sm + C::kOffFlag);    // [64]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::kOffBar);  // [0] G, [1] dFe + moments
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
     int *smax = reinterpret_cast<int *>(tslot + 1);
+    auto srec = [&](int stg) { return reinterpret_cast<GRec *>(sm + C::kOffRec + stg * C::kRecBytes); };
+    auto sgid = [&](int stg) {
+        return reinterpret_cast<uint32_t *>(sm + C::kOffRec + stg * C::kRecBytes + kBB * 48);
+    };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, chunk = blockIdx.y;
@@ -407,7 +517,8 @@ __global__ void __launch_bounds__(128, 1)
     const DevCam &cam = cs.c[ci];
     const int lt = tile - cam.tile_off;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    const int px = tx * kTile + (tid & 15), py = ty * kTile + half * 8 + (tid >> 4);
+    const int x0 = tx * kTile, y0 = ty * kTile + half * 8;
+    const int px = x0 + (tid & 15), py = y0 + (tid >> 4);
     const bool inside = px < cam.W && py < cam.H;
     const long long pix = cam.pix_off + (long long)py * cam.W + px;
     const uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
@@ -418,42 +529,14 @@ __global__ void __launch_bounds__(128, 1)
 
     if (warp == 0) tmem_alloc(tslot, C::kTmemCols);
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
         fence_mbar_init();
         *smax = 0;
     }
-    // dF slice of this CTA's pixels -> BF16 hi / lo, K-major swizzled.  Each
-    // warp copies its 32 pixel rows, 32 lanes x 16 B per 512-byte piece.
-    {
-        const int row0 = warp * 32;
-#pragma unroll 1
-        for (int r = 0; r < 32; ++r) {
-            const int prow = row0 + r;
-            const int qx = tx * kTile + (prow & 15), qy = ty * kTile + half * 8 + (prow >> 4);
-            const bool qin = qx < cam.W && qy < cam.H && gfeat != nullptr;
-            const float *src = gfeat + (cam.pix_off + (long long)qy * cam.W + qx) * D + d0;
-#pragma unroll
-            for (int f = lane * 4; f < DN; f += 128) {  // f: first of this lane's 4 features
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (qin) v = *reinterpret_cast<const float4 *>(src + f);
-                const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
-                const float2 b01 = __bfloat1622float2(h01), b23 = __bfloat1622float2(h23);
-                const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - b01.x, v.y - b01.y);
-                const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - b23.x, v.w - b23.y);
-                const uint32_t off = (f >> 6) * (128 * 128) + swz(prow, (f & 63) >> 3) + ((f & 7) ? 8 : 0);
-                uint2 hv, lv;
-                hv.x = *reinterpret_cast<const uint32_t *>(&h01);
-                hv.y = *reinterpret_cast<const uint32_t *>(&h23);
-                lv.x = *reinterpret_cast<const uint32_t *>(&l01);
-                lv.y = *reinterpret_cast<const uint32_t *>(&l23);
-                *reinterpret_cast<uint2 *>(sDh + off) = hv;
-                *reinterpret_cast<uint2 *>(sDl + off) = lv;
-            }
-        }
-        // zero M block of the weight operand (rows 64..127 of dFe read it)
-        uint4 *z = reinterpret_cast<uint4 *>(sW + 128 * 128);
-        for (int i = tid; i < 128 * 128 / 16; i += 128) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid < kBB) {
+        sFlag[tid] = 0;
+        sRgb[3 * tid] = sRgb[3 * tid + 1] = sRgb[3 * tid + 2] = 0.f;
     }
     float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
     int lastp = 0;
@@ -470,68 +553,153 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc_after();
     atomicMax(smax, lastp);
-    fence_async_smem();
     __syncthreads();
     const uint32_t taddr = *tslot;
-    const uint32_t tG = taddr, tF = taddr + C::kFCol;
+    const uint32_t tG = taddr, tM = taddr + C::kColM, tF = taddr + C::kColF;
     const int Lmax = min(*smax, (int)(e - s));
-    const uint32_t sDh_s = smem_u32(sDh), sDl_s = smem_u32(sDl), sF_s = smem_u32(sF), sW_s = smem_u32(sW);
+    const int nbat = (Lmax + kBB - 1) / kBB;
+    const uint32_t sW_s = smem_u32(sW), sDh_s = smem_u32(sDh), sDl_s = smem_u32(sDl);
+    const uint32_t sTh_s = smem_u32(sTh), sTl_s = smem_u32(sTl), sX_s = smem_u32(sX);
+    const uint32_t sF_s = smem_u32(sm + C::kOffF);
     constexpr uint32_t idG = idesc_bf16(128, kBB, false, false);
     constexpr uint32_t idF = idesc_bf16(128, DN, true, true);
+    constexpr uint32_t idM = idesc_bf16(128, 16, true, false);
 
-    const float fpx = px + 0.5f, fpy = py + 0.5f;
-    float S = T * (dC0 * p.bg0 + dC1 * p.bg1 + dC2 * p.bg2);
-    uint32_t phG = 0, phF = 0;
-    bool timeout = false;
-
-    for (int bend = Lmax; bend > 0 && !timeout; bend -= kBB) {
-        const int bstart = max(0, bend - kBB), nb = bend - bstart;
-        if (tid < kBB) {
-            sGid[tid] = tid < nb ? gids[s + bstart + tid] : 0u;
-            sFlag[tid] = 0;
-        }
-        for (int i = tid; i < kBB * 9; i += 128) sAcc[i] = 0.f;
-        __syncthreads();
-        {   // feature rows (K-major for G): [DN/64][64 g][128 B]
-            constexpr int kCPR = DN / 8;
+    // batch b covers list positions [max(0, Lmax - 64 (b+1)), Lmax - 64 b): back to front
+    auto prefetch = [&](int b, int stg) {  // records + feature rows of batch b
+        const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
+        constexpr int kCPR = DN / 8;
 #pragma unroll 4
-            for (int q = tid; q < kBB * kCPR; q += 128) {
-                const int g = q / kCPR, c = q - g * kCPR;
-                const bool valid = g < nb;
-                const __nv_bfloat16 *src = feats + (size_t)sGid[valid ? g : 0] * D + d0 + c * 8;
-                cp_async16(sF_s + (c >> 3) * (kBB * 128) + swz(g, c & 7), src, valid);
-            }
-            cp_async_commit();
+        for (int q = tid; q < kBB * kCPR; q += 128) {
+            const int g = q / kCPR, c = q - g * kCPR;
+            const bool valid = g < nb;
+            const uint32_t gid = valid ? __ldg(gids + s + bs + g) : 0u;
+            cp_async16(sF_s + (c >> 3) * (kBB * 128) + swz(g, c & 7), feats + (size_t)gid * D + d0 + c * 8, valid);
         }
         if (tid < nb) {
-            const GRec r = rec[sGid[tid]];
-            sA[tid] = r.a;
-            sB[tid] = r.b;
-            sBl[tid] = r.c.x;
+            const uint32_t gid = __ldg(gids + s + bs + tid);
+            sgid(stg)[tid] = gid;
+            const uint32_t dst = smem_u32(srec(stg) + tid);
+            const GRec *src = rec + gid;
+            cp_async16(dst, &src->a, true);
+            cp_async16(dst + 16, &src->b, true);
+            cp_async16(dst + 32, &src->c, true);
+        }
+        cp_async_commit();
+    };
+    auto issue_G = [&]() {  // G(px, g) = sum_d dF(px, d) Fe(g, d), hi + lo parts
+        tc_after();
+#pragma unroll
+        for (int ks = 0; ks < DN / 16; ++ks) {
+            const uint32_t koff = (ks >> 2) * (128 * 128) + (ks & 3) * 32;
+            const uint64_t bd = sdesc(sF_s + (ks >> 2) * (kBB * 128) + (ks & 3) * 32, 16, 1024);
+            mma_bf16(tG, sdesc(sDh_s + koff, 16, 1024), bd, idG, ks > 0 ? 1u : 0u);
+            mma_bf16(tG, sdesc(sDl_s + koff, 16, 1024), bd, idG, 1u);
+        }
+        mma_commit(&bars[0]);
+    };
+    auto issue_FM = [&]() {  // dFe = W^T dF (hi + lo) and moments = T^T X (T hi + lo)
+        tc_after();
+#pragma unroll
+        for (int ks = 0; ks < 128 / 16; ++ks) {
+            const uint64_t am = sdesc(sTh_s + ks * 2048, 128 * 128, 1024);
+            const uint64_t al = sdesc(sTl_s + ks * 2048, 128 * 128, 1024);
+            const uint64_t bx = sdesc(sX_s + (ks >> 2) * (16 * 128) + (ks & 3) * 32, 16, 1024);
+            mma_bf16(tM, am, bx, idM, ks > 0 ? 1u : 0u);
+            mma_bf16(tM, al, bx, idM, 1u);
+            if (want_fg) {
+                const uint64_t aw = sdesc(sW_s + ks * 2048, 128 * 128, 1024);
+                mma_bf16(tF, aw, sdesc(sDh_s + ks * 2048, 128 * 128, 1024), idF, ks > 0 ? 1u : 0u);
+                mma_bf16(tF, aw, sdesc(sDl_s + ks * 2048, 128 * 128, 1024), idF, 1u);
+            }
+        }
+        mma_commit(&bars[1]);
+    };
+
+    uint32_t ph0 = 0, ph1 = 0;
+    bool pend0 = false, pend1 = false;
+    bool timeout = false;
+    if (nbat > 0) {
+        prefetch(0, 0);
+        // pixel-moment rows of X: X[n][p] for p = i + 16 j
+        for (int q = tid; q < 16 * 128; q += 128) {
+            const int n = q >> 7, pp = q & 127;
+            const float i = (float)(pp & 15), jv = (float)(pp >> 4);
+            const float val = n == 0 ? 1.f : n == 1 ? i : n == 2 ? jv : n == 3 ? i * i : n == 4 ? i * jv
+                                                                                                   : n == 5 ? jv * jv : 0.f;
+            *reinterpret_cast<__nv_bfloat16 *>(sX + (pp >> 6) * (16 * 128) + swz(n, (pp & 63) >> 3) +
+                                               2 * (pp & 7)) = __float2bfloat16_rn(val);
+        }
+        // dF slice of this CTA's pixels -> BF16 hi / lo, K-major swizzled.  Each
+        // warp copies its 32 pixel rows with 8 rows of loads in flight.
+        constexpr int kL = DN >= 128 ? DN / 128 : 1;
+#pragma unroll 1
+        for (int r0 = 0; r0 < 32; r0 += 8) {
+            float4 v[8][kL];
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) {
+                const int prow = warp * 32 + r0 + rr;
+                const int qx = x0 + (prow & 15), qy = y0 + (prow >> 4);
+                const bool qin = qx < cam.W && qy < cam.H && gfeat != nullptr;
+                const float *src = gfeat + (cam.pix_off + (long long)qy * cam.W + qx) * D + d0;
+#pragma unroll
+                for (int li = 0; li < kL; ++li) {
+                    const int f = li * 128 + lane * 4;
+                    v[rr][li] = (qin && f < DN) ? *reinterpret_cast<const float4 *>(src + f)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) {
+                const int prow = warp * 32 + r0 + rr;
+#pragma unroll
+                for (int li = 0; li < kL; ++li) {
+                    const int f = li * 128 + lane * 4;
+                    if (f >= DN) continue;
+                    const float4 x = v[rr][li];
+                    const __nv_bfloat162 h01 = __floats2bfloat162_rn(x.x, x.y);
+                    const __nv_bfloat162 h23 = __floats2bfloat162_rn(x.z, x.w);
+                    const float2 b01 = __bfloat1622float2(h01), b23 = __bfloat1622float2(h23);
+                    const __nv_bfloat162 l01 = __floats2bfloat162_rn(x.x - b01.x, x.y - b01.y);
+                    const __nv_bfloat162 l23 = __floats2bfloat162_rn(x.z - b23.x, x.w - b23.y);
+                    const uint32_t off = (f >> 6) * (128 * 128) + swz(prow, (f & 63) >> 3) + ((f & 7) ? 8 : 0);
+                    uint2 hv, lv;
+                    hv.x = *reinterpret_cast<const uint32_t *>(&h01);
+                    hv.y = *reinterpret_cast<const uint32_t *>(&h23);
+                    lv.x = *reinterpret_cast<const uint32_t *>(&l01);
+                    lv.y = *reinterpret_cast<const uint32_t *>(&l23);
+                    *reinterpret_cast<uint2 *>(sDh + off) = hv;
+                    *reinterpret_cast<uint2 *>(sDl + off) = lv;
+                }
+            }
         }
         cp_async_wait_all();
         fence_async_smem();
         __syncthreads();
-        if (tid == 0) {  // G(px, g) = sum_d dF(px, d) Fe(g, d): hi and lo parts
-            tc_after();
-#pragma unroll
-            for (int ks = 0; ks < DN / 16; ++ks) {
-                const uint32_t koff = (ks >> 2) * (128 * 128) + (ks & 3) * 32;
-                const uint64_t bd = sdesc(sF_s + (ks >> 2) * (kBB * 128) + (ks & 3) * 32, 16, 1024);
-                mma_bf16(tG, sdesc(sDh_s + koff, 16, 1024), bd, idG, ks > 0 ? 1u : 0u);
-                mma_bf16(tG, sdesc(sDl_s + koff, 16, 1024), bd, idG, 1u);
-            }
-            mma_commit(&bar[0]);
-        }
+        if (tid == 0) issue_G();
+        pend0 = true;
+    }
+
+    const float fpx = px + 0.5f, fpy = py + 0.5f;
+    float S = T * (dC0 * p.bg0 + dC1 * p.bg1 + dC2 * p.bg2);
+    for (int b = 0; b < nbat; ++b) {
+        const int stg = b & 1;
+        const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
         {
-            const bool ok = mbar_wait(&bar[0], phG);
-            phG ^= 1u;
+            const bool ok = mbar_wait(&bars[0], ph0);
+            if (ok) {
+                ph0 ^= 1u;
+                pend0 = false;
+            }
             if (__syncthreads_or(!ok)) {
                 timeout = true;
                 break;
             }
         }
         tc_after();
+        // G of this batch is in TMEM: the feature stage is free for batch b+1
+        if (b + 1 < nbat) prefetch(b + 1, stg ^ 1);
+        const GRec *R = srec(stg);
         // back to front over two sub-batches of 32 Gaussians
 #pragma unroll 1
         for (int sub = 1; sub >= 0; --sub) {
@@ -542,123 +710,121 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
                 const int j = sub * 32 + jj;
-                float a = 0.f, gg = 0.f;
-                if (j < nb && bstart + j < lastp) {
-                    const float4 A4 = sA[j], B4 = sB[j];
-                    const float dx = fpx - A4.x, dy = fpy - A4.y;
-                    const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
-                    if (q2 <= p.cut) {
-                        const float G = __expf(-0.5f * q2);
-                        const float rho = B4.y * G;
-                        const float aa = fminf(p.amax, rho);
-                        if (aa >= p.amin) {
-                            a = aa;
-                            gg = rho > p.amax ? 0.f : G;
-                        }
-                    }
-                }
-                al[jj] = a;
-                gx[jj] = gg;
-                P *= 1.f - a;
+                const float4 A4 = R[j].a, B4 = R[j].b;
+                const float dx = fpx - A4.x, dy = fpy - A4.y;
+                const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
+                const float G = __expf(-0.5f * q2);
+                const float rho = B4.y * G;
+                const float aa = fminf(p.amax, rho);
+                const bool ok = (j < nb) && (bs + j < lastp) && (q2 <= p.cut) && (aa >= p.amin);
+                al[jj] = ok ? aa : 0.f;
+                gx[jj] = (ok && rho <= p.amax) ? G : 0.f;
+                P *= 1.f - al[jj];
             }
             // T before the sub-batch, then the forward prefix of transmittance
-            const float Tstart = T / P;
+            const float Tstart = __fdividef(T, P);
             float t = Tstart;
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
                 Tj[jj] = t;
                 t *= 1.f - al[jj];
             }
-            // App. A.2 back to front: dL/dalpha_k = T_k g_k - S_k / (1 - alpha_k)
+            // App. A.2 back to front: dL/dalpha_k = T_k g_k - S_k / (1 - alpha_k);
+            // gx becomes t_k = G dL/drho
 #pragma unroll
             for (int jj = 31; jj >= 0; --jj) {
                 const int j = sub * 32 + jj;
-                if (al[jj] > 0.f) {
-                    const float w = al[jj] * Tj[jj];
-                    const float4 B4 = sB[j];
-                    const float g = Gv[jj] + dC0 * B4.z + dC1 * B4.w + dC2 * sBl[j];
-                    const float dal = Tj[jj] * g - S / (1.f - al[jj]);
-                    S += w * g;
-                    gx[jj] *= dal;  // = G dL/drho (0 where alpha is clamped)
-                } else {
-                    gx[jj] = 0.f;
-                }
+                // selects, not products with zero: records past the batch end are stale
+                const bool c = al[jj] > 0.f;
+                const float w = al[jj] * Tj[jj];
+                const float4 B4 = R[j].b;
+                const float g = c ? Gv[jj] + dC0 * B4.z + dC1 * B4.w + dC2 * R[j].c.x : 0.f;
+                const float dal = Tj[jj] * g - __fdividef(S, 1.f - al[jj]);
+                S = c ? S + w * g : S;
+                gx[jj] = c ? gx[jj] * dal : 0.f;
             }
-            // weights (BF16) for dFe = W^T dF: Gaussians sub*32.. in row `tid`
+            // weights (A of dFe) and t hi/lo (A of the moments) for Gaussians sub*32..
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                uint4 pk;
-                pk.x = pack_bf16(al[8 * q + 0] * Tj[8 * q + 0], al[8 * q + 1] * Tj[8 * q + 1]);
-                pk.y = pack_bf16(al[8 * q + 2] * Tj[8 * q + 2], al[8 * q + 3] * Tj[8 * q + 3]);
-                pk.z = pack_bf16(al[8 * q + 4] * Tj[8 * q + 4], al[8 * q + 5] * Tj[8 * q + 5]);
-                pk.w = pack_bf16(al[8 * q + 6] * Tj[8 * q + 6], al[8 * q + 7] * Tj[8 * q + 7]);
-                *reinterpret_cast<uint4 *>(sW + swz(tid, sub * 4 + q)) = pk;
+                uint4 pw, ph, pl;
+                uint32_t *pwv = &pw.x, *phv = &ph.x, *plv = &pl.x;
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int j0 = 8 * q + 2 * h;
+                    pwv[h] = pack_bf16(al[j0] * Tj[j0], al[j0 + 1] * Tj[j0 + 1]);
+                    const __nv_bfloat162 th = __floats2bfloat162_rn(gx[j0], gx[j0 + 1]);
+                    const float2 tb = __bfloat1622float2(th);
+                    phv[h] = *reinterpret_cast<const uint32_t *>(&th);
+                    plv[h] = pack_bf16(gx[j0] - tb.x, gx[j0 + 1] - tb.y);
+                }
+                const uint32_t off = swz(tid, sub * 4 + q);
+                *reinterpret_cast<uint4 *>(sW + off) = pw;
+                *reinterpret_cast<uint4 *>(sTh + off) = ph;
+                *reinterpret_cast<uint4 *>(sTl + off) = pl;
             }
-            // footprint gradients: reduce over the warp's pixels, then shared atomics
+            // which Gaussians contribute anywhere in the CTA; RGB sums (slice 0)
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
                 const bool c = al[jj] > 0.f;
                 if (!__any_sync(0xffffffffu, c)) continue;
                 const int j = sub * 32 + jj;
-                const float4 A4 = sA[j], B4 = sB[j];
-                const float dx = fpx - A4.x, dy = fpy - A4.y;
-                const float gop = gx[jj];
-                const float dq2 = -0.5f * B4.y * gop;
-                const float w = al[jj] * Tj[jj];
-                float v[9];
-                v[0] = -(2.f * A4.z * dx + 2.f * A4.w * dy) * dq2;
-                v[1] = -(2.f * A4.w * dx + 2.f * B4.x * dy) * dq2;
-                v[2] = dx * dx * dq2;
-                v[3] = 2.f * dx * dy * dq2;
-                v[4] = dy * dy * dq2;
-                v[5] = gop;
-                v[6] = w * dC0;
-                v[7] = w * dC1;
-                v[8] = w * dC2;
-                const int nv = chunk == 0 ? 9 : 6;
-#pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    if (k < nv) v[k] = warp_sum(v[k]);
-                if (lane == 0) {
-                    sFlag[j] = 1;
-#pragma unroll
-                    for (int k = 0; k < 9; ++k)
-                        if (k < nv) atomicAdd(&sAcc[j * 9 + k], v[k]);
+                if (lane == 0) sFlag[j] = 1;
+                if (chunk == 0) {
+                    const float w = al[jj] * Tj[jj];
+                    float v[4] = {w * dC0, w * dC1, w * dC2, 0.f};
+                    const float r = warp_rs4(v, lane);
+                    const int k = (lane >> 3) & 3;
+                    if ((lane & 7) == 0 && k < 3) atomicAdd(&sRgb[3 * j + k], r);
                 }
             }
             T = Tstart;
         }
+        cp_async_wait_all();  // batch b+1's records and features have landed
         fence_async_smem();
         __syncthreads();
-        if (want_fg && tid == 0) {  // dFe(g, d) = sum_px W(px, g) dF(px, d): hi and lo parts
-            tc_after();
-#pragma unroll
-            for (int ks = 0; ks < 128 / 16; ++ks) {
-                const uint64_t ad = sdesc(sW_s + ks * 2048, 128 * 128, 1024);
-                mma_bf16(tF, ad, sdesc(sDh_s + ks * 2048, 128 * 128, 1024), idF, ks > 0 ? 1u : 0u);
-                mma_bf16(tF, ad, sdesc(sDl_s + ks * 2048, 128 * 128, 1024), idF, 1u);
+        if (tid == 0) {
+            issue_FM();
+            if (b + 1 < nbat) issue_G();
+        }
+        pend1 = true;
+        if (b + 1 < nbat) pend0 = true;
+        {
+            const bool ok = mbar_wait(&bars[1], ph1);
+            if (ok) {
+                ph1 ^= 1u;
+                pend1 = false;
             }
-            mma_commit(&bar[1]);
-        }
-        // flush this batch's footprint gradients (one set of atomics per Gaussian)
-        if (tid < nb && sFlag[tid]) {
-            float4 *dst = reinterpret_cast<float4 *>(g2dc + 12 * (long long)sGid[tid]);
-            const float *a = sAcc + tid * 9;
-            atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
-            atomicAdd(dst + 1, make_float4(a[4], a[5], chunk == 0 ? a[6] : 0.f, chunk == 0 ? a[7] : 0.f));
-            if (chunk == 0) atomicAdd(g2dc + 12 * (long long)sGid[tid] + 8, a[8]);
-        }
-        if (want_fg) {
-            const bool ok = mbar_wait(&bar[1], phF);
-            phF ^= 1u;
             if (__syncthreads_or(!ok)) {
                 timeout = true;
                 break;
             }
-            tc_after();
-            if (warp < 2) {  // rows 0..63 of dFe live in lanes 0..63
-                const bool mine = tid < nb && sFlag[tid] != 0;
-                float *dst = gfeatures + (size_t)sGid[tid] * D + d0;
+        }
+        tc_after();
+        if (warp < 2) {  // rows 0..63 of the moment and dFe accumulators = the batch's Gaussians
+            const int j = tid;
+            const bool mine = j < nb && sFlag[j] != 0;
+            const uint32_t gid = sgid(stg)[j];
+            float m[16];
+            tmem_ld16(tM + ((uint32_t)(warp * 32) << 16), m);
+            if (mine) {
+                const GRec r = R[j];
+                // moments about the pixel grid: dx = i - a, dy = j - b
+                const float a = r.a.x - (float)x0 - 0.5f, bb = r.a.y - (float)y0 - 0.5f;
+                const float M0 = m[0], Mi = m[1], Mj = m[2], Mii = m[3], Mij = m[4], Mjj = m[5];
+                const float Sx = Mi - a * M0, Sy = Mj - bb * M0;
+                const float Sxx = Mii - 2.f * a * Mi + a * a * M0;
+                const float Sxy = Mij - a * Mj - bb * Mi + a * bb * M0;
+                const float Syy = Mjj - 2.f * bb * Mj + bb * bb * M0;
+                const float op = r.b.y, cA = r.a.z, cB = r.a.w, cC = r.b.x;
+                float4 *dst = reinterpret_cast<float4 *>(g2dc + 12 * (long long)gid);
+                atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy), -0.5f * op * Sxx,
+                                           -op * Sxy));
+                atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, chunk == 0 ? sRgb[3 * j] : 0.f,
+                                               chunk == 0 ? sRgb[3 * j + 1] : 0.f));
+                if (chunk == 0) atomicAdd(g2dc + 12 * (long long)gid + 8, sRgb[3 * j + 2]);
+            }
+            if (want_fg) {
+                float *dst = gfeatures + (size_t)gid * D + d0;
 #pragma unroll 1
                 for (int cc = 0; cc < DN / 32; ++cc) {
                     float v[32];
@@ -671,6 +837,8 @@ __global__ void __launch_bounds__(128, 1)
                     }
                 }
             }
+            sFlag[j] = 0;
+            sRgb[3 * j] = sRgb[3 * j + 1] = sRgb[3 * j + 2] = 0.f;
         }
         tc_before();
         __syncthreads();
@@ -678,9 +846,10 @@ __global__ void __launch_bounds__(128, 1)
     }
     if (timeout) {
         if (tid == 0) latch(status, ST_TIMEOUT);
-        mbar_wait(&bar[0], phG);
-        if (want_fg) mbar_wait(&bar[1], phF);
+        if (pend0) mbar_wait(&bars[0], ph0);
+        if (pend1) mbar_wait(&bars[1], ph1);
     }
+    cp_async_wait_all();
     tc_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(taddr, C::kTmemCols);
@@ -688,9 +857,8 @@ __global__ void __launch_bounds__(128, 1)
 
 int pick_fwd_dn(int D, int d_split) {
     if (d_split == 64 || d_split == 128 || d_split == 256 || d_split == 512) return (D % d_split == 0) ? d_split : 0;
-    if (D % 256 == 0) return 256;
-    if (D % 128 == 0) return 128;
-    if (D % 64 == 0) return 64;
+    for (int dn = 512; dn >= 64; dn >>= 1)
+        if (D % dn == 0) return dn;
     return 0;
 }
 
@@ -723,7 +891,7 @@ void launch_render_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
 #define FHGS_FWD(DNV)                                                                                     \
     case DNV: {                                                                                           \
         set_smem(k_render_fwd_tc<DNV>, FwdCfg<DNV>::kSmem);                                              \
-        k_render_fwd_tc<DNV><<<grid, 128, FwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, feats, D, \
+        k_render_fwd_tc<DNV><<<grid, 256, FwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, feats, D, \
                                                                    rgb, feat, T, last, status);          \
         break;                                                                                            \
     }

@@ -77,5 +77,5 @@ def test_create_without_device_fails_cleanly(L):
 def test_null_context_is_rejected(L):
     p = api.make_params()
     assert L.fhgs_sync_status(None, None) == api.ERR_INVALID_ARG
-    assert L.fhgs_reserve(None, 1, 1, 1) == api.ERR_INVALID_ARG
+    assert L.fhgs_reserve(None, 1, None, 1) == api.ERR_INVALID_ARG
     assert L.fhgs_project(None, None, None, 0, ctypes.byref(p), None, None) == api.ERR_INVALID_ARG
