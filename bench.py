@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--width", type=int, default=1920, help="profiling only: smaller view, same scene")
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--path", choices=["tc", "fp32", "auto"], default="auto")
+    ap.add_argument("--d-split", type=int, default=0, help="feature columns per CTA (0 = auto)")
     ap.add_argument("--fp32-steps", type=int, default=3, help="timed steps of the FP32 comparison path (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -156,7 +157,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     scene, cams, t, P = make_workload(rank, args.n, args.D, dev, args.width, args.height)
     path = {"tc": api.PATH_TC, "fp32": api.PATH_FP32, "auto": api.PATH_AUTO}[args.path]
-    rast = api.Rasterizer(local, sh_degree=3, path=path)
+    rast = api.Rasterizer(local, sh_degree=3, path=path, d_split=args.d_split)
     g = (t["means"], t["scales"], t["quats"], t["opacities"], t["sh"])
     st0 = rast.prepare(*g, cams)                      # sizes the instance buffer
     I = st0["n_instances"]

@@ -319,30 +319,36 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t *a, long lo
 }
 
 // ------------------------------------------------------------- scatter
-constexpr int kScatterWarps = 2;
+constexpr int kScatterWarps = 4;
 constexpr int kStage = 128;  // entries staged in shared memory per step
 
-// One warp per (segment, camera): walks the segment's Gaussians in depth
-// order, writing each one into every tile of its rectangle at the tile's
-// running offset.  Within one Gaussian all tiles differ, so the 32 lanes
-// update distinct counters; Gaussians follow one another in order.
+// One warp per (segment, camera, band of tile rows): walks the segment's
+// Gaussians in depth order and writes each one into every tile of its
+// rectangle that lies in the band, at the tile's running offset.  Long
+// segments give each (tile, segment) run many consecutive entries (whole
+// sectors per write burst); bands restore the parallelism.  Within one
+// Gaussian all tiles differ, so the 32 lanes update distinct counters.
 __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32_t *__restrict__ order, ProjView pv,
-                                                                     long long N, int SEG, int S, CamSet cs,
-                                                                     const uint32_t *__restrict__ table,
-                                                                     int max_tiles, uint32_t *gids,
+                                                                     long long N, int SEG, int S, int nband,
+                                                                     int band_rows, CamSet cs,
+                                                                     const uint32_t *__restrict__ table, uint32_t *gids,
                                                                      long long capacity) {
     extern __shared__ uint32_t sh[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int seg = blockIdx.x * kScatterWarps + warp, ci = blockIdx.y;
-    if (seg >= S) return;  // warp-uniform; the kernel uses no block barrier
-    const int stride = (max_tiles + kStage * 6 + 3) & ~3;  // per-warp words, 16-byte multiple
-    uint32_t *ctr = sh + warp * stride;
-    int4 *st_r = reinterpret_cast<int4 *>(ctr + ((max_tiles + 3) & ~3));  // staged rectangles
-    uint32_t *st_g = reinterpret_cast<uint32_t *>(st_r + kStage);        // staged Gaussian index
-    uint32_t *st_n = st_g + kStage;                                      // staged tile count
+    const long long item = (long long)blockIdx.x * kScatterWarps + warp;
+    const int ci = blockIdx.y;
+    if (item >= (long long)S * nband) return;  // warp-uniform; the kernel uses no block barrier
+    const int seg = (int)(item / nband), band = (int)(item - (long long)seg * nband);
     const DevCam &cam = cs.c[ci];
-    const int tx = cam.tiles_x, T = cam.tiles_x * cam.tiles_y;
-    for (int t = lane; t < T; t += 32) ctr[t] = table[(long long)(cam.tile_off + t) * S + seg];
+    const int tx = cam.tiles_x;
+    const int by0 = band * band_rows, by1 = min(cam.tiles_y, by0 + band_rows);
+    if (by0 >= by1) return;
+    const int ctr_words = (band_rows * tx + 3) & ~3;
+    uint32_t *ctr = sh + warp * (ctr_words + kStage * 6);
+    int4 *st_r = reinterpret_cast<int4 *>(ctr + ctr_words);         // staged rectangles
+    uint32_t *st_g = reinterpret_cast<uint32_t *>(st_r + kStage);  // staged Gaussian index
+    const int T = (by1 - by0) * tx;
+    for (int t = lane; t < T; t += 32) ctr[t] = table[(long long)(cam.tile_off + by0 * tx + t) * S + seg];
     const long long b0 = (long long)ci * N + (long long)seg * SEG;
     const long long b1 = min((long long)(ci + 1) * N, b0 + SEG);
     for (long long c0 = b0; c0 < b1; c0 += kStage) {
@@ -350,21 +356,28 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32
         __syncwarp();
         for (int k = lane; k < m; k += 32) {
             const uint32_t e = order[c0 + k];
-            const uint32_t nt = pv.ntiles[e];
+            int4 r = make_int4(0, 0, -1, -1);  // empty unless it touches the band
+            if (pv.ntiles[e]) {
+                r = pv.trect[e];
+                r.y = max(r.y, by0);
+                r.w = min(r.w, by1 - 1);
+            }
+            st_r[k] = r;
             st_g[k] = (uint32_t)(e - (long long)ci * N);
-            st_n[k] = nt;
-            if (nt) st_r[k] = pv.trect[e];
         }
         __syncwarp();
         for (int k = 0; k < m; ++k) {
-            const uint32_t nt = st_n[k];
-            if (nt == 0) continue;
             const int4 r = st_r[k];
+            if (r.w < r.y) continue;
             const uint32_t g = st_g[k];
             const int w = r.z - r.x + 1;
+            const uint32_t nt = (uint32_t)(w * (r.w - r.y + 1));
+            const float inv_w = 1.f / (float)w;
             for (uint32_t q = lane; q < nt; q += 32) {
-                const int qy = (int)(q / (uint32_t)w), qx = (int)(q - (uint32_t)qy * w);
-                const int t = (r.y + qy) * tx + r.x + qx;
+                // q / w via a float reciprocal: exact for q < 2^22 (q + 0.5 never lands on an integer)
+                const int qy = (int)(((float)q + 0.5f) * inv_w);
+                const int qx = (int)q - qy * w;
+                const int t = (r.y - by0 + qy) * tx + r.x + qx;
                 const uint32_t pos = ctr[t];
                 if (pos < capacity) gids[pos] = g;
                 ctr[t] = pos + 1;
@@ -399,7 +412,8 @@ __global__ void __launch_bounds__(256) k_keys64(const uint32_t *__restrict__ ran
 }
 
 int seg_size(long long N, int total_tiles) {
-    int seg = 512;
+    int seg = 256;
+    while (seg < 4096 && (N + seg - 1) / seg > 256) seg <<= 1;
     while ((long long)total_tiles * ((N + seg - 1) / seg) > (32ll << 20) && seg < (1 << 20)) seg <<= 1;
     return seg;
 }
@@ -465,11 +479,8 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
     }
     // 2. per-segment tile counts
     const int SEG = sc.seg, S = sc.nseg;
-    int max_cells = 0, max_tiles = 0;
-    for (int c = 0; c < n_cams; ++c) {
-        max_cells = max(max_cells, (cs.c[c].tiles_x + 1) * (cs.c[c].tiles_y + 1));
-        max_tiles = max(max_tiles, cs.c[c].tiles_x * cs.c[c].tiles_y);
-    }
+    int max_cells = 0;
+    for (int c = 0; c < n_cams; ++c) max_cells = max(max_cells, (cs.c[c].tiles_x + 1) * (cs.c[c].tiles_y + 1));
     const int count_smem = max_cells * (int)sizeof(int);
     cudaFuncSetAttribute(k_seg_count, cudaFuncAttributeMaxDynamicSharedMemorySize, count_smem);
     note_launch(1);
@@ -485,12 +496,25 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
     note_launch(1);
     k_table_ranges<<<(cs.total_tiles + 255) / 256, 256, 0, st>>>(sc.table, S, cs.total_tiles, bins.n_instances,
                                                                  bins.capacity, bins.ranges, status);
-    const int stride_words = (((max_tiles + 3) & ~3) + kStage * 6 + 3) & ~3;
-    const int scat_smem = kScatterWarps * stride_words * (int)sizeof(uint32_t);
+    // bands of tile rows: enough (segment, band) warps to fill the GPU, at
+    // most a few thousand counters each
+    int max_ty = 0, max_tx = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        max_ty = max(max_ty, cs.c[c].tiles_y);
+        max_tx = max(max_tx, cs.c[c].tiles_x);
+    }
+    const long long want = 32ll * sc.sm_count;  // warps
+    int nband = (int)min((long long)max_ty, (want + (long long)S * n_cams - 1) / ((long long)S * n_cams));
+    nband = max(nband, 1);
+    const int band_rows = (max_ty + nband - 1) / nband;
+    nband = (max_ty + band_rows - 1) / band_rows;
+    const int ctr_words = (band_rows * max_tx + 3) & ~3;
+    const int scat_smem = kScatterWarps * (ctr_words + kStage * 6) * (int)sizeof(uint32_t);
     cudaFuncSetAttribute(k_seg_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, scat_smem);
     note_launch(1);
-    k_seg_scatter<<<dim3((S + kScatterWarps - 1) / kScatterWarps, n_cams), kScatterWarps * 32, scat_smem, st>>>(
-        order, pv, N, SEG, S, cs, sc.table, max_tiles, bins.gids, bins.capacity);
+    const long long items = (long long)S * nband;
+    k_seg_scatter<<<dim3((unsigned)((items + kScatterWarps - 1) / kScatterWarps), n_cams), kScatterWarps * 32,
+                    scat_smem, st>>>(order, pv, N, SEG, S, nband, band_rows, cs, sc.table, bins.gids, bins.capacity);
     if (bins.keys) {
         note_launch(1);
         k_keys64<<<cs.total_tiles, 256, 0, st>>>(bins.ranges, bins.gids, pv, N, cs, bins.keys);

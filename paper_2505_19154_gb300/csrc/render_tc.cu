@@ -478,15 +478,22 @@ struct BwdCfg {
     static constexpr int kRecBytes = kBB * 48 + kBB * 4;
     static constexpr int kOffRgb = kOffRec + 2 * kRecBytes;
     static constexpr int kOffFlag = kOffRgb + kBB * 3 * 4;
-    static constexpr int kOffBar = kOffFlag + kBB * 4;
+    static constexpr int kOffXch = kOffFlag + kBB * 4;    // per pixel: P1, S1, T, S
+    static constexpr int kOffBar = kOffXch + 128 * 16;
     static constexpr int kSmem = 1024 + kOffBar + 64;
     static constexpr int kTmemCols = DN <= 128 ? 256 : 512;
     static constexpr int kColM = 64;                      // moments, 16 columns
     static constexpr int kColF = DN <= 128 ? 128 : 256;   // dFe, DN columns
 };
 
+// 256 threads: two groups of 4 warps share the half tile's 128 pixels; group g
+// handles Gaussians [32 g, 32 g + 32) of each batch.  Back to front, group 1's
+// Gaussians come first: it runs the App. A.2 recursion with the true suffix
+// sum S, while group 0 runs it from S = 0 and then subtracts
+// G_k (S + S_1) / (1 - alpha_k), with S_1 the sum of w g over group 1's
+// Gaussians; transmittance needs only group 1's product of (1 - alpha).
 template <int DN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     k_render_bwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                     const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats, int D,
                     const float *__restrict__ Tfin, const int32_t *__restrict__ lastv,
@@ -503,6 +510,10 @@ __global__ void __launch_bounds__(128, 1)
     uint8_t *sX = sm + C::kOffX;
     float *sRgb = reinterpret_cast<float *>(sm + C::kOffRgb);  // [64][3]
     int *sFlag = reinterpret_cast<int *>(sm + C::kOffFlag);    // [64]
+    float *xP1 = reinterpret_cast<float *>(sm + C::kOffXch);  // [128] group 1's prod (1 - alpha)
+    float *xS1 = xP1 + 128;                                    // [128] group 1's sum w g
+    float *xT = xS1 + 128;                                     // [128] T after the batch
+    float *xS = xT + 128;                                      // [128] S after the batch
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::kOffBar);  // [0] G, [1] dFe + moments
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
     int *smax = reinterpret_cast<int *>(tslot + 1);
@@ -511,14 +522,14 @@ __global__ void __launch_bounds__(128, 1)
         return reinterpret_cast<uint32_t *>(sm + C::kOffRec + stg * C::kRecBytes + kBB * 48);
     };
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, grp = tid >> 7, pidx = tid & 127;
     const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, chunk = blockIdx.y;
     const int ci = cam_of_tile(cs, tile);
     const DevCam &cam = cs.c[ci];
     const int lt = tile - cam.tile_off;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
     const int x0 = tx * kTile, y0 = ty * kTile + half * 8;
-    const int px = x0 + (tid & 15), py = y0 + (tid >> 4);
+    const int px = x0 + (pidx & 15), py = y0 + (pidx >> 4);
     const bool inside = px < cam.W && py < cam.H;
     const long long pix = cam.pix_off + (long long)py * cam.W + px;
     const uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
@@ -552,7 +563,7 @@ __global__ void __launch_bounds__(128, 1)
     tc_before();
     __syncthreads();
     tc_after();
-    atomicMax(smax, lastp);
+    if (grp == 0) atomicMax(smax, lastp);
     __syncthreads();
     const uint32_t taddr = *tslot;
     const uint32_t tG = taddr, tM = taddr + C::kColM, tF = taddr + C::kColF;
@@ -566,24 +577,27 @@ __global__ void __launch_bounds__(128, 1)
     constexpr uint32_t idM = idesc_bf16(128, 16, true, false);
 
     // batch b covers list positions [max(0, Lmax - 64 (b+1)), Lmax - 64 b): back to front
-    auto prefetch = [&](int b, int stg) {  // records + feature rows of batch b
+    auto prefetch_rec = [&](int b, int stg) {  // Gaussian ids + records of batch b
         const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
-        constexpr int kCPR = DN / 8;
-#pragma unroll 4
-        for (int q = tid; q < kBB * kCPR; q += 128) {
-            const int g = q / kCPR, c = q - g * kCPR;
-            const bool valid = g < nb;
-            const uint32_t gid = valid ? __ldg(gids + s + bs + g) : 0u;
-            cp_async16(sF_s + (c >> 3) * (kBB * 128) + swz(g, c & 7), feats + (size_t)gid * D + d0 + c * 8, valid);
-        }
+        if (tid < kBB) sgid(stg)[tid] = tid < nb ? __ldg(gids + s + bs + tid) : 0u;
         if (tid < nb) {
-            const uint32_t gid = __ldg(gids + s + bs + tid);
-            sgid(stg)[tid] = gid;
             const uint32_t dst = smem_u32(srec(stg) + tid);
-            const GRec *src = rec + gid;
+            const GRec *src = rec + sgid(stg)[tid];
             cp_async16(dst, &src->a, true);
             cp_async16(dst + 16, &src->b, true);
             cp_async16(dst + 32, &src->c, true);
+        }
+        cp_async_commit();
+    };
+    auto prefetch_feat = [&](int b, int stg) {  // feature rows (reads the staged ids)
+        const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
+        const uint32_t *ids = sgid(stg);
+        constexpr int kCPR = DN / 8;
+#pragma unroll 4
+        for (int q = tid; q < kBB * kCPR; q += 256) {
+            const int g = q / kCPR, c = q - g * kCPR;
+            cp_async16(sF_s + (c >> 3) * (kBB * 128) + swz(g, c & 7), feats + (size_t)ids[g] * D + d0 + c * 8,
+                       g < nb);
         }
         cp_async_commit();
     };
@@ -620,9 +634,9 @@ __global__ void __launch_bounds__(128, 1)
     bool pend0 = false, pend1 = false;
     bool timeout = false;
     if (nbat > 0) {
-        prefetch(0, 0);
+        prefetch_rec(0, 0);
         // pixel-moment rows of X: X[n][p] for p = i + 16 j
-        for (int q = tid; q < 16 * 128; q += 128) {
+        for (int q = tid; q < 16 * 128; q += 256) {
             const int n = q >> 7, pp = q & 127;
             const float i = (float)(pp & 15), jv = (float)(pp >> 4);
             const float val = n == 0 ? 1.f : n == 1 ? i : n == 2 ? jv : n == 3 ? i * i : n == 4 ? i * jv
@@ -631,14 +645,14 @@ __global__ void __launch_bounds__(128, 1)
                                                2 * (pp & 7)) = __float2bfloat16_rn(val);
         }
         // dF slice of this CTA's pixels -> BF16 hi / lo, K-major swizzled.  Each
-        // warp copies its 32 pixel rows with 8 rows of loads in flight.
+        // warp copies 16 pixel rows with 8 rows of loads in flight.
         constexpr int kL = DN >= 128 ? DN / 128 : 1;
 #pragma unroll 1
-        for (int r0 = 0; r0 < 32; r0 += 8) {
+        for (int r0 = 0; r0 < 16; r0 += 8) {
             float4 v[8][kL];
 #pragma unroll
             for (int rr = 0; rr < 8; ++rr) {
-                const int prow = warp * 32 + r0 + rr;
+                const int prow = warp * 16 + r0 + rr;
                 const int qx = x0 + (prow & 15), qy = y0 + (prow >> 4);
                 const bool qin = qx < cam.W && qy < cam.H && gfeat != nullptr;
                 const float *src = gfeat + (cam.pix_off + (long long)qy * cam.W + qx) * D + d0;
@@ -651,7 +665,7 @@ __global__ void __launch_bounds__(128, 1)
             }
 #pragma unroll
             for (int rr = 0; rr < 8; ++rr) {
-                const int prow = warp * 32 + r0 + rr;
+                const int prow = warp * 16 + r0 + rr;
 #pragma unroll
                 for (int li = 0; li < kL; ++li) {
                     const int f = li * 128 + lane * 4;
@@ -673,6 +687,8 @@ __global__ void __launch_bounds__(128, 1)
                 }
             }
         }
+        __syncthreads();  // batch 0's ids are staged
+        prefetch_feat(0, 0);
         cp_async_wait_all();
         fence_async_smem();
         __syncthreads();
@@ -685,6 +701,8 @@ __global__ void __launch_bounds__(128, 1)
     for (int b = 0; b < nbat; ++b) {
         const int stg = b & 1;
         const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
+        const bool more = b + 1 < nbat;
+        if (more) prefetch_rec(b + 1, stg ^ 1);
         {
             const bool ok = mbar_wait(&bars[0], ph0);
             if (ok) {
@@ -698,96 +716,112 @@ __global__ void __launch_bounds__(128, 1)
         }
         tc_after();
         // G of this batch is in TMEM: the feature stage is free for batch b+1
-        if (b + 1 < nbat) prefetch(b + 1, stg ^ 1);
+        if (more) prefetch_feat(b + 1, stg ^ 1);
         const GRec *R = srec(stg);
-        // back to front over two sub-batches of 32 Gaussians
-#pragma unroll 1
-        for (int sub = 1; sub >= 0; --sub) {
-            float Gv[32];
-            tmem_ld32(tG + ((uint32_t)(warp * 32) << 16) + sub * 32, Gv);
-            float al[32], gx[32], Tj[32];
-            float P = 1.f;
+        float Gv[32];
+        tmem_ld32(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * 32, Gv);
+        float al[32], gx[32], Tj[32];
+        float P = 1.f;
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-                const int j = sub * 32 + jj;
-                const float4 A4 = R[j].a, B4 = R[j].b;
-                const float dx = fpx - A4.x, dy = fpy - A4.y;
-                const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
-                const float G = __expf(-0.5f * q2);
-                const float rho = B4.y * G;
-                const float aa = fminf(p.amax, rho);
-                const bool ok = (j < nb) && (bs + j < lastp) && (q2 <= p.cut) && (aa >= p.amin);
-                al[jj] = ok ? aa : 0.f;
-                gx[jj] = (ok && rho <= p.amax) ? G : 0.f;
-                P *= 1.f - al[jj];
-            }
-            // T before the sub-batch, then the forward prefix of transmittance
-            const float Tstart = __fdividef(T, P);
+        for (int jj = 0; jj < 32; ++jj) {
+            const int j = grp * 32 + jj;
+            const float4 A4 = R[j].a, B4 = R[j].b;
+            const float dx = fpx - A4.x, dy = fpy - A4.y;
+            const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
+            const float G = __expf(-0.5f * q2);
+            const float rho = B4.y * G;
+            const float aa = fminf(p.amax, rho);
+            const bool ok = (j < nb) && (bs + j < lastp) && (q2 <= p.cut) && (aa >= p.amin);
+            al[jj] = ok ? aa : 0.f;
+            gx[jj] = (ok && rho <= p.amax) ? G : 0.f;
+            P *= 1.f - al[jj];
+        }
+        if (grp == 1) xP1[pidx] = P;
+        __syncthreads();
+        // T after this group's Gaussians, then T before each of them
+        const float Tend = grp == 1 ? T : __fdividef(T, xP1[pidx]);
+        const float Tstart = __fdividef(Tend, P);
+        {
             float t = Tstart;
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
                 Tj[jj] = t;
                 t *= 1.f - al[jj];
             }
-            // App. A.2 back to front: dL/dalpha_k = T_k g_k - S_k / (1 - alpha_k);
-            // gx becomes t_k = G dL/drho
+        }
+        // App. A.2 back to front: dL/dalpha_k = T_k g_k - S_k / (1 - alpha_k);
+        // Gv becomes t_k = G dL/drho (group 0: still without S + S_1)
+        float Sg = grp == 1 ? S : 0.f;
 #pragma unroll
-            for (int jj = 31; jj >= 0; --jj) {
-                const int j = sub * 32 + jj;
-                // selects, not products with zero: records past the batch end are stale
-                const bool c = al[jj] > 0.f;
-                const float w = al[jj] * Tj[jj];
-                const float4 B4 = R[j].b;
-                const float g = c ? Gv[jj] + dC0 * B4.z + dC1 * B4.w + dC2 * R[j].c.x : 0.f;
-                const float dal = Tj[jj] * g - __fdividef(S, 1.f - al[jj]);
-                S = c ? S + w * g : S;
-                gx[jj] = c ? gx[jj] * dal : 0.f;
-            }
-            // weights (A of dFe) and t hi/lo (A of the moments) for Gaussians sub*32..
+        for (int jj = 31; jj >= 0; --jj) {
+            const int j = grp * 32 + jj;
+            // selects, not products with zero: records past the batch end are stale
+            const bool c = al[jj] > 0.f;
+            const float w = al[jj] * Tj[jj];
+            const float4 B4 = R[j].b;
+            const float g = c ? Gv[jj] + dC0 * B4.z + dC1 * B4.w + dC2 * R[j].c.x : 0.f;
+            const float dal = Tj[jj] * g - __fdividef(Sg, 1.f - al[jj]);
+            Sg = c ? Sg + w * g : Sg;
+            Gv[jj] = c ? gx[jj] * dal : 0.f;
+        }
+        if (grp == 1) xS1[pidx] = Sg - S;
+        __syncthreads();
+        if (grp == 0) {
+            const float Sb = S + xS1[pidx];  // suffix sum entering group 0's Gaussians
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint4 pw, ph, pl;
-                uint32_t *pwv = &pw.x, *phv = &ph.x, *plv = &pl.x;
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int j0 = 8 * q + 2 * h;
-                    pwv[h] = pack_bf16(al[j0] * Tj[j0], al[j0 + 1] * Tj[j0 + 1]);
-                    const __nv_bfloat162 th = __floats2bfloat162_rn(gx[j0], gx[j0 + 1]);
-                    const float2 tb = __bfloat1622float2(th);
-                    phv[h] = *reinterpret_cast<const uint32_t *>(&th);
-                    plv[h] = pack_bf16(gx[j0] - tb.x, gx[j0 + 1] - tb.y);
-                }
-                const uint32_t off = swz(tid, sub * 4 + q);
-                *reinterpret_cast<uint4 *>(sW + off) = pw;
-                *reinterpret_cast<uint4 *>(sTh + off) = ph;
-                *reinterpret_cast<uint4 *>(sTl + off) = pl;
-            }
-            // which Gaussians contribute anywhere in the CTA; RGB sums (slice 0)
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-                const bool c = al[jj] > 0.f;
-                if (!__any_sync(0xffffffffu, c)) continue;
-                const int j = sub * 32 + jj;
-                if (lane == 0) sFlag[j] = 1;
-                if (chunk == 0) {
-                    const float w = al[jj] * Tj[jj];
-                    float v[4] = {w * dC0, w * dC1, w * dC2, 0.f};
-                    const float r = warp_rs4(v, lane);
-                    const int k = (lane >> 3) & 3;
-                    if ((lane & 7) == 0 && k < 3) atomicAdd(&sRgb[3 * j + k], r);
-                }
-            }
+            for (int jj = 0; jj < 32; ++jj) Gv[jj] -= __fdividef(gx[jj] * Sb, 1.f - al[jj]);
+            S = Sb + Sg;
             T = Tstart;
+            xT[pidx] = T;
+            xS[pidx] = S;
+        }
+        // weights (A of dFe) and t hi/lo (A of the moments) of this group's Gaussians
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint4 pw, ph, pl;
+            uint32_t *pwv = &pw.x, *phv = &ph.x, *plv = &pl.x;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int j0 = 8 * q + 2 * h;
+                pwv[h] = pack_bf16(al[j0] * Tj[j0], al[j0 + 1] * Tj[j0 + 1]);
+                const __nv_bfloat162 th = __floats2bfloat162_rn(Gv[j0], Gv[j0 + 1]);
+                const float2 tb = __bfloat1622float2(th);
+                phv[h] = *reinterpret_cast<const uint32_t *>(&th);
+                plv[h] = pack_bf16(Gv[j0] - tb.x, Gv[j0 + 1] - tb.y);
+            }
+            const uint32_t off = swz(pidx, grp * 4 + q);
+            *reinterpret_cast<uint4 *>(sW + off) = pw;
+            *reinterpret_cast<uint4 *>(sTh + off) = ph;
+            *reinterpret_cast<uint4 *>(sTl + off) = pl;
+        }
+        // which Gaussians contribute anywhere in the CTA; RGB sums (slice 0)
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+            const bool c = al[jj] > 0.f;
+            if (!__any_sync(0xffffffffu, c)) continue;
+            const int j = grp * 32 + jj;
+            if (lane == 0) sFlag[j] = 1;
+            if (chunk == 0) {
+                const float w = al[jj] * Tj[jj];
+                float v[4] = {w * dC0, w * dC1, w * dC2, 0.f};
+                const float r = warp_rs4(v, lane);
+                const int k = (lane >> 3) & 3;
+                if ((lane & 7) == 0 && k < 3) atomicAdd(&sRgb[3 * j + k], r);
+            }
         }
         cp_async_wait_all();  // batch b+1's records and features have landed
         fence_async_smem();
         __syncthreads();
+        if (grp == 1) {
+            T = xT[pidx];
+            S = xS[pidx];
+        }
         if (tid == 0) {
             issue_FM();
-            if (b + 1 < nbat) issue_G();
+            if (more) issue_G();
         }
         pend1 = true;
-        if (b + 1 < nbat) pend0 = true;
+        if (more) pend0 = true;
         {
             const bool ok = mbar_wait(&bars[1], ph1);
             if (ok) {
@@ -800,35 +834,38 @@ __global__ void __launch_bounds__(128, 1)
             }
         }
         tc_after();
-        if (warp < 2) {  // rows 0..63 of the moment and dFe accumulators = the batch's Gaussians
-            const int j = tid;
+        if ((warp & 3) < 2) {  // rows 0..63 of the accumulators = the batch's Gaussians
+            const int j = (warp & 1) * 32 + lane;
             const bool mine = j < nb && sFlag[j] != 0;
             const uint32_t gid = sgid(stg)[j];
-            float m[16];
-            tmem_ld16(tM + ((uint32_t)(warp * 32) << 16), m);
-            if (mine) {
-                const GRec r = R[j];
-                // moments about the pixel grid: dx = i - a, dy = j - b
-                const float a = r.a.x - (float)x0 - 0.5f, bb = r.a.y - (float)y0 - 0.5f;
-                const float M0 = m[0], Mi = m[1], Mj = m[2], Mii = m[3], Mij = m[4], Mjj = m[5];
-                const float Sx = Mi - a * M0, Sy = Mj - bb * M0;
-                const float Sxx = Mii - 2.f * a * Mi + a * a * M0;
-                const float Sxy = Mij - a * Mj - bb * Mi + a * bb * M0;
-                const float Syy = Mjj - 2.f * bb * Mj + bb * bb * M0;
-                const float op = r.b.y, cA = r.a.z, cB = r.a.w, cC = r.b.x;
-                float4 *dst = reinterpret_cast<float4 *>(g2dc + 12 * (long long)gid);
-                atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy), -0.5f * op * Sxx,
-                                           -op * Sxy));
-                atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, chunk == 0 ? sRgb[3 * j] : 0.f,
-                                               chunk == 0 ? sRgb[3 * j + 1] : 0.f));
-                if (chunk == 0) atomicAdd(g2dc + 12 * (long long)gid + 8, sRgb[3 * j + 2]);
+            const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+            if (grp == 0) {
+                float m[16];
+                tmem_ld16(tM + lanes, m);
+                if (mine) {
+                    const GRec r = R[j];
+                    // moments about the pixel grid: dx = i - a, dy = j - b
+                    const float a = r.a.x - (float)x0 - 0.5f, bb = r.a.y - (float)y0 - 0.5f;
+                    const float M0 = m[0], Mi = m[1], Mj = m[2], Mii = m[3], Mij = m[4], Mjj = m[5];
+                    const float Sx = Mi - a * M0, Sy = Mj - bb * M0;
+                    const float Sxx = Mii - 2.f * a * Mi + a * a * M0;
+                    const float Sxy = Mij - a * Mj - bb * Mi + a * bb * M0;
+                    const float Syy = Mjj - 2.f * bb * Mj + bb * bb * M0;
+                    const float op = r.b.y, cA = r.a.z, cB = r.a.w, cC = r.b.x;
+                    float4 *dst = reinterpret_cast<float4 *>(g2dc + 12 * (long long)gid);
+                    atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy),
+                                               -0.5f * op * Sxx, -op * Sxy));
+                    atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, chunk == 0 ? sRgb[3 * j] : 0.f,
+                                                   chunk == 0 ? sRgb[3 * j + 1] : 0.f));
+                    if (chunk == 0) atomicAdd(g2dc + 12 * (long long)gid + 8, sRgb[3 * j + 2]);
+                }
             }
-            if (want_fg) {
-                float *dst = gfeatures + (size_t)gid * D + d0;
+            if (want_fg) {  // group g drains columns [g DN/2, (g+1) DN/2)
+                float *dst = gfeatures + (size_t)gid * D + d0 + grp * (DN / 2);
 #pragma unroll 1
-                for (int cc = 0; cc < DN / 32; ++cc) {
+                for (int cc = 0; cc < DN / 64; ++cc) {
                     float v[32];
-                    tmem_ld32(tF + ((uint32_t)(warp * 32) << 16) + cc * 32, v);
+                    tmem_ld32(tF + lanes + grp * (DN / 2) + cc * 32, v);
                     if (mine) {
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
@@ -837,12 +874,14 @@ __global__ void __launch_bounds__(128, 1)
                     }
                 }
             }
-            sFlag[j] = 0;
-            sRgb[3 * j] = sRgb[3 * j + 1] = sRgb[3 * j + 2] = 0.f;
         }
         tc_before();
         __syncthreads();
         tc_after();
+        if (tid < kBB) {
+            sFlag[tid] = 0;
+            sRgb[3 * tid] = sRgb[3 * tid + 1] = sRgb[3 * tid + 2] = 0.f;
+        }
     }
     if (timeout) {
         if (tid == 0) latch(status, ST_TIMEOUT);
@@ -915,7 +954,7 @@ void launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
 #define FHGS_BWD(DNV)                                                                                          \
     case DNV: {                                                                                                \
         set_smem(k_render_bwd_tc<DNV>, BwdCfg<DNV>::kSmem);                                                   \
-        k_render_bwd_tc<DNV><<<grid, 128, BwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, feats, D, T, \
+        k_render_bwd_tc<DNV><<<grid, 256, BwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, feats, D, T, \
                                                                    last, grgb, gfeat, g2d, gfeatures, status);  \
         break;                                                                                                 \
     }
