@@ -208,6 +208,38 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
                                const float *const *maps, int D, const fhgs_params *p, float *num,
                                float *den, float *out, uint32_t flags, void *stream);
 
+/* ----------------------------------------------------- allocation-free -- */
+/* Largest n_cams * n accepted by fhgs_render_bwd_noalloc.  Its scratch is
+ * 48 bytes per (camera, Gaussian): 12 MiB, reserved on every GPU that loads
+ * the library until the process exits. */
+#define FHGS_NOALLOC_MAX_ENTRIES 262144
+
+/* The paper has no counterpart to this call.  It is fhgs_render_bwd for
+ * callers that cannot allocate device memory (code inside a custom device
+ * allocator or a memory pool's callback, which must not re-enter cudaMalloc;
+ * plugin hosts that own every device allocation; loops that keep allocation
+ * out of their steady state).  It needs no context and allocates nothing:
+ * arguments, layouts and results are those of fhgs_render_bwd, on the
+ * current CUDA device.
+ *   - Its scratch (the per-(camera, Gaussian) footprint gradients) and a
+ *     status word are file-scope device arrays of the library.
+ *   - n_cams * n > FHGS_NOALLOC_MAX_ENTRIES returns FHGS_ERR_UNSUPPORTED and
+ *     launches nothing; the other argument checks return as in
+ *     fhgs_render_bwd (without a message: there is no context).
+ *   - The first call on a device looks up the arrays' device addresses with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call shares the arrays and clears the scratch first: calls that
+ *     overlap on the GPU (several streams or threads) race on it, so order
+ *     them on one stream.
+ *   - A device-side error (a bounded wait that ran out) is latched in the
+ *     library's own status word, which this call does not report. */
+fhgs_status fhgs_render_bwd_noalloc(const fhgs_gaussians *g, const void *proj, const fhgs_bins *bins,
+                                    const void *features, fhgs_dtype ftype, int D, const fhgs_camera *cams,
+                                    int n_cams, const fhgs_params *p, const float *T_final, const int32_t *last,
+                                    const float *grad_rgb, const float *grad_feat, float *grad_means,
+                                    float *grad_scales, float *grad_quats, float *grad_opac, float *grad_sh,
+                                    float *grad_features, void *stream);
+
 /* ----------------------------------------------------- instrumentation -- */
 /* Kernel timing: while enabled, every kernel group the context launches is
  * bracketed by CUDA events recorded on the launch stream (a pool of 8192

@@ -21,11 +21,12 @@ PATH_AUTO, PATH_FP32, PATH_TC = 0, 1, 2
 F32, BF16 = 0, 1
 FUSE_ACCUMULATE, FUSE_FINALIZE, FUSE_NORMALIZE = 1, 2, 4
 MAX_CAMS = 32
+NOALLOC_MAX_ENTRIES = 262144  # FHGS_NOALLOC_MAX_ENTRIES of include/fhgs.h
 
 EXPORTS = ["fhgs_create", "fhgs_destroy", "fhgs_last_error", "fhgs_status_string", "fhgs_abi_version",
            "fhgs_default_params", "fhgs_proj_bytes", "fhgs_total_tiles", "fhgs_reserve", "fhgs_sync_status",
            "fhgs_project", "fhgs_bin_sort", "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features",
-           "fhgs_profile_enable", "fhgs_profile_read", "fhgs_launch_count"]
+           "fhgs_profile_enable", "fhgs_profile_read", "fhgs_launch_count", "fhgs_render_bwd_noalloc"]
 
 
 class Camera(ctypes.Structure):
@@ -100,6 +101,10 @@ def lib():
         L.fhgs_fuse_features.argtypes = [vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), i32,
                                          ctypes.POINTER(ctypes.c_void_p), i32, ctypes.POINTER(Params), f32p, f32p,
                                          f32p, ctypes.c_uint32, vp]
+        L.fhgs_render_bwd_noalloc.argtypes = [ctypes.POINTER(Gaussians), vp, ctypes.POINTER(Bins), vp, i32, i32,
+                                              ctypes.POINTER(Camera), i32, ctypes.POINTER(Params), f32p, vp, f32p,
+                                              f32p, f32p, f32p, f32p, f32p, f32p, f32p, vp]
+        L.fhgs_render_bwd_noalloc.restype = i32
         L.fhgs_profile_enable.argtypes = [vp, i32]
         L.fhgs_profile_read.argtypes = [vp, ctypes.c_char_p, i64]
         L.fhgs_launch_count.argtypes = []
@@ -222,6 +227,17 @@ class Context:
         self.check(lib().fhgs_fuse_features(self.h, ctypes.byref(g), views, len(views), ptrs, int(D),
                                             ctypes.byref(params), _ptr(num), _ptr(den), _ptr(out), int(flags),
                                             self.stream_ptr(stream)))
+
+
+def render_bwd_noalloc(g, proj, bins, features, D, cams, params, T, last, grgb, gfeat, out: dict, stream=None) -> int:
+    """fhgs_render_bwd_noalloc: the backward without a context and without
+    allocating (scratch in a fixed device array).  Returns the status code."""
+    ft = BF16 if (features is not None and features.dtype == torch.bfloat16) else F32
+    return int(lib().fhgs_render_bwd_noalloc(ctypes.byref(g), _ptr(proj), ctypes.byref(bins), _ptr(features), ft,
+                                             int(D), cams, len(cams), ctypes.byref(params), _ptr(T), _ptr(last),
+                                             _ptr(grgb), _ptr(gfeat), _ptr(out["means"]), _ptr(out["scales"]),
+                                             _ptr(out["quats"]), _ptr(out["opacities"]), _ptr(out["sh"]),
+                                             _ptr(out.get("features")), Context.stream_ptr(stream)))
 
 
 def gaussians_struct(means, scales, quats, opacities, sh) -> Gaussians:

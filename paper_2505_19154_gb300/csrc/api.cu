@@ -214,6 +214,34 @@ bool use_tc(const fhgs_params *p, fhgs_dtype ft, int D) {
 
 }  // namespace
 
+namespace fhgs {
+// Argument checks of the allocation-free backward (fhgs_render_bwd_noalloc);
+// the same checks as fhgs_render_bwd, with ctx == nullptr (no message kept).
+fhgs_status check_bwd_args(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *proj, const fhgs_bins *bins,
+                           const void *features, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
+                           const fhgs_params *p, const float *T_final, const int32_t *last, const float *grad_rgb,
+                           const float *grad_feat, float *grad_means, float *grad_scales, float *grad_quats,
+                           float *grad_opac, float *grad_sh, float *grad_features, CamSet &cs, Params &q, bool &tc) {
+    fhgs_status s = check_params(ctx, p);
+    if (s == FHGS_OK) s = check_gaussians(ctx, g, true);
+    if (s == FHGS_OK) s = check_bins(ctx, bins);
+    if (s == FHGS_OK) s = check_features(ctx, features, ftype, D, g ? g->n : 0);
+    if (s != FHGS_OK) return s;
+    if (!proj || !T_final || !last || !grad_rgb) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL input buffer");
+    if (g->n > 0 && (!grad_means || !grad_scales || !grad_quats || !grad_opac || !grad_sh))
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL gradient buffer");
+    if (!aligned16(grad_quats)) return fail(ctx, FHGS_ERR_ALIGNMENT, "grad_quats must be 16-byte aligned");
+    if ((grad_feat && !aligned16(grad_feat)) || (grad_features && !aligned16(grad_features)))
+        return fail(ctx, FHGS_ERR_ALIGNMENT, "feature gradients must be 16-byte aligned");
+    if (p->path == FHGS_PATH_TC && D > 0 && !use_tc(p, ftype, D))
+        return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core path needs BF16 features and a supported D");
+    if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
+    q = make_params(p);
+    tc = D > 0 && use_tc(p, ftype, D) && (grad_feat || grad_features);
+    return FHGS_OK;
+}
+}  // namespace fhgs
+
 extern "C" {
 
 int fhgs_abi_version(void) { return FHGS_ABI_VERSION; }

@@ -101,6 +101,14 @@ __device__ __forceinline__ void latch(unsigned *status, unsigned bit) {
 // Counts kernel launches (fhgs_launch_count); defined in api.cu.
 void note_launch(int k);
 
+// Argument checks of the allocation-free backward (api.cu); ctx may be
+// nullptr.  Fills the device camera set, parameters and the path choice.
+fhgs_status check_bwd_args(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *proj, const fhgs_bins *bins,
+                           const void *features, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
+                           const fhgs_params *p, const float *T_final, const int32_t *last, const float *grad_rgb,
+                           const float *grad_feat, float *grad_means, float *grad_scales, float *grad_quats,
+                           float *grad_opac, float *grad_sh, float *grad_features, CamSet &cs, Params &q, bool &tc);
+
 // ---------------------------------------------------------------- launches
 // projection (project.cu)
 void launch_project(const fhgs_gaussians &g, const CamSet &cs, const Params &p, ProjView pv,
