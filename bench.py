@@ -133,15 +133,82 @@ def make_workload(seed, n, D, dev, width=1920, height=1080):
     return scene, cams, t, P
 
 
-def algorithmic_bytes(P, N, D, I):
-    """Bytes each kernel group must move at minimum (see the roofline notes
-    in the design doc): images once, features/records once per pass, gradients
-    written once, tile instances written and read once."""
+def composited_pairs(st, cams, tile=16):
+    """Q = sum over tiles of (pixels in the tile) x (Gaussians the tile walks
+    before its last pixel saturates), the per-pixel count sum_p last_p, and
+    U = how many distinct Gaussians some tile walks (their records and
+    feature rows are the ones a render pass must read).  `last` is the
+    forward output: (position of the last contributor in the tile's list)
+    + 1 per pixel."""
+    import torch
+    last, ranges, gids = st["last"], st["ranges"].to(torch.int64), st["gids"]
+    q_tile, q_pix, off, toff = 0, 0, 0, 0
+    walked = []
+    for c in cams:
+        w, h = c["width"], c["height"]
+        L = last[off:off + w * h].view(h, w).to(torch.int64)
+        off += w * h
+        ty, tx = (h + tile - 1) // tile, (w + tile - 1) // tile
+        pad = torch.zeros((ty * tile, tx * tile), dtype=torch.int64, device=L.device)
+        ones = torch.zeros_like(pad)
+        pad[:h, :w] = L
+        ones[:h, :w] = 1
+        mx = pad.view(ty, tile, tx, tile).amax(dim=(1, 3)).reshape(-1)
+        cnt = ones.view(ty, tile, tx, tile).sum(dim=(1, 3)).reshape(-1)
+        q_tile += int((mx * cnt).sum().item())
+        q_pix += int(L.sum().item())
+        start = ranges[toff:toff + ty * tx, 0]
+        toff += ty * tx
+        idx = torch.repeat_interleave(start, mx) + (
+            torch.arange(int(mx.sum().item()), device=L.device) -
+            torch.repeat_interleave(torch.cumsum(mx, 0) - mx, mx))
+        walked.append(gids[idx].to(torch.int64) + (len(walked) << 40))
+    U = int(torch.unique(torch.cat(walked)).numel()) if walked else 0
+    return q_tile, q_pix, U
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# a kernel at 1920x1080, from an ncu capture of the 960x544 centre crop scaled
+# by the pixel count (the traffic of both render kernels is the per-pixel
+# image: dF read, feature image written), with the SHA-256 of the kernel's
+# source file at capture time: a changed source reports null.
+_CROP_SCALE = (1920 * 1080) / (960 * 544)
+TRAFFIC = {
+    "render_bwd_tc": {"bytes": int((1096.5e6 + 4.6e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "8884ebe780fab59e675bb06db6c7e87c3cbfaa7e4d591d631429c43abefafd0f"},
+    "render_fwd_tc": {"bytes": int((11.7e6 + 1017.2e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "8884ebe780fab59e675bb06db6c7e87c3cbfaa7e4d591d631429c43abefafd0f"},
+}
+
+
+def traffic_for(kernel):
+    import hashlib
+    rec = TRAFFIC.get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2505_19154_gb300", "csrc", rec["file"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
+        return None
+    return rec["bytes"]
+
+
+def algorithmic_flops(N, D, Q):
+    """Tensor-core FLOPs of the feature contractions: the blend W(PxB).Fe(BxD)
+    forward (2DQ), dL/dw = dF.Fe^T and grad_Fe = W^T.dF backward (4DQ)."""
+    return {"render_fwd": 2 * D * Q, "render_bwd": 4 * D * Q}
+
+
+def algorithmic_bytes(P, N, D, I, U):
+    """Bytes each kernel group must move at minimum: images once, the
+    records and feature rows of the U Gaussians the tiles walk once per
+    pass, their feature and footprint gradients written once, per-Gaussian
+    inputs and outputs once, tile instances written and read once (4 B
+    index + 8 B key each way)."""
     return {
         "project": N * (12 + 12 + 16 + 4 + 192) + N * (48 + 16 + 8),
         "bin_sort": 24 * I,
-        "render_fwd": P * (4 * D + 20) + N * (2 * D + 48),
-        "render_bwd": P * (4 * D + 20) + N * (2 * D + 48) + N * (4 * D + 48),
+        "render_fwd": P * (4 * D + 20) + U * (2 * D + 48),
+        "render_bwd": P * (4 * D + 20) + U * (2 * D + 48) + U * (4 * D + 48),
         "project_bwd": N * (236 + 48) + N * (48 + 236),
     }
 
@@ -171,7 +238,7 @@ def run_ours(args):
         return st, rgb, feat, grads
 
     for _ in range(max(args.warmup, 1)):
-        step(rast)
+        st_w, _, _, _ = step(rast)
     torch.cuda.synchronize()
     status = rast.ctx.sync_status()
     if status != api.OK:
@@ -180,6 +247,8 @@ def run_ours(args):
         step(rast)
         torch.cuda.synchronize()
         return
+    Q, Qpix, U = composited_pairs(st_w, cams)
+    del st_w
 
     def barrier():
         if world > 1:
@@ -222,19 +291,41 @@ def run_ours(args):
     # kernel-level roofline: the dominant kernel group, algorithmic bytes / its mean duration
     peaks = load_peaks()
     N, D = args.n, args.D
-    algo = algorithmic_bytes(P, N, D, I)
+    algo = algorithmic_bytes(P, N, D, I, U)
     per = {}
     for name, (cnt, tot) in prof.items():
         base = name.replace("_tc", "").replace("_fp32", "")
         per[name] = dict(launches=cnt, ms=tot / max(cnt, 1), share=tot / max(1e-9, sum(v[1] for v in prof.values())),
                          bytes=algo.get(base))
+    flops = algorithmic_flops(N, D, Q)
+    for name, rec in per.items():
+        base = name.replace("_tc", "").replace("_fp32", "")
+        sec = rec["ms"] * 1e-3
+        if rec["bytes"]:
+            rec["hbm_frac"] = round(rec["bytes"] / sec / 1e9 / peaks["hbm"], 4)
+        if base in flops and name.endswith("_tc"):
+            rec["tensor_flops"] = flops[base]
+            rec["tensor_frac"] = round(flops[base] / sec / 1e12 / peaks["bf16_sus"], 4)
     dom = max(per, key=lambda k: per[k]["ms"] * per[k]["launches"]) if per else None
     roof = None
     if dom and per[dom]["bytes"]:
-        ach = per[dom]["bytes"] / (per[dom]["ms"] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peaks["hbm"], "unit": "GB/s",
-                "frac": round(ach / peaks["hbm"], 4), "traffic": None,
-                "peak_source": peaks["src"] + " (MEASURED_PEAKS.json hbm_gbs)" if peaks["src"] == "measured" else "fallback"}
+        # the bound is the resource whose time at peak is longer for this
+        # kernel's algorithmic work (HBM bytes vs tensor-core FLOPs)
+        t_hbm = per[dom]["bytes"] / (peaks["hbm"] * 1e9)
+        t_tc = per[dom].get("tensor_flops", 0) / (peaks["bf16_sus"] * 1e12)
+        sec = per[dom]["ms"] * 1e-3
+        src = "of measured" if peaks["src"] == "measured" else "of fallback"
+        if t_tc > t_hbm:
+            ach = per[dom]["tensor_flops"] / sec / 1e12
+            roof = {"bound": "tensor", "kernel": dom, "achieved": round(ach, 1), "peak": peaks["bf16_sus"],
+                    "unit": "TFLOP/s", "frac": round(ach / peaks["bf16_sus"], 4),
+                    "peak_source": src + " (bf16_tflops_sustained)"}
+        else:
+            ach = per[dom]["bytes"] / sec / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peaks["hbm"], "unit": "GB/s",
+                    "frac": round(ach / peaks["hbm"], 4), "peak_source": src + " (hbm_gbs)"}
+        roof["traffic"] = traffic_for(dom)
+        roof["algorithmic_bytes"] = per[dom]["bytes"]
 
     # FP32 CUDA-core path on the same inputs (the baseline the TC path must beat)
     fp32 = None
@@ -299,8 +390,12 @@ def run_ours(args):
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if used_tc else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "gaussians": N, "width": 1920, "height": 1080, "feature_dim": D,
+            "config": {"workload": WORKLOAD if (args.width, args.height) == (1920, 1080) else
+                       WORKLOAD.replace("1920x1080 view", f"{args.width}x{args.height} centre crop"),
+                       "gaussians": N, "width": args.width, "height": args.height, "feature_dim": D,
                        "sh_degree": 3, "path": "tc" if used_tc else "fp32", "tile_instances": I,
+                       "composited_pairs_tile": Q, "composited_pairs_pixel": Qpix,
+                       "gaussians_walked": U,
                        "l2": "inputs larger than L2 (features 1 GB, dL/dfeat 4.2 GB)",
                        "parallelism": f"independent views, {world} GPU(s)"},
             "roofline": roof, "kernels": per, "fp32_path": fp32, "e2e": e2e, "cpu_baseline": cpu,

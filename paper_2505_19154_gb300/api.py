@@ -334,6 +334,26 @@ class Rasterizer:
         self.ctx.fuse(g, make_cameras(views), [m.contiguous() for m in maps], D, self.params, num, den, out, flags)
         return out, num, den
 
+    def fuse_accumulate(self, gaussians: tuple, views: Sequence[dict], maps: Sequence[torch.Tensor], num, den):
+        """Add the views' fusion numerator and denominator into num/den (no
+        division)."""
+        g = gaussians_struct(*gaussians)
+        D = int(num.shape[1])
+        self.ctx.fuse(g, make_cameras(views), [m.contiguous() for m in maps], D, self.params, num, den, None,
+                      FUSE_ACCUMULATE)
+
+    def fuse_finalize(self, gaussians: tuple, num, den, normalize: bool = False):
+        """f = num / den (0 where den == 0), optionally L2-normalised."""
+        g = gaussians_struct(*gaussians)
+        out = torch.empty_like(num)
+        dummy = make_cameras([dict(width=1, height=1, fx=1.0, fy=1.0, cx=0.5, cy=0.5,
+                                   w2c=np.eye(3, 4))])  # n_views = 0: only the division runs
+        flags = FUSE_ACCUMULATE | FUSE_FINALIZE | (FUSE_NORMALIZE if normalize else 0)
+        self.ctx.check(lib().fhgs_fuse_features(self.ctx.h, ctypes.byref(g), dummy, 0, None, int(num.shape[1]),
+                                                ctypes.byref(self.params), _ptr(num), _ptr(den), _ptr(out),
+                                                int(flags), self.ctx.stream_ptr(None)))
+        return out
+
 
 class _RenderFn(torch.autograd.Function):
     @staticmethod
