@@ -48,7 +48,8 @@ extern "C" {
 typedef enum fhgs_status {
     FHGS_OK = 0,
     FHGS_ERR_INVALID_ARG = 1,  /* NULL pointer, negative size, bad camera */
-    FHGS_ERR_UNSUPPORTED = 2,  /* D % 8 != 0, sh_degree > 3, tile != 16x16, too many cameras */
+    FHGS_ERR_UNSUPPORTED = 2,  /* D % 8 != 0, sh_degree > 3, tile != 16x16, too many cameras,
+                                  a camera too large for binning */
     FHGS_ERR_ALIGNMENT = 3,    /* a pointer that needs 16-byte alignment is not */
     FHGS_ERR_CUDA = 4,         /* a CUDA runtime call failed (see fhgs_last_error) */
     FHGS_ERR_CAPACITY = 5,     /* more tile instances than the buffer holds */
@@ -61,7 +62,9 @@ typedef struct fhgs_ctx fhgs_ctx;
 
 /* Pinhole camera, OpenCV axes (x right, y down, z forward).  world_to_cam is
  * the 3x4 matrix [R|t] row by row: x_cam = R x_world + t (the matrix W of
- * Eq. 3).  width, height >= 1; fx, fy > 0. */
+ * Eq. 3).  width, height >= 1; fx, fy > 0.  Tile grid (16x16 tiles):
+ * (tiles_x + 1) * (tiles_y + 1) <= 57344 and tiles_x <= 4096 (4K frames fit;
+ * larger ones return FHGS_ERR_UNSUPPORTED). */
 typedef struct fhgs_camera {
     int32_t width, height;
     float fx, fy, cx, cy;

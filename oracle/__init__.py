@@ -290,11 +290,25 @@ def project_bwd(scene, cam, params, rec, g2d: dict) -> dict:
 
 
 # ------------------------------------------------------------- pipelines
-def prepare(scene: dict, cams: list, params: dict | None = None, tile_rect=None) -> dict:
-    """Binning (FP32 spec), tile lists and FP64 records for every camera."""
+def prepare(scene: dict, cams: list, params: dict | None = None, tile_rect=None, geometry: str = "fp64") -> dict:
+    """Binning (FP32 spec), tile lists and FP64 records for every camera.
+
+    geometry="fp32" composites over the FP32 binning specification's
+    footprints (mean and conic rounded as that specification computes them)
+    instead of the FP64 projection: every contribute/skip decision then
+    rests on the same footprint as in an FP32 renderer that follows the
+    specification, and only the compositing arithmetic stays FP64."""
     bins = [bin_f32(scene, c, params) for c in cams]
     lists = tile_lists(bins, cams, params, tile_rect=tile_rect)
     recs = [project(scene, c, params) for c in cams]
+    if geometry == "fp32":
+        for b, r in zip(bins, recs):
+            fp = b["fp"].astype(np.float64)
+            ok = b["ntiles"] > 0
+            r[:, [R_MX, R_MY, R_A, R_B, R_C]] = np.where(ok[:, None], fp[:, :5], r[:, [R_MX, R_MY, R_A, R_B, R_C]])
+            r[~ok, R_VALID] = 0.0
+    elif geometry != "fp64":
+        raise ValueError(geometry)
     return dict(bins=bins, lists=lists, recs=recs)
 
 
@@ -340,21 +354,25 @@ def backward(scene: dict, cams: list, params: dict | None, feats, dC_list, dF_li
     return tot
 
 
-def fuse(scene: dict, views: list, maps: list, params: dict | None = None, prep: dict | None = None):
-    """Fused per-Gaussian feature over all views.  maps[v]: (H, W, D)."""
+def fuse(scene: dict, views: list, maps: list, params: dict | None = None, prep: dict | None = None,
+         margin_tol: float = 1e-5):
+    """Fused per-Gaussian feature over all views.  maps[v]: (H, W, D).
+    Also returns wflip: per Gaussian, a bound on the total weight a flipped
+    near-threshold decision (within margin_tol) could move (orc_fuse_view)."""
     prep = prep or prepare(scene, views, params)
     n = len(scene["means"])
     D = int(np.asarray(maps[0]).shape[-1])
     num = np.zeros((n, D))
     den = np.zeros(n)
+    wflip = np.zeros(n)
     for vi, cam in enumerate(views):
         W, H = int(cam["width"]), int(cam["height"])
         fm = _f64(maps[vi]).reshape(-1, D)
         lib().orc_fuse_view(_p(prep["recs"][vi]), _p(np.ascontiguousarray(prep["lists"]["gids"], np.uint32)),
                             _p(_cam_ranges(prep["lists"], vi)), _p(camera_array(cam)),
                             _p(params_array(params)), 0, 0, W, H, _p(fm), ctypes.c_int(D), _p(num),
-                            _p(den))
+                            _p(den), _p(wflip), ctypes.c_double(margin_tol))
     out = np.zeros((n, D))
     flag = np.zeros(n, np.int32)
     lib().orc_fuse_finalize(ctypes.c_int64(n), ctypes.c_int(D), _p(num), _p(den), _p(out), _p(flag))
-    return dict(num=num, den=den, out=out, flag=flag)
+    return dict(num=num, den=den, out=out, flag=flag, wflip=wflip)

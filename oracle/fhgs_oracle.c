@@ -469,6 +469,7 @@ static int composite_pixel(double px, double py, const uint32_t *list, int64_t l
     return nc;
 }
 
+
 /* Tiled render of the pixels in [x0,x1) x [y0,y1) of one camera.
  * gids/ranges: the camera's depth-sorted per-tile lists (ranges[2*tile]).
  * Outputs are indexed by region pixel (row-major in the region). */
@@ -762,12 +763,71 @@ void orc_project_bwd(int64_t n, const double *means, const double *scales, const
 }
 
 /* ------------------------------------------------------------ fusion -- */
+/* Diagnostic for comparisons with a lower-precision renderer: adds to
+ * wflip[g] a bound on how much weight Gaussian g could gain or lose at this
+ * pixel if one of the pixel's threshold decisions lying within `mtol`
+ * (relative) of its threshold came out the other way.  Walking the list as
+ * composite_pixel does:
+ *   - a position whose q^2-cutoff or alpha_min decision is near its
+ *     threshold may gain or lose its own weight, at most a_thr T with a_thr
+ *     the largest alpha inside the band (op e^(-cut (1 - mtol) / 2) clamped
+ *     to alpha_max, or alpha_min (1 + mtol)); every later weight is then
+ *     rescaled by (1 - alpha)^(+-1), i.e. moves by at most a_thr / (1 - a_thr)
+ *     of itself;
+ *   - a contributor whose stop decision (T (1 - alpha) vs t_eps) is near may
+ *     be dropped, with every later contributor; the Gaussian that stopped
+ *     the walk may be added with weight alpha T;
+ *   - the alpha_max clamp is continuous and moves no weight. */
+static void flip_bounds(double px, double py, const uint32_t *list, int64_t len, const double *rec,
+                        const double *prm, double mtol, double *wflip)
+{
+    const double cut = prm[P_CUT], amin = prm[P_AMIN], amax = prm[P_AMAX], teps = prm[P_TEPS];
+    double T = 1.0, ripple = 0.0;
+    int dropping = 0;
+    for (int64_t k = 0; k < len; ++k) {
+        const uint32_t g = list[k];
+        const double *r = rec + (int64_t)ORC_REC * g;
+        if (r[R_VALID] == 0.0) continue;
+        double dx = px - r[R_MX], dy = py - r[R_MY];
+        double q2 = r[R_A] * dx * dx + 2.0 * r[R_B] * dx * dy + r[R_C] * dy * dy;
+        double a_thr = 0.0;  /* largest alpha a decision within mtol of its threshold can have */
+        if (rel(q2, cut) < mtol) {
+            double a = r[R_OP] * exp(-0.5 * cut * (1.0 - mtol));
+            a_thr = a > amax ? amax : a;
+        }
+        double alpha = 0.0;
+        if (q2 <= cut) {
+            double rho = r[R_OP] * exp(-0.5 * q2);
+            alpha = rho > amax ? amax : rho;
+            if (rel(alpha, amin) < mtol && amin * (1.0 + mtol) > a_thr) a_thr = amin * (1.0 + mtol);
+        }
+        const int contributes = q2 <= cut && alpha >= amin;
+        const double Tn = T * (1.0 - alpha);
+        const int near_stop = contributes && rel(Tn, teps) < mtol;
+        if (contributes && Tn < teps) {  /* the walk stops here */
+            if (near_stop) wflip[g] += alpha * T;
+            if (a_thr > 0.0) wflip[g] += a_thr * T;
+            break;
+        }
+        const double w = contributes ? alpha * T : 0.0;
+        wflip[g] += ripple * w + (dropping ? w : 0.0) + a_thr * T;
+        if (near_stop) {
+            wflip[g] += w;
+            dropping = 1;
+        }
+        if (a_thr > 0.0) ripple += a_thr / (1.0 - a_thr);
+        if (contributes) T = Tn;
+    }
+}
+
 /* Accumulates, for one view, num[g][c] += w_g(p) F(p)[c] and
  * den[g] += w_g(p) over the region's pixels, with w the Eq. 4 weights of
- * the tiled forward.  fmap is indexed by region pixel (row-major), D wide. */
+ * the tiled forward.  fmap is indexed by region pixel (row-major), D wide.
+ * wflip (may be NULL) accumulates, per Gaussian, the flip_bounds of the
+ * pixels that have a decision within `mtol` of its threshold. */
 void orc_fuse_view(const double *rec, const uint32_t *gids, const uint32_t *ranges,
                    const double *cam, const double *prm, int x0, int y0, int x1, int y1,
-                   const double *fmap, int D, double *num, double *den)
+                   const double *fmap, int D, double *num, double *den, double *wflip, double mtol)
 {
     const int W = (int)cam[0], tsz = (int)prm[P_TILE];
     const int tiles_x = (W + tsz - 1) / tsz;
@@ -788,6 +848,10 @@ void orc_fuse_view(const double *rec, const uint32_t *gids, const uint32_t *rang
             int nc = composite_pixel(px + 0.5, py + 0.5, list, (int64_t)e - s, rec, NULL, 0, prm, &st,
                                      NULL, ci, ca, cT, cG, ORC_MAXC);
             if (nc > ORC_MAXC) nc = ORC_MAXC;
+            if (wflip && st.margin < mtol) {
+#pragma omp critical(orc_wflip)
+                flip_bounds(px + 0.5, py + 0.5, list, (int64_t)e - s, rec, prm, mtol, wflip);
+            }
             const double *f = fmap + (int64_t)D * idx;
             for (int j = 0; j < nc; ++j) {
                 const uint32_t g = list[ci[j]];

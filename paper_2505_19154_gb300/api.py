@@ -134,6 +134,12 @@ def make_params(sh_degree: int = 0, path: int = PATH_AUTO, bg=(0.0, 0.0, 0.0), *
     return p
 
 
+def copy_params(p: Params) -> Params:
+    q = Params()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(Params))
+    return q
+
+
 def make_cameras(cams: Sequence[dict]):
     """Camera dicts (width, height, fx, fy, cx, cy, w2c 3x4) to a C array.
     Values are rounded to float32 exactly as the oracle's FP32 spec does."""
@@ -260,11 +266,21 @@ class Rasterizer:
         self.ctx = Context(device)
         self.dev = torch.device("cuda", device)
         self.params = make_params(sh_degree=sh_degree, path=path, bg=bg, **params)
+        self.params_bwd = None  # backward parameters when its D split differs
         self.keep_keys = keep_keys
         self.capacity = 0
 
     def set_path(self, path: int):
         self.params.path = int(path)
+        if self.params_bwd is not None:
+            self.params_bwd.path = int(path)
+
+    def set_splits(self, fwd: int, bwd: int):
+        """Feature columns per CTA of the tensor-core forward and backward
+        (0 = the library's choice)."""
+        self.params.d_split = int(fwd)
+        self.params_bwd = copy_params(self.params)
+        self.params_bwd.d_split = int(bwd)
 
     # --------------------------------------------------------------- steps
     def prepare(self, means, scales, quats, opacities, sh, cams: Sequence[dict], capacity: int | None = None,
@@ -317,7 +333,8 @@ class Rasterizer:
                    quats=torch.empty((n, 4), device=self.dev), opacities=torch.empty(n, device=self.dev),
                    sh=torch.empty((n, K, 3), device=self.dev),
                    features=torch.empty((n, D), device=self.dev) if (D and want_feat_grad) else None)
-        self.ctx.render_bwd(st["g"], st["proj"], st["bins"], st["features"], D, st["cams"], self.params, st["T"],
+        params = self.params_bwd if self.params_bwd is not None else self.params
+        self.ctx.render_bwd(st["g"], st["proj"], st["bins"], st["features"], D, st["cams"], params, st["T"],
                             st["last"], grad_rgb.contiguous(),
                             None if grad_feat is None else grad_feat.contiguous(), out)
         return out
@@ -353,6 +370,59 @@ class Rasterizer:
                                                 ctypes.byref(self.params), _ptr(num), _ptr(den), _ptr(out),
                                                 int(flags), self.ctx.stream_ptr(None)))
         return out
+
+
+class CapturedStep:
+    """A whole forward + backward step over fixed cameras, captured once in a
+    CUDA graph and then replayed as one launch: projection, binning, both
+    renders (all cameras of uneven size in one launch each) and the
+    projection backward.  The caller writes new inputs into `inputs` (copy_)
+    before replay(); every replay overwrites `outputs`.
+
+    The instance capacity is fixed at capture (the instance count of the
+    capture-time scene times `margin`); a replay whose scene needs more
+    latches FHGS_ERR_CAPACITY, which rast.ctx.sync_status() reports."""
+
+    def __init__(self, rast: Rasterizer, means, scales, quats, opacities, sh, features, grad_rgb, grad_feat,
+                 cams: Sequence[dict], margin: float = 1.25, warmup: int = 2):
+        self.rast = rast
+        self.cams = list(cams)
+        self.inputs = dict(means=_contig(means), scales=_contig(scales), quats=_contig(quats),
+                           opacities=_contig(opacities), sh=_contig(sh),
+                           features=None if features is None else features.detach().clone().contiguous(),
+                           grad_rgb=_contig(grad_rgb),
+                           grad_feat=None if grad_feat is None else _contig(grad_feat))
+        x = self.inputs
+        n = int(x["means"].shape[0])
+        st = rast.prepare(x["means"], x["scales"], x["quats"], x["opacities"], x["sh"], self.cams)
+        rast.capacity = int(st["n_instances"] * margin) + 1024
+        del st
+        rast.ctx.reserve(n, make_cameras(self.cams))
+        side = torch.cuda.Stream(device=rast.dev)
+        side.wait_stream(torch.cuda.current_stream(rast.dev))
+        with torch.cuda.stream(side):
+            for _ in range(max(1, warmup)):
+                self._step()
+        torch.cuda.current_stream(rast.dev).wait_stream(side)
+        torch.cuda.synchronize(rast.dev)
+        s = rast.ctx.sync_status()
+        if s != OK:
+            raise FhgsError(s, "device status after the warm-up steps")
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.outputs = self._step()
+
+    def _step(self) -> dict:
+        x, r = self.inputs, self.rast
+        st = r.prepare(x["means"], x["scales"], x["quats"], x["opacities"], x["sh"], self.cams, check=False)
+        rgb, feat = r.forward(st, x["features"])
+        grads = r.backward(st, x["grad_rgb"], x["grad_feat"])
+        return dict(rgb=rgb, feat=feat, T=st["T"], last=st["last"], ranges=st["ranges"], gids=st["gids"],
+                    count=st["count"], grads=grads)
+
+    def replay(self) -> dict:
+        self.graph.replay()
+        return self.outputs
 
 
 class _RenderFn(torch.autograd.Function):

@@ -131,6 +131,9 @@ fhgs_status make_cams(fhgs_ctx *ctx, const fhgs_camera *cams, int n_cams, CamSet
         d.H = c.height;
         d.tiles_x = (c.width + kTile - 1) / kTile;
         d.tiles_y = (c.height + kTile - 1) / kTile;
+        if ((long long)(d.tiles_x + 1) * (d.tiles_y + 1) > FHGS_MAX_TILE_CELLS || d.tiles_x > FHGS_MAX_TILES_X)
+            return fail(ctx, FHGS_ERR_UNSUPPORTED, "camera " + std::to_string(i) + " is too large for the binning "
+                        "kernels ((tiles_x + 1) * (tiles_y + 1) <= 57344, tiles_x <= 4096)");
         d.tile_off = (int)tiles;
         d.pix_off = pix;
         d.fx = c.fx;
@@ -506,7 +509,10 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
         make_cams(ctx, views + v, 1, cs);
         if ((s = ensure(ctx, ctx->fuse_ranges, sizeof(uint32_t) * 2 * (size_t)cs.total_tiles)) != FHGS_OK) return s;
         ProjView pv = proj_view(ctx->fuse_proj.p, n);
-        launch_project(*g, cs, q, pv, ctx->status, st);
+        {
+            Prof pr(ctx, "fuse_project", st);
+            launch_project(*g, cs, q, pv, ctx->status, st);
+        }
         // instance capacity: grow until this view's instances fit (reads the
         // count on the host, so fusion is not meant for stream capture)
         for (int tries = 0;; ++tries) {
@@ -520,11 +526,15 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
             b.capacity = (long long)(ctx->fuse_gids.bytes / sizeof(uint32_t));
             if ((s = ensure_bin_scratch(ctx, n, 1, cs.total_tiles)) != FHGS_OK) return s;
             BinScratch sc = bin_scratch_view(ctx->bin.p, n, 1, cs.total_tiles, ctx->sm_count);
-            launch_bin_sort(n, 1, cs, pv, b, sc, nullptr, st);
+            {
+                Prof pr(ctx, "fuse_bin_sort", st);
+                launch_bin_sort(n, 1, cs, pv, b, sc, nullptr, st);
+            }
             int64_t count = 0;
             FHGS_CUDA(ctx, cudaMemcpyAsync(&count, b.n_instances, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
             FHGS_CUDA(ctx, cudaStreamSynchronize(st));
             if (count <= b.capacity) {
+                Prof pr(ctx, "fuse_fp32", st);
                 launch_fuse_fp32(n, cs, q, pv, b, maps[v], D, num, den, st);
                 break;
             }
@@ -534,7 +544,10 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
         }
         FHGS_CUDA(ctx, cudaGetLastError());
     }
-    if (flags & FHGS_FUSE_FINALIZE) launch_fuse_finalize(n, D, num, den, out, (flags & FHGS_FUSE_NORMALIZE) != 0, st);
+    if (flags & FHGS_FUSE_FINALIZE) {
+        Prof pr(ctx, "fuse_finalize", st);
+        launch_fuse_finalize(n, D, num, den, out, (flags & FHGS_FUSE_NORMALIZE) != 0, st);
+    }
     FHGS_CUDA(ctx, cudaGetLastError());
     return FHGS_OK;
 }

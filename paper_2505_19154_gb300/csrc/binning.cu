@@ -321,6 +321,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t *a, long lo
 // ------------------------------------------------------------- scatter
 constexpr int kScatterWarps = 4;
 constexpr int kStage = 128;  // entries staged in shared memory per step
+constexpr int kScatterCtr = 8192;  // tile counters per warp at most: 143 KB per block
 
 // One warp per (segment, camera, band of tile rows): walks the segment's
 // Gaussians in depth order and writes each one into every tile of its
@@ -482,7 +483,8 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
     int max_cells = 0;
     for (int c = 0; c < n_cams; ++c) max_cells = max(max_cells, (cs.c[c].tiles_x + 1) * (cs.c[c].tiles_y + 1));
     const int count_smem = max_cells * (int)sizeof(int);
-    cudaFuncSetAttribute(k_seg_count, cudaFuncAttributeMaxDynamicSharedMemorySize, count_smem);
+    static std::atomic<unsigned long long> count_done{0};
+    allow_max_smem(count_done, k_seg_count);
     note_launch(1);
     k_seg_count<<<dim3(S, n_cams), 256, count_smem, st>>>(order, pv, N, SEG, S, cs, sc.table);
     // 3. scan of the (tile, segment) table: segment offsets and the total
@@ -506,11 +508,13 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
     const long long want = 32ll * sc.sm_count;  // warps
     int nband = (int)min((long long)max_ty, (want + (long long)S * n_cams - 1) / ((long long)S * n_cams));
     nband = max(nband, 1);
-    const int band_rows = (max_ty + nband - 1) / nband;
+    // at most kScatterCtr counters per warp (tiles_x <= 4096 keeps one row)
+    const int band_rows = max(1, min((max_ty + nband - 1) / nband, kScatterCtr / max(max_tx, 1)));
     nband = (max_ty + band_rows - 1) / band_rows;
     const int ctr_words = (band_rows * max_tx + 3) & ~3;
     const int scat_smem = kScatterWarps * (ctr_words + kStage * 6) * (int)sizeof(uint32_t);
-    cudaFuncSetAttribute(k_seg_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, scat_smem);
+    static std::atomic<unsigned long long> scatter_done{0};
+    allow_max_smem(scatter_done, k_seg_scatter);
     note_launch(1);
     const long long items = (long long)S * nband;
     k_seg_scatter<<<dim3((unsigned)((items + kScatterWarps - 1) / kScatterWarps), n_cams), kScatterWarps * 32,

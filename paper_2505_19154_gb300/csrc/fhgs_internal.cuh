@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "fhgs.h"
 
 namespace fhgs {
@@ -49,6 +51,12 @@ struct __align__(16) GRec {
     float4 a, b, c;
 };
 
+// Largest tile grid of one camera: the per-segment count kernel keeps
+// (tiles_x + 1) * (tiles_y + 1) ints in shared memory (224 KB), and the
+// scatter keeps at least one row of tile counters per warp.
+constexpr long long FHGS_MAX_TILE_CELLS = 57344;
+constexpr int FHGS_MAX_TILES_X = 4096;
+
 // Layout of the caller's projection buffer (fhgs_proj_bytes).
 struct ProjView {
     GRec *rec;        // [C*N]
@@ -58,6 +66,23 @@ struct ProjView {
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Lets `kernel` take up to the device's opt-in dynamic shared memory.  The
+// attribute is per-device state, so it is set once per device for each call
+// site (`done` holds one bit per device): the launches after the first then
+// make no runtime call but the launch itself, which keeps them legal inside
+// a stream capture.
+template <typename K>
+inline void allow_max_smem(std::atomic<unsigned long long> &done, K kernel) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) == cudaSuccess)
+        done.fetch_or(bit, std::memory_order_acq_rel);
+}
 
 inline size_t proj_bytes(long long cn) {
     return align_up(sizeof(GRec) * cn, 256) + align_up(sizeof(int4) * cn, 256) +

@@ -910,11 +910,6 @@ int pick_bwd_dn(int D, int d_split) {
     return 0;
 }
 
-template <typename K>
-void set_smem(K kernel, int bytes) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
 }  // namespace
 
 int tc_supported(int D, int d_split) {
@@ -929,7 +924,8 @@ void launch_render_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
     note_launch(1);
 #define FHGS_FWD(DNV)                                                                                     \
     case DNV: {                                                                                           \
-        set_smem(k_render_fwd_tc<DNV>, FwdCfg<DNV>::kSmem);                                              \
+        static std::atomic<unsigned long long> smem_done{0};                                            \
+        allow_max_smem(smem_done, k_render_fwd_tc<DNV>);                                                \
         k_render_fwd_tc<DNV><<<grid, 256, FwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, feats, D, \
                                                                    rgb, feat, T, last, status);          \
         break;                                                                                            \
@@ -953,7 +949,8 @@ void launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
     note_launch(1);
 #define FHGS_BWD(DNV)                                                                                          \
     case DNV: {                                                                                                \
-        set_smem(k_render_bwd_tc<DNV>, BwdCfg<DNV>::kSmem);                                                   \
+        static std::atomic<unsigned long long> smem_done{0};                                                 \
+        allow_max_smem(smem_done, k_render_bwd_tc<DNV>);                                                     \
         k_render_bwd_tc<DNV><<<grid, 256, BwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, feats, D, T, \
                                                                    last, grgb, gfeat, g2d, gfeatures, status);  \
         break;                                                                                                 \

@@ -136,6 +136,12 @@ def config4(seed: int = 0, n: int = 500_000, D: int = 256):
     return scene, config4_cameras(seed)
 
 
+def config5(seed: int = 0, n: int = 3_000_000):
+    """3M Gaussians (config-2 distributions, SH degree 3) and the 64 views of
+    the fusion workload."""
+    return make_scene(n, seed, "normal", sh_degree=3), config5_views(seed)
+
+
 def config5_views(seed: int = 0, n_views: int = 64, width: int = 1280, height: int = 720):
     g = rng(seed, 5)
     return [look_at_camera(ring_position(4.0, i * 360.0 / n_views, float(g.uniform(-30.0, 30.0))),
@@ -145,21 +151,15 @@ def config5_views(seed: int = 0, n_views: int = 64, width: int = 1280, height: i
 def smooth_feature_map(seed: int, view: int, height: int, width: int, D: int,
                        sigma: float = 8.0) -> np.ndarray:
     """N(0,1) noise, separable Gaussian blur (sigma px, radius 3 sigma,
-    reflected border), then L2-normalised per pixel.  (H, W, D) float32."""
+    reflected border without repeating the edge sample), then L2-normalised
+    per pixel.  (H, W, D) float32."""
+    from scipy import ndimage
     g = rng(seed, 1000 + view)
     x = g.standard_normal((height, width, D), dtype=np.float32)
     r = int(math.ceil(3 * sigma))
     k = np.exp(-0.5 * (np.arange(-r, r + 1) / sigma) ** 2)
     k = (k / k.sum()).astype(np.float32)
     for axis in (0, 1):
-        pad = [(0, 0)] * 3
-        pad[axis] = (r, r)
-        xp = np.pad(x, pad, mode="reflect")
-        acc = np.zeros_like(x)
-        for i, kv in enumerate(k):
-            sl = [slice(None)] * 3
-            sl[axis] = slice(i, i + x.shape[axis])
-            acc += kv * xp[tuple(sl)]
-        x = acc
+        x = ndimage.correlate1d(x, k, axis=axis, mode="mirror")
     x /= np.maximum(np.linalg.norm(x, axis=-1, keepdims=True), 1e-12)
     return x.astype(np.float32)

@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 import oracle
+from paper_2505_19154_gb300 import synth
 from tests.helpers import axis_camera, scene_from, small_random_scene
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -304,3 +305,58 @@ def test_rotated_anisotropic_profile_closed_form():
         np.testing.assert_allclose(out["feat"][32 + dy, 32 + dx, 0], a, atol=1e-13, err_msg=str((dx, dy)))
     # the two diagonals really differ (the off-diagonal term matters)
     assert abs(out["feat"][35, 35, 0] - out["feat"][29, 35, 0]) > 0.05
+
+
+def test_fusion_flip_bound_covers_threshold_perturbations():
+    """The fusion margin diagnostic (wflip) bounds the weight any flipped
+    near-threshold decision moves: moving alpha_min, the q^2 cutoff or t_eps
+    by 0.5 % flips exactly the decisions within 0.5 % of their threshold, and
+    every Gaussian's change of sum w (and of sum w F, unit-norm F) stays
+    within its wflip computed with a 1 % tolerance."""
+    sc = small_random_scene(500, seed=61, sh_degree=0, D=0, spread=0.45)
+    views = [synth.look_at_camera(synth.ring_position(2.2, a, e), 48, 40) for a, e in [(10, 5), (150, -20)]]
+    g = np.random.default_rng(9)
+    maps = []
+    for v in views:
+        m = g.normal(size=(v["height"], v["width"], 4))
+        maps.append(m / np.linalg.norm(m, axis=-1, keepdims=True))
+    base = dict(sh_degree=0)
+    prep = oracle.prepare(sc, views, base)
+    ref = oracle.fuse(sc, views, maps, base, prep=prep, margin_tol=1e-2)
+    assert (ref["den"] > 0).sum() > 100
+    moved = 0
+    for key in ("alpha_min", "cutoff_sq", "t_eps"):
+        for f in (1.0 - 5e-3, 1.0 + 5e-3):
+            prm = dict(base, **{key: oracle.DEFAULT_PARAMS[key] * f})
+            alt = oracle.fuse(sc, views, maps, prm, prep=prep, margin_tol=0.0)
+            d_den = np.abs(alt["den"] - ref["den"])
+            d_num = np.linalg.norm(alt["num"] - ref["num"], axis=1)
+            assert np.all(d_den <= ref["wflip"] * (1 + 1e-9) + 1e-15), (key, f)
+            assert np.all(d_num <= ref["wflip"] * (1 + 1e-9) + 1e-15), (key, f)
+            moved += int((d_den > 1e-12).sum())
+    assert moved > 10  # the perturbations do flip decisions
+    assert np.all(oracle.fuse(sc, views, maps, base, prep=prep, margin_tol=0.0)["wflip"] == 0.0)
+
+
+def test_fp32_geometry_option_changes_only_the_footprint():
+    """prepare(geometry="fp32") composites over the FP32 specification's mean
+    and conic: same lists, records equal to the specification's values,
+    images within FP32 rounding of the FP64-geometry render."""
+    sc = small_random_scene(300, seed=71, sh_degree=1, D=3, spread=0.5)
+    cam = synth.look_at_camera(synth.ring_position(2.5, 30, 10), 40, 32)
+    prm = dict(sh_degree=1)
+    p64 = oracle.prepare(sc, [cam], prm)
+    p32 = oracle.prepare(sc, [cam], prm, geometry="fp32")
+    np.testing.assert_array_equal(p64["lists"]["gids"], p32["lists"]["gids"])
+    ok = p32["bins"][0]["ntiles"] > 0
+    np.testing.assert_array_equal(p32["recs"][0][ok][:, :5], p32["bins"][0]["fp"][ok][:, :5].astype(np.float64))
+    r32, r64 = p32["recs"][0][ok], p64["recs"][0][ok]
+    assert np.abs(r32[:, :2] - r64[:, :2]).max() < 1e-3  # mean, pixels
+    scale = np.maximum(np.abs(r64[:, 2]), np.abs(r64[:, 4]))[:, None]
+    assert (np.abs(r32[:, 2:5] - r64[:, 2:5]) / scale).max() < 1e-4  # conic, relative to its size
+    a = oracle.forward(sc, [cam], prm, sc["features"], prep=p64)[0]
+    b = oracle.forward(sc, [cam], prm, sc["features"], prep=p32)[0]
+    ok_px = (a["margin"] > 1e-4) & (b["margin"] > 1e-4)
+    assert np.abs(a["rgb"] - b["rgb"])[ok_px].max() < 1e-4
+    with pytest.raises(ValueError):
+        oracle.prepare(sc, [cam], prm, geometry="fp16")
