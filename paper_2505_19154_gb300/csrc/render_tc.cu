@@ -152,7 +152,23 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, bool v
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(valid ? 16 : 0)
                  : "memory");
 }
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void *g, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(saddr), "l"(g), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Bulk copy (TMA engine) of `bytes` from shared to global memory; both
+// addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_s2g(void *g, uint32_t saddr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g), "r"(saddr), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Byte offset of 16-byte chunk `c` (0..7) of row `r` inside a 128B-swizzled
@@ -173,20 +189,35 @@ constexpr int kFB = 64;  // Gaussians per forward batch (MMA K)
 
 // 256 threads: two groups of 4 warps share the half tile's 128 pixels; group g
 // weighs Gaussians [32 g, 32 g + 32) of each batch.  Both groups evaluate
-// their alphas at once; group 0 then runs the transmittance chain over its 32
-// and hands (T, done, last) to group 1 through shared memory.
+// their alphas and the running products of (1 - alpha) over their own 32 at
+// once; after one exchange of group 0's product each group knows the
+// transmittance entering its Gaussians (T decreases along the list, so group
+// 0 stops inside the batch exactly when T_in P_0 < t_eps), and both
+// finalise their weights in parallel.
+//
+// Loads run ahead of use: the ids of batch b+2, the records of batch b+1 and
+// (once the MMA of batch b-1 has freed its stage) the feature rows of batch
+// b+1 are in flight while batch b is weighed.
 template <int DN>
 struct FwdCfg {
     static constexpr int kWBytes = 128 * 128;            // 128 px x 64 BF16 weights
     static constexpr int kFBytes = kFB * DN * 2;         // 64 rows x DN BF16 features
     static constexpr int kNSub = DN > 256 ? DN / 256 : 1;
     static constexpr int kMmaN = DN > 256 ? 256 : DN;
-    static constexpr int kRecBytes = kFB * 48 + kFB * 4;
+    static constexpr int kRecBytes = kFB * 48;
     static constexpr int kOffF = 2 * kWBytes;
     static constexpr int kOffRec = kOffF + 2 * kFBytes;
-    static constexpr int kOffX = kOffRec + 2 * kRecBytes;   // per-pixel exchange: T, done, last, rgb
-    static constexpr int kOffBar = kOffX + 128 * 24;
+    static constexpr int kOffGid = kOffRec + 2 * kRecBytes;  // [3][64] Gaussian ids
+    static constexpr int kOffX = kOffGid + 3 * kFB * 4;      // per-pixel exchange, 8 words per pixel
+    static constexpr int kOffBar = kOffX + 128 * 8 * 4;
     static constexpr int kSmem = 1024 + kOffBar + 64;
+    // epilogue: the accumulator leaves through shared memory in passes of
+    // kCH columns, one padded row per pixel (16 B of padding keeps the
+    // lane-per-pixel writes free of bank conflicts), then one bulk copy per
+    // pixel and pass; the staging reuses the weight and feature stages
+    static constexpr int kCH = DN == 512 ? 256 : (DN == 64 ? 64 : DN / 2);
+    static constexpr int kStageRow = (kCH + 4) * 4;
+    static_assert(128 * kStageRow <= kOffRec, "epilogue staging must fit in the weight and feature stages");
 };
 
 template <int DN>
@@ -197,17 +228,17 @@ __global__ void __launch_bounds__(256, 1)
     using C = FwdCfg<DN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
-    uint8_t *sW = sm;                                   // [2][128 rows][128 B]
-    float *xT = reinterpret_cast<float *>(sm + C::kOffX);        // [128]
+    uint8_t *sW = sm;                                            // [2][128 rows][128 B]
+    float *xT = reinterpret_cast<float *>(sm + C::kOffX);        // [128] T entering the next batch
     int *xDone = reinterpret_cast<int *>(xT + 128);               // [128]
     int *xLast = xDone + 128;                                     // [128]
-    float *xRgb = reinterpret_cast<float *>(xLast + 128);        // [128][3]
+    float *xP0 = reinterpret_cast<float *>(xLast + 128);         // [128] group 0's product of (1 - alpha)
+    int *xL0 = reinterpret_cast<int *>(xP0 + 128);                // [128] group 0's last alpha > 0, or -1
+    float *xRgb = reinterpret_cast<float *>(xL0 + 128);          // [128][3]
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + C::kOffBar);  // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
-    auto srec = [&](int stg) { return reinterpret_cast<GRec *>(sm + C::kOffRec + stg * C::kRecBytes); };
-    auto sgid = [&](int stg) {
-        return reinterpret_cast<uint32_t *>(sm + C::kOffRec + stg * C::kRecBytes + kFB * 48);
-    };
+    auto srec = [&](int b) { return reinterpret_cast<GRec *>(sm + C::kOffRec + (b & 1) * C::kRecBytes); };
+    auto sgid = [&](int b) { return reinterpret_cast<uint32_t *>(sm + C::kOffGid + (b % 3) * kFB * 4); };
 
     const int tid = threadIdx.x, warp = tid >> 5, grp = tid >> 7, pidx = tid & 127;
     const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, chunk = blockIdx.y;
@@ -219,6 +250,7 @@ __global__ void __launch_bounds__(256, 1)
     const bool inside = px < cam.W && py < cam.H;
     const long long pix = cam.pix_off + (long long)py * cam.W + px;
     const uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+    const int nbatches = (int)((e - s + kFB - 1) / kFB);
     const int d0 = chunk * DN;
     const GRec *rec = pv.rec + (long long)ci * N;
 
@@ -236,31 +268,39 @@ __global__ void __launch_bounds__(256, 1)
     const uint32_t sW_s = smem_u32(sW), sF_s = smem_u32(sm + C::kOffF);
     constexpr uint32_t idesc = idesc_bf16(128, C::kMmaN, false, true);
 
-    auto load_rec = [&](uint32_t base, int stg) {  // group A: Gaussian ids + records
-        const int nb = (int)min((uint32_t)kFB, e - base);
-        if (tid < kFB) sgid(stg)[tid] = tid < nb ? __ldg(gids + base + tid) : 0u;
-        if (tid < nb) {
-            const uint32_t gid = sgid(stg)[tid];
-            const uint32_t dst = smem_u32(srec(stg) + tid);
-            const GRec *src = rec + gid;
-            cp_async16(dst, &src->a, true);
-            cp_async16(dst + 16, &src->b, true);
-            cp_async16(dst + 32, &src->c, true);
+    // Every load helper commits exactly one cp.async group in every thread,
+    // empty or not, so that the wait_group counts below hold.
+    auto load_gid = [&](int b) {  // ids of batch b
+        if (b < nbatches && tid < kFB) {
+            const uint32_t at = s + (uint32_t)b * kFB + tid;
+            cp_async4(smem_u32(sgid(b) + tid), gids + (at < e ? at : s), at < e);
         }
         cp_async_commit();
     };
-    auto load_feat = [&](uint32_t base, int stg) {  // group B: feature rows, zero-filled past the end
-        // reads the ids that load_rec stored for this stage (a barrier lies between)
-        const int nb = (int)min((uint32_t)kFB, e - base);
-        constexpr int kCPR = DN / 8;
-        const uint32_t fb = sF_s + stg * C::kFBytes;
-        const uint32_t *ids = sgid(stg);
+    auto load_rec = [&](int b) {  // records of batch b (its ids are in shared memory)
+        if (b < nbatches && tid < kFB) {
+            const bool v = s + (uint32_t)b * kFB + tid < e;
+            const uint32_t dst = smem_u32(srec(b) + tid);
+            const GRec *src = rec + (v ? sgid(b)[tid] : 0u);
+            cp_async16(dst, &src->a, v);
+            cp_async16(dst + 16, &src->b, v);
+            cp_async16(dst + 32, &src->c, v);
+        }
+        cp_async_commit();
+    };
+    auto load_feat = [&](int b) {  // feature rows of batch b, zero-filled past the end
+        if (b < nbatches) {
+            const int nb = (int)min((uint32_t)kFB, e - (s + (uint32_t)b * kFB));
+            constexpr int kCPR = DN / 8;
+            const uint32_t fb = sF_s + (b & 1) * C::kFBytes;
+            const uint32_t *ids = sgid(b);
 #pragma unroll 4
-        for (int q = tid; q < kFB * kCPR; q += 256) {
-            const int g = q / kCPR, c = q - g * kCPR;
-            const bool valid = g < nb;
-            const uint32_t gid = ids[g];
-            cp_async16(fb + (c >> 3) * (kFB * 128) + swz(g, c & 7), feats + (size_t)gid * D + d0 + c * 8, valid);
+            for (int q = tid; q < kFB * kCPR; q += 256) {
+                const int g = q / kCPR, c = q - g * kCPR;
+                const bool valid = g < nb;
+                cp_async16(fb + (c >> 3) * (kFB * 128) + swz(g, c & 7),
+                           feats + (size_t)(valid ? ids[g] : 0u) * D + d0 + c * 8, valid);
+            }
         }
         cp_async_commit();
     };
@@ -275,20 +315,31 @@ __global__ void __launch_bounds__(256, 1)
     uint32_t ph[2] = {0u, 0u};
     int nbatch = 0;
     bool timeout = false;
-    if (s < e) load_rec(s, 0);
+    // prologue: ids of batches 0 and 1; records and features of batch 0
+    load_gid(0);
+    load_gid(1);
+    cp_async_wait<1>();
     __syncthreads();
-    if (s < e) load_feat(s, 0);
-    for (uint32_t base = s; base < e; base += kFB) {
-        const int stg = nbatch & 1;
+    load_rec(0);
+    load_feat(0);
+    for (int b = 0; b < nbatches; ++b) {
+        const int stg = b & 1;
+        const uint32_t base = s + (uint32_t)b * kFB;
         const int nb = (int)min((uint32_t)kFB, e - base);
-        const bool more = base + kFB < e;
-        if (more) load_rec(base + kFB, stg ^ 1);
-        else cp_async_commit();
-        asm volatile("cp.async.wait_group 2;" ::: "memory");  // this batch's records
+        // the newest groups are [ids b+1, records b, features b]: all but the
+        // last have landed after this wait
+        cp_async_wait<1>();
         __syncthreads();
-        // alphas of this group's 32 Gaussians (no dependence on T)
-        const GRec *R = srec(stg);
-        float a[32];
+        load_gid(b + 2);
+        load_rec(b + 1);
+        const float T_in = xT[pidx];
+        const bool done_in = xDone[pidx] != 0;
+        const int last_in = xLast[pidx];
+        // alphas of this group's 32 Gaussians and the running product of (1 - alpha)
+        const GRec *R = srec(b);
+        float a[32], l[32];
+        float P = 1.f;
+        int lastc = -1;
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
             const int j = grp * 32 + jj;
@@ -297,65 +348,83 @@ __global__ void __launch_bounds__(256, 1)
             const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
             const float al = fminf(p.amax, B4.y * __expf(-0.5f * q2));
             a[jj] = (j < nb && q2 <= p.cut && al >= p.amin) ? al : 0.f;
+            l[jj] = P;
+            P *= 1.f - a[jj];
+            lastc = a[jj] > 0.f ? jj : lastc;
         }
-        // transmittance chain: group 0 first, then group 1 from group 0's state
+        if (grp == 0) {
+            xP0[pidx] = P;
+            xL0[pidx] = lastc;
+        }
+        // the feature stage of batch b+1 is free once the MMA of batch b-1 is done
+        bool ok = true;
+        if (b >= 1) {
+            const int ps = stg ^ 1;
+            ok = mbar_wait(&bar[ps], ph[ps]);
+            if (ok) ph[ps] ^= 1u;
+        }
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+            break;
+        }
+        load_feat(b + 1);
+        // weights: group 1 starts from T_in P_0 unless group 0 stops
+        const float P0 = xP0[pidx];
+        const bool stop0 = !done_in && T_in * P0 < p.teps;
+        const float Ts = grp == 0 ? T_in : T_in * P0;
+        bool done = grp == 0 ? done_in : (done_in || stop0);
+        const bool owner = grp == 0 ? (done_in || stop0) : !(done_in || stop0);
+        float Tstop = 0.f;
+        int lastw = -1;
         uint8_t *wb = sW + stg * C::kWBytes;
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            if (grp == g) {
-                float T = xT[pidx];
-                bool done = xDone[pidx] != 0;
-                int last = xLast[pidx];
+        for (int q = 0; q < 4; ++q) {
+            float w8[8];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float w8[8];
-#pragma unroll
-                    for (int h = 0; h < 8; ++h) {
-                        const int jj = 8 * q + h, j = grp * 32 + jj;
-                        bool ok = a[jj] > 0.f && !done;
-                        const float Tn = T * (1.f - a[jj]);
-                        const bool stop = ok && Tn < p.teps;
-                        done = done || stop;
-                        ok = ok && !stop;
-                        const float w = ok ? a[jj] * T : 0.f;
-                        w8[h] = w;
-                        if (ok) {
-                            const float4 B4 = R[j].b;
-                            cr += w * B4.z;
-                            cg += w * B4.w;
-                            cb += w * R[j].c.x;
-                            T = Tn;
-                            last = (int)(base - s) + j + 1;
-                        }
-                    }
-                    uint4 pk;
-                    pk.x = pack_bf16(w8[0], w8[1]);
-                    pk.y = pack_bf16(w8[2], w8[3]);
-                    pk.z = pack_bf16(w8[4], w8[5]);
-                    pk.w = pack_bf16(w8[6], w8[7]);
-                    *reinterpret_cast<uint4 *>(wb + swz(pidx, grp * 4 + q)) = pk;
+            for (int h = 0; h < 8; ++h) {
+                const int jj = 8 * q + h, j = grp * 32 + jj;
+                const float Tj = Ts * l[jj];
+                const float Tn = Ts * (jj < 31 ? l[jj + 1] : P);
+                bool okj = a[jj] > 0.f && !done;
+                const bool stop = okj && Tn < p.teps;
+                if (stop) Tstop = Tj;
+                done = done || stop;
+                okj = okj && !stop;
+                const float w = okj ? a[jj] * Tj : 0.f;
+                w8[h] = w;
+                if (okj) {
+                    const float4 B4 = R[j].b;
+                    cr += w * B4.z;
+                    cg += w * B4.w;
+                    cb += w * R[j].c.x;
+                    lastw = jj;
                 }
-                xT[pidx] = T;
+            }
+            uint4 pk;
+            pk.x = pack_bf16(w8[0], w8[1]);
+            pk.y = pack_bf16(w8[2], w8[3]);
+            pk.z = pack_bf16(w8[4], w8[5]);
+            pk.w = pack_bf16(w8[6], w8[7]);
+            *reinterpret_cast<uint4 *>(wb + swz(pidx, grp * 4 + q)) = pk;
+        }
+        if (owner) {  // exactly one group carries the pixel's state to the next batch
+            const int pos0 = (int)(base - s);
+            if (grp == 0) {
+                xT[pidx] = done_in ? T_in : Tstop;
+                xDone[pidx] = 1;
+                xLast[pidx] = lastw >= 0 ? pos0 + lastw + 1 : last_in;
+            } else {
+                const int L0 = xL0[pidx];
+                xT[pidx] = done ? Tstop : Ts * P;
                 xDone[pidx] = done ? 1 : 0;
-                xLast[pidx] = last;
-            }
-            __syncthreads();
-        }
-        // the feature stage of batch k+1 is free once the MMA of batch k-1 is done
-        if (nbatch >= 1) {
-            const int ps = stg ^ 1;
-            const bool ok = mbar_wait(&bar[ps], ph[ps]);
-            ph[ps] ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                timeout = true;
-                break;
+                xLast[pidx] = lastw >= 0 ? pos0 + 32 + lastw + 1 : (L0 >= 0 ? pos0 + L0 + 1 : last_in);
             }
         }
-        if (more) load_feat(base + kFB, stg ^ 1);
-        else cp_async_commit();
-        asm volatile("cp.async.wait_group 2;" ::: "memory");  // this batch's features
+        // the newest groups are [ids b+2, records b+1, features b+1]: this
+        // batch's features have landed after this wait
+        cp_async_wait<3>();
         fence_async_smem();
-        const int all_done = __syncthreads_and(xDone[pidx] != 0);
+        const int all_done = __syncthreads_and(grp == 0 || done);
         if (tid == 0) {
             tc_after();
             const uint32_t wa = sW_s + stg * C::kWBytes, fb = sF_s + stg * C::kFBytes;
@@ -388,25 +457,38 @@ __global__ void __launch_bounds__(256, 1)
         }
     } else {
         tc_after();
-        // 8 warps drain the accumulator: warp w reads lanes 32 (w % 4).., columns
-        // [(w / 4) DN/2, (w / 4 + 1) DN/2)
-        const int cbase = grp * (DN / 2);
-        float *fo = feat + pix * D + d0 + cbase;
+        // accumulator -> padded rows in shared memory -> one bulk copy per
+        // pixel and pass.  Warp w reads TMEM lanes 32 (w % 4).. (pixels) and
+        // half of the pass's columns.
+        constexpr int kCH = C::kCH;
+        const int row = (warp & 3) * 32 + (tid & 31);
+        const uint32_t stage_s = smem_u32(sm);
 #pragma unroll 1
-        for (int cc = 0; cc < DN / 64; ++cc) {
-            float v[32];
-            if (nbatch > 0) {
-                tmem_ld32(taddr + ((uint32_t)((warp & 3) * 32) << 16) + cbase + cc * 32, v);
-            } else {
+        for (int pass = 0; pass < DN / kCH; ++pass) {
+#pragma unroll 1
+            for (int k = 0; k < kCH / 64; ++k) {
+                const int c = grp * (kCH / 2) + k * 32;
+                float v[32];
+                if (nbatch > 0) {
+                    tmem_ld32(taddr + ((uint32_t)((warp & 3) * 32) << 16) + pass * kCH + c, v);
+                } else {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = 0.f;
-            }
-            if (inside) {
-                float4 *d4 = reinterpret_cast<float4 *>(fo + cc * 32);
+                    for (int i = 0; i < 32; ++i) v[i] = 0.f;
+                }
+                float4 *dst = reinterpret_cast<float4 *>(sm + row * C::kStageRow + c * 4);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             }
+            fence_async_smem();
+            __syncthreads();
+            if (tid < 128) {  // thread t owns pixel t
+                if (inside) bulk_s2g(feat + pix * D + d0 + pass * kCH, stage_s + tid * C::kStageRow, kCH * 4);
+                bulk_commit();
+                bulk_wait_read_all();
+            }
+            __syncthreads();
         }
+        if (tid < 128) bulk_wait_all();
         if (chunk == 0) {
             if (grp == 1) {
                 xRgb[3 * pidx] = cr;
