@@ -527,15 +527,6 @@ __device__ __forceinline__ void rs_step(float *v, int lane, int off) {
     }
 }
 
-// Warp sums of 4 per-lane values: lane l returns the total of value (l >> 3) & 3.
-__device__ __forceinline__ float warp_rs4(float *v, int lane) {
-    rs_step<2>(v, lane, 16);
-    rs_step<1>(v, lane, 8);
-    float r = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 4);
-    r += __shfl_xor_sync(0xffffffffu, r, 2);
-    return r + __shfl_xor_sync(0xffffffffu, r, 1);
-}
-
 // Shared-memory plan of the backward CTA (byte offsets; atoms 1024-aligned):
 //   W   [128 px][64 g] BF16 weights            (A of dFe, MN-major; A of nothing else)
 //   Dh  [DN/64][128 px][64] BF16 dF hi           (A of G, K-major; B of dFe, MN-major)
@@ -591,7 +582,7 @@ __global__ void __launch_bounds__(256, 1)
     uint8_t *sTl = sm + C::kOffTl;
     uint8_t *sX = sm + C::kOffX;
     float *sRgb = reinterpret_cast<float *>(sm + C::kOffRgb);  // [64][3]
-    int *sFlag = reinterpret_cast<int *>(sm + C::kOffFlag);    // [64]
+    uint32_t *sMask = reinterpret_cast<uint32_t *>(sm + C::kOffFlag);  // [2] contributors of each group
     float *xP1 = reinterpret_cast<float *>(sm + C::kOffXch);  // [128] group 1's prod (1 - alpha)
     float *xS1 = xP1 + 128;                                    // [128] group 1's sum w g
     float *xT = xS1 + 128;                                     // [128] T after the batch
@@ -627,20 +618,16 @@ __global__ void __launch_bounds__(256, 1)
         fence_mbar_init();
         *smax = 0;
     }
-    if (tid < kBB) {
-        sFlag[tid] = 0;
-        sRgb[3 * tid] = sRgb[3 * tid + 1] = sRgb[3 * tid + 2] = 0.f;
-    }
+    if (tid < kBB) sRgb[3 * tid] = sRgb[3 * tid + 1] = sRgb[3 * tid + 2] = 0.f;
+    if (tid < 2) sMask[tid] = 0u;
     float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
     int lastp = 0;
     if (inside) {
         T = Tfin[pix];
         lastp = lastv[pix];
-        if (chunk == 0) {
-            dC0 = grgb[3 * pix];
-            dC1 = grgb[3 * pix + 1];
-            dC2 = grgb[3 * pix + 2];
-        }
+        dC0 = grgb[3 * pix];
+        dC1 = grgb[3 * pix + 1];
+        dC2 = grgb[3 * pix + 2];
     }
     tc_before();
     __syncthreads();
@@ -703,11 +690,9 @@ __global__ void __launch_bounds__(256, 1)
             const uint64_t bx = sdesc(sX_s + (ks >> 2) * (16 * 128) + (ks & 3) * 32, 16, 1024);
             mma_bf16(tM, am, bx, idM, ks > 0 ? 1u : 0u);
             mma_bf16(tM, al, bx, idM, 1u);
-            if (want_fg) {
-                const uint64_t aw = sdesc(sW_s + ks * 2048, 128 * 128, 1024);
-                mma_bf16(tF, aw, sdesc(sDh_s + ks * 2048, 128 * 128, 1024), idF, ks > 0 ? 1u : 0u);
-                mma_bf16(tF, aw, sdesc(sDl_s + ks * 2048, 128 * 128, 1024), idF, 1u);
-            }
+            if (want_fg)  // the feature gradient takes dF as BF16 (its bar is the BF16 weights')
+                mma_bf16(tF, sdesc(sW_s + ks * 2048, 128 * 128, 1024), sdesc(sDh_s + ks * 2048, 128 * 128, 1024), idF,
+                         ks > 0 ? 1u : 0u);
         }
         mma_commit(&bars[1]);
     };
@@ -779,7 +764,10 @@ __global__ void __launch_bounds__(256, 1)
     }
 
     const float fpx = px + 0.5f, fpy = py + 0.5f;
-    float S = T * (dC0 * p.bg0 + dC1 * p.bg1 + dC2 * p.bg2);
+    // the colour part of dL/dw (and the background term) belongs to slice 0
+    // only; every slice sums its own colour channels for the colour gradients
+    const float rC0 = chunk == 0 ? dC0 : 0.f, rC1 = chunk == 0 ? dC1 : 0.f, rC2 = chunk == 0 ? dC2 : 0.f;
+    float S = T * (rC0 * p.bg0 + rC1 * p.bg1 + rC2 * p.bg2);
     for (int b = 0; b < nbat; ++b) {
         const int stg = b & 1;
         const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
@@ -841,7 +829,7 @@ __global__ void __launch_bounds__(256, 1)
             const bool c = al[jj] > 0.f;
             const float w = al[jj] * Tj[jj];
             const float4 B4 = R[j].b;
-            const float g = c ? Gv[jj] + dC0 * B4.z + dC1 * B4.w + dC2 * R[j].c.x : 0.f;
+            const float g = c ? Gv[jj] + rC0 * B4.z + rC1 * B4.w + rC2 * R[j].c.x : 0.f;
             const float dal = Tj[jj] * g - __fdividef(Sg, 1.f - al[jj]);
             Sg = c ? Sg + w * g : Sg;
             Gv[jj] = c ? gx[jj] * dal : 0.f;
@@ -876,19 +864,29 @@ __global__ void __launch_bounds__(256, 1)
             *reinterpret_cast<uint4 *>(sTh + off) = ph;
             *reinterpret_cast<uint4 *>(sTl + off) = pl;
         }
-        // which Gaussians contribute anywhere in the CTA; RGB sums (slice 0)
+        // which Gaussians contribute anywhere in the CTA: one OR per warp
+        uint32_t cmask = 0;
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-            const bool c = al[jj] > 0.f;
-            if (!__any_sync(0xffffffffu, c)) continue;
-            const int j = grp * 32 + jj;
-            if (lane == 0) sFlag[j] = 1;
-            if (chunk == 0) {
-                const float w = al[jj] * Tj[jj];
-                float v[4] = {w * dC0, w * dC1, w * dC2, 0.f};
-                const float r = warp_rs4(v, lane);
-                const int k = (lane >> 3) & 3;
-                if ((lane & 7) == 0 && k < 3) atomicAdd(&sRgb[3 * j + k], r);
+        for (int jj = 0; jj < 32; ++jj) cmask |= (al[jj] > 0.f ? 1u : 0u) << jj;
+        cmask = __reduce_or_sync(0xffffffffu, cmask);
+        if (lane == 0 && cmask) atomicOr(&sMask[grp], cmask);
+        // colour sums sum_p w dC_p per Gaussian; channel c is summed by slice
+        // c % (number of slices).  A reduce-scatter over the warp's 32 pixels
+        // leaves lane l with the warp's sum for Gaussian 32 grp + l.
+        if (cmask) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (c % (int)gridDim.y != chunk) continue;
+                const float dc = c == 0 ? dC0 : (c == 1 ? dC1 : dC2);
+                float v[32];
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) v[jj] = al[jj] * Tj[jj] * dc;
+                rs_step<16>(v, lane, 16);
+                rs_step<8>(v, lane, 8);
+                rs_step<4>(v, lane, 4);
+                rs_step<2>(v, lane, 2);
+                rs_step<1>(v, lane, 1);
+                if (cmask & (1u << lane)) atomicAdd(&sRgb[3 * (grp * 32 + lane) + c], v[0]);
             }
         }
         cp_async_wait_all();  // batch b+1's records and features have landed
@@ -918,7 +916,9 @@ __global__ void __launch_bounds__(256, 1)
         tc_after();
         if ((warp & 3) < 2) {  // rows 0..63 of the accumulators = the batch's Gaussians
             const int j = (warp & 1) * 32 + lane;
-            const bool mine = j < nb && sFlag[j] != 0;
+            const uint32_t wmask = sMask[warp & 1] & (nb >= (warp & 1) * 32 + 32 ? 0xFFFFFFFFu
+                                   : (nb > (warp & 1) * 32 ? (1u << (nb - (warp & 1) * 32)) - 1u : 0u));
+            const bool mine = (wmask >> lane) & 1u;
             const uint32_t gid = sgid(stg)[j];
             const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
             if (grp == 0) {
@@ -937,33 +937,47 @@ __global__ void __launch_bounds__(256, 1)
                     float4 *dst = reinterpret_cast<float4 *>(g2dc + 12 * (long long)gid);
                     atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy),
                                                -0.5f * op * Sxx, -op * Sxy));
+                    const int nch = (int)gridDim.y;
                     atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, chunk == 0 ? sRgb[3 * j] : 0.f,
-                                                   chunk == 0 ? sRgb[3 * j + 1] : 0.f));
-                    if (chunk == 0) atomicAdd(g2dc + 12 * (long long)gid + 8, sRgb[3 * j + 2]);
+                                                   chunk == 1 % nch ? sRgb[3 * j + 1] : 0.f));
+                    if (chunk == 2 % nch) atomicAdd(g2dc + 12 * (long long)gid + 8, sRgb[3 * j + 2]);
                 }
             }
-            if (want_fg) {  // group g drains columns [g DN/2, (g+1) DN/2)
-                float *dst = gfeatures + (size_t)gid * D + d0 + grp * (DN / 2);
+            if (want_fg && wmask) {
+                // group g drains columns [g DN/2, (g+1) DN/2) in 32-column blocks,
+                // transposed through shared memory (the weight-t buffers are free
+                // once the MMAs that read them are done): each atomic then covers
+                // 128 contiguous bytes of one Gaussian's row
+                float *stage = reinterpret_cast<float *>(sTh) + ((warp & 1) + 2 * grp) * (32 * 36);
+                const int sub = lane >> 3, q4 = (lane & 7) * 4;
 #pragma unroll 1
                 for (int cc = 0; cc < DN / 64; ++cc) {
                     float v[32];
                     tmem_ld32(tF + lanes + grp * (DN / 2) + cc * 32, v);
-                    if (mine) {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            atomicAdd(reinterpret_cast<float4 *>(dst + cc * 32) + i,
-                                      make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
+                    for (int i = 0; i < 8; ++i)
+                        *reinterpret_cast<float4 *>(stage + lane * 36 + 4 * i) =
+                            make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    __syncwarp();
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int jj = it * 4 + sub;
+                        if ((wmask >> jj) & 1u) {
+                            const uint32_t g = sgid(stg)[(warp & 1) * 32 + jj];
+                            atomicAdd(reinterpret_cast<float4 *>(gfeatures + (size_t)g * D + d0 + grp * (DN / 2) +
+                                                                 cc * 32 + q4),
+                                      *reinterpret_cast<const float4 *>(stage + jj * 36 + q4));
+                        }
                     }
+                    __syncwarp();
                 }
             }
         }
         tc_before();
         __syncthreads();
         tc_after();
-        if (tid < kBB) {
-            sFlag[tid] = 0;
-            sRgb[3 * tid] = sRgb[3 * tid + 1] = sRgb[3 * tid + 2] = 0.f;
-        }
+        if (tid < kBB) sRgb[3 * tid] = sRgb[3 * tid + 1] = sRgb[3 * tid + 2] = 0.f;
+        if (tid < 2) sMask[tid] = 0u;
     }
     if (timeout) {
         if (tid == 0) latch(status, ST_TIMEOUT);
