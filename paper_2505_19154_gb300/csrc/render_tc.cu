@@ -549,11 +549,12 @@ struct BwdCfg {
     static constexpr int kOffF = kOffX + 2 * 16 * 128;
     static constexpr int kOffRec = kOffF + kNBlk * kBB * 128;
     static constexpr int kRecBytes = kBB * 48 + kBB * 4;
-    static constexpr int kOffRgb = kOffRec + 2 * kRecBytes;
-    static constexpr int kOffFlag = kOffRgb + kBB * 3 * 4;
-    static constexpr int kOffXch = kOffFlag + kBB * 4;    // per pixel: P1, S1, T, S
+    static constexpr int kOffRgb = kOffRec + 3 * kRecBytes;  // three record stages: b-1 (drain), b, b+1
+    static constexpr int kOffFlag = kOffRgb + 2 * kBB * 3 * 4;  // [2 batches][64][3] colour sums
+    static constexpr int kOffXch = kOffFlag + 16;          // [2 batches][2 groups] masks; then per pixel: P1, S1, T, S
     static constexpr int kOffBar = kOffXch + 128 * 16;
     static constexpr int kSmem = 1024 + kOffBar + 64;
+    static_assert(kSmem <= 232448, "backward CTA exceeds the opt-in shared memory");
     static constexpr int kTmemCols = DN <= 128 ? 256 : 512;
     static constexpr int kColM = 64;                      // moments, 16 columns
     static constexpr int kColF = DN <= 128 ? 128 : 256;   // dFe, DN columns
@@ -581,8 +582,8 @@ __global__ void __launch_bounds__(256, 1)
     uint8_t *sTh = sm + C::kOffTh;
     uint8_t *sTl = sm + C::kOffTl;
     uint8_t *sX = sm + C::kOffX;
-    float *sRgb = reinterpret_cast<float *>(sm + C::kOffRgb);  // [64][3]
-    uint32_t *sMask = reinterpret_cast<uint32_t *>(sm + C::kOffFlag);  // [2] contributors of each group
+    auto sRgb = [&](int b) { return reinterpret_cast<float *>(sm + C::kOffRgb) + (b & 1) * kBB * 3; };
+    auto sMask = [&](int b) { return reinterpret_cast<uint32_t *>(sm + C::kOffFlag) + (b & 1) * 2; };
     float *xP1 = reinterpret_cast<float *>(sm + C::kOffXch);  // [128] group 1's prod (1 - alpha)
     float *xS1 = xP1 + 128;                                    // [128] group 1's sum w g
     float *xT = xS1 + 128;                                     // [128] T after the batch
@@ -611,6 +612,22 @@ __global__ void __launch_bounds__(256, 1)
     float *g2dc = g2d + (long long)ci * N * 12;
     const bool want_fg = gfeatures != nullptr;
 
+    // dF slice of this CTA's pixels, 16 rows per warp, all loads in flight
+    // before anything else (their latency hides the rest of the setup)
+    constexpr int kL = DN >= 128 ? DN / 128 : 1;
+    float4 vdf[16][kL];
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+        const int prow = warp * 16 + rr;
+        const int qx = x0 + (prow & 15), qy = y0 + (prow >> 4);
+        const bool qin = qx < cam.W && qy < cam.H && gfeat != nullptr;
+        const float *src = gfeat + (cam.pix_off + (long long)qy * cam.W + qx) * D + d0;
+#pragma unroll
+        for (int li = 0; li < kL; ++li) {
+            const int f = li * 128 + lane * 4;
+            vdf[rr][li] = (qin && f < DN) ? *reinterpret_cast<const float4 *>(src + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
     if (warp == 0) tmem_alloc(tslot, C::kTmemCols);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -618,8 +635,8 @@ __global__ void __launch_bounds__(256, 1)
         fence_mbar_init();
         *smax = 0;
     }
-    if (tid < kBB) sRgb[3 * tid] = sRgb[3 * tid + 1] = sRgb[3 * tid + 2] = 0.f;
-    if (tid < 2) sMask[tid] = 0u;
+    if (tid < 2 * kBB) sRgb(0)[3 * tid] = sRgb(0)[3 * tid + 1] = sRgb(0)[3 * tid + 2] = 0.f;  // both slots
+    if (tid < 4) sMask(0)[tid] = 0u;
     float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
     int lastp = 0;
     if (inside) {
@@ -646,7 +663,7 @@ __global__ void __launch_bounds__(256, 1)
     constexpr uint32_t idM = idesc_bf16(128, 16, true, false);
 
     // batch b covers list positions [max(0, Lmax - 64 (b+1)), Lmax - 64 b): back to front
-    auto prefetch_rec = [&](int b, int stg) {  // Gaussian ids + records of batch b
+    auto prefetch_rec = [&](int b, int stg) {  // Gaussian ids + records of batch b (stage b % 3)
         const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
         if (tid < kBB) sgid(stg)[tid] = tid < nb ? __ldg(gids + s + bs + tid) : 0u;
         if (tid < nb) {
@@ -711,33 +728,16 @@ __global__ void __launch_bounds__(256, 1)
             *reinterpret_cast<__nv_bfloat16 *>(sX + (pp >> 6) * (16 * 128) + swz(n, (pp & 63) >> 3) +
                                                2 * (pp & 7)) = __float2bfloat16_rn(val);
         }
-        // dF slice of this CTA's pixels -> BF16 hi / lo, K-major swizzled.  Each
-        // warp copies 16 pixel rows with 8 rows of loads in flight.
-        constexpr int kL = DN >= 128 ? DN / 128 : 1;
-#pragma unroll 1
-        for (int r0 = 0; r0 < 16; r0 += 8) {
-            float4 v[8][kL];
+        // dF -> BF16 hi / lo, K-major swizzled
+        {
 #pragma unroll
-            for (int rr = 0; rr < 8; ++rr) {
-                const int prow = warp * 16 + r0 + rr;
-                const int qx = x0 + (prow & 15), qy = y0 + (prow >> 4);
-                const bool qin = qx < cam.W && qy < cam.H && gfeat != nullptr;
-                const float *src = gfeat + (cam.pix_off + (long long)qy * cam.W + qx) * D + d0;
-#pragma unroll
-                for (int li = 0; li < kL; ++li) {
-                    const int f = li * 128 + lane * 4;
-                    v[rr][li] = (qin && f < DN) ? *reinterpret_cast<const float4 *>(src + f)
-                                                : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int rr = 0; rr < 8; ++rr) {
-                const int prow = warp * 16 + r0 + rr;
+            for (int rr = 0; rr < 16; ++rr) {
+                const int prow = warp * 16 + rr;
 #pragma unroll
                 for (int li = 0; li < kL; ++li) {
                     const int f = li * 128 + lane * 4;
                     if (f >= DN) continue;
-                    const float4 x = v[rr][li];
+                    const float4 x = vdf[rr][li];
                     const __nv_bfloat162 h01 = __floats2bfloat162_rn(x.x, x.y);
                     const __nv_bfloat162 h23 = __floats2bfloat162_rn(x.z, x.w);
                     const float2 b01 = __bfloat1622float2(h01), b23 = __bfloat1622float2(h23);
@@ -768,11 +768,77 @@ __global__ void __launch_bounds__(256, 1)
     // only; every slice sums its own colour channels for the colour gradients
     const float rC0 = chunk == 0 ? dC0 : 0.f, rC1 = chunk == 0 ? dC1 : 0.f, rC2 = chunk == 0 ? dC2 : 0.f;
     float S = T * (rC0 * p.bg0 + rC1 * p.bg1 + rC2 * p.bg2);
+    // Batch b's feature-gradient and moment MMAs (FM) run while batch b+1 is
+    // weighed: the drain of batch b (TMEM -> moments, colour sums, feature
+    // gradients) happens in iteration b+1 after its recursion, before its
+    // weights overwrite the MMA operands.  G of batch b+1 is issued ahead of
+    // FM of batch b so that the next iteration's first wait is short.
+    auto drain = [&](int db) {
+        const int dbe = Lmax - db * kBB, dnb = dbe - max(0, dbe - kBB);
+            if ((warp & 3) < 2) {  // rows 0..63 of the accumulators = the batch's Gaussians
+                const int j = (warp & 1) * 32 + lane;
+                const uint32_t wmask = sMask(db)[warp & 1] & (dnb >= (warp & 1) * 32 + 32 ? 0xFFFFFFFFu
+                                       : (dnb > (warp & 1) * 32 ? (1u << (dnb - (warp & 1) * 32)) - 1u : 0u));
+                const bool mine = (wmask >> lane) & 1u;
+                const uint32_t gid = sgid(db % 3)[j];
+                const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+                if (grp == 0) {
+                    float m[16];
+                    tmem_ld16(tM + lanes, m);
+                    if (mine) {
+                        const GRec r = srec(db % 3)[j];
+                        // moments about the pixel grid: dx = i - a, dy = j - b
+                        const float a = r.a.x - (float)x0 - 0.5f, bb = r.a.y - (float)y0 - 0.5f;
+                        const float M0 = m[0], Mi = m[1], Mj = m[2], Mii = m[3], Mij = m[4], Mjj = m[5];
+                        const float Sx = Mi - a * M0, Sy = Mj - bb * M0;
+                        const float Sxx = Mii - 2.f * a * Mi + a * a * M0;
+                        const float Sxy = Mij - a * Mj - bb * Mi + a * bb * M0;
+                        const float Syy = Mjj - 2.f * bb * Mj + bb * bb * M0;
+                        const float op = r.b.y, cA = r.a.z, cB = r.a.w, cC = r.b.x;
+                        float4 *dst = reinterpret_cast<float4 *>(g2dc + 12 * (long long)gid);
+                        atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy),
+                                                   -0.5f * op * Sxx, -op * Sxy));
+                        const int nch = (int)gridDim.y;
+                        atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, chunk == 0 ? sRgb(db)[3 * j] : 0.f,
+                                                       chunk == 1 % nch ? sRgb(db)[3 * j + 1] : 0.f));
+                        if (chunk == 2 % nch) atomicAdd(g2dc + 12 * (long long)gid + 8, sRgb(db)[3 * j + 2]);
+                    }
+                }
+                if (want_fg && wmask) {
+                    // group g drains columns [g DN/2, (g+1) DN/2) in 32-column blocks,
+                    // transposed through shared memory (the weight-t buffers are free
+                    // once the MMAs that read them are done): each atomic then covers
+                    // 128 contiguous bytes of one Gaussian's row
+                    float *stage = reinterpret_cast<float *>(sTh) + ((warp & 1) + 2 * grp) * (32 * 36);
+                    const int sub = lane >> 3, q4 = (lane & 7) * 4;
+#pragma unroll 1
+                    for (int cc = 0; cc < DN / 64; ++cc) {
+                        float v[32];
+                        tmem_ld32(tF + lanes + grp * (DN / 2) + cc * 32, v);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            *reinterpret_cast<float4 *>(stage + lane * 36 + 4 * i) =
+                                make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        __syncwarp();
+#pragma unroll
+                        for (int it = 0; it < 8; ++it) {
+                            const int jj = it * 4 + sub;
+                            if ((wmask >> jj) & 1u) {
+                                const uint32_t g = sgid(db % 3)[(warp & 1) * 32 + jj];
+                                atomicAdd(reinterpret_cast<float4 *>(gfeatures + (size_t)g * D + d0 + grp * (DN / 2) +
+                                                                     cc * 32 + q4),
+                                          *reinterpret_cast<const float4 *>(stage + jj * 36 + q4));
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+    };
     for (int b = 0; b < nbat; ++b) {
-        const int stg = b & 1;
         const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
         const bool more = b + 1 < nbat;
-        if (more) prefetch_rec(b + 1, stg ^ 1);
+        if (more) prefetch_rec(b + 1, (b + 1) % 3);
         {
             const bool ok = mbar_wait(&bars[0], ph0);
             if (ok) {
@@ -786,8 +852,8 @@ __global__ void __launch_bounds__(256, 1)
         }
         tc_after();
         // G of this batch is in TMEM: the feature stage is free for batch b+1
-        if (more) prefetch_feat(b + 1, stg ^ 1);
-        const GRec *R = srec(stg);
+        if (more) prefetch_feat(b + 1, (b + 1) % 3);
+        const GRec *R = srec(b % 3);
         float Gv[32];
         tmem_ld32(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * 32, Gv);
         float al[32], gx[32], Tj[32];
@@ -845,6 +911,24 @@ __global__ void __launch_bounds__(256, 1)
             xT[pidx] = T;
             xS[pidx] = S;
         }
+        // FM of batch b-1 has finished: drain it, then its operands are free
+        if (b >= 1) {
+            const bool ok = mbar_wait(&bars[1], ph1);
+            if (ok) {
+                ph1 ^= 1u;
+                pend1 = false;
+            }
+            if (__syncthreads_or(!ok)) {
+                timeout = true;
+                break;
+            }
+            tc_after();
+            drain(b - 1);
+            tc_before();
+            __syncthreads();
+            if (tid < kBB) sRgb(b - 1)[3 * tid] = sRgb(b - 1)[3 * tid + 1] = sRgb(b - 1)[3 * tid + 2] = 0.f;
+            if (tid < 2) sMask(b - 1)[tid] = 0u;
+        }
         // weights (A of dFe) and t hi/lo (A of the moments) of this group's Gaussians
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -869,7 +953,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) cmask |= (al[jj] > 0.f ? 1u : 0u) << jj;
         cmask = __reduce_or_sync(0xffffffffu, cmask);
-        if (lane == 0 && cmask) atomicOr(&sMask[grp], cmask);
+        if (lane == 0 && cmask) atomicOr(&sMask(b)[grp], cmask);
         // colour sums sum_p w dC_p per Gaussian; channel c is summed by slice
         // c % (number of slices).  A reduce-scatter over the warp's 32 pixels
         // leaves lane l with the warp's sum for Gaussian 32 grp + l.
@@ -886,7 +970,7 @@ __global__ void __launch_bounds__(256, 1)
                 rs_step<4>(v, lane, 4);
                 rs_step<2>(v, lane, 2);
                 rs_step<1>(v, lane, 1);
-                if (cmask & (1u << lane)) atomicAdd(&sRgb[3 * (grp * 32 + lane) + c], v[0]);
+                if (cmask & (1u << lane)) atomicAdd(&sRgb(b)[3 * (grp * 32 + lane) + c], v[0]);
             }
         }
         cp_async_wait_all();  // batch b+1's records and features have landed
@@ -897,87 +981,24 @@ __global__ void __launch_bounds__(256, 1)
             S = xS[pidx];
         }
         if (tid == 0) {
-            issue_FM();
             if (more) issue_G();
+            issue_FM();
         }
         pend1 = true;
         if (more) pend0 = true;
-        {
-            const bool ok = mbar_wait(&bars[1], ph1);
-            if (ok) {
-                ph1 ^= 1u;
-                pend1 = false;
-            }
-            if (__syncthreads_or(!ok)) {
-                timeout = true;
-                break;
-            }
+    }
+    if (nbat > 0 && !timeout) {  // the last batch's FM
+        const bool ok = mbar_wait(&bars[1], ph1);
+        if (ok) {
+            ph1 ^= 1u;
+            pend1 = false;
         }
-        tc_after();
-        if ((warp & 3) < 2) {  // rows 0..63 of the accumulators = the batch's Gaussians
-            const int j = (warp & 1) * 32 + lane;
-            const uint32_t wmask = sMask[warp & 1] & (nb >= (warp & 1) * 32 + 32 ? 0xFFFFFFFFu
-                                   : (nb > (warp & 1) * 32 ? (1u << (nb - (warp & 1) * 32)) - 1u : 0u));
-            const bool mine = (wmask >> lane) & 1u;
-            const uint32_t gid = sgid(stg)[j];
-            const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-            if (grp == 0) {
-                float m[16];
-                tmem_ld16(tM + lanes, m);
-                if (mine) {
-                    const GRec r = R[j];
-                    // moments about the pixel grid: dx = i - a, dy = j - b
-                    const float a = r.a.x - (float)x0 - 0.5f, bb = r.a.y - (float)y0 - 0.5f;
-                    const float M0 = m[0], Mi = m[1], Mj = m[2], Mii = m[3], Mij = m[4], Mjj = m[5];
-                    const float Sx = Mi - a * M0, Sy = Mj - bb * M0;
-                    const float Sxx = Mii - 2.f * a * Mi + a * a * M0;
-                    const float Sxy = Mij - a * Mj - bb * Mi + a * bb * M0;
-                    const float Syy = Mjj - 2.f * bb * Mj + bb * bb * M0;
-                    const float op = r.b.y, cA = r.a.z, cB = r.a.w, cC = r.b.x;
-                    float4 *dst = reinterpret_cast<float4 *>(g2dc + 12 * (long long)gid);
-                    atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy),
-                                               -0.5f * op * Sxx, -op * Sxy));
-                    const int nch = (int)gridDim.y;
-                    atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, chunk == 0 ? sRgb[3 * j] : 0.f,
-                                                   chunk == 1 % nch ? sRgb[3 * j + 1] : 0.f));
-                    if (chunk == 2 % nch) atomicAdd(g2dc + 12 * (long long)gid + 8, sRgb[3 * j + 2]);
-                }
-            }
-            if (want_fg && wmask) {
-                // group g drains columns [g DN/2, (g+1) DN/2) in 32-column blocks,
-                // transposed through shared memory (the weight-t buffers are free
-                // once the MMAs that read them are done): each atomic then covers
-                // 128 contiguous bytes of one Gaussian's row
-                float *stage = reinterpret_cast<float *>(sTh) + ((warp & 1) + 2 * grp) * (32 * 36);
-                const int sub = lane >> 3, q4 = (lane & 7) * 4;
-#pragma unroll 1
-                for (int cc = 0; cc < DN / 64; ++cc) {
-                    float v[32];
-                    tmem_ld32(tF + lanes + grp * (DN / 2) + cc * 32, v);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        *reinterpret_cast<float4 *>(stage + lane * 36 + 4 * i) =
-                            make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                    __syncwarp();
-#pragma unroll
-                    for (int it = 0; it < 8; ++it) {
-                        const int jj = it * 4 + sub;
-                        if ((wmask >> jj) & 1u) {
-                            const uint32_t g = sgid(stg)[(warp & 1) * 32 + jj];
-                            atomicAdd(reinterpret_cast<float4 *>(gfeatures + (size_t)g * D + d0 + grp * (DN / 2) +
-                                                                 cc * 32 + q4),
-                                      *reinterpret_cast<const float4 *>(stage + jj * 36 + q4));
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+        } else {
+            tc_after();
+            drain(nbat - 1);
         }
-        tc_before();
-        __syncthreads();
-        tc_after();
-        if (tid < kBB) sRgb[3 * tid] = sRgb[3 * tid + 1] = sRgb[3 * tid + 2] = 0.f;
-        if (tid < 2) sMask[tid] = 0u;
     }
     if (timeout) {
         if (tid == 0) latch(status, ST_TIMEOUT);
