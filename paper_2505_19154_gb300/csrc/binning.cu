@@ -355,21 +355,32 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32
     for (long long c0 = b0; c0 < b1; c0 += kStage) {
         const int m = (int)min((long long)kStage, b1 - c0);
         __syncwarp();
-        for (int k = lane; k < m; k += 32) {
-            const uint32_t e = order[c0 + k];
-            int4 r = make_int4(0, 0, -1, -1);  // empty unless it touches the band
-            if (pv.ntiles[e]) {
-                r = pv.trect[e];
-                r.y = max(r.y, by0);
-                r.w = min(r.w, by1 - 1);
+        // stage only the Gaussians that touch the band, in order (ballot compaction)
+        int mt = 0;
+        for (int k0 = 0; k0 < m; k0 += 32) {
+            const int k = k0 + lane;
+            int4 r = make_int4(0, 0, -1, -1);
+            uint32_t e = 0;
+            if (k < m) {
+                e = order[c0 + k];
+                if (pv.ntiles[e]) {
+                    r = pv.trect[e];
+                    r.y = max(r.y, by0);
+                    r.w = min(r.w, by1 - 1);
+                }
             }
-            st_r[k] = r;
-            st_g[k] = (uint32_t)(e - (long long)ci * N);
+            const bool touch = r.w >= r.y;
+            const uint32_t bal = __ballot_sync(0xffffffffu, touch);
+            if (touch) {
+                const int at = mt + __popc(bal & ((1u << lane) - 1u));
+                st_r[at] = r;
+                st_g[at] = (uint32_t)(e - (long long)ci * N);
+            }
+            mt += __popc(bal);
         }
         __syncwarp();
-        for (int k = 0; k < m; ++k) {
+        for (int k = 0; k < mt; ++k) {
             const int4 r = st_r[k];
-            if (r.w < r.y) continue;
             const uint32_t g = st_g[k];
             const int w = r.z - r.x + 1;
             const uint32_t nt = (uint32_t)(w * (r.w - r.y + 1));
