@@ -167,6 +167,10 @@ __device__ __forceinline__ void bulk_s2g(void *g, uint32_t saddr, uint32_t bytes
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Bulk prefetch of `bytes` (16-byte aligned, multiple of 16) into L2.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *g, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -572,8 +576,9 @@ __global__ void __launch_bounds__(256, 1)
                     const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats, int D,
                     const float *__restrict__ Tfin, const int32_t *__restrict__ lastv,
                     const float *__restrict__ grgb, const float *__restrict__ gfeat, float *g2d, float *gfeatures,
-                    unsigned *status) {
+                    unsigned *status, int n_items) {
     using C = BwdCfg<DN>;
+    if ((int)blockIdx.x >= n_items) return;  // uniform over the CTA
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
     uint8_t *sW = sm + C::kOffW;
@@ -590,103 +595,49 @@ __global__ void __launch_bounds__(256, 1)
     float *xS = xT + 128;                                      // [128] S after the batch
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::kOffBar);  // [0] G, [1] dFe + moments
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
-    int *smax = reinterpret_cast<int *>(tslot + 1);
+    // [2] per item parity: max over the CTA of (item counter << 32 | last); the
+    // counter only grows, so no slot is ever reset, and a slot's next writer
+    // is two items later, past at least one barrier of every thread
+    unsigned long long *smax = reinterpret_cast<unsigned long long *>(bars + 3);
     auto srec = [&](int stg) { return reinterpret_cast<GRec *>(sm + C::kOffRec + stg * C::kRecBytes); };
     auto sgid = [&](int stg) {
         return reinterpret_cast<uint32_t *>(sm + C::kOffRec + stg * C::kRecBytes + kBB * 48);
     };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, grp = tid >> 7, pidx = tid & 127;
-    const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, chunk = blockIdx.y;
-    const int ci = cam_of_tile(cs, tile);
-    const DevCam &cam = cs.c[ci];
-    const int lt = tile - cam.tile_off;
-    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    const int x0 = tx * kTile, y0 = ty * kTile + half * 8;
-    const int px = x0 + (pidx & 15), py = y0 + (pidx >> 4);
-    const bool inside = px < cam.W && py < cam.H;
-    const long long pix = cam.pix_off + (long long)py * cam.W + px;
-    const uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
-    const int d0 = chunk * DN;
-    const GRec *rec = pv.rec + (long long)ci * N;
-    float *g2dc = g2d + (long long)ci * N * 12;
     const bool want_fg = gfeatures != nullptr;
+    const int nch = D / DN;  // D slices: items are (tile, half, slice), tile and half fastest
+    const int n_half = n_items / nch;
 
-    // dF slice of this CTA's pixels, 16 rows per warp, all loads in flight
-    // before anything else (their latency hides the rest of the setup)
-    constexpr int kL = DN >= 128 ? DN / 128 : 1;
-    float4 vdf[16][kL];
-#pragma unroll
-    for (int rr = 0; rr < 16; ++rr) {
-        const int prow = warp * 16 + rr;
-        const int qx = x0 + (prow & 15), qy = y0 + (prow >> 4);
-        const bool qin = qx < cam.W && qy < cam.H && gfeat != nullptr;
-        const float *src = gfeat + (cam.pix_off + (long long)qy * cam.W + qx) * D + d0;
-#pragma unroll
-        for (int li = 0; li < kL; ++li) {
-            const int f = li * 128 + lane * 4;
-            vdf[rr][li] = (qin && f < DN) ? *reinterpret_cast<const float4 *>(src + f) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
     if (warp == 0) tmem_alloc(tslot, C::kTmemCols);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_mbar_init();
-        *smax = 0;
+        smax[0] = smax[1] = 0ull;
     }
     if (tid < 2 * kBB) sRgb(0)[3 * tid] = sRgb(0)[3 * tid + 1] = sRgb(0)[3 * tid + 2] = 0.f;  // both slots
     if (tid < 4) sMask(0)[tid] = 0u;
-    float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
-    int lastp = 0;
-    if (inside) {
-        T = Tfin[pix];
-        lastp = lastv[pix];
-        dC0 = grgb[3 * pix];
-        dC1 = grgb[3 * pix + 1];
-        dC2 = grgb[3 * pix + 2];
+    // pixel-moment rows of X: X[n][p] for p = i + 16 j
+    for (int q = tid; q < 16 * 128; q += 256) {
+        const int n = q >> 7, pp = q & 127;
+        const float i = (float)(pp & 15), jv = (float)(pp >> 4);
+        const float val = n == 0 ? 1.f : n == 1 ? i : n == 2 ? jv : n == 3 ? i * i : n == 4 ? i * jv
+                                                   : n == 5 ? jv * jv : 0.f;
+        *reinterpret_cast<__nv_bfloat16 *>(sX + (pp >> 6) * (16 * 128) + swz(n, (pp & 63) >> 3) +
+                           2 * (pp & 7)) = __float2bfloat16_rn(val);
     }
     tc_before();
     __syncthreads();
     tc_after();
-    if (grp == 0) atomicMax(smax, lastp);
-    __syncthreads();
     const uint32_t taddr = *tslot;
     const uint32_t tG = taddr, tM = taddr + C::kColM, tF = taddr + C::kColF;
-    const int Lmax = min(*smax, (int)(e - s));
-    const int nbat = (Lmax + kBB - 1) / kBB;
     const uint32_t sW_s = smem_u32(sW), sDh_s = smem_u32(sDh), sDl_s = smem_u32(sDl);
     const uint32_t sTh_s = smem_u32(sTh), sTl_s = smem_u32(sTl), sX_s = smem_u32(sX);
     const uint32_t sF_s = smem_u32(sm + C::kOffF);
     constexpr uint32_t idG = idesc_bf16(128, kBB, false, false);
     constexpr uint32_t idF = idesc_bf16(128, DN, true, true);
     constexpr uint32_t idM = idesc_bf16(128, 16, true, false);
-
-    // batch b covers list positions [max(0, Lmax - 64 (b+1)), Lmax - 64 b): back to front
-    auto prefetch_rec = [&](int b, int stg) {  // Gaussian ids + records of batch b (stage b % 3)
-        const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
-        if (tid < kBB) sgid(stg)[tid] = tid < nb ? __ldg(gids + s + bs + tid) : 0u;
-        if (tid < nb) {
-            const uint32_t dst = smem_u32(srec(stg) + tid);
-            const GRec *src = rec + sgid(stg)[tid];
-            cp_async16(dst, &src->a, true);
-            cp_async16(dst + 16, &src->b, true);
-            cp_async16(dst + 32, &src->c, true);
-        }
-        cp_async_commit();
-    };
-    auto prefetch_feat = [&](int b, int stg) {  // feature rows (reads the staged ids)
-        const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
-        const uint32_t *ids = sgid(stg);
-        constexpr int kCPR = DN / 8;
-#pragma unroll 4
-        for (int q = tid; q < kBB * kCPR; q += 256) {
-            const int g = q / kCPR, c = q - g * kCPR;
-            cp_async16(sF_s + (c >> 3) * (kBB * 128) + swz(g, c & 7), feats + (size_t)ids[g] * D + d0 + c * 8,
-                       g < nb);
-        }
-        cp_async_commit();
-    };
     auto issue_G = [&]() {  // G(px, g) = sum_d dF(px, d) Fe(g, d), hi + lo parts
         tc_after();
 #pragma unroll
@@ -714,20 +665,187 @@ __global__ void __launch_bounds__(256, 1)
         mma_commit(&bars[1]);
     };
 
+    // the drain of batch db of an item (moments and colour sums into the
+    // footprint gradients, the feature-gradient block into grad_features);
+    // the item's geometry is passed in, it may be the previous item's
+    auto drain = [&](int db, int dnbat_end, int dx0, int dy0, float *dg2dc, int dchunk, int dd0) {
+        const int dbe = dnbat_end - db * kBB, dnb = dbe - max(0, dbe - kBB);
+            if ((warp & 3) < 2) {  // rows 0..63 of the accumulators = the batch's Gaussians
+                const int j = (warp & 1) * 32 + lane;
+                const uint32_t wmask = sMask(db)[warp & 1] & (dnb >= (warp & 1) * 32 + 32 ? 0xFFFFFFFFu
+                                       : (dnb > (warp & 1) * 32 ? (1u << (dnb - (warp & 1) * 32)) - 1u : 0u));
+                const bool mine = (wmask >> lane) & 1u;
+                const uint32_t gid = sgid(db % 3)[j];
+                const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+                if (grp == 0) {
+                    float m[16];
+                    tmem_ld16(tM + lanes, m);
+                    if (mine) {
+                        const GRec r = srec(db % 3)[j];
+                        // moments about the pixel grid: dx = i - a, dy = j - b
+                        const float a = r.a.x - (float)dx0 - 0.5f, bb = r.a.y - (float)dy0 - 0.5f;
+                        const float M0 = m[0], Mi = m[1], Mj = m[2], Mii = m[3], Mij = m[4], Mjj = m[5];
+                        const float Sx = Mi - a * M0, Sy = Mj - bb * M0;
+                        const float Sxx = Mii - 2.f * a * Mi + a * a * M0;
+                        const float Sxy = Mij - a * Mj - bb * Mi + a * bb * M0;
+                        const float Syy = Mjj - 2.f * bb * Mj + bb * bb * M0;
+                        const float op = r.b.y, cA = r.a.z, cB = r.a.w, cC = r.b.x;
+                        float4 *dst = reinterpret_cast<float4 *>(dg2dc + 12 * (long long)gid);
+                        atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy),
+                                                   -0.5f * op * Sxx, -op * Sxy));
+                                                atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, dchunk == 0 ? sRgb(db)[3 * j] : 0.f,
+                                                       dchunk == 1 % nch ? sRgb(db)[3 * j + 1] : 0.f));
+                        if (dchunk == 2 % nch) atomicAdd(dg2dc + 12 * (long long)gid + 8, sRgb(db)[3 * j + 2]);
+                    }
+                }
+                if (want_fg && wmask) {
+                    // group g drains columns [g DN/2, (g+1) DN/2) in 32-column blocks,
+                    // transposed through shared memory (the weight-t buffers are free
+                    // once the MMAs that read them are done): each atomic then covers
+                    // 128 contiguous bytes of one Gaussian's row
+                    float *stage = reinterpret_cast<float *>(sTh) + ((warp & 1) + 2 * grp) * (32 * 36);
+                    const int sub = lane >> 3, q4 = (lane & 7) * 4;
+#pragma unroll 1
+                    for (int cc = 0; cc < DN / 64; ++cc) {
+                        float v[32];
+                        tmem_ld32(tF + lanes + grp * (DN / 2) + cc * 32, v);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            *reinterpret_cast<float4 *>(stage + lane * 36 + 4 * i) =
+                                make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        __syncwarp();
+#pragma unroll
+                        for (int it = 0; it < 8; ++it) {
+                            const int jj = it * 4 + sub;
+                            if ((wmask >> jj) & 1u) {
+                                const uint32_t g = sgid(db % 3)[(warp & 1) * 32 + jj];
+                                atomicAdd(reinterpret_cast<float4 *>(gfeatures + (size_t)g * D + dd0 + grp * (DN / 2) +
+                                                                     cc * 32 + q4),
+                                          *reinterpret_cast<const float4 *>(stage + jj * 36 + q4));
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+            }    };
+    // where item `it` lives: tile, half, slice, camera and its first pixel
+    struct ItemGeo {
+        int tile, chunk, ci, x0, y0;
+    };
+    auto item_geo = [&](int it) {
+        ItemGeo g;
+        const int hx = it % n_half;
+        g.chunk = it / n_half;
+        g.tile = hx >> 1;
+        g.ci = cam_of_tile(cs, g.tile);
+        const DevCam &cm = cs.c[g.ci];
+        const int lt = g.tile - cm.tile_off;
+        g.x0 = (lt % cm.tiles_x) * kTile;
+        g.y0 = (lt / cm.tiles_x) * kTile + (hx & 1) * 8;
+        return g;
+    };
+
     uint32_t ph0 = 0, ph1 = 0;
     bool pend0 = false, pend1 = false;
     bool timeout = false;
-    if (nbat > 0) {
-        prefetch_rec(0, 0);
-        // pixel-moment rows of X: X[n][p] for p = i + 16 j
-        for (int q = tid; q < 16 * 128; q += 256) {
-            const int n = q >> 7, pp = q & 127;
-            const float i = (float)(pp & 15), jv = (float)(pp >> 4);
-            const float val = n == 0 ? 1.f : n == 1 ? i : n == 2 ? jv : n == 3 ? i * i : n == 4 ? i * jv
-                                                                                                   : n == 5 ? jv * jv : 0.f;
-            *reinterpret_cast<__nv_bfloat16 *>(sX + (pp >> 6) * (16 * 128) + swz(n, (pp & 63) >> 3) +
-                                               2 * (pp & 7)) = __float2bfloat16_rn(val);
+    // the previous item's last batch waits for its FM and drain until the
+    // next item's loads are in flight
+    bool have_prev = false;
+    int prev_b = 0, prev_end = 0, prev_x0 = 0, prev_y0 = 0, prev_chunk = 0, prev_d0 = 0;
+    float *prev_g2dc = g2d;
+    constexpr int kL = DN >= 128 ? DN / 128 : 1;
+    int k = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++k) {
+        const ItemGeo ig = item_geo(it);
+        const int chunk = ig.chunk, ci = ig.ci, x0 = ig.x0, y0 = ig.y0;
+        const DevCam &cam = cs.c[ci];
+        const int px = x0 + (pidx & 15), py = y0 + (pidx >> 4);
+        const bool inside = px < cam.W && py < cam.H;
+        const long long pix = cam.pix_off + (long long)py * cam.W + px;
+        const uint32_t s = ranges[2 * ig.tile], e = ranges[2 * ig.tile + 1];
+        const int d0 = chunk * DN;
+        const GRec *rec = pv.rec + (long long)ci * N;
+        float *g2dc = g2d + (long long)ci * N * 12;
+        // this item's dF slice, 16 rows per warp, all loads in flight at once
+        float4 vdf[16][kL];
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+        const int prow = warp * 16 + rr;
+        const int qx = x0 + (prow & 15), qy = y0 + (prow >> 4);
+        const bool qin = qx < cam.W && qy < cam.H && gfeat != nullptr;
+        const float *src = gfeat + (cam.pix_off + (long long)qy * cam.W + qx) * D + d0;
+#pragma unroll
+        for (int li = 0; li < kL; ++li) {
+            const int f = li * 128 + lane * 4;
+            vdf[rr][li] = (qin && f < DN) ? *reinterpret_cast<const float4 *>(src + f) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+    }
+        // warm L2 with the next item's dF slice, one bulk prefetch per pixel
+        if (tid < 128 && gfeat != nullptr && it + (int)gridDim.x < n_items) {
+            const ItemGeo ng = item_geo(it + gridDim.x);
+            const DevCam &nc = cs.c[ng.ci];
+            const int nx = ng.x0 + (tid & 15), ny = ng.y0 + (tid >> 4);
+            if (nx < nc.W && ny < nc.H)
+                bulk_prefetch_l2(gfeat + (nc.pix_off + (long long)ny * nc.W + nx) * D + ng.chunk * DN, DN * 4);
+        }
+        float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
+        int lastp = 0;
+        if (inside) {
+            T = Tfin[pix];
+            lastp = lastv[pix];
+            dC0 = grgb[3 * pix];
+            dC1 = grgb[3 * pix + 1];
+            dC2 = grgb[3 * pix + 2];
+        }
+        // tail of the previous item: its last FM, then its drain
+        if (have_prev) {
+            const bool ok = mbar_wait(&bars[1], ph1);
+            if (ok) {
+                ph1 ^= 1u;
+                pend1 = false;
+            }
+            if (__syncthreads_or(!ok)) {
+                timeout = true;
+                break;
+            }
+            tc_after();
+            drain(prev_b, prev_end, prev_x0, prev_y0, prev_g2dc, prev_chunk, prev_d0);
+            tc_before();
+            __syncthreads();
+            if (tid < kBB) sRgb(prev_b)[3 * tid] = sRgb(prev_b)[3 * tid + 1] = sRgb(prev_b)[3 * tid + 2] = 0.f;
+            if (tid < 2) sMask(prev_b)[tid] = 0u;
+            have_prev = false;
+        }
+        if (grp == 0) atomicMax(&smax[k & 1], ((unsigned long long)k << 32) | (uint32_t)max(lastp, 0));
+        __syncthreads();
+        const int Lmax = (int)min((unsigned long long)(e - s), smax[k & 1] & 0xFFFFFFFFull);
+        const int nbat = (Lmax + kBB - 1) / kBB;
+    auto prefetch_rec = [&](int b, int stg) {  // Gaussian ids + records of batch b (stage b % 3)
+        const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
+        if (tid < kBB) sgid(stg)[tid] = tid < nb ? __ldg(gids + s + bs + tid) : 0u;
+        if (tid < nb) {
+            const uint32_t dst = smem_u32(srec(stg) + tid);
+            const GRec *src = rec + sgid(stg)[tid];
+            cp_async16(dst, &src->a, true);
+            cp_async16(dst + 16, &src->b, true);
+            cp_async16(dst + 32, &src->c, true);
+        }
+        cp_async_commit();
+    };
+    auto prefetch_feat = [&](int b, int stg) {  // feature rows (reads the staged ids)
+        const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
+        const uint32_t *ids = sgid(stg);
+        constexpr int kCPR = DN / 8;
+#pragma unroll 4
+        for (int q = tid; q < kBB * kCPR; q += 256) {
+            const int g = q / kCPR, c = q - g * kCPR;
+            cp_async16(sF_s + (c >> 3) * (kBB * 128) + swz(g, c & 7), feats + (size_t)ids[g] * D + d0 + c * 8,
+                       g < nb);
+        }
+        cp_async_commit();
+    };
+        if (nbat > 0) {
+            prefetch_rec(0, 0);
         // dF -> BF16 hi / lo, K-major swizzled
         {
 #pragma unroll
@@ -754,240 +872,190 @@ __global__ void __launch_bounds__(256, 1)
                 }
             }
         }
-        __syncthreads();  // batch 0's ids are staged
-        prefetch_feat(0, 0);
-        cp_async_wait_all();
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) issue_G();
-        pend0 = true;
-    }
+            __syncthreads();  // batch 0's ids are staged
+            prefetch_feat(0, 0);
+            cp_async_wait_all();
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) issue_G();
+            pend0 = true;
+        }
 
-    const float fpx = px + 0.5f, fpy = py + 0.5f;
-    // the colour part of dL/dw (and the background term) belongs to slice 0
-    // only; every slice sums its own colour channels for the colour gradients
-    const float rC0 = chunk == 0 ? dC0 : 0.f, rC1 = chunk == 0 ? dC1 : 0.f, rC2 = chunk == 0 ? dC2 : 0.f;
-    float S = T * (rC0 * p.bg0 + rC1 * p.bg1 + rC2 * p.bg2);
-    // Batch b's feature-gradient and moment MMAs (FM) run while batch b+1 is
-    // weighed: the drain of batch b (TMEM -> moments, colour sums, feature
-    // gradients) happens in iteration b+1 after its recursion, before its
-    // weights overwrite the MMA operands.  G of batch b+1 is issued ahead of
-    // FM of batch b so that the next iteration's first wait is short.
-    auto drain = [&](int db) {
-        const int dbe = Lmax - db * kBB, dnb = dbe - max(0, dbe - kBB);
-            if ((warp & 3) < 2) {  // rows 0..63 of the accumulators = the batch's Gaussians
-                const int j = (warp & 1) * 32 + lane;
-                const uint32_t wmask = sMask(db)[warp & 1] & (dnb >= (warp & 1) * 32 + 32 ? 0xFFFFFFFFu
-                                       : (dnb > (warp & 1) * 32 ? (1u << (dnb - (warp & 1) * 32)) - 1u : 0u));
-                const bool mine = (wmask >> lane) & 1u;
-                const uint32_t gid = sgid(db % 3)[j];
-                const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-                if (grp == 0) {
-                    float m[16];
-                    tmem_ld16(tM + lanes, m);
-                    if (mine) {
-                        const GRec r = srec(db % 3)[j];
-                        // moments about the pixel grid: dx = i - a, dy = j - b
-                        const float a = r.a.x - (float)x0 - 0.5f, bb = r.a.y - (float)y0 - 0.5f;
-                        const float M0 = m[0], Mi = m[1], Mj = m[2], Mii = m[3], Mij = m[4], Mjj = m[5];
-                        const float Sx = Mi - a * M0, Sy = Mj - bb * M0;
-                        const float Sxx = Mii - 2.f * a * Mi + a * a * M0;
-                        const float Sxy = Mij - a * Mj - bb * Mi + a * bb * M0;
-                        const float Syy = Mjj - 2.f * bb * Mj + bb * bb * M0;
-                        const float op = r.b.y, cA = r.a.z, cB = r.a.w, cC = r.b.x;
-                        float4 *dst = reinterpret_cast<float4 *>(g2dc + 12 * (long long)gid);
-                        atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy),
-                                                   -0.5f * op * Sxx, -op * Sxy));
-                        const int nch = (int)gridDim.y;
-                        atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, chunk == 0 ? sRgb(db)[3 * j] : 0.f,
-                                                       chunk == 1 % nch ? sRgb(db)[3 * j + 1] : 0.f));
-                        if (chunk == 2 % nch) atomicAdd(g2dc + 12 * (long long)gid + 8, sRgb(db)[3 * j + 2]);
-                    }
+        const float fpx = px + 0.5f, fpy = py + 0.5f;
+        // the colour part of dL/dw (and the background term) belongs to slice 0
+        // only; every slice sums its own colour channels for the colour gradients
+        const float rC0 = chunk == 0 ? dC0 : 0.f, rC1 = chunk == 0 ? dC1 : 0.f, rC2 = chunk == 0 ? dC2 : 0.f;
+        float S = T * (rC0 * p.bg0 + rC1 * p.bg1 + rC2 * p.bg2);
+        for (int b = 0; b < nbat; ++b) {
+            const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
+            const bool more = b + 1 < nbat;
+            if (more) prefetch_rec(b + 1, (b + 1) % 3);
+            {
+                const bool ok = mbar_wait(&bars[0], ph0);
+                if (ok) {
+                    ph0 ^= 1u;
+                    pend0 = false;
                 }
-                if (want_fg && wmask) {
-                    // group g drains columns [g DN/2, (g+1) DN/2) in 32-column blocks,
-                    // transposed through shared memory (the weight-t buffers are free
-                    // once the MMAs that read them are done): each atomic then covers
-                    // 128 contiguous bytes of one Gaussian's row
-                    float *stage = reinterpret_cast<float *>(sTh) + ((warp & 1) + 2 * grp) * (32 * 36);
-                    const int sub = lane >> 3, q4 = (lane & 7) * 4;
-#pragma unroll 1
-                    for (int cc = 0; cc < DN / 64; ++cc) {
-                        float v[32];
-                        tmem_ld32(tF + lanes + grp * (DN / 2) + cc * 32, v);
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            *reinterpret_cast<float4 *>(stage + lane * 36 + 4 * i) =
-                                make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                        __syncwarp();
-#pragma unroll
-                        for (int it = 0; it < 8; ++it) {
-                            const int jj = it * 4 + sub;
-                            if ((wmask >> jj) & 1u) {
-                                const uint32_t g = sgid(db % 3)[(warp & 1) * 32 + jj];
-                                atomicAdd(reinterpret_cast<float4 *>(gfeatures + (size_t)g * D + d0 + grp * (DN / 2) +
-                                                                     cc * 32 + q4),
-                                          *reinterpret_cast<const float4 *>(stage + jj * 36 + q4));
-                            }
-                        }
-                        __syncwarp();
-                    }
+                if (__syncthreads_or(!ok)) {
+                    timeout = true;
+                    break;
                 }
-            }
-    };
-    for (int b = 0; b < nbat; ++b) {
-        const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
-        const bool more = b + 1 < nbat;
-        if (more) prefetch_rec(b + 1, (b + 1) % 3);
-        {
-            const bool ok = mbar_wait(&bars[0], ph0);
-            if (ok) {
-                ph0 ^= 1u;
-                pend0 = false;
-            }
-            if (__syncthreads_or(!ok)) {
-                timeout = true;
-                break;
-            }
-        }
-        tc_after();
-        // G of this batch is in TMEM: the feature stage is free for batch b+1
-        if (more) prefetch_feat(b + 1, (b + 1) % 3);
-        const GRec *R = srec(b % 3);
-        float Gv[32];
-        tmem_ld32(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * 32, Gv);
-        float al[32], gx[32], Tj[32];
-        float P = 1.f;
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-            const int j = grp * 32 + jj;
-            const float4 A4 = R[j].a, B4 = R[j].b;
-            const float dx = fpx - A4.x, dy = fpy - A4.y;
-            const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
-            const float G = __expf(-0.5f * q2);
-            const float rho = B4.y * G;
-            const float aa = fminf(p.amax, rho);
-            const bool ok = (j < nb) && (bs + j < lastp) && (q2 <= p.cut) && (aa >= p.amin);
-            al[jj] = ok ? aa : 0.f;
-            gx[jj] = (ok && rho <= p.amax) ? G : 0.f;
-            P *= 1.f - al[jj];
-        }
-        if (grp == 1) xP1[pidx] = P;
-        __syncthreads();
-        // T after this group's Gaussians, then T before each of them
-        const float Tend = grp == 1 ? T : __fdividef(T, xP1[pidx]);
-        const float Tstart = __fdividef(Tend, P);
-        {
-            float t = Tstart;
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-                Tj[jj] = t;
-                t *= 1.f - al[jj];
-            }
-        }
-        // App. A.2 back to front: dL/dalpha_k = T_k g_k - S_k / (1 - alpha_k);
-        // Gv becomes t_k = G dL/drho (group 0: still without S + S_1)
-        float Sg = grp == 1 ? S : 0.f;
-#pragma unroll
-        for (int jj = 31; jj >= 0; --jj) {
-            const int j = grp * 32 + jj;
-            // selects, not products with zero: records past the batch end are stale
-            const bool c = al[jj] > 0.f;
-            const float w = al[jj] * Tj[jj];
-            const float4 B4 = R[j].b;
-            const float g = c ? Gv[jj] + rC0 * B4.z + rC1 * B4.w + rC2 * R[j].c.x : 0.f;
-            const float dal = Tj[jj] * g - __fdividef(Sg, 1.f - al[jj]);
-            Sg = c ? Sg + w * g : Sg;
-            Gv[jj] = c ? gx[jj] * dal : 0.f;
-        }
-        if (grp == 1) xS1[pidx] = Sg - S;
-        __syncthreads();
-        if (grp == 0) {
-            const float Sb = S + xS1[pidx];  // suffix sum entering group 0's Gaussians
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) Gv[jj] -= __fdividef(gx[jj] * Sb, 1.f - al[jj]);
-            S = Sb + Sg;
-            T = Tstart;
-            xT[pidx] = T;
-            xS[pidx] = S;
-        }
-        // FM of batch b-1 has finished: drain it, then its operands are free
-        if (b >= 1) {
-            const bool ok = mbar_wait(&bars[1], ph1);
-            if (ok) {
-                ph1 ^= 1u;
-                pend1 = false;
-            }
-            if (__syncthreads_or(!ok)) {
-                timeout = true;
-                break;
             }
             tc_after();
-            drain(b - 1);
+            // G of this batch is in TMEM: the feature stage is free for batch b+1
+            if (more) prefetch_feat(b + 1, (b + 1) % 3);
+            const GRec *R = srec(b % 3);
+            float Gv[32];
+            tmem_ld32(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * 32, Gv);
+            float al[32], gx[32], Tj[32];
+            float P = 1.f;
+    #pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = grp * 32 + jj;
+                const float4 A4 = R[j].a, B4 = R[j].b;
+                const float dx = fpx - A4.x, dy = fpy - A4.y;
+                const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
+                const float G = __expf(-0.5f * q2);
+                const float rho = B4.y * G;
+                const float aa = fminf(p.amax, rho);
+                const bool ok = (j < nb) && (bs + j < lastp) && (q2 <= p.cut) && (aa >= p.amin);
+                al[jj] = ok ? aa : 0.f;
+                gx[jj] = (ok && rho <= p.amax) ? G : 0.f;
+                P *= 1.f - al[jj];
+            }
+            if (grp == 1) xP1[pidx] = P;
+            // batch b+1's records and features (requested before this batch's
+            // alphas) have landed, and this batch's G has left TMEM: G of batch
+            // b+1 runs under the rest of batch b
+            cp_async_wait_all();
+            fence_async_smem();
             tc_before();
             __syncthreads();
-            if (tid < kBB) sRgb(b - 1)[3 * tid] = sRgb(b - 1)[3 * tid + 1] = sRgb(b - 1)[3 * tid + 2] = 0.f;
-            if (tid < 2) sMask(b - 1)[tid] = 0u;
-        }
-        // weights (A of dFe) and t hi/lo (A of the moments) of this group's Gaussians
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint4 pw, ph, pl;
-            uint32_t *pwv = &pw.x, *phv = &ph.x, *plv = &pl.x;
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int j0 = 8 * q + 2 * h;
-                pwv[h] = pack_bf16(al[j0] * Tj[j0], al[j0 + 1] * Tj[j0 + 1]);
-                const __nv_bfloat162 th = __floats2bfloat162_rn(Gv[j0], Gv[j0 + 1]);
-                const float2 tb = __bfloat1622float2(th);
-                phv[h] = *reinterpret_cast<const uint32_t *>(&th);
-                plv[h] = pack_bf16(Gv[j0] - tb.x, Gv[j0 + 1] - tb.y);
+            if (more) {
+                if (tid == 0) issue_G();
+                pend0 = true;
             }
-            const uint32_t off = swz(pidx, grp * 4 + q);
-            *reinterpret_cast<uint4 *>(sW + off) = pw;
-            *reinterpret_cast<uint4 *>(sTh + off) = ph;
-            *reinterpret_cast<uint4 *>(sTl + off) = pl;
-        }
-        // which Gaussians contribute anywhere in the CTA: one OR per warp
-        uint32_t cmask = 0;
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) cmask |= (al[jj] > 0.f ? 1u : 0u) << jj;
-        cmask = __reduce_or_sync(0xffffffffu, cmask);
-        if (lane == 0 && cmask) atomicOr(&sMask(b)[grp], cmask);
-        // colour sums sum_p w dC_p per Gaussian; channel c is summed by slice
-        // c % (number of slices).  A reduce-scatter over the warp's 32 pixels
-        // leaves lane l with the warp's sum for Gaussian 32 grp + l.
-        if (cmask) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (c % (int)gridDim.y != chunk) continue;
-                const float dc = c == 0 ? dC0 : (c == 1 ? dC1 : dC2);
-                float v[32];
-#pragma unroll
-                for (int jj = 0; jj < 32; ++jj) v[jj] = al[jj] * Tj[jj] * dc;
-                rs_step<16>(v, lane, 16);
-                rs_step<8>(v, lane, 8);
-                rs_step<4>(v, lane, 4);
-                rs_step<2>(v, lane, 2);
-                rs_step<1>(v, lane, 1);
-                if (cmask & (1u << lane)) atomicAdd(&sRgb(b)[3 * (grp * 32 + lane) + c], v[0]);
+            // T after this group's Gaussians, then T before each of them
+            const float Tend = grp == 1 ? T : __fdividef(T, xP1[pidx]);
+            const float Tstart = __fdividef(Tend, P);
+            {
+                float t = Tstart;
+    #pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    Tj[jj] = t;
+                    t *= 1.f - al[jj];
+                }
             }
+            // App. A.2 back to front: dL/dalpha_k = T_k g_k - S_k / (1 - alpha_k);
+            // Gv becomes t_k = G dL/drho (group 0: still without S + S_1)
+            float Sg = grp == 1 ? S : 0.f;
+    #pragma unroll
+            for (int jj = 31; jj >= 0; --jj) {
+                const int j = grp * 32 + jj;
+                // selects, not products with zero: records past the batch end are stale
+                const bool c = al[jj] > 0.f;
+                const float w = al[jj] * Tj[jj];
+                const float4 B4 = R[j].b;
+                const float g = c ? Gv[jj] + rC0 * B4.z + rC1 * B4.w + rC2 * R[j].c.x : 0.f;
+                const float dal = Tj[jj] * g - __fdividef(Sg, 1.f - al[jj]);
+                Sg = c ? Sg + w * g : Sg;
+                Gv[jj] = c ? gx[jj] * dal : 0.f;
+            }
+            if (grp == 1) xS1[pidx] = Sg - S;
+            __syncthreads();
+            if (grp == 0) {
+                const float Sb = S + xS1[pidx];  // suffix sum entering group 0's Gaussians
+    #pragma unroll
+                for (int jj = 0; jj < 32; ++jj) Gv[jj] -= __fdividef(gx[jj] * Sb, 1.f - al[jj]);
+                S = Sb + Sg;
+                T = Tstart;
+                xT[pidx] = T;
+                xS[pidx] = S;
+            }
+            // FM of batch b-1 has finished: drain it, then its operands are free
+            if (b >= 1) {
+                const bool ok = mbar_wait(&bars[1], ph1);
+                if (ok) {
+                    ph1 ^= 1u;
+                    pend1 = false;
+                }
+                if (__syncthreads_or(!ok)) {
+                    timeout = true;
+                    break;
+                }
+                tc_after();
+                drain(b - 1, Lmax, x0, y0, g2dc, chunk, d0);
+                tc_before();
+                __syncthreads();
+                if (tid < kBB) sRgb(b - 1)[3 * tid] = sRgb(b - 1)[3 * tid + 1] = sRgb(b - 1)[3 * tid + 2] = 0.f;
+                if (tid < 2) sMask(b - 1)[tid] = 0u;
+            }
+            // weights (A of dFe) and t hi/lo (A of the moments) of this group's Gaussians
+    #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint4 pw, ph, pl;
+                uint32_t *pwv = &pw.x, *phv = &ph.x, *plv = &pl.x;
+    #pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int j0 = 8 * q + 2 * h;
+                    pwv[h] = pack_bf16(al[j0] * Tj[j0], al[j0 + 1] * Tj[j0 + 1]);
+                    const __nv_bfloat162 th = __floats2bfloat162_rn(Gv[j0], Gv[j0 + 1]);
+                    const float2 tb = __bfloat1622float2(th);
+                    phv[h] = *reinterpret_cast<const uint32_t *>(&th);
+                    plv[h] = pack_bf16(Gv[j0] - tb.x, Gv[j0 + 1] - tb.y);
+                }
+                const uint32_t off = swz(pidx, grp * 4 + q);
+                *reinterpret_cast<uint4 *>(sW + off) = pw;
+                *reinterpret_cast<uint4 *>(sTh + off) = ph;
+                *reinterpret_cast<uint4 *>(sTl + off) = pl;
+            }
+            // which Gaussians contribute anywhere in the CTA: one OR per warp
+            uint32_t cmask = 0;
+    #pragma unroll
+            for (int jj = 0; jj < 32; ++jj) cmask |= (al[jj] > 0.f ? 1u : 0u) << jj;
+            cmask = __reduce_or_sync(0xffffffffu, cmask);
+            if (lane == 0 && cmask) atomicOr(&sMask(b)[grp], cmask);
+            // colour sums sum_p w dC_p per Gaussian; channel c is summed by slice
+            // c % (number of slices).  A reduce-scatter over the warp's 32 pixels
+            // leaves lane l with the warp's sum for Gaussian 32 grp + l.
+            if (cmask) {
+    #pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (c % nch != chunk) continue;
+                    const float dc = c == 0 ? dC0 : (c == 1 ? dC1 : dC2);
+                    float v[32];
+    #pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) v[jj] = al[jj] * Tj[jj] * dc;
+                    rs_step<16>(v, lane, 16);
+                    rs_step<8>(v, lane, 8);
+                    rs_step<4>(v, lane, 4);
+                    rs_step<2>(v, lane, 2);
+                    rs_step<1>(v, lane, 1);
+                    if (cmask & (1u << lane)) atomicAdd(&sRgb(b)[3 * (grp * 32 + lane) + c], v[0]);
+                }
+            }
+            fence_async_smem();  // weights and t (generic writes) -> the MMA operands
+            __syncthreads();
+            if (grp == 1) {
+                T = xT[pidx];
+                S = xS[pidx];
+            }
+            if (tid == 0) issue_FM();
+            pend1 = true;
         }
-        cp_async_wait_all();  // batch b+1's records and features have landed
-        fence_async_smem();
-        __syncthreads();
-        if (grp == 1) {
-            T = xT[pidx];
-            S = xS[pidx];
+        if (timeout) break;
+        if (nbat > 0) {
+            have_prev = true;
+            prev_b = nbat - 1;
+            prev_end = Lmax;
+            prev_x0 = x0;
+            prev_y0 = y0;
+            prev_g2dc = g2dc;
+            prev_chunk = chunk;
+            prev_d0 = d0;
         }
-        if (tid == 0) {
-            if (more) issue_G();
-            issue_FM();
-        }
-        pend1 = true;
-        if (more) pend0 = true;
     }
-    if (nbat > 0 && !timeout) {  // the last batch's FM
+    if (have_prev && !timeout) {  // the last item's last FM
         const bool ok = mbar_wait(&bars[1], ph1);
         if (ok) {
             ph1 ^= 1u;
@@ -997,7 +1065,7 @@ __global__ void __launch_bounds__(256, 1)
             timeout = true;
         } else {
             tc_after();
-            drain(nbat - 1);
+            drain(prev_b, prev_end, prev_x0, prev_y0, prev_g2dc, prev_chunk, prev_d0);
         }
     }
     if (timeout) {
@@ -1028,6 +1096,19 @@ int pick_bwd_dn(int D, int d_split) {
 }
 
 }  // namespace
+
+// Streaming multiprocessors of the current device, looked up once per device.
+int sm_count_current() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
 
 int tc_supported(int D, int d_split) {
     return D > 0 && pick_fwd_dn(D, d_split) != 0 && pick_bwd_dn(D, d_split) != 0;
@@ -1062,14 +1143,17 @@ void launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
                           const float *grgb, const float *gfeat, float *g2d, float *gfeatures, unsigned *status,
                           cudaStream_t st) {
     const int dn = pick_bwd_dn(D, d_split);
-    dim3 grid(cs.total_tiles * 2, D / dn);
+    // persistent: one CTA per SM walks the (tile, half, slice) items
+    const int n_items = cs.total_tiles * 2 * (D / dn);
+    const dim3 grid((unsigned)max(1, min(n_items, sm_count_current())));
     note_launch(1);
 #define FHGS_BWD(DNV)                                                                                          \
     case DNV: {                                                                                                \
         static std::atomic<unsigned long long> smem_done{0};                                                 \
         allow_max_smem(smem_done, k_render_bwd_tc<DNV>);                                                     \
         k_render_bwd_tc<DNV><<<grid, 256, BwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, feats, D, T, \
-                                                                   last, grgb, gfeat, g2d, gfeatures, status);  \
+                                                                   last, grgb, gfeat, g2d, gfeatures, status,   \
+                                                                   n_items);                                     \
         break;                                                                                                 \
     }
     switch (dn) {
