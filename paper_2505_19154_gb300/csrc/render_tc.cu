@@ -219,9 +219,11 @@ struct FwdCfg {
     // kCH columns, one padded row per pixel (16 B of padding keeps the
     // lane-per-pixel writes free of bank conflicts), then one bulk copy per
     // pixel and pass; the staging reuses the weight and feature stages
-    static constexpr int kCH = DN == 512 ? 256 : (DN == 64 ? 64 : DN / 2);
+    static constexpr int kCH = DN >= 256 ? DN / 4 : 64;
     static constexpr int kStageRow = (kCH + 4) * 4;
-    static_assert(128 * kStageRow <= kOffRec, "epilogue staging must fit in the weight and feature stages");
+    static constexpr int kStageBytes = 128 * kStageRow;
+    static constexpr int kNBuf = 2 * kStageBytes <= kOffRec ? 2 : 1;  // passes double-buffered when they fit
+    static_assert(kStageBytes <= kOffRec, "epilogue staging must fit in the weight and feature stages");
 };
 
 template <int DN>
@@ -462,13 +464,22 @@ __global__ void __launch_bounds__(256, 1)
     } else {
         tc_after();
         // accumulator -> padded rows in shared memory -> one bulk copy per
-        // pixel and pass.  Warp w reads TMEM lanes 32 (w % 4).. (pixels) and
-        // half of the pass's columns.
+        // pixel and pass, the passes double-buffered so that the TMA engine
+        // reads one while the warps fill the next.  Warp w reads TMEM lanes
+        // 32 (w % 4).. (pixels) and half of the pass's columns.  The CTA
+        // waits only until its copies have read shared memory.
         constexpr int kCH = C::kCH;
         const int row = (warp & 3) * 32 + (tid & 31);
-        const uint32_t stage_s = smem_u32(sm);
 #pragma unroll 1
         for (int pass = 0; pass < DN / kCH; ++pass) {
+            uint8_t *stage = sm + (pass % C::kNBuf) * C::kStageBytes;
+            if (pass >= C::kNBuf) {  // the copies that last read this buffer are done reading
+                if (tid < 128) {
+                    if (C::kNBuf == 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    else bulk_wait_read_all();
+                }
+                __syncthreads();
+            }
 #pragma unroll 1
             for (int k = 0; k < kCH / 64; ++k) {
                 const int c = grp * (kCH / 2) + k * 32;
@@ -479,20 +490,19 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] = 0.f;
                 }
-                float4 *dst = reinterpret_cast<float4 *>(sm + row * C::kStageRow + c * 4);
+                float4 *dst = reinterpret_cast<float4 *>(stage + row * C::kStageRow + c * 4);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             }
             fence_async_smem();
             __syncthreads();
             if (tid < 128) {  // thread t owns pixel t
-                if (inside) bulk_s2g(feat + pix * D + d0 + pass * kCH, stage_s + tid * C::kStageRow, kCH * 4);
+                if (inside)
+                    bulk_s2g(feat + pix * D + d0 + pass * kCH, smem_u32(stage + tid * C::kStageRow), kCH * 4);
                 bulk_commit();
-                bulk_wait_read_all();
             }
-            __syncthreads();
         }
-        if (tid < 128) bulk_wait_all();
+        if (tid < 128) bulk_wait_read_all();
         if (chunk == 0) {
             if (grp == 1) {
                 xRgb[3 * pidx] = cr;
