@@ -425,6 +425,89 @@ class CapturedStep:
         return self.outputs
 
 
+class HostPipeline:
+    """Forward + backward over inputs that live in (pinned) host memory, with
+    the copies overlapped: step k's inputs go host -> device on a copy stream
+    while step k-1 computes, and each step's outputs go device -> host on a
+    second copy stream while the next step computes.  Device inputs and host
+    outputs are double-buffered; events order every reuse.
+
+    inputs: dict of pinned host tensors named means, scales, quats,
+    opacities, sh, features, grad_rgb, grad_feat.  step() queues one step and
+    returns the pinned host tensors it will fill (rgb, feat, then the
+    gradients); they are valid after finish() or once the step two later has
+    been queued and synchronised, and are reused by the step two later."""
+
+    NAMES = ("means", "scales", "quats", "opacities", "sh", "features", "grad_rgb", "grad_feat")
+
+    def __init__(self, rast: Rasterizer, cams: Sequence[dict], inputs: dict):
+        self.rast, self.cams = rast, list(cams)
+        dev = rast.dev
+        self.h_in = {k: inputs[k] for k in self.NAMES}
+        self.d_in = [{k: torch.empty_like(v, device=dev) for k, v in self.h_in.items()} for _ in range(2)]
+        self.s_h2d = torch.cuda.Stream(device=dev)
+        self.s_cmp = torch.cuda.Stream(device=dev)
+        self.s_d2h = torch.cuda.Stream(device=dev)
+        self.ev_in = [torch.cuda.Event() for _ in range(2)]  # inputs of slot j copied in
+        self.ev_used = [None, None]                          # slot j's inputs consumed
+        self.ev_out = [None, None]                           # host outputs of slot j copied out
+        self.h_out = [None, None]
+        self.k = 0
+
+    def start(self):
+        """Order the pipeline's streams after the current stream (e.g. after
+        a timing event)."""
+        cur = torch.cuda.current_stream(self.rast.dev)
+        for st in (self.s_h2d, self.s_cmp, self.s_d2h):
+            st.wait_stream(cur)
+
+    def step(self):
+        j = self.k % 2
+        d = self.d_in[j]
+        with torch.cuda.stream(self.s_h2d):
+            if self.ev_used[j] is not None:
+                self.s_h2d.wait_event(self.ev_used[j])
+            for name, h in self.h_in.items():
+                d[name].copy_(h, non_blocking=True)
+            self.ev_in[j].record(self.s_h2d)
+        with torch.cuda.stream(self.s_cmp):
+            self.s_cmp.wait_event(self.ev_in[j])
+            st = self.rast.prepare(d["means"], d["scales"], d["quats"], d["opacities"], d["sh"], self.cams,
+                                   check=False)
+            rgb, feat = self.rast.forward(st, d["features"])
+            grads = self.rast.backward(st, d["grad_rgb"], d["grad_feat"])
+            outs = [rgb, feat] + [v for v in grads.values() if v is not None]
+            used = torch.cuda.Event()
+            used.record(self.s_cmp)
+            self.ev_used[j] = used
+        if self.h_out[j] is None:
+            self.h_out[j] = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+        with torch.cuda.stream(self.s_d2h):
+            self.s_d2h.wait_event(used)
+            if self.ev_out[j] is not None:
+                self.s_d2h.wait_event(self.ev_out[j])
+            for o, ho in zip(outs, self.h_out[j]):
+                o.record_stream(self.s_d2h)
+                ho.copy_(o, non_blocking=True)
+            self.ev_out[j] = torch.cuda.Event()
+            self.ev_out[j].record(self.s_d2h)
+        for t in d.values():
+            t.record_stream(self.s_cmp)
+        self.k += 1
+        return self.h_out[j]
+
+    def finish(self):
+        """Order the current stream after everything queued."""
+        cur = torch.cuda.current_stream(self.rast.dev)
+        for st in (self.s_h2d, self.s_cmp, self.s_d2h):
+            cur.wait_stream(st)
+
+    def bytes_per_step(self):
+        h2d = sum(v.numel() * v.element_size() for v in self.h_in.values())
+        d2h = sum(v.numel() * v.element_size() for v in (self.h_out[0] or []))
+        return h2d, d2h
+
+
 class _RenderFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, means, scales, quats, opacities, sh, features, rast, cams):
