@@ -205,7 +205,10 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
  * FHGS_FUSE_FINALIZE then writes out[g][c] = num/den where den > 0, else 0;
  * FHGS_FUSE_NORMALIZE additionally L2-normalises each non-zero out row.
  * out may be NULL unless FINALIZE is set.  Uses context scratch; views are
- * processed one at a time. */
+ * processed one at a time.  p->path: FHGS_PATH_FP32 sums on the CUDA cores;
+ * FHGS_PATH_AUTO and FHGS_PATH_TC use the tensor cores when D % 64 == 0
+ * (weights and maps as BF16 hi + lo, ~16-bit products, FP32 accumulation;
+ * FHGS_PATH_TC with another D returns FHGS_ERR_UNSUPPORTED). */
 enum { FHGS_FUSE_ACCUMULATE = 1, FHGS_FUSE_FINALIZE = 2, FHGS_FUSE_NORMALIZE = 4 };
 fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhgs_camera *views, int n_views,
                                const float *const *maps, int D, const fhgs_params *p, float *num,

@@ -502,6 +502,10 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
         FHGS_CUDA(ctx, cudaMemsetAsync(den, 0, sizeof(float) * (size_t)n, st));
     }
     const Params q = make_params(p);
+    // tensor cores unless the FP32 path is asked for (needs D % 64 == 0)
+    if (p->path == FHGS_PATH_TC && !fuse_tc_dn(D))
+        return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core fusion needs D % 64 == 0");
+    const bool fuse_tc = p->path != FHGS_PATH_FP32 && fuse_tc_dn(D) != 0;
     if ((s = ensure(ctx, ctx->fuse_proj, proj_bytes(n))) != FHGS_OK) return s;
     if ((s = ensure(ctx, ctx->fuse_count, 256)) != FHGS_OK) return s;
     for (int v = 0; v < n_views && n > 0; ++v) {
@@ -534,8 +538,13 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
             FHGS_CUDA(ctx, cudaMemcpyAsync(&count, b.n_instances, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
             FHGS_CUDA(ctx, cudaStreamSynchronize(st));
             if (count <= b.capacity) {
-                Prof pr(ctx, "fuse_fp32", st);
-                launch_fuse_fp32(n, cs, q, pv, b, maps[v], D, num, den, st);
+                if (fuse_tc) {
+                    Prof pr(ctx, "fuse_tc", st);
+                    launch_fuse_tc(n, cs, q, pv, b, maps[v], D, num, den, ctx->status, st);
+                } else {
+                    Prof pr(ctx, "fuse_fp32", st);
+                    launch_fuse_fp32(n, cs, q, pv, b, maps[v], D, num, den, st);
+                }
                 break;
             }
             if (count > 0xFFFFFFFFll) return fail(ctx, FHGS_ERR_CAPACITY, "too many instances in one view");

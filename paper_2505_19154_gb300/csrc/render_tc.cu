@@ -1089,6 +1089,351 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0) tmem_dealloc(taddr, C::kTmemCols);
 }
 
+// ------------------------------------------------------------- fusion
+// Feature fusion of one view (Sec. 3.1): num[g][c] += sum_p w_g(p) F(p)[c]
+// and den[g] += sum_p w_g(p), with w the Eq. 4 weights.  Per half tile and
+// slice of DN map columns the map tile (128 px x DN, FP32) is split once into
+// BF16 hi + lo; per batch of 64 Gaussians the weights, walked front to back as
+// in the forward, are split into BF16 hi + lo as well, and
+//   num_b (64 g x DN) = Wh^T Mh + Wh^T Ml + Wl^T Mh,   den_b = (Wh + Wl)^T 1
+// accumulate in TMEM (M = 128 with the batch's Gaussians in rows 0..63), so
+// every product carries about 16 mantissa bits.  Batch b's block is drained
+// into num/den (vector atomics on contiguous rows) while batch b+1 is weighed.
+template <int DN>
+struct FuseCfg {
+    static constexpr int kNBlk = DN / 64;
+    static constexpr int kOffWh = 0;                            // [128 px][64 g] BF16, MN-major A
+    static constexpr int kOffWl = kOffWh + 128 * 128;           // (Wh's unused second M block reads it)
+    static constexpr int kOffMh = kOffWl + 128 * 128;           // [DN/64][128 px][64] BF16, MN-major B
+    static constexpr int kOffMl = kOffMh + kNBlk * 128 * 128;
+    static constexpr int kOffOne = kOffMl + kNBlk * 128 * 128;  // [2 K-blocks][16 rows][64 px]: row 0 = 1
+    static constexpr int kRecBytes = kFB * 48;
+    static constexpr int kOffRec = kOffOne + 2 * 16 * 128;
+    static constexpr int kOffGid = kOffRec + 2 * kRecBytes;      // [4][64] ids: the drain of b-1 reads them late
+    static constexpr int kOffMask = kOffGid + 4 * kFB * 4;      // [2 batches][2 groups] contributors
+    static constexpr int kOffX = kOffMask + 16;                  // per pixel: T, done, P0
+    static constexpr int kOffBar = kOffX + 128 * 3 * 4;
+    static constexpr int kSmem = 1024 + kOffBar + 64;
+    static constexpr int kColDen = DN;                           // den in 16 columns after num
+    static constexpr int kTmemCols = DN + 16 <= 128 ? 128 : (DN + 16 <= 256 ? 256 : 512);
+    static_assert(kSmem <= 232448, "fusion CTA exceeds the opt-in shared memory");
+};
+
+template <int DN>
+__global__ void __launch_bounds__(256, 1)
+    k_fuse_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
+              const uint32_t *__restrict__ ranges, const float *__restrict__ fmap, int D, float *num, float *den,
+              unsigned *status) {
+    using C = FuseCfg<DN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = align_smem_1024(smem_raw);
+    uint8_t *sWh = sm + C::kOffWh;
+    uint8_t *sWl = sm + C::kOffWl;
+    uint8_t *sMh = sm + C::kOffMh;
+    uint8_t *sMl = sm + C::kOffMl;
+    uint8_t *sOne = sm + C::kOffOne;
+    float *xT = reinterpret_cast<float *>(sm + C::kOffX);
+    int *xDone = reinterpret_cast<int *>(xT + 128);
+    float *xP0 = reinterpret_cast<float *>(xDone + 128);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + C::kOffBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    auto srec = [&](int b) { return reinterpret_cast<GRec *>(sm + C::kOffRec + (b & 1) * C::kRecBytes); };
+    auto sgid = [&](int b) { return reinterpret_cast<uint32_t *>(sm + C::kOffGid + (b & 3) * kFB * 4); };
+    auto sMask = [&](int b) { return reinterpret_cast<uint32_t *>(sm + C::kOffMask) + (b & 1) * 2; };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, grp = tid >> 7, pidx = tid & 127;
+    const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, chunk = blockIdx.y;
+    const int ci = cam_of_tile(cs, tile);
+    const DevCam &cam = cs.c[ci];
+    const int lt = tile - cam.tile_off;
+    const int x0 = (lt % cam.tiles_x) * kTile, y0 = (lt / cam.tiles_x) * kTile + half * 8;
+    const int px = x0 + (pidx & 15), py = y0 + (pidx >> 4);
+    const bool inside = px < cam.W && py < cam.H;
+    const uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+    const int nbatches = (int)((e - s + kFB - 1) / kFB);
+    const int d0 = chunk * DN;
+    const GRec *rec = pv.rec + (long long)ci * N;
+    if (nbatches == 0) return;  // uniform over the CTA: nothing to fuse
+
+    if (warp == 0) tmem_alloc(tslot, C::kTmemCols);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        fence_mbar_init();
+    }
+    if (grp == 0) {
+        xT[pidx] = 1.f;
+        xDone[pidx] = inside ? 0 : 1;
+    }
+    if (tid < 4) sMask(0)[tid] = 0u;  // both batch slots
+    // ones operand: B (K = pixels, N = 16), K-major, row 0 = 1
+    for (int q = tid; q < 16 * 128; q += 256) {
+        const int n = q >> 7, pp = q & 127;
+        *reinterpret_cast<__nv_bfloat16 *>(sOne + (pp >> 6) * (16 * 128) + swz(n, (pp & 63) >> 3) + 2 * (pp & 7)) =
+            __float2bfloat16_rn(n == 0 ? 1.f : 0.f);
+    }
+    // map tile of this CTA's pixels -> BF16 hi / lo, MN-major swizzled
+    {
+        constexpr int kL = DN >= 128 ? DN / 128 : 1;
+#pragma unroll 1
+        for (int r0 = 0; r0 < 16; r0 += 8) {
+            float4 v[8][kL];
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) {
+                const int prow = warp * 16 + r0 + rr;
+                const int qx = x0 + (prow & 15), qy = y0 + (prow >> 4);
+                const bool qin = qx < cam.W && qy < cam.H;
+                const float *src = fmap + ((long long)qy * cam.W + qx) * D + d0;
+#pragma unroll
+                for (int li = 0; li < kL; ++li) {
+                    const int f = li * 128 + lane * 4;
+                    v[rr][li] = (qin && f < DN) ? *reinterpret_cast<const float4 *>(src + f)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) {
+                const int prow = warp * 16 + r0 + rr;
+#pragma unroll
+                for (int li = 0; li < kL; ++li) {
+                    const int f = li * 128 + lane * 4;
+                    if (f >= DN) continue;
+                    const float4 x = v[rr][li];
+                    const __nv_bfloat162 h01 = __floats2bfloat162_rn(x.x, x.y);
+                    const __nv_bfloat162 h23 = __floats2bfloat162_rn(x.z, x.w);
+                    const float2 b01 = __bfloat1622float2(h01), b23 = __bfloat1622float2(h23);
+                    const __nv_bfloat162 l01 = __floats2bfloat162_rn(x.x - b01.x, x.y - b01.y);
+                    const __nv_bfloat162 l23 = __floats2bfloat162_rn(x.z - b23.x, x.w - b23.y);
+                    const uint32_t off = (f >> 6) * (128 * 128) + swz(prow, (f & 63) >> 3) + ((f & 7) ? 8 : 0);
+                    uint2 hv, lv;
+                    hv.x = *reinterpret_cast<const uint32_t *>(&h01);
+                    hv.y = *reinterpret_cast<const uint32_t *>(&h23);
+                    lv.x = *reinterpret_cast<const uint32_t *>(&l01);
+                    lv.y = *reinterpret_cast<const uint32_t *>(&l23);
+                    *reinterpret_cast<uint2 *>(sMh + off) = hv;
+                    *reinterpret_cast<uint2 *>(sMl + off) = lv;
+                }
+            }
+        }
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t taddr = *tslot;
+    const uint32_t tNum = taddr, tDen = taddr + C::kColDen;
+    const uint32_t sWh_s = smem_u32(sWh), sWl_s = smem_u32(sWl), sMh_s = smem_u32(sMh), sMl_s = smem_u32(sMl);
+    const uint32_t sOne_s = smem_u32(sOne);
+    constexpr uint32_t idN = idesc_bf16(128, DN, true, true);
+    constexpr uint32_t idD = idesc_bf16(128, 16, true, false);
+
+    auto load_gid = [&](int b) {
+        if (b < nbatches && tid < kFB) {
+            const uint32_t at = s + (uint32_t)b * kFB + tid;
+            cp_async4(smem_u32(sgid(b) + tid), gids + (at < e ? at : s), at < e);
+        }
+        cp_async_commit();
+    };
+    auto load_rec = [&](int b) {
+        if (b < nbatches && tid < kFB) {
+            const bool v = s + (uint32_t)b * kFB + tid < e;
+            const uint32_t dst = smem_u32(srec(b) + tid);
+            const GRec *src = rec + (v ? sgid(b)[tid] : 0u);
+            cp_async16(dst, &src->a, v);
+            cp_async16(dst + 16, &src->b, v);
+            cp_async16(dst + 32, &src->c, v);
+        }
+        cp_async_commit();
+    };
+    auto issue = [&]() {  // num_b and den_b of the batch whose weights are staged
+        tc_after();
+#pragma unroll
+        for (int ks = 0; ks < 128 / 16; ++ks) {
+            const uint64_t ah = sdesc(sWh_s + ks * 2048, 128 * 128, 1024);
+            const uint64_t al = sdesc(sWl_s + ks * 2048, 128 * 128, 1024);
+            const uint64_t bh = sdesc(sMh_s + ks * 2048, 128 * 128, 1024);
+            const uint64_t bl = sdesc(sMl_s + ks * 2048, 128 * 128, 1024);
+            const uint64_t bo = sdesc(sOne_s + (ks >> 2) * (16 * 128) + (ks & 3) * 32, 16, 1024);
+            mma_bf16(tNum, ah, bh, idN, ks > 0 ? 1u : 0u);
+            mma_bf16(tNum, ah, bl, idN, 1u);
+            mma_bf16(tNum, al, bh, idN, 1u);
+            mma_bf16(tDen, ah, bo, idD, ks > 0 ? 1u : 0u);
+            mma_bf16(tDen, al, bo, idD, 1u);
+        }
+        mma_commit(&bar[0]);
+    };
+    // batch db's block: den (slice 0) and num rows of the contributing Gaussians
+    auto drain = [&](int db) {
+        const int dnb = (int)min((uint32_t)kFB, e - (s + (uint32_t)db * kFB));
+        if ((warp & 3) < 2) {
+            const int h = warp & 1;
+            const uint32_t wmask = sMask(db)[h] & (dnb >= h * 32 + 32 ? 0xFFFFFFFFu
+                                   : (dnb > h * 32 ? (1u << (dnb - h * 32)) - 1u : 0u));
+            const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+            if (grp == 0 && chunk == 0) {
+                float dv[16];
+                tmem_ld16(tDen + lanes, dv);
+                if ((wmask >> lane) & 1u) atomicAdd(den + sgid(db)[h * 32 + lane], dv[0]);
+            }
+            if (wmask) {
+                float *stage = reinterpret_cast<float *>(sWh) + (h + 2 * grp) * (32 * 36);
+                const int sub = lane >> 3, q4 = (lane & 7) * 4;
+#pragma unroll 1
+                for (int cc = 0; cc < DN / 64; ++cc) {
+                    float v[32];
+                    tmem_ld32(tNum + lanes + grp * (DN / 2) + cc * 32, v);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        *reinterpret_cast<float4 *>(stage + lane * 36 + 4 * i) =
+                            make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    __syncwarp();
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int jj = it * 4 + sub;
+                        if ((wmask >> jj) & 1u) {
+                            const uint32_t g = sgid(db)[h * 32 + jj];
+                            atomicAdd(reinterpret_cast<float4 *>(num + (size_t)g * D + d0 + grp * (DN / 2) +
+                                                                 cc * 32 + q4),
+                                      *reinterpret_cast<const float4 *>(stage + jj * 36 + q4));
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+    };
+
+    const float fpx = px + 0.5f, fpy = py + 0.5f;
+    uint32_t ph = 0u;
+    bool pend = false, timeout = false;
+    int nb_done = 0;  // batches whose MMAs were issued
+    load_gid(0);
+    load_gid(1);
+    cp_async_wait<1>();
+    __syncthreads();
+    load_rec(0);
+    for (int b = 0; b < nbatches; ++b) {
+        const uint32_t base = s + (uint32_t)b * kFB;
+        const int nb = (int)min((uint32_t)kFB, e - base);
+        // the newest groups are [ids b+1, records b] (and, from b = 1, the two
+        // issued one batch ago): all have landed after this wait
+        cp_async_wait<0>();
+        __syncthreads();
+        load_gid(b + 2);
+        load_rec(b + 1);
+        const float T_in = xT[pidx];
+        const bool done_in = xDone[pidx] != 0;
+        const GRec *R = srec(b);
+        float a[32], l[32];
+        float P = 1.f;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+            const int j = grp * 32 + jj;
+            const float4 A4 = R[j].a, B4 = R[j].b;
+            const float dx = fpx - A4.x, dy = fpy - A4.y;
+            const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
+            const float al = fminf(p.amax, B4.y * __expf(-0.5f * q2));
+            a[jj] = (j < nb && q2 <= p.cut && al >= p.amin) ? al : 0.f;
+            l[jj] = P;
+            P *= 1.f - a[jj];
+        }
+        if (grp == 0) xP0[pidx] = P;
+        // the previous batch's MMAs are done: drain their block
+        bool ok = true;
+        if (pend) {
+            ok = mbar_wait(&bar[0], ph);
+            if (ok) {
+                ph ^= 1u;
+                pend = false;
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+            break;
+        }
+        if (b >= 1) {
+            tc_after();
+            drain(b - 1);
+            tc_before();
+        }
+        __syncthreads();  // the drain's staging (in the weight buffers) is free again
+        if (tid < 2) sMask(b - 1)[tid] = 0u;
+        // weights: group 1 starts from T_in P_0 unless group 0 stops
+        const float P0 = xP0[pidx];
+        const bool stop0 = !done_in && T_in * P0 < p.teps;
+        const float Ts = grp == 0 ? T_in : T_in * P0;
+        bool done = grp == 0 ? done_in : (done_in || stop0);
+        const bool owner = grp == 0 ? (done_in || stop0) : !(done_in || stop0);
+        float Tstop = 0.f;
+        uint32_t cmask = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float w8[8];
+#pragma unroll
+            for (int hh = 0; hh < 8; ++hh) {
+                const int jj = 8 * q + hh;
+                const float Tj = Ts * l[jj];
+                const float Tn = Ts * (jj < 31 ? l[jj + 1] : P);
+                bool okj = a[jj] > 0.f && !done;
+                const bool stop = okj && Tn < p.teps;
+                if (stop) Tstop = Tj;
+                done = done || stop;
+                okj = okj && !stop;
+                w8[hh] = okj ? a[jj] * Tj : 0.f;
+                cmask |= (okj ? 1u : 0u) << jj;
+            }
+            uint4 ph4, pl4;
+            uint32_t *phv = &ph4.x, *plv = &pl4.x;
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) {
+                const __nv_bfloat162 hi = __floats2bfloat162_rn(w8[2 * hh], w8[2 * hh + 1]);
+                const float2 hb = __bfloat1622float2(hi);
+                phv[hh] = *reinterpret_cast<const uint32_t *>(&hi);
+                plv[hh] = pack_bf16(w8[2 * hh] - hb.x, w8[2 * hh + 1] - hb.y);
+            }
+            const uint32_t off = swz(pidx, grp * 4 + q);
+            *reinterpret_cast<uint4 *>(sWh + off) = ph4;
+            *reinterpret_cast<uint4 *>(sWl + off) = pl4;
+        }
+        cmask = __reduce_or_sync(0xffffffffu, cmask);
+        if (lane == 0 && cmask) atomicOr(&sMask(b)[grp], cmask);
+        if (owner) {
+            if (grp == 0) {
+                xT[pidx] = done_in ? T_in : Tstop;
+                xDone[pidx] = 1;
+            } else {
+                xT[pidx] = done ? Tstop : Ts * P;
+                xDone[pidx] = done ? 1 : 0;
+            }
+        }
+        fence_async_smem();
+        const int all_done = __syncthreads_and(grp == 0 || done);
+        if (tid == 0) issue();
+        pend = true;
+        ++nb_done;
+        if (all_done) break;
+    }
+    cp_async_wait_all();
+    if (!timeout && pend) {
+        const bool ok = mbar_wait(&bar[0], ph);
+        if (ok) {
+            ph ^= 1u;
+            pend = false;
+        }
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+        } else {
+            tc_after();
+            drain(nb_done - 1);
+        }
+    }
+    if (timeout) {
+        if (tid == 0) latch(status, ST_TIMEOUT);
+        if (pend) mbar_wait(&bar[0], ph);
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, C::kTmemCols);
+}
+
 int pick_fwd_dn(int D, int d_split) {
     if (d_split == 64 || d_split == 128 || d_split == 256 || d_split == 512) return (D % d_split == 0) ? d_split : 0;
     for (int dn = 512; dn >= 64; dn >>= 1)
@@ -1173,6 +1518,35 @@ void launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
         default: break;
     }
 #undef FHGS_BWD
+}
+
+int fuse_tc_dn(int D) {
+    if (D % 256 == 0) return 256;
+    if (D % 128 == 0) return 128;
+    if (D % 64 == 0) return 64;
+    return 0;
+}
+
+void launch_fuse_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                    const float *fmap, int D, float *num, float *den, unsigned *status, cudaStream_t st) {
+    const int dn = fuse_tc_dn(D);
+    dim3 grid(cs.total_tiles * 2, D / dn);
+    note_launch(1);
+#define FHGS_FUSE(DNV)                                                                                         \
+    case DNV: {                                                                                                \
+        static std::atomic<unsigned long long> smem_done{0};                                                 \
+        allow_max_smem(smem_done, k_fuse_tc<DNV>);                                                           \
+        k_fuse_tc<DNV><<<grid, 256, FuseCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, fmap, D,  \
+                                                               num, den, status);                            \
+        break;                                                                                                 \
+    }
+    switch (dn) {
+        FHGS_FUSE(64)
+        FHGS_FUSE(128)
+        FHGS_FUSE(256)
+        default: break;
+    }
+#undef FHGS_FUSE
 }
 
 }  // namespace fhgs

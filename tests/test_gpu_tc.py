@@ -99,3 +99,42 @@ def test_tc_config2_forward_backward():
     ref = oracle.backward(scene, cams, prm, scene["features"], [dC], [dF], prep=prep)
     check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities", "sh"), tol=1e-3)
     check_grads(out["grads"], ref, keys=("features",), tol=1e-2)
+
+
+@pytest.mark.parametrize("D", [128, 192])
+def test_tc_fusion_small_against_oracle_and_fp32_path(D):
+    """Tensor-core fusion (one D slice at 128, three at 192) against the
+    oracle composited over the FP32 specification's footprints, with the
+    fusion margin rule; and against the FP32 CUDA-core fusion."""
+    sc = small_random_scene(2500, seed=33, sh_degree=1, D=0, spread=0.5)
+    sc = {k: (np.asarray(v, np.float32) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+    views = [synth.look_at_camera(synth.ring_position(3.0, a, e), w, h)
+             for a, e, w, h in [(10, 5, 80, 48), (130, -10, 64, 72), (250, 20, 50, 40)]]
+    prm = dict(sh_degree=1)
+    g = np.random.default_rng(4)
+    maps = [g.normal(size=(v["height"], v["width"], D)).astype(np.float32) for v in views]
+    prep = oracle.prepare(sc, views, prm, geometry="fp32")
+    ref = oracle.fuse(sc, views, maps, prm, prep=prep)
+    t = {k: _t(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    dmaps = [_t(m).view(-1, D) for m in maps]
+    outs = {}
+    for path in (api.PATH_TC, api.PATH_FP32):
+        rast = api.Rasterizer(0, sh_degree=1, path=path)
+        rast.ctx.profile(True)
+        o, n_, d_ = rast.fuse(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], views, dmaps)
+        torch.cuda.synchronize()
+        assert rast.ctx.sync_status() == api.OK
+        prof = rast.ctx.profile_read()
+        assert ("fuse_tc" if path == api.PATH_TC else "fuse_fp32") in prof, prof
+        outs[path] = (o.cpu().numpy().astype(np.float64), d_.cpu().numpy().astype(np.float64))
+    seen = ref["den"] > 1e-6
+    assert seen.sum() > 300
+    fn = np.maximum(np.linalg.norm(ref["out"], axis=1), 1e-30)
+    risk = 2.0 * ref["wflip"] / np.maximum(ref["den"], 1e-30) / fn
+    for path, (o, d_) in outs.items():
+        rel = np.linalg.norm(o - ref["out"], axis=1) / fn
+        chk = seen & (risk <= 1e-4)
+        assert rel[chk].max() <= 1e-4, (path, rel[chk].max())
+        assert np.all(rel[seen] <= 1e-4 + risk[seen]), path
+        assert np.abs(d_ - ref["den"]).max() <= 1e-4 * max(1.0, ref["den"].max()), path
+        assert np.all(o[ref["den"] == 0] == 0), path
