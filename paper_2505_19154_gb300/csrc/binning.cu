@@ -222,8 +222,18 @@ bool radix_sort_pairs(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, lo
 // One block per (segment, camera): per-tile counts of the segment's Gaussians
 // via a 2-D difference array of the camera's tile grid.  Writes
 // table[(tile_off + tile) * S + seg].
-__global__ void __launch_bounds__(256) k_seg_count(const uint32_t *__restrict__ order, ProjView pv, long long N,
-                                                   int SEG, int S, CamSet cs, uint32_t *table) {
+// Tile rectangles in sorted order (empty rectangle for culled entries), so
+// that the per-segment passes below read them sequentially.
+__global__ void __launch_bounds__(256) k_gather_rects(const uint32_t *__restrict__ order, ProjView pv, long long cn,
+                                                      int4 *rect) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cn) return;
+    const uint32_t e = order[i];
+    rect[i] = pv.ntiles[e] ? pv.trect[e] : make_int4(0, 0, -1, -1);
+}
+
+__global__ void __launch_bounds__(256) k_seg_count(const int4 *__restrict__ rect, long long N, int SEG, int S,
+                                                   CamSet cs, uint32_t *table) {
     extern __shared__ int diff[];
     const int seg = blockIdx.x, ci = blockIdx.y;
     const DevCam &cam = cs.c[ci];
@@ -234,9 +244,8 @@ __global__ void __launch_bounds__(256) k_seg_count(const uint32_t *__restrict__ 
     const long long b0 = (long long)ci * N + (long long)seg * SEG;
     const long long b1 = min((long long)(ci + 1) * N, b0 + SEG);
     for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-        const uint32_t e = order[i];
-        if (pv.ntiles[e] == 0) continue;
-        const int4 r = pv.trect[e];
+        const int4 r = rect[i];
+        if (r.w < r.y) continue;
         atomicAdd(&diff[r.y * pitch + r.x], 1);
         atomicAdd(&diff[r.y * pitch + r.z + 1], -1);
         atomicAdd(&diff[(r.w + 1) * pitch + r.x], -1);
@@ -329,7 +338,8 @@ constexpr int kScatterCtr = 8192;  // tile counters per warp at most: 143 KB per
 // segments give each (tile, segment) run many consecutive entries (whole
 // sectors per write burst); bands restore the parallelism.  Within one
 // Gaussian all tiles differ, so the 32 lanes update distinct counters.
-__global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32_t *__restrict__ order, ProjView pv,
+__global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32_t *__restrict__ order,
+                                                                     const int4 *__restrict__ rect,
                                                                      long long N, int SEG, int S, int nband,
                                                                      int band_rows, CamSet cs,
                                                                      const uint32_t *__restrict__ table, uint32_t *gids,
@@ -362,12 +372,10 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32
             int4 r = make_int4(0, 0, -1, -1);
             uint32_t e = 0;
             if (k < m) {
+                r = rect[c0 + k];
                 e = order[c0 + k];
-                if (pv.ntiles[e]) {
-                    r = pv.trect[e];
-                    r.y = max(r.y, by0);
-                    r.w = min(r.w, by1 - 1);
-                }
+                r.y = max(r.y, by0);
+                r.w = min(r.w, by1 - 1);
             }
             const bool touch = r.w >= r.y;
             const uint32_t bal = __ballot_sync(0xffffffffu, touch);
@@ -438,7 +446,8 @@ size_t bin_scratch_bytes(long long N, int n_cams, int total_tiles, int sm_count)
     const long long S = (N + SEG - 1) / SEG;
     const long long tab = (long long)total_tiles * (S > 0 ? S : 1);
     const int G = 2 * sm_count;
-    return 4 * align_up(sizeof(uint32_t) * (cn + 1), 256) + align_up(sizeof(uint32_t) * (tab + 1), 256) +
+    return 4 * align_up(sizeof(uint32_t) * (cn + 1), 256) + align_up(sizeof(int4) * (cn + 1), 256) +
+           align_up(sizeof(uint32_t) * (tab + 1), 256) +
            align_up(sizeof(uint32_t) * ((tab + kScanTile - 1) / kScanTile + 1), 256) +
            align_up(sizeof(uint32_t) * kBuckets * (size_t)G, 256) + 256;
 }
@@ -459,6 +468,7 @@ BinScratch bin_scratch_view(void *base, long long N, int n_cams, int total_tiles
     s.dv_a = take(sizeof(uint32_t) * (cn + 1));
     s.dk_b = take(sizeof(uint32_t) * (cn + 1));
     s.dv_b = take(sizeof(uint32_t) * (cn + 1));
+    s.rect = reinterpret_cast<int4 *>(take(sizeof(int4) * (cn + 1)));
     s.table = take(sizeof(uint32_t) * (tab + 1));
     s.partials = take(sizeof(uint32_t) * ((tab + kScanTile - 1) / kScanTile + 1));
     s.hist = take(sizeof(uint32_t) * kBuckets * (size_t)(2 * sm_count));
@@ -489,6 +499,8 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
         while ((1 << bits) < n_cams) ++bits;
         if (radix_sort_pairs(ck, order, ok2, ov2, cn, bits, sc.hist, G, st)) order = ov2;
     }
+    note_launch(1);
+    k_gather_rects<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(order, pv, cn, sc.rect);
     // 2. per-segment tile counts
     const int SEG = sc.seg, S = sc.nseg;
     int max_cells = 0;
@@ -497,7 +509,7 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
     static std::atomic<unsigned long long> count_done{0};
     allow_max_smem(count_done, k_seg_count);
     note_launch(1);
-    k_seg_count<<<dim3(S, n_cams), 256, count_smem, st>>>(order, pv, N, SEG, S, cs, sc.table);
+    k_seg_count<<<dim3(S, n_cams), 256, count_smem, st>>>(sc.rect, N, SEG, S, cs, sc.table);
     // 3. scan of the (tile, segment) table: segment offsets and the total
     const long long tab = (long long)cs.total_tiles * S;
     const unsigned nparts = (unsigned)((tab + kScanTile - 1) / kScanTile);
@@ -516,7 +528,7 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
         max_ty = max(max_ty, cs.c[c].tiles_y);
         max_tx = max(max_tx, cs.c[c].tiles_x);
     }
-    const long long want = 32ll * sc.sm_count;  // warps
+    const long long want = 128ll * sc.sm_count;  // warps
     int nband = (int)min((long long)max_ty, (want + (long long)S * n_cams - 1) / ((long long)S * n_cams));
     nband = max(nband, 1);
     // at most kScatterCtr counters per warp (tiles_x <= 4096 keeps one row)
@@ -529,7 +541,8 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
     note_launch(1);
     const long long items = (long long)S * nband;
     k_seg_scatter<<<dim3((unsigned)((items + kScatterWarps - 1) / kScatterWarps), n_cams), kScatterWarps * 32,
-                    scat_smem, st>>>(order, pv, N, SEG, S, nband, band_rows, cs, sc.table, bins.gids, bins.capacity);
+                    scat_smem, st>>>(order, sc.rect, N, SEG, S, nband, band_rows, cs, sc.table, bins.gids,
+                                     bins.capacity);
     if (bins.keys) {
         note_launch(1);
         k_keys64<<<cs.total_tiles, 256, 0, st>>>(bins.ranges, bins.gids, pv, N, cs, bins.keys);

@@ -145,6 +145,7 @@ void launch_project_bwd(const fhgs_gaussians &g, const CamSet &cs, const Params 
 // binning (binning.cu)
 struct BinScratch {
     uint32_t *dk_a, *dv_a, *dk_b, *dv_b;  // depth sort [C*N]
+    int4 *rect;                           // tile rectangles in sorted order [C*N]
     uint32_t *table;                      // per (tile, segment) counts, then offsets
     uint32_t *partials;                   // scan partials of the table
     uint32_t *hist;                       // radix histogram [256][G]
