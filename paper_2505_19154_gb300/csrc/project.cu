@@ -288,10 +288,35 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ m
                                                      float *gquats, float *gopac, float *gsh) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N) return;
+    const int K = p.K;
+    // every gradient is linear in the footprint gradients: a Gaussian that no
+    // tile composited (all of them zero) gets exact zeros, without reading
+    // its parameters
+    bool touched = false;
+    for (int ci = 0; ci < cs.n && !touched; ++ci) {
+        const long long e = (long long)ci * N + g;
+        if (pv.ntiles[e] == 0) continue;
+        const float *gg = g2d + 12 * e;
+        const float4 ga = *reinterpret_cast<const float4 *>(gg);
+        const float4 gb = *reinterpret_cast<const float4 *>(gg + 4);
+        touched = ga.x != 0.f || ga.y != 0.f || ga.z != 0.f || ga.w != 0.f || gb.x != 0.f || gb.y != 0.f ||
+                  gb.z != 0.f || gb.w != 0.f || gg[8] != 0.f;
+    }
+    if (!touched) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            gmeans[3 * g + j] = 0.f;
+            gscales[3 * g + j] = 0.f;
+        }
+        reinterpret_cast<float4 *>(gquats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        gopac[g] = 0.f;
+        float *gshg = gsh + (long long)3 * K * g;
+        for (int i = 0; i < 3 * K; ++i) gshg[i] = 0.f;
+        return;
+    }
     const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
     const float s[3] = {scales[3 * g], scales[3 * g + 1], scales[3 * g + 2]};
     const float4 q4 = quats[g];
-    const int K = p.K;
     const float *shg = sh + (long long)3 * K * g;
     float gmu[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gop = 0.f;
     float gshv[48];

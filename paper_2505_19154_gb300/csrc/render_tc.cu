@@ -561,8 +561,9 @@ struct BwdCfg {
     static constexpr int kOffX = kOffTl + 128 * 128;
     static constexpr int kOffF = kOffX + 2 * 16 * 128;
     static constexpr int kOffRec = kOffF + kNBlk * kBB * 128;
-    static constexpr int kRecBytes = kBB * 48 + kBB * 4;
-    static constexpr int kOffRgb = kOffRec + 3 * kRecBytes;  // three record stages: b-1 (drain), b, b+1
+    static constexpr int kRecBytes = kBB * 48;
+    static constexpr int kOffGid = kOffRec + 3 * kRecBytes;  // three record stages: b-1 (drain), b, b+1
+    static constexpr int kOffRgb = kOffGid + 4 * kBB * 4;    // ids of b-1 .. b+2
     static constexpr int kOffFlag = kOffRgb + 2 * kBB * 3 * 4;  // [2 batches][64][3] colour sums
     static constexpr int kOffXch = kOffFlag + 16;          // [2 batches][2 groups] masks; then per pixel: P1, S1, T, S
     static constexpr int kOffBar = kOffXch + 128 * 16;
@@ -609,9 +610,7 @@ __global__ void __launch_bounds__(256, 1)
     // is two items later, past at least one barrier of every thread
     unsigned long long *smax = reinterpret_cast<unsigned long long *>(bars + 3);
     auto srec = [&](int stg) { return reinterpret_cast<GRec *>(sm + C::kOffRec + stg * C::kRecBytes); };
-    auto sgid = [&](int stg) {
-        return reinterpret_cast<uint32_t *>(sm + C::kOffRec + stg * C::kRecBytes + kBB * 48);
-    };
+    auto sgid = [&](int b) { return reinterpret_cast<uint32_t *>(sm + C::kOffGid + (b & 3) * kBB * 4); };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, grp = tid >> 7, pidx = tid & 127;
     const bool want_fg = gfeatures != nullptr;
@@ -684,7 +683,7 @@ __global__ void __launch_bounds__(256, 1)
                 const uint32_t wmask = sMask(db)[warp & 1] & (dnb >= (warp & 1) * 32 + 32 ? 0xFFFFFFFFu
                                        : (dnb > (warp & 1) * 32 ? (1u << (dnb - (warp & 1) * 32)) - 1u : 0u));
                 const bool mine = (wmask >> lane) & 1u;
-                const uint32_t gid = sgid(db % 3)[j];
+                const uint32_t gid = sgid(db)[j];
                 const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
                 if (grp == 0) {
                     float m[16];
@@ -727,7 +726,7 @@ __global__ void __launch_bounds__(256, 1)
                         for (int it = 0; it < 8; ++it) {
                             const int jj = it * 4 + sub;
                             if ((wmask >> jj) & 1u) {
-                                const uint32_t g = sgid(db % 3)[(warp & 1) * 32 + jj];
+                                const uint32_t g = sgid(db)[(warp & 1) * 32 + jj];
                                 atomicAdd(reinterpret_cast<float4 *>(gfeatures + (size_t)g * D + dd0 + grp * (DN / 2) +
                                                                      cc * 32 + q4),
                                           *reinterpret_cast<const float4 *>(stage + jj * 36 + q4));
@@ -829,21 +828,32 @@ __global__ void __launch_bounds__(256, 1)
         __syncthreads();
         const int Lmax = (int)min((unsigned long long)(e - s), smax[k & 1] & 0xFFFFFFFFull);
         const int nbat = (Lmax + kBB - 1) / kBB;
-    auto prefetch_rec = [&](int b, int stg) {  // Gaussian ids + records of batch b (stage b % 3)
-        const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
-        if (tid < kBB) sgid(stg)[tid] = tid < nb ? __ldg(gids + s + bs + tid) : 0u;
-        if (tid < nb) {
-            const uint32_t dst = smem_u32(srec(stg) + tid);
-            const GRec *src = rec + sgid(stg)[tid];
-            cp_async16(dst, &src->a, true);
-            cp_async16(dst + 16, &src->b, true);
-            cp_async16(dst + 32, &src->c, true);
+    // Every load helper commits one cp.async group in every thread, empty or
+    // not.  Ids run two batches ahead of use, records one (from ids already
+    // in shared memory), so no thread waits on a dependent global load.
+    auto load_gid = [&](int b) {  // ids of batch b (ring slot b & 3)
+        if (b < nbat && tid < kBB) {
+            const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
+            cp_async4(smem_u32(sgid(b) + tid), gids + s + bs + (tid < nb ? tid : 0), tid < nb);
         }
         cp_async_commit();
     };
-    auto prefetch_feat = [&](int b, int stg) {  // feature rows (reads the staged ids)
+    auto load_rec = [&](int b) {  // records of batch b (stage b % 3; its ids have landed)
+        if (b < nbat) {
+            const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
+            if (tid < nb) {
+                const uint32_t dst = smem_u32(srec(b % 3) + tid);
+                const GRec *src = rec + sgid(b)[tid];
+                cp_async16(dst, &src->a, true);
+                cp_async16(dst + 16, &src->b, true);
+                cp_async16(dst + 32, &src->c, true);
+            }
+        }
+        cp_async_commit();
+    };
+    auto prefetch_feat = [&](int b) {  // feature rows (reads the staged ids)
         const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
-        const uint32_t *ids = sgid(stg);
+        const uint32_t *ids = sgid(b);
         constexpr int kCPR = DN / 8;
 #pragma unroll 4
         for (int q = tid; q < kBB * kCPR; q += 256) {
@@ -854,7 +864,11 @@ __global__ void __launch_bounds__(256, 1)
         cp_async_commit();
     };
         if (nbat > 0) {
-            prefetch_rec(0, 0);
+            load_gid(0);
+            load_gid(1);
+            cp_async_wait_all();
+            __syncthreads();  // ids of batches 0 and 1 are staged
+            load_rec(0);
         // dF -> BF16 hi / lo, K-major swizzled
         {
 #pragma unroll
@@ -881,8 +895,7 @@ __global__ void __launch_bounds__(256, 1)
                 }
             }
         }
-            __syncthreads();  // batch 0's ids are staged
-            prefetch_feat(0, 0);
+            prefetch_feat(0);
             cp_async_wait_all();
             fence_async_smem();
             __syncthreads();
@@ -898,7 +911,8 @@ __global__ void __launch_bounds__(256, 1)
         for (int b = 0; b < nbat; ++b) {
             const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
             const bool more = b + 1 < nbat;
-            if (more) prefetch_rec(b + 1, (b + 1) % 3);
+            load_gid(b + 2);
+            load_rec(b + 1);
             {
                 const bool ok = mbar_wait(&bars[0], ph0);
                 if (ok) {
@@ -912,7 +926,7 @@ __global__ void __launch_bounds__(256, 1)
             }
             tc_after();
             // G of this batch is in TMEM: the feature stage is free for batch b+1
-            if (more) prefetch_feat(b + 1, (b + 1) % 3);
+            if (more) prefetch_feat(b + 1);
             const GRec *R = srec(b % 3);
             float Gv[32];
             tmem_ld32(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * 32, Gv);
