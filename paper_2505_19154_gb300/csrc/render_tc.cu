@@ -901,6 +901,18 @@ __global__ void __launch_bounds__(256, 1)
             __syncthreads();
             if (tid == 0) issue_G();
             pend0 = true;
+            if (nbat > 1) {  // G of batch 0 done: the feature stage takes batch 1
+                const bool ok = mbar_wait(&bars[0], ph0);
+                if (ok) {
+                    ph0 ^= 1u;
+                    pend0 = false;
+                }
+                if (__syncthreads_or(!ok)) {
+                    timeout = true;
+                    break;
+                }
+                prefetch_feat(1);
+            }
         }
 
         const float fpx = px + 0.5f, fpy = py + 0.5f;
@@ -913,7 +925,7 @@ __global__ void __launch_bounds__(256, 1)
             const bool more = b + 1 < nbat;
             load_gid(b + 2);
             load_rec(b + 1);
-            {
+            if (pend0) {  // only when this item has a single batch: later G's are waited after a recursion
                 const bool ok = mbar_wait(&bars[0], ph0);
                 if (ok) {
                     ph0 ^= 1u;
@@ -925,8 +937,6 @@ __global__ void __launch_bounds__(256, 1)
                 }
             }
             tc_after();
-            // G of this batch is in TMEM: the feature stage is free for batch b+1
-            if (more) prefetch_feat(b + 1);
             const GRec *R = srec(b % 3);
             float Gv[32];
             tmem_ld32(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * 32, Gv);
@@ -985,7 +995,22 @@ __global__ void __launch_bounds__(256, 1)
                 Gv[jj] = c ? gx[jj] * dal : 0.f;
             }
             if (grp == 1) xS1[pidx] = Sg - S;
-            __syncthreads();
+            // G of batch b+1 (issued after this batch's alphas) is done by now:
+            // the feature stage takes batch b+2, a whole iteration ahead
+            bool gok = true;
+            if (more) {
+                gok = mbar_wait(&bars[0], ph0);
+                if (gok) {
+                    ph0 ^= 1u;
+                    pend0 = false;
+                }
+            }
+            if (__syncthreads_or(!gok)) {
+                timeout = true;
+                break;
+            }
+            if (b + 2 < nbat) prefetch_feat(b + 2);
+            else cp_async_commit();
             if (grp == 0) {
                 const float Sb = S + xS1[pidx];  // suffix sum entering group 0's Gaussians
     #pragma unroll
