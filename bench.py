@@ -179,10 +179,10 @@ def composited_pairs(st, cams, tile=16):
 # source file at capture time: a changed source reports null.
 _CROP_SCALE = (1920 * 1080) / (960 * 544)
 TRAFFIC = {
-    "render_bwd_tc": {"bytes": int((1102.8e6 + 4.6e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "1742d7d40839e6bba2f18ace1f54b80cf49a7f3e75ecf42ff34bbfcc9c1fe522"},
-    "render_fwd_tc": {"bytes": int((9.0e6 + 1015.3e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "1742d7d40839e6bba2f18ace1f54b80cf49a7f3e75ecf42ff34bbfcc9c1fe522"},
+    "render_bwd_tc": {"bytes": int((1103.5e6 + 4.9e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "a87e4c871bd4d4473cfd0fbc4283e04f9ae6bd8baad902b171f12bb21189d3e3"},
+    "render_fwd_tc": {"bytes": int((9.0e6 + 1015.4e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "a87e4c871bd4d4473cfd0fbc4283e04f9ae6bd8baad902b171f12bb21189d3e3"},
 }
 
 
