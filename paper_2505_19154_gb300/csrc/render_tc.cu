@@ -226,7 +226,7 @@ struct FwdCfg {
 };
 
 template <int DN>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, DN <= 256 ? 2 : 1)
     k_render_fwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                     const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats, int D,
                     float *rgb, float *feat, float *Tout, int32_t *last_out, unsigned *status) {
@@ -541,15 +541,16 @@ __device__ __forceinline__ void rs_step(float *v, int lane, int off) {
 }
 
 // Shared-memory plan of the backward CTA (byte offsets; atoms 1024-aligned):
-//   W   [128 px][64 g] BF16 weights            (A of dFe, MN-major; A of nothing else)
-//   Dh  [DN/64][128 px][64] BF16 dF hi           (A of G, K-major; B of dFe, MN-major)
+//   W   [128 px][64 g] BF16 weights            (B of dFe^T, MN-major)
+//   Dh  [DN/64][128 px][64] BF16 dF hi           (A of G, K-major; A of dFe^T, MN-major)
 //   Dl  same, dF lo = bf16(dF - hi)
 //   Th  [128 px][64 g] BF16 t = G dL/drho, hi    (A of the moments, MN-major)
 //   Tl  same, lo
 //   X   [2 K-blocks][16 rows][64 px] BF16       (B of the moments, K-major): rows 1, i, j, i^2, i j, j^2
 //   F   [DN/64][64 g][64] BF16 feature rows      (B of G, K-major)
-// W is followed by Dh and Th by Tl: the M=128 MMAs with only 64 real rows
-// read their second M block from the next buffer and those rows are unused.
+// Th is followed by Tl (and Dh by Dl): the M=128 MMAs with only 64 real rows
+// (the moments; dFe^T at DN = 64) read their second M block from the next
+// buffer and those rows are unused.
 template <int DN>
 struct BwdCfg {
     static constexpr int kNBlk = DN / 64;
@@ -569,9 +570,9 @@ struct BwdCfg {
     static constexpr int kOffBar = kOffXch + 128 * 16;
     static constexpr int kSmem = 1024 + kOffBar + 64;
     static_assert(kSmem <= 232448, "backward CTA exceeds the opt-in shared memory");
-    static constexpr int kTmemCols = DN <= 128 ? 256 : 512;
-    static constexpr int kColM = 64;                      // moments, 16 columns
-    static constexpr int kColF = DN <= 128 ? 128 : 256;   // dFe, DN columns
+    static constexpr int kTmemCols = 256;
+    static constexpr int kColM = 64;   // moments, 16 columns
+    static constexpr int kColF = 128;  // dFe^T, 64 columns per block of 128 channels
 };
 
 // 256 threads: two groups of 4 warps share the half tile's 128 pixels; group g
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(256, 1)
     const uint32_t sTh_s = smem_u32(sTh), sTl_s = smem_u32(sTl), sX_s = smem_u32(sX);
     const uint32_t sF_s = smem_u32(sm + C::kOffF);
     constexpr uint32_t idG = idesc_bf16(128, kBB, false, false);
-    constexpr uint32_t idF = idesc_bf16(128, DN, true, true);
+    constexpr uint32_t idF = idesc_bf16(128, kBB, true, true);
     constexpr uint32_t idM = idesc_bf16(128, 16, true, false);
     auto issue_G = [&]() {  // G(px, g) = sum_d dF(px, d) Fe(g, d), hi + lo parts
         tc_after();
@@ -657,7 +658,11 @@ __global__ void __launch_bounds__(256, 1)
         }
         mma_commit(&bars[0]);
     };
-    auto issue_FM = [&]() {  // dFe = W^T dF (hi + lo) and moments = T^T X (T hi + lo)
+    // dFe^T = dF^T W, one M = 128 block of channels per MMA (TMEM lanes =
+    // channels, columns = the batch's Gaussians); for DN = 64 lanes 64..127
+    // read past the channel block and are never drained
+    constexpr int kFBlk = DN >= 128 ? DN / 128 : 1;
+    auto issue_FM = [&]() {  // dFe^T = dF^T W (dF hi) and moments = T^T X (T hi + lo)
         tc_after();
 #pragma unroll
         for (int ks = 0; ks < 128 / 16; ++ks) {
@@ -666,9 +671,13 @@ __global__ void __launch_bounds__(256, 1)
             const uint64_t bx = sdesc(sX_s + (ks >> 2) * (16 * 128) + (ks & 3) * 32, 16, 1024);
             mma_bf16(tM, am, bx, idM, ks > 0 ? 1u : 0u);
             mma_bf16(tM, al, bx, idM, 1u);
-            if (want_fg)  // the feature gradient takes dF as BF16 (its bar is the BF16 weights')
-                mma_bf16(tF, sdesc(sW_s + ks * 2048, 128 * 128, 1024), sdesc(sDh_s + ks * 2048, 128 * 128, 1024), idF,
-                         ks > 0 ? 1u : 0u);
+            if (want_fg) {  // the feature gradient takes dF as BF16 (its bar is the BF16 weights')
+                const uint64_t bw = sdesc(sW_s + ks * 2048, 128 * 128, 1024);
+#pragma unroll
+                for (int mb = 0; mb < kFBlk; ++mb)
+                    mma_bf16(tF + mb * kBB, sdesc(sDh_s + mb * 2 * (128 * 128) + ks * 2048, 128 * 128, 1024), bw, idF,
+                             ks > 0 ? 1u : 0u);
+            }
         }
         mma_commit(&bars[1]);
     };
@@ -678,64 +687,69 @@ __global__ void __launch_bounds__(256, 1)
     // the item's geometry is passed in, it may be the previous item's
     auto drain = [&](int db, int dnbat_end, int dx0, int dy0, float *dg2dc, int dchunk, int dd0) {
         const int dbe = dnbat_end - db * kBB, dnb = dbe - max(0, dbe - kBB);
-            if ((warp & 3) < 2) {  // rows 0..63 of the accumulators = the batch's Gaussians
-                const int j = (warp & 1) * 32 + lane;
-                const uint32_t wmask = sMask(db)[warp & 1] & (dnb >= (warp & 1) * 32 + 32 ? 0xFFFFFFFFu
-                                       : (dnb > (warp & 1) * 32 ? (1u << (dnb - (warp & 1) * 32)) - 1u : 0u));
-                const bool mine = (wmask >> lane) & 1u;
-                const uint32_t gid = sgid(db)[j];
-                const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-                if (grp == 0) {
-                    float m[16];
-                    tmem_ld16(tM + lanes, m);
-                    if (mine) {
-                        const GRec r = srec(db % 3)[j];
-                        // moments about the pixel grid: dx = i - a, dy = j - b
-                        const float a = r.a.x - (float)dx0 - 0.5f, bb = r.a.y - (float)dy0 - 0.5f;
-                        const float M0 = m[0], Mi = m[1], Mj = m[2], Mii = m[3], Mij = m[4], Mjj = m[5];
-                        const float Sx = Mi - a * M0, Sy = Mj - bb * M0;
-                        const float Sxx = Mii - 2.f * a * Mi + a * a * M0;
-                        const float Sxy = Mij - a * Mj - bb * Mi + a * bb * M0;
-                        const float Syy = Mjj - 2.f * bb * Mj + bb * bb * M0;
-                        const float op = r.b.y, cA = r.a.z, cB = r.a.w, cC = r.b.x;
-                        float4 *dst = reinterpret_cast<float4 *>(dg2dc + 12 * (long long)gid);
-                        atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy),
-                                                   -0.5f * op * Sxx, -op * Sxy));
-                                                atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, dchunk == 0 ? sRgb(db)[3 * j] : 0.f,
-                                                       dchunk == 1 % nch ? sRgb(db)[3 * j + 1] : 0.f));
-                        if (dchunk == 2 % nch) atomicAdd(dg2dc + 12 * (long long)gid + 8, sRgb(db)[3 * j + 2]);
-                    }
-                }
-                if (want_fg && wmask) {
-                    // group g drains columns [g DN/2, (g+1) DN/2) in 32-column blocks,
-                    // transposed through shared memory (the weight-t buffers are free
-                    // once the MMAs that read them are done): each atomic then covers
-                    // 128 contiguous bytes of one Gaussian's row
-                    float *stage = reinterpret_cast<float *>(sTh) + ((warp & 1) + 2 * grp) * (32 * 36);
-                    const int sub = lane >> 3, q4 = (lane & 7) * 4;
+        const int q = warp & 3;
+        if (grp == 0 && q < 2) {  // rows 0..63 of the moments = the batch's Gaussians
+            const int j = q * 32 + lane;
+            const uint32_t wmask = sMask(db)[q] & (dnb >= q * 32 + 32 ? 0xFFFFFFFFu
+                                   : (dnb > q * 32 ? (1u << (dnb - q * 32)) - 1u : 0u));
+            const bool mine = (wmask >> lane) & 1u;
+            const uint32_t gid = sgid(db)[j];
+            float m[16];
+            tmem_ld16(tM + ((uint32_t)(q * 32) << 16), m);
+            if (mine) {
+                const GRec r = srec(db % 3)[j];
+                // moments about the pixel grid: dx = i - a, dy = j - b
+                const float a = r.a.x - (float)dx0 - 0.5f, bb = r.a.y - (float)dy0 - 0.5f;
+                const float M0 = m[0], Mi = m[1], Mj = m[2], Mii = m[3], Mij = m[4], Mjj = m[5];
+                const float Sx = Mi - a * M0, Sy = Mj - bb * M0;
+                const float Sxx = Mii - 2.f * a * Mi + a * a * M0;
+                const float Sxy = Mij - a * Mj - bb * Mi + a * bb * M0;
+                const float Syy = Mjj - 2.f * bb * Mj + bb * bb * M0;
+                const float op = r.b.y, cA = r.a.z, cB = r.a.w, cC = r.b.x;
+                float4 *dst = reinterpret_cast<float4 *>(dg2dc + 12 * (long long)gid);
+                atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy),
+                                           -0.5f * op * Sxx, -op * Sxy));
+                atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, dchunk == 0 ? sRgb(db)[3 * j] : 0.f,
+                                               dchunk == 1 % nch ? sRgb(db)[3 * j + 1] : 0.f));
+                if (dchunk == 2 % nch) atomicAdd(dg2dc + 12 * (long long)gid + 8, sRgb(db)[3 * j + 2]);
+            }
+        }
+        if (want_fg && (DN >= 128 || q < 2)) {
+            // lane l of warp w holds channel 128 mb + 32 (w % 4) + l of every
+            // Gaussian of its columns.  DN = 256: group g takes channel block
+            // g, all 64 Gaussians; DN <= 128: Gaussians [32 g, 32 g + 32).
+            // A 32 x 32 block goes through the warp's 4 KB of the t buffers
+            // (free: the MMAs that read them are done), so that each lane
+            // then adds 4 consecutive channels of one Gaussian: 4 Gaussians x
+            // 128 contiguous bytes per vector reduction.
+            const int mb = DN >= 256 ? grp : 0;
+            const int j0 = DN >= 256 ? 0 : grp * 32;
+            const uint64_t vmask = dnb >= 64 ? ~0ull : ((1ull << dnb) - 1ull);
+            const uint64_t msk = ((((uint64_t)sMask(db)[1] << 32) | sMask(db)[0]) & vmask) >> j0;
+            float *stage = reinterpret_cast<float *>(sTh) + warp * (32 * 32);
+            const int sub = lane >> 3, q4 = (lane & 7) * 4;
+            float *dst = gfeatures + dd0 + mb * 128 + q * 32 + q4;
+            const uint32_t *ids = sgid(db) + j0;
 #pragma unroll 1
-                    for (int cc = 0; cc < DN / 64; ++cc) {
-                        float v[32];
-                        tmem_ld32(tF + lanes + grp * (DN / 2) + cc * 32, v);
+            for (int h = 0; h < (DN >= 256 ? 2 : 1); ++h) {
+                const uint32_t m32 = (uint32_t)(msk >> (32 * h));
+                if (m32 == 0u) continue;  // warp-uniform
+                float v[32];
+                tmem_ld32(tF + mb * kBB + j0 + 32 * h + ((uint32_t)(q * 32) << 16), v);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            *reinterpret_cast<float4 *>(stage + lane * 36 + 4 * i) =
-                                make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                        __syncwarp();
+                for (int jj = 0; jj < 32; ++jj) stage[jj * 32 + lane] = v[jj];
+                __syncwarp();
 #pragma unroll
-                        for (int it = 0; it < 8; ++it) {
-                            const int jj = it * 4 + sub;
-                            if ((wmask >> jj) & 1u) {
-                                const uint32_t g = sgid(db)[(warp & 1) * 32 + jj];
-                                atomicAdd(reinterpret_cast<float4 *>(gfeatures + (size_t)g * D + dd0 + grp * (DN / 2) +
-                                                                     cc * 32 + q4),
-                                          *reinterpret_cast<const float4 *>(stage + jj * 36 + q4));
-                            }
-                        }
-                        __syncwarp();
-                    }
+                for (int it = 0; it < 8; ++it) {
+                    const int jj = it * 4 + sub;
+                    if ((m32 >> jj) & 1u)
+                        atomicAdd(reinterpret_cast<float4 *>(dst + (size_t)ids[32 * h + jj] * D),
+                                  *reinterpret_cast<const float4 *>(stage + jj * 32 + q4));
                 }
-            }    };
+                __syncwarp();
+            }
+        }
+    };
     // where item `it` lives: tile, half, slice, camera and its first pixel
     struct ItemGeo {
         int tile, chunk, ci, x0, y0;
