@@ -112,6 +112,22 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         : "memory");
 }
 
+// Same, with A read from tensor memory (lane = row of A, 8 columns per K step of 16).
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// Shared memory -> tensor memory: 128 rows x 256 bits (one K step of an M = 128
+// BF16 operand, described like an MMA operand) into 8 columns of lanes 0..127.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t d_tmem, uint64_t src) {
+    asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(d_tmem), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -570,9 +586,11 @@ struct BwdCfg {
     static constexpr int kOffBar = kOffXch + 128 * 16;
     static constexpr int kSmem = 1024 + kOffBar + 64;
     static_assert(kSmem <= 232448, "backward CTA exceeds the opt-in shared memory");
-    static constexpr int kTmemCols = 256;
+    static constexpr int kTmemCols = 512;
     static constexpr int kColM = 64;   // moments, 16 columns
     static constexpr int kColF = 128;  // dFe^T, 64 columns per block of 128 channels
+    static constexpr int kColD = 256;  // dF hi, then dF lo: DN / 2 columns each
+    static_assert(kColD + DN <= kTmemCols, "dF hi / lo exceed tensor memory");
 };
 
 // 256 threads: two groups of 4 warps share the half tile's 128 pixels; group g
@@ -621,7 +639,7 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0) tmem_alloc(tslot, C::kTmemCols);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        mbar_init(&bars[1], 2);  // two issuers: the feature gradient and the moments
         fence_mbar_init();
         smax[0] = smax[1] = 0ull;
     }
@@ -641,44 +659,61 @@ __global__ void __launch_bounds__(256, 1)
     tc_after();
     const uint32_t taddr = *tslot;
     const uint32_t tG = taddr, tM = taddr + C::kColM, tF = taddr + C::kColF;
+    const uint32_t tDh = taddr + C::kColD, tDl = tDh + DN / 2;
     const uint32_t sW_s = smem_u32(sW), sDh_s = smem_u32(sDh), sDl_s = smem_u32(sDl);
     const uint32_t sTh_s = smem_u32(sTh), sTl_s = smem_u32(sTl), sX_s = smem_u32(sX);
     const uint32_t sF_s = smem_u32(sm + C::kOffF);
     constexpr uint32_t idG = idesc_bf16(128, kBB, false, false);
     constexpr uint32_t idF = idesc_bf16(128, kBB, true, true);
     constexpr uint32_t idM = idesc_bf16(128, 16, true, false);
+    // dF hi / lo of the item live in TMEM as the A operand of G (copied once
+    // per item from their shared-memory tiles), so the batches of an item
+    // read only the feature rows from shared memory
+    auto issue_dF_copy = [&]() {
+#pragma unroll
+        for (int ks = 0; ks < DN / 16; ++ks) {
+            const uint32_t koff = (ks >> 2) * (128 * 128) + (ks & 3) * 32;
+            tmem_cp_128x256b(tDh + ks * 8, sdesc(sDh_s + koff, 16, 1024));
+            tmem_cp_128x256b(tDl + ks * 8, sdesc(sDl_s + koff, 16, 1024));
+        }
+    };
     auto issue_G = [&]() {  // G(px, g) = sum_d dF(px, d) Fe(g, d), hi + lo parts
         tc_after();
 #pragma unroll
         for (int ks = 0; ks < DN / 16; ++ks) {
-            const uint32_t koff = (ks >> 2) * (128 * 128) + (ks & 3) * 32;
             const uint64_t bd = sdesc(sF_s + (ks >> 2) * (kBB * 128) + (ks & 3) * 32, 16, 1024);
-            mma_bf16(tG, sdesc(sDh_s + koff, 16, 1024), bd, idG, ks > 0 ? 1u : 0u);
-            mma_bf16(tG, sdesc(sDl_s + koff, 16, 1024), bd, idG, 1u);
+            mma_bf16_ta(tG, tDh + ks * 8, bd, idG, ks > 0 ? 1u : 0u);
+            mma_bf16_ta(tG, tDl + ks * 8, bd, idG, 1u);
         }
         mma_commit(&bars[0]);
     };
     // dFe^T = dF^T W, one M = 128 block of channels per MMA (TMEM lanes =
     // channels, columns = the batch's Gaussians); for DN = 64 lanes 64..127
-    // read past the channel block and are never drained
+    // read past the channel block and are never drained.  Issued by thread 32.
     constexpr int kFBlk = DN >= 128 ? DN / 128 : 1;
-    auto issue_FM = [&]() {  // dFe^T = dF^T W (dF hi) and moments = T^T X (T hi + lo)
+    auto issue_F = [&]() {
         tc_after();
+        if (want_fg) {
 #pragma unroll
-        for (int ks = 0; ks < 128 / 16; ++ks) {
-            const uint64_t am = sdesc(sTh_s + ks * 2048, 128 * 128, 1024);
-            const uint64_t al = sdesc(sTl_s + ks * 2048, 128 * 128, 1024);
-            const uint64_t bx = sdesc(sX_s + (ks >> 2) * (16 * 128) + (ks & 3) * 32, 16, 1024);
-            mma_bf16(tM, am, bx, idM, ks > 0 ? 1u : 0u);
-            mma_bf16(tM, al, bx, idM, 1u);
-            if (want_fg) {  // the feature gradient takes dF as BF16 (its bar is the BF16 weights')
+            for (int ks = 0; ks < 128 / 16; ++ks) {
                 const uint64_t bw = sdesc(sW_s + ks * 2048, 128 * 128, 1024);
 #pragma unroll
                 for (int mb = 0; mb < kFBlk; ++mb)
-                    mma_bf16(tF + mb * kBB, sdesc(sDh_s + mb * 2 * (128 * 128) + ks * 2048, 128 * 128, 1024), bw, idF,
-                             ks > 0 ? 1u : 0u);
+                    mma_bf16(tF + mb * kBB, sdesc(sDh_s + mb * 2 * (128 * 128) + ks * 2048, 128 * 128, 1024), bw,
+                             idF, ks > 0 ? 1u : 0u);
             }
         }
+        mma_commit(&bars[1]);  // arrives at once when nothing was issued
+    };
+    // moments = T^T X with T hi in rows 0..63 and T lo in rows 64..127 of one
+    // M = 128 operand (Tl follows Th): lanes 0..63 get the hi part, 64..127
+    // the lo part.  Issued by thread 64.
+    auto issue_M = [&]() {
+        tc_after();
+#pragma unroll
+        for (int ks = 0; ks < 128 / 16; ++ks)
+            mma_bf16(tM, sdesc(sTh_s + ks * 2048, 128 * 128, 1024),
+                     sdesc(sX_s + (ks >> 2) * (16 * 128) + (ks & 3) * 32, 16, 1024), idM, ks > 0 ? 1u : 0u);
         mma_commit(&bars[1]);
     };
 
@@ -688,10 +723,14 @@ __global__ void __launch_bounds__(256, 1)
     auto drain = [&](int db, int dnbat_end, int dx0, int dy0, float *dg2dc, int dchunk, int dd0) {
         const int dbe = dnbat_end - db * kBB, dnb = dbe - max(0, dbe - kBB);
         const int q = warp & 3;
-        if (grp == 0 && q < 2) {  // rows 0..63 of the moments = the batch's Gaussians
-            const int j = q * 32 + lane;
-            const uint32_t wmask = sMask(db)[q] & (dnb >= q * 32 + 32 ? 0xFFFFFFFFu
-                                   : (dnb > q * 32 ? (1u << (dnb - q * 32)) - 1u : 0u));
+        // moments: lanes 0..63 hold the T-hi part of Gaussian (lane), read by
+        // warps 0 and 1; lanes 64..127 the T-lo part, read by warps 6 and 7.
+        // Both add their (linear) share; the colour sums go with the hi part.
+        if ((grp == 0 && q < 2) || (grp == 1 && q >= 2)) {
+            const bool hi = grp == 0;
+            const int j = (q & 1) * 32 + lane;
+            const uint32_t wmask = sMask(db)[q & 1] & (dnb >= (q & 1) * 32 + 32 ? 0xFFFFFFFFu
+                                   : (dnb > (q & 1) * 32 ? (1u << (dnb - (q & 1) * 32)) - 1u : 0u));
             const bool mine = (wmask >> lane) & 1u;
             const uint32_t gid = sgid(db)[j];
             float m[16];
@@ -709,9 +748,9 @@ __global__ void __launch_bounds__(256, 1)
                 float4 *dst = reinterpret_cast<float4 *>(dg2dc + 12 * (long long)gid);
                 atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy),
                                            -0.5f * op * Sxx, -op * Sxy));
-                atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, dchunk == 0 ? sRgb(db)[3 * j] : 0.f,
-                                               dchunk == 1 % nch ? sRgb(db)[3 * j + 1] : 0.f));
-                if (dchunk == 2 % nch) atomicAdd(dg2dc + 12 * (long long)gid + 8, sRgb(db)[3 * j + 2]);
+                atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, hi && dchunk == 0 ? sRgb(db)[3 * j] : 0.f,
+                                               hi && dchunk == 1 % nch ? sRgb(db)[3 * j + 1] : 0.f));
+                if (hi && dchunk == 2 % nch) atomicAdd(dg2dc + 12 * (long long)gid + 8, sRgb(db)[3 * j + 2]);
             }
         }
         if (want_fg && (DN >= 128 || q < 2)) {
@@ -913,7 +952,10 @@ __global__ void __launch_bounds__(256, 1)
             cp_async_wait_all();
             fence_async_smem();
             __syncthreads();
-            if (tid == 0) issue_G();
+            if (tid == 0) {  // in order: the copies, then the MMAs that read them
+                issue_dF_copy();
+                issue_G();
+            }
             pend0 = true;
             if (nbat > 1) {  // G of batch 0 done: the feature stage takes batch 1
                 const bool ok = mbar_wait(&bars[0], ph0);
@@ -1102,7 +1144,8 @@ __global__ void __launch_bounds__(256, 1)
                 T = xT[pidx];
                 S = xS[pidx];
             }
-            if (tid == 0) issue_FM();
+            if (tid == 32) issue_F();
+            if (tid == 64) issue_M();
             pend1 = true;
         }
         if (timeout) break;
