@@ -460,10 +460,11 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
     const bool tc = D > 0 && use_tc(p, ftype, D) && (grad_feat || grad_features);
     {
         Prof pr(ctx, tc ? "render_bwd_tc" : "render_bwd_fp32", st);
-        if (tc)
-            launch_render_bwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, D, p->d_split, T_final, last,
-                                 grad_rgb, grad_feat, g2d, grad_features, ctx->status, st);
-        else
+        if (tc) {
+            if (!launch_render_bwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, D, p->d_split, T_final,
+                                      last, grad_rgb, grad_feat, g2d, grad_features, ctx->status, st))
+                return fail(ctx, FHGS_ERR_CUDA, "could not encode the tensor map of grad_feat");
+        } else
             launch_render_bwd_fp32(n, cs, q, pv, *bins, features, ftype == FHGS_BF16, D, T_final, last, grad_rgb,
                                    grad_feat, g2d, D > 0 ? grad_features : nullptr, st);
     }

@@ -178,7 +178,8 @@ int tc_supported(int D, int d_split);
 void launch_render_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                           const __nv_bfloat16 *feats, int D, int d_split, float *rgb, float *feat, float *T,
                           int32_t *last, unsigned *status, cudaStream_t st);
-void launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+// false (nothing launched) when the tensor map of gfeat cannot be encoded
+bool launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                           const __nv_bfloat16 *feats, int D, int d_split, const float *T, const int32_t *last,
                           const float *grgb, const float *gfeat, float *g2d, float *gfeatures, unsigned *status,
                           cudaStream_t st);

@@ -79,10 +79,11 @@ extern "C" fhgs_status fhgs_render_bwd_noalloc(const fhgs_gaussians *g, const vo
         cudaMemsetAsync(grad_features, 0, sizeof(float) * (size_t)n * D, st) != cudaSuccess)
         return FHGS_ERR_CUDA;
     ProjView pv = proj_view(const_cast<void *>(proj), cn);
-    if (tc)
-        launch_render_bwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, D, p->d_split, T_final, last,
-                             grad_rgb, grad_feat, d.g2d, grad_features, d.status, st);
-    else
+    if (tc) {
+        if (!launch_render_bwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, D, p->d_split, T_final, last,
+                                  grad_rgb, grad_feat, d.g2d, grad_features, d.status, st))
+            return FHGS_ERR_CUDA;
+    } else
         launch_render_bwd_fp32(n, cs, q, pv, *bins, features, ftype == FHGS_BF16, D, T_final, last, grad_rgb,
                                grad_feat, d.g2d, D > 0 ? grad_features : nullptr, st);
     launch_project_bwd(*g, cs, q, pv, d.g2d, grad_means, grad_scales, grad_quats, grad_opac, grad_sh, st);

@@ -28,6 +28,11 @@
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel
 // latches FHGS_ERR_TIMEOUT, waits once more (bounded) for its MMAs, frees its
 // TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "fhgs_internal.cuh"
 
 namespace fhgs {
@@ -183,9 +188,19 @@ __device__ __forceinline__ void bulk_s2g(void *g, uint32_t saddr, uint32_t bytes
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// Bulk prefetch of `bytes` (16-byte aligned, multiple of 16) into L2.
-__device__ __forceinline__ void bulk_prefetch_l2(const void *g, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"(bytes) : "memory");
+// Tiled 2-D tensor load (TMA) of one box at (x, y) into shared memory,
+// completion counted in bytes on an mbarrier.  x * element size must be a
+// multiple of 16 bytes; parts of the box outside the tensor read as zero.
+__device__ __forceinline__ void tma_load_2d(uint32_t saddr, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            saddr),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// One arrival on `bar` that also announces `bytes` of bulk copies to come.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -604,8 +619,9 @@ __global__ void __launch_bounds__(256, 1)
     k_render_bwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                     const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats, int D,
                     const float *__restrict__ Tfin, const int32_t *__restrict__ lastv,
-                    const float *__restrict__ grgb, const float *__restrict__ gfeat, float *g2d, float *gfeatures,
-                    unsigned *status, int n_items) {
+                    const float *__restrict__ grgb, const float *__restrict__ gfeat,
+                    const __grid_constant__ CUtensorMap dfm, float *g2d, float *gfeatures, unsigned *status,
+                    int n_items) {
     using C = BwdCfg<DN>;
     if ((int)blockIdx.x >= n_items) return;  // uniform over the CTA
     extern __shared__ uint8_t smem_raw[];
@@ -622,12 +638,13 @@ __global__ void __launch_bounds__(256, 1)
     float *xS1 = xP1 + 128;                                    // [128] group 1's sum w g
     float *xT = xS1 + 128;                                     // [128] T after the batch
     float *xS = xT + 128;                                      // [128] S after the batch
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::kOffBar);  // [0] G, [1] dFe + moments
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+    // [0] G, [1] dFe + moments, [2] dF staging of pixels 0..63, [3] of pixels 64..127
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::kOffBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
     // [2] per item parity: max over the CTA of (item counter << 32 | last); the
     // counter only grows, so no slot is ever reset, and a slot's next writer
     // is two items later, past at least one barrier of every thread
-    unsigned long long *smax = reinterpret_cast<unsigned long long *>(bars + 3);
+    unsigned long long *smax = reinterpret_cast<unsigned long long *>(bars + 5);
     auto srec = [&](int stg) { return reinterpret_cast<GRec *>(sm + C::kOffRec + stg * C::kRecBytes); };
     auto sgid = [&](int b) { return reinterpret_cast<uint32_t *>(sm + C::kOffGid + (b & 3) * kBB * 4); };
 
@@ -640,6 +657,8 @@ __global__ void __launch_bounds__(256, 1)
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 2);  // two issuers: the feature gradient and the moments
+        mbar_init(&bars[2], 1);
+        mbar_init(&bars[3], 1);
         fence_mbar_init();
         smax[0] = smax[1] = 0ull;
     }
@@ -806,6 +825,40 @@ __global__ void __launch_bounds__(256, 1)
         return g;
     };
 
+    // dF arrives by TMA, staged row-major [64 px][DN] FP32 in two halves:
+    // pixels 0..63 (image rows 0..3 of the half tile) in the Dl region, free
+    // once Dl's copy into TMEM is done, so issued during the previous item;
+    // pixels 64..127 in the Dh region, free once the previous item's last FM
+    // has read it.  The tensor is dF as [total pixels][D]: one box of 16
+    // pixels x DN channels per image row.  Pixels right of or below a
+    // camera's image are read from the next row or camera (or as zero past
+    // the end) and never used.  Called by warp 0.
+    auto stage_half = [&](int item, int hf) {
+        if (lane == 0) {
+            uint64_t *bar = &bars[2 + hf];
+            if (gfeat == nullptr) {
+                mbar_arrive_expect_tx(bar, 0u);
+            } else {
+                const ItemGeo g = item_geo(item);
+                const DevCam &c = cs.c[g.ci];
+                const uint32_t dst = smem_u32(hf == 0 ? sDl : sDh);
+                mbar_arrive_expect_tx(bar, 64u * DN * 4);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const long long row = c.pix_off + (long long)(g.y0 + hf * 4 + r) * c.W + g.x0;
+                    tma_load_2d(dst + r * (16 * DN * 4), &dfm, g.chunk * DN, (int)row, bar);
+                }
+            }
+        }
+        __syncwarp();
+    };
+    uint32_t phA = 0, phB = 0;
+    bool pendA = false, pendB = false;  // staging copies in flight (for the timeout exit)
+    if (warp == 0) {
+        stage_half(blockIdx.x, 0);
+        stage_half(blockIdx.x, 1);
+    }
+    pendA = pendB = true;
     uint32_t ph0 = 0, ph1 = 0;
     bool pend0 = false, pend1 = false;
     bool timeout = false;
@@ -827,28 +880,15 @@ __global__ void __launch_bounds__(256, 1)
         const int d0 = chunk * DN;
         const GRec *rec = pv.rec + (long long)ci * N;
         float *g2dc = g2d + (long long)ci * N * 12;
-        // this item's dF slice, 16 rows per warp, all loads in flight at once
-        float4 vdf[16][kL];
-#pragma unroll
-    for (int rr = 0; rr < 16; ++rr) {
-        const int prow = warp * 16 + rr;
-        const int qx = x0 + (prow & 15), qy = y0 + (prow >> 4);
-        const bool qin = qx < cam.W && qy < cam.H && gfeat != nullptr;
-        const float *src = gfeat + (cam.pix_off + (long long)qy * cam.W + qx) * D + d0;
-#pragma unroll
-        for (int li = 0; li < kL; ++li) {
-            const int f = li * 128 + lane * 4;
-            vdf[rr][li] = (qin && f < DN) ? *reinterpret_cast<const float4 *>(src + f) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
-        // warm L2 with the next item's dF slice, one bulk prefetch per pixel
-        if (tid < 128 && gfeat != nullptr && it + (int)gridDim.x < n_items) {
-            const ItemGeo ng = item_geo(it + gridDim.x);
-            const DevCam &nc = cs.c[ng.ci];
-            const int nx = ng.x0 + (tid & 15), ny = ng.y0 + (tid >> 4);
-            if (nx < nc.W && ny < nc.H)
-                bulk_prefetch_l2(gfeat + (nc.pix_off + (long long)ny * nc.W + nx) * D + ng.chunk * DN, DN * 4);
-        }
+        // the next item's pixels 0..63 go to Dl once this item's dF is in TMEM
+        bool stageA_next = it + (int)gridDim.x < n_items;
+        auto stage_next_A = [&]() {
+            if (stageA_next) {
+                if (warp == 0) stage_half(it + gridDim.x, 0);
+                pendA = true;
+                stageA_next = false;
+            }
+        };
         float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
         int lastp = 0;
         if (inside) {
@@ -858,7 +898,8 @@ __global__ void __launch_bounds__(256, 1)
             dC1 = grgb[3 * pix + 1];
             dC2 = grgb[3 * pix + 2];
         }
-        // tail of the previous item: its last FM, then its drain
+        // tail of the previous item: its last FM (Dh is then free for this
+        // item's pixels 64..127), then its drain
         if (have_prev) {
             const bool ok = mbar_wait(&bars[1], ph1);
             if (ok) {
@@ -869,6 +910,8 @@ __global__ void __launch_bounds__(256, 1)
                 timeout = true;
                 break;
             }
+            if (warp == 0) stage_half(it, 1);
+            pendB = true;
             tc_after();
             drain(prev_b, prev_end, prev_x0, prev_y0, prev_g2dc, prev_chunk, prev_d0);
             tc_before();
@@ -876,6 +919,9 @@ __global__ void __launch_bounds__(256, 1)
             if (tid < kBB) sRgb(prev_b)[3 * tid] = sRgb(prev_b)[3 * tid + 1] = sRgb(prev_b)[3 * tid + 2] = 0.f;
             if (tid < 2) sMask(prev_b)[tid] = 0u;
             have_prev = false;
+        } else if (k > 0) {  // the previous item issued no MMA that reads Dh
+            if (warp == 0) stage_half(it, 1);
+            pendB = true;
         }
         if (grp == 0) atomicMax(&smax[k & 1], ((unsigned long long)k << 32) | (uint32_t)max(lastp, 0));
         __syncthreads();
@@ -916,11 +962,46 @@ __global__ void __launch_bounds__(256, 1)
         }
         cp_async_commit();
     };
+        // this item's staged dF: both halves are waited for also when the
+        // item has no batch, so that the staging buffers are quiet before reuse
+        {
+            const bool okA = mbar_wait(&bars[2], phA);
+            const bool okB = okA && mbar_wait(&bars[3], phB);
+            if (okA) {
+                phA ^= 1u;
+                pendA = false;
+            }
+            if (okB) {
+                phB ^= 1u;
+                pendB = false;
+            }
+            if (__syncthreads_or(!okB)) {
+                timeout = true;
+                break;
+            }
+        }
+        if (nbat == 0) stage_next_A();  // nothing reads Dl for this item
         if (nbat > 0) {
             load_gid(0);
             load_gid(1);
+            // the staged rows -> registers, 16 rows per warp; every thread has
+            // read its share before any hi / lo write overwrites the staging
+            float4 vdf[16][kL];
+#pragma unroll
+            for (int rr = 0; rr < 16; ++rr) {
+                const int prow = warp * 16 + rr;
+                const int qx = x0 + (prow & 15), qy = y0 + (prow >> 4);
+                const bool qin = qx < cam.W && qy < cam.H && gfeat != nullptr;
+                const uint8_t *row = (prow < 64 ? sDl : sDh) + (prow & 63) * (DN * 4);
+#pragma unroll
+                for (int li = 0; li < kL; ++li) {
+                    const int f = li * 128 + lane * 4;
+                    vdf[rr][li] = (qin && f < DN) ? *reinterpret_cast<const float4 *>(row + 4 * f)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
             cp_async_wait_all();
-            __syncthreads();  // ids of batches 0 and 1 are staged
+            __syncthreads();  // ids of batches 0 and 1 are staged; the staging has been read
             load_rec(0);
         // dF -> BF16 hi / lo, K-major swizzled
         {
@@ -968,6 +1049,7 @@ __global__ void __launch_bounds__(256, 1)
                     break;
                 }
                 prefetch_feat(1);
+                stage_next_A();  // the copies into TMEM (before G) have read Dl
             }
         }
 
@@ -991,6 +1073,7 @@ __global__ void __launch_bounds__(256, 1)
                     timeout = true;
                     break;
                 }
+                stage_next_A();
             }
             tc_after();
             const GRec *R = srec(b % 3);
@@ -1177,6 +1260,8 @@ __global__ void __launch_bounds__(256, 1)
         if (tid == 0) latch(status, ST_TIMEOUT);
         if (pend0) mbar_wait(&bars[0], ph0);
         if (pend1) mbar_wait(&bars[1], ph1);
+        if (pendA) mbar_wait(&bars[2], phA);
+        if (pendB) mbar_wait(&bars[3], phB);
     }
     cp_async_wait_all();
     tc_before();
@@ -1588,11 +1673,38 @@ void launch_render_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
 #undef FHGS_FWD
 }
 
-void launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+// Tensor map of dL/dfeat as a [rows][D] FP32 matrix with boxes of 16 rows x
+// dn columns (no swizzle; out-of-range elements read as zero).
+static bool make_dF_tmap(CUtensorMap *m, const float *base, long long rows, int D, int dn) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode || rows < 1 || rows >= (1ll << 31) || (reinterpret_cast<uintptr_t>(base) & 15u) || (D * 4) % 16 ||
+        dn > 256)
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)D * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)dn, 16};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                           const __nv_bfloat16 *feats, int D, int d_split, const float *T, const int32_t *last,
                           const float *grgb, const float *gfeat, float *g2d, float *gfeatures, unsigned *status,
                           cudaStream_t st) {
     const int dn = pick_bwd_dn(D, d_split);
+    CUtensorMap dfm;
+    memset(&dfm, 0, sizeof(dfm));
+    if (gfeat != nullptr && !make_dF_tmap(&dfm, gfeat, cs.total_pix, D, dn)) return false;
     // persistent: one CTA per SM walks the (tile, half, slice) items
     const int n_items = cs.total_tiles * 2 * (D / dn);
     const dim3 grid((unsigned)max(1, min(n_items, sm_count_current())));
@@ -1602,8 +1714,8 @@ void launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
         static std::atomic<unsigned long long> smem_done{0};                                                 \
         allow_max_smem(smem_done, k_render_bwd_tc<DNV>);                                                     \
         k_render_bwd_tc<DNV><<<grid, 256, BwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, feats, D, T, \
-                                                                   last, grgb, gfeat, g2d, gfeatures, status,   \
-                                                                   n_items);                                     \
+                                                                   last, grgb, gfeat, dfm, g2d, gfeatures,      \
+                                                                   status, n_items);                            \
         break;                                                                                                 \
     }
     switch (dn) {
@@ -1613,6 +1725,7 @@ void launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
         default: break;
     }
 #undef FHGS_BWD
+    return true;
 }
 
 int fuse_tc_dn(int D) {
