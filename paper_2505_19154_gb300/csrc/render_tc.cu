@@ -181,13 +181,6 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
-// Bulk copy (TMA engine) of `bytes` from shared to global memory; both
-// addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_s2g(void *g, uint32_t saddr, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g), "r"(saddr), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Tiled 2-D tensor load (TMA) of one box at (x, y) into shared memory,
 // completion counted in bytes on an mbarrier.  x * element size must be a
 // multiple of 16 bytes; parts of the box outside the tensor read as zero.
@@ -202,7 +195,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t saddr, const CUtensorMap *m
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Byte offset of 16-byte chunk `c` (0..7) of row `r` inside a 128B-swizzled
@@ -239,25 +231,23 @@ struct FwdCfg {
     static constexpr int kNSub = DN > 256 ? DN / 256 : 1;
     static constexpr int kMmaN = DN > 256 ? 256 : DN;
     static constexpr int kRecBytes = kFB * 48;
+    // two feature stages, except at DN = 512 where one keeps the CTA small
+    // enough for two per SM (one CTA's epilogue then runs beside the other's
+    // batches)
+    static constexpr int kFStages = DN >= 512 ? 1 : 2;
     static constexpr int kOffF = 2 * kWBytes;
-    static constexpr int kOffRec = kOffF + 2 * kFBytes;
+    static constexpr int kOffRec = kOffF + kFStages * kFBytes;
     static constexpr int kOffGid = kOffRec + 2 * kRecBytes;  // [3][64] Gaussian ids
     static constexpr int kOffX = kOffGid + 3 * kFB * 4;      // per-pixel exchange, 8 words per pixel
     static constexpr int kOffBar = kOffX + 128 * 8 * 4;
     static constexpr int kSmem = 1024 + kOffBar + 64;
-    // epilogue: the accumulator leaves through shared memory in passes of
-    // kCH columns, one padded row per pixel (16 B of padding keeps the
-    // lane-per-pixel writes free of bank conflicts), then one bulk copy per
-    // pixel and pass; the staging reuses the weight and feature stages
-    static constexpr int kCH = DN >= 256 ? DN / 4 : 64;
-    static constexpr int kStageRow = (kCH + 4) * 4;
-    static constexpr int kStageBytes = 128 * kStageRow;
-    static constexpr int kNBuf = 2 * kStageBytes <= kOffRec ? 2 : 1;  // passes double-buffered when they fit
-    static_assert(kStageBytes <= kOffRec, "epilogue staging must fit in the weight and feature stages");
+    // epilogue: one padded 32 x 36 FP32 tile per warp in the weight and
+    // feature stages
+    static_assert(8 * 32 * 36 * 4 <= kOffRec, "epilogue tiles must fit in the weight and feature stages");
 };
 
 template <int DN>
-__global__ void __launch_bounds__(256, DN <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(256, 2)
     k_render_fwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                     const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats, int D,
                     float *rgb, float *feat, float *Tout, int32_t *last_out, unsigned *status) {
@@ -290,7 +280,9 @@ __global__ void __launch_bounds__(256, DN <= 256 ? 2 : 1)
     const int d0 = chunk * DN;
     const GRec *rec = pv.rec + (long long)ci * N;
 
-    if (warp == 0) tmem_alloc(tslot, DN);
+    // TMEM is allocated right before the first MMA and released after the
+    // epilogue's last read of it: with two CTAs on an SM, one CTA's batches
+    // run while the other's epilogue drains to global memory
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -328,7 +320,7 @@ __global__ void __launch_bounds__(256, DN <= 256 ? 2 : 1)
         if (b < nbatches) {
             const int nb = (int)min((uint32_t)kFB, e - (s + (uint32_t)b * kFB));
             constexpr int kCPR = DN / 8;
-            const uint32_t fb = sF_s + (b & 1) * C::kFBytes;
+            const uint32_t fb = sF_s + (C::kFStages == 2 ? (b & 1) : 0) * C::kFBytes;
             const uint32_t *ids = sgid(b);
 #pragma unroll 4
             for (int q = tid; q < kFB * kCPR; q += 256) {
@@ -341,10 +333,9 @@ __global__ void __launch_bounds__(256, DN <= 256 ? 2 : 1)
         cp_async_commit();
     };
 
-    tc_before();
     __syncthreads();
-    tc_after();
-    const uint32_t taddr = *tslot;
+    uint32_t taddr = 0;
+    bool have_tmem = false;
 
     const float fpx = px + 0.5f, fpy = py + 0.5f;
     float cr = 0.f, cg = 0.f, cb = 0.f;  // this group's share of the colour
@@ -392,7 +383,9 @@ __global__ void __launch_bounds__(256, DN <= 256 ? 2 : 1)
             xP0[pidx] = P;
             xL0[pidx] = lastc;
         }
-        // the feature stage of batch b+1 is free once the MMA of batch b-1 is done
+        // two stages: the feature stage of batch b+1 is free once the MMA of
+        // batch b-1 is done; one stage: that of batch b (batch 0's came with
+        // the prologue)
         bool ok = true;
         if (b >= 1) {
             const int ps = stg ^ 1;
@@ -403,7 +396,9 @@ __global__ void __launch_bounds__(256, DN <= 256 ? 2 : 1)
             timeout = true;
             break;
         }
-        load_feat(b + 1);
+        if (C::kFStages == 2) load_feat(b + 1);
+        else if (b >= 1) load_feat(b);
+        else cp_async_commit();
         // weights: group 1 starts from T_in P_0 unless group 0 stops
         const float P0 = xP0[pidx];
         const bool stop0 = !done_in && T_in * P0 < p.teps;
@@ -456,14 +451,22 @@ __global__ void __launch_bounds__(256, DN <= 256 ? 2 : 1)
                 xLast[pidx] = lastw >= 0 ? pos0 + 32 + lastw + 1 : (L0 >= 0 ? pos0 + L0 + 1 : last_in);
             }
         }
-        // the newest groups are [ids b+2, records b+1, features b+1]: this
-        // batch's features have landed after this wait
-        cp_async_wait<3>();
+        // two stages: the newest groups are [ids b+2, records b+1, features
+        // b+1] and this batch's features have landed after wait<3>; one stage:
+        // this batch's features are the newest group
+        if (C::kFStages == 2) cp_async_wait<3>();
+        else cp_async_wait<0>();
         fence_async_smem();
+        if (!have_tmem && warp == 0) tmem_alloc(tslot, DN);  // may wait for the other CTA's release
         const int all_done = __syncthreads_and(grp == 0 || done);
+        if (!have_tmem) {
+            tc_after();
+            taddr = *tslot;
+            have_tmem = true;
+        }
         if (tid == 0) {
             tc_after();
-            const uint32_t wa = sW_s + stg * C::kWBytes, fb = sF_s + stg * C::kFBytes;
+            const uint32_t wa = sW_s + stg * C::kWBytes, fb = sF_s + (C::kFStages == 2 ? stg : 0) * C::kFBytes;
 #pragma unroll
             for (int ks = 0; ks < kFB / 16; ++ks) {
                 const uint64_t ad = sdesc(wa + ks * 32, 16, 1024);
@@ -493,46 +496,51 @@ __global__ void __launch_bounds__(256, DN <= 256 ? 2 : 1)
         }
     } else {
         tc_after();
-        // accumulator -> padded rows in shared memory -> one bulk copy per
-        // pixel and pass, the passes double-buffered so that the TMA engine
-        // reads one while the warps fill the next.  Warp w reads TMEM lanes
-        // 32 (w % 4).. (pixels) and half of the pass's columns.  The CTA
-        // waits only until its copies have read shared memory.
-        constexpr int kCH = C::kCH;
-        const int row = (warp & 3) * 32 + (tid & 31);
-#pragma unroll 1
-        for (int pass = 0; pass < DN / kCH; ++pass) {
-            uint8_t *stage = sm + (pass % C::kNBuf) * C::kStageBytes;
-            if (pass >= C::kNBuf) {  // the copies that last read this buffer are done reading
-                if (tid < 128) {
-                    if (C::kNBuf == 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-                    else bulk_wait_read_all();
-                }
-                __syncthreads();
-            }
-#pragma unroll 1
-            for (int k = 0; k < kCH / 64; ++k) {
-                const int c = grp * (kCH / 2) + k * 32;
-                float v[32];
-                if (nbatch > 0) {
-                    tmem_ld32(taddr + ((uint32_t)((warp & 3) * 32) << 16) + pass * kCH + c, v);
-                } else {
+        // accumulator -> global memory by plain 16-byte stores, no block-wide
+        // step: warp w holds pixels 32 (w % 4) .. + 31 (its TMEM lanes) and
+        // half of the columns; each 32 x 32 block goes through the warp's own
+        // padded tile in shared memory (the weight and feature stages are
+        // free), then lane l writes 16 bytes of pixel 4 i + l / 8 per step:
+        // 128 contiguous bytes per pixel and store.  The stores are posted, so
+        // the CTA leaves while the SM's write path drains them.
+        const int lane = tid & 31, q = warp & 3, sub = lane >> 3, c4 = (lane & 7) * 4;
+        float *tileb = reinterpret_cast<float *>(sm) + warp * (32 * 36);
+        long long opix[8];
+        bool oin[8];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] = 0.f;
-                }
-                float4 *dst = reinterpret_cast<float4 *>(stage + row * C::kStageRow + c * 4);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-            }
-            fence_async_smem();
-            __syncthreads();
-            if (tid < 128) {  // thread t owns pixel t
-                if (inside)
-                    bulk_s2g(feat + pix * D + d0 + pass * kCH, smem_u32(stage + tid * C::kStageRow), kCH * 4);
-                bulk_commit();
-            }
+        for (int it = 0; it < 8; ++it) {
+            const int prow = q * 32 + it * 4 + sub;
+            const int ox = tx * kTile + (prow & 15), oy = ty * kTile + half * 8 + (prow >> 4);
+            oin[it] = ox < cam.W && oy < cam.H;
+            opix[it] = cam.pix_off + (long long)oy * cam.W + ox;
         }
-        if (tid < 128) bulk_wait_read_all();
+#pragma unroll 1
+        for (int cc = 0; cc < DN / 64; ++cc) {
+            const int col = grp * (DN / 2) + cc * 32;
+            float v[32];
+            if (have_tmem) {
+                tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + col, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                *reinterpret_cast<float4 *>(tileb + lane * 36 + 4 * i) =
+                    make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            __syncwarp();
+#pragma unroll
+            for (int it = 0; it < 8; ++it)
+                if (oin[it])
+                    *reinterpret_cast<float4 *>(feat + opix[it] * D + d0 + col + c4) =
+                        *reinterpret_cast<const float4 *>(tileb + (it * 4 + sub) * 36 + c4);
+            __syncwarp();
+        }
+        // the accumulator has been read: release TMEM for the SM's other CTA
+        tc_before();
+        __syncthreads();
+        if (have_tmem && warp == 0) tmem_dealloc(taddr, DN);
+        have_tmem = false;
         if (chunk == 0) {
             if (grp == 1) {
                 xRgb[3 * pidx] = cr;
@@ -552,7 +560,7 @@ __global__ void __launch_bounds__(256, DN <= 256 ? 2 : 1)
     }
     tc_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(taddr, DN);
+    if (have_tmem && warp == 0) tmem_dealloc(taddr, DN);  // only when the epilogue was skipped
 }
 
 // ------------------------------------------------------------- backward
