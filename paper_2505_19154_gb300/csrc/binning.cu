@@ -330,7 +330,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t *a, long lo
 // ------------------------------------------------------------- scatter
 constexpr int kScatterWarps = 4;
 constexpr int kStage = 128;  // entries staged in shared memory per step
-constexpr int kScatterCtr = 8192;  // tile counters per warp at most: 143 KB per block
+constexpr int kScatterCtr = 8192;  // tile counters per warp at most: 145 KB per block
+constexpr int kScatterStageWords = kStage * 7;  // staged rectangles, indices and prefix per warp
 
 // One warp per (segment, camera, band of tile rows): walks the segment's
 // Gaussians in depth order and writes each one into every tile of its
@@ -355,9 +356,10 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32
     const int by0 = band * band_rows, by1 = min(cam.tiles_y, by0 + band_rows);
     if (by0 >= by1) return;
     const int ctr_words = (band_rows * tx + 3) & ~3;
-    uint32_t *ctr = sh + warp * (ctr_words + kStage * 6);
+    uint32_t *ctr = sh + warp * (ctr_words + kScatterStageWords);
     int4 *st_r = reinterpret_cast<int4 *>(ctr + ctr_words);         // staged rectangles
     uint32_t *st_g = reinterpret_cast<uint32_t *>(st_r + kStage);  // staged Gaussian index
+    uint32_t *st_p = st_g + kStage;                                 // exclusive prefix of their tile counts
     const int T = (by1 - by0) * tx;
     for (int t = lane; t < T; t += 32) ctr[t] = table[(long long)(cam.tile_off + by0 * tx + t) * S + seg];
     const long long b0 = (long long)ci * N + (long long)seg * SEG;
@@ -387,20 +389,61 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32
             mt += __popc(bal);
         }
         __syncwarp();
-        for (int k = 0; k < mt; ++k) {
-            const int4 r = st_r[k];
-            const uint32_t g = st_g[k];
+        // the staged Gaussians' (Gaussian, tile) pairs, flattened in order:
+        // lane l of step s takes pair 32 s + l.  Pairs of one step that hit
+        // the same tile are ranked by lane, which is their depth order.
+        uint32_t cnt[kStage / 32];
+        uint32_t lsum = 0;
+#pragma unroll
+        for (int u = 0; u < kStage / 32; ++u) {
+            const int k = lane * (kStage / 32) + u;
+            cnt[u] = 0;
+            if (k < mt) {
+                const int4 r = st_r[k];
+                cnt[u] = (uint32_t)((r.z - r.x + 1) * (r.w - r.y + 1));
+            }
+            lsum += cnt[u];
+        }
+        uint32_t incl = lsum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t run = incl - lsum;
+#pragma unroll
+        for (int u = 0; u < kStage / 32; ++u) {
+            st_p[lane * (kStage / 32) + u] = run;
+            run += cnt[u];
+        }
+        __syncwarp();
+        const uint32_t lt_mask = (1u << lane) - 1u;
+        for (uint32_t i0 = 0; i0 < total; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            const bool act = i < total;
+            // the Gaussian of pair i: the last k with prefix[k] <= i
+            int lo = 0, hi = mt - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (st_p[mid] <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            const int4 r = st_r[lo];
             const int w = r.z - r.x + 1;
-            const uint32_t nt = (uint32_t)(w * (r.w - r.y + 1));
-            const float inv_w = 1.f / (float)w;
-            for (uint32_t q = lane; q < nt; q += 32) {
-                // q / w via a float reciprocal: exact for q < 2^22 (q + 0.5 never lands on an integer)
-                const int qy = (int)(((float)q + 0.5f) * inv_w);
-                const int qx = (int)q - qy * w;
-                const int t = (r.y - by0 + qy) * tx + r.x + qx;
-                const uint32_t pos = ctr[t];
-                if (pos < capacity) gids[pos] = g;
-                ctr[t] = pos + 1;
+            const uint32_t q = i - st_p[lo];
+            // q / w via a float reciprocal: exact for q < 2^22 (q + 0.5 never lands on an integer)
+            const int qy = (int)(((float)q + 0.5f) * (1.f / (float)w));
+            const int qx = (int)q - qy * w;
+            const int t = (r.y - by0 + qy) * tx + r.x + qx;
+            const uint32_t same = __match_any_sync(0xffffffffu, act ? (uint32_t)t : (0x80000000u | (uint32_t)lane));
+            const uint32_t rank = __popc(same & lt_mask);
+            const uint32_t base = act ? ctr[t] : 0u;
+            __syncwarp();
+            if (act) {
+                const uint32_t pos = base + rank;
+                if (pos < capacity) gids[pos] = st_g[lo];
+                if (rank == 0) ctr[t] = base + (uint32_t)__popc(same);
             }
             __syncwarp();
         }
@@ -535,7 +578,7 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
     const int band_rows = max(1, min((max_ty + nband - 1) / nband, kScatterCtr / max(max_tx, 1)));
     nband = (max_ty + band_rows - 1) / band_rows;
     const int ctr_words = (band_rows * max_tx + 3) & ~3;
-    const int scat_smem = kScatterWarps * (ctr_words + kStage * 6) * (int)sizeof(uint32_t);
+    const int scat_smem = kScatterWarps * (ctr_words + kScatterStageWords) * (int)sizeof(uint32_t);
     static std::atomic<unsigned long long> scatter_done{0};
     allow_max_smem(scatter_done, k_seg_scatter);
     note_launch(1);
