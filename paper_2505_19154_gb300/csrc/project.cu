@@ -287,13 +287,17 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ m
                                                      const float *__restrict__ g2d, float *gmeans, float *gscales,
                                                      float *gquats, float *gopac, float *gsh) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= N) return;
+    const bool valid = g < N;
     const int K = p.K;
+    float gmu[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gop = 0.f;
+    float gshv[48];
+#pragma unroll
+    for (int i = 0; i < 48; ++i) gshv[i] = 0.f;
     // every gradient is linear in the footprint gradients: a Gaussian that no
     // tile composited (all of them zero) gets exact zeros, without reading
     // its parameters
     bool touched = false;
-    for (int ci = 0; ci < cs.n && !touched; ++ci) {
+    for (int ci = 0; ci < cs.n && valid && !touched; ++ci) {
         const long long e = (long long)ci * N + g;
         if (pv.ntiles[e] == 0) continue;
         const float *gg = g2d + 12 * e;
@@ -302,26 +306,11 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ m
         touched = ga.x != 0.f || ga.y != 0.f || ga.z != 0.f || ga.w != 0.f || gb.x != 0.f || gb.y != 0.f ||
                   gb.z != 0.f || gb.w != 0.f || gg[8] != 0.f;
     }
-    if (!touched) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            gmeans[3 * g + j] = 0.f;
-            gscales[3 * g + j] = 0.f;
-        }
-        reinterpret_cast<float4 *>(gquats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-        gopac[g] = 0.f;
-        float *gshg = gsh + (long long)3 * K * g;
-        for (int i = 0; i < 3 * K; ++i) gshg[i] = 0.f;
-        return;
-    }
+    if (touched) {
     const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
     const float s[3] = {scales[3 * g], scales[3 * g + 1], scales[3 * g + 2]};
     const float4 q4 = quats[g];
     const float *shg = sh + (long long)3 * K * g;
-    float gmu[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gop = 0.f;
-    float gshv[48];
-#pragma unroll
-    for (int i = 0; i < 48; ++i) gshv[i] = 0.f;
 
     // rotation from the normalised quaternion (camera independent)
     const float nq = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
@@ -472,15 +461,39 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ m
 #pragma unroll
     for (int k = 0; k < 4; ++k) gq[k] = (gqn[k] - qn[k] * dq) / nq;
 
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        gmeans[3 * g + j] = gmu[j];
-        gscales[3 * g + j] = gs[j];
     }
-    reinterpret_cast<float4 *>(gquats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-    gopac[g] = gop;
-    float *gshg = gsh + (long long)3 * K * g;
-    for (int i = 0; i < 3 * K; ++i) gshg[i] = gshv[i];
+
+    // the warp's 32 consecutive Gaussians leave through shared memory, so
+    // that every store covers contiguous bytes (rows of 3 K SH floats, 3
+    // mean and 3 scale floats per Gaussian)
+    __shared__ float sbuf[4][32 * 49];
+    const int wl = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    const long long g0 = g - ln;
+    if (g0 >= N) return;  // warp-uniform: the whole warp lies past the end
+    const int nv = (int)min(32ll, N - g0);
+    float *b = sbuf[wl];
+    if (valid) {
+        reinterpret_cast<float4 *>(gquats)[g] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        gopac[g] = gop;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) b[ln * 3 + j] = gmu[j];
+    __syncwarp();
+    for (int f = ln; f < 3 * nv; f += 32) gmeans[3 * g0 + f] = b[f];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 3; ++j) b[ln * 3 + j] = gs[j];
+    __syncwarp();
+    for (int f = ln; f < 3 * nv; f += 32) gscales[3 * g0 + f] = b[f];
+    __syncwarp();
+    const int F = 3 * K;
+#pragma unroll
+    for (int i = 0; i < 48; ++i)
+        if (i < F) b[ln * 49 + i] = gshv[i];
+    __syncwarp();
+    float *dst = gsh + (long long)F * g0;
+    for (int j = 0; j < nv; ++j)
+        for (int i = ln; i < F; i += 32) dst[j * F + i] = b[j * 49 + i];
 }
 
 }  // namespace

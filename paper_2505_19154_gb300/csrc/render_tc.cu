@@ -970,6 +970,10 @@ __global__ void __launch_bounds__(256, 1)
         }
         cp_async_commit();
     };
+        if (nbat > 0) {  // the ids' latency runs under the staging wait
+            load_gid(0);
+            load_gid(1);
+        }
         // this item's staged dF: both halves are waited for also when the
         // item has no batch, so that the staging buffers are quiet before reuse
         {
@@ -990,8 +994,6 @@ __global__ void __launch_bounds__(256, 1)
         }
         if (nbat == 0) stage_next_A();  // nothing reads Dl for this item
         if (nbat > 0) {
-            load_gid(0);
-            load_gid(1);
             // the staged rows -> registers, 16 rows per warp; every thread has
             // read its share before any hi / lo write overwrites the staging
             float4 vdf[16][kL];
@@ -1011,6 +1013,7 @@ __global__ void __launch_bounds__(256, 1)
             cp_async_wait_all();
             __syncthreads();  // ids of batches 0 and 1 are staged; the staging has been read
             load_rec(0);
+            prefetch_feat(0);
         // dF -> BF16 hi / lo, K-major swizzled
         {
 #pragma unroll
@@ -1037,14 +1040,13 @@ __global__ void __launch_bounds__(256, 1)
                 }
             }
         }
-            prefetch_feat(0);
+            fence_async_smem();
+            __syncthreads();  // hi / lo written: their copies into TMEM run while records and features land
+            if (tid == 0) issue_dF_copy();
             cp_async_wait_all();
             fence_async_smem();
             __syncthreads();
-            if (tid == 0) {  // in order: the copies, then the MMAs that read them
-                issue_dF_copy();
-                issue_G();
-            }
+            if (tid == 0) issue_G();  // the same thread as the copies: the MMAs follow them
             pend0 = true;
             if (nbat > 1) {  // G of batch 0 done: the feature stage takes batch 1
                 const bool ok = mbar_wait(&bars[0], ph0);
