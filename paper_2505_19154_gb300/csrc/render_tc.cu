@@ -31,6 +31,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
 #include <cstring>
 
 #include "fhgs_internal.cuh"
@@ -590,8 +591,11 @@ __device__ __forceinline__ void rs_step(float *v, int lane, int off) {
 // Th is followed by Tl (and Dh by Dl): the M=128 MMAs with only 64 real rows
 // (the moments; dFe^T at DN = 64) read their second M block from the next
 // buffer and those rows are unused.
-template <int DN>
+template <int DN, int kG>
 struct BwdCfg {
+    static constexpr int kThreads = 128 * kG;  // kG groups of 4 warps over the half tile's 128 pixels
+    static constexpr int kJ = kBB / kG;        // Gaussians per thread and batch
+    static constexpr int kRecStages = kG == 2 ? 3 : 2;  // with 2, the drain reads its records from global
     static constexpr int kNBlk = DN / 64;
     static constexpr int kOffW = 0;
     static constexpr int kOffDh = kOffW + 128 * 128;
@@ -602,11 +606,11 @@ struct BwdCfg {
     static constexpr int kOffF = kOffX + 2 * 16 * 128;
     static constexpr int kOffRec = kOffF + kNBlk * kBB * 128;
     static constexpr int kRecBytes = kBB * 48;
-    static constexpr int kOffGid = kOffRec + 3 * kRecBytes;  // three record stages: b-1 (drain), b, b+1
+    static constexpr int kOffGid = kOffRec + kRecStages * kRecBytes;  // record stages: (b-1 for the drain,) b, b+1
     static constexpr int kOffRgb = kOffGid + 4 * kBB * 4;    // ids of b-1 .. b+2
     static constexpr int kOffFlag = kOffRgb + 2 * kBB * 3 * 4;  // [2 batches][64][3] colour sums
-    static constexpr int kOffXch = kOffFlag + 16;          // [2 batches][2 groups] masks; then per pixel: P1, S1, T, S
-    static constexpr int kOffBar = kOffXch + 128 * 16;
+    static constexpr int kOffXch = kOffFlag + 16;  // [2 batches][64 bits] masks; then per pixel: P, S of groups 1.., T, S
+    static constexpr int kOffBar = kOffXch + 128 * 4 * (2 * (kG - 1) + 2);
     static constexpr int kSmem = 1024 + kOffBar + 64;
     static_assert(kSmem <= 232448, "backward CTA exceeds the opt-in shared memory");
     static constexpr int kTmemCols = 512;
@@ -616,21 +620,23 @@ struct BwdCfg {
     static_assert(kColD + DN <= kTmemCols, "dF hi / lo exceed tensor memory");
 };
 
-// 256 threads: two groups of 4 warps share the half tile's 128 pixels; group g
-// handles Gaussians [32 g, 32 g + 32) of each batch.  Back to front, group 1's
-// Gaussians come first: it runs the App. A.2 recursion with the true suffix
-// sum S, while group 0 runs it from S = 0 and then subtracts
-// G_k (S + S_1) / (1 - alpha_k), with S_1 the sum of w g over group 1's
-// Gaussians; transmittance needs only group 1's product of (1 - alpha).
-template <int DN>
-__global__ void __launch_bounds__(256, 1)
+// kG groups of 4 warps share the half tile's 128 pixels; group g handles
+// Gaussians [kJ g, kJ g + kJ) of each batch.  Back to front, the last
+// group's Gaussians come first: it runs the App. A.2 recursion with the true
+// suffix sum S, while group g < kG-1 runs it from S = 0 and then subtracts
+// G_k (S + S_>g) / (1 - alpha_k), with S_>g the sum of w g over the later
+// groups' Gaussians; transmittance needs the later groups' products of
+// (1 - alpha).
+template <int DN, int kG>
+__global__ void __launch_bounds__(128 * kG, 1)
     k_render_bwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                     const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats, int D,
                     const float *__restrict__ Tfin, const int32_t *__restrict__ lastv,
                     const float *__restrict__ grgb, const float *__restrict__ gfeat,
                     const __grid_constant__ CUtensorMap dfm, float *g2d, float *gfeatures, unsigned *status,
                     int n_items) {
-    using C = BwdCfg<DN>;
+    using C = BwdCfg<DN, kG>;
+    constexpr int kJ = C::kJ;
     if ((int)blockIdx.x >= n_items) return;  // uniform over the CTA
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
@@ -642,9 +648,9 @@ __global__ void __launch_bounds__(256, 1)
     uint8_t *sX = sm + C::kOffX;
     auto sRgb = [&](int b) { return reinterpret_cast<float *>(sm + C::kOffRgb) + (b & 1) * kBB * 3; };
     auto sMask = [&](int b) { return reinterpret_cast<uint32_t *>(sm + C::kOffFlag) + (b & 1) * 2; };
-    float *xP1 = reinterpret_cast<float *>(sm + C::kOffXch);  // [128] group 1's prod (1 - alpha)
-    float *xS1 = xP1 + 128;                                    // [128] group 1's sum w g
-    float *xT = xS1 + 128;                                     // [128] T after the batch
+    float *xP = reinterpret_cast<float *>(sm + C::kOffXch);  // [kG-1][128] group g's prod (1 - alpha), g >= 1
+    float *xSg = xP + (kG - 1) * 128;                          // [kG-1][128] group g's sum w g, g >= 1
+    float *xT = xSg + (kG - 1) * 128;                          // [128] T after the batch
     float *xS = xT + 128;                                      // [128] S after the batch
     // [0] G, [1] dFe + moments, [2] dF staging of pixels 0..63, [3] of pixels 64..127
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + C::kOffBar);
@@ -653,7 +659,7 @@ __global__ void __launch_bounds__(256, 1)
     // counter only grows, so no slot is ever reset, and a slot's next writer
     // is two items later, past at least one barrier of every thread
     unsigned long long *smax = reinterpret_cast<unsigned long long *>(bars + 5);
-    auto srec = [&](int stg) { return reinterpret_cast<GRec *>(sm + C::kOffRec + stg * C::kRecBytes); };
+    auto srec = [&](int b) { return reinterpret_cast<GRec *>(sm + C::kOffRec + (b % C::kRecStages) * C::kRecBytes); };
     auto sgid = [&](int b) { return reinterpret_cast<uint32_t *>(sm + C::kOffGid + (b & 3) * kBB * 4); };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, grp = tid >> 7, pidx = tid & 127;
@@ -673,7 +679,7 @@ __global__ void __launch_bounds__(256, 1)
     if (tid < 2 * kBB) sRgb(0)[3 * tid] = sRgb(0)[3 * tid + 1] = sRgb(0)[3 * tid + 2] = 0.f;  // both slots
     if (tid < 4) sMask(0)[tid] = 0u;
     // pixel-moment rows of X: X[n][p] for p = i + 16 j
-    for (int q = tid; q < 16 * 128; q += 256) {
+    for (int q = tid; q < 16 * 128; q += C::kThreads) {
         const int n = q >> 7, pp = q & 127;
         const float i = (float)(pp & 15), jv = (float)(pp >> 4);
         const float val = n == 0 ? 1.f : n == 1 ? i : n == 2 ? jv : n == 3 ? i * i : n == 4 ? i * jv
@@ -747,7 +753,7 @@ __global__ void __launch_bounds__(256, 1)
     // the drain of batch db of an item (moments and colour sums into the
     // footprint gradients, the feature-gradient block into grad_features);
     // the item's geometry is passed in, it may be the previous item's
-    auto drain = [&](int db, int dnbat_end, int dx0, int dy0, float *dg2dc, int dchunk, int dd0) {
+    auto drain = [&](int db, int dnbat_end, int dx0, int dy0, float *dg2dc, const GRec *drec, int dchunk, int dd0) {
         const int dbe = dnbat_end - db * kBB, dnb = dbe - max(0, dbe - kBB);
         const int q = warp & 3;
         // moments: lanes 0..63 hold the T-hi part of Gaussian (lane), read by
@@ -763,7 +769,8 @@ __global__ void __launch_bounds__(256, 1)
             float m[16];
             tmem_ld16(tM + ((uint32_t)(q * 32) << 16), m);
             if (mine) {
-                const GRec r = srec(db % 3)[j];
+                // the batch's records: still staged with three stages, else from global (L2)
+                const GRec r = C::kRecStages == 3 ? srec(db)[j] : drec[gid];
                 // moments about the pixel grid: dx = i - a, dy = j - b
                 const float a = r.a.x - (float)dx0 - 0.5f, bb = r.a.y - (float)dy0 - 0.5f;
                 const float M0 = m[0], Mi = m[1], Mj = m[2], Mii = m[3], Mij = m[4], Mjj = m[5];
@@ -782,34 +789,36 @@ __global__ void __launch_bounds__(256, 1)
         }
         if (want_fg && (DN >= 128 || q < 2)) {
             // lane l of warp w holds channel 128 mb + 32 (w % 4) + l of every
-            // Gaussian of its columns.  DN = 256: group g takes channel block
-            // g, all 64 Gaussians; DN <= 128: Gaussians [32 g, 32 g + 32).
-            // A 32 x 32 block goes through the warp's 4 KB of the t buffers
-            // (free: the MMAs that read them are done), so that each lane
-            // then adds 4 consecutive channels of one Gaussian: 4 Gaussians x
-            // 128 contiguous bytes per vector reduction.
-            const int mb = DN >= 256 ? grp : 0;
-            const int j0 = DN >= 256 ? 0 : grp * 32;
+            // Gaussian of its columns.  DN = 256: channel block g % 2 and
+            // Gaussians [128 / kG * (g / 2), + 128 / kG); DN <= 128: Gaussians
+            // [kJ g, kJ g + kJ).  Each kJ x 32 block goes through the warp's
+            // share of the t buffers (free: the MMAs that read them are done),
+            // so that each lane then adds 4 consecutive channels of one
+            // Gaussian: 4 Gaussians x 128 contiguous bytes per vector reduction.
+            const int mb = DN >= 256 ? (grp & 1) : 0;
+            const int jn = DN >= 256 ? 128 / kG : kJ;
+            const int j0 = DN >= 256 ? (grp >> 1) * jn : grp * kJ;
             const uint64_t vmask = dnb >= 64 ? ~0ull : ((1ull << dnb) - 1ull);
             const uint64_t msk = ((((uint64_t)sMask(db)[1] << 32) | sMask(db)[0]) & vmask) >> j0;
-            float *stage = reinterpret_cast<float *>(sTh) + warp * (32 * 32);
+            float *stage = reinterpret_cast<float *>(sTh) + warp * (kJ * 32);
             const int sub = lane >> 3, q4 = (lane & 7) * 4;
             float *dst = gfeatures + dd0 + mb * 128 + q * 32 + q4;
             const uint32_t *ids = sgid(db) + j0;
 #pragma unroll 1
-            for (int h = 0; h < (DN >= 256 ? 2 : 1); ++h) {
-                const uint32_t m32 = (uint32_t)(msk >> (32 * h));
-                if (m32 == 0u) continue;  // warp-uniform
-                float v[32];
-                tmem_ld32(tF + mb * kBB + j0 + 32 * h + ((uint32_t)(q * 32) << 16), v);
+            for (int h = 0; h < jn / kJ; ++h) {
+                const uint32_t mh = (uint32_t)(msk >> (kJ * h)) & (kJ == 32 ? 0xFFFFFFFFu : 0xFFFFu);
+                if (mh == 0u) continue;  // warp-uniform
+                float v[kJ];
+                if constexpr (kJ == 32) tmem_ld32(tF + mb * kBB + j0 + kJ * h + ((uint32_t)(q * 32) << 16), v);
+                else tmem_ld16(tF + mb * kBB + j0 + kJ * h + ((uint32_t)(q * 32) << 16), v);
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) stage[jj * 32 + lane] = v[jj];
+                for (int jj = 0; jj < kJ; ++jj) stage[jj * 32 + lane] = v[jj];
                 __syncwarp();
 #pragma unroll
-                for (int it = 0; it < 8; ++it) {
+                for (int it = 0; it < kJ / 4; ++it) {
                     const int jj = it * 4 + sub;
-                    if ((m32 >> jj) & 1u)
-                        atomicAdd(reinterpret_cast<float4 *>(dst + (size_t)ids[32 * h + jj] * D),
+                    if ((mh >> jj) & 1u)
+                        atomicAdd(reinterpret_cast<float4 *>(dst + (size_t)ids[kJ * h + jj] * D),
                                   *reinterpret_cast<const float4 *>(stage + jj * 32 + q4));
                 }
                 __syncwarp();
@@ -875,6 +884,7 @@ __global__ void __launch_bounds__(256, 1)
     bool have_prev = false;
     int prev_b = 0, prev_end = 0, prev_x0 = 0, prev_y0 = 0, prev_chunk = 0, prev_d0 = 0;
     float *prev_g2dc = g2d;
+    const GRec *prev_rec = pv.rec;
     constexpr int kL = DN >= 128 ? DN / 128 : 1;
     int k = 0;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++k) {
@@ -921,7 +931,7 @@ __global__ void __launch_bounds__(256, 1)
             if (warp == 0) stage_half(it, 1);
             pendB = true;
             tc_after();
-            drain(prev_b, prev_end, prev_x0, prev_y0, prev_g2dc, prev_chunk, prev_d0);
+            drain(prev_b, prev_end, prev_x0, prev_y0, prev_g2dc, prev_rec, prev_chunk, prev_d0);
             tc_before();
             __syncthreads();
             if (tid < kBB) sRgb(prev_b)[3 * tid] = sRgb(prev_b)[3 * tid + 1] = sRgb(prev_b)[3 * tid + 2] = 0.f;
@@ -945,11 +955,11 @@ __global__ void __launch_bounds__(256, 1)
         }
         cp_async_commit();
     };
-    auto load_rec = [&](int b) {  // records of batch b (stage b % 3; its ids have landed)
+    auto load_rec = [&](int b) {  // records of batch b (its stage; its ids have landed)
         if (b < nbat) {
             const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
             if (tid < nb) {
-                const uint32_t dst = smem_u32(srec(b % 3) + tid);
+                const uint32_t dst = smem_u32(srec(b) + tid);
                 const GRec *src = rec + sgid(b)[tid];
                 cp_async16(dst, &src->a, true);
                 cp_async16(dst + 16, &src->b, true);
@@ -963,7 +973,7 @@ __global__ void __launch_bounds__(256, 1)
         const uint32_t *ids = sgid(b);
         constexpr int kCPR = DN / 8;
 #pragma unroll 4
-        for (int q = tid; q < kBB * kCPR; q += 256) {
+        for (int q = tid; q < kBB * kCPR; q += C::kThreads) {
             const int g = q / kCPR, c = q - g * kCPR;
             cp_async16(sF_s + (c >> 3) * (kBB * 128) + swz(g, c & 7), feats + (size_t)ids[g] * D + d0 + c * 8,
                        g < nb);
@@ -996,10 +1006,11 @@ __global__ void __launch_bounds__(256, 1)
         if (nbat > 0) {
             // the staged rows -> registers, 16 rows per warp; every thread has
             // read its share before any hi / lo write overwrites the staging
-            float4 vdf[16][kL];
+            constexpr int kRows = 32 / kG;  // staged rows per warp
+            float4 vdf[kRows][kL];
 #pragma unroll
-            for (int rr = 0; rr < 16; ++rr) {
-                const int prow = warp * 16 + rr;
+            for (int rr = 0; rr < kRows; ++rr) {
+                const int prow = warp * kRows + rr;
                 const int qx = x0 + (prow & 15), qy = y0 + (prow >> 4);
                 const bool qin = qx < cam.W && qy < cam.H && gfeat != nullptr;
                 const uint8_t *row = (prow < 64 ? sDl : sDh) + (prow & 63) * (DN * 4);
@@ -1017,8 +1028,8 @@ __global__ void __launch_bounds__(256, 1)
         // dF -> BF16 hi / lo, K-major swizzled
         {
 #pragma unroll
-            for (int rr = 0; rr < 16; ++rr) {
-                const int prow = warp * 16 + rr;
+            for (int rr = 0; rr < kRows; ++rr) {
+                const int prow = warp * kRows + rr;
 #pragma unroll
                 for (int li = 0; li < kL; ++li) {
                     const int f = li * 128 + lane * 4;
@@ -1086,14 +1097,15 @@ __global__ void __launch_bounds__(256, 1)
                 stage_next_A();
             }
             tc_after();
-            const GRec *R = srec(b % 3);
-            float Gv[32];
-            tmem_ld32(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * 32, Gv);
-            float al[32], gx[32], Tj[32];
+            const GRec *R = srec(b);
+            float Gv[kJ];
+            if constexpr (kJ == 32) tmem_ld32(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * kJ, Gv);
+            else tmem_ld16(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * kJ, Gv);
+            float al[kJ], gx[kJ], Tj[kJ];
             float P = 1.f;
     #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-                const int j = grp * 32 + jj;
+            for (int jj = 0; jj < kJ; ++jj) {
+                const int j = grp * kJ + jj;
                 const float4 A4 = R[j].a, B4 = R[j].b;
                 const float dx = fpx - A4.x, dy = fpy - A4.y;
                 const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
@@ -1105,7 +1117,7 @@ __global__ void __launch_bounds__(256, 1)
                 gx[jj] = (ok && rho <= p.amax) ? G : 0.f;
                 P *= 1.f - al[jj];
             }
-            if (grp == 1) xP1[pidx] = P;
+            if (grp >= 1) xP[(grp - 1) * 128 + pidx] = P;
             // batch b+1's records and features (requested before this batch's
             // alphas) have landed, and this batch's G has left TMEM: G of batch
             // b+1 runs under the rest of batch b
@@ -1117,23 +1129,28 @@ __global__ void __launch_bounds__(256, 1)
                 if (tid == 0) issue_G();
                 pend0 = true;
             }
-            // T after this group's Gaussians, then T before each of them
-            const float Tend = grp == 1 ? T : __fdividef(T, xP1[pidx]);
+            // T after this group's Gaussians (the later groups' products of
+            // (1 - alpha) divided out), then T before each of them
+            float Pl = 1.f;
+#pragma unroll
+            for (int m = 1; m < kG; ++m)
+                if (m > grp) Pl *= xP[(m - 1) * 128 + pidx];
+            const float Tend = grp == kG - 1 ? T : __fdividef(T, Pl);
             const float Tstart = __fdividef(Tend, P);
             {
                 float t = Tstart;
     #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) {
+                for (int jj = 0; jj < kJ; ++jj) {
                     Tj[jj] = t;
                     t *= 1.f - al[jj];
                 }
             }
             // App. A.2 back to front: dL/dalpha_k = T_k g_k - S_k / (1 - alpha_k);
-            // Gv becomes t_k = G dL/drho (group 0: still without S + S_1)
-            float Sg = grp == 1 ? S : 0.f;
+            // Gv becomes t_k = G dL/drho (earlier groups: still without S + S_>g)
+            float Sg = grp == kG - 1 ? S : 0.f;
     #pragma unroll
-            for (int jj = 31; jj >= 0; --jj) {
-                const int j = grp * 32 + jj;
+            for (int jj = kJ - 1; jj >= 0; --jj) {
+                const int j = grp * kJ + jj;
                 // selects, not products with zero: records past the batch end are stale
                 const bool c = al[jj] > 0.f;
                 const float w = al[jj] * Tj[jj];
@@ -1143,7 +1160,7 @@ __global__ void __launch_bounds__(256, 1)
                 Sg = c ? Sg + w * g : Sg;
                 Gv[jj] = c ? gx[jj] * dal : 0.f;
             }
-            if (grp == 1) xS1[pidx] = Sg - S;
+            if (grp >= 1) xSg[(grp - 1) * 128 + pidx] = grp == kG - 1 ? Sg - S : Sg;
             // G of batch b+1 (issued after this batch's alphas) is done by now:
             // the feature stage takes batch b+2, a whole iteration ahead
             bool gok = true;
@@ -1160,14 +1177,19 @@ __global__ void __launch_bounds__(256, 1)
             }
             if (b + 2 < nbat) prefetch_feat(b + 2);
             else cp_async_commit();
-            if (grp == 0) {
-                const float Sb = S + xS1[pidx];  // suffix sum entering group 0's Gaussians
+            if (grp < kG - 1) {
+                float Sb = S;  // suffix sum entering this group's Gaussians
+#pragma unroll
+                for (int m = 1; m < kG; ++m)
+                    if (m > grp) Sb += xSg[(m - 1) * 128 + pidx];
     #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) Gv[jj] -= __fdividef(gx[jj] * Sb, 1.f - al[jj]);
-                S = Sb + Sg;
-                T = Tstart;
-                xT[pidx] = T;
-                xS[pidx] = S;
+                for (int jj = 0; jj < kJ; ++jj) Gv[jj] -= __fdividef(gx[jj] * Sb, 1.f - al[jj]);
+                if (grp == 0) {
+                    S = Sb + Sg;
+                    T = Tstart;
+                    xT[pidx] = T;
+                    xS[pidx] = S;
+                }
             }
             // FM of batch b-1 has finished: drain it, then its operands are free
             if (b >= 1) {
@@ -1181,15 +1203,15 @@ __global__ void __launch_bounds__(256, 1)
                     break;
                 }
                 tc_after();
-                drain(b - 1, Lmax, x0, y0, g2dc, chunk, d0);
+                drain(b - 1, Lmax, x0, y0, g2dc, rec, chunk, d0);
                 tc_before();
                 __syncthreads();
                 if (tid < kBB) sRgb(b - 1)[3 * tid] = sRgb(b - 1)[3 * tid + 1] = sRgb(b - 1)[3 * tid + 2] = 0.f;
                 if (tid < 2) sMask(b - 1)[tid] = 0u;
             }
-            // weights (A of dFe) and t hi/lo (A of the moments) of this group's Gaussians
+            // weights (B of dFe^T) and t hi/lo (A of the moments) of this group's Gaussians
     #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < kJ / 8; ++q) {
                 uint4 pw, ph, pl;
                 uint32_t *pwv = &pw.x, *phv = &ph.x, *plv = &pl.x;
     #pragma unroll
@@ -1201,7 +1223,7 @@ __global__ void __launch_bounds__(256, 1)
                     phv[h] = *reinterpret_cast<const uint32_t *>(&th);
                     plv[h] = pack_bf16(Gv[j0] - tb.x, Gv[j0 + 1] - tb.y);
                 }
-                const uint32_t off = swz(pidx, grp * 4 + q);
+                const uint32_t off = swz(pidx, grp * (kJ / 8) + q);
                 *reinterpret_cast<uint4 *>(sW + off) = pw;
                 *reinterpret_cast<uint4 *>(sTh + off) = ph;
                 *reinterpret_cast<uint4 *>(sTl + off) = pl;
@@ -1209,31 +1231,42 @@ __global__ void __launch_bounds__(256, 1)
             // which Gaussians contribute anywhere in the CTA: one OR per warp
             uint32_t cmask = 0;
     #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) cmask |= (al[jj] > 0.f ? 1u : 0u) << jj;
+            for (int jj = 0; jj < kJ; ++jj) cmask |= (al[jj] > 0.f ? 1u : 0u) << jj;
             cmask = __reduce_or_sync(0xffffffffu, cmask);
-            if (lane == 0 && cmask) atomicOr(&sMask(b)[grp], cmask);
+            if (lane == 0 && cmask) atomicOr(&sMask(b)[(grp * kJ) >> 5], cmask << ((grp * kJ) & 31));
             // colour sums sum_p w dC_p per Gaussian; channel c is summed by slice
             // c % (number of slices).  A reduce-scatter over the warp's 32 pixels
-            // leaves lane l with the warp's sum for Gaussian 32 grp + l.
+            // leaves lane l with the warp's sum for Gaussian kJ grp + l (32
+            // per group), or lanes 2l and 2l+1 with that of kJ grp + l (16).
             if (cmask) {
     #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (c % nch != chunk) continue;
                     const float dc = c == 0 ? dC0 : (c == 1 ? dC1 : dC2);
-                    float v[32];
+                    float v[kJ];
     #pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) v[jj] = al[jj] * Tj[jj] * dc;
-                    rs_step<16>(v, lane, 16);
-                    rs_step<8>(v, lane, 8);
-                    rs_step<4>(v, lane, 4);
-                    rs_step<2>(v, lane, 2);
-                    rs_step<1>(v, lane, 1);
-                    if (cmask & (1u << lane)) atomicAdd(&sRgb(b)[3 * (grp * 32 + lane) + c], v[0]);
+                    for (int jj = 0; jj < kJ; ++jj) v[jj] = al[jj] * Tj[jj] * dc;
+                    if constexpr (kJ == 32) {
+                        rs_step<16>(v, lane, 16);
+                        rs_step<8>(v, lane, 8);
+                        rs_step<4>(v, lane, 4);
+                        rs_step<2>(v, lane, 2);
+                        rs_step<1>(v, lane, 1);
+                        if (cmask & (1u << lane)) atomicAdd(&sRgb(b)[3 * (grp * kJ + lane) + c], v[0]);
+                    } else {
+                        rs_step<kJ / 2>(v, lane, 16);
+                        rs_step<kJ / 4>(v, lane, 8);
+                        rs_step<kJ / 8>(v, lane, 4);
+                        rs_step<kJ / 16>(v, lane, 2);
+                        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+                        const int jl = lane >> 1;
+                        if (!(lane & 1) && (cmask & (1u << jl))) atomicAdd(&sRgb(b)[3 * (grp * kJ + jl) + c], v[0]);
+                    }
                 }
             }
             fence_async_smem();  // weights and t (generic writes) -> the MMA operands
             __syncthreads();
-            if (grp == 1) {
+            if (grp != 0) {
                 T = xT[pidx];
                 S = xS[pidx];
             }
@@ -1249,6 +1282,7 @@ __global__ void __launch_bounds__(256, 1)
             prev_x0 = x0;
             prev_y0 = y0;
             prev_g2dc = g2dc;
+            prev_rec = rec;
             prev_chunk = chunk;
             prev_d0 = d0;
         }
@@ -1263,7 +1297,7 @@ __global__ void __launch_bounds__(256, 1)
             timeout = true;
         } else {
             tc_after();
-            drain(prev_b, prev_end, prev_x0, prev_y0, prev_g2dc, prev_chunk, prev_d0);
+            drain(prev_b, prev_end, prev_x0, prev_y0, prev_g2dc, prev_rec, prev_chunk, prev_d0);
         }
     }
     if (timeout) {
@@ -1683,6 +1717,16 @@ void launch_render_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
 #undef FHGS_FWD
 }
 
+// Gaussian groups of the backward CTA (4 warps each): FHGS_BWD_GROUPS = 2 or
+// 4, default 4.
+static int bwd_groups() {
+    static const int g = [] {
+        const char *e = getenv("FHGS_BWD_GROUPS");
+        return (e && atoi(e) == 2) ? 2 : 4;
+    }();
+    return g;
+}
+
 // Tensor map of dL/dfeat as a [rows][D] FP32 matrix with boxes of 16 rows x
 // dn columns (no swizzle; out-of-range elements read as zero).
 static bool make_dF_tmap(CUtensorMap *m, const float *base, long long rows, int D, int dn) {
@@ -1719,19 +1763,22 @@ bool launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
     const int n_items = cs.total_tiles * 2 * (D / dn);
     const dim3 grid((unsigned)max(1, min(n_items, sm_count_current())));
     note_launch(1);
-#define FHGS_BWD(DNV)                                                                                          \
-    case DNV: {                                                                                                \
+#define FHGS_BWD(DNV, GV)                                                                                      \
+    case DNV * 8 + GV: {                                                                                       \
         static std::atomic<unsigned long long> smem_done{0};                                                 \
-        allow_max_smem(smem_done, k_render_bwd_tc<DNV>);                                                     \
-        k_render_bwd_tc<DNV><<<grid, 256, BwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, feats, D, T, \
-                                                                   last, grgb, gfeat, dfm, g2d, gfeatures,      \
-                                                                   status, n_items);                            \
+        allow_max_smem(smem_done, k_render_bwd_tc<DNV, GV>);                                                 \
+        k_render_bwd_tc<DNV, GV><<<grid, BwdCfg<DNV, GV>::kThreads, BwdCfg<DNV, GV>::kSmem, st>>>(            \
+            N, cs, p, pv, bins.gids, bins.ranges, feats, D, T, last, grgb, gfeat, dfm, g2d, gfeatures, status,  \
+            n_items);                                                                                          \
         break;                                                                                                 \
     }
-    switch (dn) {
-        FHGS_BWD(64)
-        FHGS_BWD(128)
-        FHGS_BWD(256)
+    switch (dn * 8 + bwd_groups()) {
+        FHGS_BWD(64, 2)
+        FHGS_BWD(128, 2)
+        FHGS_BWD(256, 2)
+        FHGS_BWD(64, 4)
+        FHGS_BWD(128, 4)
+        FHGS_BWD(256, 4)
         default: break;
     }
 #undef FHGS_BWD
