@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(128 * kG, 1)
     if (warp == 0) tmem_alloc(tslot, C::kTmemCols);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 2);  // two issuers: the feature gradient and the moments
+        mbar_init(&bars[1], (DN >= 256 ? 2 : 1) + 1);  // one issuer per feature-gradient block, one for the moments
         mbar_init(&bars[2], 1);
         mbar_init(&bars[3], 1);
         fence_mbar_init();
@@ -710,11 +710,16 @@ __global__ void __launch_bounds__(128 * kG, 1)
             tmem_cp_128x256b(tDl + ks * 8, sdesc(sDl_s + koff, 16, 1024));
         }
     };
+    // Descriptors are a base plus a constant: the address field is the low 14
+    // bits (byte address / 16) and no sum here reaches 256 KB.
+    const uint64_t dF0 = sdesc(sF_s, 16, 1024), dW0 = sdesc(sW_s, 128 * 128, 1024);
+    const uint64_t dDh0 = sdesc(sDh_s, 128 * 128, 1024), dTh0 = sdesc(sTh_s, 128 * 128, 1024);
+    const uint64_t dX0 = sdesc(sX_s, 16, 1024);
     auto issue_G = [&]() {  // G(px, g) = sum_d dF(px, d) Fe(g, d), hi + lo parts
         tc_after();
 #pragma unroll
         for (int ks = 0; ks < DN / 16; ++ks) {
-            const uint64_t bd = sdesc(sF_s + (ks >> 2) * (kBB * 128) + (ks & 3) * 32, 16, 1024);
+            const uint64_t bd = dF0 + (uint64_t)(((ks >> 2) * (kBB * 128) + (ks & 3) * 32) >> 4);
             mma_bf16_ta(tG, tDh + ks * 8, bd, idG, ks > 0 ? 1u : 0u);
             mma_bf16_ta(tG, tDl + ks * 8, bd, idG, 1u);
         }
@@ -722,31 +727,28 @@ __global__ void __launch_bounds__(128 * kG, 1)
     };
     // dFe^T = dF^T W, one M = 128 block of channels per MMA (TMEM lanes =
     // channels, columns = the batch's Gaussians); for DN = 64 lanes 64..127
-    // read past the channel block and are never drained.  Issued by thread 32.
+    // read past the channel block and are never drained.  Block mb is issued
+    // by thread 32 (1 + mb) (separate accumulators, so no order between them).
     constexpr int kFBlk = DN >= 128 ? DN / 128 : 1;
-    auto issue_F = [&]() {
+    auto issue_F = [&](int mb) {
         tc_after();
         if (want_fg) {
 #pragma unroll
-            for (int ks = 0; ks < 128 / 16; ++ks) {
-                const uint64_t bw = sdesc(sW_s + ks * 2048, 128 * 128, 1024);
-#pragma unroll
-                for (int mb = 0; mb < kFBlk; ++mb)
-                    mma_bf16(tF + mb * kBB, sdesc(sDh_s + mb * 2 * (128 * 128) + ks * 2048, 128 * 128, 1024), bw,
-                             idF, ks > 0 ? 1u : 0u);
-            }
+            for (int ks = 0; ks < 128 / 16; ++ks)
+                mma_bf16(tF + mb * kBB, dDh0 + (uint64_t)((mb * 2 * (128 * 128) + ks * 2048) >> 4),
+                         dW0 + (uint64_t)((ks * 2048) >> 4), idF, ks > 0 ? 1u : 0u);
         }
         mma_commit(&bars[1]);  // arrives at once when nothing was issued
     };
     // moments = T^T X with T hi in rows 0..63 and T lo in rows 64..127 of one
     // M = 128 operand (Tl follows Th): lanes 0..63 get the hi part, 64..127
-    // the lo part.  Issued by thread 64.
+    // the lo part.  Issued by thread 32 (1 + kFBlk).
     auto issue_M = [&]() {
         tc_after();
 #pragma unroll
         for (int ks = 0; ks < 128 / 16; ++ks)
-            mma_bf16(tM, sdesc(sTh_s + ks * 2048, 128 * 128, 1024),
-                     sdesc(sX_s + (ks >> 2) * (16 * 128) + (ks & 3) * 32, 16, 1024), idM, ks > 0 ? 1u : 0u);
+            mma_bf16(tM, dTh0 + (uint64_t)((ks * 2048) >> 4),
+                     dX0 + (uint64_t)(((ks >> 2) * (16 * 128) + (ks & 3) * 32) >> 4), idM, ks > 0 ? 1u : 0u);
         mma_commit(&bars[1]);
     };
 
@@ -1270,8 +1272,9 @@ __global__ void __launch_bounds__(128 * kG, 1)
                 T = xT[pidx];
                 S = xS[pidx];
             }
-            if (tid == 32) issue_F();
-            if (tid == 64) issue_M();
+            if (tid == 32) issue_F(0);
+            if (kFBlk > 1 && tid == 64) issue_F(1);
+            if (tid == 32 * (1 + kFBlk)) issue_M();
             pend1 = true;
         }
         if (timeout) break;
