@@ -468,14 +468,15 @@ __global__ void __launch_bounds__(256, 2)
         if (tid == 0) {
             tc_after();
             const uint32_t wa = sW_s + stg * C::kWBytes, fb = sF_s + (C::kFStages == 2 ? stg : 0) * C::kFBytes;
+            // descriptors as a base plus constants (address field = byte address / 16)
+            const uint64_t a0 = sdesc(wa, 16, 1024), b0 = sdesc(fb, kFB * 128, 1024);
 #pragma unroll
             for (int ks = 0; ks < kFB / 16; ++ks) {
-                const uint64_t ad = sdesc(wa + ks * 32, 16, 1024);
 #pragma unroll
-                for (int nh = 0; nh < C::kNSub; ++nh) {
-                    const uint64_t bd = sdesc(fb + nh * 4 * (kFB * 128) + ks * 2048, kFB * 128, 1024);
-                    mma_bf16(taddr + nh * 256, ad, bd, idesc, (nbatch > 0 || ks > 0) ? 1u : 0u);
-                }
+                for (int nh = 0; nh < C::kNSub; ++nh)
+                    mma_bf16(taddr + nh * 256, a0 + (uint64_t)((ks * 32) >> 4),
+                             b0 + (uint64_t)((nh * 4 * (kFB * 128) + ks * 2048) >> 4), idesc,
+                             (nbatch > 0 || ks > 0) ? 1u : 0u);
             }
             mma_commit(&bar[stg]);
         }
@@ -703,11 +704,12 @@ __global__ void __launch_bounds__(128 * kG, 1)
     // per item from their shared-memory tiles), so the batches of an item
     // read only the feature rows from shared memory
     auto issue_dF_copy = [&]() {
+        const uint64_t ch0 = sdesc(sDh_s, 16, 1024), cl0 = sdesc(sDl_s, 16, 1024);
 #pragma unroll
         for (int ks = 0; ks < DN / 16; ++ks) {
-            const uint32_t koff = (ks >> 2) * (128 * 128) + (ks & 3) * 32;
-            tmem_cp_128x256b(tDh + ks * 8, sdesc(sDh_s + koff, 16, 1024));
-            tmem_cp_128x256b(tDl + ks * 8, sdesc(sDl_s + koff, 16, 1024));
+            const uint64_t koff = (uint64_t)(((ks >> 2) * (128 * 128) + (ks & 3) * 32) >> 4);
+            tmem_cp_128x256b(tDh + ks * 8, ch0 + koff);
+            tmem_cp_128x256b(tDl + ks * 8, cl0 + koff);
         }
     };
     // Descriptors are a base plus a constant: the address field is the low 14
