@@ -179,10 +179,10 @@ def composited_pairs(st, cams, tile=16):
 # source file at capture time: a changed source reports null.
 _CROP_SCALE = (1920 * 1080) / (960 * 544)
 TRAFFIC = {
-    "render_bwd_tc": {"bytes": int((1103.8e6 + 4.8e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "c3cfa1c10ec46a06cdcda63dc2befc05074676b71caef63bd78fe005a7e925b1"},
-    "render_fwd_tc": {"bytes": int((7.7e6 + 1018.7e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "c3cfa1c10ec46a06cdcda63dc2befc05074676b71caef63bd78fe005a7e925b1"},
+    "render_bwd_tc": {"bytes": int((1102.8e6 + 4.5e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "ace97e481ab9854b43cbea08a7180378c3f3b0c90a380be06ed49f6e477066bd"},
+    "render_fwd_tc": {"bytes": int((7.7e6 + 1018.8e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "ace97e481ab9854b43cbea08a7180378c3f3b0c90a380be06ed49f6e477066bd"},
 }
 
 
