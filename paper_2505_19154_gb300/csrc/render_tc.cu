@@ -198,6 +198,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// exp(-q2 / 2) as 2^(q2 * (-log2(e) / 2)) with the base-2 exponential of
+// PTX (ex2.approx): one multiply by a folded constant per evaluation.
+constexpr float kNegHalfLog2e = -0.72134752044448170368f;  // -log2(e) / 2
+__device__ __forceinline__ float gauss_q2(float q2) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(q2 * kNegHalfLog2e));
+    return y;
+}
+
 // Byte offset of 16-byte chunk `c` (0..7) of row `r` inside a 128B-swizzled
 // atom column whose rows are 128 bytes apart (atom base 1024-aligned).
 __device__ __forceinline__ uint32_t swz(uint32_t r, uint32_t c) { return r * 128u + ((c ^ (r & 7u)) << 4); }
@@ -374,7 +383,7 @@ __global__ void __launch_bounds__(256, 2)
             const float4 A4 = R[j].a, B4 = R[j].b;
             const float dx = fpx - A4.x, dy = fpy - A4.y;
             const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
-            const float al = fminf(p.amax, B4.y * __expf(-0.5f * q2));
+            const float al = fminf(p.amax, B4.y * gauss_q2(q2));
             a[jj] = (j < nb && q2 <= p.cut && al >= p.amin) ? al : 0.f;
             l[jj] = P;
             P *= 1.f - a[jj];
@@ -1107,16 +1116,17 @@ __global__ void __launch_bounds__(128 * kG, 1)
             else tmem_ld16(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * kJ, Gv);
             float al[kJ], gx[kJ], Tj[kJ];
             float P = 1.f;
+            const int jlim = min(nb, lastp - bs);  // Gaussians past the batch or the pixel's last
     #pragma unroll
             for (int jj = 0; jj < kJ; ++jj) {
                 const int j = grp * kJ + jj;
                 const float4 A4 = R[j].a, B4 = R[j].b;
                 const float dx = fpx - A4.x, dy = fpy - A4.y;
                 const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
-                const float G = __expf(-0.5f * q2);
+                const float G = gauss_q2(q2);
                 const float rho = B4.y * G;
                 const float aa = fminf(p.amax, rho);
-                const bool ok = (j < nb) && (bs + j < lastp) && (q2 <= p.cut) && (aa >= p.amin);
+                const bool ok = (j < jlim) && (q2 <= p.cut) && (aa >= p.amin);
                 al[jj] = ok ? aa : 0.f;
                 gx[jj] = (ok && rho <= p.amax) ? G : 0.f;
                 P *= 1.f - al[jj];
@@ -1559,7 +1569,7 @@ __global__ void __launch_bounds__(256, 1)
             const float4 A4 = R[j].a, B4 = R[j].b;
             const float dx = fpx - A4.x, dy = fpy - A4.y;
             const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
-            const float al = fminf(p.amax, B4.y * __expf(-0.5f * q2));
+            const float al = fminf(p.amax, B4.y * gauss_q2(q2));
             a[jj] = (j < nb && q2 <= p.cut && al >= p.amin) ? al : 0.f;
             l[jj] = P;
             P *= 1.f - a[jj];
