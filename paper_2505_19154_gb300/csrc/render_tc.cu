@@ -32,6 +32,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdlib>
+#include <type_traits>
 #include <cstring>
 
 #include "fhgs_internal.cuh"
@@ -1162,18 +1163,27 @@ __global__ void __launch_bounds__(128 * kG, 1)
             // App. A.2 back to front: dL/dalpha_k = T_k g_k - S_k / (1 - alpha_k);
             // Gv becomes t_k = G dL/drho (earlier groups: still without S + S_>g)
             float Sg = grp == kG - 1 ? S : 0.f;
+            // the colour part of g only in slice 0 (rC is zero elsewhere)
+            auto recurse = [&](auto with_colour) {
     #pragma unroll
-            for (int jj = kJ - 1; jj >= 0; --jj) {
-                const int j = grp * kJ + jj;
-                // selects, not products with zero: records past the batch end are stale
-                const bool c = al[jj] > 0.f;
-                const float w = al[jj] * Tj[jj];
-                const float4 B4 = R[j].b;
-                const float g = c ? Gv[jj] + rC0 * B4.z + rC1 * B4.w + rC2 * R[j].c.x : 0.f;
-                const float dal = Tj[jj] * g - __fdividef(Sg, 1.f - al[jj]);
-                Sg = c ? Sg + w * g : Sg;
-                Gv[jj] = c ? gx[jj] * dal : 0.f;
-            }
+                for (int jj = kJ - 1; jj >= 0; --jj) {
+                    const int j = grp * kJ + jj;
+                    // selects, not products with zero: records past the batch end are stale
+                    const bool c = al[jj] > 0.f;
+                    const float w = al[jj] * Tj[jj];
+                    float gc = Gv[jj];
+                    if constexpr (decltype(with_colour)::value) {
+                        const float4 B4 = R[j].b;
+                        gc += rC0 * B4.z + rC1 * B4.w + rC2 * R[j].c.x;
+                    }
+                    const float g = c ? gc : 0.f;
+                    const float dal = Tj[jj] * g - __fdividef(Sg, 1.f - al[jj]);
+                    Sg = c ? Sg + w * g : Sg;
+                    Gv[jj] = c ? gx[jj] * dal : 0.f;
+                }
+            };
+            if (chunk == 0) recurse(std::true_type{});
+            else recurse(std::false_type{});
             if (grp >= 1) xSg[(grp - 1) * 128 + pidx] = grp == kG - 1 ? Sg - S : Sg;
             // G of batch b+1 (issued after this batch's alphas) is done by now:
             // the feature stage takes batch b+2, a whole iteration ahead
