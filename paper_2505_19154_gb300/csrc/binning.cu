@@ -64,19 +64,32 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t 
     }
 }
 
-// In-place exclusive scan of a u32 array with one 1024-thread block, four
-// values per thread per step.  Optionally writes the total.
+// In-place exclusive scan of a u32 array with one 1024-thread block.  Each
+// step moves 16384 values: coalesced loads into shared memory, 16
+// consecutive values per thread scanned there, coalesced stores back.  The
+// step count, not the bandwidth, sets the time.  Optionally writes the total.
+constexpr int kScanSmallItems = 16;
+constexpr int kScanSmallStep = 1024 * kScanSmallItems;
+constexpr int kScanSmallSmem = kScanSmallStep * 4 + kScanSmallStep / 32 * 4;  // values, then one pad word per 32
+__device__ __forceinline__ int scan_small_slot(int i) { return i + (i >> 5); }  // pad: conflict-free per-thread rows
 __global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, int total, int64_t *total_out) {
+    extern __shared__ uint32_t sv[];
     __shared__ uint32_t carry;
     __shared__ uint32_t wsum[32];
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int base = 0; base < total; base += 4096) {
-        const int i0 = base + threadIdx.x * 4;
-        uint32_t v[4], tsum = 0;
+    for (int base = 0; base < total; base += kScanSmallStep) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[k] = (i0 + k < total) ? a[i0 + k] : 0u;
+        for (int k = 0; k < kScanSmallItems; ++k) {
+            const int i = k * 1024 + threadIdx.x;
+            sv[scan_small_slot(i)] = base + i < total ? a[base + i] : 0u;
+        }
+        __syncthreads();
+        const int r0 = threadIdx.x * kScanSmallItems;
+        uint32_t v[kScanSmallItems], tsum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanSmallItems; ++k) {
+            v[k] = sv[scan_small_slot(r0 + k)];
             tsum += v[k];
         }
         uint32_t x = tsum;
@@ -99,11 +112,16 @@ __global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, int total, int
         __syncthreads();
         uint32_t run = carry + (threadIdx.x >= 32 ? wsum[(threadIdx.x >> 5) - 1] : 0u) + x - tsum;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (i0 + k < total) a[i0 + k] = run;
+        for (int k = 0; k < kScanSmallItems; ++k) {
+            sv[scan_small_slot(r0 + k)] = run;
             run += v[k];
         }
         __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanSmallItems; ++k) {
+            const int i = k * 1024 + threadIdx.x;
+            if (base + i < total) a[base + i] = sv[scan_small_slot(i)];
+        }
         if (threadIdx.x == 1023) carry = run;
         __syncthreads();
     }
@@ -210,7 +228,9 @@ bool radix_sort_pairs(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, lo
         uint32_t *vo = a_to_b ? vB : vA;
         note_launch(3);
         k_radix_upsweep<<<G, kRadixThreads, 0, st>>>(ki, n, shift, mask, hist);
-        k_scan_small<<<1, 1024, 0, st>>>(hist, kBuckets * G, nullptr);
+        static std::atomic<unsigned long long> scan_done{0};
+        allow_max_smem(scan_done, k_scan_small);
+        k_scan_small<<<1, 1024, kScanSmallSmem, st>>>(hist, kBuckets * G, nullptr);
         k_radix_downsweep<<<G, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n, shift, mask, hist);
         shift += nb;
         a_to_b = !a_to_b;
@@ -558,7 +578,9 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
     const unsigned nparts = (unsigned)((tab + kScanTile - 1) / kScanTile);
     note_launch(3);
     k_scan_reduce<<<nparts, kScanThreads, 0, st>>>(sc.table, tab, sc.partials);
-    k_scan_small<<<1, 1024, 0, st>>>(sc.partials, (int)nparts, bins.n_instances);
+    static std::atomic<unsigned long long> scan_done{0};
+    allow_max_smem(scan_done, k_scan_small);
+    k_scan_small<<<1, 1024, kScanSmallSmem, st>>>(sc.partials, (int)nparts, bins.n_instances);
     k_scan_down<<<nparts, kScanThreads, 0, st>>>(sc.table, tab, sc.partials);
     // 4. tile ranges, then the scatter of Gaussian indices
     note_launch(1);

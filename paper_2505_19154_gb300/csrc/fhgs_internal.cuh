@@ -80,7 +80,10 @@ inline void allow_max_smem(std::atomic<unsigned long long> &done, K kernel) {
     if (done.load(std::memory_order_acquire) & bit) return;
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return;
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) == cudaSuccess)
+    cudaFuncAttributes fa;  // the opt-in limit covers static and dynamic shared memory together
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes) ==
+        cudaSuccess)
         done.fetch_or(bit, std::memory_order_acq_rel);
 }
 
