@@ -625,10 +625,11 @@ struct BwdCfg {
     static constexpr int kSmem = 1024 + kOffBar + 64;
     static_assert(kSmem <= 232448, "backward CTA exceeds the opt-in shared memory");
     static constexpr int kTmemCols = 512;
-    static constexpr int kColM = 64;   // moments, 16 columns
-    static constexpr int kColF = 128;  // dFe^T, 64 columns per block of 128 channels
-    static constexpr int kColD = 256;  // dF hi, then dF lo: DN / 2 columns each
-    static_assert(kColD + DN <= kTmemCols, "dF hi / lo exceed tensor memory");
+    static constexpr int kColGl = 64;   // G's lo part (G's hi part at column 0)
+    static constexpr int kColF = 128;   // dFe^T, 64 columns per block of 128 channels
+    static constexpr int kColM = 256;   // moments, 16 columns
+    static constexpr int kColDl = 384;  // dF lo: DN / 2 columns
+    static_assert(kColDl + DN / 2 <= kTmemCols, "dF lo exceeds tensor memory");
 };
 
 // kG groups of 4 warps share the half tile's 128 pixels; group g handles
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(128 * kG, 1)
 
     if (warp == 0) tmem_alloc(tslot, C::kTmemCols);
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
+        mbar_init(&bars[0], 2);  // G's hi and lo parts, two issuers
         mbar_init(&bars[1], (DN >= 256 ? 2 : 1) + 1);  // one issuer per feature-gradient block, one for the moments
         mbar_init(&bars[2], 1);
         mbar_init(&bars[3], 1);
@@ -702,38 +703,38 @@ __global__ void __launch_bounds__(128 * kG, 1)
     __syncthreads();
     tc_after();
     const uint32_t taddr = *tslot;
-    const uint32_t tG = taddr, tM = taddr + C::kColM, tF = taddr + C::kColF;
-    const uint32_t tDh = taddr + C::kColD, tDl = tDh + DN / 2;
+    const uint32_t tG = taddr, tGl = taddr + C::kColGl, tM = taddr + C::kColM, tF = taddr + C::kColF;
+    const uint32_t tDl = taddr + C::kColDl;
     const uint32_t sW_s = smem_u32(sW), sDh_s = smem_u32(sDh), sDl_s = smem_u32(sDl);
     const uint32_t sTh_s = smem_u32(sTh), sTl_s = smem_u32(sTl), sX_s = smem_u32(sX);
     const uint32_t sF_s = smem_u32(sm + C::kOffF);
     constexpr uint32_t idG = idesc_bf16(128, kBB, false, false);
     constexpr uint32_t idF = idesc_bf16(128, kBB, true, true);
     constexpr uint32_t idM = idesc_bf16(128, 16, true, false);
-    // dF hi / lo of the item live in TMEM as the A operand of G (copied once
-    // per item from their shared-memory tiles), so the batches of an item
-    // read only the feature rows from shared memory
-    auto issue_dF_copy = [&]() {
-        const uint64_t ch0 = sdesc(sDh_s, 16, 1024), cl0 = sdesc(sDl_s, 16, 1024);
+    // G = dF Fe^T in two accumulators, each with its own issuing thread: the
+    // hi part reads dF hi from shared memory (thread 0); the lo part reads dF
+    // lo from TMEM (thread 128), copied there once per item, so that the lo
+    // buffer in shared memory can take the next item's staged dF.
+    auto issue_dF_copy = [&]() {  // dF lo -> TMEM (thread 128, before its first G)
+        const uint64_t cl0 = sdesc(sDl_s, 16, 1024);
 #pragma unroll
-        for (int ks = 0; ks < DN / 16; ++ks) {
-            const uint64_t koff = (uint64_t)(((ks >> 2) * (128 * 128) + (ks & 3) * 32) >> 4);
-            tmem_cp_128x256b(tDh + ks * 8, ch0 + koff);
-            tmem_cp_128x256b(tDl + ks * 8, cl0 + koff);
-        }
+        for (int ks = 0; ks < DN / 16; ++ks)
+            tmem_cp_128x256b(tDl + ks * 8, cl0 + (uint64_t)(((ks >> 2) * (128 * 128) + (ks & 3) * 32) >> 4));
     };
     // Descriptors are a base plus a constant: the address field is the low 14
     // bits (byte address / 16) and no sum here reaches 256 KB.
     const uint64_t dF0 = sdesc(sF_s, 16, 1024), dW0 = sdesc(sW_s, 128 * 128, 1024);
     const uint64_t dDh0 = sdesc(sDh_s, 128 * 128, 1024), dTh0 = sdesc(sTh_s, 128 * 128, 1024);
     const uint64_t dX0 = sdesc(sX_s, 16, 1024);
-    auto issue_G = [&]() {  // G(px, g) = sum_d dF(px, d) Fe(g, d), hi + lo parts
+    const uint64_t dDhK0 = sdesc(sDh_s, 16, 1024);  // dF hi as a K-major A operand
+    auto issue_G = [&](bool lo) {  // G(px, g) = sum_d dF(px, d) Fe(g, d): hi (thread 0) or lo (thread 128)
         tc_after();
 #pragma unroll
         for (int ks = 0; ks < DN / 16; ++ks) {
             const uint64_t bd = dF0 + (uint64_t)(((ks >> 2) * (kBB * 128) + (ks & 3) * 32) >> 4);
-            mma_bf16_ta(tG, tDh + ks * 8, bd, idG, ks > 0 ? 1u : 0u);
-            mma_bf16_ta(tG, tDl + ks * 8, bd, idG, 1u);
+            if (lo) mma_bf16_ta(tGl, tDl + ks * 8, bd, idG, ks > 0 ? 1u : 0u);
+            else mma_bf16(tG, dDhK0 + (uint64_t)(((ks >> 2) * (128 * 128) + (ks & 3) * 32) >> 4), bd, idG,
+                          ks > 0 ? 1u : 0u);
         }
         mma_commit(&bars[0]);
     };
@@ -1067,11 +1068,12 @@ __global__ void __launch_bounds__(128 * kG, 1)
         }
             fence_async_smem();
             __syncthreads();  // hi / lo written: their copies into TMEM run while records and features land
-            if (tid == 0) issue_dF_copy();
+            if (tid == 128) issue_dF_copy();
             cp_async_wait_all();
             fence_async_smem();
             __syncthreads();
-            if (tid == 0) issue_G();  // the same thread as the copies: the MMAs follow them
+            if (tid == 0) issue_G(false);
+            if (tid == 128) issue_G(true);  // the same thread as the copies: the MMAs follow them
             pend0 = true;
             if (nbat > 1) {  // G of batch 0 done: the feature stage takes batch 1
                 const bool ok = mbar_wait(&bars[0], ph0);
@@ -1113,8 +1115,19 @@ __global__ void __launch_bounds__(128 * kG, 1)
             tc_after();
             const GRec *R = srec(b);
             float Gv[kJ];
-            if constexpr (kJ == 32) tmem_ld32(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * kJ, Gv);
-            else tmem_ld16(tG + ((uint32_t)((warp & 3) * 32) << 16) + grp * kJ, Gv);
+            {  // G = hi part + lo part
+                const uint32_t lq = ((uint32_t)((warp & 3) * 32) << 16) + grp * kJ;
+                float gl[kJ];
+                if constexpr (kJ == 32) {
+                    tmem_ld32(tG + lq, Gv);
+                    tmem_ld32(tGl + lq, gl);
+                } else {
+                    tmem_ld16(tG + lq, Gv);
+                    tmem_ld16(tGl + lq, gl);
+                }
+#pragma unroll
+                for (int jj = 0; jj < kJ; ++jj) Gv[jj] += gl[jj];
+            }
             float al[kJ], gx[kJ], Tj[kJ];
             float P = 1.f;
             const int jlim = min(nb, lastp - bs);  // Gaussians past the batch or the pixel's last
@@ -1141,7 +1154,8 @@ __global__ void __launch_bounds__(128 * kG, 1)
             tc_before();
             __syncthreads();
             if (more) {
-                if (tid == 0) issue_G();
+                if (tid == 0) issue_G(false);
+                if (tid == 128) issue_G(true);
                 pend0 = true;
             }
             // T after this group's Gaussians (the later groups' products of
