@@ -295,8 +295,8 @@ __global__ void __launch_bounds__(256, 2)
     // epilogue's last read of it: with two CTAs on an SM, one CTA's batches
     // run while the other's epilogue drains to global memory
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&bar[0], C::kNSub);  // one arrival per accumulator half's issuer
+        mbar_init(&bar[1], C::kNSub);
         fence_mbar_init();
     }
     if (grp == 0) {
@@ -475,19 +475,19 @@ __global__ void __launch_bounds__(256, 2)
             taddr = *tslot;
             have_tmem = true;
         }
-        if (tid == 0) {
+        // each 256-column half of the accumulator has its own issuing thread
+        // (threads 0 and 32): the halves are independent accumulators
+        if (tid == 0 || (C::kNSub > 1 && tid == 32)) {
             tc_after();
+            const int nh = tid >> 5;
             const uint32_t wa = sW_s + stg * C::kWBytes, fb = sF_s + (C::kFStages == 2 ? stg : 0) * C::kFBytes;
             // descriptors as a base plus constants (address field = byte address / 16)
             const uint64_t a0 = sdesc(wa, 16, 1024), b0 = sdesc(fb, kFB * 128, 1024);
 #pragma unroll
-            for (int ks = 0; ks < kFB / 16; ++ks) {
-#pragma unroll
-                for (int nh = 0; nh < C::kNSub; ++nh)
-                    mma_bf16(taddr + nh * 256, a0 + (uint64_t)((ks * 32) >> 4),
-                             b0 + (uint64_t)((nh * 4 * (kFB * 128) + ks * 2048) >> 4), idesc,
-                             (nbatch > 0 || ks > 0) ? 1u : 0u);
-            }
+            for (int ks = 0; ks < kFB / 16; ++ks)
+                mma_bf16(taddr + nh * 256, a0 + (uint64_t)((ks * 32) >> 4),
+                         b0 + (uint64_t)((nh * 4 * (kFB * 128) + ks * 2048) >> 4), idesc,
+                         (nbatch > 0 || ks > 0) ? 1u : 0u);
             mma_commit(&bar[stg]);
         }
         ++nbatch;
