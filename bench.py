@@ -180,9 +180,9 @@ def composited_pairs(st, cams, tile=16):
 _CROP_SCALE = (1920 * 1080) / (960 * 544)
 TRAFFIC = {
     "render_bwd_tc": {"bytes": int((1102.8e6 + 4.5e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "ace97e481ab9854b43cbea08a7180378c3f3b0c90a380be06ed49f6e477066bd"},
-    "render_fwd_tc": {"bytes": int((7.7e6 + 1018.8e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "ace97e481ab9854b43cbea08a7180378c3f3b0c90a380be06ed49f6e477066bd"},
+                      "sha256": "071e69846b069ad97fe0ff6f0a9e8486977e2c397286eae33e6b98a2a00aaefe"},
+    "render_fwd_tc": {"bytes": int((7.6e6 + 1018.6e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "071e69846b069ad97fe0ff6f0a9e8486977e2c397286eae33e6b98a2a00aaefe"},
 }
 
 
