@@ -234,7 +234,8 @@ constexpr int kFB = 64;  // Gaussians per forward batch (MMA K)
 //
 // Loads run ahead of use: the ids of batch b+2, the records of batch b+1 and
 // (once the MMA of batch b-1 has freed its stage) the feature rows of batch
-// b+1 are in flight while batch b is weighed.
+// b+1 are in flight while batch b is weighed.  With one feature stage (DN =
+// 512, two CTAs per SM) batch b's rows load under its own weights.
 template <int DN>
 struct FwdCfg {
     static constexpr int kWBytes = 128 * 128;            // 128 px x 64 BF16 weights
@@ -1019,8 +1020,8 @@ __global__ void __launch_bounds__(128 * kG, 1)
         }
         if (nbat == 0) stage_next_A();  // nothing reads Dl for this item
         if (nbat > 0) {
-            // the staged rows -> registers, 16 rows per warp; every thread has
-            // read its share before any hi / lo write overwrites the staging
+            // the staged rows -> registers, 32 / kG rows per warp; every thread
+            // has read its share before any hi / lo write overwrites the staging
             constexpr int kRows = 32 / kG;  // staged rows per warp
             float4 vdf[kRows][kL];
 #pragma unroll
@@ -1040,32 +1041,32 @@ __global__ void __launch_bounds__(128 * kG, 1)
             __syncthreads();  // ids of batches 0 and 1 are staged; the staging has been read
             load_rec(0);
             prefetch_feat(0);
-        // dF -> BF16 hi / lo, K-major swizzled
-        {
+            // dF -> BF16 hi / lo, K-major swizzled
+            {
 #pragma unroll
-            for (int rr = 0; rr < kRows; ++rr) {
-                const int prow = warp * kRows + rr;
+                for (int rr = 0; rr < kRows; ++rr) {
+                    const int prow = warp * kRows + rr;
 #pragma unroll
-                for (int li = 0; li < kL; ++li) {
-                    const int f = li * 128 + lane * 4;
-                    if (f >= DN) continue;
-                    const float4 x = vdf[rr][li];
-                    const __nv_bfloat162 h01 = __floats2bfloat162_rn(x.x, x.y);
-                    const __nv_bfloat162 h23 = __floats2bfloat162_rn(x.z, x.w);
-                    const float2 b01 = __bfloat1622float2(h01), b23 = __bfloat1622float2(h23);
-                    const __nv_bfloat162 l01 = __floats2bfloat162_rn(x.x - b01.x, x.y - b01.y);
-                    const __nv_bfloat162 l23 = __floats2bfloat162_rn(x.z - b23.x, x.w - b23.y);
-                    const uint32_t off = (f >> 6) * (128 * 128) + swz(prow, (f & 63) >> 3) + ((f & 7) ? 8 : 0);
-                    uint2 hv, lv;
-                    hv.x = *reinterpret_cast<const uint32_t *>(&h01);
-                    hv.y = *reinterpret_cast<const uint32_t *>(&h23);
-                    lv.x = *reinterpret_cast<const uint32_t *>(&l01);
-                    lv.y = *reinterpret_cast<const uint32_t *>(&l23);
-                    *reinterpret_cast<uint2 *>(sDh + off) = hv;
-                    *reinterpret_cast<uint2 *>(sDl + off) = lv;
+                    for (int li = 0; li < kL; ++li) {
+                        const int f = li * 128 + lane * 4;
+                        if (f >= DN) continue;
+                        const float4 x = vdf[rr][li];
+                        const __nv_bfloat162 h01 = __floats2bfloat162_rn(x.x, x.y);
+                        const __nv_bfloat162 h23 = __floats2bfloat162_rn(x.z, x.w);
+                        const float2 b01 = __bfloat1622float2(h01), b23 = __bfloat1622float2(h23);
+                        const __nv_bfloat162 l01 = __floats2bfloat162_rn(x.x - b01.x, x.y - b01.y);
+                        const __nv_bfloat162 l23 = __floats2bfloat162_rn(x.z - b23.x, x.w - b23.y);
+                        const uint32_t off = (f >> 6) * (128 * 128) + swz(prow, (f & 63) >> 3) + ((f & 7) ? 8 : 0);
+                        uint2 hv, lv;
+                        hv.x = *reinterpret_cast<const uint32_t *>(&h01);
+                        hv.y = *reinterpret_cast<const uint32_t *>(&h23);
+                        lv.x = *reinterpret_cast<const uint32_t *>(&l01);
+                        lv.y = *reinterpret_cast<const uint32_t *>(&l23);
+                        *reinterpret_cast<uint2 *>(sDh + off) = hv;
+                        *reinterpret_cast<uint2 *>(sDl + off) = lv;
+                    }
                 }
             }
-        }
             fence_async_smem();
             __syncthreads();  // hi / lo written: their copies into TMEM run while records and features land
             if (tid == 128) issue_dF_copy();
@@ -1131,7 +1132,7 @@ __global__ void __launch_bounds__(128 * kG, 1)
             float al[kJ], gx[kJ], Tj[kJ];
             float P = 1.f;
             const int jlim = min(nb, lastp - bs);  // Gaussians past the batch or the pixel's last
-    #pragma unroll
+#pragma unroll
             for (int jj = 0; jj < kJ; ++jj) {
                 const int j = grp * kJ + jj;
                 const float4 A4 = R[j].a, B4 = R[j].b;
@@ -1168,7 +1169,7 @@ __global__ void __launch_bounds__(128 * kG, 1)
             const float Tstart = __fdividef(Tend, P);
             {
                 float t = Tstart;
-    #pragma unroll
+#pragma unroll
                 for (int jj = 0; jj < kJ; ++jj) {
                     Tj[jj] = t;
                     t *= 1.f - al[jj];
@@ -1179,7 +1180,7 @@ __global__ void __launch_bounds__(128 * kG, 1)
             float Sg = grp == kG - 1 ? S : 0.f;
             // the colour part of g only in slice 0 (rC is zero elsewhere)
             auto recurse = [&](auto with_colour) {
-    #pragma unroll
+#pragma unroll
                 for (int jj = kJ - 1; jj >= 0; --jj) {
                     const int j = grp * kJ + jj;
                     // selects, not products with zero: records past the batch end are stale
@@ -1220,7 +1221,7 @@ __global__ void __launch_bounds__(128 * kG, 1)
 #pragma unroll
                 for (int m = 1; m < kG; ++m)
                     if (m > grp) Sb += xSg[(m - 1) * 128 + pidx];
-    #pragma unroll
+#pragma unroll
                 for (int jj = 0; jj < kJ; ++jj) Gv[jj] -= __fdividef(gx[jj] * Sb, 1.f - al[jj]);
                 if (grp == 0) {
                     S = Sb + Sg;
@@ -1248,11 +1249,11 @@ __global__ void __launch_bounds__(128 * kG, 1)
                 if (tid < 2) sMask(b - 1)[tid] = 0u;
             }
             // weights (B of dFe^T) and t hi/lo (A of the moments) of this group's Gaussians
-    #pragma unroll
+#pragma unroll
             for (int q = 0; q < kJ / 8; ++q) {
                 uint4 pw, ph, pl;
                 uint32_t *pwv = &pw.x, *phv = &ph.x, *plv = &pl.x;
-    #pragma unroll
+#pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     const int j0 = 8 * q + 2 * h;
                     pwv[h] = pack_bf16(al[j0] * Tj[j0], al[j0 + 1] * Tj[j0 + 1]);
@@ -1268,7 +1269,7 @@ __global__ void __launch_bounds__(128 * kG, 1)
             }
             // which Gaussians contribute anywhere in the CTA: one OR per warp
             uint32_t cmask = 0;
-    #pragma unroll
+#pragma unroll
             for (int jj = 0; jj < kJ; ++jj) cmask |= (al[jj] > 0.f ? 1u : 0u) << jj;
             cmask = __reduce_or_sync(0xffffffffu, cmask);
             if (lane == 0 && cmask) atomicOr(&sMask(b)[(grp * kJ) >> 5], cmask << ((grp * kJ) & 31));
@@ -1277,12 +1278,12 @@ __global__ void __launch_bounds__(128 * kG, 1)
             // leaves lane l with the warp's sum for Gaussian kJ grp + l (32
             // per group), or lanes 2l and 2l+1 with that of kJ grp + l (16).
             if (cmask) {
-    #pragma unroll
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (c % nch != chunk) continue;
                     const float dc = c == 0 ? dC0 : (c == 1 ? dC1 : dC2);
                     float v[kJ];
-    #pragma unroll
+#pragma unroll
                     for (int jj = 0; jj < kJ; ++jj) v[jj] = al[jj] * Tj[jj] * dc;
                     if constexpr (kJ == 32) {
                         rs_step<16>(v, lane, 16);
