@@ -180,9 +180,9 @@ def composited_pairs(st, cams, tile=16):
 _CROP_SCALE = (1920 * 1080) / (960 * 544)
 TRAFFIC = {
     "render_bwd_tc": {"bytes": int((1102.8e6 + 4.5e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "071e69846b069ad97fe0ff6f0a9e8486977e2c397286eae33e6b98a2a00aaefe"},
+                      "sha256": "aa67a76d3133b04e0ac9b2d1cb8f9c6e2f330ab991f5d8fae0fb7ba21331d1b4"},
     "render_fwd_tc": {"bytes": int((7.6e6 + 1018.6e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "071e69846b069ad97fe0ff6f0a9e8486977e2c397286eae33e6b98a2a00aaefe"},
+                      "sha256": "aa67a76d3133b04e0ac9b2d1cb8f9c6e2f330ab991f5d8fae0fb7ba21331d1b4"},
 }
 
 
