@@ -188,7 +188,10 @@ fhgs_status fhgs_render_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fh
  * OVERWRITTEN (not accumulated), device float32 with the shapes of the
  * inputs: grad_means [n][3], grad_scales [n][3], grad_quats [n][4],
  * grad_opac [n], grad_sh [n][K][3], grad_features [n][D] (nullable: skips
- * that contraction).  grad_feat may be NULL (treated as zero). */
+ * that contraction).  grad_feat may be NULL (treated as zero).  The
+ * tensor-core path reads grad_feat through a TMA tensor map; if the driver
+ * cannot encode it, the call returns FHGS_ERR_CUDA before the render
+ * kernel and no gradient is valid. */
 fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *proj, const fhgs_bins *bins,
                             const void *features, fhgs_dtype ftype, int D, const fhgs_camera *cams,
                             int n_cams, const fhgs_params *p, const float *T_final, const int32_t *last,
