@@ -86,6 +86,21 @@ def test_tc_backward_small(d_split):
     check_grads(out["grads"], ref, keys=("features",), tol=1e-2)
 
 
+def test_tc_backward_without_feature_upstream():
+    """grad_feat NULL with grad_features requested: the tensor-core backward
+    stages no dL/dF (zero), so the footprint gradients are the colour-only
+    ones and the feature gradient is exactly zero."""
+    sc = bf16_scene(1200, seed=47, D=256, sh_degree=2)
+    cams = [synth.look_at_camera(synth.ring_position(3.0, 200, -15), 80, 56)]
+    prm = dict(sh_degree=2, bg=(0.3, 0.1, 0.2))
+    dC, _ = synth.upstream(4, 80 * 56, 256)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_tc(sc, cams, prm, dC=dC, dF=None)
+    assert out["grads"]["features"] is not None and not np.any(out["grads"]["features"])
+    ref = oracle.backward(sc, cams, prm, sc["features"], [dC], [np.zeros((80 * 56, 256))], prep=prep)
+    check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities", "sh"), tol=1e-3)
+
+
 @pytest.mark.slow
 def test_tc_config2_forward_backward():
     scene, cams = synth.config2(0)
