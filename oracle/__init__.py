@@ -20,6 +20,10 @@ Steps and the passages they follow:
   * ``render_bwd`` / ``project_bwd`` -- exact derivative of Eq. 4 with the
                         App. A.2 identity for dL/dalpha.
   * ``fuse``         -- compositing-weight-normalised fusion (Sec. 3.1).
+  * ``ndfd`` / ``ndfd_bwd`` -- the NDFD losses L_gt (Eq. 5) and L_cf (Eq. 6,
+                        App. A.1) with the similarity activation of Sec. 3.3,
+                        and their derivative through the weights w (Sec. 3.3,
+                        App. A.2).
 """
 from __future__ import annotations
 
@@ -289,6 +293,62 @@ def project_bwd(scene, cam, params, rec, g2d: dict) -> dict:
     return out
 
 
+NDFD_K, NDFD_LAMBDA = 20.0, 0.5   # slope and threshold of the activation (Sec. 4)
+
+
+def ndfd(rec, feats, gids, ranges_cam, cam, params, fgt, region=None, k=NDFD_K, lam=NDFD_LAMBDA) -> dict:
+    """Per-pixel L_gt and L_cf of `region` (default: image); fgt is the
+    region's ground-truth feature map, (h, w, D) or (h*w, D)."""
+    W, H = int(cam["width"]), int(cam["height"])
+    x0, y0, x1, y1 = region if region is not None else (0, 0, W, H)
+    npx = (x1 - x0) * (y1 - y0)
+    D = int(np.asarray(feats).shape[1])
+    fg = _f64(fgt).reshape(npx, D)
+    Lgt, Lcf, Wn = np.zeros(npx), np.zeros(npx), np.zeros(npx)
+    nc = np.zeros(npx, np.int32)
+    lib().orc_ndfd(_p(rec), _p(_f64(feats)), ctypes.c_int(D), _p(np.ascontiguousarray(gids, np.uint32)),
+                   _p(np.ascontiguousarray(ranges_cam, np.uint32)), _p(camera_array(cam)),
+                   _p(params_array(params)), x0, y0, x1, y1, _p(fg), ctypes.c_double(k),
+                   ctypes.c_double(lam), _p(Lgt), _p(Lcf), _p(Wn), _p(nc))
+    hh, ww = y1 - y0, x1 - x0
+    return dict(Lgt=Lgt.reshape(hh, ww), Lcf=Lcf.reshape(hh, ww), W=Wn.reshape(hh, ww),
+                ncontrib=nc.reshape(hh, ww))
+
+
+def ndfd_bwd(rec, feats, gids, ranges_cam, cam, params, region, fgt, dLgt, dLcf, k=NDFD_K,
+             lam=NDFD_LAMBDA) -> dict:
+    """Footprint gradients of sum_p dLgt L_gt + dLcf L_cf over `region`
+    (rgb is zero: colour does not enter the NDFD losses)."""
+    n = rec.shape[0]
+    D = int(np.asarray(feats).shape[1])
+    x0, y0, x1, y1 = region
+    npx = (x1 - x0) * (y1 - y0)
+    out = dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), op=np.zeros(n), rgb=np.zeros((n, 3)))
+    lib().orc_ndfd_bwd(_p(rec), _p(_f64(feats)), ctypes.c_int(D), _p(np.ascontiguousarray(gids, np.uint32)),
+                       _p(np.ascontiguousarray(ranges_cam, np.uint32)), _p(camera_array(cam)),
+                       _p(params_array(params)), x0, y0, x1, y1, _p(_f64(fgt).reshape(npx, D)),
+                       ctypes.c_double(k), ctypes.c_double(lam), _p(_f64(dLgt).reshape(npx)),
+                       _p(_f64(dLcf).reshape(npx)), _p(out["mean2d"]), _p(out["conic"]), _p(out["op"]))
+    return out
+
+
+def contributors(rec, gids, ranges_cam, cam, params, x: int, y: int, cap: int = 65536) -> dict:
+    """The contributors of pixel (x, y) in compositing order: position in the
+    tile's list, Gaussian id, alpha_i and T_i."""
+    tsz = int((params or {}).get("tile", 16))
+    tiles_x = (int(cam["width"]) + tsz - 1) // tsz
+    t = (y // tsz) * tiles_x + x // tsz
+    s, e = int(ranges_cam[t][0]), int(ranges_cam[t][1])
+    lst = np.ascontiguousarray(np.asarray(gids, np.uint32)[s:e])
+    pos = np.zeros(cap, np.int64)
+    al, T = np.zeros(cap), np.zeros(cap)
+    nc = lib().orc_contributors(_p(rec), _p(lst), ctypes.c_int64(e - s), _p(params_array(params)),
+                                ctypes.c_double(x + 0.5), ctypes.c_double(y + 0.5), ctypes.c_int(cap),
+                                _p(pos), _p(al), _p(T))
+    nc = min(int(nc), cap)
+    return dict(pos=pos[:nc], gid=lst[pos[:nc]].astype(np.int64), alpha=al[:nc], T=T[:nc])
+
+
 # ------------------------------------------------------------- pipelines
 def prepare(scene: dict, cams: list, params: dict | None = None, tile_rect=None, geometry: str = "fp64") -> dict:
     """Binning (FP32 spec), tile lists and FP64 records for every camera.
@@ -376,3 +436,32 @@ def fuse(scene: dict, views: list, maps: list, params: dict | None = None, prep:
     flag = np.zeros(n, np.int32)
     lib().orc_fuse_finalize(ctypes.c_int64(n), ctypes.c_int(D), _p(num), _p(den), _p(out), _p(flag))
     return dict(num=num, den=den, out=out, flag=flag, wflip=wflip)
+
+
+def ndfd_forward(scene: dict, cams: list, params: dict | None, feats, fgt_list, prep: dict | None = None,
+                 k=NDFD_K, lam=NDFD_LAMBDA) -> list:
+    """Per-camera L_gt / L_cf maps (full images)."""
+    prep = prep or prepare(scene, cams, params)
+    return [ndfd(prep["recs"][ci], feats, prep["lists"]["gids"], _cam_ranges(prep["lists"], ci), cam, params,
+                 fgt_list[ci], k=k, lam=lam) for ci, cam in enumerate(cams)]
+
+
+def ndfd_backward(scene: dict, cams: list, params: dict | None, feats, fgt_list, dLgt_list, dLcf_list,
+                  prep: dict | None = None, k=NDFD_K, lam=NDFD_LAMBDA) -> dict:
+    """Gradients of sum_c sum_p (dLgt_c L_gt + dLcf_c L_cf) with respect to
+    means, scales, quats and opacities (sh gets zeros; features are
+    non-differentiable)."""
+    prep = prep or prepare(scene, cams, params)
+    n = len(scene["means"])
+    K = _k(scene)
+    tot = dict(means=np.zeros((n, 3)), scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+               opacities=np.zeros(n), sh=np.zeros((n, K, 3)))
+    for ci, cam in enumerate(cams):
+        W, H = int(cam["width"]), int(cam["height"])
+        g2 = ndfd_bwd(prep["recs"][ci], feats, prep["lists"]["gids"], _cam_ranges(prep["lists"], ci), cam,
+                      params, (0, 0, W, H), fgt_list[ci], dLgt_list[ci], dLcf_list[ci], k=k, lam=lam)
+        gp = project_bwd(scene, cam, params, prep["recs"][ci], g2)
+        for key in ("means", "scales", "quats", "sh"):
+            tot[key] += gp[key]
+        tot["opacities"] += g2["op"]
+    return tot

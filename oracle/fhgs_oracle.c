@@ -25,6 +25,9 @@
  *     with no tiles (the brute-force definition).
  *   - orc_fuse: the compositing-weight-normalised feature fusion
  *     f_g = sum_{v,p} w_g(v,p) F_v(p) / sum_{v,p} w_g(v,p) (Sec. 3.1).
+ *   - orc_ndfd / orc_ndfd_bwd: the NDFD losses L_gt (Eq. 5) and L_cf
+ *     (Eq. 6, App. A.1) with the activation of Sec. 3.3, over the render's
+ *     weights, and their derivative through w (Sec. 3.3, App. A.2).
  *
  * Layouts (all row-major, caller-owned):
  *   camera  double[18]: width, height, fx, fy, cx, cy, then the 3x4
@@ -544,6 +547,33 @@ void orc_render_brute(int64_t n, const double *rec, const double *depth_key, con
 }
 
 /* ---------------------------------------------------- render backward -- */
+/* dL/dalpha of one contributor at pixel centre (cx, cy) -> the footprint of
+ * Gaussian g: alpha = min(alpha_max, op G), G = exp(-q2/2) with q2 = A dx^2 +
+ * 2 B dx dy + C dy^2 and (dx, dy) = centre - mean.  The clamp passes no
+ * gradient.  Accumulates (+=, atomically) into g_op, g_conic and g_mean2d. */
+static void footprint_grad(const double *r, uint32_t g, double G, double dalpha, double cx, double cy,
+                           double amax, double *g_mean2d, double *g_conic, double *g_op)
+{
+    const double rho = r[R_OP] * G;
+    const double drho = rho > amax ? 0.0 : dalpha;
+#pragma omp atomic
+    g_op[g] += G * drho;
+    const double dq2 = -0.5 * r[R_OP] * G * drho;
+    const double dx = cx - r[R_MX], dy = cy - r[R_MY];
+#pragma omp atomic
+    g_conic[3 * g + 0] += dx * dx * dq2;
+#pragma omp atomic
+    g_conic[3 * g + 1] += 2.0 * dx * dy * dq2;
+#pragma omp atomic
+    g_conic[3 * g + 2] += dy * dy * dq2;
+    const double ddx = (2.0 * r[R_A] * dx + 2.0 * r[R_B] * dy) * dq2;
+    const double ddy = (2.0 * r[R_B] * dx + 2.0 * r[R_C] * dy) * dq2;
+#pragma omp atomic
+    g_mean2d[2 * g + 0] -= ddx;
+#pragma omp atomic
+    g_mean2d[2 * g + 1] -= ddy;
+}
+
 /* Gradient of L = sum_p dC_p . rgb_p + dF_p . feat_p over the region with
  * respect to each Gaussian's screen footprint and appearance.  Accumulates
  * (+=) into g_mean2d[n][2], g_conic[n][3] (A, B, C of q2 = A dx^2 +
@@ -600,24 +630,7 @@ void orc_render_bwd(const double *rec, const double *feat, int D, const uint32_t
                         gf[c] += w * df[c];
                     }
                 }
-                const double rho = r[R_OP] * G;
-                const double drho = rho > amax ? 0.0 : dalpha;
-#pragma omp atomic
-                g_op[g] += G * drho;
-                const double dq2 = -0.5 * r[R_OP] * G * drho;
-                const double dx = px + 0.5 - r[R_MX], dy = py + 0.5 - r[R_MY];
-#pragma omp atomic
-                g_conic[3 * g + 0] += dx * dx * dq2;
-#pragma omp atomic
-                g_conic[3 * g + 1] += 2.0 * dx * dy * dq2;
-#pragma omp atomic
-                g_conic[3 * g + 2] += dy * dy * dq2;
-                const double ddx = (2.0 * r[R_A] * dx + 2.0 * r[R_B] * dy) * dq2;
-                const double ddy = (2.0 * r[R_B] * dx + 2.0 * r[R_C] * dy) * dq2;
-#pragma omp atomic
-                g_mean2d[2 * g + 0] -= ddx;
-#pragma omp atomic
-                g_mean2d[2 * g + 1] -= ddy;
+                footprint_grad(r, g, G, dalpha, px + 0.5, py + 0.5, amax, g_mean2d, g_conic, g_op);
             }
         }
         free(ci); free(ca); free(cT); free(cG);
@@ -881,4 +894,168 @@ void orc_fuse_finalize(int64_t n, int D, const double *num, const double *den, d
             flag[g] = 1;
         }
     }
+}
+
+/* ------------------------------------------------------------- NDFD ---- */
+/* Non-differentiable feature driving (Sec. 3.2, App. A "NDFD"): per pixel,
+ * over the same tile list, weights w_i = alpha_i T_i and contributor set as
+ * the render (nearest first, i = 1), with the ground-truth feature f_gt(p)
+ * of that pixel:
+ *   sigma_i = 1 / (1 + exp(k (phi_i - lambda))),  phi_i = cos<f_i, f_gt>
+ *             (Sec. 3.3; phi_i = 0 when either vector is zero);
+ *   L_gt    = sum_i w_i sigma_i                                      (Eq. 5);
+ *   L_cf    = sum_i sigma_i w_i (W_{i-1} - F_{i-1} . f_i),
+ *             W_n = sum_{j<=n} w_j,  F_n = sum_{j<=n} w_j f_j   (Eq. 6, App. A.1).
+ * Features f_i enter L_cf through the plain dot product f_i . f_j (the paper
+ * takes them unit length, where it equals the cosine). */
+static double ndfd_sigma(const double *f, const double *fgt, int D, double kslope, double lam)
+{
+    double dot = 0.0, nf = 0.0, ng = 0.0;
+    for (int c = 0; c < D; ++c) {
+        dot += f[c] * fgt[c];
+        nf += f[c] * f[c];
+        ng += fgt[c] * fgt[c];
+    }
+    const double phi = (nf > 0.0 && ng > 0.0) ? dot / (sqrt(nf) * sqrt(ng)) : 0.0;
+    return 1.0 / (1.0 + exp(kslope * (phi - lam)));
+}
+
+static double dotd(const double *a, const double *b, int D)
+{
+    double s = 0.0;
+    for (int c = 0; c < D; ++c) s += a[c] * b[c];
+    return s;
+}
+
+/* fgt: region pixels x D (row-major in the region).  Outputs per region
+ * pixel: L_gt, L_cf, W_N (total weight) and the contributor count. */
+void orc_ndfd(const double *rec, const double *feat, int D, const uint32_t *gids, const uint32_t *ranges,
+              const double *cam, const double *prm, int x0, int y0, int x1, int y1, const double *fgt,
+              double kslope, double lam, double *out_Lgt, double *out_Lcf, double *out_W,
+              int32_t *out_ncontrib)
+{
+    const int W = (int)cam[0], tsz = (int)prm[P_TILE];
+    const int tiles_x = (W + tsz - 1) / tsz;
+    const int rw = x1 - x0, rh = y1 - y0;
+#pragma omp parallel
+    {
+        int64_t *ci = (int64_t *)malloc(sizeof(int64_t) * ORC_MAXC);
+        double *ca = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *cT = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *cG = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *F = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+            int px = x0 + (int)(idx % rw), py = y0 + (int)(idx / rw);
+            int tile = (py / tsz) * tiles_x + px / tsz;
+            uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+            const uint32_t *list = gids + s;
+            pix_state st;
+            int nc = composite_pixel(px + 0.5, py + 0.5, list, (int64_t)e - s, rec, NULL, 0, prm, &st,
+                                     NULL, ci, ca, cT, cG, ORC_MAXC);
+            if (nc > ORC_MAXC) nc = ORC_MAXC;
+            const double *fg = fgt + (int64_t)D * idx;
+            double Wc = 0.0, Lgt = 0.0, Lcf = 0.0;
+            for (int c = 0; c < D; ++c) F[c] = 0.0;
+            for (int j = 0; j < nc; ++j) {
+                const double *f = feat + (int64_t)D * list[ci[j]];
+                const double w = ca[j] * cT[j];
+                const double sg = ndfd_sigma(f, fg, D, kslope, lam);
+                Lgt += w * sg;
+                Lcf += sg * w * (Wc - dotd(F, f, D));
+                Wc += w;
+                for (int c = 0; c < D; ++c) F[c] += w * f[c];
+            }
+            out_Lgt[idx] = Lgt;
+            out_Lcf[idx] = Lcf;
+            if (out_W) out_W[idx] = Wc;
+            if (out_ncontrib) out_ncontrib[idx] = nc;
+        }
+        free(ci); free(ca); free(cT); free(cG); free(F);
+    }
+}
+
+/* Gradient of L = sum_p dLgt[p] L_gt(p) + dLcf[p] L_cf(p) over the region
+ * with respect to each Gaussian's screen footprint (mean2d, conic) and
+ * opacity; accumulates (+=) into g_mean2d[n][2], g_conic[n][3], g_op[n].
+ * Features and f_gt are constants (non-differentiable).  Per contributor k:
+ *   dL/dw_k = dLgt sigma_k + dLcf (sigma_k (W_{k-1} - F_{k-1} . f_k)
+ *             + sum_{i>k} sigma_i w_i (1 - f_i . f_k))          (Sec. 3.3),
+ * then dL/dalpha_k = T_k dL/dw_k - (1/(1 - alpha_k)) sum_{i>k} w_i dL/dw_i
+ * (App. A.2), and the footprint chain of the render backward.  The suffix
+ * sum over i > k is carried back to front as sum sigma_i w_i and
+ * sum sigma_i w_i f_i. */
+void orc_ndfd_bwd(const double *rec, const double *feat, int D, const uint32_t *gids, const uint32_t *ranges,
+                  const double *cam, const double *prm, int x0, int y0, int x1, int y1, const double *fgt,
+                  double kslope, double lam, const double *dLgt, const double *dLcf, double *g_mean2d,
+                  double *g_conic, double *g_op)
+{
+    const int W = (int)cam[0], tsz = (int)prm[P_TILE];
+    const int tiles_x = (W + tsz - 1) / tsz;
+    const int rw = x1 - x0, rh = y1 - y0;
+    const double amax = prm[P_AMAX];
+#pragma omp parallel
+    {
+        int64_t *ci = (int64_t *)malloc(sizeof(int64_t) * ORC_MAXC);
+        double *ca = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *cT = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *cG = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *sig = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *pre = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *F = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
+        double *Gs = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+            int px = x0 + (int)(idx % rw), py = y0 + (int)(idx / rw);
+            int tile = (py / tsz) * tiles_x + px / tsz;
+            uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
+            const uint32_t *list = gids + s;
+            pix_state st;
+            int nc = composite_pixel(px + 0.5, py + 0.5, list, (int64_t)e - s, rec, NULL, 0, prm, &st,
+                                     NULL, ci, ca, cT, cG, ORC_MAXC);
+            if (nc > ORC_MAXC) nc = ORC_MAXC;
+            const double *fg = fgt + (int64_t)D * idx;
+            const double cgt = dLgt[idx], ccf = dLcf[idx];
+            /* front to back: sigma_k and W_{k-1} - F_{k-1} . f_k */
+            double Wc = 0.0;
+            for (int c = 0; c < D; ++c) F[c] = 0.0;
+            for (int j = 0; j < nc; ++j) {
+                const double *f = feat + (int64_t)D * list[ci[j]];
+                const double w = ca[j] * cT[j];
+                sig[j] = ndfd_sigma(f, fg, D, kslope, lam);
+                pre[j] = Wc - dotd(F, f, D);
+                Wc += w;
+                for (int c = 0; c < D; ++c) F[c] += w * f[c];
+            }
+            /* back to front */
+            double Ss = 0.0, Sw = 0.0;
+            for (int c = 0; c < D; ++c) Gs[c] = 0.0;
+            for (int k = nc - 1; k >= 0; --k) {
+                const uint32_t g = list[ci[k]];
+                const double *f = feat + (int64_t)D * g;
+                const double alpha = ca[k], T = cT[k], w = alpha * T;
+                const double gw = cgt * sig[k] + ccf * (sig[k] * pre[k] + Ss - dotd(Gs, f, D));
+                const double dalpha = T * gw - Sw / (1.0 - alpha);
+                Sw += w * gw;
+                Ss += sig[k] * w;
+                for (int c = 0; c < D; ++c) Gs[c] += sig[k] * w * f[c];
+                footprint_grad(rec + (int64_t)ORC_REC * g, g, cG[k], dalpha, px + 0.5, py + 0.5, amax,
+                               g_mean2d, g_conic, g_op);
+            }
+        }
+        free(ci); free(ca); free(cT); free(cG); free(sig); free(pre); free(F); free(Gs);
+    }
+}
+
+/* The contributors of the pixel with centre (cx, cy) over one depth-sorted
+ * list, exactly as the render composites them: their positions in the list,
+ * alpha_i and T_i.  Returns the count (at most cap are written). */
+int orc_contributors(const double *rec, const uint32_t *list, int64_t len, const double *prm, double cx,
+                     double cy, int cap, int64_t *pos, double *alpha, double *T)
+{
+    double *G = (double *)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
+    pix_state st;
+    int nc = composite_pixel(cx, cy, list, len, rec, NULL, 0, prm, &st, NULL, pos, alpha, T, G, cap);
+    free(G);
+    return nc;
 }
