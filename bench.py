@@ -58,8 +58,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="warm-up + one step, no JSON (for ncu)")
-    ap.add_argument("--workload", choices=["render", "fusion"], default="render",
-                    help="render: fwd+bwd of the 1080p view (the headline); fusion: 3M Gaussians x 64 views")
+    ap.add_argument("--workload", choices=["render", "fusion", "ndfd"], default="render",
+                    help="render: fwd+bwd of the 1080p view (the headline); fusion: 3M Gaussians x 64 views; "
+                         "ndfd: the NDFD losses L_gt, L_cf and their backward on the 1080p view")
     ap.add_argument("--views", type=int, default=64, help="fusion: number of views")
     return ap.parse_args()
 
@@ -538,12 +539,182 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ NDFD
+NDFD_METRIC = "NDFD L_gt+L_cf fwd+bwd Mpix/s at 1M Gaussians, D=512 BF16; % of FP32 ALU roofline"
+NDFD_WORKLOAD = "1M Gaussians, 1920x1080 view, D=512 BF16 unit features and ground-truth map, NDFD fwd+bwd"
+# FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def device_ndfd_inputs(seed, n, cams, D, dev, n_proto=8, block=24, noise=0.5, chunk=1 << 17):
+    """The NDFD input recipe (clustered unit features around n_proto random
+    unit prototypes, cosine to the own prototype from ~0.98 to ~0.3; a
+    ground-truth map of block x block regions each labelled with a prototype
+    plus per-pixel noise, L2-normalised) generated on the device with torch,
+    in row chunks, rounded to BF16.  Returns (features [n, D], feat_gt [P, D])."""
+    import math
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7_000_003 * (seed + 1))
+    protos = torch.randn((n_proto, D), generator=gen, device=dev)
+    protos = protos / protos.norm(dim=1, keepdim=True)
+    feats = torch.empty((n, D), dtype=torch.bfloat16, device=dev)
+    for r0 in range(0, n, chunk):
+        m = min(chunk, n - r0)
+        lab = torch.randint(0, n_proto, (m,), generator=gen, device=dev)
+        lvl = (torch.rand((m,), generator=gen, device=dev) * 2.8 + 0.2) / math.sqrt(D)
+        f = protos[lab] + lvl[:, None] * torch.randn((m, D), generator=gen, device=dev)
+        feats[r0:r0 + m] = (f / f.norm(dim=1, keepdim=True)).to(torch.bfloat16)
+    maps = []
+    for c in cams:
+        h, w = c["height"], c["width"]
+        by, bx = (h + block - 1) // block, (w + block - 1) // block
+        lab = torch.randint(0, n_proto, (by, bx), generator=gen, device=dev)
+        lab = lab.repeat_interleave(block, 0).repeat_interleave(block, 1)[:h, :w].reshape(-1)
+        g = torch.empty((h * w, D), dtype=torch.bfloat16, device=dev)
+        for r0 in range(0, h * w, chunk):
+            m = min(chunk, h * w - r0)
+            x = protos[lab[r0:r0 + m]] + (noise / math.sqrt(D)) * torch.randn((m, D), generator=gen, device=dev)
+            g[r0:r0 + m] = (x / x.norm(dim=1, keepdim=True)).to(torch.bfloat16)
+        maps.append(g)
+    return feats, torch.cat(maps)
+
+
+def ndfd_cpu_baseline(scene, cams, feats, fgt, dLgt, dLcf, max_seconds=25.0, reps_max=3):
+    """The oracle on a bounded sample of the NDFD workload: projection and
+    FP32 binning of every Gaussian, lists of the 64x64 crop's tiles, FP64
+    NDFD forward and backward of its 4096 pixels (the features of the
+    Gaussians those lists hold are gathered from the device each time)."""
+    import torch
+    import oracle
+    from paper_2505_19154_gb300 import synth
+    x0, y0, x1, y1 = synth.CROP3
+    W = cams[0]["width"]
+    pix = torch.tensor([y * W + x for y in range(y0, y1) for x in range(x0, x1)], device=fgt.device)
+    fg = fgt[pix].float().cpu().numpy()
+    a, b = dLgt[pix].cpu().numpy(), dLcf[pix].cpu().numpy()
+    prm = dict(sh_degree=3)
+    t0 = time.time()
+    reps = 0
+    while reps < reps_max and (reps == 0 or time.time() - t0 < max_seconds / 2):
+        prep = oracle.prepare(scene, cams, prm, tile_rect=(x0 // 16, y0 // 16, (x1 - 1) // 16, (y1 - 1) // 16))
+        uniq, inv = np.unique(prep["lists"]["gids"], return_inverse=True)
+        idx = torch.from_numpy(np.ascontiguousarray(uniq, np.int64)).to(feats.device)
+        fc = feats[idx].float().cpu().numpy()
+        rec = prep["recs"][0][uniq]
+        lists = inv.astype(np.uint32)
+        ranges = oracle._cam_ranges(prep["lists"], 0)
+        oracle.ndfd(rec, fc, lists, ranges, cams[0], prm, fg, region=synth.CROP3)
+        oracle.ndfd_bwd(rec, fc, lists, ranges, cams[0], prm, synth.CROP3, fg, a, b)
+        reps += 1
+    dt = time.time() - t0
+    return {"value": round(reps * (x1 - x0) * (y1 - y0) / dt / 1e6, 6), "unit": UNIT,
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{reps} x (project + FP32-spec binning of all {len(scene['means'])} Gaussians, lists of "
+                      f"the 64x64 crop's tiles, FP64 NDFD fwd+bwd of its 4096 pixels)",
+            "seconds": round(dt, 2)}
+
+
+def run_ndfd(args):
+    import torch
+    from paper_2505_19154_gb300 import api, synth
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return   # one view: the NDFD line is a single-GPU measurement
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, cams = synth.config3(rank, n=args.n, D=0)
+    if (args.width, args.height) != (1920, 1080):
+        cams = [dict(cams[0], width=args.width, height=args.height, cx=args.width / 2.0, cy=args.height / 2.0)]
+    D = args.D
+    g = tuple(torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).to(dev)
+              for k in ("means", "scales", "quats", "opacities", "sh"))
+    feats, fgt = device_ndfd_inputs(rank, args.n, cams, D, dev)
+    P = fgt.shape[0]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(9_000_011 + rank)
+    dLgt = torch.randn(P, generator=gen, device=dev)
+    dLcf = torch.randn(P, generator=gen, device=dev)
+    rast = api.Rasterizer(local, sh_degree=3)
+    st0 = rast.prepare(*g, cams)
+    I = st0["n_instances"]
+    rast.capacity = int(I * 1.05) + 1024
+    nc = torch.empty(P, dtype=torch.int32, device=dev)
+    rast.ndfd_forward(st0, feats, fgt, ncontrib=nc)
+    C = int(nc.to(torch.int64).sum().item())   # (pixel, contributor) pairs
+    del st0
+
+    def step():
+        st = rast.prepare(*g, cams, check=False)
+        rast.ndfd_forward(st, feats, fgt)
+        rast.ndfd_backward(st, feats, fgt, dLgt, dLcf)
+
+    W_ = max(3, args.warmup)
+    for _ in range(W_):
+        step()
+    torch.cuda.synchronize()
+    if rast.ctx.sync_status() != api.OK:
+        raise RuntimeError("device status after warm-up")
+    if args.profile_only:
+        step()
+        torch.cuda.synchronize()
+        return
+    clocks = ClockSampler(local)
+    rast.ctx.profile(True)
+    clocks.start()
+    n0 = api.Context.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = max(1, args.steps)
+    e0.record()
+    for _ in range(K):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    launches = api.Context.launch_count() - n0
+    ck = clocks.stop()
+    prof = rast.ctx.profile_read()
+    if rast.ctx.sync_status() != api.OK:
+        raise RuntimeError("device status after timed region")
+    ms = e0.elapsed_time(e1) / K
+    # algorithmic FP32 FLOPs per (pixel, contributor) pair: forward f_gt.f, F.f
+    # and F += w f (3 x 2D); backward f_gt.f, F.f, G.f, F -= w f, G += s w f
+    # (5 x 2D); the backward's front-to-back rebuild of F_N is not counted
+    flops = {"ndfd_fwd": 6 * D * C, "ndfd_bwd": 10 * D * C}
+    tot = sum(v[1] for v in prof.values())
+    per = {k: {"launches": c, "ms": round(t / max(c, 1), 4), "share": round(t / max(tot, 1e-9), 4)}
+           for k, (c, t) in prof.items()}
+    for k, f in flops.items():
+        if k in per:
+            per[k]["fp32_tflops"] = round(f / (per[k]["ms"] * 1e-3) / 1e12, 2)
+    dom = max(("ndfd_fwd", "ndfd_bwd"), key=lambda k: prof.get(k, (0, 0))[1])
+    ach = flops[dom] / (per[dom]["ms"] * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
+            "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz", "traffic": None,
+            "algorithmic_flops": flops[dom]}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = ndfd_cpu_baseline(scene, cams, feats, fgt, dLgt, dLcf)
+    line = {"metric": NDFD_METRIC, "value": round(P / (ms * 1e-3) / 1e6, 2), "unit": UNIT, "n_gpus": 1,
+            "steps": K, "warmup": W_, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (NDFD inputs on the device)",
+            "config": {"workload": NDFD_WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.height,
+                       "feature_dim": D, "tile_instances": I, "contributor_pairs": C,
+                       "l2": "inputs larger than L2 (features 1 GB, ground-truth map 2.1 GB)",
+                       "step": "project + bin/sort + NDFD forward + NDFD backward + projection backward"},
+            "roofline": roof, "kernels": per, "e2e": None, "cpu_baseline": cpu, "clocks": ck,
+            "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "fusion":
         run_fusion(args)
+    elif args.workload == "ndfd":
+        run_ndfd(args)
     else:
         run_ours(args)
 

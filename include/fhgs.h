@@ -217,6 +217,53 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
                                const float *const *maps, int D, const fhgs_params *p, float *num,
                                float *den, float *out, uint32_t flags, void *stream);
 
+/* ------------------------------------------------------------------ NDFD -- */
+/* Non-differentiable feature driving (Sec. 3.2; App. A "NDFD"): per pixel,
+ * over the same depth-sorted tile lists, contributors and Eq. 4 weights
+ * w_i = alpha_i T_i as fhgs_render_fwd (i = 1 nearest), with the pixel's
+ * ground-truth feature f_gt(p):
+ *   sigma_i = 1 / (1 + exp(k (cos<f_i, f_gt(p)> - lambda)))  (Sec. 3.3; the
+ *             cosine is 0 where either vector is zero; the paper fixes
+ *             k = 20, lambda = 0.5 in Sec. 4),
+ *   L_gt(p) = sum_i w_i sigma_i                                   (Eq. 5),
+ *   L_cf(p) = sum_i sigma_i w_i (W_{i-1} - F_{i-1} . f_i),
+ *             W_n = sum_{j<=n} w_j, F_n = sum_{j<=n} w_j f_j  (Eq. 6, App. A.1).
+ * L_cf uses the plain dot product f_i . f_j, which is the cosine for the unit
+ * features the paper assumes: pass L2-normalised features.  No feature image
+ * is rendered or stored.  Arguments as fhgs_render_fwd, plus
+ *   feat_gt [P][D] device, the ground-truth feature of every pixel of every
+ *           camera (packed like the images), same dtype as features,
+ *           16-byte aligned;
+ *   k, lambda  the activation's slope and threshold (finite);
+ *   L_gt, L_cf [P] device float32, out;
+ *   n_contrib  [P] device int32, out, nullable: the number of contributors
+ *              (the i of the sums) of each pixel.
+ * D must be 32, 64, 128, 256 or 512 (else FHGS_ERR_UNSUPPORTED).  Computed in
+ * FP32 on the CUDA cores. */
+fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_bins *bins, const void *features,
+                          const void *feat_gt, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
+                          const fhgs_params *p, float k, float lambda, float *L_gt, float *L_cf, int32_t *n_contrib,
+                          void *stream);
+
+/* Derivative of L = sum_p grad_Lgt[p] L_gt(p) + grad_Lcf[p] L_cf(p) with
+ * respect to the Gaussian parameters, through the weights w only (features
+ * and f_gt are constants, Sec. 3.2):
+ *   dL/dw_k = grad_Lgt sigma_k + grad_Lcf (sigma_k (W_{k-1} - F_{k-1} . f_k)
+ *             + sum_{i>k} sigma_i w_i (1 - f_i . f_k))            (Sec. 3.3),
+ *   dL/dalpha_k = T_k dL/dw_k - (1/(1-alpha_k)) sum_{i>k} w_i dL/dw_i (App. A.2).
+ * The walk recomputes F_N front to back, then goes back to front; nothing
+ * from a forward call is needed.  grad_Lgt, grad_Lcf [P] device float32.  All
+ * gradient outputs are OVERWRITTEN, device float32 with the shapes of
+ * fhgs_render_bwd's: grad_means [n][3], grad_scales [n][3], grad_quats [n][4]
+ * (16-byte aligned), grad_opac [n], grad_sh [n][K][3] (all zero: colour
+ * does not enter the losses).  To train on L_rgb + l1 L_gt + l2 L_cf, scale
+ * grad_Lgt and grad_Lcf and add these gradients to fhgs_render_bwd's. */
+fhgs_status fhgs_ndfd_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *proj, const fhgs_bins *bins,
+                          const void *features, const void *feat_gt, fhgs_dtype ftype, int D,
+                          const fhgs_camera *cams, int n_cams, const fhgs_params *p, float k, float lambda,
+                          const float *grad_Lgt, const float *grad_Lcf, float *grad_means, float *grad_scales,
+                          float *grad_quats, float *grad_opac, float *grad_sh, void *stream);
+
 /* ----------------------------------------------------- allocation-free -- */
 /* Largest n_cams * n accepted by fhgs_render_bwd_noalloc.  Its scratch is
  * 48 bytes per (camera, Gaussian): 12 MiB, reserved on every GPU that loads

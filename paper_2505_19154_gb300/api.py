@@ -26,7 +26,9 @@ NOALLOC_MAX_ENTRIES = 262144  # FHGS_NOALLOC_MAX_ENTRIES of include/fhgs.h
 EXPORTS = ["fhgs_create", "fhgs_destroy", "fhgs_last_error", "fhgs_status_string", "fhgs_abi_version",
            "fhgs_default_params", "fhgs_proj_bytes", "fhgs_total_tiles", "fhgs_reserve", "fhgs_sync_status",
            "fhgs_project", "fhgs_bin_sort", "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features",
-           "fhgs_profile_enable", "fhgs_profile_read", "fhgs_launch_count", "fhgs_render_bwd_noalloc"]
+           "fhgs_profile_enable", "fhgs_profile_read", "fhgs_launch_count", "fhgs_render_bwd_noalloc",
+           "fhgs_ndfd_fwd", "fhgs_ndfd_bwd"]
+NDFD_K, NDFD_LAMBDA = 20.0, 0.5  # the activation's slope and threshold (Sec. 4)
 
 
 class Camera(ctypes.Structure):
@@ -105,12 +107,19 @@ def lib():
                                               ctypes.POINTER(Camera), i32, ctypes.POINTER(Params), f32p, vp, f32p,
                                               f32p, f32p, f32p, f32p, f32p, f32p, f32p, vp]
         L.fhgs_render_bwd_noalloc.restype = i32
+        f32 = ctypes.c_float
+        L.fhgs_ndfd_fwd.argtypes = [vp, i64, vp, ctypes.POINTER(Bins), vp, vp, i32, i32, ctypes.POINTER(Camera), i32,
+                                    ctypes.POINTER(Params), f32, f32, f32p, f32p, vp, vp]
+        L.fhgs_ndfd_bwd.argtypes = [vp, ctypes.POINTER(Gaussians), vp, ctypes.POINTER(Bins), vp, vp, i32, i32,
+                                    ctypes.POINTER(Camera), i32, ctypes.POINTER(Params), f32, f32, f32p, f32p,
+                                    f32p, f32p, f32p, f32p, f32p, vp]
         L.fhgs_profile_enable.argtypes = [vp, i32]
         L.fhgs_profile_read.argtypes = [vp, ctypes.c_char_p, i64]
         L.fhgs_launch_count.argtypes = []
         L.fhgs_launch_count.restype = i64
         for name in ("fhgs_create", "fhgs_reserve", "fhgs_sync_status", "fhgs_project", "fhgs_bin_sort",
-                     "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features", "fhgs_profile_enable",
+                     "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features", "fhgs_ndfd_fwd", "fhgs_ndfd_bwd",
+                     "fhgs_profile_enable",
                      "fhgs_profile_read"):
             getattr(L, name).restype = i32
         _lib = L
@@ -235,6 +244,23 @@ class Context:
                                             self.stream_ptr(stream)))
 
 
+    def ndfd_fwd(self, n, proj, bins, features, feat_gt, D, cams, params, k, lam, Lgt, Lcf, ncontrib=None,
+                 stream=None):
+        ft = BF16 if features.dtype == torch.bfloat16 else F32
+        self.check(lib().fhgs_ndfd_fwd(self.h, int(n), _ptr(proj), ctypes.byref(bins), _ptr(features), _ptr(feat_gt),
+                                       ft, int(D), cams, len(cams), ctypes.byref(params), float(k), float(lam),
+                                       _ptr(Lgt), _ptr(Lcf), _ptr(ncontrib), self.stream_ptr(stream)))
+
+    def ndfd_bwd(self, g, proj, bins, features, feat_gt, D, cams, params, k, lam, dLgt, dLcf, out: dict,
+                 stream=None):
+        ft = BF16 if features.dtype == torch.bfloat16 else F32
+        self.check(lib().fhgs_ndfd_bwd(self.h, ctypes.byref(g), _ptr(proj), ctypes.byref(bins), _ptr(features),
+                                       _ptr(feat_gt), ft, int(D), cams, len(cams), ctypes.byref(params), float(k),
+                                       float(lam), _ptr(dLgt), _ptr(dLcf), _ptr(out["means"]), _ptr(out["scales"]),
+                                       _ptr(out["quats"]), _ptr(out["opacities"]), _ptr(out["sh"]),
+                                       self.stream_ptr(stream)))
+
+
 def render_bwd_noalloc(g, proj, bins, features, D, cams, params, T, last, grgb, gfeat, out: dict, stream=None) -> int:
     """fhgs_render_bwd_noalloc: the backward without a context and without
     allocating (scratch in a fixed device array).  Returns the status code."""
@@ -337,6 +363,32 @@ class Rasterizer:
         self.ctx.render_bwd(st["g"], st["proj"], st["bins"], st["features"], D, st["cams"], params, st["T"],
                             st["last"], grad_rgb.contiguous(),
                             None if grad_feat is None else grad_feat.contiguous(), out)
+        return out
+
+    def ndfd_forward(self, st: dict, features, feat_gt, k: float = NDFD_K, lam: float = NDFD_LAMBDA,
+                     ncontrib=None):
+        """Per-pixel NDFD losses (L_gt, L_cf), each [P] float32, over the
+        prepared views; feat_gt is [P, D] in the features' dtype.  ncontrib,
+        an optional [P] int32 tensor, receives each pixel's contributor count."""
+        P = sum(int(c.width) * int(c.height) for c in st["cams"])
+        D = int(features.shape[1])
+        Lgt = torch.empty(P, dtype=torch.float32, device=self.dev)
+        Lcf = torch.empty(P, dtype=torch.float32, device=self.dev)
+        self.ctx.ndfd_fwd(st["n"], st["proj"], st["bins"], features, feat_gt.contiguous(), D, st["cams"], self.params,
+                          k, lam, Lgt, Lcf, ncontrib)
+        return Lgt, Lcf
+
+    def ndfd_backward(self, st: dict, features, feat_gt, grad_Lgt, grad_Lcf, k: float = NDFD_K,
+                      lam: float = NDFD_LAMBDA) -> dict:
+        """Gradients of sum_p grad_Lgt L_gt + grad_Lcf L_cf with respect to
+        means, scales, quats, opacities (and sh: zeros)."""
+        n, D = st["n"], int(features.shape[1])
+        K = (self.params.sh_degree + 1) ** 2
+        out = dict(means=torch.empty((n, 3), device=self.dev), scales=torch.empty((n, 3), device=self.dev),
+                   quats=torch.empty((n, 4), device=self.dev), opacities=torch.empty(n, device=self.dev),
+                   sh=torch.empty((n, K, 3), device=self.dev))
+        self.ctx.ndfd_bwd(st["g"], st["proj"], st["bins"], features, feat_gt.contiguous(), D, st["cams"],
+                          self.params, k, lam, grad_Lgt.contiguous(), grad_Lcf.contiguous(), out)
         return out
 
     def fuse(self, means, scales, quats, opacities, sh, views: Sequence[dict], maps: Sequence[torch.Tensor],

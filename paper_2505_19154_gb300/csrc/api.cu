@@ -476,6 +476,82 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
     return FHGS_OK;
 }
 
+// Shared argument checks of the two NDFD calls.
+static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, const fhgs_bins *bins,
+                              const void *features, const void *feat_gt, fhgs_dtype ftype, int D,
+                              const fhgs_params *p, float k, float lambda) {
+    fhgs_status s = check_params(ctx, p);
+    if (s == FHGS_OK) s = check_bins(ctx, bins);
+    if (s == FHGS_OK) s = check_features(ctx, features, ftype, D, n);
+    if (s != FHGS_OK) return s;
+    if (!ndfd_supported(D)) return fail(ctx, FHGS_ERR_UNSUPPORTED, "NDFD needs D in {32, 64, 128, 256, 512}");
+    if (!proj) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL input buffer");
+    if (!feat_gt) return fail(ctx, FHGS_ERR_INVALID_ARG, "feat_gt is NULL");
+    if (!aligned16(feat_gt)) return fail(ctx, FHGS_ERR_ALIGNMENT, "feat_gt must be 16-byte aligned");
+    if (!std::isfinite(k) || !std::isfinite(lambda))
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "the activation's slope and threshold must be finite");
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_bins *bins, const void *features,
+                          const void *feat_gt, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
+                          const fhgs_params *p, float k, float lambda, float *L_gt, float *L_cf, int32_t *n_contrib,
+                          void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    if (n < 0 || n >= (1ll << 31)) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad Gaussian count");
+    fhgs_status s = check_ndfd(ctx, n, proj, bins, features, feat_gt, ftype, D, p, k, lambda);
+    if (s != FHGS_OK) return s;
+    if (!L_gt || !L_cf) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL output buffer");
+    CamSet cs;
+    if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const Params q = make_params(p);
+    ProjView pv = proj_view(const_cast<void *>(proj), n * n_cams);
+    {
+        Prof pr(ctx, "ndfd_fwd", st);
+        launch_ndfd_fwd(n, cs, q, pv, *bins, features, feat_gt, ftype == FHGS_BF16, D, k, lambda, L_gt, L_cf, n_contrib, st);
+    }
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_ndfd_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *proj, const fhgs_bins *bins,
+                          const void *features, const void *feat_gt, fhgs_dtype ftype, int D,
+                          const fhgs_camera *cams, int n_cams, const fhgs_params *p, float k, float lambda,
+                          const float *grad_Lgt, const float *grad_Lcf, float *grad_means, float *grad_scales,
+                          float *grad_quats, float *grad_opac, float *grad_sh, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    fhgs_status s = check_gaussians(ctx, g, true);
+    if (s == FHGS_OK) s = check_ndfd(ctx, g->n, proj, bins, features, feat_gt, ftype, D, p, k, lambda);
+    if (s != FHGS_OK) return s;
+    if (!grad_Lgt || !grad_Lcf) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL input buffer");
+    if (g->n > 0 && (!grad_means || !grad_scales || !grad_quats || !grad_opac || !grad_sh))
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL gradient buffer");
+    if (!aligned16(grad_quats)) return fail(ctx, FHGS_ERR_ALIGNMENT, "grad_quats must be 16-byte aligned");
+    CamSet cs;
+    if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    const long long n = g->n, cn = n * n_cams;
+    if ((s = ensure(ctx, ctx->g2d, sizeof(float) * 12 * (size_t)cn + 256)) != FHGS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *g2d = (float *)ctx->g2d.p;
+    FHGS_CUDA(ctx, cudaMemsetAsync(g2d, 0, sizeof(float) * 12 * (size_t)cn, st));
+    const Params q = make_params(p);
+    ProjView pv = proj_view(const_cast<void *>(proj), cn);
+    {
+        Prof pr(ctx, "ndfd_bwd", st);
+        launch_ndfd_bwd(n, cs, q, pv, *bins, features, feat_gt, ftype == FHGS_BF16, D, k, lambda, grad_Lgt,
+                        grad_Lcf, g2d, st);
+    }
+    {
+        Prof pb(ctx, "project_bwd", st);
+        launch_project_bwd(*g, cs, q, pv, g2d, grad_means, grad_scales, grad_quats, grad_opac, grad_sh, st);
+    }
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
 fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhgs_camera *views, int n_views,
                                const float *const *maps, int D, const fhgs_params *p, float *num, float *den,
                                float *out, uint32_t flags, void *stream) {

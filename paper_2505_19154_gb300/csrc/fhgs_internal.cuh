@@ -187,4 +187,13 @@ bool launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
                           const float *grgb, const float *gfeat, float *g2d, float *gfeatures, unsigned *status,
                           cudaStream_t st);
 
+// NDFD losses and their backward (ndfd.cu): D in {32, 64, 128, 256, 512}
+bool ndfd_supported(int D);
+void launch_ndfd_fwd(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                     const void *feats, const void *fgt, int bf16, int D, float ks, float lam, float *Lgt,
+                     float *Lcf, int32_t *nc, cudaStream_t st);
+void launch_ndfd_bwd(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                     const void *feats, const void *fgt, int bf16, int D, float ks, float lam, const float *dLgt,
+                     const float *dLcf, float *g2d, cudaStream_t st);
+
 }  // namespace fhgs

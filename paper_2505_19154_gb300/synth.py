@@ -163,3 +163,38 @@ def smooth_feature_map(seed: int, view: int, height: int, width: int, D: int,
         x = ndimage.correlate1d(x, k, axis=axis, mode="mirror")
     x /= np.maximum(np.linalg.norm(x, axis=-1, keepdims=True), 1e-12)
     return x.astype(np.float32)
+
+
+# ------------------------------------------------------ NDFD inputs
+def ndfd_prototypes(seed: int, D: int, n_proto: int = 8) -> np.ndarray:
+    """n_proto random unit vectors (the 'objects' of a segmentation-like
+    embedding), (n_proto, D) float32."""
+    p = rng(seed, 2000).standard_normal((n_proto, D))
+    return (p / np.linalg.norm(p, axis=1, keepdims=True)).astype(np.float32)
+
+
+def ndfd_features(seed: int, n: int, protos: np.ndarray) -> np.ndarray:
+    """Per-Gaussian unit features clustered around the prototypes: a random
+    prototype plus isotropic noise of a random level (cosine to the prototype
+    from about 0.98 down to about 0.3), L2-normalised.  (n, D) float32."""
+    g = rng(seed, 2001)
+    k, D = protos.shape
+    lab = g.integers(0, k, n)
+    lvl = g.uniform(0.2, 3.0, n) / math.sqrt(D)
+    f = protos[lab] + lvl[:, None] * g.standard_normal((n, D))
+    return (f / np.linalg.norm(f, axis=1, keepdims=True)).astype(np.float32)
+
+
+def ndfd_ground_truth(seed: int, view: int, height: int, width: int, protos: np.ndarray,
+                      block: int = 24, noise: float = 0.5) -> np.ndarray:
+    """Ground-truth feature map: the image is cut into block x block regions,
+    each labelled with a random prototype, plus per-pixel noise (relative
+    level `noise`), L2-normalised.  (height, width, D) float32."""
+    g = rng(seed, 3000 + view)
+    k, D = protos.shape
+    by, bx = (height + block - 1) // block, (width + block - 1) // block
+    lab = g.integers(0, k, (by, bx))
+    lab = np.repeat(np.repeat(lab, block, 0), block, 1)[:height, :width]
+    f = protos[lab] + (noise / math.sqrt(D)) * g.standard_normal((height, width, D), dtype=np.float32)
+    f /= np.linalg.norm(f, axis=-1, keepdims=True)
+    return f.astype(np.float32)

@@ -1,0 +1,161 @@
+"""Parity of the NDFD losses and their backward (the CUDA path through the C
+ABI) against the FP64 oracle.
+
+Bars, for FP32 arithmetic over BF16 or FP32 inputs that the oracle reads
+exactly:
+  * L_gt and L_cf within 5e-5 absolute on every pixel with no threshold
+    decision within 1e-5 relative of its edge (those pixels stay under 1%).
+    The dot products f_gt . f_i and F . f_i carry an FP32 summation error of
+    about sqrt(D) 2^-24 |a||b| (~1.4e-6 at D = 512); the activation's slope
+    is at most k/4 = 5, and the weights sum to at most 1, so L_gt moves by
+    ~7e-6; 5e-5 leaves a factor of seven.
+  * Gradients of means, scales, quaternions and opacities within 1e-3
+    relative L2 (the render backward's bar); SH gradients exactly zero.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_19154_gb300 import api, synth
+from tests.helpers import small_random_scene
+from tests.test_gpu_parity import _t, check_grads
+
+pytestmark = pytest.mark.gpu
+
+L_TOL = 5e-5
+
+
+def ndfd_case(n, seed, D, cams, bf16=True, sh_degree=1, spread=0.5):
+    sc = small_random_scene(n, seed=seed, sh_degree=sh_degree, D=0, spread=spread)
+    sc = {k: (np.asarray(v, np.float32) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+    protos = synth.ndfd_prototypes(seed, D)
+    f = synth.ndfd_features(seed, n, protos)
+    fg = [synth.ndfd_ground_truth(seed, v, c["height"], c["width"], protos) for v, c in enumerate(cams)]
+    if bf16:
+        f = synth.to_bf16(f)
+        fg = [synth.to_bf16(x) for x in fg]
+    sc["features"] = f
+    return sc, fg
+
+
+def run_ndfd(sc, cams, prm, fg, bf16=True, grads=None):
+    dt = torch.bfloat16 if bf16 else torch.float32
+    rast = api.Rasterizer(0, sh_degree=prm.get("sh_degree", 0))
+    t = {k: _t(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    feats = _t(sc["features"], dt)
+    gt = _t(np.concatenate([x.reshape(-1, x.shape[-1]) for x in fg]), dt)
+    rast.ctx.profile(True)
+    st = rast.prepare(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams)
+    nc = torch.empty(gt.shape[0], dtype=torch.int32, device=gt.device)
+    Lgt, Lcf = rast.ndfd_forward(st, feats, gt, ncontrib=nc)
+    out = dict(Lgt=Lgt.cpu().numpy(), Lcf=Lcf.cpu().numpy(), nc=nc.cpu().numpy())
+    if grads is not None:
+        g = rast.ndfd_backward(st, feats, gt, _t(grads[0]), _t(grads[1]))
+        out["grads"] = {k: v.cpu().numpy() for k, v in g.items()}
+    torch.cuda.synchronize()
+    assert rast.ctx.sync_status() == api.OK
+    prof = rast.ctx.profile_read()
+    assert "ndfd_fwd" in prof, prof
+    if grads is not None:
+        assert "ndfd_bwd" in prof, prof
+    return out
+
+
+def check_losses(out, sc, cams, prm, fg, prep):
+    refs = oracle.ndfd_forward(sc, cams, prm, sc["features"], fg, prep=prep)
+    rend = oracle.forward(sc, cams, prm, None, prep=prep)
+    off = n_margin = n_pix = 0
+    worst = 0.0
+    for cam, ref, rr in zip(cams, refs, rend):
+        P = cam["width"] * cam["height"]
+        ok = rr["margin"].reshape(-1) > 1e-5
+        n_margin += int((~ok).sum())
+        n_pix += P
+        for key in ("Lgt", "Lcf"):
+            err = np.abs(out[key][off:off + P] - ref[key].reshape(-1))[ok].max(initial=0)
+            worst = max(worst, err)
+            assert err <= L_TOL, (key, err)
+        np.testing.assert_array_equal(out["nc"][off:off + P][ok], ref["ncontrib"].reshape(-1)[ok])
+        off += P
+    assert n_margin <= max(1, 0.01 * n_pix), (n_margin, n_pix)
+    assert max(np.abs(r["Lcf"]).max() for r in refs) > 1e-2   # the case exercises L_cf
+    return worst
+
+
+@pytest.mark.parametrize("D,bf16", [(64, True), (256, True), (512, True), (128, False), (32, False)])
+def test_ndfd_forward_small(D, bf16):
+    cams = [synth.look_at_camera(synth.ring_position(3.0, 20, 10), 64, 48)]
+    sc, fg = ndfd_case(1500, 61 + D, D, cams, bf16=bf16)
+    prm = dict(sh_degree=1)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_ndfd(sc, cams, prm, fg, bf16=bf16)
+    check_losses(out, sc, cams, prm, fg, prep)
+
+
+def test_ndfd_forward_multicamera_ragged():
+    cams = [synth.look_at_camera(synth.ring_position(3.0, a, e), w, h)
+            for a, e, w, h in [(0, 0, 70, 50), (130, 20, 33, 47), (250, -25, 96, 64)]]
+    sc, fg = ndfd_case(4000, 62, 128, cams, sh_degree=2)
+    prm = dict(sh_degree=2)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_ndfd(sc, cams, prm, fg)
+    check_losses(out, sc, cams, prm, fg, prep)
+
+
+@pytest.mark.parametrize("D,bf16", [(256, True), (512, True), (64, False)])
+def test_ndfd_backward_small(D, bf16):
+    cams = [synth.look_at_camera(synth.ring_position(3.0, 40, -10), 64, 48)]
+    sc, fg = ndfd_case(1500, 63 + D, D, cams, bf16=bf16, sh_degree=2)
+    prm = dict(sh_degree=2)
+    g = synth.rng(5, 4)
+    a = g.standard_normal(64 * 48).astype(np.float32)
+    b = g.standard_normal(64 * 48).astype(np.float32)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_ndfd(sc, cams, prm, fg, bf16=bf16, grads=(a, b))
+    check_losses(out, sc, cams, prm, fg, prep)
+    ref = oracle.ndfd_backward(sc, cams, prm, sc["features"], fg, [a], [b], prep=prep)
+    check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities"), tol=1e-3)
+    assert not np.any(out["grads"]["sh"])
+    # each loss alone (the two upstream gradients enter separately)
+    z = np.zeros_like(a)
+    out2 = run_ndfd(sc, cams, prm, fg, bf16=bf16, grads=(z, b))
+    ref2 = oracle.ndfd_backward(sc, cams, prm, sc["features"], fg, [z], [b], prep=prep)
+    check_grads(out2["grads"], ref2, keys=("means", "scales", "quats", "opacities"), tol=1e-3)
+
+
+def test_ndfd_backward_multicamera():
+    cams = [synth.look_at_camera(synth.ring_position(3.0, a, e), w, h)
+            for a, e, w, h in [(10, 5, 48, 40), (200, -15, 40, 56)]]
+    sc, fg = ndfd_case(2500, 64, 128, cams, sh_degree=1)
+    prm = dict(sh_degree=1)
+    g = synth.rng(6, 4)
+    P = sum(c["width"] * c["height"] for c in cams)
+    a = g.standard_normal(P).astype(np.float32)
+    b = g.standard_normal(P).astype(np.float32)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_ndfd(sc, cams, prm, fg, grads=(a, b))
+    split = cams[0]["width"] * cams[0]["height"]
+    ref = oracle.ndfd_backward(sc, cams, prm, sc["features"], fg, [a[:split], a[split:]], [b[:split], b[split:]],
+                               prep=prep)
+    check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities"), tol=1e-3)
+
+
+def test_ndfd_empty_scene_and_bad_arguments():
+    cams = [synth.look_at_camera(synth.ring_position(3.0, 0, 0), 40, 24)]
+    rast = api.Rasterizer(0, sh_degree=0)
+    z = torch.zeros((0, 3), device="cuda")
+    st = rast.prepare(z, z.clone() + 0.1, torch.zeros((0, 4), device="cuda"), torch.zeros(0, device="cuda"),
+                      torch.zeros((0, 1, 3), device="cuda"), cams)
+    feats = torch.zeros((0, 64), device="cuda", dtype=torch.bfloat16)
+    gt = torch.ones((40 * 24, 64), device="cuda", dtype=torch.bfloat16)
+    Lgt, Lcf = rast.ndfd_forward(st, feats, gt)
+    assert not Lgt.any() and not Lcf.any()
+    with pytest.raises(api.FhgsError) as e:
+        rast.ndfd_forward(st, torch.zeros((0, 96), device="cuda", dtype=torch.bfloat16),
+                          torch.ones((40 * 24, 96), device="cuda", dtype=torch.bfloat16))
+    assert e.value.status == api.ERR_UNSUPPORTED
+    big = torch.ones((40 * 24 * 64 + 8,), device="cuda", dtype=torch.bfloat16)
+    with pytest.raises(api.FhgsError) as e:
+        rast.ndfd_forward(st, feats, big[1:1 + 40 * 24 * 64].view(40 * 24, 64))
+    assert e.value.status == api.ERR_ALIGNMENT
