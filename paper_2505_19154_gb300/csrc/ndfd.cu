@@ -7,125 +7,144 @@
 // their derivative through w (Sec. 3.3, App. A.2).  No feature image is
 // written: the D-dimensional running feature F lives in registers.
 //
-// Layout: a block of 8 warps owns one 16-pixel row of a tile; each warp owns
-// two adjacent pixels, and lane l holds channels [l*DPL, (l+1)*DPL) of their
-// F and f_gt (D = 32 DPL).  Gaussian records and feature rows are staged in
-// shared memory 32 at a time.  Per contributor the warp forms the partial
-// dot products f_gt . f_i and F . f_i of both pixels, sums them over the
-// lanes in one reduce-scatter (10 shuffles for 4 values), and every lane
-// then updates the pixel scalars identically.  W_{i-1} = 1 - T_i (the
-// weights and the transmittance sum to one).
+// Layout.  A block of 8 warps owns one 16-pixel row of a tile; each warp owns
+// two adjacent pixels.  Lane l holds channels {128 k + 4 l + r} (DPL = D/32
+// of them) of the two pixels' F and f_gt, so that a warp's float4 reads of a
+// feature row cover contiguous bytes.  Gaussian records and feature rows
+// (converted to FP32) are staged in shared memory 32 at a time.
 //
-// The backward first walks front to back to rebuild F_N (and T_N, the last
-// contributor), then back to front with F_{k-1} = F_k - w_k f_k and the
-// suffix G_k = sum_{i>k} sigma_i w_i f_i:
+// Per chunk, lane j first decides alpha_j of entry j for both pixels (the
+// render's cutoff, alpha_min and alpha_max rules); an inclusive prefix
+// product over the lanes gives T_j, the stop rule (T_j (1 - alpha_j) < t_eps)
+// becomes the first set bit of a ballot, and w_j = alpha_j T_j.  W_{i-1} =
+// 1 - T_i (weights and transmittance sum to one).  The feature work then
+// visits only the contributors, four at a time: per contributor each lane
+// adds its channels' share of f_gt . f_i and F . f_i of both pixels to 16
+// partial sums and updates F += w_i f_i; one 16-value reduce-scatter (16
+// shuffles) completes the four contributors' dot products, and the lanes
+// that hold them accumulate L_gt and L_cf.
+//
+// The backward rebuilds F_N front to back the same way, then walks back to
+// front, two contributors k at a time, with F_{k-1} = F_k - w_k f_k and the
+// suffix G = sum_{i>k} sigma_i w_i f_i:
 //   dL/dw_k = c_gt sigma_k + c_cf (sigma_k (W_{k-1} - F_{k-1} . f_k)
-//             + sum_{i>k} sigma_i w_i - G_k . f_k),
+//             + sum_{i>k} sigma_i w_i - G . f_k),
 //   dL/dalpha_k = T_k dL/dw_k - (1/(1 - alpha_k)) sum_{i>k} w_i dL/dw_i,
-// and the footprint chain of the render backward.  Per-Gaussian footprint
-// gradients are summed over the block in shared memory, then added to the
-// per-(camera, Gaussian) gradient array with one vector atomic per chunk.
+// and the footprint chain of the render backward.  Inside a pair the later
+// contributor's share of G enters the earlier one's G . f_k through the
+// pair's Gram entry f_i . f_k.  T_k comes from T after the chunk divided by a
+// suffix product of (1 - alpha).  Per-Gaussian footprint gradients are summed
+// over the block in shared memory, then added to the per-(camera, Gaussian)
+// gradient array with one vector atomic per chunk.
 #include "fhgs_internal.cuh"
 
 namespace fhgs {
 namespace {
 
-constexpr int kNC = 32;       // Gaussians per shared-memory chunk
+constexpr int kNC = 32;       // Gaussians per shared-memory chunk (one per lane)
 constexpr int kWarps = 8;     // warps per block: 16 pixels, one tile row
 constexpr int kThreads = 32 * kWarps;
+constexpr unsigned kFull = 0xffffffffu;
 
-template <int DPL, int BF16>
-__device__ __forceinline__ void load_slice(const void *row, int lane, float (&out)[DPL]) {
-    if constexpr (BF16) {
-        const __nv_bfloat16 *r = reinterpret_cast<const __nv_bfloat16 *>(row) + lane * DPL;
-        if constexpr (DPL % 8 == 0) {
+// Channel c of lane `lane`, slot i:  DPL >= 4: 128 (i/4) + 4 lane + i%4;
+// DPL = 2: 2 lane + i;  DPL = 1: lane.
+template <int DPL>
+__device__ __forceinline__ int chan(int lane, int i) {
+    if constexpr (DPL >= 4) return 128 * (i >> 2) + 4 * lane + (i & 3);
+    else return DPL * lane + i;
+}
+
+// The lane's channels of an FP32 row (shared or global memory).
+template <int DPL>
+__device__ __forceinline__ void load_row_f32(const float *row, int lane, float (&out)[DPL]) {
+    if constexpr (DPL >= 4) {
 #pragma unroll
-            for (int q = 0; q < DPL / 8; ++q) {
-                const uint4 v = reinterpret_cast<const uint4 *>(r)[q];
-                const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float2 f = __bfloat1622float2(h[i]);
-                    out[8 * q + 2 * i] = f.x;
-                    out[8 * q + 2 * i + 1] = f.y;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < DPL; ++i) out[i] = __bfloat162float(r[i]);
+        for (int k = 0; k < DPL / 4; ++k) {
+            const float4 v = *reinterpret_cast<const float4 *>(row + 128 * k + 4 * lane);
+            out[4 * k] = v.x;
+            out[4 * k + 1] = v.y;
+            out[4 * k + 2] = v.z;
+            out[4 * k + 3] = v.w;
         }
+    } else if constexpr (DPL == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(row + 2 * lane);
+        out[0] = v.x;
+        out[1] = v.y;
     } else {
-        const float *r = reinterpret_cast<const float *>(row) + lane * DPL;
-        if constexpr (DPL % 4 == 0) {
+        out[0] = row[lane];
+    }
+}
+
+// The lane's channels of a global row of `features`' dtype.
+template <int DPL, int BF16>
+__device__ __forceinline__ void load_row_g(const void *row, int lane, float (&out)[DPL]) {
+    if constexpr (!BF16) {
+        load_row_f32<DPL>(reinterpret_cast<const float *>(row), lane, out);
+    } else {
+        const __nv_bfloat16 *r = reinterpret_cast<const __nv_bfloat16 *>(row);
+        if constexpr (DPL >= 4) {
 #pragma unroll
-            for (int q = 0; q < DPL / 4; ++q) {
-                const float4 v = reinterpret_cast<const float4 *>(r)[q];
-                out[4 * q] = v.x;
-                out[4 * q + 1] = v.y;
-                out[4 * q + 2] = v.z;
-                out[4 * q + 3] = v.w;
+            for (int k = 0; k < DPL / 4; ++k) {
+                const uint2 v = *reinterpret_cast<const uint2 *>(r + 128 * k + 4 * lane);
+                const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
+                const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
+                out[4 * k] = a.x;
+                out[4 * k + 1] = a.y;
+                out[4 * k + 2] = b.x;
+                out[4 * k + 3] = b.y;
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < DPL; ++i) out[i] = r[i];
+            for (int i = 0; i < DPL; ++i) out[i] = __bfloat162float(r[chan<DPL>(lane, i)]);
         }
     }
 }
 
 template <int DPL>
 __device__ __forceinline__ float dot_slice(const float (&a)[DPL], const float (&b)[DPL]) {
-    float s = 0.f;
+    float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-    for (int i = 0; i < DPL; ++i) s = fmaf(a[i], b[i], s);
-    return s;
+    for (int i = 0; i < DPL; i += 2) {
+        s0 = fmaf(a[i], b[i], s0);
+        if (i + 1 < DPL) s1 = fmaf(a[i + 1], b[i + 1], s1);
+    }
+    return s0 + s1;
+}
+
+template <int DPL>
+__device__ __forceinline__ void axpy_slice(float w, const float (&f)[DPL], float (&y)[DPL]) {
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) y[i] = fmaf(w, f[i], y[i]);
 }
 
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
     return x;
 }
 
-// Sums v[0..3] over the warp; every lane receives the four totals.  Halving
-// exchanges (xor 16: two values, xor 8: one) leave lane l with the partial
-// of value 2*bit4(l) + bit3(l), which xor 4, 2, 1 complete; lane 8 j then
-// holds the total of value j.
-__device__ __forceinline__ void warp_allreduce4(float (&v)[4], int lane) {
-    const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0;
-    float k0 = u16 ? v[2] : v[0], k1 = u16 ? v[3] : v[1];
-    const float s0 = u16 ? v[0] : v[2], s1 = u16 ? v[1] : v[3];
-    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
-    float k = u8 ? k1 : k0;
-    k += __shfl_xor_sync(0xffffffffu, u8 ? k0 : k1, 8);
-    k += __shfl_xor_sync(0xffffffffu, k, 4);
-    k += __shfl_xor_sync(0xffffffffu, k, 2);
-    k += __shfl_xor_sync(0xffffffffu, k, 1);
+// One halving step of a reduce-scatter: lanes with `bit` set keep the upper
+// half of v and send the lower half to their partner (lane ^ bit), which
+// keeps the lower half.
+template <int H>
+__device__ __forceinline__ void rs_step(const float *v, float *out, int lane, int bit) {
+    const bool up = (lane & bit) != 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = __shfl_sync(0xffffffffu, k, 8 * j);
+    for (int i = 0; i < H; ++i) {
+        const float keep = up ? v[H + i] : v[i], send = up ? v[i] : v[H + i];
+        out[i] = keep + __shfl_xor_sync(kFull, send, bit);
+    }
 }
 
-// The same for eight values: lane 4 j holds the total of value j.
-__device__ __forceinline__ void warp_allreduce8(float (&v)[8], int lane) {
-    const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0, u4 = (lane & 4) != 0;
-    float a[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float keep = u16 ? v[4 + i] : v[i], send = u16 ? v[i] : v[4 + i];
-        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-    float b[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float keep = u8 ? a[2 + i] : a[i], send = u8 ? a[i] : a[2 + i];
-        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    float k = u4 ? b[1] : b[0];
-    k += __shfl_xor_sync(0xffffffffu, u4 ? b[0] : b[1], 4);
-    k += __shfl_xor_sync(0xffffffffu, k, 2);
-    k += __shfl_xor_sync(0xffffffffu, k, 1);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = __shfl_sync(0xffffffffu, k, 4 * j);
+// Sums 16 per-lane values over the warp; lane l receives the total of value
+// l >> 1 (16 shuffles).
+__device__ __forceinline__ float warp_rs16(const float (&v)[16], int lane) {
+    float a[8], b[4], c[2], d[1];
+    rs_step<8>(v, a, lane, 16);
+    rs_step<4>(a, b, lane, 8);
+    rs_step<2>(b, c, lane, 4);
+    rs_step<1>(c, d, lane, 2);
+    return d[0] + __shfl_xor_sync(kFull, d[0], 1);
 }
 
 __device__ __forceinline__ float ndfd_sigma(float phi, float k, float lam) {
@@ -162,14 +181,14 @@ __device__ __forceinline__ RowCtx row_ctx(const CamSet &cs, const uint32_t *rang
 }
 
 // Stages Gaussians [base, base + nb) of the list: records, ids, feature rows
-// and the inverse feature norms (0 for a zero row).
+// as FP32 (row-major, D floats per row) and the inverse feature norms (0 for
+// a zero row).  Ends with a block barrier.
 template <int DPL, int BF16>
 __device__ __forceinline__ void stage_chunk(const GRec *rec, const uint32_t *gids, uint32_t base, int nb,
-                                            const void *feats, char *sfeat, float4 *sa, float4 *sb, uint32_t *sg,
+                                            const void *feats, float *sf, float4 *sa, float4 *sb, uint32_t *sg,
                                             float *sinv, int warp, int lane) {
     constexpr int D = 32 * DPL;
-    constexpr int kRowBytes = D * (BF16 ? 2 : 4);
-    constexpr int kRowQ = kRowBytes / 16;
+    constexpr int kRowQ = D * (BF16 ? 2 : 4) / 16;  // 16-byte words per source row
     const int tid = threadIdx.x;
     if (tid < nb) {
         const uint32_t g = gids[base + tid];
@@ -180,14 +199,24 @@ __device__ __forceinline__ void stage_chunk(const GRec *rec, const uint32_t *gid
     }
     for (int c = tid; c < nb * kRowQ; c += kThreads) {
         const int row = c / kRowQ, q = c - row * kRowQ;
-        const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(feats) +
-                                                           (size_t)gids[base + row] * kRowBytes);
-        reinterpret_cast<uint4 *>(sfeat + row * kRowBytes)[q] = src[q];
+        const uint4 v = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(feats) +
+                                                        (size_t)gids[base + row] * (kRowQ * 16))[q];
+        if constexpr (BF16) {
+            float4 *dst = reinterpret_cast<float4 *>(sf + row * D + 8 * q);
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
+            const float2 c2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.z));
+            const float2 d = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.w));
+            dst[0] = make_float4(a.x, a.y, b.x, b.y);
+            dst[1] = make_float4(c2.x, c2.y, d.x, d.y);
+        } else {
+            reinterpret_cast<uint4 *>(sf + row * D)[q] = v;
+        }
     }
     __syncthreads();
     for (int row = warp; row < nb; row += kWarps) {
         float f[DPL];
-        load_slice<DPL, BF16>(sfeat + row * kRowBytes, lane, f);
+        load_row_f32<DPL>(sf + row * D, lane, f);
         const float n2 = warp_sum(dot_slice<DPL>(f, f));
         if (lane == 0) sinv[row] = n2 > 0.f ? 1.f / sqrtf(n2) : 0.f;
     }
@@ -207,6 +236,36 @@ __device__ __forceinline__ bool ndfd_alpha(const Params &p, float4 A, float4 B, 
     return a >= p.amin;
 }
 
+// Front-to-back decisions of one chunk for pixel q, lane j <-> entry j:
+// given contrib (alpha test passed, pixel not yet done) and alpha, returns
+// the contributor mask (entries before the stop), this lane's weight w_j
+// and transmittance before it T_j, and advances T / done.
+__device__ __forceinline__ unsigned chunk_weights(bool contrib, float a, float teps, int lane, float &T, bool &done,
+                                                  float &w, float &Tj) {
+    float inc = contrib ? 1.f - a : 1.f;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float t = __shfl_up_sync(kFull, inc, d);
+        if (lane >= d) inc *= t;
+    }
+    float ex = __shfl_up_sync(kFull, inc, 1);
+    if (lane == 0) ex = 1.f;
+    Tj = T * ex;
+    const unsigned stop = __ballot_sync(kFull, contrib && T * inc < teps);
+    const unsigned before = stop ? (1u << (__ffs(stop) - 1)) - 1u : kFull;
+    const unsigned m = __ballot_sync(kFull, contrib) & before;
+    w = (m >> lane) & 1u ? a * Tj : 0.f;
+    const float Tstop = __shfl_sync(kFull, Tj, stop ? __ffs(stop) - 1 : 0);
+    const float Tall = __shfl_sync(kFull, inc, 31);
+    if (stop) {
+        done = true;
+        T = Tstop;
+    } else {
+        T *= Tall;
+    }
+    return m;
+}
+
 template <int DPL, int BF16>
 __global__ void __launch_bounds__(kThreads, 2) k_ndfd_fwd(long long N, CamSet cs, Params p, ProjView pv,
                                                         const uint32_t *__restrict__ gids,
@@ -214,8 +273,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_ndfd_fwd(long long N, CamSet cs
                                                         const void *fgt, float ks, float lam, float *Lgt_out,
                                                         float *Lcf_out, int32_t *nc_out) {
     constexpr int D = 32 * DPL;
-    constexpr int kRowBytes = D * (BF16 ? 2 : 4);
-    extern __shared__ __align__(16) char sfeat[];
+    constexpr int kGtRowBytes = D * (BF16 ? 2 : 4);
+    extern __shared__ __align__(16) float sf[];
     __shared__ float4 sa[kNC], sb[kNC];
     __shared__ uint32_t sg[kNC];
     __shared__ float sinv[kNC];
@@ -223,73 +282,113 @@ __global__ void __launch_bounds__(kThreads, 2) k_ndfd_fwd(long long N, CamSet cs
     const RowCtx rc = row_ctx(cs, ranges, warp);
     const GRec *rec = pv.rec + (long long)rc.ci * N;
 
-    float F[2][DPL], g[2][DPL], igt[2], T[2], Lgt[2], Lcf[2];
+    float F0[DPL], F1[DPL], g0[DPL], g1[DPL], igt[2], T[2] = {1.f, 1.f};
     int nc[2] = {0, 0};
-    bool done[2];
+    bool done[2] = {!rc.inside[0], !rc.inside[1]};
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        done[q] = !rc.inside[q];
-        T[q] = 1.f;
-        Lgt[q] = Lcf[q] = 0.f;
-#pragma unroll
-        for (int i = 0; i < DPL; ++i) F[q][i] = g[q][i] = 0.f;
-        if (rc.inside[q]) load_slice<DPL, BF16>(reinterpret_cast<const char *>(fgt) + rc.pix[q] * kRowBytes, lane, g[q]);
-        const float n2 = warp_sum(dot_slice<DPL>(g[q], g[q]));
-        igt[q] = n2 > 0.f ? 1.f / sqrtf(n2) : 0.f;
+    for (int i = 0; i < DPL; ++i) F0[i] = F1[i] = g0[i] = g1[i] = 0.f;
+    if (rc.inside[0]) load_row_g<DPL, BF16>(reinterpret_cast<const char *>(fgt) + rc.pix[0] * kGtRowBytes, lane, g0);
+    if (rc.inside[1]) load_row_g<DPL, BF16>(reinterpret_cast<const char *>(fgt) + rc.pix[1] * kGtRowBytes, lane, g1);
+    {
+        const float n0 = warp_sum(dot_slice<DPL>(g0, g0)), n1 = warp_sum(dot_slice<DPL>(g1, g1));
+        igt[0] = n0 > 0.f ? 1.f / sqrtf(n0) : 0.f;
+        igt[1] = n1 > 0.f ? 1.f / sqrtf(n1) : 0.f;
     }
+    // lanes l with l % 4 == 0 accumulate the terms of pixel (l >> 2) & 1
+    float acc_gt = 0.f, acc_cf = 0.f;
+    const int my_slot = lane >> 3, my_q = (lane >> 2) & 1;
 
     for (uint32_t base = rc.s; base < rc.e; base += kNC) {
         if (__syncthreads_and(done[0] && done[1])) break;
         const int nb = (int)min((uint32_t)kNC, rc.e - base);
-        stage_chunk<DPL, BF16>(rec, gids, base, nb, feats, sfeat, sa, sb, sg, sinv, warp, lane);
-        for (int j = 0; j < nb; ++j) {
-            if (done[0] && done[1]) break;
-            const float4 A = sa[j], B = sb[j];
-            bool c[2];
-            float a[2], Tn[2];
+        stage_chunk<DPL, BF16>(rec, gids, base, nb, feats, sf, sa, sb, sg, sinv, warp, lane);
+        float a[2] = {0.f, 0.f};
+        bool c[2] = {false, false};
+        if (lane < nb) {
+            const float4 A = sa[lane], B = sb[lane];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 float G, rho;
                 c[q] = !done[q] && ndfd_alpha(p, A, B, rc.fpx[q], rc.fpy, a[q], G, rho);
-                if (c[q]) {
-                    Tn[q] = T[q] * (1.f - a[q]);
-                    if (Tn[q] < p.teps) {
-                        done[q] = true;
-                        c[q] = false;
-                    }
+            }
+        }
+        float wl[2], Tl[2];
+        unsigned m[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            m[q] = chunk_weights(c[q], a[q], p.teps, lane, T[q], done[q], wl[q], Tl[q]);
+            nc[q] += __popc(m[q]);
+        }
+        unsigned U = m[0] | m[1];
+        while (U) {
+            int js[4];
+            float ww[4][2];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                js[s] = U ? __ffs(U) - 1 : -1;
+                U &= U - 1;
+                const int src = js[s] < 0 ? 0 : js[s];
+                const float w0 = __shfl_sync(kFull, wl[0], src), w1 = __shfl_sync(kFull, wl[1], src);
+                ww[s][0] = js[s] < 0 ? 0.f : w0;   // an empty slot carries no weight
+                ww[s][1] = js[s] < 0 ? 0.f : w1;
+            }
+            float v[16];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (js[s] >= 0) {
+                    float f[DPL];
+                    load_row_f32<DPL>(sf + js[s] * D, lane, f);
+                    v[4 * s + 0] = dot_slice<DPL>(g0, f);
+                    v[4 * s + 1] = dot_slice<DPL>(F0, f);
+                    v[4 * s + 2] = dot_slice<DPL>(g1, f);
+                    v[4 * s + 3] = dot_slice<DPL>(F1, f);
+                    axpy_slice<DPL>(ww[s][0], f, F0);
+                    axpy_slice<DPL>(ww[s][1], f, F1);
+                } else {
+                    v[4 * s] = v[4 * s + 1] = v[4 * s + 2] = v[4 * s + 3] = 0.f;
                 }
             }
-            if (!c[0] && !c[1]) continue;
-            float f[DPL];
-            load_slice<DPL, BF16>(sfeat + j * kRowBytes, lane, f);
-            float v[4] = {dot_slice<DPL>(g[0], f), dot_slice<DPL>(F[0], f), dot_slice<DPL>(g[1], f),
-                          dot_slice<DPL>(F[1], f)};
-            warp_allreduce4(v, lane);
-            const float inv = sinv[j];
+            // value 4 s + 2 q + t (t = 0: f_gt . f, t = 1: F . f) lands in lanes 8 s + 4 q + 2 t (+1)
+            const float tot = warp_rs16(v, lane);
+            const float X = __shfl_down_sync(kFull, tot, 2);
+            int j = -1;
+            float w = 0.f;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (!c[q]) continue;
-                const float w = a[q] * T[q];
-                const float sg_ = ndfd_sigma(v[2 * q] * inv * igt[q], ks, lam);
-                Lgt[q] = fmaf(w, sg_, Lgt[q]);
-                Lcf[q] = fmaf(sg_ * w, (1.f - T[q]) - v[2 * q + 1], Lcf[q]);
-#pragma unroll
-                for (int i = 0; i < DPL; ++i) F[q][i] = fmaf(w, f[i], F[q][i]);
-                T[q] = Tn[q];
-                ++nc[q];
+            for (int s = 0; s < 4; ++s)
+                if (s == my_slot) {
+                    j = js[s];
+                    w = my_q ? ww[s][1] : ww[s][0];
+                }
+            const int src = j < 0 ? 0 : j;
+            const float t0 = __shfl_sync(kFull, Tl[0], src), t1 = __shfl_sync(kFull, Tl[1], src);
+            if ((lane & 3) == 0 && j >= 0 && w > 0.f) {
+                const float sig = ndfd_sigma(tot * sinv[j] * (my_q ? igt[1] : igt[0]), ks, lam);
+                acc_gt = fmaf(w, sig, acc_gt);
+                acc_cf = fmaf(sig * w, (1.f - (my_q ? t1 : t0)) - X, acc_cf);
             }
         }
     }
+    const float L0 = warp_sum(my_q ? 0.f : acc_gt), L1 = warp_sum(my_q ? acc_gt : 0.f);
+    const float C0 = warp_sum(my_q ? 0.f : acc_cf), C1 = warp_sum(my_q ? acc_cf : 0.f);
     if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-            if (rc.inside[q]) {
-                Lgt_out[rc.pix[q]] = Lgt[q];
-                Lcf_out[rc.pix[q]] = Lcf[q];
-                if (nc_out) nc_out[rc.pix[q]] = nc[q];
-            }
+        if (rc.inside[0]) {
+            Lgt_out[rc.pix[0]] = L0;
+            Lcf_out[rc.pix[0]] = C0;
+            if (nc_out) nc_out[rc.pix[0]] = nc[0];
+        }
+        if (rc.inside[1]) {
+            Lgt_out[rc.pix[1]] = L1;
+            Lcf_out[rc.pix[1]] = C1;
+            if (nc_out) nc_out[rc.pix[1]] = nc[1];
+        }
     }
 }
+
+// Per-warp scalars of the chunk's entries (lane j writes entry j):
+// alpha, T_j, G and rho for both pixels.
+struct EntryScalars {
+    float a[2], T[2], G[2], rho[2];
+};
 
 template <int DPL, int BF16>
 __global__ void __launch_bounds__(kThreads, 1) k_ndfd_bwd(long long N, CamSet cs, Params p, ProjView pv,
@@ -299,29 +398,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_ndfd_bwd(long long N, CamSet cs
                                                         const float *__restrict__ dLgt,
                                                         const float *__restrict__ dLcf, float *g2d) {
     constexpr int D = 32 * DPL;
-    constexpr int kRowBytes = D * (BF16 ? 2 : 4);
-    extern __shared__ __align__(16) char sfeat[];
+    constexpr int kGtRowBytes = D * (BF16 ? 2 : 4);
+    extern __shared__ __align__(16) float sf[];
     __shared__ float4 sa[kNC], sb[kNC];
     __shared__ uint32_t sg[kNC];
     __shared__ float sinv[kNC];
     __shared__ __align__(16) float sacc[kNC][8];
+    __shared__ EntryScalars sent[kWarps][kNC];
     __shared__ int smax;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RowCtx rc = row_ctx(cs, ranges, warp);
     const GRec *rec = pv.rec + (long long)rc.ci * N;
     float *g2dc = g2d + (long long)rc.ci * N * 12;
 
-    float F[2][DPL], T[2];
-    int last[2];
-    bool done[2];
+    float F0[DPL], F1[DPL], T[2] = {1.f, 1.f};
+    int last[2] = {0, 0};
+    bool done[2] = {!rc.inside[0], !rc.inside[1]};
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        done[q] = !rc.inside[q];
-        T[q] = 1.f;
-        last[q] = 0;
-#pragma unroll
-        for (int i = 0; i < DPL; ++i) F[q][i] = 0.f;
-    }
+    for (int i = 0; i < DPL; ++i) F0[i] = F1[i] = 0.f;
     if (threadIdx.x == 0) smax = 0;
     for (int i = threadIdx.x; i < kNC * 8; i += kThreads) (&sacc[0][0])[i] = 0.f;
 
@@ -329,109 +423,194 @@ __global__ void __launch_bounds__(kThreads, 1) k_ndfd_bwd(long long N, CamSet cs
     for (uint32_t base = rc.s; base < rc.e; base += kNC) {
         if (__syncthreads_and(done[0] && done[1])) break;
         const int nb = (int)min((uint32_t)kNC, rc.e - base);
-        stage_chunk<DPL, BF16>(rec, gids, base, nb, feats, sfeat, sa, sb, sg, sinv, warp, lane);
-        for (int j = 0; j < nb; ++j) {
-            if (done[0] && done[1]) break;
-            const float4 A = sa[j], B = sb[j];
-            bool c[2];
-            float a[2];
+        stage_chunk<DPL, BF16>(rec, gids, base, nb, feats, sf, sa, sb, sg, sinv, warp, lane);
+        float a[2] = {0.f, 0.f};
+        bool c[2] = {false, false};
+        if (lane < nb) {
+            const float4 A = sa[lane], B = sb[lane];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 float G, rho;
                 c[q] = !done[q] && ndfd_alpha(p, A, B, rc.fpx[q], rc.fpy, a[q], G, rho);
-                if (c[q] && T[q] * (1.f - a[q]) < p.teps) {
-                    done[q] = true;
-                    c[q] = false;
-                }
             }
-            if (!c[0] && !c[1]) continue;
+        }
+        float wl[2], Tl[2];
+        unsigned m[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            m[q] = chunk_weights(c[q], a[q], p.teps, lane, T[q], done[q], wl[q], Tl[q]);
+            if (m[q]) last[q] = (int)(base - rc.s) + 32 - __clz(m[q]);
+        }
+        unsigned U = m[0] | m[1];
+        while (U) {
+            const int j = __ffs(U) - 1;
+            U &= U - 1;
+            const float w0 = __shfl_sync(kFull, wl[0], j), w1 = __shfl_sync(kFull, wl[1], j);
             float f[DPL];
-            load_slice<DPL, BF16>(sfeat + j * kRowBytes, lane, f);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (!c[q]) continue;
-                const float w = a[q] * T[q];
-#pragma unroll
-                for (int i = 0; i < DPL; ++i) F[q][i] = fmaf(w, f[i], F[q][i]);
-                T[q] *= 1.f - a[q];
-                last[q] = (int)(base - rc.s) + j + 1;
-            }
+            load_row_f32<DPL>(sf + j * D, lane, f);
+            axpy_slice<DPL>(w0, f, F0);
+            axpy_slice<DPL>(w1, f, F1);
         }
     }
 
     // back to front
-    float g[2][DPL], Gs[2][DPL], igt[2], cgt[2], ccf[2], Ss[2], Sw[2];
+    float g0[DPL], g1[DPL], G0[DPL], G1[DPL], igt[2], cgt[2] = {0.f, 0.f}, ccf[2] = {0.f, 0.f};
+    float Ss[2] = {0.f, 0.f}, Sw[2] = {0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int i = 0; i < DPL; ++i) g0[i] = g1[i] = G0[i] = G1[i] = 0.f;
 #pragma unroll
-        for (int i = 0; i < DPL; ++i) g[q][i] = Gs[q][i] = 0.f;
-        cgt[q] = ccf[q] = 0.f;
+    for (int q = 0; q < 2; ++q)
         if (rc.inside[q]) {
-            load_slice<DPL, BF16>(reinterpret_cast<const char *>(fgt) + rc.pix[q] * kRowBytes, lane, g[q]);
             cgt[q] = dLgt[rc.pix[q]];
             ccf[q] = dLcf[rc.pix[q]];
         }
-        const float n2 = warp_sum(dot_slice<DPL>(g[q], g[q]));
-        igt[q] = n2 > 0.f ? 1.f / sqrtf(n2) : 0.f;
-        Ss[q] = Sw[q] = 0.f;
+    if (rc.inside[0]) load_row_g<DPL, BF16>(reinterpret_cast<const char *>(fgt) + rc.pix[0] * kGtRowBytes, lane, g0);
+    if (rc.inside[1]) load_row_g<DPL, BF16>(reinterpret_cast<const char *>(fgt) + rc.pix[1] * kGtRowBytes, lane, g1);
+    {
+        const float n0 = warp_sum(dot_slice<DPL>(g0, g0)), n1 = warp_sum(dot_slice<DPL>(g1, g1));
+        igt[0] = n0 > 0.f ? 1.f / sqrtf(n0) : 0.f;
+        igt[1] = n1 > 0.f ? 1.f / sqrtf(n1) : 0.f;
     }
     __syncthreads();
     if (lane == 0) atomicMax(&smax, max(last[0], last[1]));
     __syncthreads();
     const int Lmax = min(smax, (int)(rc.e - rc.s));
+    EntryScalars *es = sent[warp];
     for (int bend = Lmax; bend > 0; bend -= kNC) {
         const int bstart = max(0, bend - kNC), nb = bend - bstart;
         __syncthreads();
-        stage_chunk<DPL, BF16>(rec, gids, rc.s + bstart, nb, feats, sfeat, sa, sb, sg, sinv, warp, lane);
-        for (int j = nb - 1; j >= 0; --j) {
-            const float4 A = sa[j], B = sb[j];
-            bool c[2];
-            float a[2], G[2], rho[2];
+        stage_chunk<DPL, BF16>(rec, gids, rc.s + bstart, nb, feats, sf, sa, sb, sg, sinv, warp, lane);
+        // alpha of entry `lane`, then T before it: T after the chunk divided
+        // by the suffix product of (1 - alpha) from the entry on
+        float a[2] = {0.f, 0.f}, Gv[2] = {0.f, 0.f}, rho[2] = {0.f, 0.f};
+        bool c[2] = {false, false};
+        if (lane < nb) {
+            const float4 A = sa[lane], B = sb[lane];
 #pragma unroll
             for (int q = 0; q < 2; ++q)
-                c[q] = bstart + j < last[q] && ndfd_alpha(p, A, B, rc.fpx[q], rc.fpy, a[q], G[q], rho[q]);
-            if (!c[0] && !c[1]) continue;
+                c[q] = bstart + lane < last[q] && ndfd_alpha(p, A, B, rc.fpx[q], rc.fpy, a[q], Gv[q], rho[q]);
+        }
+        unsigned m[2];
+        float Tb[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float suf = c[q] ? 1.f - a[q] : 1.f;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float t = __shfl_down_sync(kFull, suf, d);
+                if (lane + d < 32) suf *= t;
+            }
+            Tb[q] = T[q] / suf;
+            T[q] = __shfl_sync(kFull, Tb[q], 0);
+            m[q] = __ballot_sync(kFull, c[q]);
+        }
+        es[lane] = EntryScalars{{a[0], a[1]}, {Tb[0], Tb[1]}, {Gv[0], Gv[1]}, {rho[0], rho[1]}};
+        __syncwarp();
+        unsigned U = m[0] | m[1];
+        while (U) {
+            // two contributors in walk order: k0 (farther) then k1
+            int js[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                js[s] = U ? 31 - __clz(U) : -1;
+                if (js[s] >= 0) U &= ~(1u << js[s]);
+            }
+            float ww[2][2];
+            bool cc[2][2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    cc[s][q] = js[s] >= 0 && ((m[q] >> js[s]) & 1u);
+                    ww[s][q] = cc[s][q] ? es[js[s]].a[q] * es[js[s]].T[q] : 0.f;
+                }
+            float v[16];
             float f[DPL];
-            load_slice<DPL, BF16>(sfeat + j * kRowBytes, lane, f);
-            float w[2] = {0.f, 0.f};
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (!c[q]) continue;
-                T[q] = T[q] / (1.f - a[q]);
-                w[q] = a[q] * T[q];
+            for (int s = 0; s < 2; ++s) {
+                if (js[s] >= 0) {
+                    load_row_f32<DPL>(sf + js[s] * D, lane, f);
+                    axpy_slice<DPL>(-ww[s][0], f, F0);   // F_{k-1}
+                    axpy_slice<DPL>(-ww[s][1], f, F1);
+                    v[6 * s + 0] = dot_slice<DPL>(g0, f);
+                    v[6 * s + 1] = dot_slice<DPL>(F0, f);
+                    v[6 * s + 2] = dot_slice<DPL>(G0, f);
+                    v[6 * s + 3] = dot_slice<DPL>(g1, f);
+                    v[6 * s + 4] = dot_slice<DPL>(F1, f);
+                    v[6 * s + 5] = dot_slice<DPL>(G1, f);
+                } else {
 #pragma unroll
-                for (int i = 0; i < DPL; ++i) F[q][i] = fmaf(-w[q], f[i], F[q][i]);
+                    for (int t = 0; t < 6; ++t) v[6 * s + t] = 0.f;
+                }
             }
-            float v[8] = {dot_slice<DPL>(g[0], f), dot_slice<DPL>(F[0], f), dot_slice<DPL>(Gs[0], f),
-                          dot_slice<DPL>(g[1], f), dot_slice<DPL>(F[1], f), dot_slice<DPL>(Gs[1], f), 0.f, 0.f};
-            warp_allreduce8(v, lane);
-            const float inv = sinv[j];
-            float geo[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (!c[q]) continue;
-                const float sig = ndfd_sigma(v[3 * q] * inv * igt[q], ks, lam);
-                const float gw = cgt[q] * sig + ccf[q] * (sig * ((1.f - T[q]) - v[3 * q + 1]) + Ss[q] - v[3 * q + 2]);
-                const float oma = 1.f - a[q];
-                const float dal = T[q] * gw - Sw[q] / oma;
-                Sw[q] = fmaf(w[q], gw, Sw[q]);
-                const float sw = sig * w[q];
-                Ss[q] += sw;
-#pragma unroll
-                for (int i = 0; i < DPL; ++i) Gs[q][i] = fmaf(sw, f[i], Gs[q][i]);
-                const float drho = rho[q] > p.amax ? 0.f : dal;
-                const float dq2 = -0.5f * rho[q] * drho;
-                const float dx = rc.fpx[q] - A.x, dy = rc.fpy - A.y;
-                geo[0] -= (2.f * A.z * dx + 2.f * A.w * dy) * dq2;
-                geo[1] -= (2.f * A.w * dx + 2.f * B.x * dy) * dq2;
-                geo[2] += dx * dx * dq2;
-                geo[3] += 2.f * dx * dy * dq2;
-                geo[4] += dy * dy * dq2;
-                geo[5] += G[q] * drho;
+            if (js[1] >= 0) {   // f holds row js[1]: the pair's Gram entry f_k0 . f_k1
+                float f0[DPL];
+                load_row_f32<DPL>(sf + js[0] * D, lane, f0);
+                v[12] = dot_slice<DPL>(f0, f);
+            } else {
+                v[12] = 0.f;
             }
-            if (lane == 0) {
+            v[13] = v[14] = v[15] = 0.f;
+            const float tot = warp_rs16(v, lane);   // value i in lanes 2 i, 2 i + 1
+            float sw[2][2];
+            float geo[2][6];
+            const float gram = __shfl_sync(kFull, tot, 24);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) atomicAdd(&sacc[j][k], geo[k]);
+            for (int s = 0; s < 2; ++s) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) geo[s][k] = 0.f;
+                const float phi0 = __shfl_sync(kFull, tot, 2 * (6 * s + 0));
+                const float X0 = __shfl_sync(kFull, tot, 2 * (6 * s + 1));
+                const float A0 = __shfl_sync(kFull, tot, 2 * (6 * s + 2));
+                const float phi1 = __shfl_sync(kFull, tot, 2 * (6 * s + 3));
+                const float X1 = __shfl_sync(kFull, tot, 2 * (6 * s + 4));
+                const float A1 = __shfl_sync(kFull, tot, 2 * (6 * s + 5));
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    sw[s][q] = 0.f;
+                    if (!cc[s][q]) continue;
+                    const int j = js[s];
+                    const EntryScalars &e = es[j];
+                    const float w = ww[s][q], Tk = e.T[q], ak = e.a[q];
+                    const float sig = ndfd_sigma((q ? phi1 : phi0) * sinv[j] * igt[q], ks, lam);
+                    // G . f_k: G at the pair's start, plus the first contributor's share
+                    float Y = q ? A1 : A0;
+                    if (s == 1) Y = fmaf(sw[0][q], gram, Y);
+                    const float gw =
+                        cgt[q] * sig + ccf[q] * (sig * ((1.f - Tk) - (q ? X1 : X0)) + Ss[q] - Y);
+                    const float dal = Tk * gw - Sw[q] / (1.f - ak);
+                    Sw[q] = fmaf(w, gw, Sw[q]);
+                    sw[s][q] = sig * w;
+                    Ss[q] += sw[s][q];
+                    const float drho = e.rho[q] > p.amax ? 0.f : dal;
+                    const float dq2 = -0.5f * e.rho[q] * drho;
+                    const float4 A = sa[j], B = sb[j];
+                    const float dx = rc.fpx[q] - A.x, dy = rc.fpy - A.y;
+                    geo[s][0] -= (2.f * A.z * dx + 2.f * A.w * dy) * dq2;
+                    geo[s][1] -= (2.f * A.w * dx + 2.f * B.x * dy) * dq2;
+                    geo[s][2] += dx * dx * dq2;
+                    geo[s][3] += 2.f * dx * dy * dq2;
+                    geo[s][4] += dy * dy * dq2;
+                    geo[s][5] += e.G[q] * drho;
+                }
+            }
+            // G += sigma w f of both contributors
+            // f holds the row of the pair's last loaded contributor
+            if (js[1] >= 0) {
+                axpy_slice<DPL>(sw[1][0], f, G0);
+                axpy_slice<DPL>(sw[1][1], f, G1);
+                load_row_f32<DPL>(sf + js[0] * D, lane, f);
+            }
+            axpy_slice<DPL>(sw[0][0], f, G0);
+            axpy_slice<DPL>(sw[0][1], f, G1);
+            if (lane < 12) {   // lane 6 s + k adds component k of contributor s
+                const int s = lane >= 6 ? 1 : 0, k = lane - 6 * s;
+                float val = 0.f;
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk)
+                    if (kk == k) val = s ? geo[1][kk] : geo[0][kk];
+                const int j = s ? js[1] : js[0];
+                if (j >= 0 && val != 0.f) atomicAdd(&sacc[j][k], val);
             }
         }
         __syncthreads();
@@ -455,7 +634,7 @@ void launch_fwd_t(long long N, const CamSet &cs, const Params &p, ProjView pv, c
                   const void *feats, const void *fgt, float ks, float lam, float *Lgt, float *Lcf, int32_t *nc,
                   cudaStream_t st) {
     static std::atomic<unsigned long long> smem_set{0};
-    const int smem = kNC * 32 * DPL * (BF16 ? 2 : 4);
+    const int smem = kNC * 32 * DPL * 4;
     allow_max_smem(smem_set, k_ndfd_fwd<DPL, BF16>);
     note_launch(1);
     k_ndfd_fwd<DPL, BF16><<<(unsigned)cs.total_tiles * 16, kThreads, smem, st>>>(
@@ -467,7 +646,7 @@ void launch_bwd_t(long long N, const CamSet &cs, const Params &p, ProjView pv, c
                   const void *feats, const void *fgt, float ks, float lam, const float *dLgt, const float *dLcf,
                   float *g2d, cudaStream_t st) {
     static std::atomic<unsigned long long> smem_set{0};
-    const int smem = kNC * 32 * DPL * (BF16 ? 2 : 4);
+    const int smem = kNC * 32 * DPL * 4;
     allow_max_smem(smem_set, k_ndfd_bwd<DPL, BF16>);
     note_launch(1);
     k_ndfd_bwd<DPL, BF16><<<(unsigned)cs.total_tiles * 16, kThreads, smem, st>>>(
