@@ -546,40 +546,6 @@ NDFD_WORKLOAD = "1M Gaussians, 1920x1080 view, D=512 BF16 unit features and grou
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def device_ndfd_inputs(seed, n, cams, D, dev, n_proto=8, block=24, noise=0.5, chunk=1 << 17):
-    """The NDFD input recipe (clustered unit features around n_proto random
-    unit prototypes, cosine to the own prototype from ~0.98 to ~0.3; a
-    ground-truth map of block x block regions each labelled with a prototype
-    plus per-pixel noise, L2-normalised) generated on the device with torch,
-    in row chunks, rounded to BF16.  Returns (features [n, D], feat_gt [P, D])."""
-    import math
-    import torch
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(7_000_003 * (seed + 1))
-    protos = torch.randn((n_proto, D), generator=gen, device=dev)
-    protos = protos / protos.norm(dim=1, keepdim=True)
-    feats = torch.empty((n, D), dtype=torch.bfloat16, device=dev)
-    for r0 in range(0, n, chunk):
-        m = min(chunk, n - r0)
-        lab = torch.randint(0, n_proto, (m,), generator=gen, device=dev)
-        lvl = (torch.rand((m,), generator=gen, device=dev) * 2.8 + 0.2) / math.sqrt(D)
-        f = protos[lab] + lvl[:, None] * torch.randn((m, D), generator=gen, device=dev)
-        feats[r0:r0 + m] = (f / f.norm(dim=1, keepdim=True)).to(torch.bfloat16)
-    maps = []
-    for c in cams:
-        h, w = c["height"], c["width"]
-        by, bx = (h + block - 1) // block, (w + block - 1) // block
-        lab = torch.randint(0, n_proto, (by, bx), generator=gen, device=dev)
-        lab = lab.repeat_interleave(block, 0).repeat_interleave(block, 1)[:h, :w].reshape(-1)
-        g = torch.empty((h * w, D), dtype=torch.bfloat16, device=dev)
-        for r0 in range(0, h * w, chunk):
-            m = min(chunk, h * w - r0)
-            x = protos[lab[r0:r0 + m]] + (noise / math.sqrt(D)) * torch.randn((m, D), generator=gen, device=dev)
-            g[r0:r0 + m] = (x / x.norm(dim=1, keepdim=True)).to(torch.bfloat16)
-        maps.append(g)
-    return feats, torch.cat(maps)
-
-
 def ndfd_cpu_baseline(scene, cams, feats, fgt, dLgt, dLcf, max_seconds=25.0, reps_max=3):
     """The oracle on a bounded sample of the NDFD workload: projection and
     FP32 binning of every Gaussian, lists of the 64x64 crop's tiles, FP64
@@ -629,7 +595,7 @@ def run_ndfd(args):
     D = args.D
     g = tuple(torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).to(dev)
               for k in ("means", "scales", "quats", "opacities", "sh"))
-    feats, fgt = device_ndfd_inputs(rank, args.n, cams, D, dev)
+    feats, fgt = synth.ndfd_inputs_device(rank, args.n, cams, D, dev)
     P = fgt.shape[0]
     gen = torch.Generator(device=dev)
     gen.manual_seed(9_000_011 + rank)

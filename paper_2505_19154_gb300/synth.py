@@ -198,3 +198,38 @@ def ndfd_ground_truth(seed: int, view: int, height: int, width: int, protos: np.
     f = protos[lab] + (noise / math.sqrt(D)) * g.standard_normal((height, width, D), dtype=np.float32)
     f /= np.linalg.norm(f, axis=-1, keepdims=True)
     return f.astype(np.float32)
+
+
+def ndfd_inputs_device(seed: int, n: int, cams, D: int, dev, n_proto: int = 8, block: int = 24, noise: float = 0.5,
+                       chunk: int = 1 << 17):
+    """The NDFD input recipe (clustered unit features around n_proto random
+    unit prototypes, cosine to the own prototype from ~0.98 to ~0.3; a
+    ground-truth map of block x block regions each labelled with a prototype
+    plus per-pixel noise, L2-normalised) generated on the device with torch,
+    in row chunks, rounded to BF16: the full-size workload, too large to
+    make on the host.  Returns (features [n, D], feat_gt [P, D])."""
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7_000_003 * (seed + 1))
+    protos = torch.randn((n_proto, D), generator=gen, device=dev)
+    protos = protos / protos.norm(dim=1, keepdim=True)
+    feats = torch.empty((n, D), dtype=torch.bfloat16, device=dev)
+    for r0 in range(0, n, chunk):
+        m = min(chunk, n - r0)
+        lab = torch.randint(0, n_proto, (m,), generator=gen, device=dev)
+        lvl = (torch.rand((m,), generator=gen, device=dev) * 2.8 + 0.2) / math.sqrt(D)
+        f = protos[lab] + lvl[:, None] * torch.randn((m, D), generator=gen, device=dev)
+        feats[r0:r0 + m] = (f / f.norm(dim=1, keepdim=True)).to(torch.bfloat16)
+    maps = []
+    for c in cams:
+        h, w = c["height"], c["width"]
+        by, bx = (h + block - 1) // block, (w + block - 1) // block
+        lab = torch.randint(0, n_proto, (by, bx), generator=gen, device=dev)
+        lab = lab.repeat_interleave(block, 0).repeat_interleave(block, 1)[:h, :w].reshape(-1)
+        g = torch.empty((h * w, D), dtype=torch.bfloat16, device=dev)
+        for r0 in range(0, h * w, chunk):
+            m = min(chunk, h * w - r0)
+            x = protos[lab[r0:r0 + m]] + (noise / math.sqrt(D)) * torch.randn((m, D), generator=gen, device=dev)
+            g[r0:r0 + m] = (x / x.norm(dim=1, keepdim=True)).to(torch.bfloat16)
+        maps.append(g)
+    return feats, torch.cat(maps)
