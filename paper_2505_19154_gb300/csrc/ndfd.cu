@@ -24,9 +24,10 @@
 // shuffles) completes the four contributors' dot products, and the lanes
 // that hold them accumulate L_gt and L_cf.
 //
-// The backward rebuilds F_N front to back the same way, then walks back to
-// front, two contributors k at a time, with F_{k-1} = F_k - w_k f_k and the
-// suffix G = sum_{i>k} sigma_i w_i f_i:
+// The backward runs one pixel per warp (16 warps per block, a register
+// budget of 128 per thread).  It rebuilds F_N front to back the same way,
+// then walks back to front, two contributors k at a time, with
+// F_{k-1} = F_k - w_k f_k and the suffix G = sum_{i>k} sigma_i w_i f_i:
 //   dL/dw_k = c_gt sigma_k + c_cf (sigma_k (W_{k-1} - F_{k-1} . f_k)
 //             + sum_{i>k} sigma_i w_i - G . f_k),
 //   dL/dalpha_k = T_k dL/dw_k - (1/(1 - alpha_k)) sum_{i>k} w_i dL/dw_i,
@@ -183,7 +184,7 @@ __device__ __forceinline__ RowCtx row_ctx(const CamSet &cs, const uint32_t *rang
 // Stages Gaussians [base, base + nb) of the list: records, ids, feature rows
 // as FP32 (row-major, D floats per row) and the inverse feature norms (0 for
 // a zero row).  Ends with a block barrier.
-template <int DPL, int BF16>
+template <int DPL, int BF16, int NT = kThreads>
 __device__ __forceinline__ void stage_chunk(const GRec *rec, const uint32_t *gids, uint32_t base, int nb,
                                             const void *feats, float *sf, float4 *sa, float4 *sb, uint32_t *sg,
                                             float *sinv, int warp, int lane) {
@@ -197,7 +198,7 @@ __device__ __forceinline__ void stage_chunk(const GRec *rec, const uint32_t *gid
         sb[tid] = r.b;
         sg[tid] = g;
     }
-    for (int c = tid; c < nb * kRowQ; c += kThreads) {
+    for (int c = tid; c < nb * kRowQ; c += NT) {
         const int row = c / kRowQ, q = c - row * kRowQ;
         const uint4 v = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(feats) +
                                                         (size_t)gids[base + row] * (kRowQ * 16))[q];
@@ -214,7 +215,7 @@ __device__ __forceinline__ void stage_chunk(const GRec *rec, const uint32_t *gid
         }
     }
     __syncthreads();
-    for (int row = warp; row < nb; row += kWarps) {
+    for (int row = warp; row < nb; row += NT / 32) {
         float f[DPL];
         load_row_f32<DPL>(sf + row * D, lane, f);
         const float n2 = warp_sum(dot_slice<DPL>(f, f));
@@ -384,19 +385,52 @@ __global__ void __launch_bounds__(kThreads, 2) k_ndfd_fwd(long long N, CamSet cs
     }
 }
 
-// Per-warp scalars of the chunk's entries (lane j writes entry j):
-// alpha, T_j, G and rho for both pixels.
+// The backward runs one pixel per warp, 16 warps per block (the block's tile
+// row), so that twice as many warps hide the latency of its dependent dot
+// products and shuffles.
+constexpr int kWarpsB = 16;
+constexpr int kThreadsB = 32 * kWarpsB;
+
+// Sums 8 per-lane values over the warp; lane l receives the total of value
+// l >> 2 (9 shuffles).
+__device__ __forceinline__ float warp_rs8(const float (&v)[8], int lane) {
+    float a[4], b[2], c[1];
+    rs_step<4>(v, a, lane, 16);
+    rs_step<2>(a, b, lane, 8);
+    rs_step<1>(b, c, lane, 4);
+    const float t = c[0] + __shfl_xor_sync(kFull, c[0], 2);
+    return t + __shfl_xor_sync(kFull, t, 1);
+}
+
+// Per-warp scalars of the chunk's entries (lane j writes entry j): alpha,
+// T before the entry, G and rho.
 struct EntryScalars {
-    float a[2], T[2], G[2], rho[2];
+    float a, T, G, rho;
 };
 
+// dL/dalpha of one contributor -> its footprint gradient at the pixel
+// (mean x, y; conic A, B, C; opacity), through alpha = min(alpha_max, op G),
+// G = exp(-q2/2); the clamp passes no gradient.
+__device__ __forceinline__ void footprint_geo(float (&geo)[6], float4 A, float4 B, float fpx, float fpy,
+                                              const EntryScalars &e, float amax, float dal) {
+    const float drho = e.rho > amax ? 0.f : dal;
+    const float dq2 = -0.5f * e.rho * drho;
+    const float dx = fpx - A.x, dy = fpy - A.y;
+    geo[0] = -(2.f * A.z * dx + 2.f * A.w * dy) * dq2;
+    geo[1] = -(2.f * A.w * dx + 2.f * B.x * dy) * dq2;
+    geo[2] = dx * dx * dq2;
+    geo[3] = 2.f * dx * dy * dq2;
+    geo[4] = dy * dy * dq2;
+    geo[5] = e.G * drho;
+}
+
 template <int DPL, int BF16>
-__global__ void __launch_bounds__(kThreads, 1) k_ndfd_bwd(long long N, CamSet cs, Params p, ProjView pv,
-                                                        const uint32_t *__restrict__ gids,
-                                                        const uint32_t *__restrict__ ranges, const void *feats,
-                                                        const void *fgt, float ks, float lam,
-                                                        const float *__restrict__ dLgt,
-                                                        const float *__restrict__ dLcf, float *g2d) {
+__global__ void __launch_bounds__(kThreadsB, 1) k_ndfd_bwd(long long N, CamSet cs, Params p, ProjView pv,
+                                                         const uint32_t *__restrict__ gids,
+                                                         const uint32_t *__restrict__ ranges, const void *feats,
+                                                         const void *fgt, float ks, float lam,
+                                                         const float *__restrict__ dLgt,
+                                                         const float *__restrict__ dLcf, float *g2d) {
     constexpr int D = 32 * DPL;
     constexpr int kGtRowBytes = D * (BF16 ? 2 : 4);
     extern __shared__ __align__(16) float sf[];
@@ -404,214 +438,157 @@ __global__ void __launch_bounds__(kThreads, 1) k_ndfd_bwd(long long N, CamSet cs
     __shared__ uint32_t sg[kNC];
     __shared__ float sinv[kNC];
     __shared__ __align__(16) float sacc[kNC][8];
-    __shared__ EntryScalars sent[kWarps][kNC];
+    __shared__ __align__(16) EntryScalars sent[kWarpsB][kNC];
     __shared__ int smax;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const RowCtx rc = row_ctx(cs, ranges, warp);
-    const GRec *rec = pv.rec + (long long)rc.ci * N;
-    float *g2dc = g2d + (long long)rc.ci * N * 12;
+    // pixel `warp` of the block's tile row
+    const int tile = blockIdx.x >> 4, row = blockIdx.x & 15;
+    const int ci = cam_of_tile(cs, tile);
+    const DevCam &cam = cs.c[ci];
+    const int lt = tile - cam.tile_off;
+    const int px = (lt % cam.tiles_x) * kTile + warp, py = (lt / cam.tiles_x) * kTile + row;
+    const bool inside = px < cam.W && py < cam.H;
+    const long long pix = cam.pix_off + (long long)py * cam.W + px;
+    const float fpx = px + 0.5f, fpy = py + 0.5f;
+    const uint32_t ls = ranges[2 * tile], le = ranges[2 * tile + 1];
+    const GRec *rec = pv.rec + (long long)ci * N;
+    float *g2dc = g2d + (long long)ci * N * 12;
 
-    float F0[DPL], F1[DPL], T[2] = {1.f, 1.f};
-    int last[2] = {0, 0};
-    bool done[2] = {!rc.inside[0], !rc.inside[1]};
+    float F[DPL], T = 1.f;
+    int last = 0;
+    bool done = !inside;
 #pragma unroll
-    for (int i = 0; i < DPL; ++i) F0[i] = F1[i] = 0.f;
+    for (int i = 0; i < DPL; ++i) F[i] = 0.f;
     if (threadIdx.x == 0) smax = 0;
-    for (int i = threadIdx.x; i < kNC * 8; i += kThreads) (&sacc[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < kNC * 8; i += kThreadsB) (&sacc[0][0])[i] = 0.f;
 
-    // front to back: F_N, T_N and the last contributor of each pixel
-    for (uint32_t base = rc.s; base < rc.e; base += kNC) {
-        if (__syncthreads_and(done[0] && done[1])) break;
-        const int nb = (int)min((uint32_t)kNC, rc.e - base);
-        stage_chunk<DPL, BF16>(rec, gids, base, nb, feats, sf, sa, sb, sg, sinv, warp, lane);
-        float a[2] = {0.f, 0.f};
-        bool c[2] = {false, false};
+    // front to back: F_N, T_N and the last contributor
+    for (uint32_t base = ls; base < le; base += kNC) {
+        if (__syncthreads_and(done)) break;
+        const int nb = (int)min((uint32_t)kNC, le - base);
+        stage_chunk<DPL, BF16, kThreadsB>(rec, gids, base, nb, feats, sf, sa, sb, sg, sinv, warp, lane);
+        float a = 0.f;
+        bool c = false;
         if (lane < nb) {
-            const float4 A = sa[lane], B = sb[lane];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                float G, rho;
-                c[q] = !done[q] && ndfd_alpha(p, A, B, rc.fpx[q], rc.fpy, a[q], G, rho);
-            }
+            float G, rho;
+            c = !done && ndfd_alpha(p, sa[lane], sb[lane], fpx, fpy, a, G, rho);
         }
-        float wl[2], Tl[2];
-        unsigned m[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            m[q] = chunk_weights(c[q], a[q], p.teps, lane, T[q], done[q], wl[q], Tl[q]);
-            if (m[q]) last[q] = (int)(base - rc.s) + 32 - __clz(m[q]);
-        }
-        unsigned U = m[0] | m[1];
+        float wl, Tl;
+        const unsigned m = chunk_weights(c, a, p.teps, lane, T, done, wl, Tl);
+        if (m) last = (int)(base - ls) + 32 - __clz(m);
+        unsigned U = m;
         while (U) {
             const int j = __ffs(U) - 1;
             U &= U - 1;
-            const float w0 = __shfl_sync(kFull, wl[0], j), w1 = __shfl_sync(kFull, wl[1], j);
+            const float w = __shfl_sync(kFull, wl, j);
             float f[DPL];
             load_row_f32<DPL>(sf + j * D, lane, f);
-            axpy_slice<DPL>(w0, f, F0);
-            axpy_slice<DPL>(w1, f, F1);
+            axpy_slice<DPL>(w, f, F);
         }
     }
 
     // back to front
-    float g0[DPL], g1[DPL], G0[DPL], G1[DPL], igt[2], cgt[2] = {0.f, 0.f}, ccf[2] = {0.f, 0.f};
-    float Ss[2] = {0.f, 0.f}, Sw[2] = {0.f, 0.f};
+    float g[DPL], Gs[DPL], igt, cgt = 0.f, ccf = 0.f, Ss = 0.f, Sw = 0.f;
 #pragma unroll
-    for (int i = 0; i < DPL; ++i) g0[i] = g1[i] = G0[i] = G1[i] = 0.f;
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-        if (rc.inside[q]) {
-            cgt[q] = dLgt[rc.pix[q]];
-            ccf[q] = dLcf[rc.pix[q]];
-        }
-    if (rc.inside[0]) load_row_g<DPL, BF16>(reinterpret_cast<const char *>(fgt) + rc.pix[0] * kGtRowBytes, lane, g0);
-    if (rc.inside[1]) load_row_g<DPL, BF16>(reinterpret_cast<const char *>(fgt) + rc.pix[1] * kGtRowBytes, lane, g1);
+    for (int i = 0; i < DPL; ++i) g[i] = Gs[i] = 0.f;
+    if (inside) {
+        cgt = dLgt[pix];
+        ccf = dLcf[pix];
+        load_row_g<DPL, BF16>(reinterpret_cast<const char *>(fgt) + pix * kGtRowBytes, lane, g);
+    }
     {
-        const float n0 = warp_sum(dot_slice<DPL>(g0, g0)), n1 = warp_sum(dot_slice<DPL>(g1, g1));
-        igt[0] = n0 > 0.f ? 1.f / sqrtf(n0) : 0.f;
-        igt[1] = n1 > 0.f ? 1.f / sqrtf(n1) : 0.f;
+        const float n2 = warp_sum(dot_slice<DPL>(g, g));
+        igt = n2 > 0.f ? 1.f / sqrtf(n2) : 0.f;
     }
     __syncthreads();
-    if (lane == 0) atomicMax(&smax, max(last[0], last[1]));
+    if (lane == 0) atomicMax(&smax, last);
     __syncthreads();
-    const int Lmax = min(smax, (int)(rc.e - rc.s));
+    const int Lmax = min(smax, (int)(le - ls));
     EntryScalars *es = sent[warp];
     for (int bend = Lmax; bend > 0; bend -= kNC) {
         const int bstart = max(0, bend - kNC), nb = bend - bstart;
         __syncthreads();
-        stage_chunk<DPL, BF16>(rec, gids, rc.s + bstart, nb, feats, sf, sa, sb, sg, sinv, warp, lane);
+        stage_chunk<DPL, BF16, kThreadsB>(rec, gids, ls + bstart, nb, feats, sf, sa, sb, sg, sinv, warp, lane);
         // alpha of entry `lane`, then T before it: T after the chunk divided
         // by the suffix product of (1 - alpha) from the entry on
-        float a[2] = {0.f, 0.f}, Gv[2] = {0.f, 0.f}, rho[2] = {0.f, 0.f};
-        bool c[2] = {false, false};
-        if (lane < nb) {
-            const float4 A = sa[lane], B = sb[lane];
+        float a = 0.f, Gv = 0.f, rho = 0.f;
+        bool c = false;
+        if (lane < nb) c = bstart + lane < last && ndfd_alpha(p, sa[lane], sb[lane], fpx, fpy, a, Gv, rho);
+        float suf = c ? 1.f - a : 1.f;
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
-                c[q] = bstart + lane < last[q] && ndfd_alpha(p, A, B, rc.fpx[q], rc.fpy, a[q], Gv[q], rho[q]);
+        for (int d = 1; d < 32; d <<= 1) {
+            const float t = __shfl_down_sync(kFull, suf, d);
+            if (lane + d < 32) suf *= t;
         }
-        unsigned m[2];
-        float Tb[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            float suf = c[q] ? 1.f - a[q] : 1.f;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const float t = __shfl_down_sync(kFull, suf, d);
-                if (lane + d < 32) suf *= t;
-            }
-            Tb[q] = T[q] / suf;
-            T[q] = __shfl_sync(kFull, Tb[q], 0);
-            m[q] = __ballot_sync(kFull, c[q]);
-        }
-        es[lane] = EntryScalars{{a[0], a[1]}, {Tb[0], Tb[1]}, {Gv[0], Gv[1]}, {rho[0], rho[1]}};
+        const float Tb = T / suf;
+        T = __shfl_sync(kFull, Tb, 0);
+        const unsigned m = __ballot_sync(kFull, c);
+        es[lane] = EntryScalars{a, Tb, Gv, rho};
         __syncwarp();
-        unsigned U = m[0] | m[1];
+        unsigned U = m;
         while (U) {
-            // two contributors in walk order: k0 (farther) then k1
-            int js[2];
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                js[s] = U ? 31 - __clz(U) : -1;
-                if (js[s] >= 0) U &= ~(1u << js[s]);
-            }
-            float ww[2][2];
-            bool cc[2][2];
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    cc[s][q] = js[s] >= 0 && ((m[q] >> js[s]) & 1u);
-                    ww[s][q] = cc[s][q] ? es[js[s]].a[q] * es[js[s]].T[q] : 0.f;
-                }
-            float v[16];
-            float f[DPL];
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                if (js[s] >= 0) {
-                    load_row_f32<DPL>(sf + js[s] * D, lane, f);
-                    axpy_slice<DPL>(-ww[s][0], f, F0);   // F_{k-1}
-                    axpy_slice<DPL>(-ww[s][1], f, F1);
-                    v[6 * s + 0] = dot_slice<DPL>(g0, f);
-                    v[6 * s + 1] = dot_slice<DPL>(F0, f);
-                    v[6 * s + 2] = dot_slice<DPL>(G0, f);
-                    v[6 * s + 3] = dot_slice<DPL>(g1, f);
-                    v[6 * s + 4] = dot_slice<DPL>(F1, f);
-                    v[6 * s + 5] = dot_slice<DPL>(G1, f);
-                } else {
-#pragma unroll
-                    for (int t = 0; t < 6; ++t) v[6 * s + t] = 0.f;
-                }
-            }
-            if (js[1] >= 0) {   // f holds row js[1]: the pair's Gram entry f_k0 . f_k1
-                float f0[DPL];
-                load_row_f32<DPL>(sf + js[0] * D, lane, f0);
-                v[12] = dot_slice<DPL>(f0, f);
+            // two contributors in walk order: j0 (farther), then j1
+            const int j0 = 31 - __clz(U);
+            U &= ~(1u << j0);
+            const int j1 = U ? 31 - __clz(U) : -1;
+            if (j1 >= 0) U &= ~(1u << j1);
+            const EntryScalars e0 = es[j0];
+            const EntryScalars e1 = es[j1 < 0 ? j0 : j1];
+            const float w0 = e0.a * e0.T, w1 = j1 < 0 ? 0.f : e1.a * e1.T;
+            float v[8], f[DPL], f1[DPL];
+            load_row_f32<DPL>(sf + j0 * D, lane, f);
+            axpy_slice<DPL>(-w0, f, F);   // F_{j0 - 1}
+            v[0] = dot_slice<DPL>(g, f);
+            v[1] = dot_slice<DPL>(F, f);
+            v[2] = dot_slice<DPL>(Gs, f);
+            if (j1 >= 0) {
+                load_row_f32<DPL>(sf + j1 * D, lane, f1);
+                axpy_slice<DPL>(-w1, f1, F);   // F_{j1 - 1}
+                v[3] = dot_slice<DPL>(g, f1);
+                v[4] = dot_slice<DPL>(F, f1);
+                v[5] = dot_slice<DPL>(Gs, f1);
+                v[6] = dot_slice<DPL>(f, f1);   // the pair's Gram entry
             } else {
-                v[12] = 0.f;
+#pragma unroll
+                for (int i = 0; i < DPL; ++i) f1[i] = 0.f;
+                v[3] = v[4] = v[5] = v[6] = 0.f;
             }
-            v[13] = v[14] = v[15] = 0.f;
-            const float tot = warp_rs16(v, lane);   // value i in lanes 2 i, 2 i + 1
-            float sw[2][2];
-            float geo[2][6];
+            v[7] = 0.f;
+            const float tot = warp_rs8(v, lane);   // value i in lanes 4 i .. 4 i + 3
+            const float phi0 = __shfl_sync(kFull, tot, 0), X0 = __shfl_sync(kFull, tot, 4);
+            const float A0 = __shfl_sync(kFull, tot, 8), phi1 = __shfl_sync(kFull, tot, 12);
+            const float X1 = __shfl_sync(kFull, tot, 16), A1 = __shfl_sync(kFull, tot, 20);
             const float gram = __shfl_sync(kFull, tot, 24);
+            float geo0[6], geo1[6];
+            const float sig0 = ndfd_sigma(phi0 * sinv[j0] * igt, ks, lam);
+            const float gw0 = cgt * sig0 + ccf * (sig0 * ((1.f - e0.T) - X0) + Ss - A0);
+            footprint_geo(geo0, sa[j0], sb[j0], fpx, fpy, e0, p.amax, e0.T * gw0 - Sw / (1.f - e0.a));
+            Sw = fmaf(w0, gw0, Sw);
+            const float sw0 = sig0 * w0;
+            Ss += sw0;
+            float sw1 = 0.f;
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) geo[s][k] = 0.f;
-                const float phi0 = __shfl_sync(kFull, tot, 2 * (6 * s + 0));
-                const float X0 = __shfl_sync(kFull, tot, 2 * (6 * s + 1));
-                const float A0 = __shfl_sync(kFull, tot, 2 * (6 * s + 2));
-                const float phi1 = __shfl_sync(kFull, tot, 2 * (6 * s + 3));
-                const float X1 = __shfl_sync(kFull, tot, 2 * (6 * s + 4));
-                const float A1 = __shfl_sync(kFull, tot, 2 * (6 * s + 5));
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    sw[s][q] = 0.f;
-                    if (!cc[s][q]) continue;
-                    const int j = js[s];
-                    const EntryScalars &e = es[j];
-                    const float w = ww[s][q], Tk = e.T[q], ak = e.a[q];
-                    const float sig = ndfd_sigma((q ? phi1 : phi0) * sinv[j] * igt[q], ks, lam);
-                    // G . f_k: G at the pair's start, plus the first contributor's share
-                    float Y = q ? A1 : A0;
-                    if (s == 1) Y = fmaf(sw[0][q], gram, Y);
-                    const float gw =
-                        cgt[q] * sig + ccf[q] * (sig * ((1.f - Tk) - (q ? X1 : X0)) + Ss[q] - Y);
-                    const float dal = Tk * gw - Sw[q] / (1.f - ak);
-                    Sw[q] = fmaf(w, gw, Sw[q]);
-                    sw[s][q] = sig * w;
-                    Ss[q] += sw[s][q];
-                    const float drho = e.rho[q] > p.amax ? 0.f : dal;
-                    const float dq2 = -0.5f * e.rho[q] * drho;
-                    const float4 A = sa[j], B = sb[j];
-                    const float dx = rc.fpx[q] - A.x, dy = rc.fpy - A.y;
-                    geo[s][0] -= (2.f * A.z * dx + 2.f * A.w * dy) * dq2;
-                    geo[s][1] -= (2.f * A.w * dx + 2.f * B.x * dy) * dq2;
-                    geo[s][2] += dx * dx * dq2;
-                    geo[s][3] += 2.f * dx * dy * dq2;
-                    geo[s][4] += dy * dy * dq2;
-                    geo[s][5] += e.G[q] * drho;
-                }
+            for (int k = 0; k < 6; ++k) geo1[k] = 0.f;
+            if (j1 >= 0) {
+                const float sig1 = ndfd_sigma(phi1 * sinv[j1] * igt, ks, lam);
+                // G . f_j1: G at the pair's start plus j0's share
+                const float Y = fmaf(sw0, gram, A1);
+                const float gw1 = cgt * sig1 + ccf * (sig1 * ((1.f - e1.T) - X1) + Ss - Y);
+                footprint_geo(geo1, sa[j1], sb[j1], fpx, fpy, e1, p.amax, e1.T * gw1 - Sw / (1.f - e1.a));
+                Sw = fmaf(w1, gw1, Sw);
+                sw1 = sig1 * w1;
+                Ss += sw1;
             }
-            // G += sigma w f of both contributors
-            // f holds the row of the pair's last loaded contributor
-            if (js[1] >= 0) {
-                axpy_slice<DPL>(sw[1][0], f, G0);
-                axpy_slice<DPL>(sw[1][1], f, G1);
-                load_row_f32<DPL>(sf + js[0] * D, lane, f);
-            }
-            axpy_slice<DPL>(sw[0][0], f, G0);
-            axpy_slice<DPL>(sw[0][1], f, G1);
-            if (lane < 12) {   // lane 6 s + k adds component k of contributor s
-                const int s = lane >= 6 ? 1 : 0, k = lane - 6 * s;
-                float val = 0.f;
+            axpy_slice<DPL>(sw0, f, Gs);
+            axpy_slice<DPL>(sw1, f1, Gs);
+            // lanes 0..5 add j0's components, lanes 8..13 j1's
+            const int k = lane & 7;
+            float val = 0.f;
 #pragma unroll
-                for (int kk = 0; kk < 6; ++kk)
-                    if (kk == k) val = s ? geo[1][kk] : geo[0][kk];
-                const int j = s ? js[1] : js[0];
-                if (j >= 0 && val != 0.f) atomicAdd(&sacc[j][k], val);
-            }
+            for (int kk = 0; kk < 6; ++kk)
+                if (kk == k) val = lane < 8 ? geo0[kk] : geo1[kk];
+            const int j = lane < 8 ? j0 : j1;
+            if (lane < 16 && k < 6 && j >= 0 && inside && val != 0.f) atomicAdd(&sacc[j][k], val);
         }
         __syncthreads();
         if ((int)threadIdx.x < nb) {
@@ -649,7 +626,7 @@ void launch_bwd_t(long long N, const CamSet &cs, const Params &p, ProjView pv, c
     const int smem = kNC * 32 * DPL * 4;
     allow_max_smem(smem_set, k_ndfd_bwd<DPL, BF16>);
     note_launch(1);
-    k_ndfd_bwd<DPL, BF16><<<(unsigned)cs.total_tiles * 16, kThreads, smem, st>>>(
+    k_ndfd_bwd<DPL, BF16><<<(unsigned)cs.total_tiles * 16, kThreadsB, smem, st>>>(
         N, cs, p, pv, bins.gids, bins.ranges, feats, fgt, ks, lam, dLgt, dLcf, g2d);
 }
 
