@@ -20,6 +20,9 @@ Steps and the passages they follow:
   * ``render_bwd`` / ``project_bwd`` -- exact derivative of Eq. 4 with the
                         App. A.2 identity for dL/dalpha.
   * ``fuse``         -- compositing-weight-normalised fusion (Sec. 3.1).
+  * ``point_features`` -- the paper's point-to-feature assignment: a random
+                        visible view, the nearest pixel, its feature (Sec. 3.1,
+                        App. A "PointsFeatureFusion").
   * ``ndfd`` / ``ndfd_bwd`` -- the NDFD losses L_gt (Eq. 5) and L_cf (Eq. 6,
                         App. A.1) with the similarity activation of Sec. 3.3,
                         and their derivative through the weights w (Sec. 3.3,
@@ -465,3 +468,31 @@ def ndfd_backward(scene: dict, cams: list, params: dict | None, feats, fgt_list,
             tot[key] += gp[key]
         tot["opacities"] += g2["op"]
     return tot
+
+
+def camera_array_f32(cam: dict) -> np.ndarray:
+    """The camera as 18 binary32 values: width, height, fx, fy, cx, cy, [R|t]."""
+    return camera_array(cam, np.float32)
+
+
+def point_features(means, views: list, maps: list, u, params: dict | None = None) -> dict:
+    """Per point: the view drawn among those that see it (by u in [0, 1)),
+    the pixel it projects to there, and that pixel's feature (zeros when no
+    view sees it).  maps[v]: (H_v, W_v, D) or (H_v W_v, D)."""
+    prm = dict(DEFAULT_PARAMS)
+    prm.update(params or {})
+    m = np.ascontiguousarray(means, np.float32).reshape(-1, 3)
+    n = m.shape[0]
+    cams = np.ascontiguousarray(np.concatenate([camera_array_f32(c) for c in views]), np.float32)
+    uu = np.ascontiguousarray(u, np.float32).reshape(n)
+    view = np.zeros(n, np.int32)
+    pix = np.zeros(n, np.int32)
+    cnt = np.zeros(n, np.int32)
+    lib().orc_point_views_f32(ctypes.c_int64(n), _p(m), ctypes.c_int(len(views)), _p(cams),
+                              ctypes.c_float(prm["znear"]), _p(uu), _p(view), _p(pix), _p(cnt))
+    D = int(np.asarray(maps[0]).shape[-1])
+    flat = [np.asarray(mp).reshape(-1, D) for mp in maps]
+    out = np.zeros((n, D), np.float64)
+    for i in np.nonzero(view >= 0)[0]:
+        out[i] = flat[view[i]][pix[i]]
+    return dict(features=out, view=view, pixel=pix, count=cnt)

@@ -25,6 +25,9 @@
  *     with no tiles (the brute-force definition).
  *   - orc_fuse: the compositing-weight-normalised feature fusion
  *     f_g = sum_{v,p} w_g(v,p) F_v(p) / sum_{v,p} w_g(v,p) (Sec. 3.1).
+ *   - orc_point_views_f32: the paper's point-to-feature assignment
+ *     (Sec. 3.1, App. A "PointsFeatureFusion"): a random visible view, the
+ *     nearest pixel; binary32 projection spec (it decides integers).
  *   - orc_ndfd / orc_ndfd_bwd: the NDFD losses L_gt (Eq. 5) and L_cf
  *     (Eq. 6, App. A.1) with the activation of Sec. 3.3, over the render's
  *     weights, and their derivative through w (Sec. 3.3, App. A.2).
@@ -1058,4 +1061,57 @@ int orc_contributors(const double *rec, const uint32_t *list, int64_t len, const
     int nc = composite_pixel(cx, cy, list, len, rec, NULL, 0, prm, &st, NULL, pos, alpha, T, G, cap);
     free(G);
     return nc;
+}
+
+/* ------------------------------------------------- PointsFeatureFusion -- */
+/* The paper's point-to-feature assignment (Sec. 3.1; App. A,
+ * "PointsFeatureFusion"): a point takes the feature of the pixel it projects
+ * to in one view, drawn at random among the views that see it.  Readings:
+ * a view sees the point when its camera depth exceeds znear and the
+ * projection (x, y) lies in [0, W) x [0, H); the pixel is (floor x, floor y)
+ * (the nearest pixel centre, centres at +0.5); the draw is the k-th visible
+ * view in view order with k = floor(u |M|) for a given uniform u in [0, 1)
+ * (clamped to |M| - 1).  The projection decides an integer, so it is
+ * specified in binary32, one rounding per operation in the written order
+ * (this file is compiled with -ffp-contract=off):
+ *   c = ((R_r0 X + R_r1 Y) + R_r2 Z) + t_r  for each row r,
+ *   x = fx (c_x / c_z) + cx,  y = fy (c_y / c_z) + cy.
+ * cams: n_views x 18 floats (width, height, fx, fy, cx, cy, [R|t] row by
+ * row).  Outputs per point: the view (-1 if none sees it), the pixel index
+ * y W + x in that view, and the number of views that see it. */
+void orc_point_views_f32(int64_t n, const float *means, int n_views, const float *cams, float znear, const float *u,
+                         int32_t *out_view, int32_t *out_pixel, int32_t *out_count)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const float X = means[3 * i], Y = means[3 * i + 1], Z = means[3 * i + 2];
+        int count = 0;
+        int vis_pix[1024];
+        int vis_view[1024];
+        for (int v = 0; v < n_views && v < 1024; ++v) {
+            const float *c = cams + 18 * v;
+            const float *R = c + 6;
+            const float cx_ = ((R[0] * X + R[1] * Y) + R[2] * Z) + R[3];
+            const float cy_ = ((R[4] * X + R[5] * Y) + R[6] * Z) + R[7];
+            const float cz_ = ((R[8] * X + R[9] * Y) + R[10] * Z) + R[11];
+            if (!(cz_ > znear)) continue;
+            const float qx = cx_ / cz_, qy = cy_ / cz_;
+            const float x = c[2] * qx + c[4];
+            const float y = c[3] * qy + c[5];
+            if (!(x >= 0.0f && x < c[0] && y >= 0.0f && y < c[1])) continue;
+            vis_view[count] = v;
+            vis_pix[count] = (int)floorf(y) * (int)c[0] + (int)floorf(x);
+            ++count;
+        }
+        out_count[i] = count;
+        if (count == 0) {
+            out_view[i] = -1;
+            out_pixel[i] = -1;
+            continue;
+        }
+        int k = (int)(u[i] * (float)count);
+        if (k > count - 1) k = count - 1;
+        if (k < 0) k = 0;
+        out_view[i] = vis_view[k];
+        out_pixel[i] = vis_pix[k];
+    }
 }
