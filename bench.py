@@ -58,9 +58,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="warm-up + one step, no JSON (for ncu)")
-    ap.add_argument("--workload", choices=["render", "fusion", "ndfd"], default="render",
+    ap.add_argument("--workload", choices=["render", "fusion", "ndfd", "points"], default="render",
                     help="render: fwd+bwd of the 1080p view (the headline); fusion: 3M Gaussians x 64 views; "
-                         "ndfd: the NDFD losses L_gt, L_cf and their backward on the 1080p view")
+                         "ndfd: the NDFD losses L_gt, L_cf and their backward on the 1080p view; "
+                         "points: the paper's point-to-feature assignment, 3M points x 64 views")
     ap.add_argument("--views", type=int, default=64, help="fusion: number of views")
     return ap.parse_args()
 
@@ -539,6 +540,71 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------- point features
+def run_points(args):
+    """The paper's point-to-feature assignment over the fusion workload's
+    3M points and 64 views (maps generated on the device), one call per step."""
+    import torch
+    from paper_2505_19154_gb300 import api, synth
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, views = synth.config5(rank)
+    views = views[:args.views]
+    D = 256
+    means = torch.from_numpy(np.ascontiguousarray(scene["means"], np.float32)).to(dev)
+    N = means.shape[0]
+    maps = [device_feature_map(rank, v, views[v]["height"], views[v]["width"], D, dev) for v in range(len(views))]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5_000_011 + rank)
+    u = torch.rand(N, generator=gen, device=dev)
+    ctx = api.Context(local)
+    params = api.make_params()
+    W_ = max(3, args.warmup)
+    for _ in range(W_):
+        out, view, pixel = api.point_features(ctx, means, views, maps, u, params)
+    torch.cuda.synchronize()
+    if ctx.sync_status() != api.OK:
+        raise RuntimeError("device status after warm-up")
+    seen = int((view >= 0).sum().item())
+    clocks = ClockSampler(local)
+    ctx.profile(True)
+    clocks.start()
+    n0 = api.Context.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = max(1, args.steps)
+    e0.record()
+    for _ in range(K):
+        api.point_features(ctx, means, views, maps, u, params)
+    e1.record()
+    torch.cuda.synchronize()
+    launches = api.Context.launch_count() - n0
+    ck = clocks.stop()
+    prof = ctx.profile_read()
+    ms = e0.elapsed_time(e1) / K
+    kms = prof["point_features"][1] / max(prof["point_features"][0], 1)
+    # means and u read, view and pixel and the feature rows written, the seen
+    # points' map rows read: each once
+    algo = N * (12 + 4 + 8 + 4 * D) + seen * 4 * D
+    peaks = load_peaks()
+    ach = algo / (kms * 1e-3) / 1e9
+    line = {"metric": "point feature assignment Mpoints/s (3M points, 64 views 1280x720, D=256 FP32 maps)",
+            "value": round(N / (ms * 1e-3) / 1e6, 2), "unit": "Mpoints/s", "n_gpus": 1, "steps": K, "warmup": W_,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (maps generated on the device)",
+            "config": {"workload": "point features: 3M points, 64 views 1280x720, D=256", "views": len(views),
+                       "points": N, "seen": seen},
+            "roofline": {"bound": "hbm", "kernel": "point_features", "achieved": round(ach, 1),
+                         "peak": peaks["hbm"], "unit": "GB/s", "frac": round(ach / peaks["hbm"], 4),
+                         "peak_source": ("of measured" if peaks["src"] == "measured" else "of fallback") +
+                                        " (hbm_gbs)", "traffic": None, "algorithmic_bytes": algo},
+            "kernels": {k: {"launches": c, "ms": round(t / max(c, 1), 4)} for k, (c, t) in prof.items()},
+            "e2e": None, "cpu_baseline": None, "clocks": ck, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ NDFD
 NDFD_METRIC = "NDFD L_gt+L_cf fwd+bwd Mpix/s at 1M Gaussians, D=512 BF16; % of FP32 ALU roofline"
 NDFD_WORKLOAD = "1M Gaussians, 1920x1080 view, D=512 BF16 unit features and ground-truth map, NDFD fwd+bwd"
@@ -681,6 +747,8 @@ def main():
         run_fusion(args)
     elif args.workload == "ndfd":
         run_ndfd(args)
+    elif args.workload == "points":
+        run_points(args)
     else:
         run_ours(args)
 

@@ -217,6 +217,32 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
                                const float *const *maps, int D, const fhgs_params *p, float *num,
                                float *den, float *out, uint32_t flags, void *stream);
 
+/* ------------------------------------------------------- point features -- */
+/* The paper's point-to-feature assignment (Sec. 3.1; App. A,
+ * "PointsFeatureFusion"): point i takes the feature of the pixel it projects
+ * to in one view, drawn among the views that see it.  A view sees the point
+ * when its camera depth exceeds p->znear and the projection (x, y) lies in
+ * [0, W) x [0, H); the pixel is (floor x, floor y); the draw is the k-th
+ * visible view in view order with k = floor(u[i] |M_i|) (clamped).  The
+ * projection is binary32 with one rounding per operation in the order
+ * c_r = ((R_r0 X + R_r1 Y) + R_r2 Z) + t_r, x = fx (c_x / c_z) + cx,
+ * y = fy (c_y / c_z) + cy, so the choice is reproducible bit for bit.
+ *   means  [n][3] device float32;  u [n] device float32 in [0, 1) (the
+ *          caller's uniform draws);
+ *   views  host array of n_views (1 .. FHGS_MAX_POINT_VIEWS) cameras;
+ *   maps   host array of n_views DEVICE pointers, each [H_v*W_v][D] float32,
+ *          16-byte aligned; D a positive multiple of 8;
+ *   out    [n][D] device float32, 16-byte aligned: the feature (zeros for a
+ *          point no view sees);
+ *   view, pixel [n] device int32, nullable: the drawn view (-1 if none) and
+ *          the pixel index y W + x in it (-1 if none).
+ * Uses context scratch for the view table (copied from host memory on the
+ * stream), so it is not for stream capture. */
+#define FHGS_MAX_POINT_VIEWS 4096
+fhgs_status fhgs_point_features(fhgs_ctx *ctx, int64_t n, const float *means, const fhgs_camera *views, int n_views,
+                                const float *const *maps, int D, const float *u, const fhgs_params *p, float *out,
+                                int32_t *view, int32_t *pixel, void *stream);
+
 /* ------------------------------------------------------------------ NDFD -- */
 /* Non-differentiable feature driving (Sec. 3.2; App. A "NDFD"): per pixel,
  * over the same depth-sorted tile lists, contributors and Eq. 4 weights

@@ -27,7 +27,8 @@ EXPORTS = ["fhgs_create", "fhgs_destroy", "fhgs_last_error", "fhgs_status_string
            "fhgs_default_params", "fhgs_proj_bytes", "fhgs_total_tiles", "fhgs_reserve", "fhgs_sync_status",
            "fhgs_project", "fhgs_bin_sort", "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features",
            "fhgs_profile_enable", "fhgs_profile_read", "fhgs_launch_count", "fhgs_render_bwd_noalloc",
-           "fhgs_ndfd_fwd", "fhgs_ndfd_bwd"]
+           "fhgs_ndfd_fwd", "fhgs_ndfd_bwd", "fhgs_point_features"]
+MAX_POINT_VIEWS = 4096  # FHGS_MAX_POINT_VIEWS of include/fhgs.h
 NDFD_K, NDFD_LAMBDA = 20.0, 0.5  # the activation's slope and threshold (Sec. 4)
 
 
@@ -113,13 +114,15 @@ def lib():
         L.fhgs_ndfd_bwd.argtypes = [vp, ctypes.POINTER(Gaussians), vp, ctypes.POINTER(Bins), vp, vp, i32, i32,
                                     ctypes.POINTER(Camera), i32, ctypes.POINTER(Params), f32, f32, f32p, f32p,
                                     f32p, f32p, f32p, f32p, f32p, vp]
+        L.fhgs_point_features.argtypes = [vp, i64, f32p, ctypes.POINTER(Camera), i32, ctypes.POINTER(ctypes.c_void_p),
+                                          i32, f32p, ctypes.POINTER(Params), f32p, vp, vp, vp]
         L.fhgs_profile_enable.argtypes = [vp, i32]
         L.fhgs_profile_read.argtypes = [vp, ctypes.c_char_p, i64]
         L.fhgs_launch_count.argtypes = []
         L.fhgs_launch_count.restype = i64
         for name in ("fhgs_create", "fhgs_reserve", "fhgs_sync_status", "fhgs_project", "fhgs_bin_sort",
                      "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features", "fhgs_ndfd_fwd", "fhgs_ndfd_bwd",
-                     "fhgs_profile_enable",
+                     "fhgs_point_features", "fhgs_profile_enable",
                      "fhgs_profile_read"):
             getattr(L, name).restype = i32
         _lib = L
@@ -259,6 +262,25 @@ class Context:
                                        float(lam), _ptr(dLgt), _ptr(dLcf), _ptr(out["means"]), _ptr(out["scales"]),
                                        _ptr(out["quats"]), _ptr(out["opacities"]), _ptr(out["sh"]),
                                        self.stream_ptr(stream)))
+
+
+def point_features(ctx: "Context", means, views: Sequence[dict], maps: Sequence[torch.Tensor], u, params: Params,
+                   stream=None):
+    """fhgs_point_features: per point, the feature of its pixel in a view
+    drawn (by u in [0, 1)) among the views that see it.  maps[v]: [H*W, D]
+    float32 on the device.  Returns (features [n, D], view [n], pixel [n])."""
+    n = int(means.shape[0])
+    D = int(maps[0].shape[-1])
+    dev = means.device
+    out = torch.empty((n, D), dtype=torch.float32, device=dev)
+    view = torch.empty(n, dtype=torch.int32, device=dev)
+    pixel = torch.empty(n, dtype=torch.int32, device=dev)
+    cams = make_cameras(views)
+    ptrs = (ctypes.c_void_p * len(maps))(*[m.data_ptr() for m in maps])
+    ctx.check(lib().fhgs_point_features(ctx.h, n, _ptr(means.contiguous()), cams, len(views), ptrs, D,
+                                        _ptr(u.contiguous()), ctypes.byref(params), _ptr(out), _ptr(view),
+                                        _ptr(pixel), Context.stream_ptr(stream)))
+    return out, view, pixel
 
 
 def render_bwd_noalloc(g, proj, bins, features, D, cams, params, T, last, grgb, gfeat, out: dict, stream=None) -> int:

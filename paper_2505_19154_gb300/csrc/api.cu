@@ -34,6 +34,7 @@ struct fhgs_ctx {
     DevBuf bin;                  // binning scratch
     DevBuf g2d;                  // per (camera, Gaussian) render gradients
     DevBuf fuse_proj, fuse_gids, fuse_ranges, fuse_count;  // fusion view scratch
+    DevBuf pf_views;             // view table of the point-feature assignment
 };
 
 static std::atomic<long long> g_launches{0};
@@ -471,6 +472,51 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
     {
         Prof pb(ctx, "project_bwd", st);
         launch_project_bwd(*g, cs, q, pv, g2d, grad_means, grad_scales, grad_quats, grad_opac, grad_sh, st);
+    }
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_point_features(fhgs_ctx *ctx, int64_t n, const float *means, const fhgs_camera *views, int n_views,
+                                const float *const *maps, int D, const float *u, const fhgs_params *p, float *out,
+                                int32_t *view, int32_t *pixel, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    fhgs_status s = check_params(ctx, p);
+    if (s != FHGS_OK) return s;
+    if (n < 0 || n >= (1ll << 31)) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad point count");
+    if (D <= 0 || D % 8) return fail(ctx, FHGS_ERR_UNSUPPORTED, "D must be a positive multiple of 8");
+    if (!views || n_views < 1 || n_views > FHGS_MAX_POINT_VIEWS)
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "bad views");
+    if (!maps) return fail(ctx, FHGS_ERR_INVALID_ARG, "maps is NULL");
+    if (n > 0 && (!means || !u || !out)) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(out)) return fail(ctx, FHGS_ERR_ALIGNMENT, "out must be 16-byte aligned");
+    std::vector<PFView> tab((size_t)n_views);
+    for (int v = 0; v < n_views; ++v) {
+        const fhgs_camera &c = views[v];
+        if (c.width < 1 || c.height < 1 || !(c.fx > 0.f) || !(c.fy > 0.f))
+            return fail(ctx, FHGS_ERR_INVALID_ARG, "bad camera");
+        if (!maps[v]) return fail(ctx, FHGS_ERR_INVALID_ARG, "a feature map is NULL");
+        if (!aligned16(maps[v])) return fail(ctx, FHGS_ERR_ALIGNMENT, "feature maps must be 16-byte aligned");
+        PFView &t = tab[v];
+        t.cam[0] = (float)c.width;
+        t.cam[1] = (float)c.height;
+        t.cam[2] = c.fx;
+        t.cam[3] = c.fy;
+        t.cam[4] = c.cx;
+        t.cam[5] = c.cy;
+        for (int k = 0; k < 12; ++k) t.cam[6 + k] = c.world_to_cam[k];
+        t.pad[0] = t.pad[1] = 0;
+        t.map = maps[v];
+    }
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    if ((s = ensure(ctx, ctx->pf_views, sizeof(PFView) * (size_t)n_views)) != FHGS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    PFView *dv = (PFView *)ctx->pf_views.p;
+    // from pageable memory: staged before the call returns, so tab may go
+    FHGS_CUDA(ctx, cudaMemcpyAsync(dv, tab.data(), sizeof(PFView) * (size_t)n_views, cudaMemcpyHostToDevice, st));
+    {
+        Prof pr(ctx, "point_features", st);
+        launch_point_features(n, means, dv, n_views, p->znear, u, D, out, view, pixel, st);
     }
     FHGS_CUDA(ctx, cudaGetLastError());
     return FHGS_OK;

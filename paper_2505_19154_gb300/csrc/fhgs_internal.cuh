@@ -187,6 +187,17 @@ bool launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
                           const float *grgb, const float *gfeat, float *g2d, float *gfeatures, unsigned *status,
                           cudaStream_t st);
 
+// The paper's point-to-feature assignment (points.cu).  One view as the
+// kernel reads it: width, height, fx, fy, cx, cy, [R|t] row by row, and the
+// view's feature map [H*W][D] (device).
+struct PFView {
+    float cam[18];
+    int32_t pad[2];
+    const float *map;
+};
+void launch_point_features(long long n, const float *means, const PFView *views, int n_views, float znear,
+                           const float *u, int D, float *out, int32_t *view, int32_t *pixel, cudaStream_t st);
+
 // NDFD losses and their backward (ndfd.cu): D in {32, 64, 128, 256, 512}
 bool ndfd_supported(int D);
 void launch_ndfd_fwd(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
