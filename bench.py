@@ -601,8 +601,29 @@ def run_points(args):
                          "peak_source": ("of measured" if peaks["src"] == "measured" else "of fallback") +
                                         " (hbm_gbs)", "traffic": None, "algorithmic_bytes": algo},
             "kernels": {k: {"launches": c, "ms": round(t / max(c, 1), 4)} for k, (c, t) in prof.items()},
-            "e2e": None, "cpu_baseline": None, "clocks": ck, "gpu_launches": int(launches)}
+            "e2e": None, "cpu_baseline": None if args.no_cpu_baseline else points_cpu_baseline(means, views, maps, u),
+            "clocks": ck, "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
+
+
+def points_cpu_baseline(means, views, maps, u, n_sample=3_000_000):
+    """The oracle on the workload (the first n_sample points, all of them at
+    3M) against all views (binary32 projection spec, one host thread), then
+    their feature rows gathered from the maps by the oracle's own (view, pixel)."""
+    import oracle
+    m = means[:n_sample].cpu().numpy()
+    uu = u[:n_sample].cpu().numpy()
+    t0 = time.time()
+    r = oracle.point_views(m, views, uu)
+    rows = []
+    for v in range(len(views)):
+        sel = np.nonzero(r["view"] == v)[0]
+        if len(sel):
+            rows.append(maps[v][np.ascontiguousarray(r["pixel"][sel], np.int64)].cpu().numpy())
+    dt = time.time() - t0
+    return {"value": round(len(m) / dt / 1e6, 4), "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+            "sample": f"the first {len(m)} points against all {len(views)} views, rows gathered by the oracle's "
+                      f"(view, pixel)", "seconds": round(dt, 2)}
 
 
 # ------------------------------------------------------------------ NDFD

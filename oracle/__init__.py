@@ -475,10 +475,10 @@ def camera_array_f32(cam: dict) -> np.ndarray:
     return camera_array(cam, np.float32)
 
 
-def point_features(means, views: list, maps: list, u, params: dict | None = None) -> dict:
-    """Per point: the view drawn among those that see it (by u in [0, 1)),
-    the pixel it projects to there, and that pixel's feature (zeros when no
-    view sees it).  maps[v]: (H_v, W_v, D) or (H_v W_v, D)."""
+def point_views(means, views: list, u, params: dict | None = None) -> dict:
+    """Per point: the view drawn among those that see it (by u in [0, 1),
+    -1 if none), the pixel index it projects to there, and how many views
+    see it (binary32 projection spec)."""
     prm = dict(DEFAULT_PARAMS)
     prm.update(params or {})
     m = np.ascontiguousarray(means, np.float32).reshape(-1, 3)
@@ -490,6 +490,16 @@ def point_features(means, views: list, maps: list, u, params: dict | None = None
     cnt = np.zeros(n, np.int32)
     lib().orc_point_views_f32(ctypes.c_int64(n), _p(m), ctypes.c_int(len(views)), _p(cams),
                               ctypes.c_float(prm["znear"]), _p(uu), _p(view), _p(pix), _p(cnt))
+    return dict(view=view, pixel=pix, count=cnt)
+
+
+def point_features(means, views: list, maps: list, u, params: dict | None = None) -> dict:
+    """Per point: the view drawn among those that see it (by u in [0, 1)),
+    the pixel it projects to there, and that pixel's feature (zeros when no
+    view sees it).  maps[v]: (H_v, W_v, D) or (H_v W_v, D)."""
+    r = point_views(means, views, u, params)
+    view, pix, cnt = r["view"], r["pixel"], r["count"]
+    n = len(view)
     D = int(np.asarray(maps[0]).shape[-1])
     flat = [np.asarray(mp).reshape(-1, D) for mp in maps]
     out = np.zeros((n, D), np.float64)
