@@ -20,6 +20,9 @@ Steps and the passages they follow:
   * ``render_bwd`` / ``project_bwd`` -- exact derivative of Eq. 4 with the
                         App. A.2 identity for dL/dalpha.
   * ``fuse``         -- compositing-weight-normalised fusion (Sec. 3.1).
+  * ``splat_uv`` / ``render_2dgs_brute`` -- the surfel model of Sec. 3.1
+                        (Eq. 1-3): ray-plane intersection u(x), G(u) and the
+                        Eq. 4 compositing, per pixel over all surfels.
   * ``point_features`` -- the paper's point-to-feature assignment: a random
                         visible view, the nearest pixel, its feature (Sec. 3.1,
                         App. A "PointsFeatureFusion").
@@ -506,3 +509,42 @@ def point_features(means, views: list, maps: list, u, params: dict | None = None
     for i in np.nonzero(view >= 0)[0]:
         out[i] = flat[view[i]][pix[i]]
     return dict(features=out, view=view, pixel=pix, count=cnt)
+
+
+# ------------------------------------------------------------ 2DGS surfels
+def splat_uv(means, quats, scales2, cam: dict, px, py) -> dict:
+    """Per (pixel centre, surfel) pair: the plane coordinates (u, v) of the
+    pixel ray's intersection, its camera depth lambda, and whether the ray
+    meets the plane at all."""
+    mu = _f64(means).reshape(-1, 3)
+    m = mu.shape[0]
+    q = _f64(quats).reshape(m, 4)
+    s2 = _f64(scales2).reshape(m, 2)
+    u, v, lam = np.zeros(m), np.zeros(m), np.zeros(m)
+    hit = np.zeros(m, np.int32)
+    lib().orc_splat_uv(ctypes.c_int64(m), _p(mu), _p(q), _p(s2), _p(camera_array(cam)),
+                       _p(_f64(px).reshape(m)), _p(_f64(py).reshape(m)), _p(u), _p(v), _p(lam), _p(hit))
+    return dict(u=u, v=v, lam=lam, hit=hit.astype(bool))
+
+
+def render_2dgs_brute(surfels: dict, cam: dict, params: dict | None = None, region=None) -> dict:
+    """Brute-force surfel render (every pixel over every surfel, ordered by
+    the centre's camera depth).  surfels: means [n,3], quats [n,4],
+    scales2 [n,2] (s_u, s_v), opacities [n], rgb [n,3]."""
+    W, H = int(cam["width"]), int(cam["height"])
+    x0, y0, x1, y1 = region if region is not None else (0, 0, W, H)
+    npx = (x1 - x0) * (y1 - y0)
+    mu = _f64(surfels["means"]).reshape(-1, 3)
+    n = mu.shape[0]
+    w2c = np.asarray(cam["w2c"], np.float64).reshape(3, 4)
+    depth = mu @ w2c[2, :3] + w2c[2, 3]
+    rgb = np.zeros((npx, 3))
+    T = np.zeros(npx)
+    nc = np.zeros(npx, np.int32)
+    lib().orc_render_2dgs_brute(ctypes.c_int64(n), _p(mu), _p(_f64(surfels["quats"]).reshape(n, 4)),
+                                _p(_f64(surfels["scales2"]).reshape(n, 2)), _p(_f64(surfels["opacities"]).reshape(n)),
+                                _p(_f64(surfels["rgb"]).reshape(n, 3)), _p(np.ascontiguousarray(depth)),
+                                _p(camera_array(cam)), _p(params_array(params)), x0, y0, x1, y1, _p(rgb), _p(T),
+                                _p(nc))
+    hh, ww = y1 - y0, x1 - x0
+    return dict(rgb=rgb.reshape(hh, ww, 3), T=T.reshape(hh, ww), ncontrib=nc.reshape(hh, ww))

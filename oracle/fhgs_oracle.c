@@ -25,6 +25,9 @@
  *     with no tiles (the brute-force definition).
  *   - orc_fuse: the compositing-weight-normalised feature fusion
  *     f_g = sum_{v,p} w_g(v,p) F_v(p) / sum_{v,p} w_g(v,p) (Sec. 3.1).
+ *   - orc_splat_uv / orc_render_2dgs_brute: the surfel model of Sec. 3.1
+ *     (Eq. 1-3): the pixel ray's intersection u(x) with a surfel's plane,
+ *     G(u), and Eq. 4 compositing per pixel over all surfels.
  *   - orc_point_views_f32: the paper's point-to-feature assignment
  *     (Sec. 3.1, App. A "PointsFeatureFusion"): a random visible view, the
  *     nearest pixel; binary32 projection spec (it decides integers).
@@ -1114,4 +1117,115 @@ void orc_point_views_f32(int64_t n, const float *means, int n_views, const float
         out_view[i] = vis_view[k];
         out_pixel[i] = vis_pix[k];
     }
+}
+
+/* ------------------------------------------------------- 2DGS surfels -- */
+/* The surfel model of Sec. 3.1 (Eq. 1-3): a primitive is the tangent plane
+ * P(u, v) = p + s_u t_u u + s_v t_v v, with t_u, t_v the first two columns of
+ * R (the normalised quaternion) and density G(u) = exp(-(u^2 + v^2)/2).  A
+ * pixel's value is taken at u(x), the point of the plane that projects to
+ * the pixel: the intersection of the pixel's camera ray with the plane,
+ *   lambda d = c + u a + v b,   d = ((x - cx)/fx, (y - cy)/fy, 1),
+ *   c = R_w p + t_w,  a = R_w (s_u t_u),  b = R_w (s_v t_v),
+ * solved by Cramer's rule (lambda is the camera depth of the intersection).
+ * A ray parallel to the plane (|det| <= 1e-12 |d| |a| |b|) misses it.
+ * Returns 1 and (u, v, lambda) on a hit. */
+static int splat_uv(const double *mu, const double *q, const double *s2, const double *cam, double px,
+                    double py, double *u, double *v, double *lam)
+{
+    const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
+    double R[3][3];
+    quat_to_rot(qn, R);
+    double c[3], a[3], b[3];
+    for (int r = 0; r < 3; ++r) {
+        c[r] = cam_t(cam, r);
+        a[r] = 0.0;
+        b[r] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            c[r] += cam_R(cam, r, k) * mu[k];
+            a[r] += cam_R(cam, r, k) * R[k][0] * s2[0];
+            b[r] += cam_R(cam, r, k) * R[k][1] * s2[1];
+        }
+    }
+    const double d[3] = {(px - cam[4]) / cam[2], (py - cam[5]) / cam[3], 1.0};
+    /* columns of M: d, -a, -b */
+    const double m00 = d[0], m01 = -a[0], m02 = -b[0];
+    const double m10 = d[1], m11 = -a[1], m12 = -b[1];
+    const double m20 = d[2], m21 = -a[2], m22 = -b[2];
+    const double det = m00 * (m11 * m22 - m12 * m21) - m01 * (m10 * m22 - m12 * m20) + m02 * (m10 * m21 - m11 * m20);
+    const double nd = sqrt(d[0] * d[0] + d[1] * d[1] + 1.0);
+    const double na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double nb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    if (!(fabs(det) > 1e-12 * nd * na * nb)) return 0;
+    /* Cramer: replace one column by c */
+    const double dl = c[0] * (m11 * m22 - m12 * m21) - m01 * (c[1] * m22 - m12 * c[2]) + m02 * (c[1] * m21 - m11 * c[2]);
+    const double du = m00 * (c[1] * m22 - m12 * c[2]) - c[0] * (m10 * m22 - m12 * m20) + m02 * (m10 * c[2] - c[1] * m20);
+    const double dv = m00 * (m11 * c[2] - c[1] * m21) - m01 * (m10 * c[2] - c[1] * m20) + c[0] * (m10 * m21 - m11 * m20);
+    *lam = dl / det;
+    *u = du / det;
+    *v = dv / det;
+    return 1;
+}
+
+/* (u, v, lambda, hit) of every (pixel centre, surfel) pair given. */
+void orc_splat_uv(int64_t m, const double *mu, const double *q, const double *s2, const double *cam, const double *px,
+                  const double *py, double *u, double *v, double *lam, int32_t *hit)
+{
+    for (int64_t i = 0; i < m; ++i)
+        hit[i] = splat_uv(mu + 3 * i, q + 4 * i, s2 + 2 * i, cam, px[i], py[i], u + i, v + i, lam + i);
+}
+
+/* Brute-force surfel render of the region: every pixel composites all
+ * surfels whose centre lies beyond znear, in order of (depth_key, index),
+ * front to back with the rules of the render (Eq. 4): alpha = min(alpha_max,
+ * op G(u(x))) for u^2 + v^2 <= cutoff_sq and an intersection in front of the
+ * camera (lambda > 0), skip alpha < alpha_min, stop before T (1 - alpha) <
+ * t_eps; background added to RGB.  rgb: the surfels' colours [n][3]. */
+void orc_render_2dgs_brute(int64_t n, const double *means, const double *quats, const double *scales2,
+                           const double *opac, const double *rgb, const double *depth_key, const double *cam,
+                           const double *prm, int x0, int y0, int x1, int y1, double *out_rgb, double *out_T,
+                           int32_t *out_ncontrib)
+{
+    kd_pair *order = (kd_pair *)malloc(sizeof(kd_pair) * (size_t)(n > 0 ? n : 1));
+    int64_t m = 0;
+    for (int64_t g = 0; g < n; ++g) {
+        double cz = cam_t(cam, 2);
+        for (int k = 0; k < 3; ++k) cz += cam_R(cam, 2, k) * means[3 * g + k];
+        if (cz > prm[P_ZNEAR]) {
+            order[m].key = depth_key[g];
+            order[m].g = (uint32_t)g;
+            ++m;
+        }
+    }
+    qsort(order, (size_t)m, sizeof(kd_pair), kd_cmp);
+    const int rw = x1 - x0, rh = y1 - y0;
+    const double cut = prm[P_CUT], amin = prm[P_AMIN], amax = prm[P_AMAX], teps = prm[P_TEPS];
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+        const double px = x0 + (int)(idx % rw) + 0.5, py = y0 + (int)(idx / rw) + 0.5;
+        double T = 1.0, acc[3] = {0.0, 0.0, 0.0};
+        int nc = 0;
+        for (int64_t k = 0; k < m; ++k) {
+            const uint32_t g = order[k].g;
+            double u, v, lam;
+            if (!splat_uv(means + 3 * g, quats + 4 * g, scales2 + 2 * g, cam, px, py, &u, &v, &lam)) continue;
+            if (!(lam > 0.0)) continue;
+            const double r2 = u * u + v * v;
+            if (r2 > cut) continue;
+            const double rho = opac[g] * exp(-0.5 * r2);
+            const double alpha = rho > amax ? amax : rho;
+            if (alpha < amin) continue;
+            const double Tn = T * (1.0 - alpha);
+            if (Tn < teps) break;
+            const double w = alpha * T;
+            for (int ch = 0; ch < 3; ++ch) acc[ch] += w * rgb[3 * g + ch];
+            T = Tn;
+            ++nc;
+        }
+        for (int ch = 0; ch < 3; ++ch) out_rgb[3 * idx + ch] = acc[ch] + T * prm[P_BG0 + ch];
+        out_T[idx] = T;
+        out_ncontrib[idx] = nc;
+    }
+    free(order);
 }

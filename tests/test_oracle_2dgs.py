@@ -1,0 +1,118 @@
+"""Pins of the oracle's 2DGS surfel model (Sec. 3.1, Eq. 1-3), no GPU.
+
+(a) a face-on surfel's footprint is the closed-form isotropic Gaussian of
+    std f s / z pixels, with the cutoff and alpha_min rules;
+(b) the ray-plane solve: the surfel point P(u, v), taken to the camera,
+    lies on the pixel's ray at depth lambda;
+(c) an edge-on surfel renders nothing, and a plane met behind the camera
+    counts for nothing;
+(d) turning a surfel about its normal by 90 degrees with s_u, s_v swapped
+    gives the same image; scaling the scene about the camera changes nothing;
+(e) weights and transmittance sum to one; two stacked surfels composite
+    nearest first.
+"""
+import math
+
+import numpy as np
+
+import oracle
+from tests.helpers import axis_camera
+
+
+def _surf(means, quats, s2, op, rgb):
+    return dict(means=np.atleast_2d(means), quats=np.atleast_2d(quats), scales2=np.atleast_2d(s2),
+                opacities=np.atleast_1d(op), rgb=np.atleast_2d(rgb))
+
+
+def test_face_on_surfel_is_the_closed_form_gaussian():
+    cam = axis_camera(W=64, H=48, fx=60.0, cx=32.5, cy=24.5)
+    z, s, op = 2.0, 0.05, 0.8
+    out = oracle.render_2dgs_brute(_surf([0, 0, z], [1, 0, 0, 0], [s, s], op, [1, 0, 0]), cam)
+    sig = 60.0 * s / z   # 1.5 px
+    for py in range(48):
+        for px in range(64):
+            r2 = ((px - 32) ** 2 + (py - 24) ** 2) / sig ** 2
+            a = op * math.exp(-0.5 * r2)
+            if r2 > 9 or a < 1 / 255:
+                a = 0.0
+            assert abs(out["rgb"][py, px, 0] - a) < 1e-14, (px, py)
+            assert abs(out["T"][py, px] - (1 - a)) < 1e-14
+
+
+def test_ray_plane_solve_lands_on_the_ray():
+    g = np.random.default_rng(1)
+    cam = axis_camera(W=50, H=40, fx=45.0, fy=41.0, cx=24.0, cy=21.0, t=(0.1, -0.05, 0.3))
+    m = 500
+    mu = g.normal(0, 0.4, (m, 3)) + [0, 0, 2.5]
+    q = g.normal(size=(m, 4))
+    s2 = np.exp(g.uniform(-3, -1, (m, 2)))
+    px, py = g.uniform(0, 50, m), g.uniform(0, 40, m)
+    r = oracle.splat_uv(mu, q, s2, cam, px, py)
+    assert r["hit"].all()
+    R = oracle.quat_to_rot(q)
+    P = mu + (s2[:, :1] * r["u"][:, None]) * R[:, :, 0] + (s2[:, 1:] * r["v"][:, None]) * R[:, :, 1]
+    w2c = np.asarray(cam["w2c"]).reshape(3, 4)
+    c = P @ w2c[:, :3].T + w2c[:, 3]
+    np.testing.assert_allclose(c[:, 2], r["lam"], rtol=1e-12)
+    np.testing.assert_allclose(c[:, 0], r["lam"] * (px - 24.0) / 45.0, atol=1e-11)
+    np.testing.assert_allclose(c[:, 1], r["lam"] * (py - 21.0) / 41.0, atol=1e-11)
+
+
+def test_edge_on_surfel_renders_nothing():
+    cam = axis_camera(W=32, H=32, fx=30.0, cx=16.0, cy=16.0)
+    # 90 degrees about x: t_u = x, t_v = z, normal along -y; the plane holds the camera centre
+    h = math.sqrt(0.5)
+    out = oracle.render_2dgs_brute(_surf([0, 0, 2], [h, h, 0, 0], [0.2, 0.2], 0.9, [1, 1, 1]), cam)
+    assert (out["ncontrib"] == 0).all() and (out["T"] == 1).all()
+
+
+def test_turning_about_the_normal_and_scaling_the_scene():
+    g = np.random.default_rng(2)
+    cam = axis_camera(W=40, H=36, fx=35.0)
+    n = 12
+    mu = g.normal(0, 0.3, (n, 3)) + [0, 0, 2.2]
+    q = g.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    s2 = np.exp(g.uniform(-3, -1.8, (n, 2)))
+    op = g.uniform(0.2, 0.9, n)
+    rgb = g.uniform(0, 1, (n, 3))
+    base = oracle.render_2dgs_brute(_surf(mu, q, s2, op, rgb), cam)
+    # quaternion of a 90-degree turn about the local z (the normal): q * (cos 45, 0, 0, sin 45)
+    h = math.sqrt(0.5)
+    w, x, y, z = q.T
+    q2 = np.stack([h * w - h * z, h * x + h * y, h * y - h * x, h * z + h * w], axis=1)
+    turned = oracle.render_2dgs_brute(_surf(mu, q2, s2[:, ::-1], op, rgb), cam)
+    np.testing.assert_allclose(turned["rgb"], base["rgb"], atol=1e-12)
+    scaled = oracle.render_2dgs_brute(_surf(3.0 * mu, q, 3.0 * s2, op, rgb), cam)
+    np.testing.assert_allclose(scaled["rgb"], base["rgb"], atol=1e-12)
+    assert (base["ncontrib"] > 1).mean() > 0.05
+
+
+def test_weights_sum_and_stacking_order():
+    cam = axis_camera(W=32, H=32, fx=30.0, cx=16.5, cy=16.5)
+    out = oracle.render_2dgs_brute(_surf([[0, 0, 2], [0.02, 0, 3]], [[1, 0, 0, 0], [1, 0, 0, 0]],
+                                         [[0.1, 0.1], [0.2, 0.2]], [0.6, 0.7], [[1, 1, 1], [1, 1, 1]]), cam)
+    np.testing.assert_allclose(out["rgb"][..., 0] + out["T"], 1.0, atol=1e-14)
+    two = oracle.render_2dgs_brute(_surf([[0, 0, 2], [0, 0, 3]], [[1, 0, 0, 0], [1, 0, 0, 0]],
+                                         [[0.1, 0.1], [0.2, 0.2]], [0.6, 0.7], [[1, 0, 0], [0, 1, 0]]), cam)
+    # pixel (16, 16) is the centre of both: alpha = op there
+    np.testing.assert_allclose(two["rgb"][16, 16], [0.6, 0.4 * 0.7, 0.0], atol=1e-14)
+
+
+def test_plane_behind_the_camera_does_not_count():
+    """A large surfel tilted almost edge-on close to the camera: for the
+    lower rows its plane meets the pixel rays behind the camera (lambda < 0)
+    near its centre.  Those pixels get nothing, the others do."""
+    cam = axis_camera(W=32, H=32, fx=30.0, cx=16.0, cy=16.0)
+    phi = math.radians(85.0)
+    q = [math.cos(phi / 2), math.sin(phi / 2), 0.0, 0.0]
+    surf = _surf([0, 0, 0.5], q, [5.0, 5.0], 0.9, [1, 1, 1])
+    out = oracle.render_2dgs_brute(surf, cam)
+    ys, xs = np.mgrid[0:32, 0:32]
+    r = oracle.splat_uv(np.tile([0, 0, 0.5], (1024, 1)), np.tile(q, (1024, 1)), np.tile([5.0, 5.0], (1024, 1)), cam,
+                        xs.reshape(-1) + 0.5, ys.reshape(-1) + 0.5)
+    behind = (r["lam"] <= 0).reshape(32, 32)
+    near_centre = ((r["u"] ** 2 + r["v"] ** 2) < 9).reshape(32, 32)
+    assert (behind & near_centre).sum() > 50
+    assert (out["ncontrib"][behind] == 0).all()
+    assert (out["ncontrib"][~behind & near_centre] == 1).all() and (~behind & near_centre).sum() > 50
