@@ -57,6 +57,16 @@ class _OracleRank:
         return torch.where(d > 0, num / torch.where(d > 0, d, torch.ones_like(d)), torch.zeros_like(num))
 
 
+def _ndfd_inputs(views, D=8):
+    protos = synth.ndfd_prototypes(33, D)
+    feats = synth.ndfd_features(33, 60, protos).astype(np.float64)
+    fgts = [synth.ndfd_ground_truth(33, v, c["height"], c["width"], protos, block=8) for v, c in enumerate(views)]
+    g = np.random.default_rng(7)
+    a = [g.normal(size=c["height"] * c["width"]) for c in views]
+    b = [g.normal(size=c["height"] * c["width"]) for c in views]
+    return feats, fgts, a, b
+
+
 def _worker(rank, world, port, q):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -84,9 +94,20 @@ def _worker(rank, world, port, q):
         grads = {k: torch.from_numpy(np.ascontiguousarray(g[k], np.float64)) for k in
                  ("means", "scales", "quats", "opacities", "sh", "features")}
         shard.allreduce_sum(list(grads.values()))
+        # NDFD gradients (L_gt, L_cf): the same per-rank backward and one sum
+        nf, nfg, na, nb = _ndfd_inputs(views)
+        if mine:
+            gn = oracle.ndfd_backward(sc, [views[v] for v in mine], dict(sh_degree=1), nf, [nfg[v] for v in mine],
+                                      [na[v] for v in mine], [nb[v] for v in mine])
+        else:
+            gn = {k: np.zeros_like(np.asarray(sc[k], np.float64)) for k in ("means", "scales", "quats", "opacities")}
+        ngrads = {k: torch.from_numpy(np.ascontiguousarray(gn[k], np.float64))
+                  for k in ("means", "scales", "quats", "opacities")}
+        shard.allreduce_sum(list(ngrads.values()))
         if rank == 0:
             q.put(dict(fused=fused.numpy(), num=num.numpy(), den=den.numpy(),
-                       grads={k: v.numpy() for k, v in grads.items()}))
+                       grads={k: v.numpy() for k, v in grads.items()},
+                       ndfd={k: v.numpy() for k, v in ngrads.items()}))
     finally:
         dist.destroy_process_group()
 
@@ -130,3 +151,9 @@ def test_two_gloo_ranks_match_single_process():
                            [u[1] for u in ups])
     for k, v in res["grads"].items():
         np.testing.assert_allclose(v, gref[k], rtol=1e-10, atol=1e-12, err_msg=k)
+
+    nf, nfg, na, nb = _ndfd_inputs(views)
+    nref = oracle.ndfd_backward(sc, views, dict(sh_degree=1), nf, nfg, na, nb)
+    assert np.abs(nref["means"]).max() > 0
+    for k, v in res["ndfd"].items():
+        np.testing.assert_allclose(v, nref[k], rtol=1e-10, atol=1e-12, err_msg="ndfd " + k)
