@@ -548,3 +548,16 @@ def render_2dgs_brute(surfels: dict, cam: dict, params: dict | None = None, regi
                                 _p(nc))
     hh, ww = y1 - y0, x1 - x0
     return dict(rgb=rgb.reshape(hh, ww, 3), T=T.reshape(hh, ww), ncontrib=nc.reshape(hh, ww))
+
+
+def surfel_rect(means, quats, scales2, cam: dict, cut: float = 9.0) -> dict:
+    """Screen bounding box (xmin, xmax, ymin, ymax) of each surfel's
+    u^2 + v^2 <= cut ellipse, and whether it is bounded (the ellipse wholly
+    in front of the camera; otherwise the box is the whole image)."""
+    mu = _f64(means).reshape(-1, 3)
+    n = mu.shape[0]
+    rect = np.zeros((n, 4))
+    bounded = np.zeros(n, np.int32)
+    lib().orc_surfel_rect(ctypes.c_int64(n), _p(mu), _p(_f64(quats).reshape(n, 4)), _p(_f64(scales2).reshape(n, 2)),
+                          _p(camera_array(cam)), ctypes.c_double(cut), _p(rect), _p(bounded))
+    return dict(rect=rect, bounded=bounded.astype(bool))

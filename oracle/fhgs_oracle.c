@@ -25,9 +25,10 @@
  *     with no tiles (the brute-force definition).
  *   - orc_fuse: the compositing-weight-normalised feature fusion
  *     f_g = sum_{v,p} w_g(v,p) F_v(p) / sum_{v,p} w_g(v,p) (Sec. 3.1).
- *   - orc_splat_uv / orc_render_2dgs_brute: the surfel model of Sec. 3.1
- *     (Eq. 1-3): the pixel ray's intersection u(x) with a surfel's plane,
- *     G(u), and Eq. 4 compositing per pixel over all surfels.
+ *   - orc_splat_uv / orc_render_2dgs_brute / orc_surfel_rect: the surfel
+ *     model of Sec. 3.1 (Eq. 1-3): the pixel ray's intersection u(x) with a
+ *     surfel's plane, G(u), Eq. 4 compositing per pixel over all surfels,
+ *     and the exact screen box of a surfel's footprint (dual conic).
  *   - orc_point_views_f32: the paper's point-to-feature assignment
  *     (Sec. 3.1, App. A "PointsFeatureFusion"): a random visible view, the
  *     nearest pixel; binary32 projection spec (it decides integers).
@@ -1228,4 +1229,69 @@ void orc_render_2dgs_brute(int64_t n, const double *means, const double *quats, 
         out_ncontrib[idx] = nc;
     }
     free(order);
+}
+
+/* Screen rectangle of a surfel's footprint u^2 + v^2 <= cut (the region the
+ * render can touch): the image of that ellipse of the plane is a conic, and
+ * its axis-aligned bounding box follows from the dual conic
+ *   C* = T diag(1, 1, -1/cut) T^T,  T = [K a, K b, K c]  (3x3, columns),
+ * whose vertical tangents x = x0 solve C*00 - 2 x0 C*02 + x0^2 C*22 = 0 (and
+ * likewise for y with row 1).  The ellipse must lie wholly in front of the
+ * camera (its least depth c_z - sqrt(cut ((a_z)^2 + (b_z)^2)) > 0, with a, b
+ * the camera-space tangent vectors scaled by s_u, s_v); otherwise its image
+ * is unbounded and the rectangle is the whole image.  Output per surfel:
+ * rect = (xmin, xmax, ymin, ymax) in pixel coordinates and the flag
+ * bounded (1) / whole image (0). */
+void orc_surfel_rect(int64_t n, const double *means, const double *quats, const double *scales2, const double *cam,
+                     double cut, double *rect, int32_t *bounded)
+{
+    const double W = cam[0], H = cam[1], fx = cam[2], fy = cam[3], cx = cam[4], cy = cam[5];
+    for (int64_t g = 0; g < n; ++g) {
+        const double *q = quats + 4 * g;
+        const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
+        double R[3][3];
+        quat_to_rot(qn, R);
+        double c[3], a[3], b[3];
+        for (int r = 0; r < 3; ++r) {
+            c[r] = cam_t(cam, r);
+            a[r] = 0.0;
+            b[r] = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                c[r] += cam_R(cam, r, k) * means[3 * g + k];
+                a[r] += cam_R(cam, r, k) * R[k][0] * scales2[2 * g];
+                b[r] += cam_R(cam, r, k) * R[k][1] * scales2[2 * g + 1];
+            }
+        }
+        double *out = rect + 4 * g;
+        const double zmin = c[2] - sqrt(cut * (a[2] * a[2] + b[2] * b[2]));
+        if (!(zmin > 0.0)) {
+            out[0] = 0.0; out[1] = W; out[2] = 0.0; out[3] = H;
+            bounded[g] = 0;
+            continue;
+        }
+        /* T = K [a b c]: rows (fx a_x + cx a_z, ...), (fy a_y + cy a_z, ...), (a_z, b_z, c_z) */
+        double T[3][3];
+        const double *col[3] = {a, b, c};
+        for (int j = 0; j < 3; ++j) {
+            T[0][j] = fx * col[j][0] + cx * col[j][2];
+            T[1][j] = fy * col[j][1] + cy * col[j][2];
+            T[2][j] = col[j][2];
+        }
+        const double dq[3] = {1.0, 1.0, -1.0 / cut};
+        double Cs[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) {
+                double acc = 0.0;
+                for (int j = 0; j < 3; ++j) acc += T[r][j] * dq[j] * T[s][j];
+                Cs[r][s] = acc;
+            }
+        const double dx = sqrt(fmax(0.0, Cs[0][2] * Cs[0][2] - Cs[0][0] * Cs[2][2]));
+        const double dy = sqrt(fmax(0.0, Cs[1][2] * Cs[1][2] - Cs[1][1] * Cs[2][2]));
+        const double x1 = (Cs[0][2] - dx) / Cs[2][2], x2 = (Cs[0][2] + dx) / Cs[2][2];
+        const double y1 = (Cs[1][2] - dy) / Cs[2][2], y2 = (Cs[1][2] + dy) / Cs[2][2];
+        out[0] = fmin(x1, x2); out[1] = fmax(x1, x2);
+        out[2] = fmin(y1, y2); out[3] = fmax(y1, y2);
+        bounded[g] = 1;
+    }
 }

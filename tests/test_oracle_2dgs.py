@@ -116,3 +116,54 @@ def test_plane_behind_the_camera_does_not_count():
     assert (behind & near_centre).sum() > 50
     assert (out["ncontrib"][behind] == 0).all()
     assert (out["ncontrib"][~behind & near_centre] == 1).all() and (~behind & near_centre).sum() > 50
+
+
+def test_surfel_rect_is_the_tight_box_of_the_projected_ellipse():
+    """The dual-conic box against the projected boundary u^2 + v^2 = 9,
+    sampled densely: every sample inside, every edge reached; a face-on
+    surfel's box is its centre +- 3 f s / z; every pixel the render can
+    touch lies inside; an ellipse reaching behind the camera gets the whole
+    image."""
+    g = np.random.default_rng(4)
+    cam = axis_camera(W=80, H=60, fx=70.0, fy=66.0, cx=41.0, cy=29.0, t=(0.05, -0.1, 0.2))
+    n = 40
+    mu = g.normal(0, 0.5, (n, 3)) + [0, 0, 2.4]
+    q = g.normal(size=(n, 4))
+    s2 = np.exp(g.uniform(-3.5, -1.8, (n, 2)))
+    r = oracle.surfel_rect(mu, q, s2, cam)
+    assert r["bounded"].all()
+    R = oracle.quat_to_rot(q)
+    w2c = np.asarray(cam["w2c"]).reshape(3, 4)
+    th = np.linspace(0, 2 * np.pi, 20001)
+    for i in range(n):
+        P = (mu[i][:, None] + 3 * s2[i, 0] * np.cos(th) * R[i, :, 0][:, None]
+             + 3 * s2[i, 1] * np.sin(th) * R[i, :, 1][:, None])
+        c = w2c[:, :3] @ P + w2c[:, 3:]
+        x = 70.0 * c[0] / c[2] + 41.0
+        y = 66.0 * c[1] / c[2] + 29.0
+        box = r["rect"][i]
+        assert x.min() >= box[0] - 1e-9 and x.max() <= box[1] + 1e-9
+        assert y.min() >= box[2] - 1e-9 and y.max() <= box[3] + 1e-9
+        span = max(box[1] - box[0], box[3] - box[2])
+        assert abs(x.min() - box[0]) < 1e-6 * span and abs(x.max() - box[1]) < 1e-6 * span
+        assert abs(y.min() - box[2]) < 1e-6 * span and abs(y.max() - box[3]) < 1e-6 * span
+    # face-on
+    cam0 = axis_camera(W=64, H=48, fx=60.0, cx=32.5, cy=24.5)
+    f = oracle.surfel_rect([[0.1, -0.05, 2.0]], [[1, 0, 0, 0]], [[0.05, 0.08]], cam0)
+    cxp, cyp = 60.0 * 0.1 / 2.0 + 32.5, 60.0 * -0.05 / 2.0 + 24.5
+    np.testing.assert_allclose(f["rect"][0], [cxp - 4.5, cxp + 4.5, cyp - 7.2, cyp + 7.2], atol=1e-12)
+    # the render's coverage lies inside
+    ys, xs = np.mgrid[0:60, 0:80]
+    for i in range(0, n, 7):
+        uv = oracle.splat_uv(np.tile(mu[i], (4800, 1)), np.tile(q[i], (4800, 1)), np.tile(s2[i], (4800, 1)), cam,
+                             xs.reshape(-1) + 0.5, ys.reshape(-1) + 0.5)
+        inside = uv["hit"] & (uv["lam"] > 0) & (uv["u"] ** 2 + uv["v"] ** 2 <= 9)
+        px, py = xs.reshape(-1)[inside] + 0.5, ys.reshape(-1)[inside] + 0.5
+        box = r["rect"][i]
+        assert ((px >= box[0]) & (px <= box[1]) & (py >= box[2]) & (py <= box[3])).all()
+    # reaching behind the camera
+    b = oracle.surfel_rect([[0, 0, 0.5]], [[1, 0, 0, 0]], [[0.5, 0.5]], cam0)
+    assert b["bounded"][0] and abs(b["rect"][0][1] - b["rect"][0][0] - 2 * 3 * 60 * 0.5 / 0.5) < 1e-9
+    h = math.sqrt(0.5)
+    b = oracle.surfel_rect([[0, 0, 0.5]], [[h, h, 0, 0]], [[0.5, 0.5]], cam0)   # tilted: spans z = 0.5 +- 1.5
+    assert not b["bounded"][0] and list(b["rect"][0]) == [0, 64, 0, 48]
