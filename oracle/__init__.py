@@ -561,3 +561,23 @@ def surfel_rect(means, quats, scales2, cam: dict, cut: float = 9.0) -> dict:
     lib().orc_surfel_rect(ctypes.c_int64(n), _p(mu), _p(_f64(quats).reshape(n, 4)), _p(_f64(scales2).reshape(n, 2)),
                           _p(camera_array(cam)), ctypes.c_double(cut), _p(rect), _p(bounded))
     return dict(rect=rect, bounded=bounded.astype(bool))
+
+
+def render_2dgs_bwd_brute(surfels: dict, cam: dict, params: dict | None, dC, region=None) -> dict:
+    """Gradients of sum_p dC[p] . rgb[p] of render_2dgs_brute with respect
+    to means, quats, scales2, opacities and rgb."""
+    W, H = int(cam["width"]), int(cam["height"])
+    x0, y0, x1, y1 = region if region is not None else (0, 0, W, H)
+    mu = _f64(surfels["means"]).reshape(-1, 3)
+    n = mu.shape[0]
+    w2c = np.asarray(cam["w2c"], np.float64).reshape(3, 4)
+    depth = mu @ w2c[2, :3] + w2c[2, 3]
+    out = dict(means=np.zeros((n, 3)), quats=np.zeros((n, 4)), scales2=np.zeros((n, 2)), opacities=np.zeros(n),
+               rgb=np.zeros((n, 3)))
+    lib().orc_render_2dgs_bwd_brute(ctypes.c_int64(n), _p(mu), _p(_f64(surfels["quats"]).reshape(n, 4)),
+                                    _p(_f64(surfels["scales2"]).reshape(n, 2)),
+                                    _p(_f64(surfels["opacities"]).reshape(n)), _p(_f64(surfels["rgb"]).reshape(n, 3)),
+                                    _p(np.ascontiguousarray(depth)), _p(camera_array(cam)), _p(params_array(params)),
+                                    x0, y0, x1, y1, _p(_f64(dC).reshape(-1, 3)), _p(out["means"]), _p(out["quats"]),
+                                    _p(out["scales2"]), _p(out["opacities"]), _p(out["rgb"]))
+    return out

@@ -25,10 +25,12 @@
  *     with no tiles (the brute-force definition).
  *   - orc_fuse: the compositing-weight-normalised feature fusion
  *     f_g = sum_{v,p} w_g(v,p) F_v(p) / sum_{v,p} w_g(v,p) (Sec. 3.1).
- *   - orc_splat_uv / orc_render_2dgs_brute / orc_surfel_rect: the surfel
- *     model of Sec. 3.1 (Eq. 1-3): the pixel ray's intersection u(x) with a
- *     surfel's plane, G(u), Eq. 4 compositing per pixel over all surfels,
- *     and the exact screen box of a surfel's footprint (dual conic).
+ *   - orc_splat_uv / orc_render_2dgs_brute / orc_render_2dgs_bwd_brute /
+ *     orc_surfel_rect: the surfel model of Sec. 3.1 (Eq. 1-3): the pixel
+ *     ray's intersection u(x) with a surfel's plane, G(u), Eq. 4 compositing
+ *     per pixel over all surfels and its derivative (App. A.2 with the
+ *     ray-plane solve differentiated implicitly), and the exact screen box of
+ *     a surfel's footprint (dual conic).
  *   - orc_point_views_f32: the paper's point-to-feature assignment
  *     (Sec. 3.1, App. A "PointsFeatureFusion"): a random visible view, the
  *     nearest pixel; binary32 projection spec (it decides integers).
@@ -645,6 +647,24 @@ void orc_render_bwd(const double *rec, const double *feat, int D, const uint32_t
 }
 
 /* ------------------------------------------------ projection backward -- */
+/* dL/dR (GR, 3x3) -> dL/dq (+=) through R = R(q / |q|): the derivative of
+ * the rotation matrix of a unit quaternion, then the normalisation's
+ * Jacobian (I - qn qn^T) / |q|. */
+static void quat_grad(const double qn[4], double nq, double GR[3][3], double *gq)
+{
+    const double w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    double gqn[4];
+    gqn[0] = 2.0 * (-z * GR[0][1] + y * GR[0][2] + z * GR[1][0] - x * GR[1][2] - y * GR[2][0] + x * GR[2][1]);
+    gqn[1] = 2.0 * (y * GR[0][1] + z * GR[0][2] + y * GR[1][0] - 2.0 * x * GR[1][1] - w * GR[1][2] +
+                    z * GR[2][0] + w * GR[2][1] - 2.0 * x * GR[2][2]);
+    gqn[2] = 2.0 * (-2.0 * y * GR[0][0] + x * GR[0][1] + w * GR[0][2] + x * GR[1][0] + z * GR[1][2] -
+                    w * GR[2][0] + z * GR[2][1] - 2.0 * y * GR[2][2]);
+    gqn[3] = 2.0 * (-2.0 * z * GR[0][0] - w * GR[0][1] + x * GR[0][2] + w * GR[1][0] - 2.0 * z * GR[1][1] +
+                    y * GR[1][2] + x * GR[2][0] + y * GR[2][1]);
+    double dot = qn[0] * gqn[0] + qn[1] * gqn[1] + qn[2] * gqn[2] + qn[3] * gqn[3];
+    for (int k = 0; k < 4; ++k) gq[k] += (gqn[k] - qn[k] * dot) / nq;
+}
+
 /* Chain rule from (mean2d, conic, rgb) of one camera to the Gaussian
  * parameters; accumulates (+=) into g_means[n][3], g_scales[n][3],
  * g_quats[n][4], g_sh[n][K][3]. */
@@ -734,17 +754,7 @@ static void project_bwd_one(const double *mu, const double *s, const double *q, 
         for (int i = 0; i < 3; ++i) { acc += GM[i][j] * R[i][j]; GR[i][j] = GM[i][j] * s[j]; }
         gs[j] += acc;
     }
-    const double w = qn[0], x = qn[1], y = qn[2], z = qn[3];
-    double gqn[4];
-    gqn[0] = 2.0 * (-z * GR[0][1] + y * GR[0][2] + z * GR[1][0] - x * GR[1][2] - y * GR[2][0] + x * GR[2][1]);
-    gqn[1] = 2.0 * (y * GR[0][1] + z * GR[0][2] + y * GR[1][0] - 2.0 * x * GR[1][1] - w * GR[1][2] +
-                    z * GR[2][0] + w * GR[2][1] - 2.0 * x * GR[2][2]);
-    gqn[2] = 2.0 * (-2.0 * y * GR[0][0] + x * GR[0][1] + w * GR[0][2] + x * GR[1][0] + z * GR[1][2] -
-                    w * GR[2][0] + z * GR[2][1] - 2.0 * y * GR[2][2]);
-    gqn[3] = 2.0 * (-2.0 * z * GR[0][0] - w * GR[0][1] + x * GR[0][2] + w * GR[1][0] - 2.0 * z * GR[1][1] +
-                    y * GR[1][2] + x * GR[2][0] + y * GR[2][1]);
-    double dot = qn[0] * gqn[0] + qn[1] * gqn[1] + qn[2] * gqn[2] + qn[3] * gqn[3];
-    for (int k = 0; k < 4; ++k) gq[k] += (gqn[k] - qn[k] * dot) / nq;
+    quat_grad(qn, nq, GR, gq);
     /* SH colour */
     double cpos[3], v[3];
     for (int i = 0; i < 3; ++i)
@@ -1294,4 +1304,154 @@ void orc_surfel_rect(int64_t n, const double *means, const double *quats, const 
         out[2] = fmin(y1, y2); out[3] = fmax(y1, y2);
         bounded[g] = 1;
     }
+}
+
+/* Gradient of L = sum_p dC[p] . rgb[p] of the brute-force surfel render
+ * (orc_render_2dgs_brute) with respect to each surfel's mean, quaternion,
+ * (s_u, s_v), opacity and colour; accumulates (+=).  dL/dalpha by the App.
+ * A.2 identity with the background term, as in orc_render_bwd; then
+ * alpha = op G(u, v) (the clamp passes nothing), dG/du = -u G, dG/dv = -v G,
+ * and (lambda, u, v) = M^-1 c with M = [d, -a, -b] differentiated
+ * implicitly: d(lambda, u, v) = M^-1 (dc + u da + v db), so with
+ * w = M^-T (0, dL/du, dL/dv):  dL/dp = R_w^T w,
+ * dL/dR[:,0] = s_u u R_w^T w, dL/dR[:,1] = s_v v R_w^T w,
+ * dL/ds_u = u w . (R_w R[:,0]), dL/ds_v = v w . (R_w R[:,1]). */
+void orc_render_2dgs_bwd_brute(int64_t n, const double *means, const double *quats, const double *scales2,
+                               const double *opac, const double *rgb, const double *depth_key, const double *cam,
+                               const double *prm, int x0, int y0, int x1, int y1, const double *dC, double *g_means,
+                               double *g_quats, double *g_scales2, double *g_opac, double *g_rgb)
+{
+    kd_pair *order = (kd_pair *)malloc(sizeof(kd_pair) * (size_t)(n > 0 ? n : 1));
+    int64_t m = 0;
+    for (int64_t g = 0; g < n; ++g) {
+        double cz = cam_t(cam, 2);
+        for (int k = 0; k < 3; ++k) cz += cam_R(cam, 2, k) * means[3 * g + k];
+        if (cz > prm[P_ZNEAR]) {
+            order[m].key = depth_key[g];
+            order[m].g = (uint32_t)g;
+            ++m;
+        }
+    }
+    qsort(order, (size_t)m, sizeof(kd_pair), kd_cmp);
+    const int rw = x1 - x0, rh = y1 - y0;
+    const double cut = prm[P_CUT], amin = prm[P_AMIN], amax = prm[P_AMAX], teps = prm[P_TEPS];
+#pragma omp parallel
+    {
+        uint32_t *cg = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1));
+        double *ca = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * 5);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+            const double px = x0 + (int)(idx % rw) + 0.5, py = y0 + (int)(idx / rw) + 0.5;
+            double T = 1.0;
+            int nc = 0;
+            for (int64_t k = 0; k < m; ++k) {
+                const uint32_t g = order[k].g;
+                double u, v, lam;
+                if (!splat_uv(means + 3 * g, quats + 4 * g, scales2 + 2 * g, cam, px, py, &u, &v, &lam)) continue;
+                if (!(lam > 0.0)) continue;
+                const double r2 = u * u + v * v;
+                if (r2 > cut) continue;
+                const double G = exp(-0.5 * r2);
+                const double rho = opac[g] * G;
+                const double alpha = rho > amax ? amax : rho;
+                if (alpha < amin) continue;
+                const double Tn = T * (1.0 - alpha);
+                if (Tn < teps) break;
+                cg[nc] = g;
+                ca[5 * nc + 0] = alpha;
+                ca[5 * nc + 1] = T;
+                ca[5 * nc + 2] = G;
+                ca[5 * nc + 3] = u;
+                ca[5 * nc + 4] = v;
+                ++nc;
+                T = Tn;
+            }
+            const double *dc = dC + 3 * idx;
+            double S = T * (dc[0] * prm[P_BG0] + dc[1] * prm[P_BG1] + dc[2] * prm[P_BG2]);
+            for (int j = nc - 1; j >= 0; --j) {
+                const uint32_t g = cg[j];
+                const double alpha = ca[5 * j], Tj = ca[5 * j + 1], G = ca[5 * j + 2], u = ca[5 * j + 3],
+                             v = ca[5 * j + 4];
+                const double w = alpha * Tj;
+                const double gw = dc[0] * rgb[3 * g] + dc[1] * rgb[3 * g + 1] + dc[2] * rgb[3 * g + 2];
+                const double dalpha = Tj * gw - S / (1.0 - alpha);
+                S += w * gw;
+                for (int ch = 0; ch < 3; ++ch) {
+#pragma omp atomic
+                    g_rgb[3 * g + ch] += w * dc[ch];
+                }
+                const double rho = opac[g] * G;
+                const double drho = rho > amax ? 0.0 : dalpha;
+#pragma omp atomic
+                g_opac[g] += G * drho;
+                const double dG = opac[g] * drho;
+                const double e[3] = {0.0, -u * G * dG, -v * G * dG};
+                /* the surfel's frame in the camera */
+                const double *q = quats + 4 * g;
+                const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+                const double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
+                double R[3][3];
+                quat_to_rot(qn, R);
+                const double su = scales2[2 * g], sv = scales2[2 * g + 1];
+                double ru[3], rv[3];   /* R_w R[:,0], R_w R[:,1] */
+                for (int r = 0; r < 3; ++r) {
+                    ru[r] = 0.0;
+                    rv[r] = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        ru[r] += cam_R(cam, r, k) * R[k][0];
+                        rv[r] += cam_R(cam, r, k) * R[k][1];
+                    }
+                }
+                const double d[3] = {(px - cam[4]) / cam[2], (py - cam[5]) / cam[3], 1.0};
+                double M[3][3];
+                for (int r = 0; r < 3; ++r) {
+                    M[r][0] = d[r];
+                    M[r][1] = -su * ru[r];
+                    M[r][2] = -sv * rv[r];
+                }
+                /* w3 = M^-T e: solve M^T w3 = e by Cramer's rule on A = M^T */
+                double A[3][3];
+                for (int r = 0; r < 3; ++r)
+                    for (int k = 0; k < 3; ++k) A[r][k] = M[k][r];
+                const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                                   A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                                   A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+                double w3[3];
+                for (int col = 0; col < 3; ++col) {
+                    double B[3][3];
+                    for (int r = 0; r < 3; ++r)
+                        for (int k = 0; k < 3; ++k) B[r][k] = k == col ? e[r] : A[r][k];
+                    w3[col] = (B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1]) -
+                               B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0]) +
+                               B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0])) / det;
+                }
+                double rt[3];   /* R_w^T w3 */
+                for (int k = 0; k < 3; ++k) rt[k] = cam_R(cam, 0, k) * w3[0] + cam_R(cam, 1, k) * w3[1] + cam_R(cam, 2, k) * w3[2];
+                for (int k = 0; k < 3; ++k) {
+#pragma omp atomic
+                    g_means[3 * g + k] += rt[k];
+                }
+                const double gsu = u * (w3[0] * ru[0] + w3[1] * ru[1] + w3[2] * ru[2]);
+                const double gsv = v * (w3[0] * rv[0] + w3[1] * rv[1] + w3[2] * rv[2]);
+#pragma omp atomic
+                g_scales2[2 * g] += gsu;
+#pragma omp atomic
+                g_scales2[2 * g + 1] += gsv;
+                double GR[3][3];
+                for (int k = 0; k < 3; ++k) {
+                    GR[k][0] = su * u * rt[k];
+                    GR[k][1] = sv * v * rt[k];
+                    GR[k][2] = 0.0;
+                }
+                double gq[4] = {0.0, 0.0, 0.0, 0.0};
+                quat_grad(qn, nq, GR, gq);
+                for (int k = 0; k < 4; ++k) {
+#pragma omp atomic
+                    g_quats[4 * g + k] += gq[k];
+                }
+            }
+        }
+        free(cg); free(ca);
+    }
+    free(order);
 }

@@ -167,3 +167,48 @@ def test_surfel_rect_is_the_tight_box_of_the_projected_ellipse():
     h = math.sqrt(0.5)
     b = oracle.surfel_rect([[0, 0, 0.5]], [[h, h, 0, 0]], [[0.5, 0.5]], cam0)   # tilted: spans z = 0.5 +- 1.5
     assert not b["bounded"][0] and list(b["rect"][0]) == [0, 64, 0, 48]
+
+
+def test_surfel_backward_matches_central_differences():
+    g = np.random.default_rng(8)
+    cam = axis_camera(W=28, H=24, fx=26.0, t=(0.03, -0.02, 0.1))
+    n = 8
+    q = g.normal(size=(n, 4))
+    surf = dict(means=g.normal(0, 0.25, (n, 3)) + [0, 0, 2.0], quats=q / np.linalg.norm(q, axis=1, keepdims=True),
+                scales2=np.exp(g.uniform(-2.6, -1.6, (n, 2))), opacities=g.uniform(0.2, 0.9, n),
+                rgb=g.uniform(0, 1, (n, 3)))
+    # a wide, nearly opaque surfel in front: alpha = min(0.99, op G) clamps over a few pixels
+    surf["means"][0] = [0.02, -0.03, 1.6]
+    surf["scales2"][0] = [0.5, 0.4]
+    surf["opacities"][0] = 0.999
+    surf["quats"][0] = [1.0, 0.0, 0.0, 0.0]
+    prm = dict(bg=(0.2, 0.4, 0.1))
+    dC = g.normal(size=(24 * 28, 3))
+    grads = oracle.render_2dgs_bwd_brute(surf, cam, prm, dC)
+
+    def loss(s):
+        return float((oracle.render_2dgs_brute(s, cam, prm)["rgb"].reshape(-1, 3) * dC).sum())
+
+    checked = 0
+    for key in ("means", "quats", "scales2", "opacities", "rgb"):
+        base = np.asarray(surf[key], np.float64)
+        flat = base.reshape(-1)
+        for i in range(flat.size):
+            fds = []
+            for h in (1e-6, 5e-7):
+                vals = []
+                for sgn in (1, -1):
+                    pert = flat.copy()
+                    pert[i] += sgn * h * max(1.0, abs(flat[i]))
+                    vals.append(loss(dict(surf, **{key: pert.reshape(base.shape)})))
+                fds.append((vals[0] - vals[1]) / (2 * h * max(1.0, abs(flat[i]))))
+            if abs(fds[0] - fds[1]) > 1e-6 * max(1.0, abs(fds[0])):
+                continue   # a decision flipped inside the step
+            an = grads[key].reshape(-1)[i]
+            assert abs(fds[0] - an) <= 2e-6 * max(1.0, abs(fds[0])), (key, i, fds[0], an)
+            checked += abs(an) > 1e-8
+    assert checked > 80
+    uv = oracle.splat_uv(np.tile(surf["means"][0], (672, 1)), np.tile(surf["quats"][0], (672, 1)),
+                         np.tile(surf["scales2"][0], (672, 1)), cam, np.tile(np.arange(28) + 0.5, 24),
+                         np.repeat(np.arange(24) + 0.5, 28))
+    assert (0.999 * np.exp(-0.5 * (uv["u"] ** 2 + uv["v"] ** 2)) > 0.99).sum() >= 2
