@@ -581,3 +581,19 @@ def render_2dgs_bwd_brute(surfels: dict, cam: dict, params: dict | None, dC, reg
                                     x0, y0, x1, y1, _p(_f64(dC).reshape(-1, 3)), _p(out["means"]), _p(out["quats"]),
                                     _p(out["scales2"]), _p(out["opacities"]), _p(out["rgb"]))
     return out
+
+
+def bin_surfel_f32(means, quats, scales2, cam: dict, params: dict | None = None) -> dict:
+    """The binary32 surfel binning rule: pixel and tile rectangles (x0, y0,
+    x1, y1; inclusive), tile counts (0 = culled or off the image) and the
+    depth key bits."""
+    m = np.ascontiguousarray(means, np.float32).reshape(-1, 3)
+    n = m.shape[0]
+    pix = np.zeros((n, 4), np.int32)
+    tile = np.zeros((n, 4), np.int32)
+    nt = np.zeros(n, np.uint32)
+    db = np.zeros(n, np.uint32)
+    lib().orc_bin_surfel_f32(ctypes.c_int64(n), _p(m), _p(np.ascontiguousarray(quats, np.float32).reshape(n, 4)),
+                             _p(np.ascontiguousarray(scales2, np.float32).reshape(n, 2)), _p(camera_array_f32(cam)),
+                             _p(params_array(params, np.float32)), _p(pix), _p(tile), _p(nt), _p(db))
+    return dict(pix=pix, tile=tile, ntiles=nt, dbits=db)

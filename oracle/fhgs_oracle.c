@@ -30,7 +30,8 @@
  *     ray's intersection u(x) with a surfel's plane, G(u), Eq. 4 compositing
  *     per pixel over all surfels and its derivative (App. A.2 with the
  *     ray-plane solve differentiated implicitly), and the exact screen box of
- *     a surfel's footprint (dual conic).
+ *     a surfel's footprint (dual conic); orc_bin_surfel_f32: its binary32
+ *     binning rule (a padded box, integer decisions reproducible bit for bit).
  *   - orc_point_views_f32: the paper's point-to-feature assignment
  *     (Sec. 3.1, App. A "PointsFeatureFusion"): a random visible view, the
  *     nearest pixel; binary32 projection spec (it decides integers).
@@ -1454,4 +1455,84 @@ void orc_render_2dgs_bwd_brute(int64_t n, const double *means, const double *qua
         free(cg); free(ca);
     }
     free(order);
+}
+
+/* Binary32 binning rule for surfels (it decides integers, so it is specified
+ * operation by operation; this file is compiled with -ffp-contract=off).
+ *   qn = q / sqrt(((w w + x x) + y y) + z z); t_u, t_v = the first two
+ *   columns of R(qn) (the formulas of quat_to_rot, each product rounded);
+ *   c_r = ((W_r0 X + W_r1 Y) + W_r2 Z) + t_r;
+ *   a_r = (((W_r0 R_00 + W_r1 R_10) + W_r2 R_20)) s_u, b_r likewise with
+ *   column 1 and s_v;
+ *   the ellipse must clear the camera: c_z - sqrt(cut ((a_z a_z) + (b_z b_z)))
+ *   > znear, else the surfel is culled (no tiles);
+ *   T_0j = fx k_jx + cx k_jz, T_1j = fy k_jy + cy k_jz, T_2j = k_jz for the
+ *   columns k = a, b, c;
+ *   C*_rs = (T_r0 T_s0 + T_r1 T_s1) - (T_r2 T_s2) / cut;
+ *   the box x in [(C*_02 - e_x) / C*_22, (C*_02 + e_x) / C*_22] (ordered),
+ *   e_x = sqrt(max(0, C*_02 C*_02 - C*_00 C*_22)), likewise y with row 1;
+ *   widened by 1/64 of its larger side plus 1/2 px against the rounding of
+ *   the above;
+ *   pixels: those whose centre lies in the box, ceil(lo - 1/2) ..
+ *   floor(hi - 1/2), clamped to the image; tiles: pixel / 16.
+ * Outputs as orc_bin_f32: pix (x0, y0, x1, y1), tile (x0, y0, x1, y1),
+ * ntiles (0 if culled or off the image) and the depth bits of c_z. */
+void orc_bin_surfel_f32(int64_t n, const float *means, const float *quats, const float *scales2, const float *cam,
+                        const float *prm, int32_t *pix, int32_t *tile, uint32_t *ntiles, uint32_t *dbits)
+{
+    const float W = cam[0], H = cam[1], fx = cam[2], fy = cam[3], cx = cam[4], cy = cam[5];
+    const float *Wm = cam + 6;
+    const float cut = prm[P_CUT], znear = prm[P_ZNEAR];
+    const int tsz = (int)prm[P_TILE];
+    for (int64_t g = 0; g < n; ++g) {
+        int32_t *p4 = pix + 4 * g, *t4 = tile + 4 * g;
+        ntiles[g] = 0;
+        p4[0] = p4[1] = p4[2] = p4[3] = 0;
+        t4[0] = t4[1] = t4[2] = t4[3] = 0;
+        dbits[g] = 0xFFFFFFFFu;
+        const float *q = quats + 4 * g;
+        const float nq = sqrtf(((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3]);
+        const float w = q[0] / nq, x = q[1] / nq, y = q[2] / nq, z = q[3] / nq;
+        const float R00 = 1.0f - 2.0f * (y * y + z * z), R10 = 2.0f * (x * y + w * z), R20 = 2.0f * (x * z - w * y);
+        const float R01 = 2.0f * (x * y - w * z), R11 = 1.0f - 2.0f * (x * x + z * z), R21 = 2.0f * (y * z + w * x);
+        const float X = means[3 * g], Y = means[3 * g + 1], Z = means[3 * g + 2];
+        float c[3], a[3], b[3];
+        for (int r = 0; r < 3; ++r) {
+            const float *row = Wm + 4 * r;
+            c[r] = ((row[0] * X + row[1] * Y) + row[2] * Z) + row[3];
+            a[r] = ((row[0] * R00 + row[1] * R10) + row[2] * R20) * scales2[2 * g];
+            b[r] = ((row[0] * R01 + row[1] * R11) + row[2] * R21) * scales2[2 * g + 1];
+        }
+        const float zmin = c[2] - sqrtf(cut * (a[2] * a[2] + b[2] * b[2]));
+        if (!(zmin > znear)) continue;
+        const float *col[3] = {a, b, c};
+        float T[3][3];
+        for (int j = 0; j < 3; ++j) {
+            T[0][j] = fx * col[j][0] + cx * col[j][2];
+            T[1][j] = fy * col[j][1] + cy * col[j][2];
+            T[2][j] = col[j][2];
+        }
+        float Cs[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) Cs[r][s] = (T[r][0] * T[s][0] + T[r][1] * T[s][1]) - (T[r][2] * T[s][2]) / cut;
+        const float ex = sqrtf(fmaxf(0.0f, Cs[0][2] * Cs[0][2] - Cs[0][0] * Cs[2][2]));
+        const float ey = sqrtf(fmaxf(0.0f, Cs[1][2] * Cs[1][2] - Cs[1][1] * Cs[2][2]));
+        const float xa = (Cs[0][2] - ex) / Cs[2][2], xb = (Cs[0][2] + ex) / Cs[2][2];
+        const float ya = (Cs[1][2] - ey) / Cs[2][2], yb = (Cs[1][2] + ey) / Cs[2][2];
+        float x0 = fminf(xa, xb), x1 = fmaxf(xa, xb), y0 = fminf(ya, yb), y1 = fmaxf(ya, yb);
+        if (!isfinite(x0) || !isfinite(x1) || !isfinite(y0) || !isfinite(y1)) continue;
+        const float pad = fmaxf(x1 - x0, y1 - y0) * 0.015625f + 0.5f;
+        x0 = x0 - pad; x1 = x1 + pad; y0 = y0 - pad; y1 = y1 + pad;
+        float xlo = ceilf(x0 - 0.5f), xhi = floorf(x1 - 0.5f);
+        float ylo = ceilf(y0 - 0.5f), yhi = floorf(y1 - 0.5f);
+        xlo = fmaxf(xlo, 0.0f);
+        ylo = fmaxf(ylo, 0.0f);
+        xhi = fminf(xhi, W - 1.0f);
+        yhi = fminf(yhi, H - 1.0f);
+        if (xlo > xhi || ylo > yhi) continue;
+        p4[0] = (int)xlo; p4[1] = (int)ylo; p4[2] = (int)xhi; p4[3] = (int)yhi;
+        t4[0] = p4[0] / tsz; t4[1] = p4[1] / tsz; t4[2] = p4[2] / tsz; t4[3] = p4[3] / tsz;
+        ntiles[g] = (uint32_t)((t4[2] - t4[0] + 1) * (t4[3] - t4[1] + 1));
+        memcpy(dbits + g, &c[2], 4);
+    }
 }

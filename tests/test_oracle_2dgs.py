@@ -212,3 +212,46 @@ def test_surfel_backward_matches_central_differences():
                          np.tile(surf["scales2"][0], (672, 1)), cam, np.tile(np.arange(28) + 0.5, 24),
                          np.repeat(np.arange(24) + 0.5, 28))
     assert (0.999 * np.exp(-0.5 * (uv["u"] ** 2 + uv["v"] ** 2)) > 0.99).sum() >= 2
+
+
+def test_surfel_binning_rule_is_conservative_and_close():
+    """The binary32 binning rule: every pixel the render gives a surfel's
+    weight to lies in that surfel's pixel rectangle; the rectangle stays
+    within the exact box widened by the rule's pad plus a pixel; tiles are
+    pixel / 16; an ellipse reaching the near plane is culled."""
+    g = np.random.default_rng(12)
+    cam = axis_camera(W=96, H=72, fx=80.0, fy=76.0, cx=47.0, cy=37.0, t=(0.04, 0.02, 0.1))
+    n = 60
+    q = g.normal(size=(n, 4))
+    mu = g.normal(0, 0.45, (n, 3)) + [0, 0, 2.2]
+    s2 = np.exp(g.uniform(-3.5, -1.7, (n, 2)))
+    b = oracle.bin_surfel_f32(mu, q, s2, cam)
+    exact = oracle.surfel_rect(mu, q, s2, cam)
+    ys, xs = np.mgrid[0:72, 0:96]
+    kept = 0
+    for i in range(n):
+        if b["ntiles"][i] == 0:
+            continue
+        kept += 1
+        x0, y0, x1, y1 = b["pix"][i]
+        np.testing.assert_array_equal(b["tile"][i], [x0 // 16, y0 // 16, x1 // 16, y1 // 16])
+        uv = oracle.splat_uv(np.tile(mu[i], (xs.size, 1)), np.tile(q[i], (xs.size, 1)), np.tile(s2[i], (xs.size, 1)),
+                             cam, xs.reshape(-1) + 0.5, ys.reshape(-1) + 0.5)
+        hit = uv["hit"] & (uv["lam"] > 0) & (uv["u"] ** 2 + uv["v"] ** 2 <= 9)
+        hx, hy = xs.reshape(-1)[hit], ys.reshape(-1)[hit]
+        assert ((hx >= x0) & (hx <= x1) & (hy >= y0) & (hy <= y1)).all(), i
+        ex0, ex1, ey0, ey1 = exact["rect"][i]
+        pad = max(ex1 - ex0, ey1 - ey0) / 64 + 0.5 + 1.0
+        assert x0 >= max(0, np.floor(ex0 - pad)) and x1 <= min(95, np.ceil(ex1 + pad)), i
+        assert y0 >= max(0, np.floor(ey0 - pad)) and y1 <= min(71, np.ceil(ey1 + pad)), i
+        assert b["dbits"][i] != 0xFFFFFFFF
+    assert kept > 40
+    h = np.float32(np.sqrt(0.5))
+    near = oracle.bin_surfel_f32([[0, 0, 0.6]], [[h, h, 0, 0]], [[0.2, 0.2]], cam)   # spans z = 0.7 -+ 0.6
+    assert near["ntiles"][0] == 0
+    # face-on: centre +- 3 f s / z, widened by the pad
+    cam0 = axis_camera(W=64, H=48, fx=60.0, cx=32.0, cy=24.0)
+    f = oracle.bin_surfel_f32([[0.0, 0.0, 2.0]], [[1, 0, 0, 0]], [[0.05, 0.05]], cam0)
+    e = 3 * 60 * 0.05 / 2 + (2 * 4.5) / 64 + 0.5   # half-width + pad
+    assert list(f["pix"][0]) == [int(np.ceil(32 - e - 0.5)), int(np.ceil(24 - e - 0.5)),
+                                 int(np.floor(32 + e - 0.5)), int(np.floor(24 + e - 0.5))]
