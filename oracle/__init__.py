@@ -597,3 +597,26 @@ def bin_surfel_f32(means, quats, scales2, cam: dict, params: dict | None = None)
                              _p(np.ascontiguousarray(scales2, np.float32).reshape(n, 2)), _p(camera_array_f32(cam)),
                              _p(params_array(params, np.float32)), _p(pix), _p(tile), _p(nt), _p(db))
     return dict(pix=pix, tile=tile, ntiles=nt, dbits=db)
+
+
+def render_2dgs(surfels: dict, cam: dict, params: dict | None = None, region=None) -> dict:
+    """Tiled surfel render: the binary32 binning rule, per-tile lists sorted
+    by (tile, depth bits, id), and each pixel's walk of its tile's list."""
+    W, H = int(cam["width"]), int(cam["height"])
+    x0, y0, x1, y1 = region if region is not None else (0, 0, W, H)
+    npx = (x1 - x0) * (y1 - y0)
+    mu = _f64(surfels["means"]).reshape(-1, 3)
+    n = mu.shape[0]
+    b = bin_surfel_f32(np.asarray(surfels["means"], np.float32), np.asarray(surfels["quats"], np.float32),
+                       np.asarray(surfels["scales2"], np.float32), cam, params)
+    lists = tile_lists([b], [cam], params)
+    rgb = np.zeros((npx, 3))
+    T = np.zeros(npx)
+    nc = np.zeros(npx, np.int32)
+    lib().orc_render_2dgs(_p(mu), _p(_f64(surfels["quats"]).reshape(n, 4)), _p(_f64(surfels["scales2"]).reshape(n, 2)),
+                          _p(_f64(surfels["opacities"]).reshape(n)), _p(_f64(surfels["rgb"]).reshape(n, 3)),
+                          _p(np.ascontiguousarray(lists["gids"], np.uint32)),
+                          _p(np.ascontiguousarray(_cam_ranges(lists, 0), np.uint32)), _p(camera_array(cam)),
+                          _p(params_array(params)), x0, y0, x1, y1, _p(rgb), _p(T), _p(nc))
+    hh, ww = y1 - y0, x1 - x0
+    return dict(rgb=rgb.reshape(hh, ww, 3), T=T.reshape(hh, ww), ncontrib=nc.reshape(hh, ww), bins=b, lists=lists)

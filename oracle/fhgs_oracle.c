@@ -1536,3 +1536,45 @@ void orc_bin_surfel_f32(int64_t n, const float *means, const float *quats, const
         memcpy(dbits + g, &c[2], 4);
     }
 }
+
+/* Tiled surfel render of the region: each pixel walks its 16x16 tile's
+ * depth-sorted list (built from orc_bin_surfel_f32) with the rules of
+ * orc_render_2dgs_brute.  The surfel arrays are indexed by the lists' ids. */
+void orc_render_2dgs(const double *means, const double *quats, const double *scales2, const double *opac,
+                     const double *rgb, const uint32_t *gids, const uint32_t *ranges, const double *cam,
+                     const double *prm, int x0, int y0, int x1, int y1, double *out_rgb, double *out_T,
+                     int32_t *out_ncontrib)
+{
+    const int W = (int)cam[0], tsz = (int)prm[P_TILE];
+    const int tiles_x = (W + tsz - 1) / tsz;
+    const int rw = x1 - x0, rh = y1 - y0;
+    const double cut = prm[P_CUT], amin = prm[P_AMIN], amax = prm[P_AMAX], teps = prm[P_TEPS];
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+        const int ix = x0 + (int)(idx % rw), iy = y0 + (int)(idx / rw);
+        const double px = ix + 0.5, py = iy + 0.5;
+        const int t = (iy / tsz) * tiles_x + ix / tsz;
+        double T = 1.0, acc[3] = {0.0, 0.0, 0.0};
+        int nc = 0;
+        for (uint32_t k = ranges[2 * t]; k < ranges[2 * t + 1]; ++k) {
+            const uint32_t g = gids[k];
+            double u, v, lam;
+            if (!splat_uv(means + 3 * g, quats + 4 * g, scales2 + 2 * g, cam, px, py, &u, &v, &lam)) continue;
+            if (!(lam > 0.0)) continue;
+            const double r2 = u * u + v * v;
+            if (r2 > cut) continue;
+            const double rho = opac[g] * exp(-0.5 * r2);
+            const double alpha = rho > amax ? amax : rho;
+            if (alpha < amin) continue;
+            const double Tn = T * (1.0 - alpha);
+            if (Tn < teps) break;
+            const double w = alpha * T;
+            for (int ch = 0; ch < 3; ++ch) acc[ch] += w * rgb[3 * g + ch];
+            T = Tn;
+            ++nc;
+        }
+        for (int ch = 0; ch < 3; ++ch) out_rgb[3 * idx + ch] = acc[ch] + T * prm[P_BG0 + ch];
+        out_T[idx] = T;
+        out_ncontrib[idx] = nc;
+    }
+}

@@ -255,3 +255,20 @@ def test_surfel_binning_rule_is_conservative_and_close():
     e = 3 * 60 * 0.05 / 2 + (2 * 4.5) / 64 + 0.5   # half-width + pad
     assert list(f["pix"][0]) == [int(np.ceil(32 - e - 0.5)), int(np.ceil(24 - e - 0.5)),
                                  int(np.floor(32 + e - 0.5)), int(np.floor(24 + e - 0.5))]
+
+
+def test_tiled_surfel_render_equals_brute_force():
+    g = np.random.default_rng(14)
+    cam = axis_camera(W=70, H=52, fx=60.0, t=(0.02, -0.03, 0.0))
+    n = 150
+    q = g.normal(size=(n, 4))
+    surf = dict(means=g.normal(0, 0.4, (n, 3)) + [0, 0, 2.5], quats=q, scales2=np.exp(g.uniform(-3.2, -1.9, (n, 2))),
+                opacities=g.uniform(0.1, 0.95, n), rgb=g.uniform(0, 1, (n, 3)))
+    surf = {k: np.asarray(v, np.float32).astype(np.float64) for k, v in surf.items()}   # binary32 inputs
+    prm = dict(bg=(0.1, 0.3, 0.2))
+    tiled = oracle.render_2dgs(surf, cam, prm)
+    assert (tiled["bins"]["ntiles"] > 0).mean() > 0.9    # the rest lie off the image
+    brute = oracle.render_2dgs_brute(surf, cam, prm)
+    np.testing.assert_allclose(tiled["rgb"], brute["rgb"], atol=1e-12)
+    np.testing.assert_array_equal(tiled["ncontrib"], brute["ncontrib"])
+    assert (brute["ncontrib"] > 3).mean() > 0.2
