@@ -243,6 +243,41 @@ fhgs_status fhgs_point_features(fhgs_ctx *ctx, int64_t n, const float *means, co
                                 const float *const *maps, int D, const float *u, const fhgs_params *p, float *out,
                                 int32_t *view, int32_t *pixel, void *stream);
 
+/* ------------------------------------------------------ training step -- */
+/* The device side of one training iteration (App. A, Alg. 1 loop body,
+ * with L = L_rgb + l1 L_gt + l2 L_cf of Sec. 3.3; the gradients of the
+ * three terms come from fhgs_render_bwd and fhgs_ndfd_bwd and add).
+ *
+ * L1 photometric loss over m floats:  loss[0] += inv_count sum |a - b|
+ * (device float[1], accumulated: zero it first), grad[i] = inv_count
+ * sign(a[i] - b[i]) (0 where equal; grad nullable).  For the mean over P
+ * pixels of RGB, m = 3 P and inv_count = 1 / (3 P). */
+fhgs_status fhgs_l1_loss(fhgs_ctx *ctx, int64_t m, const float *a, const float *b, float inv_count, float *loss,
+                         float *grad, void *stream);
+
+/* Adam over the raw Gaussian parameters of the 3DGS family: means,
+ * log-scales, unnormalised quaternions, opacity logits and SH (all device
+ * float32, updated in place; the rasterizer reads means, quats and SH as
+ * they are, and scales = exp(log-scales), opacities = sigmoid(logits)).
+ * grad_* are the gradients with respect to the ACTIVATED values, as
+ * fhgs_render_bwd / fhgs_ndfd_bwd write them; the update takes them to the
+ * raw ones (d/dlog s = s d/ds, d/dlogit = op (1 - op) d/dop), then
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   theta -= lr m / (1 - b1^t) / (sqrt(v / (1 - b2^t)) + eps).
+ * state: fhgs_adam_state_floats(n, sh_degree) device floats, zeroed before
+ * step 1 (m and v of each group).  scales_out [n][3] and opacities_out [n]
+ * (nullable) receive the activated values of the updated parameters. */
+typedef struct fhgs_adam {
+    float lr[5];          /* means, log-scales, quaternions, opacity logits, SH */
+    float beta1, beta2, eps;
+    int32_t step;         /* t >= 1 of this update */
+} fhgs_adam;
+int64_t fhgs_adam_state_floats(int64_t n, int sh_degree);
+fhgs_status fhgs_adam_gaussians(fhgs_ctx *ctx, int64_t n, int sh_degree, float *means, float *log_scales, float *quats,
+                                float *logit_opacities, float *sh, const float *grad_means, const float *grad_scales,
+                                const float *grad_quats, const float *grad_opac, const float *grad_sh, float *state,
+                                const fhgs_adam *opt, float *scales_out, float *opacities_out, void *stream);
+
 /* ------------------------------------------------------------------ NDFD -- */
 /* Non-differentiable feature driving (Sec. 3.2; App. A "NDFD"): per pixel,
  * over the same depth-sorted tile lists, contributors and Eq. 4 weights

@@ -74,11 +74,19 @@ def loss_and_grads(raw: dict, sh_degree: int, cams: list, targets: list, feats, 
     b = [np.full(int(c["width"]) * int(c["height"]), lam2 / npx) for c in cams]
     g_nd = ndfd_backward(scene, cams, prm, feats, fgts, a, b, prep=prep)
     g_act = {k: g_rgb[k] + g_nd[k] for k in ("means", "scales", "quats", "opacities", "sh")}
-    op = scene["opacities"]
-    grads = dict(means=g_act["means"], log_scales=g_act["scales"] * scene["scales"], quats=g_act["quats"],
-                 logit_opacities=g_act["opacities"] * op * (1.0 - op), sh=g_act["sh"])
+    grads = raw_grads(raw, g_act)
     total = L_rgb + lam1 * L_gt + lam2 * L_cf
     return total, dict(rgb=L_rgb, gt=L_gt, cf=L_cf), grads
+
+
+def raw_grads(raw: dict, g_act: dict) -> dict:
+    """Gradients with respect to the activated values (means, scales, quats,
+    opacities, sh) taken to the raw parameters: d/dlog s = s d/ds,
+    d/dlogit = op (1 - op) d/dop."""
+    s = np.exp(raw["log_scales"])
+    op = 1.0 / (1.0 + np.exp(-raw["logit_opacities"]))
+    return dict(means=g_act["means"], log_scales=g_act["scales"] * s, quats=g_act["quats"],
+                logit_opacities=g_act["opacities"] * op * (1.0 - op), sh=g_act["sh"])
 
 
 def adam_init(raw: dict) -> dict:

@@ -27,7 +27,8 @@ EXPORTS = ["fhgs_create", "fhgs_destroy", "fhgs_last_error", "fhgs_status_string
            "fhgs_default_params", "fhgs_proj_bytes", "fhgs_total_tiles", "fhgs_reserve", "fhgs_sync_status",
            "fhgs_project", "fhgs_bin_sort", "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features",
            "fhgs_profile_enable", "fhgs_profile_read", "fhgs_launch_count", "fhgs_render_bwd_noalloc",
-           "fhgs_ndfd_fwd", "fhgs_ndfd_bwd", "fhgs_point_features"]
+           "fhgs_ndfd_fwd", "fhgs_ndfd_bwd", "fhgs_point_features", "fhgs_l1_loss", "fhgs_adam_state_floats",
+           "fhgs_adam_gaussians"]
 MAX_POINT_VIEWS = 4096  # FHGS_MAX_POINT_VIEWS of include/fhgs.h
 NDFD_K, NDFD_LAMBDA = 20.0, 0.5  # the activation's slope and threshold (Sec. 4)
 
@@ -44,6 +45,11 @@ class Params(ctypes.Structure):
                 ("znear", ctypes.c_float), ("dilation", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("t_eps", ctypes.c_float), ("cutoff_sq", ctypes.c_float),
                 ("fov_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3)]
+
+
+class Adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 5), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
 
 
 class Gaussians(ctypes.Structure):
@@ -116,13 +122,17 @@ def lib():
                                     f32p, f32p, f32p, f32p, f32p, vp]
         L.fhgs_point_features.argtypes = [vp, i64, f32p, ctypes.POINTER(Camera), i32, ctypes.POINTER(ctypes.c_void_p),
                                           i32, f32p, ctypes.POINTER(Params), f32p, vp, vp, vp]
+        L.fhgs_l1_loss.argtypes = [vp, i64, f32p, f32p, f32, f32p, f32p, vp]
+        L.fhgs_adam_state_floats.argtypes = [i64, i32]
+        L.fhgs_adam_state_floats.restype = i64
+        L.fhgs_adam_gaussians.argtypes = [vp, i64, i32] + [f32p] * 11 + [ctypes.POINTER(Adam), f32p, f32p, vp]
         L.fhgs_profile_enable.argtypes = [vp, i32]
         L.fhgs_profile_read.argtypes = [vp, ctypes.c_char_p, i64]
         L.fhgs_launch_count.argtypes = []
         L.fhgs_launch_count.restype = i64
         for name in ("fhgs_create", "fhgs_reserve", "fhgs_sync_status", "fhgs_project", "fhgs_bin_sort",
                      "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features", "fhgs_ndfd_fwd", "fhgs_ndfd_bwd",
-                     "fhgs_point_features", "fhgs_profile_enable",
+                     "fhgs_point_features", "fhgs_l1_loss", "fhgs_adam_gaussians", "fhgs_profile_enable",
                      "fhgs_profile_read"):
             getattr(L, name).restype = i32
         _lib = L
@@ -281,6 +291,42 @@ def point_features(ctx: "Context", means, views: Sequence[dict], maps: Sequence[
                                         _ptr(u.contiguous()), ctypes.byref(params), _ptr(out), _ptr(view),
                                         _ptr(pixel), Context.stream_ptr(stream)))
     return out, view, pixel
+
+
+def l1_loss(ctx: "Context", a, b, loss=None, want_grad: bool = True, stream=None):
+    """fhgs_l1_loss over all elements of a and b: returns (loss [1], grad)
+    with loss = mean |a - b| (accumulated into `loss` when given)."""
+    m = int(a.numel())
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=a.device)
+    grad = torch.empty_like(a) if want_grad else None
+    ctx.check(lib().fhgs_l1_loss(ctx.h, m, _ptr(a.contiguous()), _ptr(b.contiguous()), 1.0 / max(m, 1), _ptr(loss),
+                                 _ptr(grad), Context.stream_ptr(stream)))
+    return loss, grad
+
+
+def adam_gaussians(ctx: "Context", raw: dict, grads: dict, state, step: int, lr, sh_degree: int,
+                   beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15, scales_out=None, opac_out=None,
+                   stream=None):
+    """fhgs_adam_gaussians: one Adam update of raw = {means, log_scales,
+    quats, logit_opacities, sh} (in place) from the activated-parameter
+    gradients {means, scales, quats, opacities, sh}.  lr: five rates."""
+    opt = Adam()
+    for k in range(5):
+        opt.lr[k] = float(lr[k])
+    opt.beta1, opt.beta2, opt.eps, opt.step = beta1, beta2, eps, int(step)
+    n = int(raw["means"].shape[0])
+    ctx.check(lib().fhgs_adam_gaussians(
+        ctx.h, n, int(sh_degree), _ptr(raw["means"]), _ptr(raw["log_scales"]), _ptr(raw["quats"]),
+        _ptr(raw["logit_opacities"]), _ptr(raw["sh"]), _ptr(grads["means"]), _ptr(grads["scales"]),
+        _ptr(grads["quats"]), _ptr(grads["opacities"]), _ptr(grads["sh"]), _ptr(state), ctypes.byref(opt),
+        _ptr(scales_out), _ptr(opac_out), Context.stream_ptr(stream)))
+
+
+def adam_state(n: int, sh_degree: int, device) -> torch.Tensor:
+    """A zeroed Adam state for n Gaussians (fhgs_adam_state_floats floats)."""
+    return torch.zeros(int(lib().fhgs_adam_state_floats(int(n), int(sh_degree))), dtype=torch.float32,
+                       device=device)
 
 
 def render_bwd_noalloc(g, proj, bins, features, D, cams, params, T, last, grgb, gfeat, out: dict, stream=None) -> int:

@@ -522,6 +522,54 @@ fhgs_status fhgs_point_features(fhgs_ctx *ctx, int64_t n, const float *means, co
     return FHGS_OK;
 }
 
+fhgs_status fhgs_l1_loss(fhgs_ctx *ctx, int64_t m, const float *a, const float *b, float inv_count, float *loss,
+                         float *grad, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    if (m < 0) return fail(ctx, FHGS_ERR_INVALID_ARG, "negative size");
+    if (!loss || (m > 0 && (!a || !b))) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL buffer");
+    if (!std::isfinite(inv_count)) return fail(ctx, FHGS_ERR_INVALID_ARG, "inv_count must be finite");
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        Prof pr(ctx, "l1_loss", st);
+        launch_l1_loss(m, a, b, inv_count, loss, grad, ctx->sm_count, st);
+    }
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
+int64_t fhgs_adam_state_floats(int64_t n, int sh_degree) {
+    if (n < 0 || sh_degree < 0 || sh_degree > 3) return -1;
+    const int64_t K = (int64_t)(sh_degree + 1) * (sh_degree + 1);
+    return 2 * n * (11 + 3 * K);
+}
+
+fhgs_status fhgs_adam_gaussians(fhgs_ctx *ctx, int64_t n, int sh_degree, float *means, float *log_scales, float *quats,
+                                float *logit_opacities, float *sh, const float *grad_means, const float *grad_scales,
+                                const float *grad_quats, const float *grad_opac, const float *grad_sh, float *state,
+                                const fhgs_adam *opt, float *scales_out, float *opacities_out, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    if (n < 0 || n >= (1ll << 31)) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad Gaussian count");
+    if (sh_degree < 0 || sh_degree > 3) return fail(ctx, FHGS_ERR_UNSUPPORTED, "sh_degree must be 0..3");
+    if (!opt) return fail(ctx, FHGS_ERR_INVALID_ARG, "opt is NULL");
+    if (opt->step < 1) return fail(ctx, FHGS_ERR_INVALID_ARG, "the Adam step number starts at 1");
+    if (!(opt->beta1 >= 0.f && opt->beta1 < 1.f && opt->beta2 >= 0.f && opt->beta2 < 1.f && opt->eps >= 0.f))
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "bad Adam constants");
+    if (n > 0 && (!means || !log_scales || !quats || !logit_opacities || !sh || !grad_means || !grad_scales ||
+                  !grad_quats || !grad_opac || !grad_sh || !state))
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL buffer");
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        Prof pr(ctx, "adam", st);
+        launch_adam_gaussians(n, (sh_degree + 1) * (sh_degree + 1), means, log_scales, quats, logit_opacities, sh,
+                              grad_means, grad_scales, grad_quats, grad_opac, grad_sh, state, opt, scales_out,
+                              opacities_out, st);
+    }
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
 // Shared argument checks of the two NDFD calls.
 static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, const fhgs_bins *bins,
                               const void *features, const void *feat_gt, fhgs_dtype ftype, int D,

@@ -1,0 +1,119 @@
+// The device side of one training iteration (App. A, Alg. 1 loop body):
+// the L1 photometric loss with its gradient, and an Adam update of the raw
+// Gaussian parameters.
+//
+// Raw parameters follow the 3DGS family: means, log-scales, unnormalised
+// quaternions, opacity logits and SH.  The rasterizer's backward gives the
+// gradient with respect to the activated values (scales = exp(log-scales),
+// opacities = sigmoid(logits)), so the update first takes them to the raw
+// ones (d/dlog s = s d/ds, d/dlogit = op (1 - op) d/dop), then applies Adam
+// (m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, theta -= lr m_hat /
+// (sqrt(v_hat) + eps)) and writes the activated scales and opacities that
+// the next forward reads.  One thread owns one Gaussian.
+#include "fhgs_internal.cuh"
+
+namespace fhgs {
+namespace {
+
+__global__ void __launch_bounds__(256) k_l1_loss(long long m, const float *__restrict__ a, const float *__restrict__ b,
+                                                 float inv_count, float *loss, float *grad) {
+    float s = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        const float d = a[i] - b[i];
+        s += fabsf(d);
+        if (grad) grad[i] = d > 0.f ? inv_count : (d < 0.f ? -inv_count : 0.f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ float part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(loss, t * inv_count);
+    }
+}
+
+struct AdamArgs {
+    float lr[5];
+    float b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+};
+
+__device__ __forceinline__ float adam_one(float theta, float g, float &m, float &v, float lr, const AdamArgs &a) {
+    m = a.b1 * m + (1.f - a.b1) * g;
+    v = a.b2 * v + (1.f - a.b2) * g * g;
+    return theta - lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+}
+
+__global__ void __launch_bounds__(256) k_adam_gaussians(long long n, int K3, float *means, float *log_s, float *quats,
+                                                        float *logit, float *sh, const float *__restrict__ g_means,
+                                                        const float *__restrict__ g_scales,
+                                                        const float *__restrict__ g_quats,
+                                                        const float *__restrict__ g_opac,
+                                                        const float *__restrict__ g_sh, float *state, AdamArgs a,
+                                                        float *scales_out, float *opac_out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // state: m and v of each group, group after group, n rows each
+    float *m_mu = state, *v_mu = m_mu + 3 * n;
+    float *m_ls = v_mu + 3 * n, *v_ls = m_ls + 3 * n;
+    float *m_q = v_ls + 3 * n, *v_q = m_q + 4 * n;
+    float *m_lo = v_q + 4 * n, *v_lo = m_lo + n;
+    float *m_sh = v_lo + n, *v_sh = m_sh + K3 * n;
+    for (int k = 0; k < 3; ++k) {
+        const long long j = 3 * i + k;
+        means[j] = adam_one(means[j], g_means[j], m_mu[j], v_mu[j], a.lr[0], a);
+    }
+    for (int k = 0; k < 3; ++k) {
+        const long long j = 3 * i + k;
+        const float g = g_scales[j] * expf(log_s[j]);
+        log_s[j] = adam_one(log_s[j], g, m_ls[j], v_ls[j], a.lr[1], a);
+        if (scales_out) scales_out[j] = expf(log_s[j]);
+    }
+    for (int k = 0; k < 4; ++k) {
+        const long long j = 4 * i + k;
+        quats[j] = adam_one(quats[j], g_quats[j], m_q[j], v_q[j], a.lr[2], a);
+    }
+    {
+        const float op = 1.f / (1.f + expf(-logit[i]));
+        const float g = g_opac[i] * op * (1.f - op);
+        logit[i] = adam_one(logit[i], g, m_lo[i], v_lo[i], a.lr[3], a);
+        if (opac_out) opac_out[i] = 1.f / (1.f + expf(-logit[i]));
+    }
+    for (int k = 0; k < K3; ++k) {
+        const long long j = (long long)K3 * i + k;
+        sh[j] = adam_one(sh[j], g_sh[j], m_sh[j], v_sh[j], a.lr[4], a);
+    }
+}
+
+}  // namespace
+
+void launch_l1_loss(long long m, const float *a, const float *b, float inv_count, float *loss, float *grad,
+                    int sm_count, cudaStream_t st) {
+    if (m == 0) return;
+    note_launch(1);
+    const long long want = (m + 255) / 256;
+    const unsigned blocks = (unsigned)min(want, (long long)sm_count * 8);
+    k_l1_loss<<<blocks, 256, 0, st>>>(m, a, b, inv_count, loss, grad);
+}
+
+void launch_adam_gaussians(long long n, int K, float *means, float *log_s, float *quats, float *logit, float *sh,
+                           const float *g_means, const float *g_scales, const float *g_quats, const float *g_opac,
+                           const float *g_sh, float *state, const fhgs_adam *opt, float *scales_out, float *opac_out,
+                           cudaStream_t st) {
+    if (n == 0) return;
+    AdamArgs a;
+    for (int k = 0; k < 5; ++k) a.lr[k] = opt->lr[k];
+    a.b1 = opt->beta1;
+    a.b2 = opt->beta2;
+    a.eps = opt->eps;
+    a.c1 = 1.f - powf(opt->beta1, (float)opt->step);
+    a.c2 = 1.f - powf(opt->beta2, (float)opt->step);
+    note_launch(1);
+    k_adam_gaussians<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, 3 * K, means, log_s, quats, logit, sh, g_means,
+                                                                  g_scales, g_quats, g_opac, g_sh, state, a,
+                                                                  scales_out, opac_out);
+}
+
+}  // namespace fhgs
