@@ -48,3 +48,34 @@ def test_smooth_feature_map_is_normalised_and_smooth():
     near = np.mean(np.sum(m[:, 1:] * m[:, :-1], axis=-1))
     far = np.mean(np.abs(np.sum(m[:, 40:] * m[:, :-40], axis=-1)))
     assert near > 0.95 and far < 0.5
+
+
+def test_ndfd_recipes_follow_their_description():
+    """Unit features clustered around unit prototypes (cosine to the own
+    prototype from about 0.98 down to about 0.3), a ground-truth map of
+    constant-label blocks, and the device recipe (run here on the CPU) with
+    the same structure."""
+    import torch
+    D = 256
+    P = synth.ndfd_prototypes(3, D)
+    np.testing.assert_allclose(np.linalg.norm(P, axis=1), 1.0, rtol=1e-6)
+    f = synth.ndfd_features(3, 5000, P)
+    np.testing.assert_allclose(np.linalg.norm(f, axis=1), 1.0, rtol=1e-5)
+    own = (f @ P.T).max(1)
+    q01, q50, q99 = np.quantile(own, [0.01, 0.5, 0.99])   # cos = 1/sqrt(1 + l^2), l ~ U[0.2, 3]
+    assert 0.2 < q01 < 0.4 and 0.4 < q50 < 0.65 and 0.95 < q99 < 0.995
+    gt = synth.ndfd_ground_truth(3, 0, 48, 72, P, block=24)
+    np.testing.assert_allclose(np.linalg.norm(gt, axis=-1), 1.0, rtol=1e-5)
+    lab = (gt @ P.T).argmax(-1)
+    for by in range(2):
+        for bx in range(3):
+            blk = lab[24 * by:24 * by + 24, 24 * bx:24 * bx + 24]
+            assert (blk == blk[0, 0]).all()
+    cams = [dict(width=72, height=48)]
+    df, dg = synth.ndfd_inputs_device(3, 4000, cams, D, torch.device("cpu"))
+    assert df.dtype == torch.bfloat16 and dg.shape == (72 * 48, D)
+    dfn = df.float().norm(dim=1)
+    assert (dfn - 1).abs().max() < 1e-2
+    dgl = dg.float().reshape(48, 72, D)
+    sim = torch.einsum("hwd,hvd->hwv", dgl[:24, :24], dgl[:24, :24])   # pixels of one block share a prototype
+    assert sim.mean() > 0.7
