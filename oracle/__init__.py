@@ -620,3 +620,38 @@ def render_2dgs(surfels: dict, cam: dict, params: dict | None = None, region=Non
                           _p(params_array(params)), x0, y0, x1, y1, _p(rgb), _p(T), _p(nc))
     hh, ww = y1 - y0, x1 - x0
     return dict(rgb=rgb.reshape(hh, ww, 3), T=T.reshape(hh, ww), ncontrib=nc.reshape(hh, ww), bins=b, lists=lists)
+
+
+def splat_uv_T(means, quats, scales2, cam: dict, px, py) -> dict:
+    """u(x), v(x) and the camera depth through the surfel's projective map
+    T = K [a b c] and the two planes T_0 - x T_2, T_1 - y T_2."""
+    mu = _f64(means).reshape(-1, 3)
+    m = mu.shape[0]
+    u, v, dep = np.zeros(m), np.zeros(m), np.zeros(m)
+    lib().orc_splat_uv_T(ctypes.c_int64(m), _p(mu), _p(_f64(quats).reshape(m, 4)), _p(_f64(scales2).reshape(m, 2)),
+                         _p(camera_array(cam)), _p(_f64(px).reshape(m)), _p(_f64(py).reshape(m)), _p(u), _p(v),
+                         _p(dep))
+    return dict(u=u, v=v, depth=dep)
+
+
+def render_2dgs_bwd(surfels: dict, cam: dict, params: dict | None, dC, region=None) -> dict:
+    """Gradients of sum_p dC[p] . rgb[p] of the tiled surfel render
+    (render_2dgs) with respect to means, quats, scales2, opacities and rgb."""
+    W, H = int(cam["width"]), int(cam["height"])
+    x0, y0, x1, y1 = region if region is not None else (0, 0, W, H)
+    mu = _f64(surfels["means"]).reshape(-1, 3)
+    n = mu.shape[0]
+    b = bin_surfel_f32(np.asarray(surfels["means"], np.float32), np.asarray(surfels["quats"], np.float32),
+                       np.asarray(surfels["scales2"], np.float32), cam, params)
+    lists = tile_lists([b], [cam], params)
+    out = dict(means=np.zeros((n, 3)), quats=np.zeros((n, 4)), scales2=np.zeros((n, 2)), opacities=np.zeros(n),
+               rgb=np.zeros((n, 3)))
+    lib().orc_render_2dgs_bwd(ctypes.c_int64(n), _p(mu), _p(_f64(surfels["quats"]).reshape(n, 4)),
+                              _p(_f64(surfels["scales2"]).reshape(n, 2)), _p(_f64(surfels["opacities"]).reshape(n)),
+                              _p(_f64(surfels["rgb"]).reshape(n, 3)),
+                              _p(np.ascontiguousarray(lists["gids"], np.uint32)),
+                              _p(np.ascontiguousarray(_cam_ranges(lists, 0), np.uint32)), _p(camera_array(cam)),
+                              _p(params_array(params)), x0, y0, x1, y1, _p(_f64(dC).reshape(-1, 3)),
+                              _p(out["means"]), _p(out["quats"]), _p(out["scales2"]), _p(out["opacities"]),
+                              _p(out["rgb"]))
+    return out

@@ -31,7 +31,9 @@
  *     per pixel over all surfels and its derivative (App. A.2 with the
  *     ray-plane solve differentiated implicitly), and the exact screen box of
  *     a surfel's footprint (dual conic); orc_bin_surfel_f32: its binary32
- *     binning rule (a padded box, integer decisions reproducible bit for bit).
+ *     binning rule (a padded box, integer decisions reproducible bit for bit);
+ *     orc_render_2dgs / orc_render_2dgs_bwd: the tiled render and backward;
+ *     orc_splat_uv_T: u(x) through the projective map T = K [a b c].
  *   - orc_point_views_f32: the paper's point-to-feature assignment
  *     (Sec. 3.1, App. A "PointsFeatureFusion"): a random visible view, the
  *     nearest pixel; binary32 projection spec (it decides integers).
@@ -1307,16 +1309,133 @@ void orc_surfel_rect(int64_t n, const double *means, const double *quats, const 
     }
 }
 
-/* Gradient of L = sum_p dC[p] . rgb[p] of the brute-force surfel render
- * (orc_render_2dgs_brute) with respect to each surfel's mean, quaternion,
- * (s_u, s_v), opacity and colour; accumulates (+=).  dL/dalpha by the App.
- * A.2 identity with the background term, as in orc_render_bwd; then
- * alpha = op G(u, v) (the clamp passes nothing), dG/du = -u G, dG/dv = -v G,
- * and (lambda, u, v) = M^-1 c with M = [d, -a, -b] differentiated
- * implicitly: d(lambda, u, v) = M^-1 (dc + u da + v db), so with
- * w = M^-T (0, dL/du, dL/dv):  dL/dp = R_w^T w,
- * dL/dR[:,0] = s_u u R_w^T w, dL/dR[:,1] = s_v v R_w^T w,
- * dL/ds_u = u w . (R_w R[:,0]), dL/ds_v = v w . (R_w R[:,1]). */
+/* Gradient of L = sum_p dC[p] . rgb[p] of the surfel render with respect to
+ * each surfel's mean, quaternion, (s_u, s_v), opacity and colour;
+ * accumulates (+=).  dL/dalpha by the App. A.2 identity with the background
+ * term, as in orc_render_bwd; then alpha = op G(u, v) (the clamp passes
+ * nothing), dG/du = -u G, dG/dv = -v G, and (lambda, u, v) = M^-1 c with
+ * M = [d, -a, -b] differentiated implicitly: d(lambda, u, v) =
+ * M^-1 (dc + u da + v db), so with w = M^-T (0, dL/du, dL/dv):
+ * dL/dp = R_w^T w, dL/dR[:,0] = s_u u R_w^T w, dL/dR[:,1] = s_v v R_w^T w,
+ * dL/ds_u = u w . (R_w R[:,0]), dL/ds_v = v w . (R_w R[:,1]).
+ * One pixel (centre px, py) over one depth-ordered list; cg, ca: scratch of
+ * len and 5 len entries. */
+static void surfel_pixel_bwd(double px, double py, const uint32_t *list, int64_t len, const double *means,
+                             const double *quats, const double *scales2, const double *opac, const double *rgb,
+                             const double *cam, const double *prm, const double *dc, uint32_t *cg, double *ca,
+                             double *g_means, double *g_quats, double *g_scales2, double *g_opac, double *g_rgb)
+{
+    const double cut = prm[P_CUT], amin = prm[P_AMIN], amax = prm[P_AMAX], teps = prm[P_TEPS];
+    double T = 1.0;
+    int nc = 0;
+    for (int64_t k = 0; k < len; ++k) {
+        const uint32_t g = list[k];
+        double u, v, lam;
+        if (!splat_uv(means + 3 * g, quats + 4 * g, scales2 + 2 * g, cam, px, py, &u, &v, &lam)) continue;
+        if (!(lam > 0.0)) continue;
+        const double r2 = u * u + v * v;
+        if (r2 > cut) continue;
+        const double G = exp(-0.5 * r2);
+        const double rho = opac[g] * G;
+        const double alpha = rho > amax ? amax : rho;
+        if (alpha < amin) continue;
+        const double Tn = T * (1.0 - alpha);
+        if (Tn < teps) break;
+        cg[nc] = g;
+        ca[5 * nc + 0] = alpha;
+        ca[5 * nc + 1] = T;
+        ca[5 * nc + 2] = G;
+        ca[5 * nc + 3] = u;
+        ca[5 * nc + 4] = v;
+        ++nc;
+        T = Tn;
+    }
+    double S = T * (dc[0] * prm[P_BG0] + dc[1] * prm[P_BG1] + dc[2] * prm[P_BG2]);
+    for (int j = nc - 1; j >= 0; --j) {
+        const uint32_t g = cg[j];
+        const double alpha = ca[5 * j], Tj = ca[5 * j + 1], G = ca[5 * j + 2], u = ca[5 * j + 3], v = ca[5 * j + 4];
+        const double w = alpha * Tj;
+        const double gw = dc[0] * rgb[3 * g] + dc[1] * rgb[3 * g + 1] + dc[2] * rgb[3 * g + 2];
+        const double dalpha = Tj * gw - S / (1.0 - alpha);
+        S += w * gw;
+        for (int ch = 0; ch < 3; ++ch) {
+#pragma omp atomic
+            g_rgb[3 * g + ch] += w * dc[ch];
+        }
+        const double rho = opac[g] * G;
+        const double drho = rho > amax ? 0.0 : dalpha;
+#pragma omp atomic
+        g_opac[g] += G * drho;
+        const double dG = opac[g] * drho;
+        const double e[3] = {0.0, -u * G * dG, -v * G * dG};
+        /* the surfel's frame in the camera */
+        const double *q = quats + 4 * g;
+        const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
+        double R[3][3];
+        quat_to_rot(qn, R);
+        const double su = scales2[2 * g], sv = scales2[2 * g + 1];
+        double ru[3], rv[3];   /* R_w R[:,0], R_w R[:,1] */
+        for (int r = 0; r < 3; ++r) {
+            ru[r] = 0.0;
+            rv[r] = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                ru[r] += cam_R(cam, r, k) * R[k][0];
+                rv[r] += cam_R(cam, r, k) * R[k][1];
+            }
+        }
+        const double d[3] = {(px - cam[4]) / cam[2], (py - cam[5]) / cam[3], 1.0};
+        double M[3][3];
+        for (int r = 0; r < 3; ++r) {
+            M[r][0] = d[r];
+            M[r][1] = -su * ru[r];
+            M[r][2] = -sv * rv[r];
+        }
+        /* w3 = M^-T e: solve M^T w3 = e by Cramer's rule on A = M^T */
+        double A[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k) A[r][k] = M[k][r];
+        const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                           A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+        double w3[3];
+        for (int col = 0; col < 3; ++col) {
+            double B[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int k = 0; k < 3; ++k) B[r][k] = k == col ? e[r] : A[r][k];
+            w3[col] = (B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1]) -
+                       B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0]) +
+                       B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0])) / det;
+        }
+        double rt[3];   /* R_w^T w3 */
+        for (int k = 0; k < 3; ++k) rt[k] = cam_R(cam, 0, k) * w3[0] + cam_R(cam, 1, k) * w3[1] + cam_R(cam, 2, k) * w3[2];
+        for (int k = 0; k < 3; ++k) {
+#pragma omp atomic
+            g_means[3 * g + k] += rt[k];
+        }
+        const double gsu = u * (w3[0] * ru[0] + w3[1] * ru[1] + w3[2] * ru[2]);
+        const double gsv = v * (w3[0] * rv[0] + w3[1] * rv[1] + w3[2] * rv[2]);
+#pragma omp atomic
+        g_scales2[2 * g] += gsu;
+#pragma omp atomic
+        g_scales2[2 * g + 1] += gsv;
+        double GR[3][3];
+        for (int k = 0; k < 3; ++k) {
+            GR[k][0] = su * u * rt[k];
+            GR[k][1] = sv * v * rt[k];
+            GR[k][2] = 0.0;
+        }
+        double gq[4] = {0.0, 0.0, 0.0, 0.0};
+        quat_grad(qn, nq, GR, gq);
+        for (int k = 0; k < 4; ++k) {
+#pragma omp atomic
+            g_quats[4 * g + k] += gq[k];
+        }
+    }
+}
+
+/* The backward of orc_render_2dgs_brute (every surfel with its centre
+ * beyond znear, ordered by (depth_key, index), for every pixel). */
 void orc_render_2dgs_bwd_brute(int64_t n, const double *means, const double *quats, const double *scales2,
                                const double *opac, const double *rgb, const double *depth_key, const double *cam,
                                const double *prm, int x0, int y0, int x1, int y1, const double *dC, double *g_means,
@@ -1334,127 +1453,48 @@ void orc_render_2dgs_bwd_brute(int64_t n, const double *means, const double *qua
         }
     }
     qsort(order, (size_t)m, sizeof(kd_pair), kd_cmp);
+    uint32_t *list = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1));
+    for (int64_t k = 0; k < m; ++k) list[k] = order[k].g;
+    free(order);
     const int rw = x1 - x0, rh = y1 - y0;
-    const double cut = prm[P_CUT], amin = prm[P_AMIN], amax = prm[P_AMAX], teps = prm[P_TEPS];
 #pragma omp parallel
     {
         uint32_t *cg = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1));
         double *ca = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * 5);
 #pragma omp for schedule(dynamic, 16)
+        for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx)
+            surfel_pixel_bwd(x0 + (int)(idx % rw) + 0.5, y0 + (int)(idx / rw) + 0.5, list, m, means, quats, scales2,
+                             opac, rgb, cam, prm, dC + 3 * idx, cg, ca, g_means, g_quats, g_scales2, g_opac, g_rgb);
+        free(cg); free(ca);
+    }
+    free(list);
+}
+
+/* The backward of orc_render_2dgs (tiled lists). */
+void orc_render_2dgs_bwd(int64_t n, const double *means, const double *quats, const double *scales2,
+                         const double *opac, const double *rgb, const uint32_t *gids, const uint32_t *ranges,
+                         const double *cam, const double *prm, int x0, int y0, int x1, int y1, const double *dC,
+                         double *g_means, double *g_quats, double *g_scales2, double *g_opac, double *g_rgb)
+{
+    const int W = (int)cam[0], tsz = (int)prm[P_TILE];
+    const int tiles_x = (W + tsz - 1) / tsz;
+    const int rw = x1 - x0, rh = y1 - y0;
+    (void)n;
+#pragma omp parallel
+    {
+        uint32_t *cg = (uint32_t *)malloc(sizeof(uint32_t) * ORC_MAXC);
+        double *ca = (double *)malloc(sizeof(double) * ORC_MAXC * 5);
+#pragma omp for schedule(dynamic, 16)
         for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
-            const double px = x0 + (int)(idx % rw) + 0.5, py = y0 + (int)(idx / rw) + 0.5;
-            double T = 1.0;
-            int nc = 0;
-            for (int64_t k = 0; k < m; ++k) {
-                const uint32_t g = order[k].g;
-                double u, v, lam;
-                if (!splat_uv(means + 3 * g, quats + 4 * g, scales2 + 2 * g, cam, px, py, &u, &v, &lam)) continue;
-                if (!(lam > 0.0)) continue;
-                const double r2 = u * u + v * v;
-                if (r2 > cut) continue;
-                const double G = exp(-0.5 * r2);
-                const double rho = opac[g] * G;
-                const double alpha = rho > amax ? amax : rho;
-                if (alpha < amin) continue;
-                const double Tn = T * (1.0 - alpha);
-                if (Tn < teps) break;
-                cg[nc] = g;
-                ca[5 * nc + 0] = alpha;
-                ca[5 * nc + 1] = T;
-                ca[5 * nc + 2] = G;
-                ca[5 * nc + 3] = u;
-                ca[5 * nc + 4] = v;
-                ++nc;
-                T = Tn;
-            }
-            const double *dc = dC + 3 * idx;
-            double S = T * (dc[0] * prm[P_BG0] + dc[1] * prm[P_BG1] + dc[2] * prm[P_BG2]);
-            for (int j = nc - 1; j >= 0; --j) {
-                const uint32_t g = cg[j];
-                const double alpha = ca[5 * j], Tj = ca[5 * j + 1], G = ca[5 * j + 2], u = ca[5 * j + 3],
-                             v = ca[5 * j + 4];
-                const double w = alpha * Tj;
-                const double gw = dc[0] * rgb[3 * g] + dc[1] * rgb[3 * g + 1] + dc[2] * rgb[3 * g + 2];
-                const double dalpha = Tj * gw - S / (1.0 - alpha);
-                S += w * gw;
-                for (int ch = 0; ch < 3; ++ch) {
-#pragma omp atomic
-                    g_rgb[3 * g + ch] += w * dc[ch];
-                }
-                const double rho = opac[g] * G;
-                const double drho = rho > amax ? 0.0 : dalpha;
-#pragma omp atomic
-                g_opac[g] += G * drho;
-                const double dG = opac[g] * drho;
-                const double e[3] = {0.0, -u * G * dG, -v * G * dG};
-                /* the surfel's frame in the camera */
-                const double *q = quats + 4 * g;
-                const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-                const double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
-                double R[3][3];
-                quat_to_rot(qn, R);
-                const double su = scales2[2 * g], sv = scales2[2 * g + 1];
-                double ru[3], rv[3];   /* R_w R[:,0], R_w R[:,1] */
-                for (int r = 0; r < 3; ++r) {
-                    ru[r] = 0.0;
-                    rv[r] = 0.0;
-                    for (int k = 0; k < 3; ++k) {
-                        ru[r] += cam_R(cam, r, k) * R[k][0];
-                        rv[r] += cam_R(cam, r, k) * R[k][1];
-                    }
-                }
-                const double d[3] = {(px - cam[4]) / cam[2], (py - cam[5]) / cam[3], 1.0};
-                double M[3][3];
-                for (int r = 0; r < 3; ++r) {
-                    M[r][0] = d[r];
-                    M[r][1] = -su * ru[r];
-                    M[r][2] = -sv * rv[r];
-                }
-                /* w3 = M^-T e: solve M^T w3 = e by Cramer's rule on A = M^T */
-                double A[3][3];
-                for (int r = 0; r < 3; ++r)
-                    for (int k = 0; k < 3; ++k) A[r][k] = M[k][r];
-                const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
-                                   A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-                                   A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
-                double w3[3];
-                for (int col = 0; col < 3; ++col) {
-                    double B[3][3];
-                    for (int r = 0; r < 3; ++r)
-                        for (int k = 0; k < 3; ++k) B[r][k] = k == col ? e[r] : A[r][k];
-                    w3[col] = (B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1]) -
-                               B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0]) +
-                               B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0])) / det;
-                }
-                double rt[3];   /* R_w^T w3 */
-                for (int k = 0; k < 3; ++k) rt[k] = cam_R(cam, 0, k) * w3[0] + cam_R(cam, 1, k) * w3[1] + cam_R(cam, 2, k) * w3[2];
-                for (int k = 0; k < 3; ++k) {
-#pragma omp atomic
-                    g_means[3 * g + k] += rt[k];
-                }
-                const double gsu = u * (w3[0] * ru[0] + w3[1] * ru[1] + w3[2] * ru[2]);
-                const double gsv = v * (w3[0] * rv[0] + w3[1] * rv[1] + w3[2] * rv[2]);
-#pragma omp atomic
-                g_scales2[2 * g] += gsu;
-#pragma omp atomic
-                g_scales2[2 * g + 1] += gsv;
-                double GR[3][3];
-                for (int k = 0; k < 3; ++k) {
-                    GR[k][0] = su * u * rt[k];
-                    GR[k][1] = sv * v * rt[k];
-                    GR[k][2] = 0.0;
-                }
-                double gq[4] = {0.0, 0.0, 0.0, 0.0};
-                quat_grad(qn, nq, GR, gq);
-                for (int k = 0; k < 4; ++k) {
-#pragma omp atomic
-                    g_quats[4 * g + k] += gq[k];
-                }
-            }
+            const int ix = x0 + (int)(idx % rw), iy = y0 + (int)(idx / rw);
+            const int t = (iy / tsz) * tiles_x + ix / tsz;
+            const uint32_t s0 = ranges[2 * t], e0 = ranges[2 * t + 1];
+            const int64_t len = (int64_t)e0 - s0 < ORC_MAXC ? (int64_t)e0 - s0 : ORC_MAXC;
+            surfel_pixel_bwd(ix + 0.5, iy + 0.5, gids + s0, len, means, quats, scales2, opac, rgb, cam, prm,
+                             dC + 3 * idx, cg, ca, g_means, g_quats, g_scales2, g_opac, g_rgb);
         }
         free(cg); free(ca);
     }
-    free(order);
 }
 
 /* Binary32 binning rule for surfels (it decides integers, so it is specified
@@ -1576,5 +1616,50 @@ void orc_render_2dgs(const double *means, const double *quats, const double *sca
         for (int ch = 0; ch < 3; ++ch) out_rgb[3 * idx + ch] = acc[ch] + T * prm[P_BG0 + ch];
         out_T[idx] = T;
         out_ncontrib[idx] = nc;
+    }
+}
+
+/* u(x) through the surfel's projective map instead of the ray solve: with
+ * T = K [a b c] (a, b, c as in splat_uv) a plane point (u, v) lands on the
+ * homogeneous pixel T (u, v, 1)^T, so the pixel (x, y) holds the point where
+ * the two planes h_u = T_0 - x T_2 and h_v = T_1 - y T_2 (rows of T) vanish:
+ *   u = (h_u1 h_v2 - h_u2 h_v1) / (h_u0 h_v1 - h_u1 h_v0),
+ *   v = (h_u2 h_v0 - h_u0 h_v2) / (h_u0 h_v1 - h_u1 h_v0),
+ * and the camera depth of that point is T_2 (u, v, 1)^T. */
+void orc_splat_uv_T(int64_t m, const double *mu, const double *q, const double *s2, const double *cam, const double *px,
+                    const double *py, double *u, double *v, double *depth)
+{
+    for (int64_t i = 0; i < m; ++i) {
+        const double *qi = q + 4 * i;
+        const double nq = sqrt(qi[0] * qi[0] + qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]);
+        const double qn[4] = {qi[0] / nq, qi[1] / nq, qi[2] / nq, qi[3] / nq};
+        double R[3][3];
+        quat_to_rot(qn, R);
+        double k3[3][3];   /* columns a, b, c in the camera */
+        for (int r = 0; r < 3; ++r) {
+            k3[r][2] = cam_t(cam, r);
+            k3[r][0] = 0.0;
+            k3[r][1] = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                k3[r][2] += cam_R(cam, r, k) * mu[3 * i + k];
+                k3[r][0] += cam_R(cam, r, k) * R[k][0] * s2[2 * i];
+                k3[r][1] += cam_R(cam, r, k) * R[k][1] * s2[2 * i + 1];
+            }
+        }
+        double T[3][3];
+        for (int j = 0; j < 3; ++j) {
+            T[0][j] = cam[2] * k3[0][j] + cam[4] * k3[2][j];
+            T[1][j] = cam[3] * k3[1][j] + cam[5] * k3[2][j];
+            T[2][j] = k3[2][j];
+        }
+        double hu[3], hv[3];
+        for (int j = 0; j < 3; ++j) {
+            hu[j] = T[0][j] - px[i] * T[2][j];
+            hv[j] = T[1][j] - py[i] * T[2][j];
+        }
+        const double den = hu[0] * hv[1] - hu[1] * hv[0];
+        u[i] = (hu[1] * hv[2] - hu[2] * hv[1]) / den;
+        v[i] = (hu[2] * hv[0] - hu[0] * hv[2]) / den;
+        depth[i] = T[2][0] * u[i] + T[2][1] * v[i] + T[2][2];
     }
 }
