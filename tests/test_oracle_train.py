@@ -11,7 +11,6 @@ total loss of Sec. 3.3), no GPU.
 (d) a few Adam steps lower the loss of a perturbed scene towards its target.
 """
 import numpy as np
-import pytest
 
 import oracle
 from oracle import train
