@@ -83,3 +83,16 @@ def test_null_context_is_rejected(L):
                            None, None) == api.ERR_INVALID_ARG
     assert L.fhgs_ndfd_bwd(None, None, None, None, None, None, 0, 64, None, 1, ctypes.byref(p), 20.0, 0.5, None, None,
                            None, None, None, None, None, None) == api.ERR_INVALID_ARG
+
+
+def test_new_calls_reject_a_null_context_and_size_the_adam_state(L):
+    p = api.make_params()
+    assert L.fhgs_point_features(None, 0, None, None, 1, None, 8, None, ctypes.byref(p), None, None, None,
+                                 None) == api.ERR_INVALID_ARG
+    assert L.fhgs_l1_loss(None, 0, None, None, 1.0, None, None, None) == api.ERR_INVALID_ARG
+    opt = api.Adam()
+    assert L.fhgs_adam_gaussians(None, 0, 0, *([None] * 11), ctypes.byref(opt), None, None, None) == api.ERR_INVALID_ARG
+    for deg in range(4):
+        K = (deg + 1) ** 2
+        assert L.fhgs_adam_state_floats(1000, deg) == 2 * 1000 * (11 + 3 * K)
+    assert L.fhgs_adam_state_floats(-1, 0) == -1 and L.fhgs_adam_state_floats(10, 4) == -1
