@@ -655,3 +655,41 @@ def render_2dgs_bwd(surfels: dict, cam: dict, params: dict | None, dC, region=No
                               _p(out["means"]), _p(out["quats"]), _p(out["scales2"]), _p(out["opacities"]),
                               _p(out["rgb"]))
     return out
+
+
+def _surfel_colour_scene(scene: dict) -> dict:
+    """The surfels as a Gaussian scene for the colour record (SH along the
+    view direction, + 0.5, clamped at 0): projection's colour depends only on
+    the mean and SH; the third scale is a stand-in that nothing reads back."""
+    s2 = _f64(scene["scales2"]).reshape(-1, 2)
+    return dict(means=scene["means"], scales=np.concatenate([s2, s2[:, 1:]], axis=1), quats=scene["quats"],
+                opacities=scene["opacities"], sh=scene["sh"], sh_degree=scene.get("sh_degree", 0))
+
+
+def surfel_forward(scene: dict, cam: dict, params: dict | None = None) -> dict:
+    """Tiled surfel render of a surfel scene (means, quats, scales2,
+    opacities, sh) with SH colour."""
+    prm = dict(params or {})
+    prm["sh_degree"] = scene.get("sh_degree", 0)
+    rec = project(_surfel_colour_scene(scene), cam, prm)
+    surf = dict(means=scene["means"], quats=scene["quats"], scales2=scene["scales2"], opacities=scene["opacities"],
+                rgb=rec[:, R_R:R_BL + 1])
+    out = render_2dgs(surf, cam, prm)
+    out["rec"] = rec
+    return out
+
+
+def surfel_backward(scene: dict, cam: dict, params: dict | None, dC) -> dict:
+    """Gradients of sum_p dC[p] . rgb[p] of surfel_forward with respect to
+    means (footprint and view direction), quats, scales2, opacities, sh."""
+    prm = dict(params or {})
+    prm["sh_degree"] = scene.get("sh_degree", 0)
+    cs = _surfel_colour_scene(scene)
+    rec = project(cs, cam, prm)
+    surf = dict(means=scene["means"], quats=scene["quats"], scales2=scene["scales2"], opacities=scene["opacities"],
+                rgb=rec[:, R_R:R_BL + 1])
+    g = render_2dgs_bwd(surf, cam, prm, dC)
+    n = len(g["opacities"])
+    gp = project_bwd(cs, cam, prm, rec, dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), rgb=g["rgb"]))
+    return dict(means=g["means"] + gp["means"], quats=g["quats"], scales2=g["scales2"], opacities=g["opacities"],
+                sh=gp["sh"])
