@@ -693,3 +693,28 @@ def surfel_backward(scene: dict, cam: dict, params: dict | None, dC) -> dict:
     gp = project_bwd(cs, cam, prm, rec, dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), rgb=g["rgb"]))
     return dict(means=g["means"] + gp["means"], quats=g["quats"], scales2=g["scales2"], opacities=g["opacities"],
                 sh=gp["sh"])
+
+
+def ndfd_2dgs(surfels: dict, cam: dict, params: dict | None, feats, fgt, region=None, k=NDFD_K,
+              lam=NDFD_LAMBDA) -> dict:
+    """Per-pixel L_gt and L_cf over the tiled surfel render's contributors
+    (the paper's NDFD on 2DGS geometry)."""
+    W, H = int(cam["width"]), int(cam["height"])
+    x0, y0, x1, y1 = region if region is not None else (0, 0, W, H)
+    npx = (x1 - x0) * (y1 - y0)
+    mu = _f64(surfels["means"]).reshape(-1, 3)
+    n = mu.shape[0]
+    D = int(np.asarray(feats).shape[1])
+    b = bin_surfel_f32(np.asarray(surfels["means"], np.float32), np.asarray(surfels["quats"], np.float32),
+                       np.asarray(surfels["scales2"], np.float32), cam, params)
+    lists = tile_lists([b], [cam], params)
+    Lgt, Lcf = np.zeros(npx), np.zeros(npx)
+    nc = np.zeros(npx, np.int32)
+    lib().orc_ndfd_2dgs(_p(mu), _p(_f64(surfels["quats"]).reshape(n, 4)), _p(_f64(surfels["scales2"]).reshape(n, 2)),
+                        _p(_f64(surfels["opacities"]).reshape(n)), _p(np.ascontiguousarray(lists["gids"], np.uint32)),
+                        _p(np.ascontiguousarray(_cam_ranges(lists, 0), np.uint32)), _p(camera_array(cam)),
+                        _p(params_array(params)), x0, y0, x1, y1, _p(_f64(feats)), ctypes.c_int(D),
+                        _p(_f64(fgt).reshape(npx, D)), ctypes.c_double(k), ctypes.c_double(lam), _p(Lgt), _p(Lcf),
+                        _p(nc))
+    hh, ww = y1 - y0, x1 - x0
+    return dict(Lgt=Lgt.reshape(hh, ww), Lcf=Lcf.reshape(hh, ww), ncontrib=nc.reshape(hh, ww))

@@ -33,7 +33,8 @@
  *     a surfel's footprint (dual conic); orc_bin_surfel_f32: its binary32
  *     binning rule (a padded box, integer decisions reproducible bit for bit);
  *     orc_render_2dgs / orc_render_2dgs_bwd: the tiled render and backward;
- *     orc_splat_uv_T: u(x) through the projective map T = K [a b c].
+ *     orc_splat_uv_T: u(x) through the projective map T = K [a b c];
+ *     orc_ndfd_2dgs: the NDFD losses over the surfel render's weights.
  *   - orc_point_views_f32: the paper's point-to-feature assignment
  *     (Sec. 3.1, App. A "PointsFeatureFusion"): a random visible view, the
  *     nearest pixel; binary32 projection spec (it decides integers).
@@ -947,6 +948,27 @@ static double dotd(const double *a, const double *b, int D)
     return s;
 }
 
+/* L_gt, L_cf and W_N of one pixel from its contributors in order (ids,
+ * weights w_i), its ground-truth feature fg and the D-wide scratch F. */
+static void ndfd_losses(const uint32_t *ids, const double *ws, int nc, const double *feat, int D, const double *fg,
+                        double kslope, double lam, double *F, double *out_Lgt, double *out_Lcf, double *out_W)
+{
+    double Wc = 0.0, Lgt = 0.0, Lcf = 0.0;
+    for (int c = 0; c < D; ++c) F[c] = 0.0;
+    for (int j = 0; j < nc; ++j) {
+        const double *f = feat + (int64_t)D * ids[j];
+        const double w = ws[j];
+        const double sg = ndfd_sigma(f, fg, D, kslope, lam);
+        Lgt += w * sg;
+        Lcf += sg * w * (Wc - dotd(F, f, D));
+        Wc += w;
+        for (int c = 0; c < D; ++c) F[c] += w * f[c];
+    }
+    *out_Lgt = Lgt;
+    *out_Lcf = Lcf;
+    *out_W = Wc;
+}
+
 /* fgt: region pixels x D (row-major in the region).  Outputs per region
  * pixel: L_gt, L_cf, W_N (total weight) and the contributor count. */
 void orc_ndfd(const double *rec, const double *feat, int D, const uint32_t *gids, const uint32_t *ranges,
@@ -963,6 +985,8 @@ void orc_ndfd(const double *rec, const double *feat, int D, const uint32_t *gids
         double *ca = (double *)malloc(sizeof(double) * ORC_MAXC);
         double *cT = (double *)malloc(sizeof(double) * ORC_MAXC);
         double *cG = (double *)malloc(sizeof(double) * ORC_MAXC);
+        uint32_t *ids = (uint32_t *)malloc(sizeof(uint32_t) * ORC_MAXC);
+        double *ws = (double *)malloc(sizeof(double) * ORC_MAXC);
         double *F = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
 #pragma omp for schedule(dynamic, 16)
         for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
@@ -974,24 +998,18 @@ void orc_ndfd(const double *rec, const double *feat, int D, const uint32_t *gids
             int nc = composite_pixel(px + 0.5, py + 0.5, list, (int64_t)e - s, rec, NULL, 0, prm, &st,
                                      NULL, ci, ca, cT, cG, ORC_MAXC);
             if (nc > ORC_MAXC) nc = ORC_MAXC;
-            const double *fg = fgt + (int64_t)D * idx;
-            double Wc = 0.0, Lgt = 0.0, Lcf = 0.0;
-            for (int c = 0; c < D; ++c) F[c] = 0.0;
             for (int j = 0; j < nc; ++j) {
-                const double *f = feat + (int64_t)D * list[ci[j]];
-                const double w = ca[j] * cT[j];
-                const double sg = ndfd_sigma(f, fg, D, kslope, lam);
-                Lgt += w * sg;
-                Lcf += sg * w * (Wc - dotd(F, f, D));
-                Wc += w;
-                for (int c = 0; c < D; ++c) F[c] += w * f[c];
+                ids[j] = list[ci[j]];
+                ws[j] = ca[j] * cT[j];
             }
+            double Lgt, Lcf, Wc;
+            ndfd_losses(ids, ws, nc, feat, D, fgt + (int64_t)D * idx, kslope, lam, F, &Lgt, &Lcf, &Wc);
             out_Lgt[idx] = Lgt;
             out_Lcf[idx] = Lcf;
             if (out_W) out_W[idx] = Wc;
             if (out_ncontrib) out_ncontrib[idx] = nc;
         }
-        free(ci); free(ca); free(cT); free(cG); free(F);
+        free(ci); free(ca); free(cT); free(cG); free(ids); free(ws); free(F);
     }
 }
 
@@ -1661,5 +1679,58 @@ void orc_splat_uv_T(int64_t m, const double *mu, const double *q, const double *
         u[i] = (hu[1] * hv[2] - hu[2] * hv[1]) / den;
         v[i] = (hu[2] * hv[0] - hu[0] * hv[2]) / den;
         depth[i] = T[2][0] * u[i] + T[2][1] * v[i] + T[2][2];
+    }
+}
+
+
+/* NDFD over surfels (the paper's combination of Sec. 3.1-3.3): the
+ * contributors and weights of each pixel come from the tiled surfel render
+ * (orc_render_2dgs's walk), the losses from the same per-pixel arithmetic as
+ * orc_ndfd. */
+void orc_ndfd_2dgs(const double *means, const double *quats, const double *scales2, const double *opac,
+                   const uint32_t *gids, const uint32_t *ranges, const double *cam, const double *prm, int x0, int y0,
+                   int x1, int y1, const double *feat, int D, const double *fgt, double kslope, double lam,
+                   double *out_Lgt, double *out_Lcf, int32_t *out_ncontrib)
+{
+    const int W = (int)cam[0], tsz = (int)prm[P_TILE];
+    const int tiles_x = (W + tsz - 1) / tsz;
+    const int rw = x1 - x0, rh = y1 - y0;
+    const double cut = prm[P_CUT], amin = prm[P_AMIN], amax = prm[P_AMAX], teps = prm[P_TEPS];
+#pragma omp parallel
+    {
+        uint32_t *ids = (uint32_t *)malloc(sizeof(uint32_t) * ORC_MAXC);
+        double *ws = (double *)malloc(sizeof(double) * ORC_MAXC);
+        double *F = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+            const int ix = x0 + (int)(idx % rw), iy = y0 + (int)(idx / rw);
+            const double px = ix + 0.5, py = iy + 0.5;
+            const int t = (iy / tsz) * tiles_x + ix / tsz;
+            double T = 1.0;
+            int nc = 0;
+            for (uint32_t k = ranges[2 * t]; k < ranges[2 * t + 1] && nc < ORC_MAXC; ++k) {
+                const uint32_t g = gids[k];
+                double u, v, lamd;
+                if (!splat_uv(means + 3 * g, quats + 4 * g, scales2 + 2 * g, cam, px, py, &u, &v, &lamd)) continue;
+                if (!(lamd > 0.0)) continue;
+                const double r2 = u * u + v * v;
+                if (r2 > cut) continue;
+                const double rho = opac[g] * exp(-0.5 * r2);
+                const double alpha = rho > amax ? amax : rho;
+                if (alpha < amin) continue;
+                const double Tn = T * (1.0 - alpha);
+                if (Tn < teps) break;
+                ids[nc] = g;
+                ws[nc] = alpha * T;
+                ++nc;
+                T = Tn;
+            }
+            double Lgt, Lcf, Wc;
+            ndfd_losses(ids, ws, nc, feat, D, fgt + (int64_t)D * idx, kslope, lam, F, &Lgt, &Lcf, &Wc);
+            out_Lgt[idx] = Lgt;
+            out_Lcf[idx] = Lcf;
+            if (out_ncontrib) out_ncontrib[idx] = nc;
+        }
+        free(ids); free(ws); free(F);
     }
 }

@@ -348,3 +348,57 @@ def test_surfel_pipeline_with_sh_colour_matches_central_differences():
             assert abs(fds[0] - an) <= 2e-6 * max(1.0, abs(fds[0])), (key, i, fds[0], an)
             checked += abs(an) > 1e-8
     assert checked > 100
+
+
+def test_ndfd_over_surfels():
+    """NDFD on surfel weights: with a constant f_gt, L_gt is the surfel render
+    of each surfel's sigma; the contributor counts are the render's; L_cf is
+    the pair sum of Eq. 6 over each pixel's contributors, composited here
+    directly from the ray-plane solve."""
+    g = np.random.default_rng(18)
+    cam = axis_camera(W=26, H=22, fx=24.0, t=(0.0, 0.01, 0.0))
+    n, D = 30, 6
+    surf = dict(means=g.normal(0, 0.3, (n, 3)) + [0, 0, 2.0], quats=g.normal(size=(n, 4)),
+                scales2=np.exp(g.uniform(-2.6, -1.8, (n, 2))), opacities=g.uniform(0.2, 0.9, n))
+    surf = {k: np.asarray(v, np.float32).astype(np.float64) for k, v in surf.items()}
+    f = g.normal(size=(n, D))
+    f /= np.linalg.norm(f, axis=1, keepdims=True)
+    gt = g.normal(size=D)
+    K, LAM = oracle.NDFD_K, oracle.NDFD_LAMBDA
+    sig = 1.0 / (1.0 + np.exp(K * (f @ gt / np.linalg.norm(gt) - LAM)))
+    out = oracle.ndfd_2dgs(surf, cam, {}, f, np.broadcast_to(gt, (22, 26, D)))
+    ren = oracle.render_2dgs(dict(surf, rgb=np.stack([sig, 0 * sig, 0 * sig], 1)), cam, {})
+    np.testing.assert_allclose(out["Lgt"], ren["rgb"][..., 0], atol=1e-13)
+    np.testing.assert_array_equal(out["ncontrib"], ren["ncontrib"])
+    # Eq. 6 pair sum with per-pixel ground truth
+    fg = g.normal(size=(22, 26, D))
+    out = oracle.ndfd_2dgs(surf, cam, {}, f, fg)
+    lists = ren["lists"]
+    ranges = lists["ranges"]
+    checked = 0
+    for y in range(22):
+        for x in range(26):
+            t = (y // 16) * 2 + x // 16
+            ids = lists["gids"][ranges[t][0]:ranges[t][1]]
+            uv = oracle.splat_uv(surf["means"][ids], surf["quats"][ids], surf["scales2"][ids], cam,
+                                 np.full(len(ids), x + 0.5), np.full(len(ids), y + 0.5))
+            T, ws, fs = 1.0, [], []
+            for j, gid in enumerate(ids):
+                if not uv["hit"][j] or uv["lam"][j] <= 0:
+                    continue
+                r2 = uv["u"][j] ** 2 + uv["v"][j] ** 2
+                if r2 > 9:
+                    continue
+                a = min(0.99, surf["opacities"][gid] * math.exp(-0.5 * r2))
+                if a < 1 / 255:
+                    continue
+                if T * (1 - a) < 1e-4:
+                    break
+                ws.append(a * T)
+                fs.append(f[gid])
+                T *= 1 - a
+            s = [1.0 / (1.0 + math.exp(K * (fi @ fg[y, x] / np.linalg.norm(fg[y, x]) - LAM))) for fi in fs]
+            lcf = sum(s[i] * ws[i] * ws[j] * (1 - fs[i] @ fs[j]) for i in range(len(ws)) for j in range(i))
+            assert abs(out["Lcf"][y, x] - lcf) < 1e-13
+            checked += len(ws) >= 3
+    assert checked > 30
