@@ -718,3 +718,27 @@ def ndfd_2dgs(surfels: dict, cam: dict, params: dict | None, feats, fgt, region=
                         _p(nc))
     hh, ww = y1 - y0, x1 - x0
     return dict(Lgt=Lgt.reshape(hh, ww), Lcf=Lcf.reshape(hh, ww), ncontrib=nc.reshape(hh, ww))
+
+
+def ndfd_2dgs_bwd(surfels: dict, cam: dict, params: dict | None, feats, fgt, dLgt, dLcf, k=NDFD_K,
+                  lam=NDFD_LAMBDA) -> dict:
+    """Gradients of sum_p dLgt L_gt + dLcf L_cf of ndfd_2dgs (full image)
+    with respect to means, quats, scales2 and opacities."""
+    W, H = int(cam["width"]), int(cam["height"])
+    npx = W * H
+    mu = _f64(surfels["means"]).reshape(-1, 3)
+    n = mu.shape[0]
+    D = int(np.asarray(feats).shape[1])
+    b = bin_surfel_f32(np.asarray(surfels["means"], np.float32), np.asarray(surfels["quats"], np.float32),
+                       np.asarray(surfels["scales2"], np.float32), cam, params)
+    lists = tile_lists([b], [cam], params)
+    out = dict(means=np.zeros((n, 3)), quats=np.zeros((n, 4)), scales2=np.zeros((n, 2)), opacities=np.zeros(n))
+    lib().orc_ndfd_2dgs_bwd(_p(mu), _p(_f64(surfels["quats"]).reshape(n, 4)), _p(_f64(surfels["scales2"]).reshape(n, 2)),
+                            _p(_f64(surfels["opacities"]).reshape(n)),
+                            _p(np.ascontiguousarray(lists["gids"], np.uint32)),
+                            _p(np.ascontiguousarray(_cam_ranges(lists, 0), np.uint32)), _p(camera_array(cam)),
+                            _p(params_array(params)), 0, 0, W, H, _p(_f64(feats)), ctypes.c_int(D),
+                            _p(_f64(fgt).reshape(npx, D)), ctypes.c_double(k), ctypes.c_double(lam),
+                            _p(_f64(dLgt).reshape(npx)), _p(_f64(dLcf).reshape(npx)), _p(out["means"]),
+                            _p(out["quats"]), _p(out["scales2"]), _p(out["opacities"]))
+    return out

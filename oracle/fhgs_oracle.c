@@ -34,7 +34,8 @@
  *     binning rule (a padded box, integer decisions reproducible bit for bit);
  *     orc_render_2dgs / orc_render_2dgs_bwd: the tiled render and backward;
  *     orc_splat_uv_T: u(x) through the projective map T = K [a b c];
- *     orc_ndfd_2dgs: the NDFD losses over the surfel render's weights.
+ *     orc_ndfd_2dgs / orc_ndfd_2dgs_bwd: the NDFD losses over the surfel
+ *     render's weights and their derivative.
  *   - orc_point_views_f32: the paper's point-to-feature assignment
  *     (Sec. 3.1, App. A "PointsFeatureFusion"): a random visible view, the
  *     nearest pixel; binary32 projection spec (it decides integers).
@@ -1327,6 +1328,89 @@ void orc_surfel_rect(int64_t n, const double *means, const double *quats, const 
     }
 }
 
+/* dL/dalpha of contributor g at pixel centre (px, py), where the surfel
+ * sits at plane coordinates (u, v) with G = exp(-(u^2 + v^2)/2), taken to
+ * the surfel's opacity, mean, quaternion and (s_u, s_v); accumulates (+=).
+ * alpha = min(alpha_max, op G) (the clamp passes nothing), dG/du = -u G,
+ * dG/dv = -v G, and the ray-plane solve differentiated implicitly:
+ * w = M^-T (0, dL/du, dL/dv), dL/dp = R_w^T w, dL/dR[:,0] = s_u u R_w^T w,
+ * dL/dR[:,1] = s_v v R_w^T w, dL/ds_u = u w . (R_w R[:,0]),
+ * dL/ds_v = v w . (R_w R[:,1]). */
+static void surfel_alpha_chain(uint32_t g, double G, double u, double v, double dalpha, double px, double py,
+                               const double *quats, const double *scales2, const double *opac, const double *cam,
+                               double amax, double *g_means, double *g_quats, double *g_scales2, double *g_opac)
+{
+    const double rho = opac[g] * G;
+    const double drho = rho > amax ? 0.0 : dalpha;
+#pragma omp atomic
+    g_opac[g] += G * drho;
+    const double dG = opac[g] * drho;
+    const double e[3] = {0.0, -u * G * dG, -v * G * dG};
+    /* the surfel's frame in the camera */
+    const double *q = quats + 4 * g;
+    const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
+    double R[3][3];
+    quat_to_rot(qn, R);
+    const double su = scales2[2 * g], sv = scales2[2 * g + 1];
+    double ru[3], rv[3];   /* R_w R[:,0], R_w R[:,1] */
+    for (int r = 0; r < 3; ++r) {
+        ru[r] = 0.0;
+        rv[r] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            ru[r] += cam_R(cam, r, k) * R[k][0];
+            rv[r] += cam_R(cam, r, k) * R[k][1];
+        }
+    }
+    const double d[3] = {(px - cam[4]) / cam[2], (py - cam[5]) / cam[3], 1.0};
+    double M[3][3];
+    for (int r = 0; r < 3; ++r) {
+        M[r][0] = d[r];
+        M[r][1] = -su * ru[r];
+        M[r][2] = -sv * rv[r];
+    }
+    /* w3 = M^-T e: solve M^T w3 = e by Cramer's rule on A = M^T */
+    double A[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) A[r][k] = M[k][r];
+    const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                       A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                       A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    double w3[3];
+    for (int col = 0; col < 3; ++col) {
+        double B[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k) B[r][k] = k == col ? e[r] : A[r][k];
+        w3[col] = (B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1]) -
+                   B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0]) +
+                   B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0])) / det;
+    }
+    double rt[3];   /* R_w^T w3 */
+    for (int k = 0; k < 3; ++k) rt[k] = cam_R(cam, 0, k) * w3[0] + cam_R(cam, 1, k) * w3[1] + cam_R(cam, 2, k) * w3[2];
+    for (int k = 0; k < 3; ++k) {
+#pragma omp atomic
+        g_means[3 * g + k] += rt[k];
+    }
+    const double gsu = u * (w3[0] * ru[0] + w3[1] * ru[1] + w3[2] * ru[2]);
+    const double gsv = v * (w3[0] * rv[0] + w3[1] * rv[1] + w3[2] * rv[2]);
+#pragma omp atomic
+    g_scales2[2 * g] += gsu;
+#pragma omp atomic
+    g_scales2[2 * g + 1] += gsv;
+    double GR[3][3];
+    for (int k = 0; k < 3; ++k) {
+        GR[k][0] = su * u * rt[k];
+        GR[k][1] = sv * v * rt[k];
+        GR[k][2] = 0.0;
+    }
+    double gq[4] = {0.0, 0.0, 0.0, 0.0};
+    quat_grad(qn, nq, GR, gq);
+    for (int k = 0; k < 4; ++k) {
+#pragma omp atomic
+        g_quats[4 * g + k] += gq[k];
+    }
+}
+
 /* Gradient of L = sum_p dC[p] . rgb[p] of the surfel render with respect to
  * each surfel's mean, quaternion, (s_u, s_v), opacity and colour;
  * accumulates (+=).  dL/dalpha by the App. A.2 identity with the background
@@ -1380,75 +1464,8 @@ static void surfel_pixel_bwd(double px, double py, const uint32_t *list, int64_t
 #pragma omp atomic
             g_rgb[3 * g + ch] += w * dc[ch];
         }
-        const double rho = opac[g] * G;
-        const double drho = rho > amax ? 0.0 : dalpha;
-#pragma omp atomic
-        g_opac[g] += G * drho;
-        const double dG = opac[g] * drho;
-        const double e[3] = {0.0, -u * G * dG, -v * G * dG};
-        /* the surfel's frame in the camera */
-        const double *q = quats + 4 * g;
-        const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-        const double qn[4] = {q[0] / nq, q[1] / nq, q[2] / nq, q[3] / nq};
-        double R[3][3];
-        quat_to_rot(qn, R);
-        const double su = scales2[2 * g], sv = scales2[2 * g + 1];
-        double ru[3], rv[3];   /* R_w R[:,0], R_w R[:,1] */
-        for (int r = 0; r < 3; ++r) {
-            ru[r] = 0.0;
-            rv[r] = 0.0;
-            for (int k = 0; k < 3; ++k) {
-                ru[r] += cam_R(cam, r, k) * R[k][0];
-                rv[r] += cam_R(cam, r, k) * R[k][1];
-            }
-        }
-        const double d[3] = {(px - cam[4]) / cam[2], (py - cam[5]) / cam[3], 1.0};
-        double M[3][3];
-        for (int r = 0; r < 3; ++r) {
-            M[r][0] = d[r];
-            M[r][1] = -su * ru[r];
-            M[r][2] = -sv * rv[r];
-        }
-        /* w3 = M^-T e: solve M^T w3 = e by Cramer's rule on A = M^T */
-        double A[3][3];
-        for (int r = 0; r < 3; ++r)
-            for (int k = 0; k < 3; ++k) A[r][k] = M[k][r];
-        const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
-                           A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-                           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
-        double w3[3];
-        for (int col = 0; col < 3; ++col) {
-            double B[3][3];
-            for (int r = 0; r < 3; ++r)
-                for (int k = 0; k < 3; ++k) B[r][k] = k == col ? e[r] : A[r][k];
-            w3[col] = (B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1]) -
-                       B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0]) +
-                       B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0])) / det;
-        }
-        double rt[3];   /* R_w^T w3 */
-        for (int k = 0; k < 3; ++k) rt[k] = cam_R(cam, 0, k) * w3[0] + cam_R(cam, 1, k) * w3[1] + cam_R(cam, 2, k) * w3[2];
-        for (int k = 0; k < 3; ++k) {
-#pragma omp atomic
-            g_means[3 * g + k] += rt[k];
-        }
-        const double gsu = u * (w3[0] * ru[0] + w3[1] * ru[1] + w3[2] * ru[2]);
-        const double gsv = v * (w3[0] * rv[0] + w3[1] * rv[1] + w3[2] * rv[2]);
-#pragma omp atomic
-        g_scales2[2 * g] += gsu;
-#pragma omp atomic
-        g_scales2[2 * g + 1] += gsv;
-        double GR[3][3];
-        for (int k = 0; k < 3; ++k) {
-            GR[k][0] = su * u * rt[k];
-            GR[k][1] = sv * v * rt[k];
-            GR[k][2] = 0.0;
-        }
-        double gq[4] = {0.0, 0.0, 0.0, 0.0};
-        quat_grad(qn, nq, GR, gq);
-        for (int k = 0; k < 4; ++k) {
-#pragma omp atomic
-            g_quats[4 * g + k] += gq[k];
-        }
+        surfel_alpha_chain(g, G, u, v, dalpha, px, py, quats, scales2, opac, cam, amax, g_means, g_quats, g_scales2,
+                           g_opac);
     }
 }
 
@@ -1732,5 +1749,87 @@ void orc_ndfd_2dgs(const double *means, const double *quats, const double *scale
             if (out_ncontrib) out_ncontrib[idx] = nc;
         }
         free(ids); free(ws); free(F);
+    }
+}
+
+
+/* Gradient of L = sum_p dLgt[p] L_gt(p) + dLcf[p] L_cf(p) of orc_ndfd_2dgs
+ * with respect to the surfels' means, quaternions, (s_u, s_v) and
+ * opacities; accumulates (+=).  dL/dw_k and dL/dalpha_k as in orc_ndfd_bwd
+ * (Sec. 3.3, App. A.2), then the surfel chain of surfel_alpha_chain. */
+void orc_ndfd_2dgs_bwd(const double *means, const double *quats, const double *scales2, const double *opac,
+                       const uint32_t *gids, const uint32_t *ranges, const double *cam, const double *prm, int x0,
+                       int y0, int x1, int y1, const double *feat, int D, const double *fgt, double kslope,
+                       double lam, const double *dLgt, const double *dLcf, double *g_means, double *g_quats,
+                       double *g_scales2, double *g_opac)
+{
+    const int W = (int)cam[0], tsz = (int)prm[P_TILE];
+    const int tiles_x = (W + tsz - 1) / tsz;
+    const int rw = x1 - x0, rh = y1 - y0;
+    const double cut = prm[P_CUT], amin = prm[P_AMIN], amax = prm[P_AMAX], teps = prm[P_TEPS];
+#pragma omp parallel
+    {
+        uint32_t *ids = (uint32_t *)malloc(sizeof(uint32_t) * ORC_MAXC);
+        double *cs = (double *)malloc(sizeof(double) * ORC_MAXC * 7);   /* alpha, T, G, u, v, sigma, pre */
+        double *F = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
+        double *Gs = (double *)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx) {
+            const int ix = x0 + (int)(idx % rw), iy = y0 + (int)(idx / rw);
+            const double px = ix + 0.5, py = iy + 0.5;
+            const int t = (iy / tsz) * tiles_x + ix / tsz;
+            double T = 1.0;
+            int nc = 0;
+            for (uint32_t k = ranges[2 * t]; k < ranges[2 * t + 1] && nc < ORC_MAXC; ++k) {
+                const uint32_t g = gids[k];
+                double u, v, lamd;
+                if (!splat_uv(means + 3 * g, quats + 4 * g, scales2 + 2 * g, cam, px, py, &u, &v, &lamd)) continue;
+                if (!(lamd > 0.0)) continue;
+                const double r2 = u * u + v * v;
+                if (r2 > cut) continue;
+                const double G = exp(-0.5 * r2);
+                const double rho = opac[g] * G;
+                const double alpha = rho > amax ? amax : rho;
+                if (alpha < amin) continue;
+                const double Tn = T * (1.0 - alpha);
+                if (Tn < teps) break;
+                ids[nc] = g;
+                double *c = cs + 7 * nc;
+                c[0] = alpha; c[1] = T; c[2] = G; c[3] = u; c[4] = v;
+                ++nc;
+                T = Tn;
+            }
+            const double *fg = fgt + (int64_t)D * idx;
+            const double cgt = dLgt[idx], ccf = dLcf[idx];
+            /* front to back: sigma_k and W_{k-1} - F_{k-1} . f_k */
+            double Wc = 0.0;
+            for (int c = 0; c < D; ++c) F[c] = 0.0;
+            for (int j = 0; j < nc; ++j) {
+                const double *f = feat + (int64_t)D * ids[j];
+                double *c = cs + 7 * j;
+                const double w = c[0] * c[1];
+                c[5] = ndfd_sigma(f, fg, D, kslope, lam);
+                c[6] = Wc - dotd(F, f, D);
+                Wc += w;
+                for (int q = 0; q < D; ++q) F[q] += w * f[q];
+            }
+            /* back to front */
+            double Ss = 0.0, Sw = 0.0;
+            for (int c = 0; c < D; ++c) Gs[c] = 0.0;
+            for (int k = nc - 1; k >= 0; --k) {
+                const uint32_t g = ids[k];
+                const double *f = feat + (int64_t)D * g;
+                const double *c = cs + 7 * k;
+                const double alpha = c[0], Tk = c[1], w = alpha * Tk, sg = c[5];
+                const double gw = cgt * sg + ccf * (sg * c[6] + Ss - dotd(Gs, f, D));
+                const double dalpha = Tk * gw - Sw / (1.0 - alpha);
+                Sw += w * gw;
+                Ss += sg * w;
+                for (int q = 0; q < D; ++q) Gs[q] += sg * w * f[q];
+                surfel_alpha_chain(g, c[2], c[3], c[4], dalpha, px, py, quats, scales2, opac, cam, amax, g_means,
+                                   g_quats, g_scales2, g_opac);
+            }
+        }
+        free(ids); free(cs); free(F); free(Gs);
     }
 }

@@ -402,3 +402,41 @@ def test_ndfd_over_surfels():
             assert abs(out["Lcf"][y, x] - lcf) < 1e-13
             checked += len(ws) >= 3
     assert checked > 30
+
+
+def test_ndfd_over_surfels_backward_matches_central_differences():
+    g = np.random.default_rng(19)
+    cam = axis_camera(W=24, H=22, fx=23.0, t=(0.01, 0.0, 0.0))
+    n, D = 9, 5
+    q = g.normal(size=(n, 4))
+    surf = dict(means=g.normal(0, 0.25, (n, 3)) + [0, 0, 2.0], quats=q / np.linalg.norm(q, axis=1, keepdims=True),
+                scales2=np.exp(g.uniform(-2.4, -1.7, (n, 2))), opacities=g.uniform(0.2, 0.9, n))
+    f = g.normal(size=(n, D))
+    f /= np.linalg.norm(f, axis=1, keepdims=True)
+    fg = g.normal(size=(22, 24, D))
+    a, b = g.normal(size=(22, 24)), g.normal(size=(22, 24))
+    grads = oracle.ndfd_2dgs_bwd(surf, cam, {}, f, fg, a, b)
+
+    def loss(s):
+        r = oracle.ndfd_2dgs(s, cam, {}, f, fg)
+        return float((r["Lgt"] * a).sum() + (r["Lcf"] * b).sum())
+
+    checked = 0
+    for key in ("means", "quats", "scales2", "opacities"):
+        base = np.asarray(surf[key], np.float64)
+        flat = base.reshape(-1)
+        for i in range(flat.size):
+            fds = []
+            for h in (1e-6, 5e-7):
+                vals = []
+                for sgn in (1, -1):
+                    pert = flat.copy()
+                    pert[i] += sgn * h
+                    vals.append(loss(dict(surf, **{key: pert.reshape(base.shape)})))
+                fds.append((vals[0] - vals[1]) / (2 * h))
+            if abs(fds[0] - fds[1]) > 1e-6 * max(1.0, abs(fds[0])):
+                continue
+            an = grads[key].reshape(-1)[i]
+            assert abs(fds[0] - an) <= 2e-6 * max(1.0, abs(fds[0])), (key, i, fds[0], an)
+            checked += abs(an) > 1e-8
+    assert checked > 60
