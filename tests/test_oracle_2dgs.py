@@ -440,3 +440,26 @@ def test_ndfd_over_surfels_backward_matches_central_differences():
             assert abs(fds[0] - an) <= 2e-6 * max(1.0, abs(fds[0])), (key, i, fds[0], an)
             checked += abs(an) > 1e-8
     assert checked > 60
+
+
+def test_surfel_binning_rule_covers_the_exact_box_at_1080p():
+    """At the bench's scale (1920x1080, f = 1662.8, surfels at depth ~4 with
+    log-scales U[-5, -2]) the binary32 rule's pixel rectangle contains the
+    exact box's pixels for every binned surfel, with a few pixels of pad."""
+    g = np.random.default_rng(1)
+    cam = axis_camera(W=1920, H=1080, fx=1662.8, cx=960, cy=540)
+    m = 50000
+    mu = (g.normal(0, 0.6, (m, 3)) + [0, 0, 4.0]).astype(np.float32)
+    q = g.normal(size=(m, 4)).astype(np.float32)
+    s2 = np.exp(g.uniform(-5, -2, (m, 2))).astype(np.float32)
+    b = oracle.bin_surfel_f32(mu, q, s2, cam)
+    ex = oracle.surfel_rect(mu.astype(np.float64), q.astype(np.float64), s2.astype(np.float64), cam)
+    ok = (b["ntiles"] > 0) & ex["bounded"]
+    r, p = ex["rect"][ok], b["pix"][ok]
+    xl, xh = np.maximum(np.ceil(r[:, 0] - 0.5), 0), np.minimum(np.floor(r[:, 1] - 0.5), 1919)
+    yl, yh = np.maximum(np.ceil(r[:, 2] - 0.5), 0), np.minimum(np.floor(r[:, 3] - 0.5), 1079)
+    valid = (xl <= xh) & (yl <= yh)
+    assert valid.sum() > 40000
+    assert not (valid & ((p[:, 0] > xl) | (p[:, 2] < xh) | (p[:, 1] > yl) | (p[:, 3] < yh))).any()
+    over = np.maximum(np.maximum(xl - p[:, 0], p[:, 2] - xh), np.maximum(yl - p[:, 1], p[:, 3] - yh))[valid]
+    assert np.median(over) <= 3
