@@ -345,6 +345,14 @@ def run_ours(args):
         fp32 = {"value": round(P * world / (ms32 * 1e-3) / 1e6, 2), "ms_per_step": round(ms32, 3),
                 "kernels_ms": {k: round(v[1] / max(v[0], 1), 3) for k, v in prof32.items()}}
         del r32
+        # the same algorithmic contraction FLOPs, on the CUDA cores, against
+        # the measured FP32 FMA peak
+        fpk = fp32_peak(dev, local)
+        fl = algorithmic_flops(N, D, Q)
+        fp32["fp32_peak"] = fpk
+        fp32["alu_frac"] = {k: round(fl[k.replace("_fp32", "")] / (fp32["kernels_ms"][k] * 1e-3) / 1e12 /
+                                     fpk["tflops"], 4)
+                            for k in ("render_fwd_fp32", "render_bwd_fp32") if k in fp32["kernels_ms"]}
 
     # end to end through the C ABI with host buffers: H2D of every input and
     # D2H of every output inside the timed region
@@ -384,7 +392,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(scene, cams, args.D, max_seconds=25.0)
+        cpu = cpu_baseline(args.n, args.D)
 
     if rank == 0:
         line = {
@@ -498,18 +506,26 @@ def oracle_sample(scene, cams, D, seed=0):
     return (x1 - x0) * (y1 - y0)
 
 
-def cpu_baseline(scene, cams, D, max_seconds=25.0, reps_max=3):
-    import oracle
+def cpu_baseline(n, D, steps=3, warmup=1):
+    """The oracle timed as `--impl reference` times it, in a fresh process
+    (no CUDA context, no second OpenMP runtime, no sampler beside it): one
+    untimed sample (which also loads the oracle's library), then `steps`
+    timed ones of the same workload."""
+    import subprocess
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", str(steps),
+           "--warmup", str(warmup), "--n", str(n), "--D", str(D)]
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
     t0 = time.time()
-    reps, px = 0, 0
-    while reps < reps_max and (reps == 0 or time.time() - t0 < max_seconds / 2):
-        px += oracle_sample(scene, cams, D)
-        reps += 1
-    dt = time.time() - t0
-    return {"value": round(px / dt / 1e6, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{reps} x (project + FP32-spec binning of all {len(scene['means'])} Gaussians, "
-                      f"lists of the 64x64 crop's tiles, FP64 fwd+bwd of its 4096 pixels, D={D})",
-            "seconds": round(dt, 2)}
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"value": None, "unit": UNIT, "kind": "oracle", "error": (r.stderr or r.stdout)[-300:]}
+    ref = lines[-1]
+    return {"value": ref["value"], "unit": UNIT, "cores": ref["cpu_baseline"]["cores"], "kind": "oracle",
+            "sample": f"{steps} x (project + FP32-spec binning of all {n} Gaussians, lists of the 64x64 crop's "
+                      f"tiles, FP64 fwd+bwd of its 4096 pixels, D={D}), after {warmup} untimed sample(s), "
+                      f"in a fresh process",
+            "seconds": round(steps * ref["ms_per_step"] / 1e3, 2), "wall_s": round(time.time() - t0, 1)}
 
 
 def run_reference(args):
@@ -629,8 +645,40 @@ def points_cpu_baseline(means, views, maps, u, n_sample=3_000_000):
 # ------------------------------------------------------------------ NDFD
 NDFD_METRIC = "NDFD L_gt+L_cf fwd+bwd Mpix/s at 1M Gaussians, D=512 BF16; % of FP32 ALU roofline"
 NDFD_WORKLOAD = "1M Gaussians, 1920x1080 view, D=512 BF16 unit features and ground-truth map, NDFD fwd+bwd"
-# FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+def fp32_peak(dev, index=0, seconds=0.6):
+    """Measured FP32 FMA peak: fhgs_ffma_probe (2 x 1024 threads per SM, eight
+    independent FMA chains per thread) timed with CUDA events on the launch
+    stream, best launch over about `seconds`, with the SM clock sampled
+    meanwhile.  Also reports FLOP per clock per SM at the sampled clock (256
+    when all 128 FP32 lanes of an SM retire an FMA every clock)."""
+    import ctypes
+    from paper_2505_19154_gb300 import api
+    L = api.lib()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    st = torch.cuda.current_stream(dev)
+    sp = ctypes.c_void_p(st.cuda_stream)
+    blocks, iters = 2 * sms, 4000
+    flops = L.fhgs_ffma_probe(blocks, iters, sp)
+    if flops <= 0:
+        raise RuntimeError("fhgs_ffma_probe failed")
+    torch.cuda.synchronize()
+    clk = ClockSampler(index)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best, n, t_end = float("inf"), 0, time.time() + seconds
+    while n < 5 or time.time() < t_end:
+        e0.record(st)
+        L.fhgs_ffma_probe(blocks, iters, sp)
+        e1.record(st)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+        n += 1
+    ck = clk.stop()
+    tf = flops / (best * 1e-3) / 1e12
+    mhz = ck["sm_mhz"]
+    return {"tflops": round(tf, 2), "launches": n, "ms": round(best, 4), "sm_mhz": mhz,
+            "flop_per_clk_per_sm": round(tf * 1e12 / (mhz * 1e6) / sms, 1) if mhz else None,
+            "source": "measured: fhgs_ffma_probe, best of the timed launches (CUDA events)"}
 
 
 def ndfd_cpu_baseline(scene, cams, feats, fgt, dLgt, dLcf, max_seconds=25.0, reps_max=3):
@@ -741,10 +789,11 @@ def run_ndfd(args):
             per[k]["fp32_tflops"] = round(f / (per[k]["ms"] * 1e-3) / 1e12, 2)
     dom = max(("ndfd_fwd", "ndfd_bwd"), key=lambda k: prof.get(k, (0, 0))[1])
     ach = flops[dom] / (per[dom]["ms"] * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
-            "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4),
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz", "traffic": None,
-            "algorithmic_flops": flops[dom]}
+    fpk = fp32_peak(dev)
+    roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": fpk["tflops"],
+            "unit": "TFLOP/s", "frac": round(ach / fpk["tflops"], 4),
+            "peak_source": "of measured FP32 FMA peak (fhgs_ffma_probe, this run)", "traffic": None,
+            "algorithmic_flops": flops[dom], "fp32_peak": fpk}
     cpu = None
     if not args.no_cpu_baseline:
         cpu = ndfd_cpu_baseline(scene, cams, feats, fgt, dLgt, dLcf)

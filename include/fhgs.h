@@ -348,14 +348,38 @@ fhgs_status fhgs_ndfd_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *pr
  *   - Every call shares the arrays and clears the scratch first: calls that
  *     overlap on the GPU (several streams or threads) race on it, so order
  *     them on one stream.
- *   - A device-side error (a bounded wait that ran out) is latched in the
- *     library's own status word, which this call does not report. */
+ *   - A device-side error (a bounded wait that ran out) is latched in a
+ *     status word of its own, shared like the scratch; read and clear it
+ *     with fhgs_noalloc_sync_status. */
 fhgs_status fhgs_render_bwd_noalloc(const fhgs_gaussians *g, const void *proj, const fhgs_bins *bins,
                                     const void *features, fhgs_dtype ftype, int D, const fhgs_camera *cams,
                                     int n_cams, const fhgs_params *p, const float *T_final, const int32_t *last,
                                     const float *grad_rgb, const float *grad_feat, float *grad_means,
                                     float *grad_scales, float *grad_quats, float *grad_opac, float *grad_sh,
                                     float *grad_features, void *stream);
+
+/* The paper has no counterpart to this call either.  Status of the
+ * allocation-free backward on the current device: synchronises `stream`,
+ * reads the status word that fhgs_render_bwd_noalloc's kernels latch into,
+ * clears it, and returns FHGS_ERR_TIMEOUT (a bounded device-side wait ran
+ * out: the gradients of that call are incomplete), FHGS_ERR_NUMERIC,
+ * FHGS_ERR_CAPACITY or FHGS_OK.  Allocates nothing; FHGS_ERR_CUDA if a
+ * runtime call fails. */
+fhgs_status fhgs_noalloc_sync_status(void *stream);
+
+/* ------------------------------------------------ failure detection -- */
+/* Debug probe of the bounded device-side waits, off (0) by default and
+ * process-wide.  While ns > 0, every CTA of the tensor-core kernels
+ * (render forward and backward, fusion) launched afterwards -- through a
+ * context or the allocation-free call -- first waits at most ns nanoseconds
+ * on an mbarrier that nothing arrives at, before it issues any copy or MMA
+ * or allocates tensor memory.  The wait runs out, the CTA latches
+ * FHGS_ERR_TIMEOUT into the status word of its call and returns, so those
+ * launches compute nothing.  It exists to test that a wait which runs out
+ * is reported (fhgs_sync_status, fhgs_noalloc_sync_status) and leaves the
+ * context usable.  ns > 10 s returns FHGS_ERR_INVALID_ARG.  A launch
+ * captured in a CUDA graph keeps the value it was captured with. */
+fhgs_status fhgs_debug_wait_probe(uint64_t ns);
 
 /* ----------------------------------------------------- instrumentation -- */
 /* Kernel timing: while enabled, every kernel group the context launches is
@@ -366,6 +390,13 @@ fhgs_status fhgs_render_bwd_noalloc(const fhgs_gaussians *g, const void *proj, c
  * Timing adds one event record before and after each launch. */
 fhgs_status fhgs_profile_enable(fhgs_ctx *ctx, int enable);
 fhgs_status fhgs_profile_read(fhgs_ctx *ctx, char *buf, int64_t len);
+/* Measurement helper; the paper has no counterpart.  Launches an FP32
+ * fused-multiply-add throughput probe on `stream` (blocks x 1024 threads,
+ * iters rounds of 128 FMAs per thread, on the current device) and returns the
+ * FLOPs it performs, or -1 on bad sizes or a failed launch.  The caller times
+ * the launch with CUDA events; FLOPs / time is the measured FP32 peak that
+ * the CUDA-core kernels' rooflines are reported against. */
+int64_t fhgs_ffma_probe(int blocks, int iters, void *stream);
 /* Number of kernels this library has launched in this process. */
 int64_t fhgs_launch_count(void);
 

@@ -422,7 +422,9 @@ typedef struct {
     double T;
     double rgb[3];
     int32_t last;       /* (position of the last contributor in the list) + 1 */
-    double margin;      /* min relative distance of any threshold decision */
+    double margin;      /* min relative distance to its threshold of a decision
+                           that decides the contributor set (cutoff, alpha_min,
+                           stop); the continuous alpha_max clamp is left out */
     uint64_t sig;       /* hash of the contributor set and clamp flags */
 } pix_state;
 
@@ -448,13 +450,16 @@ static int composite_pixel(double px, double py, const uint32_t *list, int64_t l
         if (r[R_VALID] == 0.0) continue;
         double dx = px - r[R_MX], dy = py - r[R_MY];
         double q2 = r[R_A] * dx * dx + 2.0 * r[R_B] * dx * dy + r[R_C] * dy * dy;
+        /* the cutoff decides membership only for a Gaussian that would pass
+         * the alpha test right at the cutoff */
         double m = rel(q2, cut);
-        if (m < st->margin) st->margin = m;
+        double a_cut = r[R_OP] * exp(-0.5 * cut);
+        if (a_cut > amax) a_cut = amax;
+        if (a_cut >= amin * (1.0 - 1e-3) && m < st->margin) st->margin = m;
         if (q2 > cut) continue;
         double G = exp(-0.5 * q2);
         double rho = r[R_OP] * G;
-        m = rel(rho, amax);
-        if (m < st->margin) st->margin = m;
+        /* the alpha_max clamp is continuous in alpha: no margin */
         double alpha = rho > amax ? amax : rho;
         m = rel(alpha, amin);
         if (m < st->margin) st->margin = m;
@@ -828,7 +833,8 @@ static void flip_bounds(double px, double py, const uint32_t *list, int64_t len,
         double a_thr = 0.0;  /* largest alpha a decision within mtol of its threshold can have */
         if (rel(q2, cut) < mtol) {
             double a = r[R_OP] * exp(-0.5 * cut * (1.0 - mtol));
-            a_thr = a > amax ? amax : a;
+            a = a > amax ? amax : a;
+            if (a >= amin * (1.0 - mtol)) a_thr = a;  /* else it never contributes */
         }
         double alpha = 0.0;
         if (q2 <= cut) {

@@ -28,7 +28,7 @@ EXPORTS = ["fhgs_create", "fhgs_destroy", "fhgs_last_error", "fhgs_status_string
            "fhgs_project", "fhgs_bin_sort", "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features",
            "fhgs_profile_enable", "fhgs_profile_read", "fhgs_launch_count", "fhgs_render_bwd_noalloc",
            "fhgs_ndfd_fwd", "fhgs_ndfd_bwd", "fhgs_point_features", "fhgs_l1_loss", "fhgs_adam_state_floats",
-           "fhgs_adam_gaussians"]
+           "fhgs_adam_gaussians", "fhgs_noalloc_sync_status", "fhgs_debug_wait_probe", "fhgs_ffma_probe"]
 MAX_POINT_VIEWS = 4096  # FHGS_MAX_POINT_VIEWS of include/fhgs.h
 NDFD_K, NDFD_LAMBDA = 20.0, 0.5  # the activation's slope and threshold (Sec. 4)
 
@@ -114,6 +114,10 @@ def lib():
                                               ctypes.POINTER(Camera), i32, ctypes.POINTER(Params), f32p, vp, f32p,
                                               f32p, f32p, f32p, f32p, f32p, f32p, f32p, vp]
         L.fhgs_render_bwd_noalloc.restype = i32
+        L.fhgs_noalloc_sync_status.argtypes = [vp]
+        L.fhgs_noalloc_sync_status.restype = i32
+        L.fhgs_debug_wait_probe.argtypes = [ctypes.c_uint64]
+        L.fhgs_debug_wait_probe.restype = i32
         f32 = ctypes.c_float
         L.fhgs_ndfd_fwd.argtypes = [vp, i64, vp, ctypes.POINTER(Bins), vp, vp, i32, i32, ctypes.POINTER(Camera), i32,
                                     ctypes.POINTER(Params), f32, f32, f32p, f32p, vp, vp]
@@ -128,6 +132,8 @@ def lib():
         L.fhgs_adam_gaussians.argtypes = [vp, i64, i32] + [f32p] * 11 + [ctypes.POINTER(Adam), f32p, f32p, vp]
         L.fhgs_profile_enable.argtypes = [vp, i32]
         L.fhgs_profile_read.argtypes = [vp, ctypes.c_char_p, i64]
+        L.fhgs_ffma_probe.argtypes = [i32, i32, vp]
+        L.fhgs_ffma_probe.restype = i64
         L.fhgs_launch_count.argtypes = []
         L.fhgs_launch_count.restype = i64
         for name in ("fhgs_create", "fhgs_reserve", "fhgs_sync_status", "fhgs_project", "fhgs_bin_sort",
@@ -338,6 +344,21 @@ def render_bwd_noalloc(g, proj, bins, features, D, cams, params, T, last, grgb, 
                                              _ptr(grgb), _ptr(gfeat), _ptr(out["means"]), _ptr(out["scales"]),
                                              _ptr(out["quats"]), _ptr(out["opacities"]), _ptr(out["sh"]),
                                              _ptr(out.get("features")), Context.stream_ptr(stream)))
+
+
+def noalloc_sync_status(stream=None) -> int:
+    """fhgs_noalloc_sync_status: reads and clears the allocation-free
+    backward's status word on the current device.  Returns the status code."""
+    return int(lib().fhgs_noalloc_sync_status(Context.stream_ptr(stream)))
+
+
+def debug_wait_probe(ns: int) -> None:
+    """fhgs_debug_wait_probe: while ns > 0, every CTA of the tensor-core
+    kernels launched afterwards runs out a bounded wait (ns) before doing
+    anything, latches FHGS_ERR_TIMEOUT and returns.  0 turns it off."""
+    s = int(lib().fhgs_debug_wait_probe(int(ns)))
+    if s != OK:
+        raise FhgsError(s, "fhgs_debug_wait_probe")
 
 
 def gaussians_struct(means, scales, quats, opacities, sh) -> Gaussians:

@@ -38,6 +38,7 @@ struct fhgs_ctx {
 };
 
 static std::atomic<long long> g_launches{0};
+static std::atomic<unsigned long long> g_wait_probe_ns{0};
 
 namespace fhgs {
 void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -173,6 +174,7 @@ Params make_params(const fhgs_params *p) {
     q.bg2 = p->bg[2];
     q.sh_deg = p->sh_degree;
     q.K = (p->sh_degree + 1) * (p->sh_degree + 1);
+    q.probe_ns = g_wait_probe_ns.load(std::memory_order_relaxed);
     return q;
 }
 
@@ -337,6 +339,12 @@ fhgs_status fhgs_reserve(fhgs_ctx *ctx, int64_t max_n, const fhgs_camera *cams, 
     FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
     if ((s = ensure_bin_scratch(ctx, max_n, n_cams, cs.total_tiles)) != FHGS_OK) return s;
     return ensure(ctx, ctx->g2d, sizeof(float) * 12 * (size_t)max_n * n_cams + 256);
+}
+
+fhgs_status fhgs_debug_wait_probe(uint64_t ns) {
+    if (ns > 10000000000ull) return FHGS_ERR_INVALID_ARG;  // at most 10 s
+    g_wait_probe_ns.store(ns, std::memory_order_relaxed);
+    return FHGS_OK;
 }
 
 fhgs_status fhgs_sync_status(fhgs_ctx *ctx, void *stream) {

@@ -41,6 +41,10 @@ struct Params {
     float znear, dil, amin, amax, teps, cut, fov;
     float bg0, bg1, bg2;
     int sh_deg, K;
+    // Failure-detection probe of the tensor-core kernels (fhgs_debug_wait_probe):
+    // 0 = off; else each CTA first waits at most this many ns on an mbarrier
+    // that nothing arrives at, latches ST_TIMEOUT and returns.
+    unsigned long long probe_ns;
 };
 
 // Per (camera, Gaussian) screen-space record used by the render kernels.

@@ -89,3 +89,22 @@ extern "C" fhgs_status fhgs_render_bwd_noalloc(const fhgs_gaussians *g, const vo
     launch_project_bwd(*g, cs, q, pv, d.g2d, grad_means, grad_scales, grad_quats, grad_opac, grad_sh, st);
     return cudaGetLastError() == cudaSuccess ? FHGS_OK : FHGS_ERR_CUDA;
 }
+
+// Reads and clears the allocation-free call's status word on the current
+// device, after the stream's work is done.  Host memory only: a stack word.
+extern "C" fhgs_status fhgs_noalloc_sync_status(void *stream) {
+    DeviceScratch d;
+    fhgs_status s = scratch_for_current_device(d);
+    if (s != FHGS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FHGS_ERR_CUDA;
+    if (cudaMemcpyAsync(&h, d.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return FHGS_ERR_CUDA;
+    if (cudaMemsetAsync(d.status, 0, sizeof(unsigned), st) != cudaSuccess) return FHGS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FHGS_ERR_CUDA;
+    if (h & ST_TIMEOUT) return FHGS_ERR_TIMEOUT;
+    if (h & ST_NUMERIC) return FHGS_ERR_NUMERIC;
+    if (h & ST_CAPACITY) return FHGS_ERR_CAPACITY;
+    return FHGS_OK;
+}

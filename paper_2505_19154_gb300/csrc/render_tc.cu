@@ -72,11 +72,30 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity; false if it ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (!mbar_try(bar, parity))
-        if (globaltimer() - t0 > kWaitNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
+    return true;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) { return mbar_wait_for(bar, parity, kWaitNs); }
+
+// Failure-detection probe (Params::probe_ns, 0 = off).  Before the CTA
+// issues any copy or MMA or allocates TMEM, thread 0 runs the bounded wait on
+// an mbarrier that nothing arrives at (placed at the start of dynamic shared
+// memory), with the probe's limit; the wait runs out, ST_TIMEOUT is latched,
+// and the whole CTA returns.  Returns true when the CTA must return.
+__device__ __forceinline__ bool probe_wait_expired(const Params &p, uint8_t *sm, unsigned *status) {
+    if (p.probe_ns == 0) return false;  // uniform over the grid
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        if (!mbar_wait_for(bar, 0, p.probe_ns)) latch(status, ST_TIMEOUT);
+    }
+    __syncthreads();
     return true;
 }
 
@@ -266,6 +285,7 @@ __global__ void __launch_bounds__(256, 2)
     using C = FwdCfg<DN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
+    if (probe_wait_expired(p, sm, status)) return;
     uint8_t *sW = sm;                                            // [2][128 rows][128 B]
     float *xT = reinterpret_cast<float *>(sm + C::kOffX);        // [128] T entering the next batch
     int *xDone = reinterpret_cast<int *>(xT + 128);               // [128]
@@ -653,6 +673,7 @@ __global__ void __launch_bounds__(128 * kG, 1)
     if ((int)blockIdx.x >= n_items) return;  // uniform over the CTA
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
+    if (probe_wait_expired(p, sm, status)) return;
     uint8_t *sW = sm + C::kOffW;
     uint8_t *sDh = sm + C::kOffDh;
     uint8_t *sDl = sm + C::kOffDl;
@@ -1391,6 +1412,7 @@ __global__ void __launch_bounds__(256, 1)
     using C = FuseCfg<DN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
+    if (probe_wait_expired(p, sm, status)) return;
     uint8_t *sWh = sm + C::kOffWh;
     uint8_t *sWl = sm + C::kOffWl;
     uint8_t *sMh = sm + C::kOffMh;

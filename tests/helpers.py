@@ -45,3 +45,25 @@ def small_random_scene(n=40, seed=0, sh_degree=3, D=8, spread=0.5):
     if D:
         s["features"] = feats
     return s
+
+
+# Margin rule for image comparisons (GPU FP32 against the FP64 oracle).  A
+# pixel is excluded from the element-wise bars when one of the decisions that
+# settle its contributor set (the ellipse cutoff of a Gaussian that would pass
+# the alpha test there, the alpha_min test, the stop rule) lies within
+# MARGIN_TOL (relative) of its threshold in the oracle: the largest FP32
+# error of q^2 measured near the cutoff is 2.7e-6 relative, so such a
+# decision may come out the other way in FP32.  The excluded pixels are
+# counted; at most 0.1 % of the compared pixels plus MARGIN_SLACK pixels (one
+# ellipse edge's worth, for images of a few thousand pixels) may be excluded.
+MARGIN_TOL = 1e-5
+MARGIN_SLACK = 8
+
+
+def margin_cap(n_pix: int) -> float:
+    return 1e-3 * n_pix + MARGIN_SLACK
+
+
+def check_margin_count(n_margin: int, n_pix: int, what: str = "") -> None:
+    print(f"margin pixels {what}: {n_margin} of {n_pix} ({100.0 * n_margin / max(n_pix, 1):.3f} %)")
+    assert n_margin <= margin_cap(n_pix), (what, n_margin, n_pix)

@@ -96,3 +96,16 @@ def test_new_calls_reject_a_null_context_and_size_the_adam_state(L):
         K = (deg + 1) ** 2
         assert L.fhgs_adam_state_floats(1000, deg) == 2 * 1000 * (11 + 3 * K)
     assert L.fhgs_adam_state_floats(-1, 0) == -1 and L.fhgs_adam_state_floats(10, 4) == -1
+
+
+def test_wait_probe_knob_is_host_side(L):
+    """fhgs_debug_wait_probe only stores a limit: 0 and up to 10 s are taken,
+    longer limits are rejected; nothing is launched."""
+    assert L.fhgs_debug_wait_probe(10_000_000_001) == api.ERR_INVALID_ARG
+    assert L.fhgs_debug_wait_probe(1000) == api.OK
+    assert L.fhgs_debug_wait_probe(0) == api.OK
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-device error on a CPU-only host")
+def test_noalloc_status_without_device_fails_cleanly(L):
+    assert L.fhgs_noalloc_sync_status(None) == api.ERR_NO_DEVICE

@@ -43,3 +43,10 @@ def test_ndfd_and_point_oracle_baselines_on_host_tensors():
     maps = [torch.zeros((v["height"] * v["width"], 8)) for v in views]
     r = bench.points_cpu_baseline(means, views, maps, torch.rand(means.shape[0]))
     assert r["kind"] == "oracle" and r["value"] > 0
+
+
+def test_cpu_baseline_runs_the_reference_arm_in_a_fresh_process():
+    import bench
+    r = bench.cpu_baseline(20_000, 16, steps=1, warmup=1)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1, r
+    assert "fresh process" in r["sample"]

@@ -45,11 +45,13 @@ def test_config5_one_full_view_against_oracle():
     seen = den_r > 1e-6
     assert seen.sum() > 2_000, seen.sum()  # the dense ball saturates within its outer shell
     assert np.abs(den_g - den_r).max() <= 1e-4 * max(1.0, den_r.max())
-    # margin rule for fusion: where an oracle decision lies within 1e-5
-    # (relative) of its threshold, FP32 may flip it.  wflip bounds the weight
-    # such flips could move; with unit-norm maps the fused feature then moves
-    # by at most 2 wflip / den, so Gaussians where that could exceed the bar
-    # are excluded and counted.
+    # margin rule for fusion: where an oracle decision that settles a
+    # contributor set lies within 1e-5 (relative) of its threshold, FP32 may
+    # flip it.  wflip bounds the weight such flips could move; with unit-norm
+    # maps the fused feature then moves by at most 2 wflip / den.  Gaussians
+    # where that could exceed the bar are excluded and counted (at most 6 %
+    # of the seen ones; 5.2 % in this view); every other seen Gaussian is held
+    # to the plain 1e-4 bar.
     f_g = out.cpu().numpy().astype(np.float64)
     fn = np.maximum(np.linalg.norm(ref["out"], axis=1), 1e-30)
     risk = 2.0 * ref["wflip"] / np.maximum(den_r, 1e-30) / fn
@@ -63,7 +65,7 @@ def test_config5_one_full_view_against_oracle():
     assert np.percentile(rel[chk], 99) <= 1e-5, stats
     # the excluded ones stay within the bar plus what their flips can explain
     assert np.all(rel[seen] <= 1e-4 + risk[seen]), stats
-    assert (seen & near).sum() <= 0.10 * seen.sum(), stats
+    assert (seen & near).sum() <= 0.06 * seen.sum(), stats
     assert np.all(out.cpu().numpy()[~seen & (den_r == 0)] == 0)
 
 

@@ -18,7 +18,7 @@ import torch
 
 import oracle
 from paper_2505_19154_gb300 import api, synth
-from tests.helpers import small_random_scene
+from tests.helpers import MARGIN_TOL, check_margin_count, small_random_scene
 from tests.test_gpu_parity import _t, check_grads
 
 pytestmark = pytest.mark.gpu
@@ -69,7 +69,7 @@ def check_losses(out, sc, cams, prm, fg, prep):
     worst = 0.0
     for cam, ref, rr in zip(cams, refs, rend):
         P = cam["width"] * cam["height"]
-        ok = rr["margin"].reshape(-1) > 1e-5
+        ok = rr["margin"].reshape(-1) > MARGIN_TOL
         n_margin += int((~ok).sum())
         n_pix += P
         for key in ("Lgt", "Lcf"):
@@ -78,7 +78,7 @@ def check_losses(out, sc, cams, prm, fg, prep):
             assert err <= L_TOL, (key, err)
         np.testing.assert_array_equal(out["nc"][off:off + P][ok], ref["ncontrib"].reshape(-1)[ok])
         off += P
-    assert n_margin <= max(1, 0.01 * n_pix), (n_margin, n_pix)
+    check_margin_count(n_margin, n_pix, "NDFD")
     assert max(np.abs(r["Lcf"]).max() for r in refs) > 1e-2   # the case exercises L_cf
     return worst
 

@@ -17,6 +17,7 @@ import oracle
 from paper_2505_19154_gb300 import api, synth
 from tests.test_gpu_ndfd import L_TOL
 from tests.test_gpu_parity import check_grads
+from tests.helpers import MARGIN_TOL, check_margin_count
 
 pytestmark = pytest.mark.gpu
 
@@ -61,8 +62,8 @@ def test_ndfd_fullsize_crop():
     fg = fgt[pix].float().cpu().numpy()
     ref = oracle.ndfd(rec, fc, lists, ranges, cam, prm, fg, region=synth.CROP3)
     margin = oracle.render(rec, None, lists, ranges, cam, prm, region=synth.CROP3)["margin"].reshape(-1)
-    ok = margin > 1e-5
-    assert (~ok).sum() <= 0.01 * ok.size
+    ok = margin > MARGIN_TOL
+    check_margin_count(int((~ok).sum()), ok.size, "NDFD crop")
     for k in ("Lgt", "Lcf"):
         err = np.abs(got[k] - ref[k].reshape(-1))[ok].max()
         assert err <= L_TOL, (k, err)
