@@ -58,10 +58,13 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="warm-up + one step, no JSON (for ncu)")
-    ap.add_argument("--workload", choices=["render", "fusion", "ndfd", "points"], default="render",
+    ap.add_argument("--workload", choices=["render", "fusion", "ndfd", "points", "train", "batched"],
+                    default="render",
                     help="render: fwd+bwd of the 1080p view (the headline); fusion: 3M Gaussians x 64 views; "
                          "ndfd: the NDFD losses L_gt, L_cf and their backward on the 1080p view; "
-                         "points: the paper's point-to-feature assignment, 3M points x 64 views")
+                         "points: the paper's point-to-feature assignment, 3M points x 64 views; "
+                         "train: one training iteration (render, L1, NDFD, Adam) on the 1080p view; "
+                         "batched: 16 uneven cameras, 500k Gaussians, D=256, one CUDA graph per step")
     ap.add_argument("--views", type=int, default=64, help="fusion: number of views")
     return ap.parse_args()
 
@@ -652,6 +655,7 @@ def fp32_peak(dev, index=0, seconds=0.6):
     meanwhile.  Also reports FLOP per clock per SM at the sampled clock (256
     when all 128 FP32 lanes of an SM retire an FMA every clock)."""
     import ctypes
+    import torch
     from paper_2505_19154_gb300 import api
     L = api.lib()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -809,6 +813,254 @@ def run_ndfd(args):
     print(json.dumps(line), flush=True)
 
 
+BATCH_METRIC = "fwd+bwd Mpix/s, 16 cameras of uneven size in one captured CUDA graph, 500k Gaussians, D=256 BF16"
+BATCH_WORKLOAD = ("500k Gaussians, 16 cameras W~U{640..1600} x H~U{480..900} on a ring, SH degree 3, "
+                  "D=256 BF16 features, fwd+bwd replayed as one CUDA graph, autotuned D split")
+
+
+def batched_cpu_baseline(scene, cams, D, ci=0, steps=3):
+    """The oracle on a bounded sample of the batched workload: projection and
+    FP32 binning of every Gaussian for camera ci, lists of the tiles of its
+    64x64 centre crop, FP64 forward + backward of those 4096 pixels, after
+    one untimed sample."""
+    import oracle
+    from paper_2505_19154_gb300 import synth
+    cam = cams[ci]
+    x0, y0 = (cam["width"] // 2 - 32) // 16 * 16, (cam["height"] // 2 - 32) // 16 * 16
+    reg = (x0, y0, x0 + 64, y0 + 64)
+    prm = dict(sh_degree=3)
+    dC, dF = synth.upstream(ci, 64 * 64, D)
+
+    def one():
+        prep = oracle.prepare(scene, [cam], prm, tile_rect=(x0 // 16, y0 // 16, (x0 + 63) // 16, (y0 + 63) // 16))
+        oracle.forward(scene, [cam], prm, scene["features"], region=reg, prep=prep)
+        oracle.backward(scene, [cam], prm, scene["features"], [dC], [dF], region=reg, prep=prep)
+
+    one()
+    t0 = time.time()
+    for _ in range(steps):
+        one()
+    dt = time.time() - t0
+    return {"value": round(steps * 4096 / dt / 1e6, 6), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"{steps} x (project + FP32-spec binning of all {len(scene['means'])} Gaussians for camera "
+                      f"{ci}, lists of its 64x64 centre crop's tiles, FP64 fwd+bwd of the 4096 pixels, D={D}), "
+                      f"after one untimed sample"}
+
+
+def run_batched(args):
+    """Config 4: the whole fwd+bwd step over 16 cameras of uneven size,
+    captured once in a CUDA graph (api.CapturedStep) and replayed; the D
+    split is chosen by the autotuner on this scene."""
+    import torch
+    from paper_2505_19154_gb300 import api, autotune, synth
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    D = 256
+    scene, cams = synth.config4(rank, n=args.n if args.n != 1_000_000 else 500_000, D=D)
+    t = {k: torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).to(dev)
+         for k in ("means", "scales", "quats", "opacities", "sh")}
+    t["features"] = torch.from_numpy(scene["features"]).to(dev).to(torch.bfloat16)
+    P = sum(c["width"] * c["height"] for c in cams)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4000 + rank)
+    dC = torch.randn((P, 3), generator=gen, device=dev)
+    dF = torch.randn((P, D), generator=gen, device=dev)
+    rast = api.Rasterizer(local, sh_degree=3, path=api.PATH_TC)
+    st = rast.prepare(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams)
+    rast.forward(st, t["features"])
+    tuned = autotune.tune_splits(rast, st, t["features"], dC, dF, cams, use_cache=False)
+    Q, Qpix, U = composited_pairs(st, cams)
+    I = st["n_instances"]
+    del st
+    step = api.CapturedStep(rast, t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], t["features"],
+                            dC, dF, cams)
+    for _ in range(max(args.warmup, 3)):
+        step.replay()
+    torch.cuda.synchronize()
+    if rast.ctx.sync_status() != api.OK:
+        raise RuntimeError("device status after warm-up")
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    n0 = api.Context.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = max(1, args.steps)
+    e0.record()
+    for _ in range(K):
+        step.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    per_replay = None  # kernels inside a graph are not counted by the library's host counter
+    ms = e0.elapsed_time(e1) / K
+    if world > 1:
+        x = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        ms = float(x.item())
+    if rast.ctx.sync_status() != api.OK:
+        raise RuntimeError("device status after timed region")
+    # kernel split: one eager step with the same splits, timed per kernel group
+    rast.ctx.profile(True)
+    n1 = api.Context.launch_count()
+    st = rast.prepare(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams)
+    rast.forward(st, t["features"])
+    rast.backward(st, dC, dF)
+    torch.cuda.synchronize()
+    per_replay = api.Context.launch_count() - n1
+    prof = rast.ctx.profile_read()
+    rast.ctx.profile(False)
+    tot = sum(v[1] for v in prof.values())
+    peaks = load_peaks()
+    N = len(scene["means"])
+    algo = algorithmic_bytes(P, N, D, I, U)
+    per = {}
+    for k, (c, tm) in prof.items():
+        sec = tm / max(c, 1) * 1e-3
+        per[k] = {"launches": c, "ms": round(sec * 1e3, 4), "share": round(tm / max(tot, 1e-9), 4)}
+        base = k.replace("_tc", "").replace("_fp32", "")
+        if base in algo:
+            per[k]["bytes"] = algo[base]
+            per[k]["hbm_frac"] = round(algo[base] / sec / 1e9 / peaks["hbm"], 4)
+    dom = max(prof, key=lambda k: prof[k][1])
+    base = dom.replace("_tc", "")
+    roof = None
+    if base in algo:
+        ach = algo[base] / (per[dom]["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peaks["hbm"], "unit": "GB/s",
+                "frac": round(ach / peaks["hbm"], 4),
+                "peak_source": ("of measured" if peaks["src"] == "measured" else "of fallback") + " (hbm_gbs)",
+                "traffic": None, "algorithmic_bytes": algo[base]}
+    e2e = None
+    if not args.no_e2e and world == 1:
+        h_in = {"means": t["means"], "scales": t["scales"], "quats": t["quats"], "opacities": t["opacities"],
+                "sh": t["sh"], "features": t["features"], "grad_rgb": dC, "grad_feat": dF}
+        h_in = {k: v.cpu().pin_memory() for k, v in h_in.items()}
+        pipe = api.HostPipeline(rast, cams, h_in)
+        pipe.start()
+        for _ in range(2):
+            pipe.step()
+        pipe.finish()
+        torch.cuda.synchronize()
+        bi, bo = pipe.bytes_per_step()
+        Ke = 3
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        pipe.start()
+        for _ in range(Ke):
+            pipe.step()
+        pipe.finish()
+        f1.record()
+        torch.cuda.synchronize()
+        mse = f0.elapsed_time(f1) / Ke
+        del pipe, h_in
+        e2e = {"value": round(P / (mse * 1e-3) / 1e6, 2), "unit": UNIT, "ms_per_step": round(mse, 3),
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo), "api": "api.HostPipeline (eager)"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = batched_cpu_baseline(scene, cams, D)
+    if rank == 0:
+        line = {"metric": BATCH_METRIC, "value": round(P * world / (ms * 1e-3) / 1e6, 2), "unit": UNIT,
+                "n_gpus": world, "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                "data": "synthetic",
+                "config": {"workload": BATCH_WORKLOAD, "gaussians": N, "cameras": len(cams), "pixels": P,
+                           "feature_dim": D, "d_split": {"fwd": tuned["fwd"], "bwd": tuned["bwd"]},
+                           "tile_instances": I, "composited_pairs_tile": Q, "composited_pairs_pixel": Qpix,
+                           "gaussians_walked": U, "graph": "one CUDA graph per step (api.CapturedStep)",
+                           "l2": "inputs larger than L2 (dL/dfeat 12.7 GB)",
+                           "parallelism": f"independent view sets, {world} GPU(s)"},
+                "roofline": roof, "kernels": per, "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
+                "gpu_launches": int(per_replay) * K}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+TRAIN_METRIC = "training iteration Mpix/s at 1M Gaussians, 1080p, NDFD D=512 BF16 (render + L1 + NDFD + Adam)"
+TRAIN_WORKLOAD = ("1M Gaussians, 1920x1080 view, SH degree 3, D=512 BF16 frozen features and ground-truth map: "
+                  "one Adam iteration of L = L_rgb + L_gt + L_cf")
+
+
+def run_train(args):
+    """One training iteration per step (App. A, Alg. 1 loop body; Sec. 3.3):
+    projection, binning, RGB forward, L1, NDFD forward, render backward,
+    NDFD backward, projection backward, Adam over both gradient sets -- the
+    composed TrainStep over the library backend."""
+    import torch
+    from paper_2505_19154_gb300 import api, synth
+    from paper_2505_19154_gb300.train import LibraryBackend, TrainStep
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return   # one view: a single-GPU measurement
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, cams = synth.config3(rank, n=args.n, D=0)
+    cam = cams[0]
+    D = args.D
+    # raw parameters of the 3DGS family (host-side input preparation)
+    raw = {"means": scene["means"], "log_scales": np.log(scene["scales"]), "quats": scene["quats"],
+           "logit_opacities": np.log(scene["opacities"] / (1.0 - scene["opacities"])), "sh": scene["sh"]}
+    raw = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).to(dev) for k, v in raw.items()}
+    feats, fgt = synth.ndfd_inputs_device(rank, args.n, cams, D, dev)
+    P = fgt.shape[0]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(9_100_003 + rank)
+    target = torch.rand((P, 3), generator=gen, device=dev)
+    be = LibraryBackend(local, sh_degree=3)
+    act = be.activate(raw)
+    st0 = be.rast.prepare(raw["means"], act["scales"], raw["quats"], act["opacities"], raw["sh"], [cam])
+    be.rast.capacity = int(st0["n_instances"] * 1.2) + 1024   # room for the instances to grow as Adam moves them
+    I = st0["n_instances"]
+    del st0
+    step = TrainStep(be, raw, 3, feats)
+    W_ = max(args.warmup, 3)
+    for _ in range(W_):
+        step(cam, target, fgt)
+    torch.cuda.synchronize()
+    if be.rast.ctx.sync_status() != api.OK:
+        raise RuntimeError("device status after warm-up")
+    be.rast.ctx.profile(True)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    n0 = api.Context.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = max(1, args.steps)
+    e0.record()
+    for _ in range(K):
+        out = step(cam, target, fgt)
+    e1.record()
+    torch.cuda.synchronize()
+    launches = api.Context.launch_count() - n0
+    ck = clocks.stop()
+    prof = be.rast.ctx.profile_read()
+    if be.rast.ctx.sync_status() != api.OK:
+        raise RuntimeError("device status after timed region")
+    ms = e0.elapsed_time(e1) / K
+    tot = sum(v[1] for v in prof.values())
+    per = {k: {"launches": c, "ms": round(t / max(c, 1), 4), "share": round(t / max(tot, 1e-9), 4)}
+           for k, (c, t) in prof.items()}
+    dom = max(prof, key=lambda k: prof[k][1])
+    losses = {k: round(float(out[k].item()), 6) for k in ("total", "rgb", "gt", "cf")}
+    line = {"metric": TRAIN_METRIC, "value": round(P / (ms * 1e-3) / 1e6, 2), "unit": UNIT, "n_gpus": 1,
+            "steps": K, "warmup": W_, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (NDFD inputs on the device)",
+            "config": {"workload": TRAIN_WORKLOAD, "gaussians": args.n, "width": cam["width"],
+                       "height": cam["height"], "feature_dim": D, "tile_instances_at_start": I,
+                       "l2": "inputs larger than L2 (features 1 GB, ground-truth map 2.1 GB)",
+                       "step": "activation + project + bin/sort + render fwd (RGB) + L1 + NDFD fwd + render bwd + "
+                               "NDFD bwd + projection bwd (x2) + Adam"},
+            "dominant_kernel": dom, "kernels": per, "losses_last_step": losses, "roofline": None,
+            "e2e": None, "cpu_baseline": None, "clocks": ck, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -819,6 +1071,10 @@ def main():
         run_ndfd(args)
     elif args.workload == "points":
         run_points(args)
+    elif args.workload == "train":
+        run_train(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

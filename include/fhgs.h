@@ -259,9 +259,12 @@ fhgs_status fhgs_l1_loss(fhgs_ctx *ctx, int64_t m, const float *a, const float *
  * log-scales, unnormalised quaternions, opacity logits and SH (all device
  * float32, updated in place; the rasterizer reads means, quats and SH as
  * they are, and scales = exp(log-scales), opacities = sigmoid(logits)).
- * grad_* are the gradients with respect to the ACTIVATED values, as
- * fhgs_render_bwd / fhgs_ndfd_bwd write them; the update takes them to the
- * raw ones (d/dlog s = s d/ds, d/dlogit = op (1 - op) d/dop), then
+ * grads[0 .. n_grad_sets-1] (1 to FHGS_MAX_GRAD_SETS sets, host array of
+ * device pointers) are gradients with respect to the ACTIVATED values, as
+ * fhgs_render_bwd / fhgs_ndfd_bwd write them; the update adds the sets
+ * element by element (the loss terms' gradients add, Sec. 3.3), takes the
+ * sum to the raw parameters (d/dlog s = s d/ds, d/dlogit = op (1 - op)
+ * d/dop), then
  *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
  *   theta -= lr m / (1 - b1^t) / (sqrt(v / (1 - b2^t)) + eps).
  * state: fhgs_adam_state_floats(n, sh_degree) device floats, zeroed before
@@ -272,11 +275,27 @@ typedef struct fhgs_adam {
     float beta1, beta2, eps;
     int32_t step;         /* t >= 1 of this update */
 } fhgs_adam;
+typedef struct fhgs_grads {
+    const float *means, *scales, *quats, *opacities, *sh; /* device, [n][3], [n][3], [n][4], [n], [n][K][3] */
+} fhgs_grads;
+#define FHGS_MAX_GRAD_SETS 4
 int64_t fhgs_adam_state_floats(int64_t n, int sh_degree);
 fhgs_status fhgs_adam_gaussians(fhgs_ctx *ctx, int64_t n, int sh_degree, float *means, float *log_scales, float *quats,
-                                float *logit_opacities, float *sh, const float *grad_means, const float *grad_scales,
-                                const float *grad_quats, const float *grad_opac, const float *grad_sh, float *state,
-                                const fhgs_adam *opt, float *scales_out, float *opacities_out, void *stream);
+                                float *logit_opacities, float *sh, const fhgs_grads *grads, int n_grad_sets,
+                                float *state, const fhgs_adam *opt, float *scales_out, float *opacities_out,
+                                void *stream);
+
+/* The activated parameters the rasterizer reads, from the raw ones:
+ * scales_out = exp(log_scales) [n][3], opacities_out = sigmoid(logits) [n]
+ * (all device float32), the same values fhgs_adam_gaussians writes after an
+ * update; for the first forward of a training run. */
+fhgs_status fhgs_activate_gaussians(fhgs_ctx *ctx, int64_t n, const float *log_scales, const float *logit_opacities,
+                                    float *scales_out, float *opacities_out, void *stream);
+
+/* out[0] += sum of x[0 .. m-1] (device float32; out accumulated, zero it
+ * first): the per-pixel NDFD loss maps' totals, L_gt and L_cf of Sec. 3.3,
+ * in FP32 partial sums. */
+fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void *stream);
 
 /* ------------------------------------------------------------------ NDFD -- */
 /* Non-differentiable feature driving (Sec. 3.2; App. A "NDFD"): per pixel,

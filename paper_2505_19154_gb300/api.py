@@ -28,7 +28,8 @@ EXPORTS = ["fhgs_create", "fhgs_destroy", "fhgs_last_error", "fhgs_status_string
            "fhgs_project", "fhgs_bin_sort", "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features",
            "fhgs_profile_enable", "fhgs_profile_read", "fhgs_launch_count", "fhgs_render_bwd_noalloc",
            "fhgs_ndfd_fwd", "fhgs_ndfd_bwd", "fhgs_point_features", "fhgs_l1_loss", "fhgs_adam_state_floats",
-           "fhgs_adam_gaussians", "fhgs_noalloc_sync_status", "fhgs_debug_wait_probe", "fhgs_ffma_probe"]
+           "fhgs_adam_gaussians", "fhgs_noalloc_sync_status", "fhgs_debug_wait_probe", "fhgs_ffma_probe",
+           "fhgs_activate_gaussians", "fhgs_sum"]
 MAX_POINT_VIEWS = 4096  # FHGS_MAX_POINT_VIEWS of include/fhgs.h
 NDFD_K, NDFD_LAMBDA = 20.0, 0.5  # the activation's slope and threshold (Sec. 4)
 
@@ -50,6 +51,11 @@ class Params(ctypes.Structure):
 class Adam(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float * 5), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
 
 
 class Gaussians(ctypes.Structure):
@@ -129,7 +135,10 @@ def lib():
         L.fhgs_l1_loss.argtypes = [vp, i64, f32p, f32p, f32, f32p, f32p, vp]
         L.fhgs_adam_state_floats.argtypes = [i64, i32]
         L.fhgs_adam_state_floats.restype = i64
-        L.fhgs_adam_gaussians.argtypes = [vp, i64, i32] + [f32p] * 11 + [ctypes.POINTER(Adam), f32p, f32p, vp]
+        L.fhgs_adam_gaussians.argtypes = [vp, i64, i32] + [f32p] * 5 + [ctypes.POINTER(Grads), i32, f32p,
+                                                                       ctypes.POINTER(Adam), f32p, f32p, vp]
+        L.fhgs_activate_gaussians.argtypes = [vp, i64, f32p, f32p, f32p, f32p, vp]
+        L.fhgs_sum.argtypes = [vp, i64, f32p, f32p, vp]
         L.fhgs_profile_enable.argtypes = [vp, i32]
         L.fhgs_profile_read.argtypes = [vp, ctypes.c_char_p, i64]
         L.fhgs_ffma_probe.argtypes = [i32, i32, vp]
@@ -139,6 +148,7 @@ def lib():
         for name in ("fhgs_create", "fhgs_reserve", "fhgs_sync_status", "fhgs_project", "fhgs_bin_sort",
                      "fhgs_render_fwd", "fhgs_render_bwd", "fhgs_fuse_features", "fhgs_ndfd_fwd", "fhgs_ndfd_bwd",
                      "fhgs_point_features", "fhgs_l1_loss", "fhgs_adam_gaussians", "fhgs_profile_enable",
+                     "fhgs_activate_gaussians", "fhgs_sum",
                      "fhgs_profile_read"):
             getattr(L, name).restype = i32
         _lib = L
@@ -311,12 +321,18 @@ def l1_loss(ctx: "Context", a, b, loss=None, want_grad: bool = True, stream=None
     return loss, grad
 
 
-def adam_gaussians(ctx: "Context", raw: dict, grads: dict, state, step: int, lr, sh_degree: int,
+def adam_gaussians(ctx: "Context", raw: dict, grads, state, step: int, lr, sh_degree: int,
                    beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15, scales_out=None, opac_out=None,
                    stream=None):
     """fhgs_adam_gaussians: one Adam update of raw = {means, log_scales,
     quats, logit_opacities, sh} (in place) from the activated-parameter
-    gradients {means, scales, quats, opacities, sh}.  lr: five rates."""
+    gradients {means, scales, quats, opacities, sh} -- one dict, or a list of
+    up to four whose sum the kernel takes.  lr: five rates."""
+    sets = [grads] if isinstance(grads, dict) else list(grads)
+    arr = (Grads * len(sets))()
+    for i, g in enumerate(sets):
+        arr[i].means, arr[i].scales, arr[i].quats = _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"])
+        arr[i].opacities, arr[i].sh = _ptr(g["opacities"]), _ptr(g["sh"])
     opt = Adam()
     for k in range(5):
         opt.lr[k] = float(lr[k])
@@ -324,9 +340,27 @@ def adam_gaussians(ctx: "Context", raw: dict, grads: dict, state, step: int, lr,
     n = int(raw["means"].shape[0])
     ctx.check(lib().fhgs_adam_gaussians(
         ctx.h, n, int(sh_degree), _ptr(raw["means"]), _ptr(raw["log_scales"]), _ptr(raw["quats"]),
-        _ptr(raw["logit_opacities"]), _ptr(raw["sh"]), _ptr(grads["means"]), _ptr(grads["scales"]),
-        _ptr(grads["quats"]), _ptr(grads["opacities"]), _ptr(grads["sh"]), _ptr(state), ctypes.byref(opt),
+        _ptr(raw["logit_opacities"]), _ptr(raw["sh"]), arr, len(sets), _ptr(state), ctypes.byref(opt),
         _ptr(scales_out), _ptr(opac_out), Context.stream_ptr(stream)))
+
+
+def activate_gaussians(ctx: "Context", log_scales, logit_opacities, stream=None):
+    """fhgs_activate_gaussians: (exp(log_scales), sigmoid(logits)) on the device."""
+    n = int(log_scales.shape[0])
+    scales = torch.empty((n, 3), dtype=torch.float32, device=log_scales.device)
+    opac = torch.empty(n, dtype=torch.float32, device=log_scales.device)
+    ctx.check(lib().fhgs_activate_gaussians(ctx.h, n, _ptr(log_scales), _ptr(logit_opacities), _ptr(scales),
+                                            _ptr(opac), Context.stream_ptr(stream)))
+    return scales, opac
+
+
+def sum_f32(ctx: "Context", x, out=None, stream=None):
+    """fhgs_sum: the sum of all elements of x, as a device float[1]
+    (accumulated into `out` when given)."""
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float32, device=x.device)
+    ctx.check(lib().fhgs_sum(ctx.h, int(x.numel()), _ptr(x.contiguous()), _ptr(out), Context.stream_ptr(stream)))
+    return out
 
 
 def adam_state(n: int, sh_degree: int, device) -> torch.Tensor:

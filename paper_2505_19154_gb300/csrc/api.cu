@@ -553,9 +553,9 @@ int64_t fhgs_adam_state_floats(int64_t n, int sh_degree) {
 }
 
 fhgs_status fhgs_adam_gaussians(fhgs_ctx *ctx, int64_t n, int sh_degree, float *means, float *log_scales, float *quats,
-                                float *logit_opacities, float *sh, const float *grad_means, const float *grad_scales,
-                                const float *grad_quats, const float *grad_opac, const float *grad_sh, float *state,
-                                const fhgs_adam *opt, float *scales_out, float *opacities_out, void *stream) {
+                                float *logit_opacities, float *sh, const fhgs_grads *grads, int n_grad_sets,
+                                float *state, const fhgs_adam *opt, float *scales_out, float *opacities_out,
+                                void *stream) {
     if (!ctx) return FHGS_ERR_INVALID_ARG;
     if (n < 0 || n >= (1ll << 31)) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad Gaussian count");
     if (sh_degree < 0 || sh_degree > 3) return fail(ctx, FHGS_ERR_UNSUPPORTED, "sh_degree must be 0..3");
@@ -563,16 +563,49 @@ fhgs_status fhgs_adam_gaussians(fhgs_ctx *ctx, int64_t n, int sh_degree, float *
     if (opt->step < 1) return fail(ctx, FHGS_ERR_INVALID_ARG, "the Adam step number starts at 1");
     if (!(opt->beta1 >= 0.f && opt->beta1 < 1.f && opt->beta2 >= 0.f && opt->beta2 < 1.f && opt->eps >= 0.f))
         return fail(ctx, FHGS_ERR_INVALID_ARG, "bad Adam constants");
-    if (n > 0 && (!means || !log_scales || !quats || !logit_opacities || !sh || !grad_means || !grad_scales ||
-                  !grad_quats || !grad_opac || !grad_sh || !state))
+    if (n_grad_sets < 1 || n_grad_sets > FHGS_MAX_GRAD_SETS || !grads)
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "1..4 gradient sets");
+    if (n > 0 && (!means || !log_scales || !quats || !logit_opacities || !sh || !state))
         return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL buffer");
+    for (int k = 0; k < n_grad_sets && n > 0; ++k)
+        if (!grads[k].means || !grads[k].scales || !grads[k].quats || !grads[k].opacities || !grads[k].sh)
+            return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL gradient buffer");
     FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     {
         Prof pr(ctx, "adam", st);
         launch_adam_gaussians(n, (sh_degree + 1) * (sh_degree + 1), means, log_scales, quats, logit_opacities, sh,
-                              grad_means, grad_scales, grad_quats, grad_opac, grad_sh, state, opt, scales_out,
-                              opacities_out, st);
+                              grads, n_grad_sets, state, opt, scales_out, opacities_out, st);
+    }
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_activate_gaussians(fhgs_ctx *ctx, int64_t n, const float *log_scales, const float *logit_opacities,
+                                    float *scales_out, float *opacities_out, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    if (n < 0 || n >= (1ll << 31)) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad Gaussian count");
+    if (n > 0 && (!log_scales || !logit_opacities || !scales_out || !opacities_out))
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL buffer");
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        Prof pr(ctx, "activate", st);
+        launch_activate(n, log_scales, logit_opacities, scales_out, opacities_out, st);
+    }
+    FHGS_CUDA(ctx, cudaGetLastError());
+    return FHGS_OK;
+}
+
+fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void *stream) {
+    if (!ctx) return FHGS_ERR_INVALID_ARG;
+    if (m < 0) return fail(ctx, FHGS_ERR_INVALID_ARG, "negative size");
+    if (!out || (m > 0 && !x)) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL buffer");
+    FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        Prof pr(ctx, "sum", st);
+        launch_sum(m, x, out, ctx->sm_count, st);
     }
     FHGS_CUDA(ctx, cudaGetLastError());
     return FHGS_OK;

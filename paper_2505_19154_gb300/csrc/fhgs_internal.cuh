@@ -206,9 +206,11 @@ void launch_point_features(long long n, const float *means, const PFView *views,
 void launch_l1_loss(long long m, const float *a, const float *b, float inv_count, float *loss, float *grad,
                     int sm_count, cudaStream_t st);
 void launch_adam_gaussians(long long n, int K, float *means, float *log_s, float *quats, float *logit, float *sh,
-                           const float *g_means, const float *g_scales, const float *g_quats, const float *g_opac,
-                           const float *g_sh, float *state, const fhgs_adam *opt, float *scales_out, float *opac_out,
-                           cudaStream_t st);
+                           const fhgs_grads *grads, int n_sets, float *state, const fhgs_adam *opt, float *scales_out,
+                           float *opac_out, cudaStream_t st);
+void launch_activate(long long n, const float *log_s, const float *logit, float *scales, float *opac,
+                     cudaStream_t st);
+void launch_sum(long long m, const float *x, float *out, int sm_count, cudaStream_t st);
 
 // NDFD losses and their backward (ndfd.cu): D in {32, 64, 128, 256, 512}
 bool ndfd_supported(int D);

@@ -46,15 +46,24 @@ __device__ __forceinline__ float adam_one(float theta, float g, float &m, float 
     return theta - lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
 }
 
+// Up to four gradient sets (render, NDFD, ...) that the update sums.
+struct GradSets {
+    const float *means[4], *scales[4], *quats[4], *opac[4], *sh[4];
+    int n;
+};
+
+__device__ __forceinline__ float gsum(const float *const *g, int ns, long long j) {
+    float s = g[0][j];
+    for (int k = 1; k < ns; ++k) s += g[k][j];
+    return s;
+}
+
 __global__ void __launch_bounds__(256) k_adam_gaussians(long long n, int K3, float *means, float *log_s, float *quats,
-                                                        float *logit, float *sh, const float *__restrict__ g_means,
-                                                        const float *__restrict__ g_scales,
-                                                        const float *__restrict__ g_quats,
-                                                        const float *__restrict__ g_opac,
-                                                        const float *__restrict__ g_sh, float *state, AdamArgs a,
+                                                        float *logit, float *sh, GradSets gs, float *state, AdamArgs a,
                                                         float *scales_out, float *opac_out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int ns = gs.n;
     // state: m and v of each group, group after group, n rows each
     float *m_mu = state, *v_mu = m_mu + 3 * n;
     float *m_ls = v_mu + 3 * n, *v_ls = m_ls + 3 * n;
@@ -63,27 +72,54 @@ __global__ void __launch_bounds__(256) k_adam_gaussians(long long n, int K3, flo
     float *m_sh = v_lo + n, *v_sh = m_sh + K3 * n;
     for (int k = 0; k < 3; ++k) {
         const long long j = 3 * i + k;
-        means[j] = adam_one(means[j], g_means[j], m_mu[j], v_mu[j], a.lr[0], a);
+        means[j] = adam_one(means[j], gsum(gs.means, ns, j), m_mu[j], v_mu[j], a.lr[0], a);
     }
     for (int k = 0; k < 3; ++k) {
         const long long j = 3 * i + k;
-        const float g = g_scales[j] * expf(log_s[j]);
+        const float g = gsum(gs.scales, ns, j) * expf(log_s[j]);
         log_s[j] = adam_one(log_s[j], g, m_ls[j], v_ls[j], a.lr[1], a);
         if (scales_out) scales_out[j] = expf(log_s[j]);
     }
     for (int k = 0; k < 4; ++k) {
         const long long j = 4 * i + k;
-        quats[j] = adam_one(quats[j], g_quats[j], m_q[j], v_q[j], a.lr[2], a);
+        quats[j] = adam_one(quats[j], gsum(gs.quats, ns, j), m_q[j], v_q[j], a.lr[2], a);
     }
     {
         const float op = 1.f / (1.f + expf(-logit[i]));
-        const float g = g_opac[i] * op * (1.f - op);
+        const float g = gsum(gs.opac, ns, i) * op * (1.f - op);
         logit[i] = adam_one(logit[i], g, m_lo[i], v_lo[i], a.lr[3], a);
         if (opac_out) opac_out[i] = 1.f / (1.f + expf(-logit[i]));
     }
     for (int k = 0; k < K3; ++k) {
         const long long j = (long long)K3 * i + k;
-        sh[j] = adam_one(sh[j], g_sh[j], m_sh[j], v_sh[j], a.lr[4], a);
+        sh[j] = adam_one(sh[j], gsum(gs.sh, ns, j), m_sh[j], v_sh[j], a.lr[4], a);
+    }
+}
+
+// The activated values the rasterizer reads: scales = exp(log-scales),
+// opacities = sigmoid(logits), as the Adam kernel writes them after an update.
+__global__ void __launch_bounds__(256) k_activate(long long n, const float *__restrict__ log_s,
+                                                  const float *__restrict__ logit, float *scales, float *opac) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < 3; ++k) scales[3 * i + k] = expf(log_s[3 * i + k]);
+    opac[i] = 1.f / (1.f + expf(-logit[i]));
+}
+
+// out[0] += sum x (block partial sums, one float atomic per block).
+__global__ void __launch_bounds__(256) k_sum(long long m, const float *__restrict__ x, float *out) {
+    float s = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+        s += x[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ float part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(out, t);
     }
 }
 
@@ -99,10 +135,19 @@ void launch_l1_loss(long long m, const float *a, const float *b, float inv_count
 }
 
 void launch_adam_gaussians(long long n, int K, float *means, float *log_s, float *quats, float *logit, float *sh,
-                           const float *g_means, const float *g_scales, const float *g_quats, const float *g_opac,
-                           const float *g_sh, float *state, const fhgs_adam *opt, float *scales_out, float *opac_out,
-                           cudaStream_t st) {
+                           const fhgs_grads *grads, int n_sets, float *state, const fhgs_adam *opt, float *scales_out,
+                           float *opac_out, cudaStream_t st) {
     if (n == 0) return;
+    GradSets gs;
+    gs.n = n_sets;
+    for (int k = 0; k < 4; ++k) {
+        const fhgs_grads &g = grads[k < n_sets ? k : 0];
+        gs.means[k] = g.means;
+        gs.scales[k] = g.scales;
+        gs.quats[k] = g.quats;
+        gs.opac[k] = g.opacities;
+        gs.sh[k] = g.sh;
+    }
     AdamArgs a;
     for (int k = 0; k < 5; ++k) a.lr[k] = opt->lr[k];
     a.b1 = opt->beta1;
@@ -111,9 +156,23 @@ void launch_adam_gaussians(long long n, int K, float *means, float *log_s, float
     a.c1 = 1.f - powf(opt->beta1, (float)opt->step);
     a.c2 = 1.f - powf(opt->beta2, (float)opt->step);
     note_launch(1);
-    k_adam_gaussians<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, 3 * K, means, log_s, quats, logit, sh, g_means,
-                                                                  g_scales, g_quats, g_opac, g_sh, state, a,
-                                                                  scales_out, opac_out);
+    k_adam_gaussians<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, 3 * K, means, log_s, quats, logit, sh, gs,
+                                                                  state, a, scales_out, opac_out);
+}
+
+void launch_activate(long long n, const float *log_s, const float *logit, float *scales, float *opac,
+                     cudaStream_t st) {
+    if (n == 0) return;
+    note_launch(1);
+    k_activate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, log_s, logit, scales, opac);
+}
+
+void launch_sum(long long m, const float *x, float *out, int sm_count, cudaStream_t st) {
+    if (m == 0) return;
+    note_launch(1);
+    const long long want = (m + 255) / 256;
+    const unsigned blocks = (unsigned)min(want, (long long)sm_count * 8);
+    k_sum<<<blocks, 256, 0, st>>>(m, x, out);
 }
 
 }  // namespace fhgs

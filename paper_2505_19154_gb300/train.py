@@ -76,13 +76,14 @@ class LibraryBackend:
         self.api, self.torch = api, torch
         self.rast = api.Rasterizer(device, sh_degree=sh_degree, **params)
         self.dev = torch.device("cuda", device)
+        self._up = {}
 
     def adam_init(self, raw, sh_degree):
         return self.api.adam_state(int(raw["means"].shape[0]), sh_degree, self.dev)
 
     def activate(self, raw):
-        torch = self.torch
-        return dict(scales=torch.exp(raw["log_scales"]), opacities=torch.sigmoid(raw["logit_opacities"]))
+        s, o = self.api.activate_gaussians(self.rast.ctx, raw["log_scales"], raw["logit_opacities"])
+        return dict(scales=s, opacities=o)
 
     def prepare(self, params, cam):
         return self.rast.prepare(params["means"], params["scales"], params["quats"], params["opacities"],
@@ -100,19 +101,24 @@ class LibraryBackend:
         return self.rast.ndfd_forward(st, features, feat_gt)
 
     def total(self, x):
-        return x.sum()
+        return self.api.sum_f32(self.rast.ctx, x)
 
     def backward(self, st, grad_rgb):
         return self.rast.backward(st, grad_rgb, None)
 
     def ndfd_backward(self, st, features, feat_gt, a, b):
+        # the loss terms are pixel means, so the upstream gradients are the
+        # constants lambda / P, filled once per (size, value) and reused
         P = feat_gt.shape[0]
-        full = self.torch.full
-        return self.rast.ndfd_backward(st, features, feat_gt, full((P,), a, device=self.dev),
-                                       full((P,), b, device=self.dev))
+        key = (P, a, b)
+        if key not in self._up:
+            self._up = {key: (self.torch.full((P,), a, device=self.dev), self.torch.full((P,), b, device=self.dev))}
+        ua, ub = self._up[key]
+        return self.rast.ndfd_backward(st, features, feat_gt, ua, ub)
 
     def add(self, g1, g2):
-        return {k: g1[k] + g2[k] for k in ("means", "scales", "quats", "opacities", "sh")}
+        # the Adam kernel adds the gradient sets itself
+        return [g1, g2]
 
     def adam(self, raw, grads, state, t, lr, beta1, beta2, eps):
         n = int(raw["means"].shape[0])

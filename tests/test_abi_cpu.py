@@ -91,7 +91,10 @@ def test_new_calls_reject_a_null_context_and_size_the_adam_state(L):
                                  None) == api.ERR_INVALID_ARG
     assert L.fhgs_l1_loss(None, 0, None, None, 1.0, None, None, None) == api.ERR_INVALID_ARG
     opt = api.Adam()
-    assert L.fhgs_adam_gaussians(None, 0, 0, *([None] * 11), ctypes.byref(opt), None, None, None) == api.ERR_INVALID_ARG
+    assert L.fhgs_adam_gaussians(None, 0, 0, *([None] * 5), None, 1, None, ctypes.byref(opt), None, None,
+                                 None) == api.ERR_INVALID_ARG
+    assert L.fhgs_activate_gaussians(None, 0, None, None, None, None, None) == api.ERR_INVALID_ARG
+    assert L.fhgs_sum(None, 0, None, None, None) == api.ERR_INVALID_ARG
     for deg in range(4):
         K = (deg + 1) ** 2
         assert L.fhgs_adam_state_floats(1000, deg) == 2 * 1000 * (11 + 3 * K)

@@ -59,7 +59,8 @@ def _case(path, feat_dtype, n, cams, seed, dev):
     ref = rast.backward(st, dC, dF)
     torch.cuda.synchronize()
     assert rast.ctx.sync_status() == api.OK
-    return dict(rast=rast, st=st, feats=feats, D=D, n=n, dC=dC, dF=dF, ref=ref)
+    # the prepared state holds raw pointers only: keep the inputs alive with it
+    return dict(rast=rast, st=st, feats=feats, D=D, n=n, dC=dC, dF=dF, ref=ref, keep=(means, scales, q, opac, sh))
 
 
 def _noalloc(c, dev, check_free=False):
