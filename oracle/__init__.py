@@ -599,9 +599,11 @@ def bin_surfel_f32(means, quats, scales2, cam: dict, params: dict | None = None)
     return dict(pix=pix, tile=tile, ntiles=nt, dbits=db)
 
 
-def render_2dgs(surfels: dict, cam: dict, params: dict | None = None, region=None) -> dict:
+def render_2dgs(surfels: dict, cam: dict, params: dict | None = None, region=None, feats=None) -> dict:
     """Tiled surfel render: the binary32 binning rule, per-tile lists sorted
-    by (tile, depth bits, id), and each pixel's walk of its tile's list."""
+    by (tile, depth bits, id), and each pixel's walk of its tile's list.
+    feats [n, D] (optional) are blended with the same weights.  Also returns
+    each pixel's margin (decisions settling its contributor set)."""
     W, H = int(cam["width"]), int(cam["height"])
     x0, y0, x1, y1 = region if region is not None else (0, 0, W, H)
     npx = (x1 - x0) * (y1 - y0)
@@ -613,13 +615,18 @@ def render_2dgs(surfels: dict, cam: dict, params: dict | None = None, region=Non
     rgb = np.zeros((npx, 3))
     T = np.zeros(npx)
     nc = np.zeros(npx, np.int32)
+    margin = np.zeros(npx)
+    D = 0 if feats is None else int(np.asarray(feats).shape[1])
+    fa = None if feats is None else _f64(feats).reshape(n, D)
+    F = np.zeros((npx, D)) if feats is not None else None
     lib().orc_render_2dgs(_p(mu), _p(_f64(surfels["quats"]).reshape(n, 4)), _p(_f64(surfels["scales2"]).reshape(n, 2)),
                           _p(_f64(surfels["opacities"]).reshape(n)), _p(_f64(surfels["rgb"]).reshape(n, 3)),
-                          _p(np.ascontiguousarray(lists["gids"], np.uint32)),
+                          _p(fa), ctypes.c_int(D), _p(np.ascontiguousarray(lists["gids"], np.uint32)),
                           _p(np.ascontiguousarray(_cam_ranges(lists, 0), np.uint32)), _p(camera_array(cam)),
-                          _p(params_array(params)), x0, y0, x1, y1, _p(rgb), _p(T), _p(nc))
+                          _p(params_array(params)), x0, y0, x1, y1, _p(rgb), _p(F), _p(T), _p(nc), _p(margin))
     hh, ww = y1 - y0, x1 - x0
-    return dict(rgb=rgb.reshape(hh, ww, 3), T=T.reshape(hh, ww), ncontrib=nc.reshape(hh, ww), bins=b, lists=lists)
+    return dict(rgb=rgb.reshape(hh, ww, 3), T=T.reshape(hh, ww), ncontrib=nc.reshape(hh, ww), bins=b, lists=lists,
+                margin=margin.reshape(hh, ww), feat=None if F is None else F.reshape(hh, ww, D))
 
 
 def splat_uv_T(means, quats, scales2, cam: dict, px, py) -> dict:
@@ -634,9 +641,10 @@ def splat_uv_T(means, quats, scales2, cam: dict, px, py) -> dict:
     return dict(u=u, v=v, depth=dep)
 
 
-def render_2dgs_bwd(surfels: dict, cam: dict, params: dict | None, dC, region=None) -> dict:
-    """Gradients of sum_p dC[p] . rgb[p] of the tiled surfel render
-    (render_2dgs) with respect to means, quats, scales2, opacities and rgb."""
+def render_2dgs_bwd(surfels: dict, cam: dict, params: dict | None, dC, region=None, feats=None, dF=None) -> dict:
+    """Gradients of sum_p dC[p] . rgb[p] (+ dF[p] . feat[p] with features)
+    of the tiled surfel render (render_2dgs) with respect to means, quats,
+    scales2, opacities, rgb (and features)."""
     W, H = int(cam["width"]), int(cam["height"])
     x0, y0, x1, y1 = region if region is not None else (0, 0, W, H)
     mu = _f64(surfels["means"]).reshape(-1, 3)
@@ -646,14 +654,18 @@ def render_2dgs_bwd(surfels: dict, cam: dict, params: dict | None, dC, region=No
     lists = tile_lists([b], [cam], params)
     out = dict(means=np.zeros((n, 3)), quats=np.zeros((n, 4)), scales2=np.zeros((n, 2)), opacities=np.zeros(n),
                rgb=np.zeros((n, 3)))
+    D = 0 if feats is None else int(np.asarray(feats).shape[1])
+    fa = None if feats is None else _f64(feats).reshape(n, D)
+    dFa = None if (feats is None or dF is None) else _f64(dF).reshape(-1, D)
+    out["features"] = np.zeros((n, D)) if dFa is not None else None
     lib().orc_render_2dgs_bwd(ctypes.c_int64(n), _p(mu), _p(_f64(surfels["quats"]).reshape(n, 4)),
                               _p(_f64(surfels["scales2"]).reshape(n, 2)), _p(_f64(surfels["opacities"]).reshape(n)),
-                              _p(_f64(surfels["rgb"]).reshape(n, 3)),
+                              _p(_f64(surfels["rgb"]).reshape(n, 3)), _p(fa), ctypes.c_int(D), _p(dFa),
                               _p(np.ascontiguousarray(lists["gids"], np.uint32)),
                               _p(np.ascontiguousarray(_cam_ranges(lists, 0), np.uint32)), _p(camera_array(cam)),
                               _p(params_array(params)), x0, y0, x1, y1, _p(_f64(dC).reshape(-1, 3)),
                               _p(out["means"]), _p(out["quats"]), _p(out["scales2"]), _p(out["opacities"]),
-                              _p(out["rgb"]))
+                              _p(out["rgb"]), _p(out["features"]))
     return out
 
 
@@ -666,33 +678,34 @@ def _surfel_colour_scene(scene: dict) -> dict:
                 opacities=scene["opacities"], sh=scene["sh"], sh_degree=scene.get("sh_degree", 0))
 
 
-def surfel_forward(scene: dict, cam: dict, params: dict | None = None) -> dict:
+def surfel_forward(scene: dict, cam: dict, params: dict | None = None, feats=None) -> dict:
     """Tiled surfel render of a surfel scene (means, quats, scales2,
-    opacities, sh) with SH colour."""
+    opacities, sh) with SH colour (and features [n, D] when given)."""
     prm = dict(params or {})
     prm["sh_degree"] = scene.get("sh_degree", 0)
     rec = project(_surfel_colour_scene(scene), cam, prm)
     surf = dict(means=scene["means"], quats=scene["quats"], scales2=scene["scales2"], opacities=scene["opacities"],
                 rgb=rec[:, R_R:R_BL + 1])
-    out = render_2dgs(surf, cam, prm)
+    out = render_2dgs(surf, cam, prm, feats=feats)
     out["rec"] = rec
     return out
 
 
-def surfel_backward(scene: dict, cam: dict, params: dict | None, dC) -> dict:
-    """Gradients of sum_p dC[p] . rgb[p] of surfel_forward with respect to
-    means (footprint and view direction), quats, scales2, opacities, sh."""
+def surfel_backward(scene: dict, cam: dict, params: dict | None, dC, feats=None, dF=None) -> dict:
+    """Gradients of sum_p dC[p] . rgb[p] (+ dF[p] . feat[p]) of
+    surfel_forward with respect to means (footprint and view direction),
+    quats, scales2, opacities, sh (and features)."""
     prm = dict(params or {})
     prm["sh_degree"] = scene.get("sh_degree", 0)
     cs = _surfel_colour_scene(scene)
     rec = project(cs, cam, prm)
     surf = dict(means=scene["means"], quats=scene["quats"], scales2=scene["scales2"], opacities=scene["opacities"],
                 rgb=rec[:, R_R:R_BL + 1])
-    g = render_2dgs_bwd(surf, cam, prm, dC)
+    g = render_2dgs_bwd(surf, cam, prm, dC, feats=feats, dF=dF)
     n = len(g["opacities"])
     gp = project_bwd(cs, cam, prm, rec, dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), rgb=g["rgb"]))
     return dict(means=g["means"] + gp["means"], quats=g["quats"], scales2=g["scales2"], opacities=g["opacities"],
-                sh=gp["sh"])
+                sh=gp["sh"], features=g["features"])
 
 
 def ndfd_2dgs(surfels: dict, cam: dict, params: dict | None, feats, fgt, region=None, k=NDFD_K,

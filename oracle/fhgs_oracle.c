@@ -1430,8 +1430,9 @@ static void surfel_alpha_chain(uint32_t g, double G, double u, double v, double 
  * len and 5 len entries. */
 static void surfel_pixel_bwd(double px, double py, const uint32_t *list, int64_t len, const double *means,
                              const double *quats, const double *scales2, const double *opac, const double *rgb,
-                             const double *cam, const double *prm, const double *dc, uint32_t *cg, double *ca,
-                             double *g_means, double *g_quats, double *g_scales2, double *g_opac, double *g_rgb)
+                             const double *feat, int D, const double *dF, const double *cam, const double *prm,
+                             const double *dc, uint32_t *cg, double *ca, double *g_means, double *g_quats,
+                             double *g_scales2, double *g_opac, double *g_rgb, double *g_feat)
 {
     const double cut = prm[P_CUT], amin = prm[P_AMIN], amax = prm[P_AMAX], teps = prm[P_TEPS];
     double T = 1.0;
@@ -1463,13 +1464,20 @@ static void surfel_pixel_bwd(double px, double py, const uint32_t *list, int64_t
         const uint32_t g = cg[j];
         const double alpha = ca[5 * j], Tj = ca[5 * j + 1], G = ca[5 * j + 2], u = ca[5 * j + 3], v = ca[5 * j + 4];
         const double w = alpha * Tj;
-        const double gw = dc[0] * rgb[3 * g] + dc[1] * rgb[3 * g + 1] + dc[2] * rgb[3 * g + 2];
+        double gw = dc[0] * rgb[3 * g] + dc[1] * rgb[3 * g + 1] + dc[2] * rgb[3 * g + 2];
+        if (feat && dF)  /* the feature term of dL/dw: dF . f_g */
+            for (int k = 0; k < D; ++k) gw += dF[k] * feat[(int64_t)D * g + k];
         const double dalpha = Tj * gw - S / (1.0 - alpha);
         S += w * gw;
         for (int ch = 0; ch < 3; ++ch) {
 #pragma omp atomic
             g_rgb[3 * g + ch] += w * dc[ch];
         }
+        if (g_feat && dF)
+            for (int k = 0; k < D; ++k) {
+#pragma omp atomic
+                g_feat[(int64_t)D * g + k] += w * dF[k];
+            }
         surfel_alpha_chain(g, G, u, v, dalpha, px, py, quats, scales2, opac, cam, amax, g_means, g_quats, g_scales2,
                            g_opac);
     }
@@ -1505,17 +1513,21 @@ void orc_render_2dgs_bwd_brute(int64_t n, const double *means, const double *qua
 #pragma omp for schedule(dynamic, 16)
         for (int64_t idx = 0; idx < (int64_t)rw * rh; ++idx)
             surfel_pixel_bwd(x0 + (int)(idx % rw) + 0.5, y0 + (int)(idx / rw) + 0.5, list, m, means, quats, scales2,
-                             opac, rgb, cam, prm, dC + 3 * idx, cg, ca, g_means, g_quats, g_scales2, g_opac, g_rgb);
+                             opac, rgb, NULL, 0, NULL, cam, prm, dC + 3 * idx, cg, ca, g_means, g_quats, g_scales2,
+                             g_opac, g_rgb, NULL);
         free(cg); free(ca);
     }
     free(list);
 }
 
-/* The backward of orc_render_2dgs (tiled lists). */
+/* The backward of orc_render_2dgs (tiled lists).  With features (feat
+ * [n][D], dF [region pixels][D] and g_feat [n][D], all NULL or none),
+ * dL/dw_g also takes the feature term dF . f_g and g_feat[g] += w_g dF. */
 void orc_render_2dgs_bwd(int64_t n, const double *means, const double *quats, const double *scales2,
-                         const double *opac, const double *rgb, const uint32_t *gids, const uint32_t *ranges,
-                         const double *cam, const double *prm, int x0, int y0, int x1, int y1, const double *dC,
-                         double *g_means, double *g_quats, double *g_scales2, double *g_opac, double *g_rgb)
+                         const double *opac, const double *rgb, const double *feat, int D, const double *dF,
+                         const uint32_t *gids, const uint32_t *ranges, const double *cam, const double *prm, int x0,
+                         int y0, int x1, int y1, const double *dC, double *g_means, double *g_quats,
+                         double *g_scales2, double *g_opac, double *g_rgb, double *g_feat)
 {
     const int W = (int)cam[0], tsz = (int)prm[P_TILE];
     const int tiles_x = (W + tsz - 1) / tsz;
@@ -1531,8 +1543,9 @@ void orc_render_2dgs_bwd(int64_t n, const double *means, const double *quats, co
             const int t = (iy / tsz) * tiles_x + ix / tsz;
             const uint32_t s0 = ranges[2 * t], e0 = ranges[2 * t + 1];
             const int64_t len = (int64_t)e0 - s0 < ORC_MAXC ? (int64_t)e0 - s0 : ORC_MAXC;
-            surfel_pixel_bwd(ix + 0.5, iy + 0.5, gids + s0, len, means, quats, scales2, opac, rgb, cam, prm,
-                             dC + 3 * idx, cg, ca, g_means, g_quats, g_scales2, g_opac, g_rgb);
+            surfel_pixel_bwd(ix + 0.5, iy + 0.5, gids + s0, len, means, quats, scales2, opac, rgb, feat, D,
+                             dF ? dF + (int64_t)D * idx : NULL, cam, prm, dC + 3 * idx, cg, ca, g_means, g_quats,
+                             g_scales2, g_opac, g_rgb, g_feat);
         }
         free(cg); free(ca);
     }
@@ -1620,11 +1633,16 @@ void orc_bin_surfel_f32(int64_t n, const float *means, const float *quats, const
 
 /* Tiled surfel render of the region: each pixel walks its 16x16 tile's
  * depth-sorted list (built from orc_bin_surfel_f32) with the rules of
- * orc_render_2dgs_brute.  The surfel arrays are indexed by the lists' ids. */
+ * orc_render_2dgs_brute.  The surfel arrays are indexed by the lists' ids.
+ * feat [n][D] (NULL: none) is blended into out_feat [region pixels][D] with
+ * the same weights (Eq. 4).  out_margin (NULL: none) receives, per pixel,
+ * the smallest relative distance to its threshold of a decision that
+ * settles the contributor set: the cutoff of a surfel that would pass the
+ * alpha test there, the alpha_min test and the stop rule. */
 void orc_render_2dgs(const double *means, const double *quats, const double *scales2, const double *opac,
-                     const double *rgb, const uint32_t *gids, const uint32_t *ranges, const double *cam,
-                     const double *prm, int x0, int y0, int x1, int y1, double *out_rgb, double *out_T,
-                     int32_t *out_ncontrib)
+                     const double *rgb, const double *feat, int D, const uint32_t *gids, const uint32_t *ranges,
+                     const double *cam, const double *prm, int x0, int y0, int x1, int y1, double *out_rgb,
+                     double *out_feat, double *out_T, int32_t *out_ncontrib, double *out_margin)
 {
     const int W = (int)cam[0], tsz = (int)prm[P_TILE];
     const int tiles_x = (W + tsz - 1) / tsz;
@@ -1635,7 +1653,10 @@ void orc_render_2dgs(const double *means, const double *quats, const double *sca
         const int ix = x0 + (int)(idx % rw), iy = y0 + (int)(idx / rw);
         const double px = ix + 0.5, py = iy + 0.5;
         const int t = (iy / tsz) * tiles_x + ix / tsz;
-        double T = 1.0, acc[3] = {0.0, 0.0, 0.0};
+        double T = 1.0, acc[3] = {0.0, 0.0, 0.0}, margin = INFINITY;
+        double *F = out_feat ? out_feat + (int64_t)D * idx : NULL;
+        if (F)
+            for (int k = 0; k < D; ++k) F[k] = 0.0;
         int nc = 0;
         for (uint32_t k = ranges[2 * t]; k < ranges[2 * t + 1]; ++k) {
             const uint32_t g = gids[k];
@@ -1643,20 +1664,28 @@ void orc_render_2dgs(const double *means, const double *quats, const double *sca
             if (!splat_uv(means + 3 * g, quats + 4 * g, scales2 + 2 * g, cam, px, py, &u, &v, &lam)) continue;
             if (!(lam > 0.0)) continue;
             const double r2 = u * u + v * v;
+            double a_cut = opac[g] * exp(-0.5 * cut);
+            if (a_cut > amax) a_cut = amax;
+            if (a_cut >= amin * (1.0 - 1e-3) && rel(r2, cut) < margin) margin = rel(r2, cut);
             if (r2 > cut) continue;
             const double rho = opac[g] * exp(-0.5 * r2);
             const double alpha = rho > amax ? amax : rho;
+            if (rel(alpha, amin) < margin) margin = rel(alpha, amin);
             if (alpha < amin) continue;
             const double Tn = T * (1.0 - alpha);
+            if (rel(Tn, teps) < margin) margin = rel(Tn, teps);
             if (Tn < teps) break;
             const double w = alpha * T;
             for (int ch = 0; ch < 3; ++ch) acc[ch] += w * rgb[3 * g + ch];
+            if (F && feat)
+                for (int c = 0; c < D; ++c) F[c] += w * feat[(int64_t)D * g + c];
             T = Tn;
             ++nc;
         }
         for (int ch = 0; ch < 3; ++ch) out_rgb[3 * idx + ch] = acc[ch] + T * prm[P_BG0 + ch];
         out_T[idx] = T;
         out_ncontrib[idx] = nc;
+        if (out_margin) out_margin[idx] = margin;
     }
 }
 

@@ -9,7 +9,7 @@
 // ones (d/dlog s = s d/ds, d/dlogit = op (1 - op) d/dop), then applies Adam
 // (m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, theta -= lr m_hat /
 // (sqrt(v_hat) + eps)) and writes the activated scales and opacities that
-// the next forward reads.  One thread owns one Gaussian.
+// the next forward reads.  The update is elementwise over flat arrays.
 #include "fhgs_internal.cuh"
 
 namespace fhgs {
@@ -58,41 +58,46 @@ __device__ __forceinline__ float gsum(const float *const *g, int ns, long long j
     return s;
 }
 
+// Adam is elementwise: one flat index space over the five groups (means,
+// log-scales, quaternions, opacity logits, SH), one element per thread in
+// a grid-stride loop, so that every parameter, moment and gradient array is
+// read and written with unit stride.  The raw-gradient factors (s for the
+// log-scales, op (1 - op) for the logits) use the element's own value.
 __global__ void __launch_bounds__(256) k_adam_gaussians(long long n, int K3, float *means, float *log_s, float *quats,
                                                         float *logit, float *sh, GradSets gs, float *state, AdamArgs a,
                                                         float *scales_out, float *opac_out) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     const int ns = gs.n;
-    // state: m and v of each group, group after group, n rows each
+    // group boundaries in the flat index: means 3n, log-scales 3n, quats 4n, logits n, SH K3 n
+    const long long e0 = 3 * n, e1 = 6 * n, e2 = 10 * n, e3 = 11 * n, e4 = (11 + (long long)K3) * n;
+    // state: m and v of each group, group after group
     float *m_mu = state, *v_mu = m_mu + 3 * n;
     float *m_ls = v_mu + 3 * n, *v_ls = m_ls + 3 * n;
     float *m_q = v_ls + 3 * n, *v_q = m_q + 4 * n;
     float *m_lo = v_q + 4 * n, *v_lo = m_lo + n;
-    float *m_sh = v_lo + n, *v_sh = m_sh + K3 * n;
-    for (int k = 0; k < 3; ++k) {
-        const long long j = 3 * i + k;
-        means[j] = adam_one(means[j], gsum(gs.means, ns, j), m_mu[j], v_mu[j], a.lr[0], a);
-    }
-    for (int k = 0; k < 3; ++k) {
-        const long long j = 3 * i + k;
-        const float g = gsum(gs.scales, ns, j) * expf(log_s[j]);
-        log_s[j] = adam_one(log_s[j], g, m_ls[j], v_ls[j], a.lr[1], a);
-        if (scales_out) scales_out[j] = expf(log_s[j]);
-    }
-    for (int k = 0; k < 4; ++k) {
-        const long long j = 4 * i + k;
-        quats[j] = adam_one(quats[j], gsum(gs.quats, ns, j), m_q[j], v_q[j], a.lr[2], a);
-    }
-    {
-        const float op = 1.f / (1.f + expf(-logit[i]));
-        const float g = gsum(gs.opac, ns, i) * op * (1.f - op);
-        logit[i] = adam_one(logit[i], g, m_lo[i], v_lo[i], a.lr[3], a);
-        if (opac_out) opac_out[i] = 1.f / (1.f + expf(-logit[i]));
-    }
-    for (int k = 0; k < K3; ++k) {
-        const long long j = (long long)K3 * i + k;
-        sh[j] = adam_one(sh[j], gsum(gs.sh, ns, j), m_sh[j], v_sh[j], a.lr[4], a);
+    float *m_sh = v_lo + n, *v_sh = m_sh + (long long)K3 * n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e4; i += (long long)gridDim.x * blockDim.x) {
+        if (i < e0) {
+            means[i] = adam_one(means[i], gsum(gs.means, ns, i), m_mu[i], v_mu[i], a.lr[0], a);
+        } else if (i < e1) {
+            const long long j = i - e0;
+            const float g = gsum(gs.scales, ns, j) * expf(log_s[j]);
+            const float t = adam_one(log_s[j], g, m_ls[j], v_ls[j], a.lr[1], a);
+            log_s[j] = t;
+            if (scales_out) scales_out[j] = expf(t);
+        } else if (i < e2) {
+            const long long j = i - e1;
+            quats[j] = adam_one(quats[j], gsum(gs.quats, ns, j), m_q[j], v_q[j], a.lr[2], a);
+        } else if (i < e3) {
+            const long long j = i - e2;
+            const float op = 1.f / (1.f + expf(-logit[j]));
+            const float g = gsum(gs.opac, ns, j) * op * (1.f - op);
+            const float t = adam_one(logit[j], g, m_lo[j], v_lo[j], a.lr[3], a);
+            logit[j] = t;
+            if (opac_out) opac_out[j] = 1.f / (1.f + expf(-t));
+        } else {
+            const long long j = i - e3;
+            sh[j] = adam_one(sh[j], gsum(gs.sh, ns, j), m_sh[j], v_sh[j], a.lr[4], a);
+        }
     }
 }
 
@@ -156,8 +161,12 @@ void launch_adam_gaussians(long long n, int K, float *means, float *log_s, float
     a.c1 = 1.f - powf(opt->beta1, (float)opt->step);
     a.c2 = 1.f - powf(opt->beta2, (float)opt->step);
     note_launch(1);
-    k_adam_gaussians<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, 3 * K, means, log_s, quats, logit, sh, gs,
-                                                                  state, a, scales_out, opac_out);
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long total = (11 + 3ll * K) * n;
+    const unsigned blocks = (unsigned)min((total + 255) / 256, (long long)sms * 16);
+    k_adam_gaussians<<<blocks, 256, 0, st>>>(n, 3 * K, means, log_s, quats, logit, sh, gs, state, a, scales_out,
+                                             opac_out);
 }
 
 void launch_activate(long long n, const float *log_s, const float *logit, float *scales, float *opac,

@@ -463,3 +463,88 @@ def test_surfel_binning_rule_covers_the_exact_box_at_1080p():
     assert not (valid & ((p[:, 0] > xl) | (p[:, 2] < xh) | (p[:, 1] > yl) | (p[:, 3] < yh))).any()
     over = np.maximum(np.maximum(xl - p[:, 0], p[:, 2] - xh), np.maximum(yl - p[:, 1], p[:, 3] - yh))[valid]
     assert np.median(over) <= 3
+
+
+def _random_surfels(seed, n, W, H):
+    g = np.random.default_rng(seed)
+    surf = dict(means=g.normal(0, 0.35, (n, 3)) + [0, 0, 2.4], quats=g.normal(size=(n, 4)),
+                scales2=np.exp(g.uniform(-3.0, -1.9, (n, 2))), opacities=g.uniform(0.1, 0.95, n),
+                rgb=g.uniform(0, 1, (n, 3)))
+    return {k: np.asarray(v, np.float32).astype(np.float64) for k, v in surf.items()}, g
+
+
+def test_tiled_surfel_features_are_blended_with_the_weights():
+    """Eq. 4's feature blend over surfels: a constant unit feature gives
+    sum w = 1 - T at every pixel (the weights and the transmittance
+    telescope), and the blend is linear in the features."""
+    cam = axis_camera(W=48, H=40, fx=44.0, t=(0.01, -0.02, 0.0))
+    surf, g = _random_surfels(21, 80, 48, 40)
+    ones = np.ones((80, 1))
+    out = oracle.render_2dgs(surf, cam, None, feats=ones)
+    np.testing.assert_allclose(out["feat"][..., 0] + out["T"], 1.0, atol=1e-12)
+    assert (out["ncontrib"] > 3).mean() > 0.2
+    f1, f2 = g.normal(size=(80, 5)), g.normal(size=(80, 5))
+    a = oracle.render_2dgs(surf, cam, None, feats=f1)["feat"]
+    b = oracle.render_2dgs(surf, cam, None, feats=f2)["feat"]
+    c = oracle.render_2dgs(surf, cam, None, feats=f1 + 2.0 * f2)["feat"]
+    np.testing.assert_allclose(c, a + 2.0 * b, atol=1e-12)
+
+
+def test_tiled_surfel_margin_covers_every_flipped_decision():
+    """Moving alpha_min, the cutoff or t_eps by a relative 1e-3 changes the
+    image only at pixels whose margin is below 1e-3."""
+    cam = axis_camera(W=52, H=44, fx=46.0, t=(0.01, 0.02, 0.0))
+    surf, _ = _random_surfels(22, 120, 52, 44)
+    base = oracle.render_2dgs(surf, cam, None)
+    changed_total = 0
+    for key in ("alpha_min", "cutoff_sq", "t_eps"):
+        for f in (1.0 - 1e-3, 1.0 + 1e-3):
+            prm = {key: oracle.DEFAULT_PARAMS[key] * f}
+            alt = oracle.render_2dgs(surf, cam, prm)
+            changed = np.abs(alt["rgb"] - base["rgb"]).max(axis=-1) > 0
+            assert np.all(base["margin"][changed] < 1e-3), key
+            changed_total += int(changed.sum())
+    assert changed_total > 0
+
+
+def test_surfel_pipeline_with_features_matches_central_differences():
+    """The surfel backward's feature term: dL/dw takes dF . f, and the
+    feature gradient is sum_p w dF, against central differences of the
+    whole forward (SH colour and features)."""
+    g = np.random.default_rng(23)
+    cam = axis_camera(W=26, H=22, fx=24.0, t=(0.02, 0.01, 0.0))
+    n, D = 7, 3
+    q = g.normal(size=(n, 4))
+    sc = dict(means=g.normal(0, 0.25, (n, 3)) + [0, 0, 2.0], quats=q / np.linalg.norm(q, axis=1, keepdims=True),
+              scales2=np.exp(g.uniform(-2.6, -1.7, (n, 2))), opacities=g.uniform(0.2, 0.9, n),
+              sh=g.normal(0, 0.3, (n, 1, 3)), sh_degree=0)
+    sc["sh"][:, 0, :] += 1.0
+    feats = g.normal(size=(n, D))
+    prm = dict(bg=(0.1, 0.2, 0.3))
+    dC, dF = g.normal(size=(22 * 26, 3)), g.normal(size=(22 * 26, D))
+    grads = oracle.surfel_backward(sc, cam, prm, dC, feats=feats, dF=dF)
+
+    def loss(s, f):
+        out = oracle.surfel_forward(s, cam, prm, feats=f)
+        return float((out["rgb"].reshape(-1, 3) * dC).sum() + (out["feat"].reshape(-1, D) * dF).sum())
+
+    checked = 0
+    for key in ("means", "quats", "scales2", "opacities", "features"):
+        base = np.asarray(feats if key == "features" else sc[key], np.float64)
+        flat = base.reshape(-1)
+        for i in range(flat.size):
+            fds = []
+            for h in (1e-6, 5e-7):
+                vals = []
+                for sgn in (1, -1):
+                    pert = flat.copy()
+                    pert[i] += sgn * h
+                    pb = pert.reshape(base.shape)
+                    vals.append(loss(sc, pb) if key == "features" else loss(dict(sc, **{key: pb}), feats))
+                fds.append((vals[0] - vals[1]) / (2 * h))
+            if abs(fds[0] - fds[1]) > 1e-6 * max(1.0, abs(fds[0])):
+                continue
+            an = grads[key].reshape(-1)[i]
+            assert abs(fds[0] - an) <= 2e-6 * max(1.0, abs(fds[0])), (key, i, fds[0], an)
+            checked += abs(an) > 1e-8
+    assert checked > 40
