@@ -58,13 +58,14 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="warm-up + one step, no JSON (for ncu)")
-    ap.add_argument("--workload", choices=["render", "fusion", "ndfd", "points", "train", "batched"],
+    ap.add_argument("--workload", choices=["render", "fusion", "ndfd", "points", "train", "batched", "surfel"],
                     default="render",
                     help="render: fwd+bwd of the 1080p view (the headline); fusion: 3M Gaussians x 64 views; "
                          "ndfd: the NDFD losses L_gt, L_cf and their backward on the 1080p view; "
                          "points: the paper's point-to-feature assignment, 3M points x 64 views; "
                          "train: one training iteration (render, L1, NDFD, Adam) on the 1080p view; "
-                         "batched: 16 uneven cameras, 500k Gaussians, D=256, one CUDA graph per step")
+                         "batched: 16 uneven cameras, 500k Gaussians, D=256, one CUDA graph per step; "
+                         "surfel: the 2DGS surfel geometry on the 1080p view (FP32 path)")
     ap.add_argument("--views", type=int, default=64, help="fusion: number of views")
     return ap.parse_args()
 
@@ -982,6 +983,118 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
+SURFEL_METRIC = "fwd+bwd Mpix/s at 1M 2DGS surfels, 1080p, D=512 BF16 features, FP32 CUDA-core path"
+SURFEL_WORKLOAD = ("1M 2DGS surfels (config-3 distributions, s_u, s_v the first two scales), 1920x1080 view, "
+                   "SH degree 3, D=512 BF16 features, fwd+bwd")
+
+
+def surfel_cpu_baseline(scene, cam, D, steps=2):
+    """The oracle on a bounded sample of the surfel workload: binary32
+    binning of every surfel, lists of the 64x64 crop's tiles, FP64 surfel
+    forward + backward of its 4096 pixels with SH colour and features,
+    after one untimed sample."""
+    import oracle
+    from paper_2505_19154_gb300 import synth
+    x0, y0, x1, y1 = synth.CROP3
+    prm = dict(sh_degree=3)
+    sc = dict(scene, scales2=np.asarray(scene["scales"])[:, :2])
+    dC, dF = synth.upstream(0, (x1 - x0) * (y1 - y0), D)
+
+    def one():
+        oracle.surfel_forward(sc, cam, prm, feats=scene["features"], region=synth.CROP3)
+        oracle.surfel_backward(sc, cam, prm, dC, feats=scene["features"], dF=dF, region=synth.CROP3)
+
+    one()
+    t0 = time.time()
+    for _ in range(steps):
+        one()
+    dt = time.time() - t0
+    return {"value": round(steps * 4096 / dt / 1e6, 6), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"{steps} x (binary32 binning of all {len(scene['means'])} surfels, lists of the 64x64 "
+                      f"crop's tiles, FP64 surfel fwd+bwd of its 4096 pixels, D={D}), after one untimed sample"}
+
+
+def run_surfel(args):
+    """The 2DGS surfel geometry (Sec. 3.1) on the headline scene and view:
+    projection, binning, forward and backward with the D-dim feature blend
+    on the FP32 CUDA-core kernels."""
+    import torch
+    from paper_2505_19154_gb300 import api, synth
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, cams, t, P = make_workload(rank, args.n, args.D, dev)
+    D = args.D
+    rast = api.Rasterizer(local, sh_degree=3, geometry=api.GEOM_SURFEL)
+    g = (t["means"], t["scales"], t["quats"], t["opacities"], t["sh"])
+    st0 = rast.prepare(*g, cams)
+    I = st0["n_instances"]
+    rast.capacity = int(I * 1.05) + 1024
+    rast.forward(st0, t["features"])
+    Q, Qpix, U = composited_pairs(st0, cams)
+    del st0
+
+    def step():
+        st = rast.prepare(*g, cams, check=False)
+        rast.forward(st, t["features"])
+        rast.backward(st, t["dC"], t["dF"])
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if rast.ctx.sync_status() != api.OK:
+        raise RuntimeError("device status after warm-up")
+    K = max(1, args.steps)
+    rast.ctx.profile(True)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    n0 = api.Context.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    launches = api.Context.launch_count() - n0
+    ck = clocks.stop()
+    prof = rast.ctx.profile_read()
+    if rast.ctx.sync_status() != api.OK:
+        raise RuntimeError("device status after timed region")
+    ms = e0.elapsed_time(e1) / K
+    tot = sum(v[1] for v in prof.values())
+    per = {k: {"launches": c, "ms": round(tm / max(c, 1), 4), "share": round(tm / max(tot, 1e-9), 4)}
+           for k, (c, tm) in prof.items()}
+    fl = algorithmic_flops(args.n, D, Q)
+    fpk = fp32_peak(dev, local)
+    for k, base in (("render_fwd_surfel", "render_fwd"), ("render_bwd_surfel", "render_bwd")):
+        if k in per:
+            per[k]["fp32_tflops"] = round(fl[base] / (per[k]["ms"] * 1e-3) / 1e12, 2)
+    dom = max(("render_fwd_surfel", "render_bwd_surfel"), key=lambda k: prof.get(k, (0, 0))[1])
+    base = dom.replace("_surfel", "")
+    ach = fl[base] / (per[dom]["ms"] * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": fpk["tflops"], "unit": "TFLOP/s",
+            "frac": round(ach / fpk["tflops"], 4),
+            "peak_source": "of measured FP32 FMA peak (fhgs_ffma_probe, this run)", "traffic": None,
+            "algorithmic_flops": fl[base], "fp32_peak": fpk}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = surfel_cpu_baseline(scene, cams[0], D)
+    line = {"metric": SURFEL_METRIC, "value": round(P / (ms * 1e-3) / 1e6, 2), "unit": UNIT, "n_gpus": 1,
+            "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SURFEL_WORKLOAD, "gaussians": args.n, "width": cams[0]["width"],
+                       "height": cams[0]["height"], "feature_dim": D, "tile_instances": I,
+                       "composited_pairs_tile": Q, "composited_pairs_pixel": Qpix, "gaussians_walked": U,
+                       "l2": "inputs larger than L2 (features 1 GB, dL/dfeat 4.2 GB)"},
+            "roofline": roof, "kernels": per, "e2e": None, "cpu_baseline": cpu, "clocks": ck,
+            "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
 TRAIN_METRIC = "training iteration Mpix/s at 1M Gaussians, 1080p, NDFD D=512 BF16 (render + L1 + NDFD + Adam)"
 TRAIN_WORKLOAD = ("1M Gaussians, 1920x1080 view, SH degree 3, D=512 BF16 frozen features and ground-truth map: "
                   "one Adam iteration of L = L_rgb + L_gt + L_cf")
@@ -1075,6 +1188,8 @@ def main():
         run_train(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "surfel":
+        run_surfel(args)
     else:
         run_ours(args)
 

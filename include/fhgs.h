@@ -88,7 +88,21 @@ typedef struct fhgs_params {
     float cutoff_sq;         /* skip a pixel outside the ellipse q2 > cutoff_sq (9) */
     float fov_clamp;         /* Jacobian uses x/z clamped to +-fov_clamp*W/(2 fx) (1.3) */
     float bg[3];             /* background colour behind the remaining transmittance */
+    int32_t geometry;        /* FHGS_GEOM_*: the primitives' footprint model */
 } fhgs_params;
+
+/* Footprint models.  FHGS_GEOM_EWA: 3-D Gaussians splatted to screen conics
+ * (the 3DGS rasterizer the paper builds on, App. A).  FHGS_GEOM_SURFEL: the
+ * 2DGS surfels of Sec. 3.1 (Eq. 1-3): the plane p + s_u t_u u + s_v t_v v
+ * (t_u, t_v the first two columns of R(q); s_u, s_v = scales[i][0..1],
+ * scales[i][2] is ignored and gets a zero gradient) with density
+ * exp(-(u^2 + v^2)/2) at the point u(x) where the pixel's ray meets the
+ * plane; binning follows the binary32 rule of the surfel footprint's
+ * dual-conic box.  The surfel model runs fhgs_project, fhgs_bin_sort and
+ * the FP32 CUDA-core render (forward and backward; FHGS_PATH_TC is
+ * FHGS_ERR_UNSUPPORTED, FHGS_PATH_AUTO takes the FP32 kernels); fusion,
+ * NDFD and the allocation-free backward return FHGS_ERR_UNSUPPORTED. */
+enum { FHGS_GEOM_EWA = 0, FHGS_GEOM_SURFEL = 1 };
 
 enum {
     FHGS_PATH_AUTO = 0, /* tensor-core feature blend when D > 0 and features are BF16 */

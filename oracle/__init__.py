@@ -599,7 +599,8 @@ def bin_surfel_f32(means, quats, scales2, cam: dict, params: dict | None = None)
     return dict(pix=pix, tile=tile, ntiles=nt, dbits=db)
 
 
-def render_2dgs(surfels: dict, cam: dict, params: dict | None = None, region=None, feats=None) -> dict:
+def render_2dgs(surfels: dict, cam: dict, params: dict | None = None, region=None, feats=None,
+                tile_rect=None) -> dict:
     """Tiled surfel render: the binary32 binning rule, per-tile lists sorted
     by (tile, depth bits, id), and each pixel's walk of its tile's list.
     feats [n, D] (optional) are blended with the same weights.  Also returns
@@ -611,7 +612,7 @@ def render_2dgs(surfels: dict, cam: dict, params: dict | None = None, region=Non
     n = mu.shape[0]
     b = bin_surfel_f32(np.asarray(surfels["means"], np.float32), np.asarray(surfels["quats"], np.float32),
                        np.asarray(surfels["scales2"], np.float32), cam, params)
-    lists = tile_lists([b], [cam], params)
+    lists = tile_lists([b], [cam], params, tile_rect=tile_rect)
     rgb = np.zeros((npx, 3))
     T = np.zeros(npx)
     nc = np.zeros(npx, np.int32)
@@ -641,7 +642,8 @@ def splat_uv_T(means, quats, scales2, cam: dict, px, py) -> dict:
     return dict(u=u, v=v, depth=dep)
 
 
-def render_2dgs_bwd(surfels: dict, cam: dict, params: dict | None, dC, region=None, feats=None, dF=None) -> dict:
+def render_2dgs_bwd(surfels: dict, cam: dict, params: dict | None, dC, region=None, feats=None, dF=None,
+                    tile_rect=None) -> dict:
     """Gradients of sum_p dC[p] . rgb[p] (+ dF[p] . feat[p] with features)
     of the tiled surfel render (render_2dgs) with respect to means, quats,
     scales2, opacities, rgb (and features)."""
@@ -651,7 +653,7 @@ def render_2dgs_bwd(surfels: dict, cam: dict, params: dict | None, dC, region=No
     n = mu.shape[0]
     b = bin_surfel_f32(np.asarray(surfels["means"], np.float32), np.asarray(surfels["quats"], np.float32),
                        np.asarray(surfels["scales2"], np.float32), cam, params)
-    lists = tile_lists([b], [cam], params)
+    lists = tile_lists([b], [cam], params, tile_rect=tile_rect)
     out = dict(means=np.zeros((n, 3)), quats=np.zeros((n, 4)), scales2=np.zeros((n, 2)), opacities=np.zeros(n),
                rgb=np.zeros((n, 3)))
     D = 0 if feats is None else int(np.asarray(feats).shape[1])
@@ -678,7 +680,7 @@ def _surfel_colour_scene(scene: dict) -> dict:
                 opacities=scene["opacities"], sh=scene["sh"], sh_degree=scene.get("sh_degree", 0))
 
 
-def surfel_forward(scene: dict, cam: dict, params: dict | None = None, feats=None) -> dict:
+def surfel_forward(scene: dict, cam: dict, params: dict | None = None, feats=None, region=None) -> dict:
     """Tiled surfel render of a surfel scene (means, quats, scales2,
     opacities, sh) with SH colour (and features [n, D] when given)."""
     prm = dict(params or {})
@@ -686,12 +688,13 @@ def surfel_forward(scene: dict, cam: dict, params: dict | None = None, feats=Non
     rec = project(_surfel_colour_scene(scene), cam, prm)
     surf = dict(means=scene["means"], quats=scene["quats"], scales2=scene["scales2"], opacities=scene["opacities"],
                 rgb=rec[:, R_R:R_BL + 1])
-    out = render_2dgs(surf, cam, prm, feats=feats)
+    tr = None if region is None else (region[0] // 16, region[1] // 16, (region[2] - 1) // 16, (region[3] - 1) // 16)
+    out = render_2dgs(surf, cam, prm, feats=feats, region=region, tile_rect=tr)
     out["rec"] = rec
     return out
 
 
-def surfel_backward(scene: dict, cam: dict, params: dict | None, dC, feats=None, dF=None) -> dict:
+def surfel_backward(scene: dict, cam: dict, params: dict | None, dC, feats=None, dF=None, region=None) -> dict:
     """Gradients of sum_p dC[p] . rgb[p] (+ dF[p] . feat[p]) of
     surfel_forward with respect to means (footprint and view direction),
     quats, scales2, opacities, sh (and features)."""
@@ -701,7 +704,8 @@ def surfel_backward(scene: dict, cam: dict, params: dict | None, dC, feats=None,
     rec = project(cs, cam, prm)
     surf = dict(means=scene["means"], quats=scene["quats"], scales2=scene["scales2"], opacities=scene["opacities"],
                 rgb=rec[:, R_R:R_BL + 1])
-    g = render_2dgs_bwd(surf, cam, prm, dC, feats=feats, dF=dF)
+    tr = None if region is None else (region[0] // 16, region[1] // 16, (region[2] - 1) // 16, (region[3] - 1) // 16)
+    g = render_2dgs_bwd(surf, cam, prm, dC, feats=feats, dF=dF, region=region, tile_rect=tr)
     n = len(g["opacities"])
     gp = project_bwd(cs, cam, prm, rec, dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), rgb=g["rgb"]))
     return dict(means=g["means"] + gp["means"], quats=g["quats"], scales2=g["scales2"], opacities=g["opacities"],

@@ -18,6 +18,7 @@ from . import _build
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_ALIGNMENT, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NUMERIC, \
     ERR_NO_DEVICE = range(9)
 PATH_AUTO, PATH_FP32, PATH_TC = 0, 1, 2
+GEOM_EWA, GEOM_SURFEL = 0, 1
 F32, BF16 = 0, 1
 FUSE_ACCUMULATE, FUSE_FINALIZE, FUSE_NORMALIZE = 1, 2, 4
 MAX_CAMS = 32
@@ -45,7 +46,7 @@ class Params(ctypes.Structure):
                 ("path", ctypes.c_int32), ("batch", ctypes.c_int32), ("d_split", ctypes.c_int32),
                 ("znear", ctypes.c_float), ("dilation", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("t_eps", ctypes.c_float), ("cutoff_sq", ctypes.c_float),
-                ("fov_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3)]
+                ("fov_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3), ("geometry", ctypes.c_int32)]
 
 
 class Adam(ctypes.Structure):

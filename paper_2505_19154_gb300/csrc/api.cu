@@ -110,6 +110,8 @@ fhgs_status check_params(fhgs_ctx *ctx, const fhgs_params *p) {
         return fail(ctx, FHGS_ERR_INVALID_ARG, "parameter out of range");
     if (p->path < FHGS_PATH_AUTO || p->path > FHGS_PATH_TC)
         return fail(ctx, FHGS_ERR_INVALID_ARG, "unknown path");
+    if (p->geometry != FHGS_GEOM_EWA && p->geometry != FHGS_GEOM_SURFEL)
+        return fail(ctx, FHGS_ERR_INVALID_ARG, "unknown geometry");
     return FHGS_OK;
 }
 
@@ -175,6 +177,7 @@ Params make_params(const fhgs_params *p) {
     q.sh_deg = p->sh_degree;
     q.K = (p->sh_degree + 1) * (p->sh_degree + 1);
     q.probe_ns = g_wait_probe_ns.load(std::memory_order_relaxed);
+    q.geom = p->geometry;
     return q;
 }
 
@@ -241,6 +244,7 @@ fhgs_status check_bwd_args(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *p
         return fail(ctx, FHGS_ERR_ALIGNMENT, "feature gradients must be 16-byte aligned");
     if (p->path == FHGS_PATH_TC && D > 0 && !use_tc(p, ftype, D))
         return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core path needs BF16 features and a supported D");
+    if (p->geometry != FHGS_GEOM_EWA) return fail(ctx, FHGS_ERR_UNSUPPORTED, "EWA geometry only");
     if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
     q = make_params(p);
     tc = D > 0 && use_tc(p, ftype, D) && (grad_feat || grad_features);
@@ -374,7 +378,11 @@ fhgs_status fhgs_project(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhgs_came
     const Params q = make_params(p);
     {
         Prof pr(ctx, "project", (cudaStream_t)stream);
-        launch_project(*g, cs, q, proj_view(proj, (long long)g->n * n_cams), ctx->status, (cudaStream_t)stream);
+        if (p->geometry == FHGS_GEOM_SURFEL)
+            launch_project_surfel(*g, cs, q, proj_view(proj, (long long)g->n * n_cams), ctx->status,
+                                  (cudaStream_t)stream);
+        else
+            launch_project(*g, cs, q, proj_view(proj, (long long)g->n * n_cams), ctx->status, (cudaStream_t)stream);
     }
     FHGS_CUDA(ctx, cudaGetLastError());
     return FHGS_OK;
@@ -417,6 +425,8 @@ fhgs_status fhgs_render_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fh
     if (feat && !aligned16(feat)) return fail(ctx, FHGS_ERR_ALIGNMENT, "feat must be 16-byte aligned");
     if (p->path == FHGS_PATH_TC && D > 0 && !use_tc(p, ftype, D))
         return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core path needs BF16 features and a supported D");
+    if (p->geometry == FHGS_GEOM_SURFEL && p->path == FHGS_PATH_TC)
+        return fail(ctx, FHGS_ERR_UNSUPPORTED, "surfels render on the FP32 path");
     CamSet cs;
     if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
     FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -424,6 +434,15 @@ fhgs_status fhgs_render_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fh
     ProjView pv = proj_view(const_cast<void *>(proj), (long long)n * n_cams);
     cudaStream_t st = (cudaStream_t)stream;
     const int Df = feat ? D : 0;
+    if (p->geometry == FHGS_GEOM_SURFEL) {
+        {
+            Prof pr(ctx, "render_fwd_surfel", st);
+            launch_render_fwd_surfel(n, cs, q, pv, *bins, features, ftype == FHGS_BF16, Df, rgb, feat, T_final, last,
+                                     st);
+        }
+        FHGS_CUDA(ctx, cudaGetLastError());
+        return FHGS_OK;
+    }
     const bool tc = Df > 0 && use_tc(p, ftype, D);
     Prof pr(ctx, tc ? "render_fwd_tc" : "render_fwd_fp32", st);
     if (tc)
@@ -455,12 +474,35 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
         return fail(ctx, FHGS_ERR_ALIGNMENT, "feature gradients must be 16-byte aligned");
     if (p->path == FHGS_PATH_TC && D > 0 && !use_tc(p, ftype, D))
         return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core path needs BF16 features and a supported D");
+    if (p->geometry == FHGS_GEOM_SURFEL && p->path == FHGS_PATH_TC)
+        return fail(ctx, FHGS_ERR_UNSUPPORTED, "surfels render on the FP32 path");
     CamSet cs;
     if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
     FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
     const long long n = g->n, cn = n * n_cams;
-    if ((s = ensure(ctx, ctx->g2d, sizeof(float) * 12 * (size_t)cn + 256)) != FHGS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if (p->geometry == FHGS_GEOM_SURFEL) {
+        if ((s = ensure(ctx, ctx->g2d, sizeof(float) * kSurfelG2d * (size_t)cn + 256)) != FHGS_OK) return s;
+        float *g2d = (float *)ctx->g2d.p;
+        FHGS_CUDA(ctx, cudaMemsetAsync(g2d, 0, sizeof(float) * kSurfelG2d * (size_t)cn, st));
+        if (grad_features && D > 0)
+            FHGS_CUDA(ctx, cudaMemsetAsync(grad_features, 0, sizeof(float) * (size_t)n * D, st));
+        const Params q = make_params(p);
+        ProjView pv = proj_view(const_cast<void *>(proj), cn);
+        {
+            Prof pr(ctx, "render_bwd_surfel", st);
+            launch_render_bwd_surfel(n, cs, q, pv, *bins, features, ftype == FHGS_BF16, D, T_final, last, grad_rgb,
+                                     grad_feat, g2d, D > 0 ? grad_features : nullptr, st);
+        }
+        {
+            Prof pb(ctx, "project_bwd", st);
+            launch_project_surfel_bwd(*g, cs, q, pv, g2d, grad_means, grad_scales, grad_quats, grad_opac, grad_sh,
+                                      st);
+        }
+        FHGS_CUDA(ctx, cudaGetLastError());
+        return FHGS_OK;
+    }
+    if ((s = ensure(ctx, ctx->g2d, sizeof(float) * 12 * (size_t)cn + 256)) != FHGS_OK) return s;
     float *g2d = (float *)ctx->g2d.p;
     FHGS_CUDA(ctx, cudaMemsetAsync(g2d, 0, sizeof(float) * 12 * (size_t)cn, st));
     if (grad_features && D > 0) FHGS_CUDA(ctx, cudaMemsetAsync(grad_features, 0, sizeof(float) * (size_t)n * D, st));
@@ -619,6 +661,7 @@ static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, cons
     if (s == FHGS_OK) s = check_bins(ctx, bins);
     if (s == FHGS_OK) s = check_features(ctx, features, ftype, D, n);
     if (s != FHGS_OK) return s;
+    if (p->geometry != FHGS_GEOM_EWA) return fail(ctx, FHGS_ERR_UNSUPPORTED, "NDFD runs on the EWA geometry");
     if (!ndfd_supported(D)) return fail(ctx, FHGS_ERR_UNSUPPORTED, "NDFD needs D in {32, 64, 128, 256, 512}");
     if (!proj) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL input buffer");
     if (!feat_gt) return fail(ctx, FHGS_ERR_INVALID_ARG, "feat_gt is NULL");
@@ -694,6 +737,7 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
     fhgs_status s = check_params(ctx, p);
     if (s == FHGS_OK) s = check_gaussians(ctx, g, true);
     if (s != FHGS_OK) return s;
+    if (p->geometry != FHGS_GEOM_EWA) return fail(ctx, FHGS_ERR_UNSUPPORTED, "fusion runs on the EWA geometry");
     if (!views || n_views < 0) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad views");
     if (n_views > 0 && !maps) return fail(ctx, FHGS_ERR_INVALID_ARG, "maps is NULL");
     if (D <= 0 || D % 8) return fail(ctx, FHGS_ERR_UNSUPPORTED, "D must be a positive multiple of 8");

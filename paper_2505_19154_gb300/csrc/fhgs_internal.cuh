@@ -45,6 +45,7 @@ struct Params {
     // 0 = off; else each CTA first waits at most this many ns on an mbarrier
     // that nothing arrives at, latches ST_TIMEOUT and returns.
     unsigned long long probe_ns;
+    int geom;  // FHGS_GEOM_EWA or FHGS_GEOM_SURFEL
 };
 
 // Per (camera, Gaussian) screen-space record used by the render kernels.
@@ -54,6 +55,19 @@ struct Params {
 struct __align__(16) GRec {
     float4 a, b, c;
 };
+
+// Per (camera, surfel) record of the 2DGS path (surfel.cu): the projected
+// centre and M = T'^-1 of the surfel's centred projective map (per pixel
+// u = (M00 dx + M01 dy) / w, v = (M10 dx + M11 dy) / w, w = M20 dx + M21 dy
+// + M22), opacity, colour:
+//   a = (x_c, y_c, M00, M01)   b = (M10, M11, M20, M21)
+//   c = (M22, opacity, r, g)   d = (b, view depth, colour clamp mask bits, 0)
+struct __align__(16) SRec {
+    float4 a, b, c, d;
+};
+// floats per (camera, surfel) in the render-gradient scratch of the 2DGS
+// path: d(x_c, y_c, M00, M01, M10, M11, M20, M21, M22, opacity, r, g, b)
+constexpr int kSurfelG2d = 16;
 
 // Largest tile grid of one camera: the per-segment count kernel keeps
 // (tiles_x + 1) * (tiles_y + 1) ints in shared memory (224 KB), and the
@@ -67,6 +81,7 @@ struct ProjView {
     int4 *trect;      // [C*N] tile rectangle (tx0, ty0, tx1, ty1), inclusive
     uint32_t *ntiles; // [C*N] tiles in the rectangle, 0 if culled
     uint32_t *dkey;   // [C*N] IEEE bits of the view depth, 0xFFFFFFFF if culled
+    SRec *srec;       // [C*N] surfel records (2DGS geometry only)
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -93,7 +108,7 @@ inline void allow_max_smem(std::atomic<unsigned long long> &done, K kernel) {
 
 inline size_t proj_bytes(long long cn) {
     return align_up(sizeof(GRec) * cn, 256) + align_up(sizeof(int4) * cn, 256) +
-           2 * align_up(sizeof(uint32_t) * cn, 256) + 256;
+           2 * align_up(sizeof(uint32_t) * cn, 256) + align_up(sizeof(SRec) * cn, 256) + 256;
 }
 
 inline ProjView proj_view(void *base, long long cn) {
@@ -106,6 +121,8 @@ inline ProjView proj_view(void *base, long long cn) {
     v.ntiles = (uint32_t *)p;
     p += align_up(sizeof(uint32_t) * cn, 256);
     v.dkey = (uint32_t *)p;
+    p += align_up(sizeof(uint32_t) * cn, 256);
+    v.srec = (SRec *)p;
     return v;
 }
 
@@ -201,6 +218,21 @@ struct PFView {
 };
 void launch_point_features(long long n, const float *means, const PFView *views, int n_views, float znear,
                            const float *u, int D, float *out, int32_t *view, int32_t *pixel, cudaStream_t st);
+
+// 2DGS surfel geometry (surfel.cu): projection with the binary32 binning
+// rule, the FP32 render forward and backward, and the projection backward;
+// g2d holds kSurfelG2d floats per (camera, surfel)
+void launch_project_surfel(const fhgs_gaussians &g, const CamSet &cs, const Params &p, ProjView pv, unsigned *status,
+                           cudaStream_t st);
+void launch_render_fwd_surfel(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                              const void *feats, int bf16, int D, float *rgb, float *feat, float *T, int32_t *last,
+                              cudaStream_t st);
+void launch_render_bwd_surfel(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                              const void *feats, int bf16, int D, const float *T, const int32_t *last,
+                              const float *grgb, const float *gfeat, float *g2d, float *gfeatures, cudaStream_t st);
+void launch_project_surfel_bwd(const fhgs_gaussians &g, const CamSet &cs, const Params &p, ProjView pv,
+                               const float *g2d, float *gmeans, float *gscales, float *gquats, float *gop,
+                               float *gsh, cudaStream_t st);
 
 // training-step kernels (train.cu)
 void launch_l1_loss(long long m, const float *a, const float *b, float inv_count, float *loss, float *grad,
