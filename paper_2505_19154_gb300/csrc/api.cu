@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -212,6 +213,14 @@ fhgs_status check_features(fhgs_ctx *ctx, const void *features, fhgs_dtype ft, i
 fhgs_status ensure_bin_scratch(fhgs_ctx *ctx, long long N, int n_cams, int total_tiles) {
     const size_t bytes = bin_scratch_bytes(N, n_cams, total_tiles, ctx->sm_count);
     return bytes > ctx->bin.bytes ? ensure(ctx, ctx->bin, bytes) : FHGS_OK;
+}
+
+bool bwd_stream_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("FHGS_BWD_STREAM");
+        return e && e[0] == '1';
+    }();
+    return on;
 }
 
 bool use_tc(const fhgs_params *p, fhgs_dtype ft, int D) {
@@ -511,7 +520,16 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
     const bool tc = D > 0 && use_tc(p, ftype, D) && (grad_feat || grad_features);
     {
         Prof pr(ctx, tc ? "render_bwd_tc" : "render_bwd_fp32", st);
-        if (tc) {
+        // d_split 1: the streamed kernel (all D channels per item, dL/dF in
+        // 64-channel chunks), when D % 128 == 0 and dL/dF is given; d_split 0
+        // (auto) takes it only when FHGS_BWD_STREAM=1 is set in the environment
+        const bool stream_ok = tc && grad_feat != nullptr && bwd_stream_supported(D) &&
+                               (p->d_split == 1 || (p->d_split == 0 && bwd_stream_enabled()));
+        if (stream_ok) {
+            if (!launch_render_bwd_stream(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, D, T_final, last,
+                                          grad_rgb, grad_feat, g2d, grad_features, ctx->status, st))
+                return fail(ctx, FHGS_ERR_CUDA, "could not encode the tensor map of grad_feat");
+        } else if (tc) {
             if (!launch_render_bwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, D, p->d_split, T_final,
                                       last, grad_rgb, grad_feat, g2d, grad_features, ctx->status, st))
                 return fail(ctx, FHGS_ERR_CUDA, "could not encode the tensor map of grad_feat");

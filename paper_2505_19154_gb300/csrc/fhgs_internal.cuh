@@ -208,6 +208,15 @@ bool launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
                           const float *grgb, const float *gfeat, float *g2d, float *gfeatures, unsigned *status,
                           cudaStream_t st);
 
+// tcgen05 backward with dL/dF streamed through shared memory in 64-channel
+// chunks (render_bwd_stream.cu): D % 128 == 0 and grad_feat given; false
+// (nothing launched) otherwise or when the tensor map cannot be encoded
+bool bwd_stream_supported(int D);
+bool launch_render_bwd_stream(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                              const __nv_bfloat16 *feats, int D, const float *T, const int32_t *last,
+                              const float *grgb, const float *gfeat, float *g2d, float *gfeatures, unsigned *status,
+                              cudaStream_t st);
+
 // The paper's point-to-feature assignment (points.cu).  One view as the
 // kernel reads it: width, height, fx, fy, cx, cy, [R|t] row by row, and the
 // view's feature map [H*W][D] (device).

@@ -155,3 +155,47 @@ def test_tc_fusion_small_against_oracle_and_fp32_path(D):
         assert np.all(rel[seen] <= 1e-4 + risk[seen]), path
         assert np.abs(d_ - ref["den"]).max() <= 1e-4 * max(1.0, ref["den"].max()), path
         assert np.all(o[ref["den"] == 0] == 0), path
+
+
+@pytest.mark.parametrize("D,cams_spec", [(256, [(30, 10, 64, 48)]),
+                                         (384, [(0, 0, 70, 50), (130, 20, 33, 47), (250, -25, 96, 64)]),
+                                         (128, [(200, 15, 80, 56)])])
+def test_tc_backward_streamed(D, cams_spec):
+    """The streamed backward (d_split 1: dL/dF in 64-channel chunks, one
+    scalar pass per batch over all D channels) against the oracle: one
+    camera at D = 256, three ragged cameras at D = 384 (three 128-channel
+    feature-gradient blocks per batch), D = 128 (one block)."""
+    sc = bf16_scene(1500, seed=44 + D, D=D, sh_degree=3)
+    cams = [synth.look_at_camera(synth.ring_position(3.0, a, e), w, h) for a, e, w, h in cams_spec]
+    prm = dict(sh_degree=3, bg=(0.2, 0.1, 0.3))
+    P = sum(c["width"] * c["height"] for c in cams)
+    dC, dF = synth.upstream(10 + D, P, D)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_tc(sc, cams, prm, d_split=1, dC=dC, dF=dF)
+    refs = oracle.forward(sc, cams, prm, sc["features"], prep=prep)
+    check_image(out, refs, cams, feat_tol=1e-2)
+    offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
+    ref = oracle.backward(sc, cams, prm, sc["features"], [dC[offs[i]:offs[i + 1]] for i in range(len(cams))],
+                          [dF[offs[i]:offs[i + 1]] for i in range(len(cams))], prep=prep)
+    check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities", "sh"), tol=1e-3)
+    check_grads(out["grads"], ref, keys=("features",), tol=1e-2)
+
+
+def test_tc_backward_streamed_without_feature_gradient():
+    """grad_features not requested: the streamed kernel still computes G for
+    dL/dw and issues no feature-gradient MMA."""
+    sc = bf16_scene(1200, seed=48, D=256, sh_degree=2)
+    cams = [synth.look_at_camera(synth.ring_position(3.0, 100, -5), 72, 40)]
+    prm = dict(sh_degree=2)
+    dC, dF = synth.upstream(21, 72 * 40, 256)
+    rast = api.Rasterizer(0, sh_degree=2, path=api.PATH_TC, d_split=1)
+    t = {k: _t(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    st = rast.prepare(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams)
+    rast.forward(st, _t(sc["features"], torch.bfloat16))
+    g = rast.backward(st, _t(dC), _t(dF), want_feat_grad=False)
+    torch.cuda.synchronize()
+    assert rast.ctx.sync_status() == api.OK
+    assert g.get("features") is None
+    ref = oracle.backward(sc, cams, prm, sc["features"], [dC], [dF], want_feat=False)
+    got = {k: v.cpu().numpy() for k, v in g.items() if v is not None}
+    check_grads(got, ref, keys=("means", "scales", "quats", "opacities", "sh"), tol=1e-3)
