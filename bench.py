@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--d-split", type=int, default=0, help="feature columns per CTA (0 = auto)")
     ap.add_argument("--fp32-steps", type=int, default=3, help="timed steps of the FP32 comparison path (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of the captured step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="warm-up + one step, no JSON (for ncu)")
     ap.add_argument("--workload", choices=["render", "fusion", "ndfd", "points", "train", "batched", "surfel"],
@@ -224,6 +225,49 @@ def algorithmic_bytes(P, N, D, I, U):
     }
 
 
+def copy_rates(dev, nbytes=1 << 30, reps=3):
+    """Pinned host <-> device copy rates (GB/s, best of `reps`, CUDA events):
+    host to device alone, device to host alone, and both at once on two
+    streams (bytes of both directions over the time of both)."""
+    import torch
+    h_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d_b = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def timed(fn):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    def both():
+        cur = torch.cuda.current_stream(dev)
+        s1.wait_stream(cur)
+        s2.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            d_a.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_b, non_blocking=True)
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+
+    t_h2d = timed(lambda: d_a.copy_(h_in, non_blocking=True))
+    t_d2h = timed(lambda: h_out.copy_(d_b, non_blocking=True))
+    t_both = timed(both)
+    del h_in, h_out, d_a, d_b
+    return {"h2d_gbs": round(nbytes / (t_h2d * 1e-3) / 1e9, 1), "d2h_gbs": round(nbytes / (t_d2h * 1e-3) / 1e9, 1),
+            "both_gbs": round(2 * nbytes / (t_both * 1e-3) / 1e9, 1), "bytes_each": nbytes,
+            "how": "pinned host <-> device copies of 1 GiB, best of 3, CUDA events"}
+
+
 def run_ours(args):
     import torch
     from paper_2505_19154_gb300 import api
@@ -293,9 +337,42 @@ def run_ours(args):
         return ms, prof, launches, ck
 
     K = args.steps
-    ms, prof, launches, clocks = timed(rast, K, True)
+    # per-kernel times from an eager, event-bracketed pass (the same kernels)
+    ms_eager, prof, launches, clocks = timed(rast, K, True)
     if rast.ctx.sync_status() != api.OK:
         raise RuntimeError("device status after timed region")
+    ms = ms_eager
+    graph_note = "eager launches"
+    if not args.no_graph:
+        # the step as one CUDA graph (api.CapturedStep): projection, binning,
+        # forward, backward and projection backward, replayed K times
+        cstep = api.CapturedStep(rast, *g, t["features"], t["dC"], t["dF"], cams)
+        for _ in range(max(args.warmup, 3)):
+            cstep.replay()
+        torch.cuda.synchronize()
+        if rast.ctx.sync_status() != api.OK:
+            raise RuntimeError("device status after the graph warm-up")
+        gclk = ClockSampler(local)
+        barrier()
+        torch.cuda.synchronize()
+        gclk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            cstep.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        clocks = gclk.stop()
+        ms = e0.elapsed_time(e1) / K
+        if world > 1:
+            x = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+            ms = float(x.item())
+        if rast.ctx.sync_status() != api.OK:
+            raise RuntimeError("device status after the timed graph replays")
+        del cstep
+        graph_note = "one CUDA graph per step (api.CapturedStep); per-kernel times from the eager pass"
     value = P * world / (ms * 1e-3) / 1e6
     used_tc = any(k.endswith("_tc") for k in prof)
 
@@ -393,6 +470,12 @@ def run_ours(args):
         del pipe
         e2e = {"value": round(P * world / (mse * 1e-3) / 1e6, 2), "unit": UNIT, "ms_per_step": round(mse, 3),
                "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
+        # the link the end-to-end number is bound by: plain pinned copies of
+        # 1 GiB alone in each direction and both directions together
+        link = copy_rates(dev)
+        e2e["link"] = link
+        e2e["copy_floor_ms"] = round(max(bi / link["h2d_gbs"], bo / link["d2h_gbs"],
+                                         (bi + bo) / link["both_gbs"]) / 1e6, 3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -410,7 +493,8 @@ def run_ours(args):
                        "composited_pairs_tile": Q, "composited_pairs_pixel": Qpix,
                        "gaussians_walked": U,
                        "l2": "inputs larger than L2 (features 1 GB, dL/dfeat 4.2 GB)",
-                       "parallelism": f"independent views, {world} GPU(s)"},
+                       "parallelism": f"independent views, {world} GPU(s)", "launch": graph_note,
+                       "eager_ms_per_step": round(ms_eager, 3)},
             "roofline": roof, "kernels": per, "fp32_path": fp32, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clocks, "gpu_launches": int(launches),
         }
@@ -453,7 +537,8 @@ def run_fusion(args):
     g = tuple(torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).to(dev)
               for k in ("means", "scales", "quats", "opacities", "sh"))
     maps = [device_feature_map(rank, v, views[v]["height"], views[v]["width"], D, dev) for v in range(len(views))]
-    rast = api.Rasterizer(local, sh_degree=3)
+    path = {"tc": api.PATH_TC, "fp32": api.PATH_FP32, "auto": api.PATH_AUTO}[args.path]
+    rast = api.Rasterizer(local, sh_degree=3, path=path)
     for _ in range(max(1, args.warmup)):
         rast.fuse(*g, views, maps)
     torch.cuda.synchronize()
@@ -1026,7 +1111,7 @@ def run_surfel(args):
         return
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    scene, cams, t, P = make_workload(rank, args.n, args.D, dev)
+    scene, cams, t, P = make_workload(rank, args.n, args.D, dev, args.width, args.height)
     D = args.D
     rast = api.Rasterizer(local, sh_degree=3, geometry=api.GEOM_SURFEL)
     g = (t["means"], t["scales"], t["quats"], t["opacities"], t["sh"])
@@ -1114,6 +1199,8 @@ def run_train(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     scene, cams = synth.config3(rank, n=args.n, D=0)
+    if (args.width, args.height) != (1920, 1080):  # centre crop of the same view: same focal length
+        cams = [dict(cams[0], width=args.width, height=args.height, cx=args.width / 2.0, cy=args.height / 2.0)]
     cam = cams[0]
     D = args.D
     # raw parameters of the 3DGS family (host-side input preparation)

@@ -39,6 +39,8 @@ struct fhgs_ctx {
 };
 
 static std::atomic<long long> g_launches{0};
+// the context's small device area: word 0 is the status word
+constexpr size_t kStatusBytes = 64;
 static std::atomic<unsigned long long> g_wait_probe_ns{0};
 
 namespace fhgs {
@@ -309,8 +311,7 @@ fhgs_status fhgs_create(fhgs_ctx **out, int device) {
     fhgs_ctx *ctx = new fhgs_ctx();
     ctx->device = device;
     ctx->sm_count = prop.multiProcessorCount;
-    if (cudaMalloc(&ctx->status, sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess) {
+    if (cudaMalloc(&ctx->status, kStatusBytes) != cudaSuccess || cudaMemset(ctx->status, 0, kStatusBytes) != cudaSuccess) {
         delete ctx;
         return FHGS_ERR_CUDA;
     }
