@@ -186,10 +186,10 @@ def composited_pairs(st, cams, tile=16):
 # source file at capture time: a changed source reports null.
 _CROP_SCALE = (1920 * 1080) / (960 * 544)
 TRAFFIC = {
-    "render_bwd_tc": {"bytes": int((1102.8e6 + 4.5e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "aa67a76d3133b04e0ac9b2d1cb8f9c6e2f330ab991f5d8fae0fb7ba21331d1b4"},
-    "render_fwd_tc": {"bytes": int((7.6e6 + 1018.6e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "aa67a76d3133b04e0ac9b2d1cb8f9c6e2f330ab991f5d8fae0fb7ba21331d1b4"},
+    "render_bwd_tc": {"bytes": int((1102.7e6 + 7.6e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "85cbe8ce1091a39704b17f2ef8bf70e7bdab44a620471f6410bea418bf1403df"},
+    "render_fwd_tc": {"bytes": int((7.7e6 + 1022.9e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "85cbe8ce1091a39704b17f2ef8bf70e7bdab44a620471f6410bea418bf1403df"},
 }
 
 

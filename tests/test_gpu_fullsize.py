@@ -79,7 +79,12 @@ def compare_crop(rgb, feat, T, last, ranges, gids, cams, ci, region, scene, prm,
     assert np.abs(T[idx].cpu().numpy() - ref["T"].reshape(-1))[ok].max(initial=0) <= 1e-5
     np.testing.assert_array_equal(last[idx].cpu().numpy()[ok], ref["last"].reshape(-1)[ok])
     fr = ref["feat"].reshape(-1, D)
-    err = np.abs(feat[idx].cpu().numpy() - fr)[ok].max(initial=0) / max(1.0, np.abs(fr).max())
+    diff = np.abs(feat[idx].cpu().numpy() - fr)
+    err = diff[ok].max(initial=0) / max(1.0, np.abs(fr).max())
+    big = ok[:, None] & (np.abs(fr) >= 0.1 * np.abs(fr).max())
+    rel = (diff[big] / np.abs(fr)[big]).max(initial=0)
+    print(f"camera {ci} crop features: max abs err / max|F| {err:.3g}, "
+          f"max rel err where |F| >= 0.1 max|F| {rel:.3g}")
     assert err <= 1e-2, err
     assert ref["ncontrib"].mean() > 10  # the crop is well inside the scene
     return prep, idx
