@@ -332,8 +332,14 @@ fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void 
  *   L_gt, L_cf [P] device float32, out;
  *   n_contrib  [P] device int32, out, nullable: the number of contributors
  *              (the i of the sums) of each pixel.
- * D must be 32, 64, 128, 256 or 512 (else FHGS_ERR_UNSUPPORTED).  Computed in
- * FP32 on the CUDA cores. */
+ * D must be 32, 64, 128, 256 or 512 (else FHGS_ERR_UNSUPPORTED).  With BF16
+ * features and D = 256 or 512 and p->path AUTO or TC, the D-deep dot
+ * products run on the tensor cores (BF16 operands, FP32 accumulation; the
+ * weights and the running F as BF16 hi + lo pairs), split over a cluster of
+ * D / 128 CTAs per half tile; otherwise (or with FHGS_PATH_FP32) they run in
+ * FP32 on the CUDA cores.  p->path TC with any other dtype or D returns
+ * FHGS_ERR_UNSUPPORTED.  A wait of the tensor-core kernel that runs out
+ * latches FHGS_ERR_TIMEOUT (read by fhgs_sync_status). */
 fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_bins *bins, const void *features,
                           const void *feat_gt, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
                           const fhgs_params *p, float k, float lambda, float *L_gt, float *L_cf, int32_t *n_contrib,

@@ -673,6 +673,12 @@ fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void 
 }
 
 // Shared argument checks of the two NDFD calls.
+// The NDFD losses run on the tensor cores unless the FP32 path is asked for
+// or the features are not BF16 with D in {256, 512}.
+static bool ndfd_use_tc(const fhgs_params *p, fhgs_dtype ftype, int D) {
+    return p->path != FHGS_PATH_FP32 && ftype == FHGS_BF16 && ndfd_tc_supported(D);
+}
+
 static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, const fhgs_bins *bins,
                               const void *features, const void *feat_gt, fhgs_dtype ftype, int D,
                               const fhgs_params *p, float k, float lambda) {
@@ -687,6 +693,8 @@ static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, cons
     if (!aligned16(feat_gt)) return fail(ctx, FHGS_ERR_ALIGNMENT, "feat_gt must be 16-byte aligned");
     if (!std::isfinite(k) || !std::isfinite(lambda))
         return fail(ctx, FHGS_ERR_INVALID_ARG, "the activation's slope and threshold must be finite");
+    if (p->path == FHGS_PATH_TC && !ndfd_use_tc(p, ftype, D))
+        return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core NDFD needs BF16 features with D in {256, 512}");
     return FHGS_OK;
 }
 
@@ -705,7 +713,11 @@ fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs
     cudaStream_t st = (cudaStream_t)stream;
     const Params q = make_params(p);
     ProjView pv = proj_view(const_cast<void *>(proj), n * n_cams);
-    {
+    if (ndfd_use_tc(p, ftype, D)) {
+        Prof pr(ctx, "ndfd_fwd_tc", st);
+        launch_ndfd_fwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, (const __nv_bfloat16 *)feat_gt, D, k,
+                           lambda, L_gt, L_cf, n_contrib, ctx->status, st);
+    } else {
         Prof pr(ctx, "ndfd_fwd", st);
         launch_ndfd_fwd(n, cs, q, pv, *bins, features, feat_gt, ftype == FHGS_BF16, D, k, lambda, L_gt, L_cf, n_contrib, st);
     }

@@ -262,4 +262,11 @@ void launch_ndfd_bwd(long long N, const CamSet &cs, const Params &p, ProjView pv
                      const void *feats, const void *fgt, int bf16, int D, float ks, float lam, const float *dLgt,
                      const float *dLcf, float *g2d, cudaStream_t st);
 
+// NDFD on the tensor cores (ndfd_tc.cu): BF16 features and ground truth, D
+// in {256, 512}, split over a cluster of D / 128 CTAs
+bool ndfd_tc_supported(int D);
+void launch_ndfd_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                        const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam, float *Lgt,
+                        float *Lcf, int32_t *nc, unsigned *status, cudaStream_t st);
+
 }  // namespace fhgs

@@ -1,0 +1,792 @@
+// NDFD losses on the tensor cores (Sec. 3.2-3.3, Eq. 5-6, App. A.1):
+//   L_gt(p) = sum_i w_i sigma_i,   L_cf(p) = sum_i sigma_i w_i (W_{i-1} - F_{i-1} . f_i)
+// over the render's depth-sorted tile lists and Eq. 4 weights (i = 1 the
+// nearest), sigma_i = 1 / (1 + exp(k (cos<f_i, f_gt(p)> - lambda))).
+//
+// Per chunk of 64 list entries and half tile of P = 128 pixels the D-deep
+// work is four products:
+//   Phi   = F_gt . F_c^T                     (P x 64)  f_gt . f_i
+//   X     = F_start . F_c^T + W . Gs         (P x 64)  F_{i-1} . f_i
+//   Gamma = F_c . F_c^T                      (64 x 64) the chunk's Gram matrix
+//   F    += W . F_c                          (P x D)   the running feature
+// where W holds the chunk's weights and Gs the strictly upper part of Gamma
+// (Gs[j][i] = f_j . f_i for j < i), so that W . Gs adds the chunk's own
+// earlier entries to F_{i-1} . f_i.  The weights are decided on the CUDA cores
+// exactly as the tensor-core render decides them (FP32 alpha, transmittance
+// and stop rule).  W, F and Gs enter the products as BF16 hi + lo pairs (the
+// features themselves are BF16), so X carries ~16 mantissa bits.
+//
+// D = 128 NC is split over a cluster of NC CTAs (NC = 2 or 4), each owning
+// 128 channels of every row: its F slice (FP32, 128 TMEM columns), the F_gt
+// slice and the chunk's feature slice.  Every CTA decides all 128 pixels'
+// weights itself: the same inputs and instructions give the same decisions,
+// and recomputing them costs less than sending them (distributed shared
+// memory carries only some 10 bytes per cycle per SM here).  Phi, X and the
+// Gram diagonal (the squared feature norms) are partial sums over the
+// channel slice; after every chunk each CTA sends the rows of pixel slice r
+// (128 / NC pixels) to CTA r, which adds the NC partials and forms cos,
+// sigma and the two loss terms of its pixels.  The exchange is paced by
+// mbarriers with bounded waits (rows ready at the receiver, slots free at
+// the sender).
+//
+// Tensor memory (512 columns): F [0, 128), F hi [128, 192), F lo [192, 256)
+// (two channels per column: the A operand of X read from TMEM), Phi
+// [256, 320), X [320, 384), Gamma [384, 448).
+//
+// Every wait is bounded (2 s of %globaltimer); on expiry the kernel latches
+// FHGS_ERR_TIMEOUT, stops walking, waits (bounded) for its own MMAs, frees its
+// tensor memory and meets its cluster once more before it returns.
+#include <cuda.h>
+
+#include <atomic>
+
+#include "fhgs_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fhgs {
+namespace {
+
+using namespace tc;
+
+constexpr int kC = 64;  // list entries per chunk
+
+constexpr int cal(int x, int a) { return (x + a - 1) / a * a; }
+
+constexpr int kStashRow = 68;  // floats per own pixel in the weight stash (64 + 4: spreads the banks)
+
+template <int NC>
+struct NCfg {
+    static constexpr int kOwn = 128 / NC;    // pixels whose losses this CTA completes
+    static constexpr int kTpp = 256 / kOwn;  // threads per own pixel in the loss pass
+    static constexpr int kEpt = kC / kTpp;   // entries per thread in the loss pass
+    static constexpr int kRow = 2 * kC + 4;  // floats per exchanged pixel row: Phi[64], X[64], 4 of padding
+    // one sender's slot at a receiver: rows, then the Gram diagonal [64], then
+    // the partial |f_gt|^2 of the receiver's pixels
+    static constexpr int kSlotF = kOwn * kRow + kC + kOwn;
+    static constexpr int kOffGt = 0;                        // [2][128 px][64 ch] BF16, K-major, swizzled
+    static constexpr int kOffF = kOffGt + 2 * 128 * 128;    // [2 stages][2][64 g][64 ch] BF16
+    static constexpr int kOffWh = kOffF + 2 * 2 * kC * 128;  // [128 px][64 g] BF16 weights, hi
+    static constexpr int kOffWl = kOffWh + 128 * 128;       // lo
+    static constexpr int kOffGh = kOffWl + 128 * 128;       // [64 i][64 j] BF16 strict Gram part, hi
+    static constexpr int kOffGl = kOffGh + kC * 128;        // lo
+    static constexpr int kOffRecv = kOffGl + kC * 128;      // [NC][kSlotF] floats
+    static constexpr int kOffStash = kOffRecv + cal(NC * kSlotF * 4, 16);  // [kOwn][kStashRow] w, then T
+    static constexpr int kOffRec = kOffStash + 2 * kOwn * kStashRow * 4;  // [2 stages][64] (a, b) records
+    static constexpr int kOffGid = kOffRec + 2 * kC * 32;          // [3][64] ids
+    static constexpr int kOffPix = kOffGid + 3 * kC * 4;           // per pixel: T, done, last, P0, L0, |f_gt|^2
+    static constexpr int kOffDiag = kOffPix + 6 * 128 * 4;         // [64] Gram diagonal of the chunk
+    static constexpr int kOffAcc = kOffDiag + kC * 4;              // [3][kOwn] L_gt, L_cf, count of own pixels
+    static constexpr int kOffBar = cal(kOffAcc + 3 * kOwn * 4, 8);
+    static constexpr int kSmem = 1024 + kOffBar + 64;  // 6 barriers and the TMEM slot
+    static_assert(kSmem <= 232448, "NDFD CTA exceeds the opt-in shared memory");
+    static_assert(8 * 32 * 20 * 4 <= kOffGh - kOffWh, "the row staging must fit in the weight operands");
+    static constexpr uint32_t kColF = 0, kColFh = 128, kColFl = 192, kColPhi = 256, kColX = 320, kColGam = 384;
+};
+
+// BF16 hi + lo parts of x: hi = bf16(x), lo = bf16(x - hi).
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Byte offset of K-step ks (16 BF16 along K) inside a K-major operand whose
+// 64-element K blocks are `blk` bytes apart.
+__device__ __forceinline__ uint32_t kstep(int ks, uint32_t blk) { return (uint32_t)(ks >> 2) * blk + (uint32_t)(ks & 3) * 32u; }
+
+// Everything a CTA needs to know about its item (tile, half) and its place
+// in the cluster.
+struct Item {
+    int ci, tx, ty, half, q;
+    uint32_t s, e;
+    const DevCam *cam;
+};
+
+__device__ __forceinline__ Item make_item(const CamSet &cs, const uint32_t *ranges, int item, int q) {
+    Item it;
+    const int tile = item >> 1;
+    it.half = item & 1;
+    it.ci = cam_of_tile(cs, tile);
+    it.cam = &cs.c[it.ci];
+    const int lt = tile - it.cam->tile_off;
+    it.tx = lt % it.cam->tiles_x;
+    it.ty = lt / it.cam->tiles_x;
+    it.s = ranges[2 * tile];
+    it.e = ranges[2 * tile + 1];
+    it.q = q;
+    return it;
+}
+
+// Pixel `pidx` (0..127) of the item's half tile: (i, j) = (pidx % 16, pidx / 16).
+__device__ __forceinline__ bool item_pixel(const Item &it, int pidx, long long &pix, float &fpx, float &fpy) {
+    const int px = it.tx * kTile + (pidx & 15), py = it.ty * kTile + it.half * 8 + (pidx >> 4);
+    pix = it.cam->pix_off + (long long)py * it.cam->W + px;
+    fpx = px + 0.5f;
+    fpy = py + 0.5f;
+    return px < it.cam->W && py < it.cam->H;
+}
+
+
+struct __align__(16) RecAB {
+    float4 a, b;  // GRec.a, GRec.b: mean, conic, opacity
+};
+
+// Per-pixel walk state in shared memory (one entry per pixel of the half tile).
+struct PixState {
+    float *T;   // transmittance entering the next chunk
+    int *done;  // the pixel's walk has stopped
+    int *last;  // list position after its last contributor
+    float *P0;  // group 0's product of (1 - alpha) over its 32 entries
+    int *L0;    // group 0's last entry with alpha > 0, or -1
+};
+
+// Front-to-back weights of one chunk (list entries [pos0, pos0 + nb), records
+// R) for the half tile's 128 pixels, by the tensor-core render's rules: 256
+// threads, group g = tid / 128 takes entries [32 g, 32 g + 32); both groups
+// evaluate their alphas and running products of (1 - alpha) at once, then
+// group 1 starts from T_in P_0 unless group 0 stops.  alpha = min(alpha_max,
+// op G) counts when q2 <= cutoff and alpha >= alpha_min; the walk stops at
+// the first counted entry j with T_j (1 - alpha_j) < t_eps, which itself does
+// not contribute.  Every CTA of a cluster takes the same decisions (same
+// inputs, same instructions), which costs less than exchanging them.  Writes
+// w (negated when `neg`) as BF16 hi + lo into the K-major [128 px][64]
+// operands, and w and T (before the entry) of the pixels [own0, own0 + own)
+// into the stash.  Returns, uniformly over the CTA, whether every pixel has
+// stopped after the chunk.
+__device__ __forceinline__ bool chunk_weights(const Params &p, const RecAB *R, int nb, int pos0, int pidx, int grp,
+                                              float fpx, float fpy, PixState ps, uint8_t *sWh, uint8_t *sWl,
+                                              float *stash_w, float *stash_T, int own0, int own, bool neg) {
+    const float T_in = ps.T[pidx];
+    const bool done_in = ps.done[pidx] != 0;
+    const int last_in = ps.last[pidx];
+    float a[32], l[32];
+    float P = 1.f;
+    int lastc = -1;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+        const int j = grp * 32 + jj;
+        const float4 A4 = R[j].a, B4 = R[j].b;
+        const float dx = fpx - A4.x, dy = fpy - A4.y;
+        const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
+        const float al = fminf(p.amax, B4.y * gauss_q2(q2));
+        a[jj] = (j < nb && q2 <= p.cut && al >= p.amin) ? al : 0.f;
+        l[jj] = P;
+        P *= 1.f - a[jj];
+        lastc = a[jj] > 0.f ? jj : lastc;
+    }
+    if (grp == 0) {
+        ps.P0[pidx] = P;
+        ps.L0[pidx] = lastc;
+    }
+    __syncthreads();
+    const float P0 = ps.P0[pidx];
+    const bool stop0 = !done_in && T_in * P0 < p.teps;
+    const float Ts = grp == 0 ? T_in : T_in * P0;
+    bool done = grp == 0 ? done_in : (done_in || stop0);
+    const bool owner = grp == 0 ? (done_in || stop0) : !(done_in || stop0);
+    const int pl = pidx - own0;
+    const bool mine = pl >= 0 && pl < own;
+    float Tstop = 0.f;
+    int lastw = -1;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+        uint32_t hw[4], lw[4];
+        float w8[8], T8[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int jj = 8 * qq + h;
+            const float Tj = Ts * l[jj];
+            const float Tn = Ts * (jj < 31 ? l[jj + 1] : P);
+            bool okj = a[jj] > 0.f && !done;
+            const bool stop = okj && Tn < p.teps;
+            if (stop) Tstop = Tj;
+            done = done || stop;
+            okj = okj && !stop;
+            w8[h] = okj ? a[jj] * Tj : 0.f;
+            T8[h] = Tj;
+            if (okj) lastw = jj;
+        }
+        if (mine) {
+            float *dw = stash_w + pl * kStashRow + grp * 32 + 8 * qq, *dT = stash_T + pl * kStashRow + grp * 32 + 8 * qq;
+            *reinterpret_cast<float4 *>(dw) = make_float4(w8[0], w8[1], w8[2], w8[3]);
+            *reinterpret_cast<float4 *>(dw + 4) = make_float4(w8[4], w8[5], w8[6], w8[7]);
+            *reinterpret_cast<float4 *>(dT) = make_float4(T8[0], T8[1], T8[2], T8[3]);
+            *reinterpret_cast<float4 *>(dT + 4) = make_float4(T8[4], T8[5], T8[6], T8[7]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(neg ? -w8[2 * u] : w8[2 * u], h0, l0);
+            split_bf16(neg ? -w8[2 * u + 1] : w8[2 * u + 1], h1, l1);
+            hw[u] = pack2(h0, h1);
+            lw[u] = pack2(l0, l1);
+        }
+        *reinterpret_cast<uint4 *>(sWh + swz(pidx, grp * 4 + qq)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(sWl + swz(pidx, grp * 4 + qq)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    if (owner) {  // exactly one group carries the pixel's state to the next chunk
+        if (grp == 0) {
+            ps.T[pidx] = done_in ? T_in : Tstop;
+            ps.done[pidx] = 1;
+            ps.last[pidx] = lastw >= 0 ? pos0 + lastw + 1 : last_in;
+        } else {
+            const int L0 = ps.L0[pidx];
+            ps.T[pidx] = done ? Tstop : Ts * P;
+            ps.done[pidx] = done ? 1 : 0;
+            ps.last[pidx] = lastw >= 0 ? pos0 + 32 + lastw + 1 : (L0 >= 0 ? pos0 + L0 + 1 : last_in);
+        }
+    }
+    return __syncthreads_and(grp == 0 || done) != 0;
+}
+
+// F (FP32, TMEM columns [colF, colF + 128)) -> BF16 hi + lo copies in TMEM,
+// two channels per column (the layout of an A operand read from TMEM: lane =
+// pixel, 8 columns per K step of 16).  Warp w converts channels
+// [64 (w / 4), + 64) of its lane quadrant.
+__device__ __forceinline__ void split_to_tmem(uint32_t taddr, uint32_t colF, uint32_t colH, uint32_t colL, int warp) {
+    const uint32_t lq = (uint32_t)((warp & 3) * 32) << 16;
+    const int h = warp >> 2;
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+        float v[32];
+        tmem_ld32(taddr + lq + colF + 64 * h + 32 * part, v);
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(v[2 * i], h0, l0);
+            split_bf16(v[2 * i + 1], h1, l1);
+            hi[i] = pack2(h0, h1);
+            lo[i] = pack2(l0, l1);
+        }
+        tmem_st16(taddr + lq + colH + 32 * h + 16 * part, hi);
+        tmem_st16(taddr + lq + colL + 32 * h + 16 * part, lo);
+    }
+    tmem_st_wait();
+}
+
+// Gamma (TMEM lanes = entries i, columns = entries j) -> one masked part as a
+// K-major B operand [64 rows i][64 j] (BF16 hi + lo): `before` keeps j < i
+// (the entries before i), else j > i.  Warps 0, 1 (lanes = rows 0..63) take
+// columns 0..31, warps 4, 5 columns 32..63; the warp holding column i also
+// writes the diagonal entry.
+__device__ __forceinline__ void gram_part(uint32_t taddr, uint32_t colG, int warp, int lane, bool before,
+                                          uint8_t *sGh, uint8_t *sGl, float *diag) {
+    const int i = (warp & 3) * 32 + lane, ch = warp >> 2;
+    float g[32];
+    tmem_ld32(taddr + ((uint32_t)((warp & 3) * 32) << 16) + colG + 32 * ch, g);
+    float dg = 0.f;
+    bool mine = false;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int h = 0; h < 8; h += 2) {
+            float v2[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int jl = 8 * c + h + u, j = 32 * ch + jl;
+                if (j == i) {
+                    dg = g[jl];
+                    mine = true;
+                }
+                v2[u] = (before ? j < i : j > i) ? g[jl] : 0.f;
+            }
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(v2[0], h0, l0);
+            split_bf16(v2[1], h1, l1);
+            hw[h >> 1] = pack2(h0, h1);
+            lw[h >> 1] = pack2(l0, l1);
+        }
+        *reinterpret_cast<uint4 *>(sGh + swz(i, 4 * ch + c)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(sGl + swz(i, 4 * ch + c)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    if (mine) diag[i] = dg;
+}
+
+// Shared-memory views and loaders of one CTA's item, common to the forward
+// and the backward.
+template <int NC>
+struct ItemSmem {
+    using C = NCfg<NC>;
+    uint8_t *sm;
+    uint32_t sm_s;
+    __device__ RecAB *rec(int b) const { return reinterpret_cast<RecAB *>(sm + C::kOffRec + (b & 1) * kC * 32); }
+    __device__ uint32_t *gid(int b) const {
+        return reinterpret_cast<uint32_t *>(sm + C::kOffGid + ((b % 3 + 3) % 3) * kC * 4);
+    }
+    __device__ uint32_t feat_s(int b) const { return sm_s + C::kOffF + (uint32_t)(b & 1) * (2 * kC * 128); }
+    __device__ PixState pix() const {
+        int *base = reinterpret_cast<int *>(sm + C::kOffPix);
+        return PixState{reinterpret_cast<float *>(base), base + 128, base + 256, reinterpret_cast<float *>(base + 384),
+                        base + 512};
+    }
+    __device__ float *ngt() const { return reinterpret_cast<float *>(sm + C::kOffPix) + 640; }
+    __device__ float *diag() const { return reinterpret_cast<float *>(sm + C::kOffDiag); }
+    __device__ float *recv() const { return reinterpret_cast<float *>(sm + C::kOffRecv); }
+    __device__ float *stash_w() const { return reinterpret_cast<float *>(sm + C::kOffStash); }
+    __device__ float *stash_T() const { return stash_w() + C::kOwn * kStashRow; }
+    __device__ float *acc(int k) const { return reinterpret_cast<float *>(sm + C::kOffAcc) + k * C::kOwn; }
+    __device__ uint64_t *bars() const { return reinterpret_cast<uint64_t *>(sm + C::kOffBar); }
+};
+
+// Every loader commits exactly one cp.async group in every thread, empty or
+// not, so that the waits on group counts hold.  Chunk b of the item holds list
+// entries [s + 64 b, s + 64 b + 64) of camera ci; `q` selects the CTA's 128
+// channels.
+template <int NC>
+struct Loader {
+    const ItemSmem<NC> &S;
+    const uint32_t *gids;
+    const GRec *rec;
+    const __nv_bfloat16 *feats;
+    uint32_t s, e;
+    int nchunks, q, tid;
+    __device__ void gid(int b) const {
+        if (b >= 0 && b < nchunks && tid < kC) {
+            const uint32_t at = s + (uint32_t)b * kC + tid;
+            cp_async4(smem_u32(S.gid(b) + tid), gids + (at < e ? at : s), at < e);
+        }
+        cp_async_commit();
+    }
+    __device__ void records(int b) const {
+        if (b >= 0 && b < nchunks && tid < kC) {
+            const bool v = s + (uint32_t)b * kC + tid < e;
+            const uint32_t dst = smem_u32(S.rec(b) + tid);
+            const GRec *src = rec + (v ? S.gid(b)[tid] : 0u);
+            cp_async16(dst, &src->a, v);
+            cp_async16(dst + 16, &src->b, v);
+        }
+        cp_async_commit();
+    }
+    __device__ void features(int b) const {
+        if (b >= 0 && b < nchunks) {
+            const int nb = (int)min((uint32_t)kC, e - (s + (uint32_t)b * kC));
+            const uint32_t fb = S.feat_s(b);
+            const uint32_t *ids = S.gid(b);
+#pragma unroll
+            for (int c = tid; c < kC * 16; c += 256) {
+                const int g = c >> 4, cc = c & 15;
+                const bool valid = g < nb;
+                cp_async16(fb + (uint32_t)(cc >> 3) * (kC * 128) + swz(g, cc & 7),
+                           feats + (size_t)(valid ? ids[g] : 0u) * (128 * NC) + 128 * q + cc * 8, valid);
+            }
+        }
+        cp_async_commit();
+    }
+};
+
+// Descriptors of the chunk's operands (address field = byte address / 16).
+struct ChunkDesc {
+    uint64_t FK, FM;  // chunk features as a K-major operand (rows = entries) and as an MN-major B (K = entries)
+};
+__device__ __forceinline__ ChunkDesc chunk_desc(uint32_t fb) {
+    return ChunkDesc{sdesc(fb, 16, 1024), sdesc(fb, kC * 128, 1024)};
+}
+constexpr uint32_t kId64 = idesc_bf16(128, kC, false, false);    // P x 64 products, K-major A and B
+constexpr uint32_t kId128 = idesc_bf16(128, 128, false, true);   // P x 128 channel update, MN-major B
+
+// Gamma = F_c F_c^T: M = 128 rows of A read the chunk's 64 rows and the 64
+// rows after them (lanes 64..127 of the result are never read).
+__device__ __forceinline__ void issue_gram(uint32_t tG, const ChunkDesc &cd) {
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks) {
+        const uint64_t o = (uint64_t)(kstep(ks, kC * 128) >> 4);
+        mma_bf16(tG, cd.FK + o, cd.FK + o, kId64, ks > 0 ? 1u : 0u);
+    }
+}
+// D (P x 64) [+]= A(P x 128 channels) F_c^T, A a K-major operand in shared memory with 64-channel blocks `blk` apart.
+__device__ __forceinline__ void issue_rows_x_chunk(uint32_t tD, uint64_t a0, uint32_t blk, const ChunkDesc &cd,
+                                                   bool acc) {
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks)
+        mma_bf16(tD, a0 + (uint64_t)(kstep(ks, blk) >> 4), cd.FK + (uint64_t)(kstep(ks, kC * 128) >> 4), kId64,
+                 (acc || ks > 0) ? 1u : 0u);
+}
+// D (P x 64) [+]= (hi + lo)(P x 128 channels, TMEM) F_c^T.
+__device__ __forceinline__ void issue_tmem_x_chunk(uint32_t tD, uint32_t tH, uint32_t tL, const ChunkDesc &cd,
+                                                   bool acc) {
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks)
+        mma_bf16_ta(tD, tH + 8 * ks, cd.FK + (uint64_t)(kstep(ks, kC * 128) >> 4), kId64, (acc || ks > 0) ? 1u : 0u);
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks) mma_bf16_ta(tD, tL + 8 * ks, cd.FK + (uint64_t)(kstep(ks, kC * 128) >> 4), kId64, 1u);
+}
+// F (P x 128) [+]= (Wh + Wl)(P x 64) F_c(64 x 128).
+__device__ __forceinline__ void issue_update(uint32_t tF, uint64_t wh, uint64_t wl, const ChunkDesc &cd, bool acc) {
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks)
+        mma_bf16(tF, wh + (uint64_t)((ks * 32) >> 4), cd.FM + (uint64_t)((ks * 2048) >> 4), kId128,
+                 (acc || ks > 0) ? 1u : 0u);
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks)
+        mma_bf16(tF, wl + (uint64_t)((ks * 32) >> 4), cd.FM + (uint64_t)((ks * 2048) >> 4), kId128, 1u);
+}
+// D (P x 64) [+]= Wh Gh + Wl Gh + Wh Gl (the chunk's own Gram part).
+__device__ __forceinline__ void issue_w_gram(uint32_t tD, uint64_t wh, uint64_t wl, uint64_t gh, uint64_t gl,
+                                             bool acc) {
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks)
+        mma_bf16(tD, wh + (uint64_t)((ks * 32) >> 4), gh + (uint64_t)((ks * 32) >> 4), kId64,
+                 (acc || ks > 0) ? 1u : 0u);
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) mma_bf16(tD, wl + (uint64_t)((ks * 32) >> 4), gh + (uint64_t)((ks * 32) >> 4), kId64, 1u);
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) mma_bf16(tD, wh + (uint64_t)((ks * 32) >> 4), gl + (uint64_t)((ks * 32) >> 4), kId64, 1u);
+}
+
+// The partial Phi (warps 0..3) or X (warps 4..7) rows of this warp's lane
+// quadrant -> the slot of this CTA at the receiver of those pixels, then one
+// arrival per thread on the receiver's "data ready" barrier.  The rows go
+// through a 2 KB staging tile per warp (`stage`, free shared memory), 16
+// columns at a time, so that each remote store instruction writes 64
+// contiguous bytes of 8 rows rather than 16 bytes of 32 rows.  Warps 0..3
+// also send the pixels' partial |f_gt|^2, and the receiver's first X warp
+// the chunk's Gram diagonal.
+template <int NC>
+__device__ __forceinline__ void send_rows(const ItemSmem<NC> &S, uint32_t taddr, uint32_t colA, uint32_t colB, int q,
+                                          int warp, int lane, float *stage) {
+    using C = NCfg<NC>;
+    constexpr int kSR = 20;  // floats per staged row (16 + 4: spreads the banks)
+    const int qd = warp & 3, dst = qd * NC / 4;
+    const int row0 = qd * 32 - dst * C::kOwn;  // the warp's first row in the receiver's slot
+    const uint32_t slot = mapa(smem_u32(S.recv() + q * C::kSlotF), (uint32_t)dst);
+    const bool second = warp >= 4;
+    float *st = stage + warp * 32 * kSR;
+#pragma unroll
+    for (int piece = 0; piece < 4; ++piece) {
+        float v[16];
+        tmem_ld16(taddr + ((uint32_t)(qd * 32) << 16) + (second ? colB : colA) + 16 * piece, v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            *reinterpret_cast<float4 *>(st + lane * kSR + 4 * i) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const int r = 8 * it + (lane >> 2), c4 = (lane & 3) * 4;
+            const float4 x = *reinterpret_cast<const float4 *>(st + r * kSR + c4);
+            st_cluster_v4(slot + (uint32_t)((row0 + r) * C::kRow + (second ? kC : 0) + 16 * piece + c4) * 4u, x.x, x.y,
+                          x.z, x.w);
+        }
+        __syncwarp();
+    }
+    const int row = row0 + lane;
+    if (!second) {
+        st_cluster_f32(slot + (uint32_t)(C::kOwn * C::kRow + kC + row) * 4u, S.ngt()[qd * 32 + lane]);
+    } else if (qd == dst * (4 / NC)) {
+        st_cluster_v2(slot + (uint32_t)(C::kOwn * C::kRow + 2 * lane) * 4u, S.diag()[2 * lane], S.diag()[2 * lane + 1]);
+    }
+    mbar_arrive_cluster(mapa(smem_u32(&S.bars()[2]), (uint32_t)dst));
+}
+
+// Stages the CTA's F_gt slice (BF16, K-major [2][128 px][64 ch]) of the
+// item's pixels, zero outside the image; commits one cp.async group.
+template <int NC>
+__device__ __forceinline__ void load_gt(const ItemSmem<NC> &S, const Item &it, const __nv_bfloat16 *fgt, int q,
+                                        int tid) {
+    using C = NCfg<NC>;
+    const uint32_t g0 = S.sm_s + C::kOffGt;
+    for (int c = tid; c < 128 * 16; c += 256) {
+        const int row = c >> 4, cc = c & 15;
+        long long rp;
+        float fx, fy;
+        const bool v = item_pixel(it, row, rp, fx, fy);
+        cp_async16(g0 + (uint32_t)(cc >> 3) * (128 * 128) + swz(row, cc & 7),
+                   fgt + (size_t)(v ? rp : 0) * (128 * NC) + 128 * q + cc * 8, v);
+    }
+    cp_async_commit();
+}
+
+// Partial |f_gt|^2 over the CTA's channels of pixel tid (tid < 128).
+template <int NC>
+__device__ __forceinline__ void gt_norm(const ItemSmem<NC> &S, int tid) {
+    using C = NCfg<NC>;
+    if (tid >= 128) return;
+    float s2 = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < 16; ++cc) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(S.sm + C::kOffGt + (cc >> 3) * (128 * 128) + swz(tid, cc & 7));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float lo = __uint_as_float(w[u] << 16), hi = __uint_as_float(w[u] & 0xFFFF0000u);
+            s2 = fmaf(lo, lo, s2);
+            s2 = fmaf(hi, hi, s2);
+        }
+    }
+    S.ngt()[tid] = s2;
+}
+
+// 1 / |f_i| of the chunk's entries (tid < 64) from the NC senders' Gram
+// diagonals, 0 for a zero feature row, into `inv`.
+template <int NC>
+__device__ __forceinline__ void entry_inv_norms(const ItemSmem<NC> &S, int tid, float *inv) {
+    using C = NCfg<NC>;
+    if (tid >= kC) return;
+    float n2 = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < NC; ++sl) n2 += S.recv()[sl * C::kSlotF + C::kOwn * C::kRow + tid];
+    inv[tid] = n2 > 0.f ? 1.f / sqrtf(n2) : 0.f;
+}
+
+// sigma = 1 / (1 + exp(k (phi - lambda))) with the fast exponential and
+// reciprocal (relative error ~1e-6, far inside the loss bar).
+__device__ __forceinline__ float sigma_fast(float phi, float k, float lam) {
+    return __frcp_rn(1.f + __expf(k * (phi - lam)));
+}
+
+// The loss pass of the own pixels: kTpp threads per pixel, kEpt consecutive
+// entries each; adds the NC senders' partial Phi and X, then sigma and the
+// two loss terms of every contributor (w > 0).
+template <int NC>
+__device__ __forceinline__ void own_losses(const ItemSmem<NC> &S, int tid, float ks, float lam, const float *inv) {
+    using C = NCfg<NC>;
+    constexpr int E = C::kEpt;
+    const int pl = tid / C::kTpp, k0 = (tid % C::kTpp) * E;
+    const float *rv = S.recv();
+    float ph[E], x[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) ph[k] = x[k] = 0.f;
+    float n2 = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < NC; ++sl) {
+        const float *slot = rv + sl * C::kSlotF;
+        n2 += slot[C::kOwn * C::kRow + kC + pl];
+#pragma unroll
+        for (int k = 0; k < E; k += 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(slot + pl * C::kRow + k0 + k);
+            const float4 b = *reinterpret_cast<const float4 *>(slot + pl * C::kRow + kC + k0 + k);
+            ph[k] += a.x; ph[k + 1] += a.y; ph[k + 2] += a.z; ph[k + 3] += a.w;
+            x[k] += b.x; x[k + 1] += b.y; x[k + 2] += b.z; x[k + 3] += b.w;
+        }
+    }
+    const float igt = n2 > 0.f ? 1.f / sqrtf(n2) : 0.f;
+    float lg = 0.f, lc = 0.f, cnt = 0.f;
+#pragma unroll
+    for (int k = 0; k < E; k += 4) {
+        const float4 w4 = *reinterpret_cast<const float4 *>(S.stash_w() + pl * kStashRow + k0 + k);
+        const float4 T4 = *reinterpret_cast<const float4 *>(S.stash_T() + pl * kStashRow + k0 + k);
+        const float4 i4 = *reinterpret_cast<const float4 *>(inv + k0 + k);
+        const float wv[4] = {w4.x, w4.y, w4.z, w4.w}, Tv[4] = {T4.x, T4.y, T4.z, T4.w};
+        const float iv[4] = {i4.x, i4.y, i4.z, i4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (wv[u] > 0.f) {
+                const float sig = sigma_fast(ph[k + u] * iv[u] * igt, ks, lam);
+                lg = fmaf(wv[u], sig, lg);
+                lc = fmaf(sig * wv[u], (1.f - Tv[u]) - x[k + u], lc);
+                cnt += 1.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = C::kTpp / 2; o > 0; o >>= 1) {
+        lg += __shfl_xor_sync(0xffffffffu, lg, o);
+        lc += __shfl_xor_sync(0xffffffffu, lc, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (tid % C::kTpp == 0) {
+        S.acc(0)[pl] += lg;
+        S.acc(1)[pl] += lc;
+        S.acc(2)[pl] += cnt;
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(256, 1)
+    k_ndfd_fwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
+                  const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats,
+                  const __nv_bfloat16 *__restrict__ fgt, float ks, float lam, float *Lgt_out, float *Lcf_out,
+                  int32_t *nc_out, unsigned *status) {
+    using C = NCfg<NC>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = align_smem_1024(smem_raw);
+    if (probe_wait_expired(p, sm, status)) return;  // uniform over the grid, before any cluster operation
+    const ItemSmem<NC> S{sm, smem_u32(sm)};
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = (int)cluster_rank();
+    const Item it = make_item(cs, ranges, (int)(blockIdx.x / NC), q);
+    // a wait that ran out anywhere in the grid makes the later CTAs skip their
+    // walk (no waits), so that a fault of the exchange costs seconds, not a
+    // wave of timeouts per CTA; a cluster's CTAs may disagree, which only
+    // makes the walking ones' waits run out too
+    const bool skip = (*(volatile unsigned *)status & ST_TIMEOUT) != 0;
+    const int nchunks = skip ? 0 : (int)((it.e - it.s + kC - 1) / kC);
+    uint64_t *bars = S.bars();  // [0] Gamma done, [1] chunk's MMAs done, [2] rows ready, [3] slots free
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
+    const PixState ps = S.pix();
+    const int grp = tid >> 7, pidx = tid & 127, own0 = q * C::kOwn;
+    long long pix;
+    float fpx, fpy;
+    const bool inside = item_pixel(it, pidx, pix, fpx, fpy);
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 256);  // NC senders x 256 / NC threads
+        mbar_init(&bars[3], NC);   // one arrival per receiver
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(tslot, 512);
+    if (grp == 0) {
+        ps.T[pidx] = 1.f;
+        ps.done[pidx] = inside ? 0 : 1;
+        ps.last[pidx] = 0;
+    }
+    if (tid < C::kOwn) S.acc(0)[tid] = S.acc(1)[tid] = S.acc(2)[tid] = 0.f;
+    const Loader<NC> L{S, gids, pv.rec + (long long)it.ci * N, feats, it.s, it.e, nchunks, q, tid};
+    load_gt<NC>(S, it, fgt, q, tid);
+    L.gid(0);
+    L.gid(1);
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t taddr = *tslot;
+    cluster_sync();  // every CTA's barriers are initialised before the first remote arrival
+    cp_async_wait<1>();  // F_gt and the ids of chunk 0
+    __syncthreads();
+    L.records(0);
+    L.features(0);
+    gt_norm<NC>(S, tid);
+
+    const uint32_t sGt = S.sm_s + C::kOffGt, sWh = S.sm_s + C::kOffWh, sWl = S.sm_s + C::kOffWl;
+    const uint32_t sGh = S.sm_s + C::kOffGh, sGl = S.sm_s + C::kOffGl;
+    const uint64_t dGt = sdesc(sGt, 16, 1024), dWh = sdesc(sWh, 16, 1024), dWl = sdesc(sWl, 16, 1024);
+    const uint64_t dGh = sdesc(sGh, 16, 1024), dGl = sdesc(sGl, 16, 1024);
+    const uint32_t tF = taddr + C::kColF, tFh = taddr + C::kColFh, tFl = taddr + C::kColFl;
+    const uint32_t tPhi = taddr + C::kColPhi, tX = taddr + C::kColX, tGam = taddr + C::kColGam;
+
+    bool timeout = false, pending = false;
+    int b = 0;
+    for (; b < nchunks; ++b) {
+        const uint32_t base = it.s + (uint32_t)b * kC;
+        const int nb = (int)min((uint32_t)kC, it.e - base);
+        cp_async_wait<0>();  // ids of b+1, records and features of b
+        __syncthreads();
+        L.gid(b + 2);
+        L.records(b + 1);
+        L.features(b + 1);  // its stage was last read by the MMAs of chunk b-1, complete
+        const bool all_done = chunk_weights(p, S.rec(b), nb, (int)(base - it.s), pidx, grp, fpx, fpy, ps, sm + C::kOffWh,
+                                            sm + C::kOffWl, S.stash_w(), S.stash_T(), own0, C::kOwn, false);
+        if (b > 0) split_to_tmem(taddr, C::kColF, C::kColFh, C::kColFl, warp);  // F after chunk b-1
+        fence_async_smem();
+        tc_before();
+        __syncthreads();
+        const ChunkDesc cd = chunk_desc(S.feat_s(b));
+        if (tid == 0) {
+            tc_after();
+            issue_gram(tGam, cd);
+            mma_commit(&bars[0]);
+            issue_rows_x_chunk(tPhi, dGt, 128 * 128, cd, false);
+            if (b > 0) issue_tmem_x_chunk(tX, tFh, tFl, cd, false);
+            issue_update(tF, dWh, dWl, cd, b > 0);
+        }
+        bool ok = true;
+        if ((warp & 3) < 2) {
+            ok = mbar_wait(&bars[0], (uint32_t)(b & 1));
+            if (ok) {
+                tc_after();
+                gram_part(taddr, C::kColGam, warp, lane, true, sm + C::kOffGh, sm + C::kOffGl, S.diag());
+            }
+            fence_async_smem();
+        }
+        const bool tmo = __syncthreads_or(!ok) != 0;
+        if (tid == 0) {
+            tc_after();
+            if (!tmo) issue_w_gram(tX, dWh, dWl, dGh, dGl, b > 0);
+            mma_commit(&bars[1]);
+        }
+        pending = true;
+        ok = mbar_wait(&bars[1], (uint32_t)(b & 1));
+        if (__syncthreads_or(!ok) || tmo) {
+            timeout = true;
+            if (tid == 0) latch(status, ST_TIMEOUT);
+            break;
+        }
+        pending = false;
+        tc_after();
+        // exchange: every receiver has consumed this CTA's slots of chunk b-1
+        ok = b == 0 || mbar_wait_cluster(&bars[3], (uint32_t)((b - 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+            if (tid == 0) latch(status, ST_TIMEOUT);
+            break;
+        }
+        // the weight operands are free until the next chunk's weights: 8 warps x 2.5 KB of staging
+        send_rows<NC>(S, taddr, C::kColPhi, C::kColX, q, warp, lane, reinterpret_cast<float *>(sm + C::kOffWh));
+        ok = mbar_wait_cluster(&bars[2], (uint32_t)(b & 1));
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+            if (tid == 0) latch(status, ST_TIMEOUT);
+            break;
+        }
+        entry_inv_norms<NC>(S, tid, S.diag());  // the diagonal itself was sent: reuse its buffer
+        __syncthreads();
+        own_losses<NC>(S, tid, ks, lam, S.diag());
+        __syncthreads();
+        if (tid < NC) mbar_arrive_cluster(mapa(smem_u32(&bars[3]), (uint32_t)tid));  // this CTA's slots are read
+        if (all_done) break;
+    }
+    cp_async_wait_all();
+    if (timeout) {
+        if (pending) mbar_wait(&bars[1], (uint32_t)(b & 1));
+    } else if (tid < C::kOwn && !skip) {
+        long long opix;
+        float fx, fy;
+        if (item_pixel(it, own0 + tid, opix, fx, fy)) {
+            Lgt_out[opix] = S.acc(0)[tid];
+            Lcf_out[opix] = S.acc(1)[tid];
+            if (nc_out) nc_out[opix] = (int32_t)S.acc(2)[tid];
+        }
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, 512);
+    cluster_sync();  // no CTA leaves while another may still write to its shared memory
+}
+
+// Launches one cluster of NC CTAs per (tile, half): grid = 2 NC tiles.
+template <int NC, typename... Args>
+void launch_cluster(void (*kernel)(Args...), int smem, unsigned n_items, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_items * NC);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = NC;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    note_launch(1);
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <int NC>
+void launch_fwd_tc_t(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                     const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, float ks, float lam, float *Lgt,
+                     float *Lcf, int32_t *nc, unsigned *status, cudaStream_t st) {
+    static std::atomic<unsigned long long> smem_set{0};
+    allow_max_smem(smem_set, k_ndfd_fwd_tc<NC>);
+    launch_cluster<NC>(k_ndfd_fwd_tc<NC>, NCfg<NC>::kSmem, (unsigned)cs.total_tiles * 2u, st, N, cs, p, pv,
+                       (const uint32_t *)bins.gids, (const uint32_t *)bins.ranges, feats, fgt, ks, lam, Lgt, Lcf, nc,
+                       status);
+}
+
+}  // namespace
+
+bool ndfd_tc_supported(int D) { return D == 256 || D == 512; }
+
+void launch_ndfd_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                        const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam, float *Lgt,
+                        float *Lcf, int32_t *nc, unsigned *status, cudaStream_t st) {
+    if (cs.total_tiles == 0) return;
+    if (D == 512) launch_fwd_tc_t<4>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, status, st);
+    else if (D == 256) launch_fwd_tc_t<2>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, status, st);
+}
+
+}  // namespace fhgs

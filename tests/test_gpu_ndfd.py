@@ -39,9 +39,15 @@ def ndfd_case(n, seed, D, cams, bf16=True, sh_degree=1, spread=0.5):
     return sc, fg
 
 
-def run_ndfd(sc, cams, prm, fg, bf16=True, grads=None):
+def tc_expected(D, bf16, path):
+    """The tensor-core NDFD kernels take BF16 features with D in {256, 512}
+    unless the FP32 path is asked for."""
+    return bf16 and D in (256, 512) and path != api.PATH_FP32
+
+
+def run_ndfd(sc, cams, prm, fg, bf16=True, grads=None, path=api.PATH_AUTO):
     dt = torch.bfloat16 if bf16 else torch.float32
-    rast = api.Rasterizer(0, sh_degree=prm.get("sh_degree", 0))
+    rast = api.Rasterizer(0, sh_degree=prm.get("sh_degree", 0), path=path)
     t = {k: _t(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
     feats = _t(sc["features"], dt)
     gt = _t(np.concatenate([x.reshape(-1, x.shape[-1]) for x in fg]), dt)
@@ -56,7 +62,8 @@ def run_ndfd(sc, cams, prm, fg, bf16=True, grads=None):
     torch.cuda.synchronize()
     assert rast.ctx.sync_status() == api.OK
     prof = rast.ctx.profile_read()
-    assert "ndfd_fwd" in prof, prof
+    tc = tc_expected(int(sc["features"].shape[1]), bf16, path)
+    assert ("ndfd_fwd_tc" if tc else "ndfd_fwd") in prof, prof
     if grads is not None:
         assert "ndfd_bwd" in prof, prof
     return out
@@ -83,14 +90,34 @@ def check_losses(out, sc, cams, prm, fg, prep):
     return worst
 
 
-@pytest.mark.parametrize("D,bf16", [(64, True), (256, True), (512, True), (128, False), (32, False)])
-def test_ndfd_forward_small(D, bf16):
+@pytest.mark.parametrize("D,bf16,path", [(64, True, api.PATH_AUTO), (256, True, api.PATH_AUTO),
+                                         (512, True, api.PATH_AUTO), (256, True, api.PATH_FP32),
+                                         (512, True, api.PATH_FP32), (128, False, api.PATH_AUTO),
+                                         (32, False, api.PATH_AUTO)])
+def test_ndfd_forward_small(D, bf16, path):
     cams = [synth.look_at_camera(synth.ring_position(3.0, 20, 10), 64, 48)]
     sc, fg = ndfd_case(1500, 61 + D, D, cams, bf16=bf16)
     prm = dict(sh_degree=1)
     prep = oracle.prepare(sc, cams, prm)
-    out = run_ndfd(sc, cams, prm, fg, bf16=bf16)
-    check_losses(out, sc, cams, prm, fg, prep)
+    out = run_ndfd(sc, cams, prm, fg, bf16=bf16, path=path)
+    worst = check_losses(out, sc, cams, prm, fg, prep)
+    print(f"NDFD D={D} path={path}: worst loss error {worst:.3g}")
+
+
+@pytest.mark.parametrize("D", [256, 512])
+def test_ndfd_forward_tensor_core_ragged_multicamera_long_lists(D):
+    """The tensor-core kernel over ragged cameras (partial tiles, both
+    halves), lists of several 64-entry chunks, and a dense scene whose pixels
+    stop early (the walk ends before the list does)."""
+    cams = [synth.look_at_camera(synth.ring_position(2.4, a, e), w, h)
+            for a, e, w, h in [(10, 5, 70, 50), (140, 25, 33, 47), (260, -20, 96, 64)]]
+    sc, fg = ndfd_case(9000, 64 + D, D, cams, sh_degree=1, spread=0.45)
+    prm = dict(sh_degree=1)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_ndfd(sc, cams, prm, fg, path=api.PATH_TC)
+    worst = check_losses(out, sc, cams, prm, fg, prep)
+    assert out["nc"].max() > 64   # some pixel's contributors span more than one chunk
+    print(f"tensor-core NDFD D={D}: worst loss error {worst:.3g}, max contributors {out['nc'].max()}")
 
 
 def test_ndfd_forward_multicamera_ragged():
