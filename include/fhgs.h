@@ -98,10 +98,11 @@ typedef struct fhgs_params {
  * scales[i][2] is ignored and gets a zero gradient) with density
  * exp(-(u^2 + v^2)/2) at the point u(x) where the pixel's ray meets the
  * plane; binning follows the binary32 rule of the surfel footprint's
- * dual-conic box.  The surfel model runs fhgs_project, fhgs_bin_sort and
- * the FP32 CUDA-core render (forward and backward; FHGS_PATH_TC is
- * FHGS_ERR_UNSUPPORTED, FHGS_PATH_AUTO takes the FP32 kernels); fusion,
- * NDFD and the allocation-free backward return FHGS_ERR_UNSUPPORTED. */
+ * dual-conic box.  The surfel model runs fhgs_project, fhgs_bin_sort, the
+ * FP32 CUDA-core render (forward and backward; FHGS_PATH_TC is
+ * FHGS_ERR_UNSUPPORTED, FHGS_PATH_AUTO takes the FP32 kernels) and the NDFD
+ * losses with their backward over surfel weights (CUDA cores); fusion and
+ * the allocation-free backward return FHGS_ERR_UNSUPPORTED. */
 enum { FHGS_GEOM_EWA = 0, FHGS_GEOM_SURFEL = 1 };
 
 enum {
@@ -339,7 +340,10 @@ fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void 
  * D / 128 CTAs per half tile; otherwise (or with FHGS_PATH_FP32) they run in
  * FP32 on the CUDA cores.  p->path TC with any other dtype or D returns
  * FHGS_ERR_UNSUPPORTED.  A wait of the tensor-core kernel that runs out
- * latches FHGS_ERR_TIMEOUT (read by fhgs_sync_status). */
+ * latches FHGS_ERR_TIMEOUT (read by fhgs_sync_status).  With
+ * p->geometry = FHGS_GEOM_SURFEL the weights are the 2DGS surfel render's
+ * (the ray-plane solve of Sec. 3.1, the paper's own combination) and the
+ * products run on the CUDA cores (FHGS_PATH_TC is FHGS_ERR_UNSUPPORTED). */
 fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_bins *bins, const void *features,
                           const void *feat_gt, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
                           const fhgs_params *p, float k, float lambda, float *L_gt, float *L_cf, int32_t *n_contrib,
@@ -357,7 +361,10 @@ fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs
  * fhgs_render_bwd's: grad_means [n][3], grad_scales [n][3], grad_quats [n][4]
  * (16-byte aligned), grad_opac [n], grad_sh [n][K][3] (all zero: colour
  * does not enter the losses).  To train on L_rgb + l1 L_gt + l2 L_cf, scale
- * grad_Lgt and grad_Lcf and add these gradients to fhgs_render_bwd's. */
+ * grad_Lgt and grad_Lcf and add these gradients to fhgs_render_bwd's.  For
+ * surfels (FHGS_GEOM_SURFEL) the footprint chain is the surfel render
+ * backward's (implicit differentiation of the ray-plane solve) and
+ * grad_scales[i][2] is zero. */
 fhgs_status fhgs_ndfd_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *proj, const fhgs_bins *bins,
                           const void *features, const void *feat_gt, fhgs_dtype ftype, int D,
                           const fhgs_camera *cams, int n_cams, const fhgs_params *p, float k, float lambda,

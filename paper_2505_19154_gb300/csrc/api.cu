@@ -676,7 +676,7 @@ fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void 
 // The NDFD losses run on the tensor cores unless the FP32 path is asked for
 // or the features are not BF16 with D in {256, 512}.
 static bool ndfd_use_tc(const fhgs_params *p, fhgs_dtype ftype, int D) {
-    return p->path != FHGS_PATH_FP32 && ftype == FHGS_BF16 && ndfd_tc_supported(D);
+    return p->path != FHGS_PATH_FP32 && p->geometry == FHGS_GEOM_EWA && ftype == FHGS_BF16 && ndfd_tc_supported(D);
 }
 
 static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, const fhgs_bins *bins,
@@ -686,7 +686,6 @@ static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, cons
     if (s == FHGS_OK) s = check_bins(ctx, bins);
     if (s == FHGS_OK) s = check_features(ctx, features, ftype, D, n);
     if (s != FHGS_OK) return s;
-    if (p->geometry != FHGS_GEOM_EWA) return fail(ctx, FHGS_ERR_UNSUPPORTED, "NDFD runs on the EWA geometry");
     if (!ndfd_supported(D)) return fail(ctx, FHGS_ERR_UNSUPPORTED, "NDFD needs D in {32, 64, 128, 256, 512}");
     if (!proj) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL input buffer");
     if (!feat_gt) return fail(ctx, FHGS_ERR_INVALID_ARG, "feat_gt is NULL");
@@ -694,7 +693,8 @@ static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, cons
     if (!std::isfinite(k) || !std::isfinite(lambda))
         return fail(ctx, FHGS_ERR_INVALID_ARG, "the activation's slope and threshold must be finite");
     if (p->path == FHGS_PATH_TC && !ndfd_use_tc(p, ftype, D))
-        return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core NDFD needs BF16 features with D in {256, 512}");
+        return fail(ctx, FHGS_ERR_UNSUPPORTED,
+                    "tensor-core NDFD needs the EWA geometry and BF16 features with D in {256, 512}");
     return FHGS_OK;
 }
 
@@ -718,7 +718,7 @@ fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs
         launch_ndfd_fwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, (const __nv_bfloat16 *)feat_gt, D, k,
                            lambda, L_gt, L_cf, n_contrib, ctx->status, st);
     } else {
-        Prof pr(ctx, "ndfd_fwd", st);
+        Prof pr(ctx, p->geometry == FHGS_GEOM_SURFEL ? "ndfd_fwd_surfel" : "ndfd_fwd", st);
         launch_ndfd_fwd(n, cs, q, pv, *bins, features, feat_gt, ftype == FHGS_BF16, D, k, lambda, L_gt, L_cf, n_contrib, st);
     }
     FHGS_CUDA(ctx, cudaGetLastError());
@@ -742,20 +742,25 @@ fhgs_status fhgs_ndfd_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *pr
     if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
     FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
     const long long n = g->n, cn = n * n_cams;
-    if ((s = ensure(ctx, ctx->g2d, sizeof(float) * 12 * (size_t)cn + 256)) != FHGS_OK) return s;
+    const bool surfel = p->geometry == FHGS_GEOM_SURFEL;
+    const size_t per = surfel ? kSurfelG2d : 12;  // footprint-gradient floats per (camera, primitive)
+    if ((s = ensure(ctx, ctx->g2d, sizeof(float) * per * (size_t)cn + 256)) != FHGS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     float *g2d = (float *)ctx->g2d.p;
-    FHGS_CUDA(ctx, cudaMemsetAsync(g2d, 0, sizeof(float) * 12 * (size_t)cn, st));
+    FHGS_CUDA(ctx, cudaMemsetAsync(g2d, 0, sizeof(float) * per * (size_t)cn, st));
     const Params q = make_params(p);
     ProjView pv = proj_view(const_cast<void *>(proj), cn);
     {
-        Prof pr(ctx, "ndfd_bwd", st);
+        Prof pr(ctx, surfel ? "ndfd_bwd_surfel" : "ndfd_bwd", st);
         launch_ndfd_bwd(n, cs, q, pv, *bins, features, feat_gt, ftype == FHGS_BF16, D, k, lambda, grad_Lgt,
                         grad_Lcf, g2d, st);
     }
     {
         Prof pb(ctx, "project_bwd", st);
-        launch_project_bwd(*g, cs, q, pv, g2d, grad_means, grad_scales, grad_quats, grad_opac, grad_sh, st);
+        if (surfel)
+            launch_project_surfel_bwd(*g, cs, q, pv, g2d, grad_means, grad_scales, grad_quats, grad_opac, grad_sh, st);
+        else
+            launch_project_bwd(*g, cs, q, pv, g2d, grad_means, grad_scales, grad_quats, grad_opac, grad_sh, st);
     }
     FHGS_CUDA(ctx, cudaGetLastError());
     return FHGS_OK;

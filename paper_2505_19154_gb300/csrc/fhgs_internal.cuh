@@ -143,6 +143,31 @@ __device__ __forceinline__ float eval_q2(float dx, float dy, float A, float B, f
     return __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(C, dy), dy));
 }
 
+// u(x), v(x) of a 2DGS surfel at a pixel centre from its record's a, b and
+// M22 (explicit roundings, so that the surfel render, its backward and the
+// NDFD kernels take the same decisions): (dx, dy) = pixel centre - x_c,
+// w = M20 dx + M21 dy + M22, u = (M00 dx + M01 dy) / w, v = (M10 dx + M11 dy)
+// / w.  False when the pixel's ray meets the plane behind the camera (w <= 0)
+// or outside the cutoff u^2 + v^2 <= cutoff_sq.
+struct SurfelHit {
+    float dx, dy, iw, u, v, r2;
+};
+
+__device__ __forceinline__ bool surfel_uv(const float4 &A, const float4 &B, float M22, float fpx, float fpy, float cut,
+                                          SurfelHit &h) {
+    h.dx = __fsub_rn(fpx, A.x);
+    h.dy = __fsub_rn(fpy, A.y);
+    const float w = __fmaf_rn(B.z, h.dx, __fmaf_rn(B.w, h.dy, M22));
+    if (!(w > 0.f)) return false;
+    const float nu = __fmaf_rn(A.z, h.dx, __fmul_rn(A.w, h.dy));
+    const float nv = __fmaf_rn(B.x, h.dx, __fmul_rn(B.y, h.dy));
+    h.iw = __frcp_rn(w);
+    h.u = __fmul_rn(nu, h.iw);
+    h.v = __fmul_rn(nv, h.iw);
+    h.r2 = __fmaf_rn(h.u, h.u, __fmul_rn(h.v, h.v));
+    return h.r2 <= cut;
+}
+
 __device__ __forceinline__ void latch(unsigned *status, unsigned bit) {
     if (status) atomicOr(status, bit);
 }

@@ -181,21 +181,29 @@ __device__ __forceinline__ RowCtx row_ctx(const CamSet &cs, const uint32_t *rang
     return r;
 }
 
-// Stages Gaussians [base, base + nb) of the list: records, ids, feature rows
+// Stages Gaussians [base, base + nb) of the list: records (a, b of the EWA
+// record; a, b, c of the surfel record), ids, feature rows
 // as FP32 (row-major, D floats per row) and the inverse feature norms (0 for
 // a zero row).  Ends with a block barrier.
-template <int DPL, int BF16, int NT = kThreads>
-__device__ __forceinline__ void stage_chunk(const GRec *rec, const uint32_t *gids, uint32_t base, int nb,
-                                            const void *feats, float *sf, float4 *sa, float4 *sb, uint32_t *sg,
-                                            float *sinv, int warp, int lane) {
+template <int DPL, int BF16, int GEOM, int NT = kThreads>
+__device__ __forceinline__ void stage_chunk(const void *rec, const uint32_t *gids, uint32_t base, int nb,
+                                            const void *feats, float *sf, float4 *sa, float4 *sb, float4 *sc,
+                                            uint32_t *sg, float *sinv, int warp, int lane) {
     constexpr int D = 32 * DPL;
     constexpr int kRowQ = D * (BF16 ? 2 : 4) / 16;  // 16-byte words per source row
     const int tid = threadIdx.x;
     if (tid < nb) {
         const uint32_t g = gids[base + tid];
-        const GRec r = rec[g];
-        sa[tid] = r.a;
-        sb[tid] = r.b;
+        if constexpr (GEOM == FHGS_GEOM_EWA) {
+            const GRec r = static_cast<const GRec *>(rec)[g];
+            sa[tid] = r.a;
+            sb[tid] = r.b;
+        } else {
+            const SRec r = static_cast<const SRec *>(rec)[g];
+            sa[tid] = r.a;
+            sb[tid] = r.b;
+            sc[tid] = r.c;
+        }
         sg[tid] = g;
     }
     for (int c = tid; c < nb * kRowQ; c += NT) {
@@ -224,15 +232,25 @@ __device__ __forceinline__ void stage_chunk(const GRec *rec, const uint32_t *gid
     __syncthreads();
 }
 
-// alpha of one Gaussian at a pixel, exactly as the render takes it:
-// q2 <= cutoff, alpha = min(alpha_max, op G) >= alpha_min.
-__device__ __forceinline__ bool ndfd_alpha(const Params &p, float4 A, float4 B, float fpx, float fpy, float &a,
-                                           float &G, float &rho) {
-    const float dx = fpx - A.x, dy = fpy - A.y;
-    const float q2 = eval_q2(dx, dy, A.z, A.w, B.x);
-    if (q2 > p.cut) return false;
-    G = __expf(-0.5f * q2);
-    rho = B.y * G;
+// alpha of one primitive at a pixel, exactly as the render takes it: EWA,
+// q2 <= cutoff on the conic; a 2DGS surfel, u^2 + v^2 <= cutoff at the
+// ray-plane intersection (Sec. 3.1, Eq. 1-3); then G = exp(-r^2 / 2) and
+// alpha = min(alpha_max, op G) >= alpha_min.
+template <int GEOM>
+__device__ __forceinline__ bool ndfd_alpha(const Params &p, float4 A, float4 B, float4 C, float fpx, float fpy,
+                                           float &a, float &G, float &rho) {
+    if constexpr (GEOM == FHGS_GEOM_EWA) {
+        const float dx = fpx - A.x, dy = fpy - A.y;
+        const float q2 = eval_q2(dx, dy, A.z, A.w, B.x);
+        if (q2 > p.cut) return false;
+        G = __expf(-0.5f * q2);
+        rho = B.y * G;
+    } else {
+        SurfelHit h;
+        if (!surfel_uv(A, B, C.x, fpx, fpy, p.cut, h)) return false;
+        G = __expf(-0.5f * h.r2);
+        rho = C.y * G;
+    }
     a = fminf(p.amax, rho);
     return a >= p.amin;
 }
@@ -267,7 +285,7 @@ __device__ __forceinline__ unsigned chunk_weights(bool contrib, float a, float t
     return m;
 }
 
-template <int DPL, int BF16>
+template <int DPL, int BF16, int GEOM>
 __global__ void __launch_bounds__(kThreads, 2) k_ndfd_fwd(long long N, CamSet cs, Params p, ProjView pv,
                                                         const uint32_t *__restrict__ gids,
                                                         const uint32_t *__restrict__ ranges, const void *feats,
@@ -276,12 +294,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_ndfd_fwd(long long N, CamSet cs
     constexpr int D = 32 * DPL;
     constexpr int kGtRowBytes = D * (BF16 ? 2 : 4);
     extern __shared__ __align__(16) float sf[];
-    __shared__ float4 sa[kNC], sb[kNC];
+    __shared__ float4 sa[kNC], sb[kNC], sc[kNC];
     __shared__ uint32_t sg[kNC];
     __shared__ float sinv[kNC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const RowCtx rc = row_ctx(cs, ranges, warp);
-    const GRec *rec = pv.rec + (long long)rc.ci * N;
+    const void *rec = GEOM == FHGS_GEOM_EWA ? static_cast<const void *>(pv.rec + (long long)rc.ci * N)
+                                            : static_cast<const void *>(pv.srec + (long long)rc.ci * N);
 
     float F0[DPL], F1[DPL], g0[DPL], g1[DPL], igt[2], T[2] = {1.f, 1.f};
     int nc[2] = {0, 0};
@@ -302,15 +321,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_ndfd_fwd(long long N, CamSet cs
     for (uint32_t base = rc.s; base < rc.e; base += kNC) {
         if (__syncthreads_and(done[0] && done[1])) break;
         const int nb = (int)min((uint32_t)kNC, rc.e - base);
-        stage_chunk<DPL, BF16>(rec, gids, base, nb, feats, sf, sa, sb, sg, sinv, warp, lane);
+        stage_chunk<DPL, BF16, GEOM>(rec, gids, base, nb, feats, sf, sa, sb, sc, sg, sinv, warp, lane);
         float a[2] = {0.f, 0.f};
         bool c[2] = {false, false};
         if (lane < nb) {
-            const float4 A = sa[lane], B = sb[lane];
+            const float4 A = sa[lane], B = sb[lane], Cc = sc[lane];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 float G, rho;
-                c[q] = !done[q] && ndfd_alpha(p, A, B, rc.fpx[q], rc.fpy, a[q], G, rho);
+                c[q] = !done[q] && ndfd_alpha<GEOM>(p, A, B, Cc, rc.fpx[q], rc.fpy, a[q], G, rho);
             }
         }
         float wl[2], Tl[2];
@@ -408,23 +427,55 @@ struct EntryScalars {
     float a, T, G, rho;
 };
 
-// dL/dalpha of one contributor -> its footprint gradient at the pixel
-// (mean x, y; conic A, B, C; opacity), through alpha = min(alpha_max, op G),
-// G = exp(-q2/2); the clamp passes no gradient.
-__device__ __forceinline__ void footprint_geo(float (&geo)[6], float4 A, float4 B, float fpx, float fpy,
-                                              const EntryScalars &e, float amax, float dal) {
+// Footprint gradients per (camera, primitive): EWA, d(mean x, y; conic A,
+// B, C; opacity) (6 of 12 floats, the render backward's layout); surfel,
+// d(x_c, y_c, M00, M01, M10, M11, M20, M21, M22, opacity) (10 of 16).
+template <int GEOM>
+struct GeoG {
+    static constexpr int kN = GEOM == FHGS_GEOM_EWA ? 6 : 10;     // components
+    static constexpr int kPad = GEOM == FHGS_GEOM_EWA ? 8 : 12;   // shared-memory row
+    static constexpr int kG2d = GEOM == FHGS_GEOM_EWA ? 12 : kSurfelG2d;
+};
+
+// dL/dalpha of one contributor -> its footprint gradient at the pixel,
+// through alpha = min(alpha_max, op G), G = exp(-r^2/2) (the clamp passes no
+// gradient): EWA r^2 = q2 of the conic at (dx, dy); surfel r^2 = u^2 + v^2
+// with u = (M00 dx + M01 dy) / w, v = (M10 dx + M11 dy) / w, w = M20 dx +
+// M21 dy + M22 (the ray-plane solve recomputed at the pixel).
+template <int GEOM>
+__device__ __forceinline__ void footprint_geo(float (&geo)[GeoG<GEOM>::kN], float4 A, float4 B, float4 C, float fpx,
+                                              float fpy, const EntryScalars &e, float amax, float dal) {
     const float drho = e.rho > amax ? 0.f : dal;
-    const float dq2 = -0.5f * e.rho * drho;
-    const float dx = fpx - A.x, dy = fpy - A.y;
-    geo[0] = -(2.f * A.z * dx + 2.f * A.w * dy) * dq2;
-    geo[1] = -(2.f * A.w * dx + 2.f * B.x * dy) * dq2;
-    geo[2] = dx * dx * dq2;
-    geo[3] = 2.f * dx * dy * dq2;
-    geo[4] = dy * dy * dq2;
-    geo[5] = e.G * drho;
+    if constexpr (GEOM == FHGS_GEOM_EWA) {
+        const float dq2 = -0.5f * e.rho * drho;
+        const float dx = fpx - A.x, dy = fpy - A.y;
+        geo[0] = -(2.f * A.z * dx + 2.f * A.w * dy) * dq2;
+        geo[1] = -(2.f * A.w * dx + 2.f * B.x * dy) * dq2;
+        geo[2] = dx * dx * dq2;
+        geo[3] = 2.f * dx * dy * dq2;
+        geo[4] = dy * dy * dq2;
+        geo[5] = e.G * drho;
+    } else {
+        SurfelHit h;
+        surfel_uv(A, B, C.x, fpx, fpy, 3.4e38f, h);  // a contributor: the ray meets the plane in front
+        const float dr2 = -0.5f * e.rho * drho;
+        const float du = 2.f * h.u * dr2, dv = 2.f * h.v * dr2;
+        const float dnu = du * h.iw, dnv = dv * h.iw;
+        const float dw = -(du * h.u + dv * h.v) * h.iw;
+        geo[0] = -(dnu * A.z + dnv * B.x + dw * B.z);
+        geo[1] = -(dnu * A.w + dnv * B.y + dw * B.w);
+        geo[2] = dnu * h.dx;
+        geo[3] = dnu * h.dy;
+        geo[4] = dnv * h.dx;
+        geo[5] = dnv * h.dy;
+        geo[6] = dw * h.dx;
+        geo[7] = dw * h.dy;
+        geo[8] = dw;
+        geo[9] = e.G * drho;
+    }
 }
 
-template <int DPL, int BF16>
+template <int DPL, int BF16, int GEOM>
 __global__ void __launch_bounds__(kThreadsB, 1) k_ndfd_bwd(long long N, CamSet cs, Params p, ProjView pv,
                                                          const uint32_t *__restrict__ gids,
                                                          const uint32_t *__restrict__ ranges, const void *feats,
@@ -434,10 +485,11 @@ __global__ void __launch_bounds__(kThreadsB, 1) k_ndfd_bwd(long long N, CamSet c
     constexpr int D = 32 * DPL;
     constexpr int kGtRowBytes = D * (BF16 ? 2 : 4);
     extern __shared__ __align__(16) float sf[];
-    __shared__ float4 sa[kNC], sb[kNC];
+    using GG = GeoG<GEOM>;
+    __shared__ float4 sa[kNC], sb[kNC], sc[kNC];
     __shared__ uint32_t sg[kNC];
     __shared__ float sinv[kNC];
-    __shared__ __align__(16) float sacc[kNC][8];
+    __shared__ __align__(16) float sacc[kNC][GG::kPad];
     __shared__ __align__(16) EntryScalars sent[kWarpsB][kNC];
     __shared__ int smax;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -451,8 +503,9 @@ __global__ void __launch_bounds__(kThreadsB, 1) k_ndfd_bwd(long long N, CamSet c
     const long long pix = cam.pix_off + (long long)py * cam.W + px;
     const float fpx = px + 0.5f, fpy = py + 0.5f;
     const uint32_t ls = ranges[2 * tile], le = ranges[2 * tile + 1];
-    const GRec *rec = pv.rec + (long long)ci * N;
-    float *g2dc = g2d + (long long)ci * N * 12;
+    const void *rec = GEOM == FHGS_GEOM_EWA ? static_cast<const void *>(pv.rec + (long long)ci * N)
+                                            : static_cast<const void *>(pv.srec + (long long)ci * N);
+    float *g2dc = g2d + (long long)ci * N * GG::kG2d;
 
     float F[DPL], T = 1.f;
     int last = 0;
@@ -460,18 +513,18 @@ __global__ void __launch_bounds__(kThreadsB, 1) k_ndfd_bwd(long long N, CamSet c
 #pragma unroll
     for (int i = 0; i < DPL; ++i) F[i] = 0.f;
     if (threadIdx.x == 0) smax = 0;
-    for (int i = threadIdx.x; i < kNC * 8; i += kThreadsB) (&sacc[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < kNC * GG::kPad; i += kThreadsB) (&sacc[0][0])[i] = 0.f;
 
     // front to back: F_N, T_N and the last contributor
     for (uint32_t base = ls; base < le; base += kNC) {
         if (__syncthreads_and(done)) break;
         const int nb = (int)min((uint32_t)kNC, le - base);
-        stage_chunk<DPL, BF16, kThreadsB>(rec, gids, base, nb, feats, sf, sa, sb, sg, sinv, warp, lane);
+        stage_chunk<DPL, BF16, GEOM, kThreadsB>(rec, gids, base, nb, feats, sf, sa, sb, sc, sg, sinv, warp, lane);
         float a = 0.f;
         bool c = false;
         if (lane < nb) {
             float G, rho;
-            c = !done && ndfd_alpha(p, sa[lane], sb[lane], fpx, fpy, a, G, rho);
+            c = !done && ndfd_alpha<GEOM>(p, sa[lane], sb[lane], sc[lane], fpx, fpy, a, G, rho);
         }
         float wl, Tl;
         const unsigned m = chunk_weights(c, a, p.teps, lane, T, done, wl, Tl);
@@ -508,12 +561,14 @@ __global__ void __launch_bounds__(kThreadsB, 1) k_ndfd_bwd(long long N, CamSet c
     for (int bend = Lmax; bend > 0; bend -= kNC) {
         const int bstart = max(0, bend - kNC), nb = bend - bstart;
         __syncthreads();
-        stage_chunk<DPL, BF16, kThreadsB>(rec, gids, ls + bstart, nb, feats, sf, sa, sb, sg, sinv, warp, lane);
+        stage_chunk<DPL, BF16, GEOM, kThreadsB>(rec, gids, ls + bstart, nb, feats, sf, sa, sb, sc, sg, sinv, warp,
+                                                lane);
         // alpha of entry `lane`, then T before it: T after the chunk divided
         // by the suffix product of (1 - alpha) from the entry on
         float a = 0.f, Gv = 0.f, rho = 0.f;
         bool c = false;
-        if (lane < nb) c = bstart + lane < last && ndfd_alpha(p, sa[lane], sb[lane], fpx, fpy, a, Gv, rho);
+        if (lane < nb)
+            c = bstart + lane < last && ndfd_alpha<GEOM>(p, sa[lane], sb[lane], sc[lane], fpx, fpy, a, Gv, rho);
         float suf = c ? 1.f - a : 1.f;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -559,74 +614,80 @@ __global__ void __launch_bounds__(kThreadsB, 1) k_ndfd_bwd(long long N, CamSet c
             const float A0 = __shfl_sync(kFull, tot, 8), phi1 = __shfl_sync(kFull, tot, 12);
             const float X1 = __shfl_sync(kFull, tot, 16), A1 = __shfl_sync(kFull, tot, 20);
             const float gram = __shfl_sync(kFull, tot, 24);
-            float geo0[6], geo1[6];
+            float geo0[GG::kN], geo1[GG::kN];
             const float sig0 = ndfd_sigma(phi0 * sinv[j0] * igt, ks, lam);
             const float gw0 = cgt * sig0 + ccf * (sig0 * ((1.f - e0.T) - X0) + Ss - A0);
-            footprint_geo(geo0, sa[j0], sb[j0], fpx, fpy, e0, p.amax, e0.T * gw0 - Sw / (1.f - e0.a));
+            footprint_geo<GEOM>(geo0, sa[j0], sb[j0], sc[j0], fpx, fpy, e0, p.amax, e0.T * gw0 - Sw / (1.f - e0.a));
             Sw = fmaf(w0, gw0, Sw);
             const float sw0 = sig0 * w0;
             Ss += sw0;
             float sw1 = 0.f;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) geo1[k] = 0.f;
+            for (int k = 0; k < GG::kN; ++k) geo1[k] = 0.f;
             if (j1 >= 0) {
                 const float sig1 = ndfd_sigma(phi1 * sinv[j1] * igt, ks, lam);
                 // G . f_j1: G at the pair's start plus j0's share
                 const float Y = fmaf(sw0, gram, A1);
                 const float gw1 = cgt * sig1 + ccf * (sig1 * ((1.f - e1.T) - X1) + Ss - Y);
-                footprint_geo(geo1, sa[j1], sb[j1], fpx, fpy, e1, p.amax, e1.T * gw1 - Sw / (1.f - e1.a));
+                footprint_geo<GEOM>(geo1, sa[j1], sb[j1], sc[j1], fpx, fpy, e1, p.amax,
+                                    e1.T * gw1 - Sw / (1.f - e1.a));
                 Sw = fmaf(w1, gw1, Sw);
                 sw1 = sig1 * w1;
                 Ss += sw1;
             }
             axpy_slice<DPL>(sw0, f, Gs);
             axpy_slice<DPL>(sw1, f1, Gs);
-            // lanes 0..5 add j0's components, lanes 8..13 j1's
-            const int k = lane & 7;
+            // lanes 0..kN-1 add j0's components, lanes 16..16+kN-1 j1's
+            const int k = lane & 15;
             float val = 0.f;
 #pragma unroll
-            for (int kk = 0; kk < 6; ++kk)
-                if (kk == k) val = lane < 8 ? geo0[kk] : geo1[kk];
-            const int j = lane < 8 ? j0 : j1;
-            if (lane < 16 && k < 6 && j >= 0 && inside && val != 0.f) atomicAdd(&sacc[j][k], val);
+            for (int kk = 0; kk < GG::kN; ++kk)
+                if (kk == k) val = lane < 16 ? geo0[kk] : geo1[kk];
+            const int j = lane < 16 ? j0 : j1;
+            if (k < GG::kN && j >= 0 && inside && val != 0.f) atomicAdd(&sacc[j][k], val);
         }
         __syncthreads();
         if ((int)threadIdx.x < nb) {
             const int j = threadIdx.x;
-            const float4 u = *reinterpret_cast<const float4 *>(&sacc[j][0]);
-            const float2 t = *reinterpret_cast<const float2 *>(&sacc[j][4]);
-            if (u.x != 0.f || u.y != 0.f || u.z != 0.f || u.w != 0.f || t.x != 0.f || t.y != 0.f) {
-                float *dst = g2dc + 12 * (long long)sg[j];
-                atomicAdd(reinterpret_cast<float4 *>(dst), u);
-                atomicAdd(reinterpret_cast<float2 *>(dst + 4), t);
+            float *dst = g2dc + GG::kG2d * (long long)sg[j];
+#pragma unroll
+            for (int k = 0; k < GG::kN; k += 4) {
+                if (k + 4 <= GG::kN) {
+                    const float4 u = *reinterpret_cast<const float4 *>(&sacc[j][k]);
+                    if (u.x != 0.f || u.y != 0.f || u.z != 0.f || u.w != 0.f)
+                        atomicAdd(reinterpret_cast<float4 *>(dst + k), u);
+                    *reinterpret_cast<float4 *>(&sacc[j][k]) = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    const float2 t = *reinterpret_cast<const float2 *>(&sacc[j][k]);
+                    if (t.x != 0.f || t.y != 0.f) atomicAdd(reinterpret_cast<float2 *>(dst + k), t);
+                    *reinterpret_cast<float2 *>(&sacc[j][k]) = make_float2(0.f, 0.f);
+                }
             }
-            *reinterpret_cast<float4 *>(&sacc[j][0]) = make_float4(0.f, 0.f, 0.f, 0.f);
-            *reinterpret_cast<float2 *>(&sacc[j][4]) = make_float2(0.f, 0.f);
         }
     }
 }
 
-template <int DPL, int BF16>
+template <int DPL, int BF16, int GEOM>
 void launch_fwd_t(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                   const void *feats, const void *fgt, float ks, float lam, float *Lgt, float *Lcf, int32_t *nc,
                   cudaStream_t st) {
     static std::atomic<unsigned long long> smem_set{0};
     const int smem = kNC * 32 * DPL * 4;
-    allow_max_smem(smem_set, k_ndfd_fwd<DPL, BF16>);
+    allow_max_smem(smem_set, k_ndfd_fwd<DPL, BF16, GEOM>);
     note_launch(1);
-    k_ndfd_fwd<DPL, BF16><<<(unsigned)cs.total_tiles * 16, kThreads, smem, st>>>(
+    k_ndfd_fwd<DPL, BF16, GEOM><<<(unsigned)cs.total_tiles * 16, kThreads, smem, st>>>(
         N, cs, p, pv, bins.gids, bins.ranges, feats, fgt, ks, lam, Lgt, Lcf, nc);
 }
 
-template <int DPL, int BF16>
+template <int DPL, int BF16, int GEOM>
 void launch_bwd_t(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                   const void *feats, const void *fgt, float ks, float lam, const float *dLgt, const float *dLcf,
                   float *g2d, cudaStream_t st) {
     static std::atomic<unsigned long long> smem_set{0};
     const int smem = kNC * 32 * DPL * 4;
-    allow_max_smem(smem_set, k_ndfd_bwd<DPL, BF16>);
+    allow_max_smem(smem_set, k_ndfd_bwd<DPL, BF16, GEOM>);
     note_launch(1);
-    k_ndfd_bwd<DPL, BF16><<<(unsigned)cs.total_tiles * 16, kThreadsB, smem, st>>>(
+    k_ndfd_bwd<DPL, BF16, GEOM><<<(unsigned)cs.total_tiles * 16, kThreadsB, smem, st>>>(
         N, cs, p, pv, bins.gids, bins.ranges, feats, fgt, ks, lam, dLgt, dLcf, g2d);
 }
 
@@ -634,20 +695,22 @@ void launch_bwd_t(long long N, const CamSet &cs, const Params &p, ProjView pv, c
 
 bool ndfd_supported(int D) { return D == 32 || D == 64 || D == 128 || D == 256 || D == 512; }
 
-#define FHGS_NDFD_CASES(X, BF) \
-    X(1, BF) X(2, BF) X(4, BF) X(8, BF) X(16, BF)
+#define FHGS_NDFD_CASES(X, BF, G) \
+    X(1, BF, G) X(2, BF, G) X(4, BF, G) X(8, BF, G) X(16, BF, G)
 
 void launch_ndfd_fwd(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                      const void *feats, const void *fgt, int bf16, int D, float ks, float lam, float *Lgt,
                      float *Lcf, int32_t *nc, cudaStream_t st) {
     if (cs.total_tiles == 0) return;
-#define X(DPL, BF)                                                                            \
-    if (D == 32 * DPL && bf16 == BF) {                                                        \
-        launch_fwd_t<DPL, BF>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, st);     \
-        return;                                                                               \
+#define X(DPL, BF, G)                                                                          \
+    if (D == 32 * DPL && bf16 == BF && p.geom == G) {                                          \
+        launch_fwd_t<DPL, BF, G>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, st);   \
+        return;                                                                                \
     }
-    FHGS_NDFD_CASES(X, 0)
-    FHGS_NDFD_CASES(X, 1)
+    FHGS_NDFD_CASES(X, 0, FHGS_GEOM_EWA)
+    FHGS_NDFD_CASES(X, 1, FHGS_GEOM_EWA)
+    FHGS_NDFD_CASES(X, 0, FHGS_GEOM_SURFEL)
+    FHGS_NDFD_CASES(X, 1, FHGS_GEOM_SURFEL)
 #undef X
 }
 
@@ -655,13 +718,15 @@ void launch_ndfd_bwd(long long N, const CamSet &cs, const Params &p, ProjView pv
                      const void *feats, const void *fgt, int bf16, int D, float ks, float lam, const float *dLgt,
                      const float *dLcf, float *g2d, cudaStream_t st) {
     if (cs.total_tiles == 0) return;
-#define X(DPL, BF)                                                                                  \
-    if (D == 32 * DPL && bf16 == BF) {                                                              \
-        launch_bwd_t<DPL, BF>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, st);        \
-        return;                                                                                     \
+#define X(DPL, BF, G)                                                                                \
+    if (D == 32 * DPL && bf16 == BF && p.geom == G) {                                                \
+        launch_bwd_t<DPL, BF, G>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, st);      \
+        return;                                                                                      \
     }
-    FHGS_NDFD_CASES(X, 0)
-    FHGS_NDFD_CASES(X, 1)
+    FHGS_NDFD_CASES(X, 0, FHGS_GEOM_EWA)
+    FHGS_NDFD_CASES(X, 1, FHGS_GEOM_EWA)
+    FHGS_NDFD_CASES(X, 0, FHGS_GEOM_SURFEL)
+    FHGS_NDFD_CASES(X, 1, FHGS_GEOM_SURFEL)
 #undef X
 }
 

@@ -292,29 +292,6 @@ __global__ void __launch_bounds__(256) k_project_surfel(const float *__restrict_
 }
 
 // ------------------------------------------------------------------ render
-// u(x), v(x) at a pixel centre from the record (explicit roundings, so that
-// the forward and the backward take the same decisions).  False when the
-// pixel's ray meets the plane behind the camera (w <= 0) or outside the
-// cutoff u^2 + v^2 <= cutoff_sq.
-struct SurfelHit {
-    float dx, dy, iw, u, v, r2;
-};
-
-__device__ __forceinline__ bool surfel_uv(const float4 &A, const float4 &B, float M22, float fpx, float fpy, float cut,
-                                          SurfelHit &h) {
-    h.dx = fs(fpx, A.x);
-    h.dy = fs(fpy, A.y);
-    const float w = __fmaf_rn(B.z, h.dx, __fmaf_rn(B.w, h.dy, M22));
-    if (!(w > 0.f)) return false;
-    const float nu = __fmaf_rn(A.z, h.dx, fm(A.w, h.dy));
-    const float nv = __fmaf_rn(B.x, h.dx, fm(B.y, h.dy));
-    h.iw = __frcp_rn(w);
-    h.u = fm(nu, h.iw);
-    h.v = fm(nv, h.iw);
-    h.r2 = __fmaf_rn(h.u, h.u, fm(h.v, h.v));
-    return h.r2 <= cut;
-}
-
 template <int BF16>
 __device__ __forceinline__ void load8(const void *feats, int D, uint32_t g, int c, float *dst) {
     if (c >= D) {

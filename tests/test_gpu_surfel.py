@@ -166,3 +166,57 @@ def test_surfel_bf16_features_and_unsupported_combinations():
         rast.fuse(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams,
                   [torch.ones((48 * 40, 64), device=rgb.device)])
     assert e.value.status == api.ERR_UNSUPPORTED
+
+
+def _surfel_ndfd_case(n, seed, D, cam, bf16):
+    sc = surfel_scene(n, seed=seed, sh_degree=0, D=0)
+    protos = synth.ndfd_prototypes(seed, D)
+    f = synth.ndfd_features(seed, n, protos)
+    fg = synth.ndfd_ground_truth(seed, 0, cam["height"], cam["width"], protos)
+    if bf16:
+        f, fg = synth.to_bf16(f), synth.to_bf16(fg)
+    return sc, np.asarray(f, np.float64), np.asarray(fg, np.float64).reshape(-1, D)
+
+
+@pytest.mark.parametrize("D,bf16", [(64, False), (256, True), (512, True)])
+def test_surfel_ndfd_losses_and_gradients(D, bf16):
+    """NDFD over surfel weights (Sec. 3.1-3.3; the paper's own combination):
+    L_gt, L_cf and contributor counts against orc_ndfd_2dgs outside the
+    surfel render's margin pixels, the gradients against orc_ndfd_2dgs_bwd
+    within 1e-3 relative L2, SH and the third scale exactly zero."""
+    cam = synth.look_at_camera(synth.ring_position(2.6, 35, 12), 64, 48)
+    sc, f, fg = _surfel_ndfd_case(1200, 70 + D, D, cam, bf16)
+    prm = dict(sh_degree=0)
+    dt = torch.bfloat16 if bf16 else torch.float32
+    rast = api.Rasterizer(0, sh_degree=0, geometry=api.GEOM_SURFEL)
+    t = {k: _t(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    feats, gt = _t(f, dt), _t(fg, dt)
+    rast.ctx.profile(True)
+    st = rast.prepare(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], [cam])
+    nc = torch.empty(gt.shape[0], dtype=torch.int32, device=gt.device)
+    Lgt, Lcf = rast.ndfd_forward(st, feats, gt, ncontrib=nc)
+    P = cam["width"] * cam["height"]
+    a, b = synth.upstream(17, P, 1)[0][:, 0].copy(), synth.upstream(18, P, 1)[0][:, 0].copy()
+    g = rast.ndfd_backward(st, feats, gt, _t(a), _t(b))
+    torch.cuda.synchronize()
+    assert rast.ctx.sync_status() == api.OK
+    prof = rast.ctx.profile_read()
+    assert "ndfd_fwd_surfel" in prof and "ndfd_bwd_surfel" in prof, prof
+    with pytest.raises(api.FhgsError) as e:   # the tensor-core NDFD is EWA-only: refused before any launch
+        rast.set_path(api.PATH_TC)
+        rast.ndfd_forward(st, feats, gt)
+    assert e.value.status == api.ERR_UNSUPPORTED
+    ref = oracle.ndfd_2dgs(sc, cam, prm, f, fg)
+    ok = oracle.surfel_forward(sc, cam, prm)["margin"].reshape(-1) > MARGIN_TOL
+    check_margin_count(int((~ok).sum()), P, "surfel NDFD")
+    for key, got in (("Lgt", Lgt), ("Lcf", Lcf)):
+        err = np.abs(got.cpu().numpy() - ref[key].reshape(-1))[ok].max(initial=0)
+        print(f"surfel NDFD D={D}: {key} err {err:.3g}")
+        assert err <= 5e-5, (key, err)
+    np.testing.assert_array_equal(nc.cpu().numpy()[ok], ref["ncontrib"].reshape(-1)[ok])
+    assert (ref["ncontrib"] > 2).mean() > 0.1 and np.abs(ref["Lcf"]).max() > 1e-2
+    gr = oracle.ndfd_2dgs_bwd(sc, cam, prm, f, fg, a, b)
+    got = {k: v.cpu().numpy() for k, v in g.items()}
+    assert np.all(got["scales"][:, 2] == 0.0) and np.all(got["sh"] == 0.0)
+    got["scales2"] = got["scales"][:, :2]
+    check_grads(got, gr, keys=("means", "scales2", "quats", "opacities"), tol=1e-3)
