@@ -750,7 +750,11 @@ fhgs_status fhgs_ndfd_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *pr
     FHGS_CUDA(ctx, cudaMemsetAsync(g2d, 0, sizeof(float) * per * (size_t)cn, st));
     const Params q = make_params(p);
     ProjView pv = proj_view(const_cast<void *>(proj), cn);
-    {
+    if (ndfd_use_tc(p, ftype, D)) {
+        Prof pr(ctx, "ndfd_bwd_tc", st);
+        launch_ndfd_bwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, (const __nv_bfloat16 *)feat_gt, D, k,
+                           lambda, grad_Lgt, grad_Lcf, g2d, ctx->status, st);
+    } else {
         Prof pr(ctx, surfel ? "ndfd_bwd_surfel" : "ndfd_bwd", st);
         launch_ndfd_bwd(n, cs, q, pv, *bins, features, feat_gt, ftype == FHGS_BF16, D, k, lambda, grad_Lgt,
                         grad_Lcf, g2d, st);

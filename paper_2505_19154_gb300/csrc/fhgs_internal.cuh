@@ -293,5 +293,9 @@ bool ndfd_tc_supported(int D);
 void launch_ndfd_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                         const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam, float *Lgt,
                         float *Lcf, int32_t *nc, unsigned *status, cudaStream_t st);
+// g2d: 12 floats per (camera, Gaussian), accumulated (zero it first)
+void launch_ndfd_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                        const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam,
+                        const float *dLgt, const float *dLcf, float *g2d, unsigned *status, cudaStream_t st);
 
 }  // namespace fhgs

@@ -56,6 +56,8 @@ constexpr int kStashRow = 68;  // floats per own pixel in the weight stash (64 +
 
 template <int NC>
 struct NCfg {
+    static constexpr int kNC = NC;
+    static constexpr int kFStages = 2;       // feature stages (chunk b + 1 loads under chunk b)
     static constexpr int kOwn = 128 / NC;    // pixels whose losses this CTA completes
     static constexpr int kTpp = 256 / kOwn;  // threads per own pixel in the loss pass
     static constexpr int kEpt = kC / kTpp;   // entries per thread in the loss pass
@@ -308,16 +310,17 @@ __device__ __forceinline__ void gram_part(uint32_t taddr, uint32_t colG, int war
 
 // Shared-memory views and loaders of one CTA's item, common to the forward
 // and the backward.
-template <int NC>
+template <class C>
 struct ItemSmem {
-    using C = NCfg<NC>;
     uint8_t *sm;
     uint32_t sm_s;
     __device__ RecAB *rec(int b) const { return reinterpret_cast<RecAB *>(sm + C::kOffRec + (b & 1) * kC * 32); }
     __device__ uint32_t *gid(int b) const {
         return reinterpret_cast<uint32_t *>(sm + C::kOffGid + ((b % 3 + 3) % 3) * kC * 4);
     }
-    __device__ uint32_t feat_s(int b) const { return sm_s + C::kOffF + (uint32_t)(b & 1) * (2 * kC * 128); }
+    __device__ uint32_t feat_s(int b) const {
+        return sm_s + C::kOffF + (C::kFStages == 2 ? (uint32_t)(b & 1) : 0u) * (2 * kC * 128);
+    }
     __device__ PixState pix() const {
         int *base = reinterpret_cast<int *>(sm + C::kOffPix);
         return PixState{reinterpret_cast<float *>(base), base + 128, base + 256, reinterpret_cast<float *>(base + 384),
@@ -336,9 +339,10 @@ struct ItemSmem {
 // not, so that the waits on group counts hold.  Chunk b of the item holds list
 // entries [s + 64 b, s + 64 b + 64) of camera ci; `q` selects the CTA's 128
 // channels.
-template <int NC>
+template <class C>
 struct Loader {
-    const ItemSmem<NC> &S;
+    static constexpr int NC = C::kNC;
+    const ItemSmem<C> &S;
     const uint32_t *gids;
     const GRec *rec;
     const __nv_bfloat16 *feats;
@@ -445,10 +449,10 @@ __device__ __forceinline__ void issue_w_gram(uint32_t tD, uint64_t wh, uint64_t 
 // contiguous bytes of 8 rows rather than 16 bytes of 32 rows.  Warps 0..3
 // also send the pixels' partial |f_gt|^2, and the receiver's first X warp
 // the chunk's Gram diagonal.
-template <int NC>
-__device__ __forceinline__ void send_rows(const ItemSmem<NC> &S, uint32_t taddr, uint32_t colA, uint32_t colB, int q,
+template <class C>
+__device__ __forceinline__ void send_rows(const ItemSmem<C> &S, uint32_t taddr, uint32_t colA, uint32_t colB, int q,
                                           int warp, int lane, float *stage) {
-    using C = NCfg<NC>;
+    constexpr int NC = C::kNC;
     constexpr int kSR = 20;  // floats per staged row (16 + 4: spreads the banks)
     const int qd = warp & 3, dst = qd * NC / 4;
     const int row0 = qd * 32 - dst * C::kOwn;  // the warp's first row in the receiver's slot
@@ -483,10 +487,10 @@ __device__ __forceinline__ void send_rows(const ItemSmem<NC> &S, uint32_t taddr,
 
 // Stages the CTA's F_gt slice (BF16, K-major [2][128 px][64 ch]) of the
 // item's pixels, zero outside the image; commits one cp.async group.
-template <int NC>
-__device__ __forceinline__ void load_gt(const ItemSmem<NC> &S, const Item &it, const __nv_bfloat16 *fgt, int q,
+template <class C>
+__device__ __forceinline__ void load_gt(const ItemSmem<C> &S, const Item &it, const __nv_bfloat16 *fgt, int q,
                                         int tid) {
-    using C = NCfg<NC>;
+    constexpr int NC = C::kNC;
     const uint32_t g0 = S.sm_s + C::kOffGt;
     for (int c = tid; c < 128 * 16; c += 256) {
         const int row = c >> 4, cc = c & 15;
@@ -500,9 +504,8 @@ __device__ __forceinline__ void load_gt(const ItemSmem<NC> &S, const Item &it, c
 }
 
 // Partial |f_gt|^2 over the CTA's channels of pixel tid (tid < 128).
-template <int NC>
-__device__ __forceinline__ void gt_norm(const ItemSmem<NC> &S, int tid) {
-    using C = NCfg<NC>;
+template <class C>
+__device__ __forceinline__ void gt_norm(const ItemSmem<C> &S, int tid) {
     if (tid >= 128) return;
     float s2 = 0.f;
 #pragma unroll
@@ -521,9 +524,9 @@ __device__ __forceinline__ void gt_norm(const ItemSmem<NC> &S, int tid) {
 
 // 1 / |f_i| of the chunk's entries (tid < 64) from the NC senders' Gram
 // diagonals, 0 for a zero feature row, into `inv`.
-template <int NC>
-__device__ __forceinline__ void entry_inv_norms(const ItemSmem<NC> &S, int tid, float *inv) {
-    using C = NCfg<NC>;
+template <class C>
+__device__ __forceinline__ void entry_inv_norms(const ItemSmem<C> &S, int tid, float *inv) {
+    constexpr int NC = C::kNC;
     if (tid >= kC) return;
     float n2 = 0.f;
 #pragma unroll
@@ -540,9 +543,9 @@ __device__ __forceinline__ float sigma_fast(float phi, float k, float lam) {
 // The loss pass of the own pixels: kTpp threads per pixel, kEpt consecutive
 // entries each; adds the NC senders' partial Phi and X, then sigma and the
 // two loss terms of every contributor (w > 0).
-template <int NC>
-__device__ __forceinline__ void own_losses(const ItemSmem<NC> &S, int tid, float ks, float lam, const float *inv) {
-    using C = NCfg<NC>;
+template <class C>
+__device__ __forceinline__ void own_losses(const ItemSmem<C> &S, int tid, float ks, float lam, const float *inv) {
+    constexpr int NC = C::kNC;
     constexpr int E = C::kEpt;
     const int pl = tid / C::kTpp, k0 = (tid % C::kTpp) * E;
     const float *rv = S.recv();
@@ -604,7 +607,7 @@ __global__ void __launch_bounds__(256, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
     if (probe_wait_expired(p, sm, status)) return;  // uniform over the grid, before any cluster operation
-    const ItemSmem<NC> S{sm, smem_u32(sm)};
+    const ItemSmem<C> S{sm, smem_u32(sm)};
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = (int)cluster_rank();
     const Item it = make_item(cs, ranges, (int)(blockIdx.x / NC), q);
@@ -636,8 +639,8 @@ __global__ void __launch_bounds__(256, 1)
         ps.last[pidx] = 0;
     }
     if (tid < C::kOwn) S.acc(0)[tid] = S.acc(1)[tid] = S.acc(2)[tid] = 0.f;
-    const Loader<NC> L{S, gids, pv.rec + (long long)it.ci * N, feats, it.s, it.e, nchunks, q, tid};
-    load_gt<NC>(S, it, fgt, q, tid);
+    const Loader<C> L{S, gids, pv.rec + (long long)it.ci * N, feats, it.s, it.e, nchunks, q, tid};
+    load_gt<C>(S, it, fgt, q, tid);
     L.gid(0);
     L.gid(1);
     tc_before();
@@ -649,7 +652,7 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     L.records(0);
     L.features(0);
-    gt_norm<NC>(S, tid);
+    gt_norm<C>(S, tid);
 
     const uint32_t sGt = S.sm_s + C::kOffGt, sWh = S.sm_s + C::kOffWh, sWl = S.sm_s + C::kOffWl;
     const uint32_t sGh = S.sm_s + C::kOffGh, sGl = S.sm_s + C::kOffGl;
@@ -715,16 +718,16 @@ __global__ void __launch_bounds__(256, 1)
             break;
         }
         // the weight operands are free until the next chunk's weights: 8 warps x 2.5 KB of staging
-        send_rows<NC>(S, taddr, C::kColPhi, C::kColX, q, warp, lane, reinterpret_cast<float *>(sm + C::kOffWh));
+        send_rows<C>(S, taddr, C::kColPhi, C::kColX, q, warp, lane, reinterpret_cast<float *>(sm + C::kOffWh));
         ok = mbar_wait_cluster(&bars[2], (uint32_t)(b & 1));
         if (__syncthreads_or(!ok)) {
             timeout = true;
             if (tid == 0) latch(status, ST_TIMEOUT);
             break;
         }
-        entry_inv_norms<NC>(S, tid, S.diag());  // the diagonal itself was sent: reuse its buffer
+        entry_inv_norms<C>(S, tid, S.diag());  // the diagonal itself was sent: reuse its buffer
         __syncthreads();
-        own_losses<NC>(S, tid, ks, lam, S.diag());
+        own_losses<C>(S, tid, ks, lam, S.diag());
         __syncthreads();
         if (tid < NC) mbar_arrive_cluster(mapa(smem_u32(&bars[3]), (uint32_t)tid));  // this CTA's slots are read
         if (all_done) break;
@@ -741,6 +744,601 @@ __global__ void __launch_bounds__(256, 1)
             if (nc_out) nc_out[opix] = (int32_t)S.acc(2)[tid];
         }
     }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, 512);
+    cluster_sync();  // no CTA leaves while another may still write to its shared memory
+}
+
+// ------------------------------------------------------------- backward
+// The backward (App. A.2 with the NDFD terms of Sec. 3.3):
+//   dL/dw_k = c_gt sigma_k + c_cf (sigma_k (W_{k-1} - F_{k-1} . f_k) + S_k - G_k . f_k),
+//   S_k = sum_{i>k} sigma_i w_i,  G_k = sum_{i>k} sigma_i w_i f_i,
+//   dL/dalpha_k = T_k dL/dw_k - Sw_k / (1 - alpha_k),  Sw_k = sum_{i>k} w_i dL/dw_i,
+// then the footprint chain of the render backward.  Pass A rebuilds F_N
+// front to back (weights and F += W F_c).  Pass B walks the chunks back to
+// front; per chunk, with F_end and G_end the sums over the later entries:
+//   X = F_end . F_c^T - W . Gs      (F_{k-1} . f_k plus w_k Gamma_kk)
+//   Y = G_end . F_c^T + (sigma W) . Gs   (G_k . f_k)
+//   F -= W . F_c,  G += (sigma W) . F_c
+// with Gs[i][k] = f_i . f_k for i > k.  sigma needs the full Phi: the
+// partial Phi rows go to the pixels' owner (round 1), which returns sigma w
+// to every CTA (round 2); the partial X and Y rows then go to the owner
+// (round 3), which runs the recursion for its pixels and adds their
+// footprint gradients to the per-(camera, Gaussian) array.
+
+template <int NC>
+struct NBCfg {
+    static constexpr int kNC = NC;
+    static constexpr int kOwn = 128 / NC, kTpp = 256 / kOwn, kEpt = kC / kTpp;
+    static constexpr int kRow = 2 * kC + 4;
+    static constexpr int kSlotF = kOwn * kRow + kC + kOwn;   // rows; Gram diagonal [64]; partial |f_gt|^2
+    static constexpr int kFStages = 1;  // chunk b's features load under its weights
+    static constexpr int kOffGt = 0;
+    static constexpr int kOffF = kOffGt + 2 * 128 * 128;
+    static constexpr int kOffWh = kOffF + kFStages * 2 * kC * 128;  // -W, then sigma W (hi)
+    static constexpr int kOffWl = kOffWh + 128 * 128;
+    static constexpr int kOffGh = kOffWl + 128 * 128;                // Gs: f_i . f_k for i > k (hi, lo)
+    static constexpr int kOffGl = kOffGh + kC * 128;
+    static constexpr int kOffRecv = kOffGl + kC * 128;
+    static constexpr int kOffStash = kOffRecv + cal(NC * kSlotF * 4, 16);  // [3][kOwn][kStashRow]: alpha, T, sigma
+    static constexpr int kOffRec = kOffStash + 3 * kOwn * kStashRow * 4;
+    static constexpr int kOffGid = kOffRec + 2 * kC * 32;
+    // [9][128]: T, done, last, P0, L0, |f_gt|^2 per pixel, then 5 x kOwn scalars of the own pixels
+    static constexpr int kOffPix = kOffGid + 3 * kC * 4;
+    static constexpr int kOffDiag = kOffPix + 9 * 128 * 4;  // [2][64]: full Gram diagonal, inverse norms
+    static constexpr int kOffAcc = kOffDiag + 2 * kC * 4;   // [64][8] footprint gradients of the own pixels
+    static constexpr int kOffBar = cal(kOffAcc + kC * 8 * 4, 8);
+    static constexpr int kSmem = 1024 + kOffBar + 128;      // 11 barriers, the TMEM slot, Lmax
+    static_assert(kSmem <= 232448, "NDFD backward CTA exceeds the opt-in shared memory");
+    static constexpr uint32_t kColF = 0, kColG = 128, kColA = 256, kColB = 320, kColH = 384, kColL = 448;
+};
+
+// Back-to-front weights of one chunk for the 128 pixels.  The contributors
+// are the entries before the pixel's last contributor (pos < last) that pass
+// the alpha test; with T_end, the transmittance after the chunk, group 1
+// (entries 32..63) starts from T_end / P_1 and group 0 from that / P_0 (P_g
+// the product of (1 - alpha) over the group's contributors), then a forward
+// running product gives T before each entry.  Writes -w (BF16 hi + lo) into
+// the K-major weight operand, alpha and T of the own pixels into the stash,
+// and T entering the chunk back into the state.
+__device__ __forceinline__ void chunk_weights_bwd(const Params &p, const RecAB *R, int nb, int pos0, int pidx, int grp,
+                                                  float fpx, float fpy, PixState ps, uint8_t *sWh, uint8_t *sWl,
+                                                  float *stash_a, float *stash_T, int own0, int own) {
+    const float T_end = ps.T[pidx];
+    const int last = ps.last[pidx];
+    float a[32], l[32];
+    float P = 1.f;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+        const int j = grp * 32 + jj;
+        const float4 A4 = R[j].a, B4 = R[j].b;
+        const float dx = fpx - A4.x, dy = fpy - A4.y;
+        const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
+        const float al = fminf(p.amax, B4.y * gauss_q2(q2));
+        a[jj] = (j < nb && pos0 + j < last && q2 <= p.cut && al >= p.amin) ? al : 0.f;
+        l[jj] = P;
+        P *= 1.f - a[jj];
+    }
+    if (grp == 1) ps.P0[pidx] = P;
+    __syncthreads();
+    const float T1 = T_end / ps.P0[pidx];         // T entering group 1
+    const float Ts = grp == 1 ? T1 : T1 / P;      // T entering this group
+    const int pl = pidx - own0;
+    const bool mine = pl >= 0 && pl < own;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+        float w8[8], T8[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int jj = 8 * qq + h;
+            T8[h] = Ts * l[jj];
+            w8[h] = a[jj] * T8[h];
+        }
+        if (mine) {
+            float *da = stash_a + pl * kStashRow + grp * 32 + 8 * qq, *dT = stash_T + pl * kStashRow + grp * 32 + 8 * qq;
+            *reinterpret_cast<float4 *>(da) = make_float4(a[8 * qq], a[8 * qq + 1], a[8 * qq + 2], a[8 * qq + 3]);
+            *reinterpret_cast<float4 *>(da + 4) = make_float4(a[8 * qq + 4], a[8 * qq + 5], a[8 * qq + 6], a[8 * qq + 7]);
+            *reinterpret_cast<float4 *>(dT) = make_float4(T8[0], T8[1], T8[2], T8[3]);
+            *reinterpret_cast<float4 *>(dT + 4) = make_float4(T8[4], T8[5], T8[6], T8[7]);
+        }
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(-w8[2 * u], h0, l0);
+            split_bf16(-w8[2 * u + 1], h1, l1);
+            hw[u] = pack2(h0, h1);
+            lw[u] = pack2(l0, l1);
+        }
+        *reinterpret_cast<uint4 *>(sWh + swz(pidx, grp * 4 + qq)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(sWl + swz(pidx, grp * 4 + qq)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    __syncthreads();  // T_end and P_1 are read before T is rewritten
+    if (grp == 0) ps.T[pidx] = Ts;
+}
+
+// Half of a pixel row exchange: warps w and w + 4 (lane quadrant w % 4) send
+// columns [32 (w / 4), + 32) of the TMEM accumulator at `col` into the
+// `half` (0: first 64 floats, 1: second) of this CTA's slot at the owner of
+// those pixels, through a 2.5 KB staging tile per warp; warps 0..3 add the
+// partial |f_gt|^2 when `ngt`, the owner's first warp w >= 4 the Gram
+// diagonal when `diag`; every thread then arrives once on the owner's
+// barrier `bar` (unless `arrive` is false: a second call completes the
+// exchange).  Without a staging tile (stage == nullptr) each thread stores
+// its own row.
+template <class C>
+__device__ __forceinline__ void send_half(const ItemSmem<C> &S, uint32_t taddr, uint32_t col, int half, int q,
+                                          int warp, int lane, float *stage, bool ngt, bool diag, const float *dvals,
+                                          uint64_t *bar, bool arrive = true) {
+    constexpr int NC = C::kNC;
+    constexpr int kSR = 20;
+    const int qd = warp & 3, dst = qd * NC / 4, h2 = warp >> 2;
+    const int row0 = qd * 32 - dst * C::kOwn;
+    const uint32_t slot = mapa(smem_u32(S.recv() + q * C::kSlotF), (uint32_t)dst);
+#pragma unroll
+    for (int piece = 0; piece < 2; ++piece) {
+        float v[16];
+        tmem_ld16(taddr + ((uint32_t)(qd * 32) << 16) + col + 32 * h2 + 16 * piece, v);
+        if (stage == nullptr) {  // no free shared memory: each thread stores its own row
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                st_cluster_v4(slot + (uint32_t)((row0 + lane) * C::kRow + half * kC + 32 * h2 + 16 * piece + 4 * i) * 4u,
+                              v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            continue;
+        }
+        float *st = stage + warp * 32 * kSR;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            *reinterpret_cast<float4 *>(st + lane * kSR + 4 * i) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const int r = 8 * it + (lane >> 2), c4 = (lane & 3) * 4;
+            const float4 x = *reinterpret_cast<const float4 *>(st + r * kSR + c4);
+            st_cluster_v4(slot + (uint32_t)((row0 + r) * C::kRow + half * kC + 32 * h2 + 16 * piece + c4) * 4u, x.x,
+                          x.y, x.z, x.w);
+        }
+        __syncwarp();
+    }
+    if (ngt && h2 == 0) st_cluster_f32(slot + (uint32_t)(C::kOwn * C::kRow + kC + row0 + lane) * 4u, S.ngt()[qd * 32 + lane]);
+    if (diag && h2 == 1 && qd == dst * (4 / NC))
+        st_cluster_v2(slot + (uint32_t)(C::kOwn * C::kRow + 2 * lane) * 4u, dvals[2 * lane], dvals[2 * lane + 1]);
+    if (arrive) mbar_arrive_cluster(mapa(smem_u32(bar), (uint32_t)dst));
+}
+
+// Round 1 at the owner: adds the NC partial Phi rows of its pixels, forms
+// sigma of every contributor (w = alpha T > 0; 0 otherwise) into the stash
+// and sends sigma w of its pixels to the second half of its slot in every
+// CTA (round 2), one arrival per thread and CTA on their `bar`.  inv holds
+// the entries' inverse feature norms, igt the own pixels' inverse |f_gt|.
+template <class C>
+__device__ __forceinline__ void owner_sigma(const ItemSmem<C> &S, int tid, int q, float ks, float lam, const float *inv,
+                                            const float *igt, float *stash_a, float *stash_T, float *stash_s,
+                                            uint64_t *bar) {
+    constexpr int NC = C::kNC, E = C::kEpt;
+    const int pl = tid / C::kTpp, k0 = (tid % C::kTpp) * E;
+    float ph[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) ph[k] = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < NC; ++sl) {
+        const float *row = S.recv() + sl * C::kSlotF + pl * C::kRow + k0;
+#pragma unroll
+        for (int k = 0; k < E; k += 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(row + k);
+            ph[k] += a.x; ph[k + 1] += a.y; ph[k + 2] += a.z; ph[k + 3] += a.w;
+        }
+    }
+    const float ig = igt[pl];
+    float sw[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const float al = stash_a[pl * kStashRow + k0 + k], T = stash_T[pl * kStashRow + k0 + k];
+        const float w = al * T;
+        const float sg = w > 0.f ? sigma_fast(ph[k] * inv[k0 + k] * ig, ks, lam) : 0.f;
+        stash_s[pl * kStashRow + k0 + k] = sg;
+        sw[k] = sg * w;
+    }
+    const uint32_t off = (uint32_t)(q * C::kSlotF + pl * C::kRow + kC + k0) * 4u;
+#pragma unroll
+    for (int d = 0; d < NC; ++d) {
+        const uint32_t dst = mapa(smem_u32(S.recv()) + off, (uint32_t)d);
+#pragma unroll
+        for (int k = 0; k < E; k += 4) st_cluster_v4(dst + 4u * k, sw[k], sw[k + 1], sw[k + 2], sw[k + 3]);
+    }
+#pragma unroll
+    for (int d = 0; d < NC; ++d) mbar_arrive_cluster(mapa(smem_u32(bar), (uint32_t)d));
+}
+
+// Round 2 at every CTA: sigma w of all 128 pixels (second halves of the
+// owners' slots) -> the K-major [128 px][64] operand as BF16 hi + lo.
+template <class C>
+__device__ __forceinline__ void build_sigma_w(const ItemSmem<C> &S, int pidx, int grp, uint8_t *sWh, uint8_t *sWl) {
+    const int r = pidx / C::kOwn, pl = pidx - r * C::kOwn;
+    const float *row = S.recv() + r * C::kSlotF + pl * C::kRow + kC + grp * 32;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+        const float4 a = *reinterpret_cast<const float4 *>(row + 8 * qq);
+        const float4 b = *reinterpret_cast<const float4 *>(row + 8 * qq + 4);
+        const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(v[2 * u], h0, l0);
+            split_bf16(v[2 * u + 1], h1, l1);
+            hw[u] = pack2(h0, h1);
+            lw[u] = pack2(l0, l1);
+        }
+        *reinterpret_cast<uint4 *>(sWh + swz(pidx, grp * 4 + qq)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(sWl + swz(pidx, grp * 4 + qq)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+}
+
+// Round 3 at the owner: X and Y of its pixels (sums of the NC partials), then
+// back to front over the chunk, per pixel: S_k, dL/dw_k, Sw_k and dL/dalpha_k,
+// and the footprint gradients of every contributor added to acc[entry][0..5]
+// (mean x, y; conic A, B, C; opacity) in shared memory.  kTpp threads per
+// pixel, kEpt entries each; suffix sums over the threads by shuffles.  own
+// holds per own pixel: c_gt, c_cf, S and Sw of the later chunks (updated).
+template <class C>
+__device__ __forceinline__ void owner_grads(const ItemSmem<C> &S, int tid, const Params &p, const RecAB *R, float fpx,
+                                            float fpy, bool inside, const float *diag, const float *stash_a,
+                                            const float *stash_T, const float *stash_s, float *own, float *acc) {
+    constexpr int NC = C::kNC, E = C::kEpt, TP = C::kTpp;
+    const int pl = tid / TP, sub = tid % TP, k0 = sub * E;
+    float X[E], Y[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) X[k] = Y[k] = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < NC; ++sl) {
+        const float *row = S.recv() + sl * C::kSlotF + pl * C::kRow + k0;
+#pragma unroll
+        for (int k = 0; k < E; k += 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(row + k);
+            const float4 b = *reinterpret_cast<const float4 *>(row + kC + k);
+            X[k] += a.x; X[k + 1] += a.y; X[k + 2] += a.z; X[k + 3] += a.w;
+            Y[k] += b.x; Y[k + 1] += b.y; Y[k + 2] += b.z; Y[k + 3] += b.w;
+        }
+    }
+    float al[E], T[E], sg[E], w[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        al[k] = stash_a[pl * kStashRow + k0 + k];
+        T[k] = stash_T[pl * kStashRow + k0 + k];
+        sg[k] = stash_s[pl * kStashRow + k0 + k];
+        w[k] = al[k] * T[k];
+        X[k] -= w[k] * diag[k0 + k];  // F_{k-1} . f_k: the product above took F after entry k
+    }
+    const float cgt = own[pl], ccf = own[C::kOwn + pl];
+    // suffix sums of sigma w over the later entries of the chunk
+    float loc = 0.f;
+#pragma unroll
+    for (int k = 0; k < E; ++k) loc += sg[k] * w[k];
+    float incl = loc;  // inclusive suffix over threads sub, sub + 1, ...
+#pragma unroll
+    for (int d = 1; d < TP; d <<= 1) {
+        const float t = __shfl_down_sync(0xffffffffu, incl, d, TP);
+        if (sub + d < TP) incl += t;
+    }
+    const float Send = own[2 * C::kOwn + pl];
+    float Sk = Send + (incl - loc);  // entries after this thread's
+    float gw[E];
+#pragma unroll
+    for (int k = E - 1; k >= 0; --k) {
+        gw[k] = cgt * sg[k] + ccf * (sg[k] * ((1.f - T[k]) - X[k]) + Sk - Y[k]);
+        Sk += sg[k] * w[k];
+    }
+    float loc2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < E; ++k) loc2 += w[k] * gw[k];
+    float incl2 = loc2;
+#pragma unroll
+    for (int d = 1; d < TP; d <<= 1) {
+        const float t = __shfl_down_sync(0xffffffffu, incl2, d, TP);
+        if (sub + d < TP) incl2 += t;
+    }
+    const float Swend = own[3 * C::kOwn + pl];
+    float Sw = Swend + (incl2 - loc2);
+#pragma unroll
+    for (int k = E - 1; k >= 0; --k) {
+        if (w[k] > 0.f && inside) {
+            const float dal = T[k] * gw[k] - Sw / (1.f - al[k]);
+            const int j = k0 + k;
+            const float4 A = R[j].a, B = R[j].b;
+            const float dx = fpx - A.x, dy = fpy - A.y;
+            const float q2 = eval_q2(dx, dy, A.z, A.w, B.x);
+            const float G = gauss_q2(q2), rho = B.y * G;
+            const float drho = rho > p.amax ? 0.f : dal;
+            const float dq2 = -0.5f * rho * drho;
+            atomicAdd(&acc[j * 8 + 0], -(2.f * A.z * dx + 2.f * A.w * dy) * dq2);
+            atomicAdd(&acc[j * 8 + 1], -(2.f * A.w * dx + 2.f * B.x * dy) * dq2);
+            atomicAdd(&acc[j * 8 + 2], dx * dx * dq2);
+            atomicAdd(&acc[j * 8 + 3], 2.f * dx * dy * dq2);
+            atomicAdd(&acc[j * 8 + 4], dy * dy * dq2);
+            atomicAdd(&acc[j * 8 + 5], G * drho);
+        }
+        Sw += w[k] * gw[k];
+    }
+    // the chunk's totals carry to the earlier chunks
+    const float tot1 = __shfl_sync(0xffffffffu, incl, (tid & 31) - sub, 32);
+    const float tot2 = __shfl_sync(0xffffffffu, incl2, (tid & 31) - sub, 32);
+    if (sub == 0) {
+        own[2 * C::kOwn + pl] = Send + tot1;
+        own[3 * C::kOwn + pl] = Swend + tot2;
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(256, 1)
+    k_ndfd_bwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
+                  const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats,
+                  const __nv_bfloat16 *__restrict__ fgt, float ks, float lam, const float *__restrict__ dLgt,
+                  const float *__restrict__ dLcf, float *g2d, unsigned *status) {
+    using C = NBCfg<NC>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = align_smem_1024(smem_raw);
+    if (probe_wait_expired(p, sm, status)) return;  // uniform over the grid, before any cluster operation
+    const ItemSmem<C> S{sm, smem_u32(sm)};
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, grp = tid >> 7, pidx = tid & 127;
+    const int q = (int)cluster_rank(), own0 = q * C::kOwn;
+    const Item it = make_item(cs, ranges, (int)(blockIdx.x / NC), q);
+    const bool skip = (*(volatile unsigned *)status & ST_TIMEOUT) != 0;  // see the forward
+    const int nlist = skip ? 0 : (int)((it.e - it.s + kC - 1) / kC);
+    // [0] pass-A update, [1] Gamma + Phi, [2] X + F update, [3] Y + G update (local commits);
+    // [4] round-1 rows, [5] round-2 sigma w, [6] round-3 rows (data ready here);
+    // [7] round-2 data consumed, [8] round-3 rows consumed (at the senders)
+    uint64_t *bars = S.bars();
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 9);
+    int *sLmax = reinterpret_cast<int *>(bars + 10);
+    const PixState ps = S.pix();
+    float *own = S.ngt() + 128;  // [4][kOwn]: c_gt, c_cf, S, Sw of the own pixels; then [kOwn] inverse |f_gt|
+    float *igt = own + 4 * C::kOwn;
+    float *stash_a = reinterpret_cast<float *>(sm + C::kOffStash), *stash_T = stash_a + C::kOwn * kStashRow;
+    float *stash_s = stash_T + C::kOwn * kStashRow;
+    float *diag = reinterpret_cast<float *>(sm + C::kOffDiag), *inv = diag + kC;
+    float *acc = reinterpret_cast<float *>(sm + C::kOffAcc);
+    long long pix;
+    float fpx, fpy;
+    const bool inside = item_pixel(it, pidx, pix, fpx, fpy);
+    long long opix;
+    float ofx, ofy;  // this thread's own pixel in the owner passes
+    const int opl = tid / C::kTpp;
+    const bool oin = item_pixel(it, own0 + opl, opix, ofx, ofy);
+
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+        mbar_init(&bars[4], 256);
+        mbar_init(&bars[5], 256 * NC);
+        mbar_init(&bars[6], 256);
+        mbar_init(&bars[7], NC);
+        mbar_init(&bars[8], NC);
+        fence_mbar_init();
+        *sLmax = 0;
+    }
+    if (warp == 0) tmem_alloc(tslot, 512);
+    if (grp == 0) {
+        ps.T[pidx] = 1.f;
+        ps.done[pidx] = inside ? 0 : 1;
+        ps.last[pidx] = 0;
+    }
+    if (tid < C::kOwn) {
+        long long op;
+        float fx, fy;
+        const bool in = item_pixel(it, own0 + tid, op, fx, fy);
+        own[tid] = in ? dLgt[op] : 0.f;
+        own[C::kOwn + tid] = in ? dLcf[op] : 0.f;
+        own[2 * C::kOwn + tid] = own[3 * C::kOwn + tid] = 0.f;
+    }
+    for (int i = tid; i < kC * 8; i += 256) acc[i] = 0.f;
+    const Loader<C> L{S, gids, pv.rec + (long long)it.ci * N, feats, it.s, it.e, nlist, q, tid};
+    float *g2dc = g2d + (long long)it.ci * N * 12;
+    load_gt<C>(S, it, fgt, q, tid);
+    L.gid(0);
+    L.gid(1);
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t taddr = *tslot;
+    cluster_sync();  // every CTA's barriers are initialised before the first remote arrival
+    cp_async_wait<1>();  // F_gt and the ids of chunk 0
+    __syncthreads();
+    L.records(0);
+    gt_norm<C>(S, tid);
+
+    const uint32_t sGt = S.sm_s + C::kOffGt, sWh = S.sm_s + C::kOffWh, sWl = S.sm_s + C::kOffWl;
+    const uint32_t sGh = S.sm_s + C::kOffGh, sGl = S.sm_s + C::kOffGl;
+    const uint64_t dGt = sdesc(sGt, 16, 1024), dWh = sdesc(sWh, 16, 1024), dWl = sdesc(sWl, 16, 1024);
+    const uint64_t dGh = sdesc(sGh, 16, 1024), dGl = sdesc(sGl, 16, 1024);
+    const uint32_t tF = taddr + C::kColF, tG = taddr + C::kColG, tA = taddr + C::kColA, tB = taddr + C::kColB;
+    const uint32_t tH = taddr + C::kColH, tL = taddr + C::kColL;
+    float *stage = reinterpret_cast<float *>(sm + C::kOffWh);  // row staging while the weight operands are free
+
+    bool timeout = false;
+    int pend = -1;  // a commit barrier whose phase `pend_ph` may still be in flight
+    uint32_t pend_ph = 0;
+    // ---- pass A: F_N, T after the walk and the last contributors, front to back
+    for (int b = 0; b < nlist; ++b) {
+        const uint32_t base = it.s + (uint32_t)b * kC;
+        const int nb = (int)min((uint32_t)kC, it.e - base);
+        L.features(b);  // its stage was last read by the previous chunk's update, complete
+        cp_async_wait<1>();  // ids of b+1 and records of b (the features of b are the newest group)
+        __syncthreads();
+        L.gid(b + 2);
+        L.records(b + 1);
+        const bool all_done = chunk_weights(p, S.rec(b), nb, (int)(base - it.s), pidx, grp, fpx, fpy, ps, sm + C::kOffWh,
+                                            sm + C::kOffWl, stash_a, stash_T, own0, C::kOwn, false);
+        cp_async_wait<2>();  // the features of b
+        fence_async_smem();
+        tc_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_after();
+            issue_update(tF, dWh, dWl, chunk_desc(S.feat_s(b)), b > 0);
+            mma_commit(&bars[0]);
+        }
+        pend = 0;
+        pend_ph = (uint32_t)(b & 1);
+        const bool ok = mbar_wait(&bars[0], (uint32_t)(b & 1));  // the operands are reused by the next chunk
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+            if (tid == 0) latch(status, ST_TIMEOUT);
+            break;
+        }
+        pend = -1;
+        if (all_done) break;
+    }
+    cp_async_wait_all();
+    if (grp == 0) atomicMax(sLmax, ps.last[pidx]);
+    tc_after();
+    __syncthreads();
+    const int nB = timeout ? 0 : (min(*sLmax, (int)(it.e - it.s)) + kC - 1) / kC;
+    if (tid < C::kOwn) {  // inverse |f_gt| of the own pixels: the partial norms are exchanged in round 1
+        igt[tid] = 0.f;
+    }
+
+    // ---- pass B: back to front
+    if (nB > 0) {
+        L.gid(nB - 1);
+        L.gid(nB - 2);
+        cp_async_wait<1>();
+        __syncthreads();
+        L.records(nB - 1);
+    }
+    for (int b = nB - 1, itn = 0; b >= 0; --b, ++itn) {
+        const uint32_t ph = (uint32_t)(itn & 1);
+        const uint32_t base = it.s + (uint32_t)b * kC;
+        const int nb = (int)min((uint32_t)kC, it.e - base);
+        L.features(b);
+        cp_async_wait<1>();  // ids of b-1 and records of b (features of b are the newest group)
+        __syncthreads();
+        L.gid(b - 2);
+        L.records(b - 1);
+        chunk_weights_bwd(p, S.rec(b), nb, (int)(base - it.s), pidx, grp, fpx, fpy, ps, sm + C::kOffWh, sm + C::kOffWl,
+                          stash_a, stash_T, own0, C::kOwn);
+        split_to_tmem(taddr, C::kColF, C::kColH, C::kColL, warp);  // F_end
+        cp_async_wait<2>();  // the features of b (the records of b-1 and ids of b-2 may be in flight)
+        fence_async_smem();
+        tc_before();
+        __syncthreads();
+        const ChunkDesc cd = chunk_desc(S.feat_s(b));
+        if (tid == 0) {
+            tc_after();
+            issue_gram(tA, cd);
+            issue_rows_x_chunk(tB, dGt, 128 * 128, cd, false);
+            mma_commit(&bars[1]);
+        }
+        pend = 1;
+        pend_ph = ph;
+        bool ok = mbar_wait(&bars[1], ph);
+        tc_after();
+        if ((warp & 3) < 2 && ok) gram_part(taddr, C::kColA, warp, lane, false, sm + C::kOffGh, sm + C::kOffGl, diag);
+        fence_async_smem();
+        // round 1: every owner has consumed the round-3 rows of the previous chunk
+        if (ok && itn > 0) ok = mbar_wait_cluster(&bars[8], (uint32_t)((itn - 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+            if (tid == 0) latch(status, ST_TIMEOUT);
+            break;
+        }
+        pend = -1;
+        // the weight operands still feed X and the F update: no staging tile
+        send_half<C>(S, taddr, C::kColB, 0, q, warp, lane, nullptr, true, true, diag, &bars[4]);
+        tc_before();
+        __syncthreads();  // Gamma and Phi are read: their columns take X and Y
+        if (tid == 0) {
+            tc_after();
+            issue_tmem_x_chunk(tA, tH, tL, cd, false);        // X = F_end F_c^T
+            issue_w_gram(tA, dWh, dWl, dGh, dGl, true);       //   - W Gs
+            issue_update(tF, dWh, dWl, cd, true);             // F -= W F_c
+            mma_commit(&bars[2]);
+        }
+        pend = 2;
+        pend_ph = ph;
+        // round 1 at the owner: sigma of its pixels, sigma w to every CTA
+        ok = mbar_wait_cluster(&bars[4], ph);
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+            if (tid == 0) latch(status, ST_TIMEOUT);
+            break;
+        }
+        if (tid < kC) {
+            float d2 = 0.f;
+#pragma unroll
+            for (int sl = 0; sl < NC; ++sl) d2 += S.recv()[sl * C::kSlotF + C::kOwn * C::kRow + tid];
+            diag[tid] = d2;
+            inv[tid] = d2 > 0.f ? 1.f / sqrtf(d2) : 0.f;
+        }
+        if (itn == 0 && tid < C::kOwn) {
+            float n2 = 0.f;
+#pragma unroll
+            for (int sl = 0; sl < NC; ++sl) n2 += S.recv()[sl * C::kSlotF + C::kOwn * C::kRow + kC + tid];
+            igt[tid] = n2 > 0.f ? 1.f / sqrtf(n2) : 0.f;
+        }
+        __syncthreads();
+        owner_sigma<C>(S, tid, q, ks, lam, inv, igt, stash_a, stash_T, stash_s, &bars[5]);
+        // X's reads of F hi/lo and of -W are done: G_end -> hi/lo, sigma w -> the weight operands
+        ok = mbar_wait(&bars[2], ph);
+        if (ok) {
+            tc_after();
+            if (itn > 0) split_to_tmem(taddr, C::kColG, C::kColH, C::kColL, warp);
+        }
+        if (ok) ok = mbar_wait_cluster(&bars[5], ph);
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+            if (tid == 0) latch(status, ST_TIMEOUT);
+            break;
+        }
+        build_sigma_w<C>(S, pidx, grp, sm + C::kOffWh, sm + C::kOffWl);
+        fence_async_smem();
+        tc_before();
+        __syncthreads();
+        if (tid < NC) mbar_arrive_cluster(mapa(smem_u32(&bars[7]), (uint32_t)tid));  // round-2 data consumed
+        if (tid == 0) {
+            tc_after();
+            if (itn > 0) issue_tmem_x_chunk(tB, tH, tL, cd, false);   // Y = G_end F_c^T
+            issue_w_gram(tB, dWh, dWl, dGh, dGl, itn > 0);            //   + sigma W Gs
+            issue_update(tG, dWh, dWl, cd, itn > 0);                  // G += sigma W F_c
+            mma_commit(&bars[3]);
+        }
+        pend = 3;
+        pend_ph = ph;
+        ok = mbar_wait(&bars[3], ph);
+        if (ok) ok = mbar_wait_cluster(&bars[7], ph);  // every owner has built its sigma W operand
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+            if (tid == 0) latch(status, ST_TIMEOUT);
+            break;
+        }
+        pend = -1;
+        tc_after();
+        // round 3: X (first halves) and Y (second halves) to the owners
+        send_half<C>(S, taddr, C::kColA, 0, q, warp, lane, stage, false, false, diag, &bars[6], false);
+        send_half<C>(S, taddr, C::kColB, 1, q, warp, lane, stage, false, false, diag, &bars[6]);
+        ok = mbar_wait_cluster(&bars[6], ph);
+        if (__syncthreads_or(!ok)) {
+            timeout = true;
+            if (tid == 0) latch(status, ST_TIMEOUT);
+            break;
+        }
+        owner_grads<C>(S, tid, p, S.rec(b), ofx, ofy, oin, diag, stash_a, stash_T, stash_s, own, acc);
+        __syncthreads();
+        if (tid < NC) mbar_arrive_cluster(mapa(smem_u32(&bars[8]), (uint32_t)tid));  // round-3 rows consumed
+        if (tid < kC && tid < nb) {  // the own pixels' footprint gradients of the chunk's Gaussians
+            const float4 u = *reinterpret_cast<const float4 *>(acc + tid * 8);
+            const float2 t = *reinterpret_cast<const float2 *>(acc + tid * 8 + 4);
+            if (u.x != 0.f || u.y != 0.f || u.z != 0.f || u.w != 0.f || t.x != 0.f || t.y != 0.f) {
+                float *dst = g2dc + 12 * (long long)S.gid(b)[tid];
+                atomicAdd(reinterpret_cast<float4 *>(dst), u);
+                atomicAdd(reinterpret_cast<float2 *>(dst + 4), t);
+            }
+            *reinterpret_cast<float4 *>(acc + tid * 8) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float2 *>(acc + tid * 8 + 4) = make_float2(0.f, 0.f);
+        }
+    }
+    cp_async_wait_all();
+    if (timeout && pend >= 0) mbar_wait(&bars[pend], pend_ph);
     tc_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(taddr, 512);
@@ -777,9 +1375,28 @@ void launch_fwd_tc_t(long long N, const CamSet &cs, const Params &p, ProjView pv
                        status);
 }
 
+template <int NC>
+void launch_bwd_tc_t(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                     const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, float ks, float lam, const float *dLgt,
+                     const float *dLcf, float *g2d, unsigned *status, cudaStream_t st) {
+    static std::atomic<unsigned long long> smem_set{0};
+    allow_max_smem(smem_set, k_ndfd_bwd_tc<NC>);
+    launch_cluster<NC>(k_ndfd_bwd_tc<NC>, NBCfg<NC>::kSmem, (unsigned)cs.total_tiles * 2u, st, N, cs, p, pv,
+                       (const uint32_t *)bins.gids, (const uint32_t *)bins.ranges, feats, fgt, ks, lam, dLgt, dLcf,
+                       g2d, status);
+}
+
 }  // namespace
 
 bool ndfd_tc_supported(int D) { return D == 256 || D == 512; }
+
+void launch_ndfd_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
+                        const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam,
+                        const float *dLgt, const float *dLcf, float *g2d, unsigned *status, cudaStream_t st) {
+    if (cs.total_tiles == 0) return;
+    if (D == 512) launch_bwd_tc_t<4>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, status, st);
+    else if (D == 256) launch_bwd_tc_t<2>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, status, st);
+}
 
 void launch_ndfd_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                         const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam, float *Lgt,

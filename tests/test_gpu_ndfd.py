@@ -65,7 +65,7 @@ def run_ndfd(sc, cams, prm, fg, bf16=True, grads=None, path=api.PATH_AUTO):
     tc = tc_expected(int(sc["features"].shape[1]), bf16, path)
     assert ("ndfd_fwd_tc" if tc else "ndfd_fwd") in prof, prof
     if grads is not None:
-        assert "ndfd_bwd" in prof, prof
+        assert ("ndfd_bwd_tc" if tc else "ndfd_bwd") in prof, prof
     return out
 
 
@@ -130,8 +130,10 @@ def test_ndfd_forward_multicamera_ragged():
     check_losses(out, sc, cams, prm, fg, prep)
 
 
-@pytest.mark.parametrize("D,bf16", [(256, True), (512, True), (64, False)])
-def test_ndfd_backward_small(D, bf16):
+@pytest.mark.parametrize("D,bf16,path", [(256, True, api.PATH_AUTO), (512, True, api.PATH_AUTO),
+                                         (256, True, api.PATH_FP32), (512, True, api.PATH_FP32),
+                                         (64, False, api.PATH_AUTO)])
+def test_ndfd_backward_small(D, bf16, path):
     cams = [synth.look_at_camera(synth.ring_position(3.0, 40, -10), 64, 48)]
     sc, fg = ndfd_case(1500, 63 + D, D, cams, bf16=bf16, sh_degree=2)
     prm = dict(sh_degree=2)
@@ -139,16 +141,38 @@ def test_ndfd_backward_small(D, bf16):
     a = g.standard_normal(64 * 48).astype(np.float32)
     b = g.standard_normal(64 * 48).astype(np.float32)
     prep = oracle.prepare(sc, cams, prm)
-    out = run_ndfd(sc, cams, prm, fg, bf16=bf16, grads=(a, b))
+    out = run_ndfd(sc, cams, prm, fg, bf16=bf16, grads=(a, b), path=path)
     check_losses(out, sc, cams, prm, fg, prep)
     ref = oracle.ndfd_backward(sc, cams, prm, sc["features"], fg, [a], [b], prep=prep)
     check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities"), tol=1e-3)
     assert not np.any(out["grads"]["sh"])
     # each loss alone (the two upstream gradients enter separately)
     z = np.zeros_like(a)
-    out2 = run_ndfd(sc, cams, prm, fg, bf16=bf16, grads=(z, b))
-    ref2 = oracle.ndfd_backward(sc, cams, prm, sc["features"], fg, [z], [b], prep=prep)
-    check_grads(out2["grads"], ref2, keys=("means", "scales", "quats", "opacities"), tol=1e-3)
+    for ga, gb in ((z, b), (a, z)):
+        out2 = run_ndfd(sc, cams, prm, fg, bf16=bf16, grads=(ga, gb), path=path)
+        ref2 = oracle.ndfd_backward(sc, cams, prm, sc["features"], fg, [ga], [gb], prep=prep)
+        check_grads(out2["grads"], ref2, keys=("means", "scales", "quats", "opacities"), tol=1e-3)
+
+
+@pytest.mark.parametrize("D", [256, 512])
+def test_ndfd_backward_tensor_core_ragged_multicamera_long_lists(D):
+    """The tensor-core backward over ragged cameras, walks of several
+    64-entry chunks and pixels that stop early, against the oracle."""
+    cams = [synth.look_at_camera(synth.ring_position(2.4, a, e), w, h)
+            for a, e, w, h in [(10, 5, 70, 50), (140, 25, 33, 47), (260, -20, 96, 64)]]
+    sc, fg = ndfd_case(9000, 65 + D, D, cams, sh_degree=1, spread=0.45)
+    prm = dict(sh_degree=1)
+    P = [c["width"] * c["height"] for c in cams]
+    offs = np.cumsum([0] + P)
+    g = synth.rng(7, 4)
+    a = g.standard_normal(offs[-1]).astype(np.float32)
+    b = g.standard_normal(offs[-1]).astype(np.float32)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_ndfd(sc, cams, prm, fg, grads=(a, b), path=api.PATH_TC)
+    assert out["nc"].max() > 64
+    ref = oracle.ndfd_backward(sc, cams, prm, sc["features"], fg, [a[offs[i]:offs[i + 1]] for i in range(3)],
+                               [b[offs[i]:offs[i + 1]] for i in range(3)], prep=prep)
+    check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities"), tol=1e-3)
 
 
 def test_ndfd_backward_multicamera():
