@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(256, 1)
 template <int NC>
 struct NBCfg {
     static constexpr int kNC = NC;
-    static constexpr int kOwn = 128 / NC, kTpp = 256 / kOwn, kEpt = kC / kTpp;
+    static constexpr int kOwn = 128 / NC;  // the owner passes: warp w takes own pixels w, w + 8, ...
     static constexpr int kRow = 2 * kC + 4;
     static constexpr int kSlotF = kOwn * kRow + kC + kOwn;   // rows; Gram diagonal [64]; partial |f_gt|^2
     static constexpr int kFStages = 1;  // chunk b's features load under its weights
@@ -910,42 +910,38 @@ __device__ __forceinline__ void send_half(const ItemSmem<C> &S, uint32_t taddr, 
 // Round 1 at the owner: adds the NC partial Phi rows of its pixels, forms
 // sigma of every contributor (w = alpha T > 0; 0 otherwise) into the stash
 // and sends sigma w of its pixels to the second half of its slot in every
-// CTA (round 2), one arrival per thread and CTA on their `bar`.  inv holds
-// the entries' inverse feature norms, igt the own pixels' inverse |f_gt|.
+// CTA (round 2), one arrival per thread and CTA on their `bar`.  Warp w
+// takes the own pixels w, w + 8, ...; lane l entries l and l + 32, so that
+// each remote store writes 128 contiguous bytes.  inv holds the entries'
+// inverse feature norms, igt the own pixels' inverse |f_gt|.
 template <class C>
-__device__ __forceinline__ void owner_sigma(const ItemSmem<C> &S, int tid, int q, float ks, float lam, const float *inv,
-                                            const float *igt, float *stash_a, float *stash_T, float *stash_s,
-                                            uint64_t *bar) {
-    constexpr int NC = C::kNC, E = C::kEpt;
-    const int pl = tid / C::kTpp, k0 = (tid % C::kTpp) * E;
-    float ph[E];
+__device__ __forceinline__ void owner_sigma(const ItemSmem<C> &S, int warp, int lane, int q, float ks, float lam,
+                                            const float *inv, const float *igt, const float *stash_a,
+                                            const float *stash_T, float *stash_s, uint64_t *bar) {
+    constexpr int NC = C::kNC;
+    const float inv0 = inv[lane], inv1 = inv[lane + 32];
+    for (int pl = warp; pl < C::kOwn; pl += 8) {
+        float ph0 = 0.f, ph1 = 0.f;
 #pragma unroll
-    for (int k = 0; k < E; ++k) ph[k] = 0.f;
-#pragma unroll
-    for (int sl = 0; sl < NC; ++sl) {
-        const float *row = S.recv() + sl * C::kSlotF + pl * C::kRow + k0;
-#pragma unroll
-        for (int k = 0; k < E; k += 4) {
-            const float4 a = *reinterpret_cast<const float4 *>(row + k);
-            ph[k] += a.x; ph[k + 1] += a.y; ph[k + 2] += a.z; ph[k + 3] += a.w;
+        for (int sl = 0; sl < NC; ++sl) {
+            const float *row = S.recv() + sl * C::kSlotF + pl * C::kRow;
+            ph0 += row[lane];
+            ph1 += row[lane + 32];
         }
-    }
-    const float ig = igt[pl];
-    float sw[E];
+        const float ig = igt[pl];
+        const float w0 = stash_a[pl * kStashRow + lane] * stash_T[pl * kStashRow + lane];
+        const float w1 = stash_a[pl * kStashRow + lane + 32] * stash_T[pl * kStashRow + lane + 32];
+        const float s0 = w0 > 0.f ? sigma_fast(ph0 * inv0 * ig, ks, lam) : 0.f;
+        const float s1 = w1 > 0.f ? sigma_fast(ph1 * inv1 * ig, ks, lam) : 0.f;
+        stash_s[pl * kStashRow + lane] = s0;
+        stash_s[pl * kStashRow + lane + 32] = s1;
+        const uint32_t off = smem_u32(S.recv()) + (uint32_t)(q * C::kSlotF + pl * C::kRow + kC + lane) * 4u;
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-        const float al = stash_a[pl * kStashRow + k0 + k], T = stash_T[pl * kStashRow + k0 + k];
-        const float w = al * T;
-        const float sg = w > 0.f ? sigma_fast(ph[k] * inv[k0 + k] * ig, ks, lam) : 0.f;
-        stash_s[pl * kStashRow + k0 + k] = sg;
-        sw[k] = sg * w;
-    }
-    const uint32_t off = (uint32_t)(q * C::kSlotF + pl * C::kRow + kC + k0) * 4u;
-#pragma unroll
-    for (int d = 0; d < NC; ++d) {
-        const uint32_t dst = mapa(smem_u32(S.recv()) + off, (uint32_t)d);
-#pragma unroll
-        for (int k = 0; k < E; k += 4) st_cluster_v4(dst + 4u * k, sw[k], sw[k + 1], sw[k + 2], sw[k + 3]);
+        for (int d = 0; d < NC; ++d) {
+            const uint32_t dst = mapa(off, (uint32_t)d);
+            st_cluster_f32(dst, s0 * w0);
+            st_cluster_f32(dst + 128u, s1 * w1);
+        }
     }
 #pragma unroll
     for (int d = 0; d < NC; ++d) mbar_arrive_cluster(mapa(smem_u32(bar), (uint32_t)d));
@@ -976,97 +972,94 @@ __device__ __forceinline__ void build_sigma_w(const ItemSmem<C> &S, int pidx, in
     }
 }
 
+// Inclusive suffix sum over the lanes: lane l gets the sum of lanes l..31.
+__device__ __forceinline__ float lane_suffix(float x, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float t = __shfl_down_sync(0xffffffffu, x, d);
+        if (lane + d < 32) x += t;
+    }
+    return x;
+}
+
 // Round 3 at the owner: X and Y of its pixels (sums of the NC partials), then
 // back to front over the chunk, per pixel: S_k, dL/dw_k, Sw_k and dL/dalpha_k,
-// and the footprint gradients of every contributor added to acc[entry][0..5]
-// (mean x, y; conic A, B, C; opacity) in shared memory.  kTpp threads per
-// pixel, kEpt entries each; suffix sums over the threads by shuffles.  own
-// holds per own pixel: c_gt, c_cf, S and Sw of the later chunks (updated).
+// and the footprint gradients (mean x, y; conic A, B, C; opacity) of every
+// contributor.  Warp w takes the own pixels w, w + 8, ...; lane l entries l
+// and l + 32 (entry l + 32 comes later in the walk), so the suffix sums are
+// lane scans and each lane sums its two entries' gradients over its pixels
+// in registers before one shared-memory atomic per component and warp into
+// acc[entry][0..5].  own holds per own pixel: c_gt, c_cf, and S and Sw of the
+// later chunks (updated).
 template <class C>
-__device__ __forceinline__ void owner_grads(const ItemSmem<C> &S, int tid, const Params &p, const RecAB *R, float fpx,
-                                            float fpy, bool inside, const float *diag, const float *stash_a,
+__device__ __forceinline__ void owner_grads(const ItemSmem<C> &S, int warp, int lane, const Params &p, const RecAB *R,
+                                            const Item &it, int own0, const float *diag, const float *stash_a,
                                             const float *stash_T, const float *stash_s, float *own, float *acc) {
-    constexpr int NC = C::kNC, E = C::kEpt, TP = C::kTpp;
-    const int pl = tid / TP, sub = tid % TP, k0 = sub * E;
-    float X[E], Y[E];
+    constexpr int NC = C::kNC;
+    const float4 A0 = R[lane].a, B0 = R[lane].b, A1 = R[lane + 32].a, B1 = R[lane + 32].b;
+    const float dg0 = diag[lane], dg1 = diag[lane + 32];
+    float g0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, g1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int pl = warp; pl < C::kOwn; pl += 8) {
+        long long pix;
+        float fpx, fpy;
+        const bool inside = item_pixel(it, own0 + pl, pix, fpx, fpy);
+        float X0 = 0.f, X1 = 0.f, Y0 = 0.f, Y1 = 0.f;
 #pragma unroll
-    for (int k = 0; k < E; ++k) X[k] = Y[k] = 0.f;
-#pragma unroll
-    for (int sl = 0; sl < NC; ++sl) {
-        const float *row = S.recv() + sl * C::kSlotF + pl * C::kRow + k0;
-#pragma unroll
-        for (int k = 0; k < E; k += 4) {
-            const float4 a = *reinterpret_cast<const float4 *>(row + k);
-            const float4 b = *reinterpret_cast<const float4 *>(row + kC + k);
-            X[k] += a.x; X[k + 1] += a.y; X[k + 2] += a.z; X[k + 3] += a.w;
-            Y[k] += b.x; Y[k + 1] += b.y; Y[k + 2] += b.z; Y[k + 3] += b.w;
+        for (int sl = 0; sl < NC; ++sl) {
+            const float *row = S.recv() + sl * C::kSlotF + pl * C::kRow;
+            X0 += row[lane];
+            X1 += row[lane + 32];
+            Y0 += row[kC + lane];
+            Y1 += row[kC + lane + 32];
         }
-    }
-    float al[E], T[E], sg[E], w[E];
+        const float a0 = stash_a[pl * kStashRow + lane], a1 = stash_a[pl * kStashRow + lane + 32];
+        const float T0 = stash_T[pl * kStashRow + lane], T1 = stash_T[pl * kStashRow + lane + 32];
+        const float s0 = stash_s[pl * kStashRow + lane], s1 = stash_s[pl * kStashRow + lane + 32];
+        const float w0 = a0 * T0, w1 = a1 * T1;
+        X0 -= w0 * dg0;  // F_{k-1} . f_k: the product took F after entry k
+        X1 -= w1 * dg1;
+        const float cgt = own[pl], ccf = own[C::kOwn + pl];
+        const float Send = own[2 * C::kOwn + pl], Swend = own[3 * C::kOwn + pl];
+        // S_k = S of the later chunks + sigma w of the chunk's later entries
+        const float v0 = s0 * w0, v1 = s1 * w1;
+        const float i1 = lane_suffix(v1, lane), i0 = lane_suffix(v0, lane);
+        const float t1 = __shfl_sync(0xffffffffu, i1, 0), t0 = __shfl_sync(0xffffffffu, i0, 0);
+        const float S1 = Send + (i1 - v1), S0 = Send + t1 + (i0 - v0);
+        const float gw0 = cgt * s0 + ccf * (s0 * ((1.f - T0) - X0) + S0 - Y0);
+        const float gw1 = cgt * s1 + ccf * (s1 * ((1.f - T1) - X1) + S1 - Y1);
+        const float u0 = w0 * gw0, u1 = w1 * gw1;
+        const float j1 = lane_suffix(u1, lane), j0 = lane_suffix(u0, lane);
+        const float r1 = __shfl_sync(0xffffffffu, j1, 0), r0 = __shfl_sync(0xffffffffu, j0, 0);
+        const float Sw1 = Swend + (j1 - u1), Sw0 = Swend + r1 + (j0 - u0);
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-        al[k] = stash_a[pl * kStashRow + k0 + k];
-        T[k] = stash_T[pl * kStashRow + k0 + k];
-        sg[k] = stash_s[pl * kStashRow + k0 + k];
-        w[k] = al[k] * T[k];
-        X[k] -= w[k] * diag[k0 + k];  // F_{k-1} . f_k: the product above took F after entry k
-    }
-    const float cgt = own[pl], ccf = own[C::kOwn + pl];
-    // suffix sums of sigma w over the later entries of the chunk
-    float loc = 0.f;
-#pragma unroll
-    for (int k = 0; k < E; ++k) loc += sg[k] * w[k];
-    float incl = loc;  // inclusive suffix over threads sub, sub + 1, ...
-#pragma unroll
-    for (int d = 1; d < TP; d <<= 1) {
-        const float t = __shfl_down_sync(0xffffffffu, incl, d, TP);
-        if (sub + d < TP) incl += t;
-    }
-    const float Send = own[2 * C::kOwn + pl];
-    float Sk = Send + (incl - loc);  // entries after this thread's
-    float gw[E];
-#pragma unroll
-    for (int k = E - 1; k >= 0; --k) {
-        gw[k] = cgt * sg[k] + ccf * (sg[k] * ((1.f - T[k]) - X[k]) + Sk - Y[k]);
-        Sk += sg[k] * w[k];
-    }
-    float loc2 = 0.f;
-#pragma unroll
-    for (int k = 0; k < E; ++k) loc2 += w[k] * gw[k];
-    float incl2 = loc2;
-#pragma unroll
-    for (int d = 1; d < TP; d <<= 1) {
-        const float t = __shfl_down_sync(0xffffffffu, incl2, d, TP);
-        if (sub + d < TP) incl2 += t;
-    }
-    const float Swend = own[3 * C::kOwn + pl];
-    float Sw = Swend + (incl2 - loc2);
-#pragma unroll
-    for (int k = E - 1; k >= 0; --k) {
-        if (w[k] > 0.f && inside) {
-            const float dal = T[k] * gw[k] - Sw / (1.f - al[k]);
-            const int j = k0 + k;
-            const float4 A = R[j].a, B = R[j].b;
+        for (int h = 0; h < 2; ++h) {
+            const float w = h ? w1 : w0;
+            if (!(w > 0.f && inside)) continue;
+            const float al = h ? a1 : a0, T = h ? T1 : T0, gw = h ? gw1 : gw0, Sw = h ? Sw1 : Sw0;
+            const float4 A = h ? A1 : A0, B = h ? B1 : B0;
+            const float dal = T * gw - Sw / (1.f - al);
             const float dx = fpx - A.x, dy = fpy - A.y;
             const float q2 = eval_q2(dx, dy, A.z, A.w, B.x);
             const float G = gauss_q2(q2), rho = B.y * G;
             const float drho = rho > p.amax ? 0.f : dal;
             const float dq2 = -0.5f * rho * drho;
-            atomicAdd(&acc[j * 8 + 0], -(2.f * A.z * dx + 2.f * A.w * dy) * dq2);
-            atomicAdd(&acc[j * 8 + 1], -(2.f * A.w * dx + 2.f * B.x * dy) * dq2);
-            atomicAdd(&acc[j * 8 + 2], dx * dx * dq2);
-            atomicAdd(&acc[j * 8 + 3], 2.f * dx * dy * dq2);
-            atomicAdd(&acc[j * 8 + 4], dy * dy * dq2);
-            atomicAdd(&acc[j * 8 + 5], G * drho);
+            float *g = h ? g1 : g0;
+            g[0] += -(2.f * A.z * dx + 2.f * A.w * dy) * dq2;
+            g[1] += -(2.f * A.w * dx + 2.f * B.x * dy) * dq2;
+            g[2] += dx * dx * dq2;
+            g[3] += 2.f * dx * dy * dq2;
+            g[4] += dy * dy * dq2;
+            g[5] += G * drho;
         }
-        Sw += w[k] * gw[k];
+        if (lane == 0) {  // the chunk's totals carry to the earlier chunks
+            own[2 * C::kOwn + pl] = Send + t1 + t0;
+            own[3 * C::kOwn + pl] = Swend + r1 + r0;
+        }
     }
-    // the chunk's totals carry to the earlier chunks
-    const float tot1 = __shfl_sync(0xffffffffu, incl, (tid & 31) - sub, 32);
-    const float tot2 = __shfl_sync(0xffffffffu, incl2, (tid & 31) - sub, 32);
-    if (sub == 0) {
-        own[2 * C::kOwn + pl] = Send + tot1;
-        own[3 * C::kOwn + pl] = Swend + tot2;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        if (g0[c] != 0.f) atomicAdd(&acc[lane * 8 + c], g0[c]);
+        if (g1[c] != 0.f) atomicAdd(&acc[(lane + 32) * 8 + c], g1[c]);
     }
 }
 
@@ -1102,10 +1095,6 @@ __global__ void __launch_bounds__(256, 1)
     long long pix;
     float fpx, fpy;
     const bool inside = item_pixel(it, pidx, pix, fpx, fpy);
-    long long opix;
-    float ofx, ofy;  // this thread's own pixel in the owner passes
-    const int opl = tid / C::kTpp;
-    const bool oin = item_pixel(it, own0 + opl, opix, ofx, ofy);
 
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
@@ -1277,7 +1266,7 @@ __global__ void __launch_bounds__(256, 1)
             igt[tid] = n2 > 0.f ? 1.f / sqrtf(n2) : 0.f;
         }
         __syncthreads();
-        owner_sigma<C>(S, tid, q, ks, lam, inv, igt, stash_a, stash_T, stash_s, &bars[5]);
+        owner_sigma<C>(S, warp, lane, q, ks, lam, inv, igt, stash_a, stash_T, stash_s, &bars[5]);
         // X's reads of F hi/lo and of -W are done: G_end -> hi/lo, sigma w -> the weight operands
         ok = mbar_wait(&bars[2], ph);
         if (ok) {
@@ -1322,7 +1311,7 @@ __global__ void __launch_bounds__(256, 1)
             if (tid == 0) latch(status, ST_TIMEOUT);
             break;
         }
-        owner_grads<C>(S, tid, p, S.rec(b), ofx, ofy, oin, diag, stash_a, stash_T, stash_s, own, acc);
+        owner_grads<C>(S, warp, lane, p, S.rec(b), it, own0, diag, stash_a, stash_T, stash_s, own, acc);
         __syncthreads();
         if (tid < NC) mbar_arrive_cluster(mapa(smem_u32(&bars[8]), (uint32_t)tid));  // round-3 rows consumed
         if (tid < kC && tid < nb) {  // the own pixels' footprint gradients of the chunk's Gaussians
