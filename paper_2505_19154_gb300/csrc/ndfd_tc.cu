@@ -920,6 +920,7 @@ __device__ __forceinline__ void owner_sigma(const ItemSmem<C> &S, int warp, int 
                                             const float *stash_T, float *stash_s, uint64_t *bar) {
     constexpr int NC = C::kNC;
     const float inv0 = inv[lane], inv1 = inv[lane + 32];
+#pragma unroll
     for (int pl = warp; pl < C::kOwn; pl += 8) {
         float ph0 = 0.f, ph1 = 0.f;
 #pragma unroll
@@ -999,6 +1000,7 @@ __device__ __forceinline__ void owner_grads(const ItemSmem<C> &S, int warp, int 
     const float4 A0 = R[lane].a, B0 = R[lane].b, A1 = R[lane + 32].a, B1 = R[lane + 32].b;
     const float dg0 = diag[lane], dg1 = diag[lane + 32];
     float g0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, g1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
     for (int pl = warp; pl < C::kOwn; pl += 8) {
         long long pix;
         float fpx, fpy;
