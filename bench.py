@@ -1098,7 +1098,8 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
-SURFEL_METRIC = "fwd+bwd Mpix/s at 1M 2DGS surfels, 1080p, D=512 BF16 features, FP32 CUDA-core path"
+SURFEL_METRIC = ("fwd+bwd Mpix/s at 1M 2DGS surfels, 1080p, D=512 BF16 features, tensor-core forward blend, "
+                 "FP32 CUDA-core backward")
 SURFEL_WORKLOAD = ("1M 2DGS surfels (config-3 distributions, s_u, s_v the first two scales), 1920x1080 view, "
                    "SH degree 3, D=512 BF16 features, fwd+bwd")
 
@@ -1185,11 +1186,12 @@ def run_surfel(args):
            for k, (c, tm) in prof.items()}
     fl = algorithmic_flops(args.n, D, Q)
     fpk = fp32_peak(dev, local)
-    for k, base in (("render_fwd_surfel", "render_fwd"), ("render_bwd_surfel", "render_bwd")):
+    fk = "render_fwd_tc_surfel" if "render_fwd_tc_surfel" in per else "render_fwd_surfel"
+    for k, base in ((fk, "render_fwd"), ("render_bwd_surfel", "render_bwd")):
         if k in per:
-            per[k]["fp32_tflops"] = round(fl[base] / (per[k]["ms"] * 1e-3) / 1e12, 2)
-    dom = max(("render_fwd_surfel", "render_bwd_surfel"), key=lambda k: prof.get(k, (0, 0))[1])
-    base = dom.replace("_surfel", "")
+            per[k]["algorithmic_tflops"] = round(fl[base] / (per[k]["ms"] * 1e-3) / 1e12, 2)
+    dom = max((fk, "render_bwd_surfel"), key=lambda k: prof.get(k, (0, 0))[1])
+    base = "render_fwd" if dom == fk else "render_bwd"
     ach = fl[base] / (per[dom]["ms"] * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": fpk["tflops"], "unit": "TFLOP/s",
             "frac": round(ach / fpk["tflops"], 4),

@@ -435,8 +435,6 @@ fhgs_status fhgs_render_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fh
     if (feat && !aligned16(feat)) return fail(ctx, FHGS_ERR_ALIGNMENT, "feat must be 16-byte aligned");
     if (p->path == FHGS_PATH_TC && D > 0 && !use_tc(p, ftype, D))
         return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core path needs BF16 features and a supported D");
-    if (p->geometry == FHGS_GEOM_SURFEL && p->path == FHGS_PATH_TC)
-        return fail(ctx, FHGS_ERR_UNSUPPORTED, "surfels render on the FP32 path");
     CamSet cs;
     if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
     FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -444,7 +442,8 @@ fhgs_status fhgs_render_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fh
     ProjView pv = proj_view(const_cast<void *>(proj), (long long)n * n_cams);
     cudaStream_t st = (cudaStream_t)stream;
     const int Df = feat ? D : 0;
-    if (p->geometry == FHGS_GEOM_SURFEL) {
+    const bool tc = Df > 0 && use_tc(p, ftype, D);
+    if (p->geometry == FHGS_GEOM_SURFEL && !tc) {
         {
             Prof pr(ctx, "render_fwd_surfel", st);
             launch_render_fwd_surfel(n, cs, q, pv, *bins, features, ftype == FHGS_BF16, Df, rgb, feat, T_final, last,
@@ -453,8 +452,8 @@ fhgs_status fhgs_render_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fh
         FHGS_CUDA(ctx, cudaGetLastError());
         return FHGS_OK;
     }
-    const bool tc = Df > 0 && use_tc(p, ftype, D);
-    Prof pr(ctx, tc ? "render_fwd_tc" : "render_fwd_fp32", st);
+    Prof pr(ctx, tc ? (p->geometry == FHGS_GEOM_SURFEL ? "render_fwd_tc_surfel" : "render_fwd_tc") : "render_fwd_fp32",
+            st);
     if (tc)
         launch_render_fwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, D, p->d_split, rgb, feat, T_final,
                              last, ctx->status, st);
@@ -485,7 +484,7 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
     if (p->path == FHGS_PATH_TC && D > 0 && !use_tc(p, ftype, D))
         return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core path needs BF16 features and a supported D");
     if (p->geometry == FHGS_GEOM_SURFEL && p->path == FHGS_PATH_TC)
-        return fail(ctx, FHGS_ERR_UNSUPPORTED, "surfels render on the FP32 path");
+        return fail(ctx, FHGS_ERR_UNSUPPORTED, "the surfel backward runs on the FP32 path (use FHGS_PATH_AUTO)");
     CamSet cs;
     if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
     FHGS_CUDA(ctx, cudaSetDevice(ctx->device));

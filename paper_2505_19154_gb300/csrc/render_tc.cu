@@ -58,13 +58,13 @@ constexpr int kFB = 64;  // Gaussians per forward batch (MMA K)
 // (once the MMA of batch b-1 has freed its stage) the feature rows of batch
 // b+1 are in flight while batch b is weighed.  With one feature stage (DN =
 // 512, two CTAs per SM) batch b's rows load under its own weights.
-template <int DN>
+template <int DN, int GEOM = FHGS_GEOM_EWA>
 struct FwdCfg {
     static constexpr int kWBytes = 128 * 128;            // 128 px x 64 BF16 weights
     static constexpr int kFBytes = kFB * DN * 2;         // 64 rows x DN BF16 features
     static constexpr int kNSub = DN > 256 ? DN / 256 : 1;
     static constexpr int kMmaN = DN > 256 ? 256 : DN;
-    static constexpr int kRecBytes = kFB * 48;
+    static constexpr int kRecBytes = kFB * (GEOM == FHGS_GEOM_SURFEL ? 64 : 48);  // GRec or SRec
     // two feature stages, except at DN = 512 where one keeps the CTA small
     // enough for two per SM (one CTA's epilogue then runs beside the other's
     // batches)
@@ -80,12 +80,45 @@ struct FwdCfg {
     static_assert(8 * 32 * 36 * 4 <= kOffRec, "epilogue tiles must fit in the weight and feature stages");
 };
 
-template <int DN>
+// alpha and colour of one record at a pixel, by the FP32 paths' rules: EWA,
+// q2 <= cutoff on the conic, alpha = min(alpha_max, op 2^(-q2 log2(e) / 2));
+// a 2DGS surfel (Sec. 3.1, Eq. 1-3), u^2 + v^2 <= cutoff at the ray-plane
+// intersection and alpha = min(alpha_max, op exp(-(u^2 + v^2) / 2)) with the
+// exponential of the surfel FP32 render, so that its backward (which reads
+// this forward's T and last contributor) takes the same decisions.
+template <int GEOM>
+struct FwdRec;
+template <>
+struct FwdRec<FHGS_GEOM_EWA> {
+    using T = GRec;
+    __device__ static float alpha(const GRec &r, float fpx, float fpy, const Params &p) {
+        const float dx = fpx - r.a.x, dy = fpy - r.a.y;
+        const float q2 = eval_q2(dx, dy, r.a.z, r.a.w, r.b.x);
+        const float al = fminf(p.amax, r.b.y * gauss_q2(q2));
+        return (q2 <= p.cut && al >= p.amin) ? al : 0.f;
+    }
+    __device__ static float3 rgb(const GRec &r) { return make_float3(r.b.z, r.b.w, r.c.x); }
+};
+template <>
+struct FwdRec<FHGS_GEOM_SURFEL> {
+    using T = SRec;
+    __device__ static float alpha(const SRec &r, float fpx, float fpy, const Params &p) {
+        SurfelHit h;
+        if (!surfel_uv(r.a, r.b, r.c.x, fpx, fpy, p.cut, h)) return 0.f;
+        const float al = fminf(p.amax, r.c.y * __expf(-0.5f * h.r2));
+        return al >= p.amin ? al : 0.f;
+    }
+    __device__ static float3 rgb(const SRec &r) { return make_float3(r.c.z, r.c.w, r.d.x); }
+};
+
+template <int DN, int GEOM = FHGS_GEOM_EWA>
 __global__ void __launch_bounds__(256, 2)
     k_render_fwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                     const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats, int D,
                     float *rgb, float *feat, float *Tout, int32_t *last_out, unsigned *status) {
-    using C = FwdCfg<DN>;
+    using C = FwdCfg<DN, GEOM>;
+    using FR = FwdRec<GEOM>;
+    using Rec = typename FR::T;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
     if (probe_wait_expired(p, sm, status)) return;
@@ -98,7 +131,7 @@ __global__ void __launch_bounds__(256, 2)
     float *xRgb = reinterpret_cast<float *>(xL0 + 128);          // [128][3]
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + C::kOffBar);  // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
-    auto srec = [&](int b) { return reinterpret_cast<GRec *>(sm + C::kOffRec + (b & 1) * C::kRecBytes); };
+    auto srec = [&](int b) { return reinterpret_cast<Rec *>(sm + C::kOffRec + (b & 1) * C::kRecBytes); };
     auto sgid = [&](int b) { return reinterpret_cast<uint32_t *>(sm + C::kOffGid + (b % 3) * kFB * 4); };
 
     const int tid = threadIdx.x, warp = tid >> 5, grp = tid >> 7, pidx = tid & 127;
@@ -113,7 +146,9 @@ __global__ void __launch_bounds__(256, 2)
     const uint32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
     const int nbatches = (int)((e - s + kFB - 1) / kFB);
     const int d0 = chunk * DN;
-    const GRec *rec = pv.rec + (long long)ci * N;
+    const Rec *rec = (GEOM == FHGS_GEOM_SURFEL ? reinterpret_cast<const Rec *>(pv.srec)
+                                              : reinterpret_cast<const Rec *>(pv.rec)) +
+                     (long long)ci * N;
 
     // TMEM is allocated right before the first MMA and released after the
     // epilogue's last read of it: with two CTAs on an SM, one CTA's batches
@@ -144,10 +179,10 @@ __global__ void __launch_bounds__(256, 2)
         if (b < nbatches && tid < kFB) {
             const bool v = s + (uint32_t)b * kFB + tid < e;
             const uint32_t dst = smem_u32(srec(b) + tid);
-            const GRec *src = rec + (v ? sgid(b)[tid] : 0u);
-            cp_async16(dst, &src->a, v);
-            cp_async16(dst + 16, &src->b, v);
-            cp_async16(dst + 32, &src->c, v);
+            const Rec *src = rec + (v ? sgid(b)[tid] : 0u);
+#pragma unroll
+            for (int w4 = 0; w4 < (int)(sizeof(Rec) / 16); ++w4)
+                cp_async16(dst + 16 * w4, reinterpret_cast<const float4 *>(src) + w4, v);
         }
         cp_async_commit();
     };
@@ -198,18 +233,15 @@ __global__ void __launch_bounds__(256, 2)
         const bool done_in = xDone[pidx] != 0;
         const int last_in = xLast[pidx];
         // alphas of this group's 32 Gaussians and the running product of (1 - alpha)
-        const GRec *R = srec(b);
+        const Rec *R = srec(b);
         float a[32], l[32];
         float P = 1.f;
         int lastc = -1;
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
             const int j = grp * 32 + jj;
-            const float4 A4 = R[j].a, B4 = R[j].b;
-            const float dx = fpx - A4.x, dy = fpy - A4.y;
-            const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
-            const float al = fminf(p.amax, B4.y * gauss_q2(q2));
-            a[jj] = (j < nb && q2 <= p.cut && al >= p.amin) ? al : 0.f;
+            const float al = FR::alpha(R[j], fpx, fpy, p);
+            a[jj] = j < nb ? al : 0.f;
             l[jj] = P;
             P *= 1.f - a[jj];
             lastc = a[jj] > 0.f ? jj : lastc;
@@ -259,10 +291,10 @@ __global__ void __launch_bounds__(256, 2)
                 const float w = okj ? a[jj] * Tj : 0.f;
                 w8[h] = w;
                 if (okj) {
-                    const float4 B4 = R[j].b;
-                    cr += w * B4.z;
-                    cg += w * B4.w;
-                    cb += w * R[j].c.x;
+                    const float3 c3 = FR::rgb(R[j]);
+                    cr += w * c3.x;
+                    cg += w * c3.y;
+                    cb += w * c3.z;
                     lastw = jj;
                 }
             }
@@ -1566,10 +1598,17 @@ void launch_render_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
     note_launch(1);
 #define FHGS_FWD(DNV)                                                                                     \
     case DNV: {                                                                                           \
-        static std::atomic<unsigned long long> smem_done{0};                                            \
-        allow_max_smem(smem_done, k_render_fwd_tc<DNV>);                                                \
-        k_render_fwd_tc<DNV><<<grid, 256, FwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, feats, D, \
-                                                                   rgb, feat, T, last, status);          \
+        if (p.geom == FHGS_GEOM_SURFEL) {                                                                 \
+            static std::atomic<unsigned long long> smem_done{0};                                        \
+            allow_max_smem(smem_done, k_render_fwd_tc<DNV, FHGS_GEOM_SURFEL>);                          \
+            k_render_fwd_tc<DNV, FHGS_GEOM_SURFEL><<<grid, 256, FwdCfg<DNV, FHGS_GEOM_SURFEL>::kSmem, st>>>( \
+                N, cs, p, pv, bins.gids, bins.ranges, feats, D, rgb, feat, T, last, status);              \
+        } else {                                                                                          \
+            static std::atomic<unsigned long long> smem_done{0};                                        \
+            allow_max_smem(smem_done, k_render_fwd_tc<DNV>);                                            \
+            k_render_fwd_tc<DNV><<<grid, 256, FwdCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, \
+                                                                       feats, D, rgb, feat, T, last, status); \
+        }                                                                                                 \
         break;                                                                                            \
     }
     switch (dn) {

@@ -144,28 +144,57 @@ def test_surfel_ragged_multicamera_sh3():
     check_grads(got, ref, keys=("means", "scales2", "quats", "opacities", "sh"), tol=1e-3)
 
 
-def test_surfel_bf16_features_and_unsupported_combinations():
-    sc = surfel_scene(600, seed=5, sh_degree=0, D=64)
+def test_surfel_tensor_core_forward_then_fp32_backward():
+    """BF16 features: FHGS_PATH_AUTO renders surfels with the tensor-core
+    feature blend (the same surfel weights, BF16 weights in the blend:
+    features within 1e-2 of max|F|, the EWA tensor-core bar) and takes the FP32
+    backward, which reads the forward's T and last contributor; the gradients
+    keep the FP32 bars.  FHGS_PATH_TC renders too, but its backward and fusion
+    are refused before any launch."""
+    sc = surfel_scene(1500, seed=5, sh_degree=1, D=256, spread=0.45)
     sc["features"] = synth.to_bf16(sc["features"])
-    cams = [synth.look_at_camera(synth.ring_position(2.6, 120, -10), 48, 40)]
-    prm = dict(sh_degree=0)
-    rast = api.Rasterizer(0, sh_degree=0, geometry=api.GEOM_SURFEL)   # AUTO takes the FP32 surfel kernels
+    cams = [synth.look_at_camera(synth.ring_position(2.6, a, e), w, h)
+            for a, e, w, h in [(120, -10, 48, 40), (300, 15, 70, 52)]]
+    prm = dict(sh_degree=1)
+    P = sum(c["width"] * c["height"] for c in cams)
+    dC, dF = synth.upstream(21, P, 256)
+    rast = api.Rasterizer(0, sh_degree=1, geometry=api.GEOM_SURFEL)
     t = {k: _t(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    rast.ctx.profile(True)
     st = rast.prepare(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams)
-    rgb, feat = rast.forward(st, _t(sc["features"], torch.bfloat16))
+    feats = _t(sc["features"], torch.bfloat16)
+    rgb, feat = rast.forward(st, feats)
+    g = rast.backward(st, _t(dC), _t(dF))
     torch.cuda.synchronize()
     assert rast.ctx.sync_status() == api.OK
-    check_surfel_image(dict(rgb=rgb.cpu().numpy(), feat=feat.cpu().numpy(), T=st["T"].cpu().numpy()), sc, cams, prm)
-    # the tensor-core path, fusion and NDFD are EWA-only: refused before any launch
+    prof = rast.ctx.profile_read()
+    assert "render_fwd_tc_surfel" in prof and "render_bwd_surfel" in prof, prof
+    check_surfel_image(dict(rgb=rgb.cpu().numpy(), feat=feat.cpu().numpy(), T=st["T"].cpu().numpy()), sc, cams, prm,
+                       feat_tol=1e-2)
+    ref = surfel_ref_grads(sc, cams, prm, dC, dF)
+    got = {k: (None if v is None else v.cpu().numpy()) for k, v in g.items()}
+    got["scales2"] = got["scales"][:, :2]
+    check_grads(got, ref, keys=("means", "scales2", "quats", "opacities", "sh"), tol=1e-3)
+    check_grads(got, ref, keys=("features",), tol=1e-3)
+    # FHGS_PATH_TC: the forward runs on the tensor cores, the backward and fusion are refused
     rast.set_path(api.PATH_TC)
+    rgb2, feat2 = rast.forward(st, feats)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb2, rgb) and torch.equal(feat2, feat)
     with pytest.raises(api.FhgsError) as e:
-        rast.forward(st, _t(sc["features"], torch.bfloat16))
+        rast.backward(st, _t(dC), _t(dF))
     assert e.value.status == api.ERR_UNSUPPORTED
     rast.set_path(api.PATH_AUTO)
     with pytest.raises(api.FhgsError) as e:
-        rast.fuse(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams,
-                  [torch.ones((48 * 40, 64), device=rgb.device)])
+        rast.fuse(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams[:1],
+                  [torch.ones((48 * 40, 256), device=rgb.device)])
     assert e.value.status == api.ERR_UNSUPPORTED
+    # FHGS_PATH_FP32 renders the surfel image on the CUDA cores (the FP32 bars)
+    rast.set_path(api.PATH_FP32)
+    rgb3, feat3 = rast.forward(st, feats)
+    torch.cuda.synchronize()
+    check_surfel_image(dict(rgb=rgb3.cpu().numpy(), feat=feat3.cpu().numpy(), T=st["T"].cpu().numpy()), sc, cams,
+                       prm)
 
 
 def _surfel_ndfd_case(n, seed, D, cam, bf16):
