@@ -1098,8 +1098,7 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
-SURFEL_METRIC = ("fwd+bwd Mpix/s at 1M 2DGS surfels, 1080p, D=512 BF16 features, tensor-core forward blend, "
-                 "FP32 CUDA-core backward")
+SURFEL_METRIC = "fwd+bwd Mpix/s at 1M 2DGS surfels, 1080p, D=512 BF16 features, BF16-TC path; % of roofline"
 SURFEL_WORKLOAD = ("1M 2DGS surfels (config-3 distributions, s_u, s_v the first two scales), 1920x1080 view, "
                    "SH degree 3, D=512 BF16 features, fwd+bwd")
 
@@ -1187,16 +1186,27 @@ def run_surfel(args):
     fl = algorithmic_flops(args.n, D, Q)
     fpk = fp32_peak(dev, local)
     fk = "render_fwd_tc_surfel" if "render_fwd_tc_surfel" in per else "render_fwd_surfel"
-    for k, base in ((fk, "render_fwd"), ("render_bwd_surfel", "render_bwd")):
+    bk = "render_bwd_tc_surfel" if "render_bwd_tc_surfel" in per else "render_bwd_surfel"
+    by = algorithmic_bytes(P, args.n, D, I, U)
+    pk = load_peaks()
+    for k, base in ((fk, "render_fwd"), (bk, "render_bwd")):
         if k in per:
             per[k]["algorithmic_tflops"] = round(fl[base] / (per[k]["ms"] * 1e-3) / 1e12, 2)
-    dom = max((fk, "render_bwd_surfel"), key=lambda k: prof.get(k, (0, 0))[1])
+            per[k]["bytes"] = by[base]
+            per[k]["hbm_frac"] = round(by[base] / (per[k]["ms"] * 1e-3) / 1e9 / pk["hbm"], 4)
+    dom = max((fk, bk), key=lambda k: prof.get(k, (0, 0))[1])
     base = "render_fwd" if dom == fk else "render_bwd"
-    ach = fl[base] / (per[dom]["ms"] * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": fpk["tflops"], "unit": "TFLOP/s",
-            "frac": round(ach / fpk["tflops"], 4),
-            "peak_source": "of measured FP32 FMA peak (fhgs_ffma_probe, this run)", "traffic": None,
-            "algorithmic_flops": fl[base], "fp32_peak": fpk}
+    if "_tc_" in dom:  # the tensor-core kernels: HBM-bound by the image I/O, as for EWA
+        achb = by[base] / (per[dom]["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achb, 1), "peak": pk["hbm"], "unit": "GB/s",
+                "frac": round(achb / pk["hbm"], 4), "peak_source": f"of {pk['src']} (hbm_gbs)", "traffic": None,
+                "algorithmic_bytes": by[base]}
+    else:
+        ach = fl[base] / (per[dom]["ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": fpk["tflops"], "unit": "TFLOP/s",
+                "frac": round(ach / fpk["tflops"], 4),
+                "peak_source": "of measured FP32 FMA peak (fhgs_ffma_probe, this run)", "traffic": None,
+                "algorithmic_flops": fl[base], "fp32_peak": fpk}
     cpu = None
     if not args.no_cpu_baseline:
         cpu = surfel_cpu_baseline(scene, cams[0], D)

@@ -99,10 +99,10 @@ typedef struct fhgs_params {
  * exp(-(u^2 + v^2)/2) at the point u(x) where the pixel's ray meets the
  * plane; binning follows the binary32 rule of the surfel footprint's
  * dual-conic box.  The surfel model runs fhgs_project, fhgs_bin_sort, the
- * render forward (the tensor-core feature blend for BF16 features and a
- * supported D, else FP32 on the CUDA cores), the FP32 CUDA-core render
- * backward (fhgs_render_bwd with FHGS_PATH_TC is FHGS_ERR_UNSUPPORTED;
- * FHGS_PATH_AUTO takes it) and the NDFD losses with their backward over
+ * render forward and backward (on the tensor cores for BF16 features and a
+ * supported D, as for EWA: the feature blend and its transpose as tcgen05
+ * products, the per-(pixel, surfel) footprint chain on the CUDA cores; else
+ * FP32 on the CUDA cores) and the NDFD losses with their backward over
  * surfel weights (CUDA cores); fusion and the allocation-free backward return
  * FHGS_ERR_UNSUPPORTED. */
 enum { FHGS_GEOM_EWA = 0, FHGS_GEOM_SURFEL = 1 };

@@ -483,8 +483,6 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
         return fail(ctx, FHGS_ERR_ALIGNMENT, "feature gradients must be 16-byte aligned");
     if (p->path == FHGS_PATH_TC && D > 0 && !use_tc(p, ftype, D))
         return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core path needs BF16 features and a supported D");
-    if (p->geometry == FHGS_GEOM_SURFEL && p->path == FHGS_PATH_TC)
-        return fail(ctx, FHGS_ERR_UNSUPPORTED, "the surfel backward runs on the FP32 path (use FHGS_PATH_AUTO)");
     CamSet cs;
     if ((s = make_cams(ctx, cams, n_cams, cs)) != FHGS_OK) return s;
     FHGS_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -498,7 +496,13 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
             FHGS_CUDA(ctx, cudaMemsetAsync(grad_features, 0, sizeof(float) * (size_t)n * D, st));
         const Params q = make_params(p);
         ProjView pv = proj_view(const_cast<void *>(proj), cn);
-        {
+        const bool tc = D > 0 && use_tc(p, ftype, D) && (grad_feat || grad_features);
+        if (tc) {
+            Prof pr(ctx, "render_bwd_tc_surfel", st);
+            if (!launch_render_bwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, D, p->d_split, T_final,
+                                      last, grad_rgb, grad_feat, g2d, grad_features, ctx->status, st))
+                return fail(ctx, FHGS_ERR_CUDA, "could not encode the tensor map of grad_feat");
+        } else {
             Prof pr(ctx, "render_bwd_surfel", st);
             launch_render_bwd_surfel(n, cs, q, pv, *bins, features, ftype == FHGS_BF16, D, T_final, last, grad_rgb,
                                      grad_feat, g2d, D > 0 ? grad_features : nullptr, st);

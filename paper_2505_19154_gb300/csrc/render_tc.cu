@@ -458,8 +458,10 @@ __device__ __forceinline__ void rs_step(float *v, int lane, int off) {
 // Th is followed by Tl (and Dh by Dl): the M=128 MMAs with only 64 real rows
 // (the moments; dFe^T at DN = 64) read their second M block from the next
 // buffer and those rows are unused.
-template <int DN, int kG>
+template <int DN, int kG, int GEOM = FHGS_GEOM_EWA>
 struct BwdCfg {
+    static constexpr bool kSurf = GEOM == FHGS_GEOM_SURFEL;
+    static constexpr int kG2 = kSurf ? kSurfelG2d : 12;  // footprint-gradient floats per (camera, primitive)
     static constexpr int kThreads = 128 * kG;  // kG groups of 4 warps over the half tile's 128 pixels
     static constexpr int kJ = kBB / kG;        // Gaussians per thread and batch
     static constexpr int kRecStages = kG == 2 ? 3 : 2;  // with 2, the drain reads its records from global
@@ -474,7 +476,9 @@ struct BwdCfg {
     static constexpr int kOffRec = kOffF + kNBlk * kBB * 128;
     static constexpr int kRecBytes = kBB * 48;
     static constexpr int kOffGid = kOffRec + kRecStages * kRecBytes;  // record stages: (b-1 for the drain,) b, b+1
-    static constexpr int kOffRgb = kOffGid + 4 * kBB * 4;    // ids of b-1 .. b+2
+    // surfels: the records' a, b, c stages like a GRec, the blue colour (d.x) beside them
+    static constexpr int kOffBlue = kOffGid + 4 * kBB * 4;   // ids of b-1 .. b+2
+    static constexpr int kOffRgb = kOffBlue + (GEOM == FHGS_GEOM_SURFEL ? kRecStages * kBB * 4 : 0);
     static constexpr int kOffFlag = kOffRgb + 2 * kBB * 3 * 4;  // [2 batches][64][3] colour sums
     static constexpr int kOffXch = kOffFlag + 16;  // [2 batches][64 bits] masks; then per pixel: P, S of groups 1.., T, S
     static constexpr int kOffBar = kOffXch + 128 * 4 * (2 * (kG - 1) + 2);
@@ -495,7 +499,7 @@ struct BwdCfg {
 // G_k (S + S_>g) / (1 - alpha_k), with S_>g the sum of w g over the later
 // groups' Gaussians; transmittance needs the later groups' products of
 // (1 - alpha).
-template <int DN, int kG>
+template <int DN, int kG, int GEOM = FHGS_GEOM_EWA>
 __global__ void __launch_bounds__(128 * kG, 1)
     k_render_bwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                     const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats, int D,
@@ -503,7 +507,7 @@ __global__ void __launch_bounds__(128 * kG, 1)
                     const float *__restrict__ grgb, const float *__restrict__ gfeat,
                     const __grid_constant__ CUtensorMap dfm, float *g2d, float *gfeatures, unsigned *status,
                     int n_items) {
-    using C = BwdCfg<DN, kG>;
+    using C = BwdCfg<DN, kG, GEOM>;
     constexpr int kJ = C::kJ;
     if ((int)blockIdx.x >= n_items) return;  // uniform over the CTA
     extern __shared__ uint8_t smem_raw[];
@@ -529,6 +533,12 @@ __global__ void __launch_bounds__(128 * kG, 1)
     // is two items later, past at least one barrier of every thread
     unsigned long long *smax = reinterpret_cast<unsigned long long *>(bars + 5);
     auto srec = [&](int b) { return reinterpret_cast<GRec *>(sm + C::kOffRec + (b % C::kRecStages) * C::kRecBytes); };
+    auto sblue = [&](int b) { return reinterpret_cast<float *>(sm + C::kOffBlue) + (b % C::kRecStages) * kBB; };
+    // surfels: dL/drho of the batch, [64 surfels][128 px] FP32 with the pixel
+    // index XOR (surfel % 32) (conflict-free both ways), in the t buffers;
+    // the footprint-gradient sums of the batch, [64][12], in the X buffer
+    float *sDr = reinterpret_cast<float *>(sTh);
+    float *sGeo = reinterpret_cast<float *>(sX);
     auto sgid = [&](int b) { return reinterpret_cast<uint32_t *>(sm + C::kOffGid + (b & 3) * kBB * 4); };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, grp = tid >> 7, pidx = tid & 127;
@@ -547,14 +557,18 @@ __global__ void __launch_bounds__(128 * kG, 1)
     }
     if (tid < 2 * kBB) sRgb(0)[3 * tid] = sRgb(0)[3 * tid + 1] = sRgb(0)[3 * tid + 2] = 0.f;  // both slots
     if (tid < 4) sMask(0)[tid] = 0u;
-    // pixel-moment rows of X: X[n][p] for p = i + 16 j
-    for (int q = tid; q < 16 * 128; q += C::kThreads) {
-        const int n = q >> 7, pp = q & 127;
-        const float i = (float)(pp & 15), jv = (float)(pp >> 4);
-        const float val = n == 0 ? 1.f : n == 1 ? i : n == 2 ? jv : n == 3 ? i * i : n == 4 ? i * jv
-                                                   : n == 5 ? jv * jv : 0.f;
-        *reinterpret_cast<__nv_bfloat16 *>(sX + (pp >> 6) * (16 * 128) + swz(n, (pp & 63) >> 3) +
-                           2 * (pp & 7)) = __float2bfloat16_rn(val);
+    if constexpr (C::kSurf) {
+        for (int q = tid; q < kBB * 12; q += C::kThreads) sGeo[q] = 0.f;
+    } else {
+        // pixel-moment rows of X: X[n][p] for p = i + 16 j
+        for (int q = tid; q < 16 * 128; q += C::kThreads) {
+            const int n = q >> 7, pp = q & 127;
+            const float i = (float)(pp & 15), jv = (float)(pp >> 4);
+            const float val = n == 0 ? 1.f : n == 1 ? i : n == 2 ? jv : n == 3 ? i * i : n == 4 ? i * jv
+                                                       : n == 5 ? jv * jv : 0.f;
+            *reinterpret_cast<__nv_bfloat16 *>(sX + (pp >> 6) * (16 * 128) + swz(n, (pp & 63) >> 3) +
+                               2 * (pp & 7)) = __float2bfloat16_rn(val);
+        }
     }
     tc_before();
     __syncthreads();
@@ -615,10 +629,12 @@ __global__ void __launch_bounds__(128 * kG, 1)
     // the lo part.  Issued by thread 32 (1 + kFBlk).
     auto issue_M = [&]() {
         tc_after();
+        if constexpr (!C::kSurf) {  // surfels: no moments (the commit arrives at once)
 #pragma unroll
-        for (int ks = 0; ks < 128 / 16; ++ks)
-            mma_bf16(tM, dTh0 + (uint64_t)((ks * 2048) >> 4),
-                     dX0 + (uint64_t)(((ks >> 2) * (16 * 128) + (ks & 3) * 32) >> 4), idM, ks > 0 ? 1u : 0u);
+            for (int ks = 0; ks < 128 / 16; ++ks)
+                mma_bf16(tM, dTh0 + (uint64_t)((ks * 2048) >> 4),
+                         dX0 + (uint64_t)(((ks >> 2) * (16 * 128) + (ks & 3) * 32) >> 4), idM, ks > 0 ? 1u : 0u);
+        }
         mma_commit(&bars[1]);
     };
 
@@ -631,7 +647,8 @@ __global__ void __launch_bounds__(128 * kG, 1)
         // moments: lanes 0..63 hold the T-hi part of Gaussian (lane), read by
         // warps 0 and 1; lanes 64..127 the T-lo part, read by warps 6 and 7.
         // Both add their (linear) share; the colour sums go with the hi part.
-        if ((grp == 0 && q < 2) || (grp == 1 && q >= 2)) {
+        // (Surfels: their footprint and colour sums left with the batch.)
+        if (!C::kSurf && ((grp == 0 && q < 2) || (grp == 1 && q >= 2))) {
             const bool hi = grp == 0;
             const int j = (q & 1) * 32 + lane;
             const uint32_t wmask = sMask(db)[q & 1] & (dnb >= (q & 1) * 32 + 32 ? 0xFFFFFFFFu
@@ -651,12 +668,12 @@ __global__ void __launch_bounds__(128 * kG, 1)
                 const float Sxy = Mij - a * Mj - bb * Mi + a * bb * M0;
                 const float Syy = Mjj - 2.f * bb * Mj + bb * bb * M0;
                 const float op = r.b.y, cA = r.a.z, cB = r.a.w, cC = r.b.x;
-                float4 *dst = reinterpret_cast<float4 *>(dg2dc + 12 * (long long)gid);
+                float4 *dst = reinterpret_cast<float4 *>(dg2dc + C::kG2 * (long long)gid);
                 atomicAdd(dst, make_float4(op * (cA * Sx + cB * Sy), op * (cB * Sx + cC * Sy),
                                            -0.5f * op * Sxx, -op * Sxy));
                 atomicAdd(dst + 1, make_float4(-0.5f * op * Syy, M0, hi && dchunk == 0 ? sRgb(db)[3 * j] : 0.f,
                                                hi && dchunk == 1 % nch ? sRgb(db)[3 * j + 1] : 0.f));
-                if (hi && dchunk == 2 % nch) atomicAdd(dg2dc + 12 * (long long)gid + 8, sRgb(db)[3 * j + 2]);
+                if (hi && dchunk == 2 % nch) atomicAdd(dg2dc + C::kG2 * (long long)gid + 8, sRgb(db)[3 * j + 2]);
             }
         }
         if (want_fg && (DN >= 128 || q < 2)) {
@@ -769,7 +786,8 @@ __global__ void __launch_bounds__(128 * kG, 1)
         const uint32_t s = ranges[2 * ig.tile], e = ranges[2 * ig.tile + 1];
         const int d0 = chunk * DN;
         const GRec *rec = pv.rec + (long long)ci * N;
-        float *g2dc = g2d + (long long)ci * N * 12;
+        const SRec *srecg = C::kSurf ? pv.srec + (long long)ci * N : nullptr;  // surfels
+        float *g2dc = g2d + (long long)ci * N * C::kG2;
         // the next item's pixels 0..63 go to Dl once this item's dF is in TMEM
         bool stageA_next = it + (int)gridDim.x < n_items;
         auto stage_next_A = [&]() {
@@ -832,10 +850,18 @@ __global__ void __launch_bounds__(128 * kG, 1)
             const int be = Lmax - b * kBB, bs = max(0, be - kBB), nb = be - bs;
             if (tid < nb) {
                 const uint32_t dst = smem_u32(srec(b) + tid);
-                const GRec *src = rec + sgid(b)[tid];
-                cp_async16(dst, &src->a, true);
-                cp_async16(dst + 16, &src->b, true);
-                cp_async16(dst + 32, &src->c, true);
+                if constexpr (C::kSurf) {
+                    const SRec *src = srecg + sgid(b)[tid];
+                    cp_async16(dst, &src->a, true);
+                    cp_async16(dst + 16, &src->b, true);
+                    cp_async16(dst + 32, &src->c, true);
+                    cp_async4(smem_u32(sblue(b) + tid), &src->d.x, true);
+                } else {
+                    const GRec *src = rec + sgid(b)[tid];
+                    cp_async16(dst, &src->a, true);
+                    cp_async16(dst + 16, &src->b, true);
+                    cp_async16(dst + 32, &src->c, true);
+                }
             }
         }
         cp_async_commit();
@@ -992,14 +1018,25 @@ __global__ void __launch_bounds__(128 * kG, 1)
             for (int jj = 0; jj < kJ; ++jj) {
                 const int j = grp * kJ + jj;
                 const float4 A4 = R[j].a, B4 = R[j].b;
-                const float dx = fpx - A4.x, dy = fpy - A4.y;
-                const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
-                const float G = gauss_q2(q2);
-                const float rho = B4.y * G;
-                const float aa = fminf(p.amax, rho);
-                const bool ok = (j < jlim) && (q2 <= p.cut) && (aa >= p.amin);
-                al[jj] = ok ? aa : 0.f;
-                gx[jj] = (ok && rho <= p.amax) ? G : 0.f;
+                if constexpr (C::kSurf) {  // the surfel render's hit and exponential
+                    SurfelHit h;
+                    const bool hit = surfel_uv(A4, B4, R[j].c.x, fpx, fpy, p.cut, h);
+                    const float G = __expf(-0.5f * h.r2);
+                    const float rho = R[j].c.y * G;
+                    const float aa = fminf(p.amax, rho);
+                    const bool ok = (j < jlim) && hit && (aa >= p.amin);
+                    al[jj] = ok ? aa : 0.f;
+                    gx[jj] = (ok && rho <= p.amax) ? G : 0.f;
+                } else {
+                    const float dx = fpx - A4.x, dy = fpy - A4.y;
+                    const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
+                    const float G = gauss_q2(q2);
+                    const float rho = B4.y * G;
+                    const float aa = fminf(p.amax, rho);
+                    const bool ok = (j < jlim) && (q2 <= p.cut) && (aa >= p.amin);
+                    al[jj] = ok ? aa : 0.f;
+                    gx[jj] = (ok && rho <= p.amax) ? G : 0.f;
+                }
                 P *= 1.f - al[jj];
             }
             if (grp >= 1) xP[(grp - 1) * 128 + pidx] = P;
@@ -1044,8 +1081,13 @@ __global__ void __launch_bounds__(128 * kG, 1)
                     const float w = al[jj] * Tj[jj];
                     float gc = Gv[jj];
                     if constexpr (decltype(with_colour)::value) {
-                        const float4 B4 = R[j].b;
-                        gc += rC0 * B4.z + rC1 * B4.w + rC2 * R[j].c.x;
+                        if constexpr (C::kSurf) {
+                            const float4 C4 = R[j].c;
+                            gc += rC0 * C4.z + rC1 * C4.w + rC2 * sblue(b)[j];
+                        } else {
+                            const float4 B4 = R[j].b;
+                            gc += rC0 * B4.z + rC1 * B4.w + rC2 * R[j].c.x;
+                        }
                     }
                     const float g = c ? gc : 0.f;
                     const float dal = Tj[jj] * g - __fdividef(Sg, 1.f - al[jj]);
@@ -1113,15 +1155,26 @@ __global__ void __launch_bounds__(128 * kG, 1)
                 for (int h = 0; h < 4; ++h) {
                     const int j0 = 8 * q + 2 * h;
                     pwv[h] = pack_bf16(al[j0] * Tj[j0], al[j0 + 1] * Tj[j0 + 1]);
-                    const __nv_bfloat162 th = __floats2bfloat162_rn(Gv[j0], Gv[j0 + 1]);
-                    const float2 tb = __bfloat1622float2(th);
-                    phv[h] = *reinterpret_cast<const uint32_t *>(&th);
-                    plv[h] = pack_bf16(Gv[j0] - tb.x, Gv[j0 + 1] - tb.y);
+                    if constexpr (!C::kSurf) {
+                        const __nv_bfloat162 th = __floats2bfloat162_rn(Gv[j0], Gv[j0 + 1]);
+                        const float2 tb = __bfloat1622float2(th);
+                        phv[h] = *reinterpret_cast<const uint32_t *>(&th);
+                        plv[h] = pack_bf16(Gv[j0] - tb.x, Gv[j0 + 1] - tb.y);
+                    }
                 }
                 const uint32_t off = swz(pidx, grp * (kJ / 8) + q);
                 *reinterpret_cast<uint4 *>(sW + off) = pw;
-                *reinterpret_cast<uint4 *>(sTh + off) = ph;
-                *reinterpret_cast<uint4 *>(sTl + off) = pl;
+                if constexpr (!C::kSurf) {
+                    *reinterpret_cast<uint4 *>(sTh + off) = ph;
+                    *reinterpret_cast<uint4 *>(sTl + off) = pl;
+                }
+            }
+            if constexpr (C::kSurf) {  // dL/drho = t / G of the unclamped contributors
+#pragma unroll
+                for (int jj = 0; jj < kJ; ++jj) {
+                    const int j = grp * kJ + jj;
+                    sDr[j * 128 + (pidx ^ (j & 31))] = gx[jj] > 0.f ? Gv[jj] / gx[jj] : 0.f;
+                }
             }
             // which Gaussians contribute anywhere in the CTA: one OR per warp
             uint32_t cmask = 0;
@@ -1169,6 +1222,67 @@ __global__ void __launch_bounds__(128 * kG, 1)
             if (kFBlk > 1 && tid == 64) issue_F(1);
             if (tid == 32 * (1 + kFBlk)) issue_M();
             pend1 = true;
+            if constexpr (C::kSurf) {
+                // surfels: footprint gradients d(x_c, y_c, M00, M01, M10, M11, M20,
+                // M21, M22, opacity) of the batch, summed over the half tile's
+                // pixels while the feature-gradient MMAs run.  Thread t takes
+                // surfel t % 64 and pixels [P (t / 64), + P) (P = 128 / threads
+                // per surfel), recomputes the ray-plane hit at each pixel with a
+                // nonzero dL/drho and applies the surfel render backward's chain.
+                constexpr int kTPG = C::kThreads / kBB, kPPT = 128 / kTPG;
+                const int j = tid & (kBB - 1), qq = tid / kBB;
+                if (j < nb) {
+                    const float4 A4 = R[j].a, B4 = R[j].b, C4 = R[j].c;
+                    float ga[10];
+#pragma unroll
+                    for (int c = 0; c < 10; ++c) ga[c] = 0.f;
+#pragma unroll 4
+                    for (int i = 0; i < kPPT; ++i) {
+                        const int pp = qq * kPPT + i;
+                        const float drho = sDr[j * 128 + (pp ^ (j & 31))];
+                        if (drho == 0.f) continue;
+                        SurfelHit h;
+                        surfel_uv(A4, B4, C4.x, (float)(x0 + (pp & 15)) + 0.5f, (float)(y0 + (pp >> 4)) + 0.5f,
+                                  3.4e38f, h);
+                        const float G = __expf(-0.5f * h.r2), rho = C4.y * G;
+                        const float dr2 = -0.5f * rho * drho;
+                        const float du = 2.f * h.u * dr2, dv = 2.f * h.v * dr2;
+                        const float dnu = du * h.iw, dnv = dv * h.iw, dw = -(du * h.u + dv * h.v) * h.iw;
+                        ga[0] -= dnu * A4.z + dnv * B4.x + dw * B4.z;
+                        ga[1] -= dnu * A4.w + dnv * B4.y + dw * B4.w;
+                        ga[2] += dnu * h.dx;
+                        ga[3] += dnu * h.dy;
+                        ga[4] += dnv * h.dx;
+                        ga[5] += dnv * h.dy;
+                        ga[6] += dw * h.dx;
+                        ga[7] += dw * h.dy;
+                        ga[8] += dw;
+                        ga[9] += G * drho;
+                    }
+#pragma unroll
+                    for (int c = 0; c < 10; ++c)
+                        if (ga[c] != 0.f) atomicAdd(&sGeo[j * 12 + c], ga[c]);
+                }
+                __syncthreads();
+                if (tid < nb) {  // one set of vector reductions per surfel of the batch, with its colour sums
+                    float *gs = sGeo + tid * 12;
+                    const float r0 = chunk == 0 ? sRgb(b)[3 * tid] : 0.f;
+                    const float r1 = chunk == 1 % nch ? sRgb(b)[3 * tid + 1] : 0.f;
+                    const float r2 = chunk == 2 % nch ? sRgb(b)[3 * tid + 2] : 0.f;
+                    bool any = r0 != 0.f || r1 != 0.f || r2 != 0.f;
+#pragma unroll
+                    for (int c = 0; c < 10; ++c) any = any || gs[c] != 0.f;
+                    if (any) {
+                        float *dst = g2dc + C::kG2 * (long long)sgid(b)[tid];
+                        atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(gs[0], gs[1], gs[2], gs[3]));
+                        atomicAdd(reinterpret_cast<float4 *>(dst + 4), make_float4(gs[4], gs[5], gs[6], gs[7]));
+                        atomicAdd(reinterpret_cast<float4 *>(dst + 8), make_float4(gs[8], gs[9], r0, r1));
+                        if (r2 != 0.f) atomicAdd(dst + 12, r2);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) gs[c] = 0.f;
+                }
+            }
         }
         if (timeout) break;
         if (nbat > 0) {
@@ -1649,15 +1763,19 @@ bool launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
     const int n_items = cs.total_tiles * 2 * (D / dn);
     const dim3 grid((unsigned)max(1, min(n_items, sm_count_current())));
     note_launch(1);
-#define FHGS_BWD(DNV, GV)                                                                                      \
-    case DNV * 8 + GV: {                                                                                       \
+#define FHGS_BWD_G(DNV, GV, GEO)                                                                               \
+    {                                                                                                          \
         static std::atomic<unsigned long long> smem_done{0};                                                 \
-        allow_max_smem(smem_done, k_render_bwd_tc<DNV, GV>);                                                 \
-        k_render_bwd_tc<DNV, GV><<<grid, BwdCfg<DNV, GV>::kThreads, BwdCfg<DNV, GV>::kSmem, st>>>(            \
+        allow_max_smem(smem_done, k_render_bwd_tc<DNV, GV, GEO>);                                            \
+        k_render_bwd_tc<DNV, GV, GEO><<<grid, BwdCfg<DNV, GV, GEO>::kThreads, BwdCfg<DNV, GV, GEO>::kSmem, st>>>( \
             N, cs, p, pv, bins.gids, bins.ranges, feats, D, T, last, grgb, gfeat, dfm, g2d, gfeatures, status,  \
             n_items);                                                                                          \
-        break;                                                                                                 \
     }
+#define FHGS_BWD(DNV, GV)                                                                                      \
+    case DNV * 8 + GV:                                                                                         \
+        if (p.geom == FHGS_GEOM_SURFEL) FHGS_BWD_G(DNV, 4, FHGS_GEOM_SURFEL) /* kG = 2 has no room */         \
+        else FHGS_BWD_G(DNV, GV, FHGS_GEOM_EWA)                                                                \
+        break;
     switch (dn * 8 + bwd_groups()) {
         FHGS_BWD(64, 2)
         FHGS_BWD(128, 2)
@@ -1668,6 +1786,7 @@ bool launch_render_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjVi
         default: break;
     }
 #undef FHGS_BWD
+#undef FHGS_BWD_G
     return true;
 }
 

@@ -144,13 +144,14 @@ def test_surfel_ragged_multicamera_sh3():
     check_grads(got, ref, keys=("means", "scales2", "quats", "opacities", "sh"), tol=1e-3)
 
 
-def test_surfel_tensor_core_forward_then_fp32_backward():
-    """BF16 features: FHGS_PATH_AUTO renders surfels with the tensor-core
-    feature blend (the same surfel weights, BF16 weights in the blend:
-    features within 1e-2 of max|F|, the EWA tensor-core bar) and takes the FP32
-    backward, which reads the forward's T and last contributor; the gradients
-    keep the FP32 bars.  FHGS_PATH_TC renders too, but its backward and fusion
-    are refused before any launch."""
+def test_surfel_tensor_core_forward_and_backward():
+    """BF16 features: FHGS_PATH_AUTO renders surfels on the tensor cores (the
+    same surfel weights, BF16 weights in the blend: features within 1e-2 of
+    max|F|, the EWA tensor-core bar) and runs the tensor-core backward (the
+    footprint chain per (pixel, surfel) on the CUDA cores): geometry
+    gradients within 1e-3, feature gradients within 1e-2 (BF16 weights), the
+    EWA tensor-core bars.  The FP32 path still renders and differentiates the
+    same scene within the FP32 bars; fusion is refused before any launch."""
     sc = surfel_scene(1500, seed=5, sh_degree=1, D=256, spread=0.45)
     sc["features"] = synth.to_bf16(sc["features"])
     cams = [synth.look_at_camera(synth.ring_position(2.6, a, e), w, h)
@@ -168,33 +169,44 @@ def test_surfel_tensor_core_forward_then_fp32_backward():
     torch.cuda.synchronize()
     assert rast.ctx.sync_status() == api.OK
     prof = rast.ctx.profile_read()
-    assert "render_fwd_tc_surfel" in prof and "render_bwd_surfel" in prof, prof
+    assert "render_fwd_tc_surfel" in prof and "render_bwd_tc_surfel" in prof, prof
     check_surfel_image(dict(rgb=rgb.cpu().numpy(), feat=feat.cpu().numpy(), T=st["T"].cpu().numpy()), sc, cams, prm,
                        feat_tol=1e-2)
     ref = surfel_ref_grads(sc, cams, prm, dC, dF)
     got = {k: (None if v is None else v.cpu().numpy()) for k, v in g.items()}
+    assert np.all(got["scales"][:, 2] == 0.0)
     got["scales2"] = got["scales"][:, :2]
     check_grads(got, ref, keys=("means", "scales2", "quats", "opacities", "sh"), tol=1e-3)
-    check_grads(got, ref, keys=("features",), tol=1e-3)
-    # FHGS_PATH_TC: the forward runs on the tensor cores, the backward and fusion are refused
+    check_grads(got, ref, keys=("features",), tol=1e-2)
+    # the colour-only backward (no feature upstream) on the tensor-core kernel
+    g0 = rast.backward(st, _t(dC), None)
+    ref0 = surfel_ref_grads(sc, cams, prm, dC, None)
+    got0 = {k: (None if v is None else v.cpu().numpy()) for k, v in g0.items()}
+    got0["scales2"] = got0["scales"][:, :2]
+    check_grads(got0, ref0, keys=("means", "scales2", "quats", "opacities", "sh"), tol=1e-3)
+    # FHGS_PATH_TC gives the same forward
     rast.set_path(api.PATH_TC)
     rgb2, feat2 = rast.forward(st, feats)
     torch.cuda.synchronize()
     assert torch.equal(rgb2, rgb) and torch.equal(feat2, feat)
-    with pytest.raises(api.FhgsError) as e:
-        rast.backward(st, _t(dC), _t(dF))
-    assert e.value.status == api.ERR_UNSUPPORTED
     rast.set_path(api.PATH_AUTO)
     with pytest.raises(api.FhgsError) as e:
         rast.fuse(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams[:1],
                   [torch.ones((48 * 40, 256), device=rgb.device)])
     assert e.value.status == api.ERR_UNSUPPORTED
-    # FHGS_PATH_FP32 renders the surfel image on the CUDA cores (the FP32 bars)
+    # FHGS_PATH_FP32 renders and differentiates the surfel scene on the CUDA cores (the FP32 bars)
     rast.set_path(api.PATH_FP32)
+    rast.ctx.profile_read()
     rgb3, feat3 = rast.forward(st, feats)
+    g3 = rast.backward(st, _t(dC), _t(dF))
     torch.cuda.synchronize()
+    prof = rast.ctx.profile_read()
+    assert "render_fwd_surfel" in prof and "render_bwd_surfel" in prof, prof
     check_surfel_image(dict(rgb=rgb3.cpu().numpy(), feat=feat3.cpu().numpy(), T=st["T"].cpu().numpy()), sc, cams,
                        prm)
+    got3 = {k: (None if v is None else v.cpu().numpy()) for k, v in g3.items()}
+    got3["scales2"] = got3["scales"][:, :2]
+    check_grads(got3, ref, keys=("means", "scales2", "quats", "opacities", "sh", "features"), tol=1e-3)
 
 
 def _surfel_ndfd_case(n, seed, D, cam, bf16):
