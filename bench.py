@@ -1162,6 +1162,10 @@ def run_surfel(args):
     torch.cuda.synchronize()
     if rast.ctx.sync_status() != api.OK:
         raise RuntimeError("device status after warm-up")
+    if args.profile_only:
+        step()
+        torch.cuda.synchronize()
+        return
     K = max(1, args.steps)
     rast.ctx.profile(True)
     clocks = ClockSampler(local)

@@ -679,7 +679,7 @@ fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void 
 // The NDFD losses run on the tensor cores unless the FP32 path is asked for
 // or the features are not BF16 with D in {256, 512}.
 static bool ndfd_use_tc(const fhgs_params *p, fhgs_dtype ftype, int D) {
-    return p->path != FHGS_PATH_FP32 && p->geometry == FHGS_GEOM_EWA && ftype == FHGS_BF16 && ndfd_tc_supported(D);
+    return p->path != FHGS_PATH_FP32 && ftype == FHGS_BF16 && ndfd_tc_supported(D, p->geometry);
 }
 
 static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, const fhgs_bins *bins,
@@ -697,7 +697,7 @@ static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, cons
         return fail(ctx, FHGS_ERR_INVALID_ARG, "the activation's slope and threshold must be finite");
     if (p->path == FHGS_PATH_TC && !ndfd_use_tc(p, ftype, D))
         return fail(ctx, FHGS_ERR_UNSUPPORTED,
-                    "tensor-core NDFD needs the EWA geometry and BF16 features with D in {256, 512}");
+                    "tensor-core NDFD needs BF16 features with D in {256, 512} (EWA) or D = 512 (surfels)");
     return FHGS_OK;
 }
 
@@ -717,7 +717,7 @@ fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs
     const Params q = make_params(p);
     ProjView pv = proj_view(const_cast<void *>(proj), n * n_cams);
     if (ndfd_use_tc(p, ftype, D)) {
-        Prof pr(ctx, "ndfd_fwd_tc", st);
+        Prof pr(ctx, p->geometry == FHGS_GEOM_SURFEL ? "ndfd_fwd_tc_surfel" : "ndfd_fwd_tc", st);
         launch_ndfd_fwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, (const __nv_bfloat16 *)feat_gt, D, k,
                            lambda, L_gt, L_cf, n_contrib, ctx->status, st);
     } else {
@@ -754,7 +754,7 @@ fhgs_status fhgs_ndfd_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *pr
     const Params q = make_params(p);
     ProjView pv = proj_view(const_cast<void *>(proj), cn);
     if (ndfd_use_tc(p, ftype, D)) {
-        Prof pr(ctx, "ndfd_bwd_tc", st);
+        Prof pr(ctx, surfel ? "ndfd_bwd_tc_surfel" : "ndfd_bwd_tc", st);
         launch_ndfd_bwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, (const __nv_bfloat16 *)feat_gt, D, k,
                            lambda, grad_Lgt, grad_Lcf, g2d, ctx->status, st);
     } else {

@@ -288,8 +288,9 @@ void launch_ndfd_bwd(long long N, const CamSet &cs, const Params &p, ProjView pv
                      const float *dLcf, float *g2d, cudaStream_t st);
 
 // NDFD on the tensor cores (ndfd_tc.cu): BF16 features and ground truth, D
-// in {256, 512}, split over a cluster of D / 128 CTAs
-bool ndfd_tc_supported(int D);
+// in {256, 512} (EWA) or 512 (surfels), split over a cluster of D / 128 CTAs;
+// g2d has 12 (EWA) or kSurfelG2d (surfel) floats per (camera, primitive)
+bool ndfd_tc_supported(int D, int geom);
 void launch_ndfd_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                         const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam, float *Lgt,
                         float *Lcf, int32_t *nc, unsigned *status, cudaStream_t st);

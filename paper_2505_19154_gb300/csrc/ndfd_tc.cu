@@ -54,9 +54,96 @@ constexpr int cal(int x, int a) { return (x + a - 1) / a * a; }
 
 constexpr int kStashRow = 68;  // floats per own pixel in the weight stash (64 + 4: spreads the banks)
 
-template <int NC>
+// The part of a projected record the NDFD kernels stage, per footprint
+// model: EWA, GRec.a and .b (mean, conic, opacity); 2DGS surfel, SRec.a, .b
+// and .c (centre, M = T'^-1, opacity).  alpha() takes the render's decision
+// at a pixel: EWA q2 <= cutoff and alpha = min(alpha_max, op 2^(-q2 log2(e)/2));
+// surfel u^2 + v^2 <= cutoff at the ray-plane hit and alpha = min(alpha_max,
+// op exp(-(u^2 + v^2)/2)) (the surfel render's exponential).  Both return 0
+// for a primitive that does not count, and G and rho = op G.
+struct __align__(16) RecAB {
+    float4 a, b;
+};
+struct __align__(16) RecABC {
+    float4 a, b, c;
+};
+template <int GEOM>
+struct NRec;
+template <>
+struct NRec<FHGS_GEOM_EWA> {
+    using T = RecAB;
+    using Src = GRec;
+    static constexpr int kG2 = 12;   // footprint-gradient floats per (camera, Gaussian)
+    static constexpr int kAcc = 8;   // shared accumulator row
+    static constexpr int kN = 6;     // d(mean x, y; conic A, B, C; opacity)
+    // adds the footprint gradient of dL/dalpha at a pixel to g[0..5] (the
+    // clamp alpha = alpha_max passes none)
+    __device__ static void footprint(const RecAB &r, float fpx, float fpy, float dal, const Params &p, float *g) {
+        const float4 A = r.a, B = r.b;
+        const float dx = fpx - A.x, dy = fpy - A.y;
+        const float q2 = eval_q2(dx, dy, A.z, A.w, B.x);
+        const float G = gauss_q2(q2), rho = B.y * G;
+        const float drho = rho > p.amax ? 0.f : dal;
+        const float dq2 = -0.5f * rho * drho;
+        g[0] += -(2.f * A.z * dx + 2.f * A.w * dy) * dq2;
+        g[1] += -(2.f * A.w * dx + 2.f * B.x * dy) * dq2;
+        g[2] += dx * dx * dq2;
+        g[3] += 2.f * dx * dy * dq2;
+        g[4] += dy * dy * dq2;
+        g[5] += G * drho;
+    }
+    __device__ static float alpha(const RecAB &r, float fpx, float fpy, const Params &p, float &G, float &rho) {
+        const float dx = fpx - r.a.x, dy = fpy - r.a.y;
+        const float q2 = eval_q2(dx, dy, r.a.z, r.a.w, r.b.x);
+        G = gauss_q2(q2);
+        rho = r.b.y * G;
+        const float al = fminf(p.amax, rho);
+        return (q2 <= p.cut && al >= p.amin) ? al : 0.f;
+    }
+};
+template <>
+struct NRec<FHGS_GEOM_SURFEL> {
+    using T = RecABC;
+    using Src = SRec;
+    static constexpr int kG2 = kSurfelG2d;
+    static constexpr int kAcc = 12;
+    static constexpr int kN = 10;    // d(x_c, y_c, M00, M01, M10, M11, M20, M21, M22, opacity)
+    // the surfel render backward's chain through u, v and w of the ray-plane hit
+    __device__ static void footprint(const RecABC &r, float fpx, float fpy, float dal, const Params &p, float *g) {
+        SurfelHit h;
+        surfel_uv(r.a, r.b, r.c.x, fpx, fpy, 3.4e38f, h);  // a contributor: the ray meets the plane in front
+        const float G = __expf(-0.5f * h.r2), rho = r.c.y * G;
+        const float drho = rho > p.amax ? 0.f : dal;
+        const float dr2 = -0.5f * rho * drho;
+        const float du = 2.f * h.u * dr2, dv = 2.f * h.v * dr2;
+        const float dnu = du * h.iw, dnv = dv * h.iw, dw = -(du * h.u + dv * h.v) * h.iw;
+        g[0] -= dnu * r.a.z + dnv * r.b.x + dw * r.b.z;
+        g[1] -= dnu * r.a.w + dnv * r.b.y + dw * r.b.w;
+        g[2] += dnu * h.dx;
+        g[3] += dnu * h.dy;
+        g[4] += dnv * h.dx;
+        g[5] += dnv * h.dy;
+        g[6] += dw * h.dx;
+        g[7] += dw * h.dy;
+        g[8] += dw;
+        g[9] += G * drho;
+    }
+    __device__ static float alpha(const RecABC &r, float fpx, float fpy, const Params &p, float &G, float &rho) {
+        SurfelHit h;
+        const bool hit = surfel_uv(r.a, r.b, r.c.x, fpx, fpy, p.cut, h);
+        G = __expf(-0.5f * h.r2);
+        rho = r.c.y * G;
+        const float al = fminf(p.amax, rho);
+        return (hit && al >= p.amin) ? al : 0.f;
+    }
+};
+
+template <int NC, int GEOM = FHGS_GEOM_EWA>
 struct NCfg {
     static constexpr int kNC = NC;
+    using Rec = typename NRec<GEOM>::T;
+    using RecSrc = typename NRec<GEOM>::Src;
+    static constexpr int kGeom = GEOM;
     static constexpr int kFStages = 2;       // feature stages (chunk b + 1 loads under chunk b)
     static constexpr int kOwn = 128 / NC;    // pixels whose losses this CTA completes
     static constexpr int kTpp = 256 / kOwn;  // threads per own pixel in the loss pass
@@ -73,8 +160,8 @@ struct NCfg {
     static constexpr int kOffGl = kOffGh + kC * 128;        // lo
     static constexpr int kOffRecv = kOffGl + kC * 128;      // [NC][kSlotF] floats
     static constexpr int kOffStash = kOffRecv + cal(NC * kSlotF * 4, 16);  // [kOwn][kStashRow] w, then T
-    static constexpr int kOffRec = kOffStash + 2 * kOwn * kStashRow * 4;  // [2 stages][64] (a, b) records
-    static constexpr int kOffGid = kOffRec + 2 * kC * 32;          // [3][64] ids
+    static constexpr int kOffRec = kOffStash + 2 * kOwn * kStashRow * 4;  // [2 stages][64] staged records
+    static constexpr int kOffGid = kOffRec + 2 * kC * (int)sizeof(Rec);  // [3][64] ids
     static constexpr int kOffPix = kOffGid + 3 * kC * 4;           // per pixel: T, done, last, P0, L0, |f_gt|^2
     static constexpr int kOffDiag = kOffPix + 6 * 128 * 4;         // [64] Gram diagonal of the chunk
     static constexpr int kOffAcc = kOffDiag + kC * 4;              // [3][kOwn] L_gt, L_cf, count of own pixels
@@ -131,9 +218,6 @@ __device__ __forceinline__ bool item_pixel(const Item &it, int pidx, long long &
 }
 
 
-struct __align__(16) RecAB {
-    float4 a, b;  // GRec.a, GRec.b: mean, conic, opacity
-};
 
 // Per-pixel walk state in shared memory (one entry per pixel of the half tile).
 struct PixState {
@@ -157,7 +241,9 @@ struct PixState {
 // operands, and w and T (before the entry) of the pixels [own0, own0 + own)
 // into the stash.  Returns, uniformly over the CTA, whether every pixel has
 // stopped after the chunk.
-__device__ __forceinline__ bool chunk_weights(const Params &p, const RecAB *R, int nb, int pos0, int pidx, int grp,
+template <int GEOM>
+__device__ __forceinline__ bool chunk_weights(const Params &p, const typename NRec<GEOM>::T *R, int nb, int pos0,
+                                              int pidx, int grp,
                                               float fpx, float fpy, PixState ps, uint8_t *sWh, uint8_t *sWl,
                                               float *stash_w, float *stash_T, int own0, int own, bool neg) {
     const float T_in = ps.T[pidx];
@@ -169,11 +255,9 @@ __device__ __forceinline__ bool chunk_weights(const Params &p, const RecAB *R, i
 #pragma unroll
     for (int jj = 0; jj < 32; ++jj) {
         const int j = grp * 32 + jj;
-        const float4 A4 = R[j].a, B4 = R[j].b;
-        const float dx = fpx - A4.x, dy = fpy - A4.y;
-        const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
-        const float al = fminf(p.amax, B4.y * gauss_q2(q2));
-        a[jj] = (j < nb && q2 <= p.cut && al >= p.amin) ? al : 0.f;
+        float G, rho;
+        const float al = NRec<GEOM>::alpha(R[j], fpx, fpy, p, G, rho);
+        a[jj] = j < nb ? al : 0.f;
         l[jj] = P;
         P *= 1.f - a[jj];
         lastc = a[jj] > 0.f ? jj : lastc;
@@ -314,7 +398,9 @@ template <class C>
 struct ItemSmem {
     uint8_t *sm;
     uint32_t sm_s;
-    __device__ RecAB *rec(int b) const { return reinterpret_cast<RecAB *>(sm + C::kOffRec + (b & 1) * kC * 32); }
+    __device__ typename C::Rec *rec(int b) const {
+        return reinterpret_cast<typename C::Rec *>(sm + C::kOffRec + (b & 1) * kC * (int)sizeof(typename C::Rec));
+    }
     __device__ uint32_t *gid(int b) const {
         return reinterpret_cast<uint32_t *>(sm + C::kOffGid + ((b % 3 + 3) % 3) * kC * 4);
     }
@@ -344,7 +430,7 @@ struct Loader {
     static constexpr int NC = C::kNC;
     const ItemSmem<C> &S;
     const uint32_t *gids;
-    const GRec *rec;
+    const typename C::RecSrc *rec;
     const __nv_bfloat16 *feats;
     uint32_t s, e;
     int nchunks, q, tid;
@@ -359,9 +445,9 @@ struct Loader {
         if (b >= 0 && b < nchunks && tid < kC) {
             const bool v = s + (uint32_t)b * kC + tid < e;
             const uint32_t dst = smem_u32(S.rec(b) + tid);
-            const GRec *src = rec + (v ? S.gid(b)[tid] : 0u);
-            cp_async16(dst, &src->a, v);
-            cp_async16(dst + 16, &src->b, v);
+            const float4 *src = reinterpret_cast<const float4 *>(rec + (v ? S.gid(b)[tid] : 0u));
+#pragma unroll
+            for (int w4 = 0; w4 < (int)(sizeof(typename C::Rec) / 16); ++w4) cp_async16(dst + 16 * w4, src + w4, v);
         }
         cp_async_commit();
     }
@@ -597,13 +683,13 @@ __device__ __forceinline__ void own_losses(const ItemSmem<C> &S, int tid, float 
     }
 }
 
-template <int NC>
+template <int NC, int GEOM>
 __global__ void __launch_bounds__(256, 1)
     k_ndfd_fwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                   const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats,
                   const __nv_bfloat16 *__restrict__ fgt, float ks, float lam, float *Lgt_out, float *Lcf_out,
                   int32_t *nc_out, unsigned *status) {
-    using C = NCfg<NC>;
+    using C = NCfg<NC, GEOM>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
     if (probe_wait_expired(p, sm, status)) return;  // uniform over the grid, before any cluster operation
@@ -639,7 +725,11 @@ __global__ void __launch_bounds__(256, 1)
         ps.last[pidx] = 0;
     }
     if (tid < C::kOwn) S.acc(0)[tid] = S.acc(1)[tid] = S.acc(2)[tid] = 0.f;
-    const Loader<C> L{S, gids, pv.rec + (long long)it.ci * N, feats, it.s, it.e, nchunks, q, tid};
+    const typename C::RecSrc *recs =
+        reinterpret_cast<const typename C::RecSrc *>(GEOM == FHGS_GEOM_SURFEL ? (const void *)pv.srec
+                                                                             : (const void *)pv.rec) +
+        (long long)it.ci * N;
+    const Loader<C> L{S, gids, recs, feats, it.s, it.e, nchunks, q, tid};
     load_gt<C>(S, it, fgt, q, tid);
     L.gid(0);
     L.gid(1);
@@ -671,8 +761,9 @@ __global__ void __launch_bounds__(256, 1)
         L.gid(b + 2);
         L.records(b + 1);
         L.features(b + 1);  // its stage was last read by the MMAs of chunk b-1, complete
-        const bool all_done = chunk_weights(p, S.rec(b), nb, (int)(base - it.s), pidx, grp, fpx, fpy, ps, sm + C::kOffWh,
-                                            sm + C::kOffWl, S.stash_w(), S.stash_T(), own0, C::kOwn, false);
+        const bool all_done = chunk_weights<GEOM>(p, S.rec(b), nb, (int)(base - it.s), pidx, grp, fpx, fpy, ps,
+                                                  sm + C::kOffWh, sm + C::kOffWl, S.stash_w(), S.stash_T(), own0,
+                                                  C::kOwn, false);
         if (b > 0) split_to_tmem(taddr, C::kColF, C::kColFh, C::kColFl, warp);  // F after chunk b-1
         fence_async_smem();
         tc_before();
@@ -767,9 +858,13 @@ __global__ void __launch_bounds__(256, 1)
 // (round 3), which runs the recursion for its pixels and adds their
 // footprint gradients to the per-(camera, Gaussian) array.
 
-template <int NC>
+template <int NC, int GEOM = FHGS_GEOM_EWA>
 struct NBCfg {
     static constexpr int kNC = NC;
+    using Rec = typename NRec<GEOM>::T;
+    using RecSrc = typename NRec<GEOM>::Src;
+    static constexpr int kGeom = GEOM;
+    static constexpr int kG2 = NRec<GEOM>::kG2, kAcc = NRec<GEOM>::kAcc;
     static constexpr int kOwn = 128 / NC;  // the owner passes: warp w takes own pixels w, w + 8, ...
     static constexpr int kRow = 2 * kC + 4;
     static constexpr int kSlotF = kOwn * kRow + kC + kOwn;   // rows; Gram diagonal [64]; partial |f_gt|^2
@@ -783,12 +878,12 @@ struct NBCfg {
     static constexpr int kOffRecv = kOffGl + kC * 128;
     static constexpr int kOffStash = kOffRecv + cal(NC * kSlotF * 4, 16);  // [3][kOwn][kStashRow]: alpha, T, sigma
     static constexpr int kOffRec = kOffStash + 3 * kOwn * kStashRow * 4;
-    static constexpr int kOffGid = kOffRec + 2 * kC * 32;
+    static constexpr int kOffGid = kOffRec + 2 * kC * (int)sizeof(Rec);
     // [9][128]: T, done, last, P0, L0, |f_gt|^2 per pixel, then 5 x kOwn scalars of the own pixels
     static constexpr int kOffPix = kOffGid + 3 * kC * 4;
     static constexpr int kOffDiag = kOffPix + 9 * 128 * 4;  // [2][64]: full Gram diagonal, inverse norms
-    static constexpr int kOffAcc = kOffDiag + 2 * kC * 4;   // [64][8] footprint gradients of the own pixels
-    static constexpr int kOffBar = cal(kOffAcc + kC * 8 * 4, 8);
+    static constexpr int kOffAcc = kOffDiag + 2 * kC * 4;   // [64][kAcc] footprint gradients of the own pixels
+    static constexpr int kOffBar = cal(kOffAcc + kC * kAcc * 4, 8);
     static constexpr int kSmem = 1024 + kOffBar + 128;      // 11 barriers, the TMEM slot, Lmax
     static_assert(kSmem <= 232448, "NDFD backward CTA exceeds the opt-in shared memory");
     static constexpr uint32_t kColF = 0, kColG = 128, kColA = 256, kColB = 320, kColH = 384, kColL = 448;
@@ -802,7 +897,9 @@ struct NBCfg {
 // running product gives T before each entry.  Writes -w (BF16 hi + lo) into
 // the K-major weight operand, alpha and T of the own pixels into the stash,
 // and T entering the chunk back into the state.
-__device__ __forceinline__ void chunk_weights_bwd(const Params &p, const RecAB *R, int nb, int pos0, int pidx, int grp,
+template <int GEOM>
+__device__ __forceinline__ void chunk_weights_bwd(const Params &p, const typename NRec<GEOM>::T *R, int nb, int pos0,
+                                                  int pidx, int grp,
                                                   float fpx, float fpy, PixState ps, uint8_t *sWh, uint8_t *sWl,
                                                   float *stash_a, float *stash_T, int own0, int own) {
     const float T_end = ps.T[pidx];
@@ -812,11 +909,9 @@ __device__ __forceinline__ void chunk_weights_bwd(const Params &p, const RecAB *
 #pragma unroll
     for (int jj = 0; jj < 32; ++jj) {
         const int j = grp * 32 + jj;
-        const float4 A4 = R[j].a, B4 = R[j].b;
-        const float dx = fpx - A4.x, dy = fpy - A4.y;
-        const float q2 = eval_q2(dx, dy, A4.z, A4.w, B4.x);
-        const float al = fminf(p.amax, B4.y * gauss_q2(q2));
-        a[jj] = (j < nb && pos0 + j < last && q2 <= p.cut && al >= p.amin) ? al : 0.f;
+        float G, rho;
+        const float al = NRec<GEOM>::alpha(R[j], fpx, fpy, p, G, rho);
+        a[jj] = (j < nb && pos0 + j < last) ? al : 0.f;
         l[jj] = P;
         P *= 1.f - a[jj];
     }
@@ -993,13 +1088,17 @@ __device__ __forceinline__ float lane_suffix(float x, int lane) {
 // acc[entry][0..5].  own holds per own pixel: c_gt, c_cf, and S and Sw of the
 // later chunks (updated).
 template <class C>
-__device__ __forceinline__ void owner_grads(const ItemSmem<C> &S, int warp, int lane, const Params &p, const RecAB *R,
-                                            const Item &it, int own0, const float *diag, const float *stash_a,
-                                            const float *stash_T, const float *stash_s, float *own, float *acc) {
+__device__ __forceinline__ void owner_grads(const ItemSmem<C> &S, int warp, int lane, const Params &p,
+                                            const typename C::Rec *R, const Item &it, int own0, const float *diag,
+                                            const float *stash_a, const float *stash_T, const float *stash_s,
+                                            float *own, float *acc) {
     constexpr int NC = C::kNC;
-    const float4 A0 = R[lane].a, B0 = R[lane].b, A1 = R[lane + 32].a, B1 = R[lane + 32].b;
+    using NR = NRec<C::kGeom>;
+    const typename C::Rec rec0 = R[lane], rec1 = R[lane + 32];
     const float dg0 = diag[lane], dg1 = diag[lane + 32];
-    float g0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, g1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float g0[NR::kN], g1[NR::kN];
+#pragma unroll
+    for (int c = 0; c < NR::kN; ++c) g0[c] = g1[c] = 0.f;
 #pragma unroll 2
     for (int pl = warp; pl < C::kOwn; pl += 8) {
         long long pix;
@@ -1038,20 +1137,9 @@ __device__ __forceinline__ void owner_grads(const ItemSmem<C> &S, int warp, int 
             const float w = h ? w1 : w0;
             if (!(w > 0.f && inside)) continue;
             const float al = h ? a1 : a0, T = h ? T1 : T0, gw = h ? gw1 : gw0, Sw = h ? Sw1 : Sw0;
-            const float4 A = h ? A1 : A0, B = h ? B1 : B0;
             const float dal = T * gw - Sw / (1.f - al);
-            const float dx = fpx - A.x, dy = fpy - A.y;
-            const float q2 = eval_q2(dx, dy, A.z, A.w, B.x);
-            const float G = gauss_q2(q2), rho = B.y * G;
-            const float drho = rho > p.amax ? 0.f : dal;
-            const float dq2 = -0.5f * rho * drho;
-            float *g = h ? g1 : g0;
-            g[0] += -(2.f * A.z * dx + 2.f * A.w * dy) * dq2;
-            g[1] += -(2.f * A.w * dx + 2.f * B.x * dy) * dq2;
-            g[2] += dx * dx * dq2;
-            g[3] += 2.f * dx * dy * dq2;
-            g[4] += dy * dy * dq2;
-            g[5] += G * drho;
+            if (h) NR::footprint(rec1, fpx, fpy, dal, p, g1);
+            else NR::footprint(rec0, fpx, fpy, dal, p, g0);
         }
         if (lane == 0) {  // the chunk's totals carry to the earlier chunks
             own[2 * C::kOwn + pl] = Send + t1 + t0;
@@ -1059,19 +1147,19 @@ __device__ __forceinline__ void owner_grads(const ItemSmem<C> &S, int warp, int 
         }
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        if (g0[c] != 0.f) atomicAdd(&acc[lane * 8 + c], g0[c]);
-        if (g1[c] != 0.f) atomicAdd(&acc[(lane + 32) * 8 + c], g1[c]);
+    for (int c = 0; c < NR::kN; ++c) {
+        if (g0[c] != 0.f) atomicAdd(&acc[lane * NR::kAcc + c], g0[c]);
+        if (g1[c] != 0.f) atomicAdd(&acc[(lane + 32) * NR::kAcc + c], g1[c]);
     }
 }
 
-template <int NC>
+template <int NC, int GEOM>
 __global__ void __launch_bounds__(256, 1)
     k_ndfd_bwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                   const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats,
                   const __nv_bfloat16 *__restrict__ fgt, float ks, float lam, const float *__restrict__ dLgt,
                   const float *__restrict__ dLcf, float *g2d, unsigned *status) {
-    using C = NBCfg<NC>;
+    using C = NBCfg<NC, GEOM>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
     if (probe_wait_expired(p, sm, status)) return;  // uniform over the grid, before any cluster operation
@@ -1122,9 +1210,13 @@ __global__ void __launch_bounds__(256, 1)
         own[C::kOwn + tid] = in ? dLcf[op] : 0.f;
         own[2 * C::kOwn + tid] = own[3 * C::kOwn + tid] = 0.f;
     }
-    for (int i = tid; i < kC * 8; i += 256) acc[i] = 0.f;
-    const Loader<C> L{S, gids, pv.rec + (long long)it.ci * N, feats, it.s, it.e, nlist, q, tid};
-    float *g2dc = g2d + (long long)it.ci * N * 12;
+    for (int i = tid; i < kC * C::kAcc; i += 256) acc[i] = 0.f;
+    const typename C::RecSrc *recs =
+        reinterpret_cast<const typename C::RecSrc *>(GEOM == FHGS_GEOM_SURFEL ? (const void *)pv.srec
+                                                                             : (const void *)pv.rec) +
+        (long long)it.ci * N;
+    const Loader<C> L{S, gids, recs, feats, it.s, it.e, nlist, q, tid};
+    float *g2dc = g2d + (long long)it.ci * N * C::kG2;
     load_gt<C>(S, it, fgt, q, tid);
     L.gid(0);
     L.gid(1);
@@ -1158,8 +1250,9 @@ __global__ void __launch_bounds__(256, 1)
         __syncthreads();
         L.gid(b + 2);
         L.records(b + 1);
-        const bool all_done = chunk_weights(p, S.rec(b), nb, (int)(base - it.s), pidx, grp, fpx, fpy, ps, sm + C::kOffWh,
-                                            sm + C::kOffWl, stash_a, stash_T, own0, C::kOwn, false);
+        const bool all_done = chunk_weights<GEOM>(p, S.rec(b), nb, (int)(base - it.s), pidx, grp, fpx, fpy, ps,
+                                                  sm + C::kOffWh, sm + C::kOffWl, stash_a, stash_T, own0, C::kOwn,
+                                                  false);
         cp_async_wait<2>();  // the features of b
         fence_async_smem();
         tc_before();
@@ -1206,8 +1299,8 @@ __global__ void __launch_bounds__(256, 1)
         __syncthreads();
         L.gid(b - 2);
         L.records(b - 1);
-        chunk_weights_bwd(p, S.rec(b), nb, (int)(base - it.s), pidx, grp, fpx, fpy, ps, sm + C::kOffWh, sm + C::kOffWl,
-                          stash_a, stash_T, own0, C::kOwn);
+        chunk_weights_bwd<GEOM>(p, S.rec(b), nb, (int)(base - it.s), pidx, grp, fpx, fpy, ps, sm + C::kOffWh,
+                                sm + C::kOffWl, stash_a, stash_T, own0, C::kOwn);
         split_to_tmem(taddr, C::kColF, C::kColH, C::kColL, warp);  // F_end
         cp_async_wait<2>();  // the features of b (the records of b-1 and ids of b-2 may be in flight)
         fence_async_smem();
@@ -1316,16 +1409,22 @@ __global__ void __launch_bounds__(256, 1)
         owner_grads<C>(S, warp, lane, p, S.rec(b), it, own0, diag, stash_a, stash_T, stash_s, own, acc);
         __syncthreads();
         if (tid < NC) mbar_arrive_cluster(mapa(smem_u32(&bars[8]), (uint32_t)tid));  // round-3 rows consumed
-        if (tid < kC && tid < nb) {  // the own pixels' footprint gradients of the chunk's Gaussians
-            const float4 u = *reinterpret_cast<const float4 *>(acc + tid * 8);
-            const float2 t = *reinterpret_cast<const float2 *>(acc + tid * 8 + 4);
-            if (u.x != 0.f || u.y != 0.f || u.z != 0.f || u.w != 0.f || t.x != 0.f || t.y != 0.f) {
-                float *dst = g2dc + 12 * (long long)S.gid(b)[tid];
-                atomicAdd(reinterpret_cast<float4 *>(dst), u);
-                atomicAdd(reinterpret_cast<float2 *>(dst + 4), t);
+        if (tid < kC && tid < nb) {  // the own pixels' footprint gradients of the chunk's primitives
+            float *a = acc + tid * C::kAcc;
+            float *dst = g2dc + C::kG2 * (long long)S.gid(b)[tid];
+#pragma unroll
+            for (int k = 0; k < NRec<GEOM>::kN; k += 4) {
+                if (k + 4 <= NRec<GEOM>::kN) {
+                    const float4 u = *reinterpret_cast<const float4 *>(a + k);
+                    if (u.x != 0.f || u.y != 0.f || u.z != 0.f || u.w != 0.f)
+                        atomicAdd(reinterpret_cast<float4 *>(dst + k), u);
+                    *reinterpret_cast<float4 *>(a + k) = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    const float2 t = *reinterpret_cast<const float2 *>(a + k);
+                    if (t.x != 0.f || t.y != 0.f) atomicAdd(reinterpret_cast<float2 *>(dst + k), t);
+                    *reinterpret_cast<float2 *>(a + k) = make_float2(0.f, 0.f);
+                }
             }
-            *reinterpret_cast<float4 *>(acc + tid * 8) = make_float4(0.f, 0.f, 0.f, 0.f);
-            *reinterpret_cast<float2 *>(acc + tid * 8 + 4) = make_float2(0.f, 0.f);
         }
     }
     cp_async_wait_all();
@@ -1355,46 +1454,60 @@ void launch_cluster(void (*kernel)(Args...), int smem, unsigned n_items, cudaStr
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <int NC>
+template <int NC, int GEOM>
 void launch_fwd_tc_t(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                      const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, float ks, float lam, float *Lgt,
                      float *Lcf, int32_t *nc, unsigned *status, cudaStream_t st) {
     static std::atomic<unsigned long long> smem_set{0};
-    allow_max_smem(smem_set, k_ndfd_fwd_tc<NC>);
-    launch_cluster<NC>(k_ndfd_fwd_tc<NC>, NCfg<NC>::kSmem, (unsigned)cs.total_tiles * 2u, st, N, cs, p, pv,
+    allow_max_smem(smem_set, k_ndfd_fwd_tc<NC, GEOM>);
+    launch_cluster<NC>(k_ndfd_fwd_tc<NC, GEOM>, NCfg<NC, GEOM>::kSmem, (unsigned)cs.total_tiles * 2u, st, N, cs, p, pv,
                        (const uint32_t *)bins.gids, (const uint32_t *)bins.ranges, feats, fgt, ks, lam, Lgt, Lcf, nc,
                        status);
 }
 
-template <int NC>
+template <int NC, int GEOM>
 void launch_bwd_tc_t(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                      const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, float ks, float lam, const float *dLgt,
                      const float *dLcf, float *g2d, unsigned *status, cudaStream_t st) {
     static std::atomic<unsigned long long> smem_set{0};
-    allow_max_smem(smem_set, k_ndfd_bwd_tc<NC>);
-    launch_cluster<NC>(k_ndfd_bwd_tc<NC>, NBCfg<NC>::kSmem, (unsigned)cs.total_tiles * 2u, st, N, cs, p, pv,
+    allow_max_smem(smem_set, k_ndfd_bwd_tc<NC, GEOM>);
+    launch_cluster<NC>(k_ndfd_bwd_tc<NC, GEOM>, NBCfg<NC, GEOM>::kSmem, (unsigned)cs.total_tiles * 2u, st, N, cs, p, pv,
                        (const uint32_t *)bins.gids, (const uint32_t *)bins.ranges, feats, fgt, ks, lam, dLgt, dLcf,
                        g2d, status);
 }
 
 }  // namespace
 
-bool ndfd_tc_supported(int D) { return D == 256 || D == 512; }
+bool ndfd_tc_supported(int D, int geom) {
+    return geom == FHGS_GEOM_SURFEL ? D == 512 : (D == 256 || D == 512);  // surfels: the 4-CTA layout only fits
+}
 
 void launch_ndfd_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                         const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam,
                         const float *dLgt, const float *dLcf, float *g2d, unsigned *status, cudaStream_t st) {
     if (cs.total_tiles == 0) return;
-    if (D == 512) launch_bwd_tc_t<4>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, status, st);
-    else if (D == 256) launch_bwd_tc_t<2>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, status, st);
+    if (p.geom == FHGS_GEOM_SURFEL) {
+        if (D == 512)
+            launch_bwd_tc_t<4, FHGS_GEOM_SURFEL>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, status, st);
+    } else if (D == 512) {
+        launch_bwd_tc_t<4, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, status, st);
+    } else if (D == 256) {
+        launch_bwd_tc_t<2, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, status, st);
+    }
 }
 
 void launch_ndfd_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                         const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam, float *Lgt,
                         float *Lcf, int32_t *nc, unsigned *status, cudaStream_t st) {
     if (cs.total_tiles == 0) return;
-    if (D == 512) launch_fwd_tc_t<4>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, status, st);
-    else if (D == 256) launch_fwd_tc_t<2>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, status, st);
+    if (p.geom == FHGS_GEOM_SURFEL) {
+        if (D == 512)
+            launch_fwd_tc_t<4, FHGS_GEOM_SURFEL>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, status, st);
+    } else if (D == 512) {
+        launch_fwd_tc_t<4, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, status, st);
+    } else if (D == 256) {
+        launch_fwd_tc_t<2, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, status, st);
+    }
 }
 
 }  // namespace fhgs

@@ -242,11 +242,15 @@ def test_surfel_ndfd_losses_and_gradients(D, bf16):
     torch.cuda.synchronize()
     assert rast.ctx.sync_status() == api.OK
     prof = rast.ctx.profile_read()
-    assert "ndfd_fwd_surfel" in prof and "ndfd_bwd_surfel" in prof, prof
-    with pytest.raises(api.FhgsError) as e:   # the tensor-core NDFD is EWA-only: refused before any launch
-        rast.set_path(api.PATH_TC)
-        rast.ndfd_forward(st, feats, gt)
-    assert e.value.status == api.ERR_UNSUPPORTED
+    tc = bf16 and D == 512   # surfels take the tensor-core NDFD kernels at D = 512 (the 4-CTA layout)
+    sfx = "_tc_surfel" if tc else "_surfel"
+    assert "ndfd_fwd" + sfx in prof and "ndfd_bwd" + sfx in prof, prof
+    if not tc:   # FHGS_PATH_TC is refused before any launch where the tensor-core kernels do not apply
+        with pytest.raises(api.FhgsError) as e:
+            rast.set_path(api.PATH_TC)
+            rast.ndfd_forward(st, feats, gt)
+        assert e.value.status == api.ERR_UNSUPPORTED
+        rast.set_path(api.PATH_AUTO)
     ref = oracle.ndfd_2dgs(sc, cam, prm, f, fg)
     ok = oracle.surfel_forward(sc, cam, prm)["margin"].reshape(-1) > MARGIN_TOL
     check_margin_count(int((~ok).sum()), P, "surfel NDFD")
