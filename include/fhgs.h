@@ -344,8 +344,9 @@ fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void 
  * FHGS_ERR_UNSUPPORTED.  A wait of the tensor-core kernel that runs out
  * latches FHGS_ERR_TIMEOUT (read by fhgs_sync_status).  With
  * p->geometry = FHGS_GEOM_SURFEL the weights are the 2DGS surfel render's
- * (the ray-plane solve of Sec. 3.1, the paper's own combination) and the
- * products run on the CUDA cores (FHGS_PATH_TC is FHGS_ERR_UNSUPPORTED). */
+ * (the ray-plane solve of Sec. 3.1, the paper's own combination); the
+ * tensor-core kernels then take BF16 features at D = 512 only (FHGS_PATH_TC
+ * with any other D is FHGS_ERR_UNSUPPORTED). */
 fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_bins *bins, const void *features,
                           const void *feat_gt, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
                           const fhgs_params *p, float k, float lambda, float *L_gt, float *L_cf, int32_t *n_contrib,
