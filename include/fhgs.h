@@ -103,7 +103,8 @@ typedef struct fhgs_params {
  * supported D, as for EWA: the feature blend and its transpose as tcgen05
  * products, the per-(pixel, surfel) footprint chain on the CUDA cores; else
  * FP32 on the CUDA cores) and the NDFD losses with their backward over
- * surfel weights (CUDA cores); fusion and the allocation-free backward return
+ * surfel weights (on the tensor cores for BF16 features at D = 512, else the
+ * CUDA cores); fusion and the allocation-free backward return
  * FHGS_ERR_UNSUPPORTED. */
 enum { FHGS_GEOM_EWA = 0, FHGS_GEOM_SURFEL = 1 };
 
