@@ -68,6 +68,8 @@ def parse_args():
                          "batched: 16 uneven cameras, 500k Gaussians, D=256, one CUDA graph per step; "
                          "surfel: the 2DGS surfel geometry on the 1080p view (FP32 path)")
     ap.add_argument("--views", type=int, default=64, help="fusion: number of views")
+    ap.add_argument("--list-cut", type=int, choices=[0, 1], default=1,
+                    help="cut the tile lists where every pixel has stopped (identical outputs); 0 = full lists")
     return ap.parse_args()
 
 
@@ -279,12 +281,17 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     scene, cams, t, P = make_workload(rank, args.n, args.D, dev, args.width, args.height)
     path = {"tc": api.PATH_TC, "fp32": api.PATH_FP32, "auto": api.PATH_AUTO}[args.path]
-    rast = api.Rasterizer(local, sh_degree=3, path=path, d_split=args.d_split)
+    rast = api.Rasterizer(local, sh_degree=3, path=path, d_split=args.d_split, list_cut=args.list_cut)
     g = (t["means"], t["scales"], t["quats"], t["opacities"], t["sh"])
     st0 = rast.prepare(*g, cams)                      # sizes the instance buffer
     I = st0["n_instances"]
     rast.capacity = int(I * 1.05) + 1024
     del st0
+    I_full = I
+    if args.list_cut:  # the instance count of the full lists, for the record
+        rf = api.Rasterizer(local, sh_degree=3, path=path, d_split=args.d_split, list_cut=0)
+        I_full = rf.prepare(*g, cams)["n_instances"]
+        del rf
 
     def step(rr):
         st = rr.prepare(*g, cams, check=False)
@@ -418,7 +425,7 @@ def run_ours(args):
     # FP32 CUDA-core path on the same inputs (the baseline the TC path must beat)
     fp32 = None
     if args.fp32_steps > 0 and used_tc:
-        r32 = api.Rasterizer(local, sh_degree=3, path=api.PATH_FP32)
+        r32 = api.Rasterizer(local, sh_degree=3, path=api.PATH_FP32, list_cut=args.list_cut)
         r32.capacity = rast.capacity
         step(r32)
         torch.cuda.synchronize()
@@ -490,6 +497,7 @@ def run_ours(args):
                        WORKLOAD.replace("1920x1080 view", f"{args.width}x{args.height} centre crop"),
                        "gaussians": N, "width": args.width, "height": args.height, "feature_dim": D,
                        "sh_degree": 3, "path": "tc" if used_tc else "fp32", "tile_instances": I,
+                       "tile_instances_full_lists": I_full, "list_cut": bool(args.list_cut),
                        "composited_pairs_tile": Q, "composited_pairs_pixel": Qpix,
                        "gaussians_walked": U,
                        "l2": "inputs larger than L2 (features 1 GB, dL/dfeat 4.2 GB)",
@@ -538,7 +546,7 @@ def run_fusion(args):
               for k in ("means", "scales", "quats", "opacities", "sh"))
     maps = [device_feature_map(rank, v, views[v]["height"], views[v]["width"], D, dev) for v in range(len(views))]
     path = {"tc": api.PATH_TC, "fp32": api.PATH_FP32, "auto": api.PATH_AUTO}[args.path]
-    rast = api.Rasterizer(local, sh_degree=3, path=path)
+    rast = api.Rasterizer(local, sh_degree=3, path=path, list_cut=args.list_cut)
     for _ in range(max(1, args.warmup)):
         rast.fuse(*g, views, maps)
     torch.cuda.synchronize()
@@ -566,7 +574,7 @@ def run_fusion(args):
             "value": round(P / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s", "n_gpus": 1, "steps": K,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (maps generated on the device)",
-            "config": {"workload": "fusion: 3M Gaussians, 64 views 1280x720, D=256", "views": len(views),
+            "config": {"workload": "fusion: 3M Gaussians, 64 views 1280x720, D=256", "views": len(views), "list_cut": bool(args.list_cut),
                        "gaussians": N, "seen": int((den > 0).sum().item())},
             "roofline": {"bound": "hbm", "achieved": round(algo / (ms * 1e-3) / 1e9, 1),
                          "peak": load_peaks()["hbm"], "unit": "GB/s",
@@ -826,7 +834,7 @@ def run_ndfd(args):
     gen.manual_seed(9_000_011 + rank)
     dLgt = torch.randn(P, generator=gen, device=dev)
     dLcf = torch.randn(P, generator=gen, device=dev)
-    rast = api.Rasterizer(local, sh_degree=3)
+    rast = api.Rasterizer(local, sh_degree=3, list_cut=args.list_cut)
     st0 = rast.prepare(*g, cams)
     I = st0["n_instances"]
     rast.capacity = int(I * 1.05) + 1024
@@ -920,7 +928,7 @@ def run_ndfd(args):
     line = {"metric": NDFD_METRIC, "value": round(P / (ms * 1e-3) / 1e6, 2), "unit": UNIT, "n_gpus": 1,
             "steps": K, "warmup": W_, "ms_per_step": round(ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (NDFD inputs on the device)",
-            "config": {"workload": NDFD_WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.height,
+            "config": {"workload": NDFD_WORKLOAD, "gaussians": args.n, "width": args.width, "height": args.height, "list_cut": bool(args.list_cut),
                        "feature_dim": D, "tile_instances": I, "contributor_pairs": C,
                        "l2": "inputs larger than L2 (features 1 GB, ground-truth map 2.1 GB)",
                        "step": "project + bin/sort + NDFD forward + NDFD backward + projection backward"},
@@ -985,7 +993,7 @@ def run_batched(args):
     gen.manual_seed(4000 + rank)
     dC = torch.randn((P, 3), generator=gen, device=dev)
     dF = torch.randn((P, D), generator=gen, device=dev)
-    rast = api.Rasterizer(local, sh_degree=3, path=api.PATH_TC)
+    rast = api.Rasterizer(local, sh_degree=3, path=api.PATH_TC, list_cut=args.list_cut)
     st = rast.prepare(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams)
     rast.forward(st, t["features"])
     tuned = autotune.tune_splits(rast, st, t["features"], dC, dF, cams, use_cache=False)
@@ -1085,7 +1093,7 @@ def run_batched(args):
                 "n_gpus": world, "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
                 "data": "synthetic",
-                "config": {"workload": BATCH_WORKLOAD, "gaussians": N, "cameras": len(cams), "pixels": P,
+                "config": {"workload": BATCH_WORKLOAD, "gaussians": N, "cameras": len(cams), "pixels": P, "list_cut": bool(args.list_cut),
                            "feature_dim": D, "d_split": {"fwd": tuned["fwd"], "bwd": tuned["bwd"]},
                            "tile_instances": I, "composited_pairs_tile": Q, "composited_pairs_pixel": Qpix,
                            "gaussians_walked": U, "graph": "one CUDA graph per step (api.CapturedStep)",
@@ -1143,7 +1151,7 @@ def run_surfel(args):
     dev = torch.device("cuda", local)
     scene, cams, t, P = make_workload(rank, args.n, args.D, dev, args.width, args.height)
     D = args.D
-    rast = api.Rasterizer(local, sh_degree=3, geometry=api.GEOM_SURFEL)
+    rast = api.Rasterizer(local, sh_degree=3, geometry=api.GEOM_SURFEL, list_cut=args.list_cut)
     g = (t["means"], t["scales"], t["quats"], t["opacities"], t["sh"])
     st0 = rast.prepare(*g, cams)
     I = st0["n_instances"]
@@ -1217,7 +1225,7 @@ def run_surfel(args):
     line = {"metric": SURFEL_METRIC, "value": round(P / (ms * 1e-3) / 1e6, 2), "unit": UNIT, "n_gpus": 1,
             "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": SURFEL_WORKLOAD, "gaussians": args.n, "width": cams[0]["width"],
+            "config": {"workload": SURFEL_WORKLOAD, "gaussians": args.n, "width": cams[0]["width"], "list_cut": bool(args.list_cut),
                        "height": cams[0]["height"], "feature_dim": D, "tile_instances": I,
                        "composited_pairs_tile": Q, "composited_pairs_pixel": Qpix, "gaussians_walked": U,
                        "l2": "inputs larger than L2 (features 1 GB, dL/dfeat 4.2 GB)"},
@@ -1258,7 +1266,7 @@ def run_train(args):
     gen = torch.Generator(device=dev)
     gen.manual_seed(9_100_003 + rank)
     target = torch.rand((P, 3), generator=gen, device=dev)
-    be = LibraryBackend(local, sh_degree=3)
+    be = LibraryBackend(local, sh_degree=3, list_cut=args.list_cut)
     act = be.activate(raw)
     st0 = be.rast.prepare(raw["means"], act["scales"], raw["quats"], act["opacities"], raw["sh"], [cam])
     be.rast.capacity = int(st0["n_instances"] * 1.2) + 1024   # room for the instances to grow as Adam moves them
@@ -1297,7 +1305,7 @@ def run_train(args):
     line = {"metric": TRAIN_METRIC, "value": round(P / (ms * 1e-3) / 1e6, 2), "unit": UNIT, "n_gpus": 1,
             "steps": K, "warmup": W_, "ms_per_step": round(ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (NDFD inputs on the device)",
-            "config": {"workload": TRAIN_WORKLOAD, "gaussians": args.n, "width": cam["width"],
+            "config": {"workload": TRAIN_WORKLOAD, "gaussians": args.n, "width": cam["width"], "list_cut": bool(args.list_cut),
                        "height": cam["height"], "feature_dim": D, "tile_instances_at_start": I,
                        "l2": "inputs larger than L2 (features 1 GB, ground-truth map 2.1 GB)",
                        "step": "activation + project + bin/sort + render fwd (RGB) + L1 + NDFD fwd + render bwd + "

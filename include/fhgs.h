@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define FHGS_ABI_VERSION 1
+#define FHGS_ABI_VERSION 2
 #define FHGS_MAX_CAMS 32 /* cameras per call */
 #define FHGS_MAX_SH_DEGREE 3
 
@@ -89,6 +89,8 @@ typedef struct fhgs_params {
     float fov_clamp;         /* Jacobian uses x/z clamped to +-fov_clamp*W/(2 fx) (1.3) */
     float bg[3];             /* background colour behind the remaining transmittance */
     int32_t geometry;        /* FHGS_GEOM_*: the primitives' footprint model */
+    int32_t list_cut;        /* 0: full tile lists; 1: lists cut where every pixel has stopped (see
+                                fhgs_bin_sort); fhgs_default_params sets 0 */
 } fhgs_params;
 
 /* Footprint models.  FHGS_GEOM_EWA: 3-D Gaussians splatted to screen conics
@@ -180,7 +182,20 @@ fhgs_status fhgs_project(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhgs_came
 /* Duplicate each projected Gaussian into every 16x16 tile its
  * rectangle overlaps, sort the instances by (global tile id, depth,
  * Gaussian index) and find each tile's range (App. A).  Fills `bins`;
- * bins->keys may be NULL.  Uses context scratch. */
+ * bins->keys may be NULL.  Uses context scratch.
+ *
+ * With p->list_cut = 1 (EWA geometry; otherwise the lists stay full) each
+ * tile's list is cut after a point that every pixel of the tile provably never
+ * passes: compositing stops before a Gaussian that would take T below t_eps,
+ * and Gaussians whose alpha is at least a_lo at every pixel centre of the tile
+ * (nested boxes inside the ellipses q2 <= 3 and q2 <= 1, alpha bounded by
+ * min(alpha_max, op exp(-q/2)) with margins above FP32 rounding) each multiply
+ * T by at most 1 - a_lo.  The cut falls at the end of the depth segment (of
+ * the sort's segments of the depth order) in which the sum of -ln(1 - a_lo)
+ * first passes -ln(t_eps).  Each cut list is a prefix of the full one, every
+ * render, NDFD and fusion output over the cut lists equals the output over
+ * the full lists, and n_instances counts the cut instances.  Cameras whose
+ * tile grid exceeds (tiles_x + 1)(tiles_y + 1) = 28672 keep full lists. */
 fhgs_status fhgs_bin_sort(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_camera *cams, int n_cams,
                           const fhgs_params *p, const fhgs_bins *bins, void *stream);
 
@@ -229,7 +244,9 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
  * processed one at a time.  p->path: FHGS_PATH_FP32 sums on the CUDA cores;
  * FHGS_PATH_AUTO and FHGS_PATH_TC use the tensor cores when D % 64 == 0
  * (weights and maps as BF16 hi + lo, ~16-bit products, FP32 accumulation;
- * FHGS_PATH_TC with another D returns FHGS_ERR_UNSUPPORTED). */
+ * FHGS_PATH_TC with another D returns FHGS_ERR_UNSUPPORTED).  Each view's
+ * lists follow p->list_cut as in fhgs_bin_sort (the sums are the same); the
+ * projection of a view skips the SH colour, which fusion does not read. */
 enum { FHGS_FUSE_ACCUMULATE = 1, FHGS_FUSE_FINALIZE = 2, FHGS_FUSE_NORMALIZE = 4 };
 fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhgs_camera *views, int n_views,
                                const float *const *maps, int D, const fhgs_params *p, float *num,

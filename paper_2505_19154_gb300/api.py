@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("path", ctypes.c_int32), ("batch", ctypes.c_int32), ("d_split", ctypes.c_int32),
                 ("znear", ctypes.c_float), ("dilation", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("t_eps", ctypes.c_float), ("cutoff_sq", ctypes.c_float),
-                ("fov_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3), ("geometry", ctypes.c_int32)]
+                ("fov_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3), ("geometry", ctypes.c_int32),
+                ("list_cut", ctypes.c_int32)]
 
 
 class Adam(ctypes.Structure):
@@ -448,6 +449,7 @@ class Rasterizer:
             self.capacity = max(1024, 16 * n * len(cams))
         while True:
             st = dict(n=n, g=g, cams=ccams, ncam=len(cams), proj=proj, total_tiles=total_tiles,
+                      params=(means, scales, quats, opacities, sh),  # g points into these: keep them alive
                       gids=torch.empty(self.capacity, dtype=torch.int32, device=self.dev),
                       keys=torch.empty(self.capacity, dtype=torch.int64, device=self.dev) if self.keep_keys else None,
                       ranges=torch.empty((total_tiles, 2), dtype=torch.int32, device=self.dev),

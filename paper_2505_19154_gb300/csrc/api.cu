@@ -115,6 +115,7 @@ fhgs_status check_params(fhgs_ctx *ctx, const fhgs_params *p) {
         return fail(ctx, FHGS_ERR_INVALID_ARG, "unknown path");
     if (p->geometry != FHGS_GEOM_EWA && p->geometry != FHGS_GEOM_SURFEL)
         return fail(ctx, FHGS_ERR_INVALID_ARG, "unknown geometry");
+    if (p->list_cut != 0 && p->list_cut != 1) return fail(ctx, FHGS_ERR_INVALID_ARG, "list_cut must be 0 or 1");
     return FHGS_OK;
 }
 
@@ -413,10 +414,11 @@ fhgs_status fhgs_bin_sort(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs
     const long long cn = (long long)n * n_cams;
     if ((s = ensure_bin_scratch(ctx, n, n_cams, cs.total_tiles)) != FHGS_OK) return s;
     BinScratch sc = bin_scratch_view(ctx->bin.p, n, n_cams, cs.total_tiles, ctx->sm_count);
+    const Params q = make_params(p);
     {
-        Prof pr(ctx, "bin_sort", (cudaStream_t)stream);
-        launch_bin_sort(n, n_cams, cs, proj_view(const_cast<void *>(proj), cn), *bins, sc, ctx->status,
-                        (cudaStream_t)stream);
+        Prof pr(ctx, p->list_cut ? "bin_sort_cut" : "bin_sort", (cudaStream_t)stream);
+        launch_bin_sort(n, n_cams, cs, proj_view(const_cast<void *>(proj), cn), *bins, sc,
+                        p->list_cut ? &q : nullptr, ctx->status, (cudaStream_t)stream);
     }
     FHGS_CUDA(ctx, cudaGetLastError());
     return FHGS_OK;
@@ -805,6 +807,10 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
     if (p->path == FHGS_PATH_TC && !fuse_tc_dn(D))
         return fail(ctx, FHGS_ERR_UNSUPPORTED, "tensor-core fusion needs D % 64 == 0");
     const bool fuse_tc = p->path != FHGS_PATH_FP32 && fuse_tc_dn(D) != 0;
+    // fusion reads no colour: the projection skips the SH
+    Params qp = q;
+    qp.sh_deg = 0;
+    qp.K = 0;
     if ((s = ensure(ctx, ctx->fuse_proj, proj_bytes(n))) != FHGS_OK) return s;
     if ((s = ensure(ctx, ctx->fuse_count, 256)) != FHGS_OK) return s;
     for (int v = 0; v < n_views && n > 0; ++v) {
@@ -814,24 +820,24 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
         ProjView pv = proj_view(ctx->fuse_proj.p, n);
         {
             Prof pr(ctx, "fuse_project", st);
-            launch_project(*g, cs, q, pv, ctx->status, st);
+            launch_project(*g, cs, qp, pv, ctx->status, st);
         }
-        // instance capacity: grow until this view's instances fit (reads the
-        // count on the host, so fusion is not meant for stream capture)
+        if ((s = ensure_bin_scratch(ctx, n, 1, cs.total_tiles)) != FHGS_OK) return s;
+        BinScratch sc = bin_scratch_view(ctx->bin.p, n, 1, cs.total_tiles, ctx->sm_count);
+        fhgs_bins b;
+        b.keys = nullptr;
+        b.ranges = (uint32_t *)ctx->fuse_ranges.p;
+        b.n_instances = (int64_t *)ctx->fuse_count.p;
+        // instance capacity: grow until this view's instances fit (reads
+        // the count on the host, so fusion is not meant for stream capture)
         for (int tries = 0;; ++tries) {
             if (tries > 3) return fail(ctx, FHGS_ERR_CAPACITY, "instance buffer did not converge");
             if ((s = ensure(ctx, ctx->fuse_gids, sizeof(uint32_t) * 1024)) != FHGS_OK) return s;
-            fhgs_bins b;
             b.gids = (uint32_t *)ctx->fuse_gids.p;
-            b.keys = nullptr;
-            b.ranges = (uint32_t *)ctx->fuse_ranges.p;
-            b.n_instances = (int64_t *)ctx->fuse_count.p;
             b.capacity = (long long)(ctx->fuse_gids.bytes / sizeof(uint32_t));
-            if ((s = ensure_bin_scratch(ctx, n, 1, cs.total_tiles)) != FHGS_OK) return s;
-            BinScratch sc = bin_scratch_view(ctx->bin.p, n, 1, cs.total_tiles, ctx->sm_count);
             {
                 Prof pr(ctx, "fuse_bin_sort", st);
-                launch_bin_sort(n, 1, cs, pv, b, sc, nullptr, st);
+                launch_bin_sort(n, 1, cs, pv, b, sc, p->list_cut ? &q : nullptr, nullptr, st);
             }
             int64_t count = 0;
             FHGS_CUDA(ctx, cudaMemcpyAsync(&count, b.n_instances, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -847,7 +853,8 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
                 break;
             }
             if (count > 0xFFFFFFFFll) return fail(ctx, FHGS_ERR_CAPACITY, "too many instances in one view");
-            if ((s = ensure(ctx, ctx->fuse_gids, sizeof(uint32_t) * (size_t)(count + count / 8 + 1024))) != FHGS_OK)
+            if ((s = ensure(ctx, ctx->fuse_gids, sizeof(uint32_t) * (size_t)(count + count / 8 + 1024))) !=
+                FHGS_OK)
                 return s;
         }
         FHGS_CUDA(ctx, cudaGetLastError());

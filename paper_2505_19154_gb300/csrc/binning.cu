@@ -244,22 +244,108 @@ bool radix_sort_pairs(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, lo
 // table[(tile_off + tile) * S + seg].
 // Tile rectangles in sorted order (empty rectangle for culled entries), so
 // that the per-segment passes below read them sequentially.
+//
+// List cut.  Compositing stops at a pixel once its transmittance would fall
+// below t_eps, so the entries of a tile's list that follow the point where
+// every pixel of the tile has stopped are never read.  A bound finds such a
+// point without compositing: if a Gaussian's alpha is at least a_lo at every
+// pixel centre of a tile, each pixel that has not stopped multiplies its T by
+// at most (1 - a_lo), so once the sum of -ln(1 - a_lo) over such Gaussians
+// passes -ln(t_eps) every pixel of the tile has stopped (a pixel that had not
+// would hold T < t_eps).  Per sorted entry two nested boxes, inside the
+// ellipses q2 <= 3 and q2 <= 1, give the tiles whose pixel centres all lie in
+// them; on those tiles alpha >= min(alpha_max, op exp(-q/2)).  The bounds are
+// shrunk by margins far above FP32 rounding, and a level whose bound falls
+// below alpha_min counts nothing, so the cut only ever drops entries that no
+// pixel reaches: every output is the one the full lists give.
+constexpr float kCutUnits = 256.f;  // mass units per unit of -ln(1 - a)
+__host__ __device__ constexpr float cut_level(int l) { return l == 0 ? 3.f : 1.f; }  // outer, inner q2
+
+__device__ __forceinline__ uint32_t pack_range(int lo, int hi) {
+    return (uint32_t)(lo & 0xFFFF) | ((uint32_t)(hi & 0xFFFF) << 16);
+}
+
+// Tile range of the pixel centres inside [m - h, m + h] (centres of tile k are
+// 16 k + 0.5 .. 16 k + 15.5), within the rectangle's [lo, hi].
+__device__ __forceinline__ uint32_t inner_range(float m, float h, int lo, int hi) {
+    const float f0 = fminf(fmaxf(ceilf((m - h - 0.5f) * (1.f / kTile)), -1e6f), 1e6f);
+    const float f1 = fminf(fmaxf(floorf((m + h - (kTile - 0.5f)) * (1.f / kTile)), -1e6f), 1e6f);
+    const int k0 = max(lo, (int)f0), k1 = min(hi, (int)f1);
+    return k0 <= k1 ? pack_range(k0, k1) : pack_range(1, 0);
+}
+
+__device__ __forceinline__ uint32_t cut_units(float op, float q, float amin, float amax) {
+    const float alo = fminf(amax, op * expf(-0.5f * q)) * (1.f - 1e-3f);
+    if (!(alo > 0.f) || alo < amin * (1.f + 1e-3f)) return 0u;
+    return (uint32_t)floorf(-log1pf(-alo) * kCutUnits * (1.f - 1e-4f));
+}
+
 __global__ void __launch_bounds__(256) k_gather_rects(const uint32_t *__restrict__ order, ProjView pv, long long cn,
-                                                      int4 *rect) {
+                                                      int4 *rect, int4 *inner, uint32_t *imass, Params p) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cn) return;
     const uint32_t e = order[i];
-    rect[i] = pv.ntiles[e] ? pv.trect[e] : make_int4(0, 0, -1, -1);
+    const bool live = pv.ntiles[e] != 0u;
+    const int4 r = live ? pv.trect[e] : make_int4(0, 0, -1, -1);
+    rect[i] = r;
+    if (inner == nullptr) return;
+    // the two boxes |dx| <= a, |dy| <= b with b = a sqrt(A/C): their corners
+    // give q2 = 2 a^2 (A + |B| sqrt(A/C)) = q
+    uint32_t bx[2] = {pack_range(1, 0), pack_range(1, 0)}, by[2] = {pack_range(1, 0), pack_range(1, 0)};
+    uint32_t u[2] = {0u, 0u};
+    if (live) {
+        const GRec g = pv.rec[e];
+        const float A = g.a.z, B = g.a.w, C = g.b.x, op = g.b.y;
+        if (A > 0.f && C > 0.f) {
+            const float rr = sqrtf(A / C);
+            const float den = 2.f * (A + fabsf(B) * rr);
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const float q = cut_level(l);
+                if (q > p.cut) continue;
+                u[l] = cut_units(op, q, p.amin, p.amax);
+                if (u[l] == 0u) continue;
+                const float a0 = sqrtf(q / den);
+                const float ha = a0 * (1.f - 1e-3f) - 1e-2f, hb = a0 * rr * (1.f - 1e-3f) - 1e-2f;
+                if (!(ha > 0.f) || !(hb > 0.f)) {
+                    u[l] = 0u;
+                    continue;
+                }
+                bx[l] = inner_range(g.a.x, ha, r.x, r.z);
+                by[l] = inner_range(g.a.y, hb, r.y, r.w);
+            }
+        }
+    }
+    if (u[1] < u[0]) u[1] = u[0];  // the inner box holds at least the outer bound
+    inner[i] = make_int4((int)bx[0], (int)by[0], (int)bx[1], (int)by[1]);
+    imass[i] = u[0] | ((u[1] - u[0]) << 16);
 }
 
-__global__ void __launch_bounds__(256) k_seg_count(const int4 *__restrict__ rect, long long N, int SEG, int S,
-                                                   CamSet cs, uint32_t *table) {
+__device__ __forceinline__ void add_box(int *d, int pitch, uint32_t rx, uint32_t ry, int v) {
+    const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16), y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
+    if (v == 0 || x0 > x1 || y0 > y1) return;
+    atomicAdd(&d[y0 * pitch + x0], v);
+    atomicAdd(&d[y0 * pitch + x1 + 1], -v);
+    atomicAdd(&d[(y1 + 1) * pitch + x0], -v);
+    atomicAdd(&d[(y1 + 1) * pitch + x1 + 1], v);
+}
+
+// With the list cut (CUT) the same pass sums the segment's opacity mass per
+// tile (a second difference array over the nested boxes) into mass[].
+template <bool CUT>
+__global__ void __launch_bounds__(256) k_seg_count(const int4 *__restrict__ rect, const int4 *__restrict__ inner,
+                                                   const uint32_t *__restrict__ imass, long long N, int SEG, int S,
+                                                   CamSet cs, uint32_t *table, uint32_t *mass) {
     extern __shared__ int diff[];
     const int seg = blockIdx.x, ci = blockIdx.y;
     const DevCam &cam = cs.c[ci];
     const int tx = cam.tiles_x, ty = cam.tiles_y, pitch = tx + 1;
     const int cells = pitch * (ty + 1);
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) diff[i] = 0;
+    int *dm = diff + cells;
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+        diff[i] = 0;
+        if (CUT) dm[i] = 0;
+    }
     __syncthreads();
     const long long b0 = (long long)ci * N + (long long)seg * SEG;
     const long long b1 = min((long long)(ci + 1) * N, b0 + SEG);
@@ -270,28 +356,75 @@ __global__ void __launch_bounds__(256) k_seg_count(const int4 *__restrict__ rect
         atomicAdd(&diff[r.y * pitch + r.z + 1], -1);
         atomicAdd(&diff[(r.w + 1) * pitch + r.x], -1);
         atomicAdd(&diff[(r.w + 1) * pitch + r.z + 1], 1);
+        if (CUT) {
+            const int4 ib = inner[i];
+            const uint32_t m = imass[i];
+            add_box(dm, pitch, (uint32_t)ib.x, (uint32_t)ib.y, (int)(m & 0xFFFFu));
+            add_box(dm, pitch, (uint32_t)ib.z, (uint32_t)ib.w, (int)(m >> 16));
+        }
     }
     __syncthreads();
     for (int y = threadIdx.x; y < ty; y += blockDim.x) {  // prefix along x
-        int acc = 0;
+        int acc = 0, am = 0;
         for (int x = 0; x < tx; ++x) {
             acc += diff[y * pitch + x];
             diff[y * pitch + x] = acc;
+            if (CUT) {
+                am += dm[y * pitch + x];
+                dm[y * pitch + x] = am;
+            }
         }
     }
     __syncthreads();
     for (int x = threadIdx.x; x < tx; x += blockDim.x) {  // prefix along y
-        int acc = 0;
+        int acc = 0, am = 0;
         for (int y = 0; y < ty; ++y) {
             acc += diff[y * pitch + x];
             diff[y * pitch + x] = acc;
+            if (CUT) {
+                am += dm[y * pitch + x];
+                dm[y * pitch + x] = am;
+            }
         }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < tx * ty; t += blockDim.x) {
         const int y = t / tx, x = t - y * tx;
         table[(long long)(cam.tile_off + t) * S + seg] = (uint32_t)diff[y * pitch + x];
+        if (CUT) mass[(long long)(cam.tile_off + t) * S + seg] = (uint32_t)dm[y * pitch + x];
     }
+}
+
+// One warp per tile: the first segment by whose end the tile's opacity mass
+// reaches thr closes the tile; the counts of all later segments become 0, so
+// the scan and the scatter give the tile only the entries up to that segment.
+// close[t] = S when the mass never reaches thr.
+__global__ void __launch_bounds__(256) k_close_tiles(const uint32_t *__restrict__ mass, int S, int total_tiles,
+                                                     uint32_t thr, uint32_t *table, int *close) {
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (t >= total_tiles) return;
+    const uint32_t *m = mass + (long long)t * S;
+    uint32_t *c = table + (long long)t * S;
+    uint32_t run = 0;
+    int cs = S;
+    for (int s0 = 0; s0 < S; s0 += 32) {
+        const int s = s0 + lane;
+        const uint32_t v = s < S ? min(m[s], thr) : 0u;  // capped: the sums stay far below 2^32
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t hit = __ballot_sync(0xffffffffu, run + incl >= thr);
+        if (hit) {
+            cs = s0 + __ffs(hit) - 1;
+            break;
+        }
+        run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    for (int s = cs + 1 + lane; s < S; s += 32) c[s] = 0u;
+    if (lane == 0) close[t] = cs;
 }
 
 // ------------------------------------------------------------- big scan
@@ -470,6 +603,126 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32
     }
 }
 
+// The scatter of the list cut: one warp per (segment, camera, tile row).
+// Tiles closed before this segment (close[t] < seg) take no entries.  The
+// row's open tiles are listed in shared memory (olist; opre[x] = open tiles
+// left of x), a staged Gaussian's pairs are the open tiles of its x range in
+// order, and a warp whose row has no open tile leaves at once.
+__global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter_cut(const uint32_t *__restrict__ order,
+                                                                         const int4 *__restrict__ rect, long long N,
+                                                                         int SEG, int S, int max_ty, int row_words,
+                                                                         CamSet cs, const int *__restrict__ close,
+                                                                         const uint32_t *__restrict__ table,
+                                                                         uint32_t *gids, long long capacity) {
+    extern __shared__ uint32_t sh[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long item = (long long)blockIdx.x * kScatterWarps + warp;
+    const int ci = blockIdx.y;
+    if (item >= (long long)S * max_ty) return;  // warp-uniform; the kernel uses no block barrier
+    const int seg = (int)(item / max_ty), row = (int)(item - (long long)seg * max_ty);
+    const DevCam &cam = cs.c[ci];
+    if (row >= cam.tiles_y) return;
+    const int tx = cam.tiles_x;
+    uint32_t *ctr = sh + warp * (3 * row_words + kScatterStageWords);
+    uint32_t *opre = ctr + row_words;
+    uint32_t *olist = opre + row_words;
+    uint32_t *st_o = olist + row_words;  // staged: first open index, pair count, Gaussian, pair prefix
+    uint32_t *st_c = st_o + kStage;
+    uint32_t *st_g = st_c + kStage;
+    uint32_t *st_p = st_g + kStage;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int tbase = cam.tile_off + row * tx;
+    uint32_t nopen = 0;
+    for (int x0 = 0; x0 < tx; x0 += 32) {
+        const int x = x0 + lane;
+        const bool open = x < tx && seg <= close[tbase + x];
+        const uint32_t bal = __ballot_sync(0xffffffffu, open);
+        const uint32_t at = nopen + __popc(bal & lt_mask);
+        if (x < tx) opre[x] = at;
+        if (open) {
+            olist[at] = (uint32_t)x;
+            ctr[x] = table[(long long)(tbase + x) * S + seg];
+        }
+        nopen += __popc(bal);
+    }
+    if (nopen == 0) return;
+    if (lane == 0) opre[tx] = nopen;
+    __syncwarp();
+    const long long b0 = (long long)ci * N + (long long)seg * SEG;
+    const long long b1 = min((long long)(ci + 1) * N, b0 + SEG);
+    for (long long c0 = b0; c0 < b1; c0 += kStage) {
+        const int m = (int)min((long long)kStage, b1 - c0);
+        __syncwarp();
+        int mt = 0;
+        for (int k0 = 0; k0 < m; k0 += 32) {
+            const int k = k0 + lane;
+            uint32_t o0 = 0, cnt = 0, e = 0;
+            if (k < m) {
+                const int4 r = rect[c0 + k];
+                if (r.y <= row && row <= r.w) {
+                    o0 = opre[r.x];
+                    cnt = opre[r.z + 1] - o0;
+                    e = order[c0 + k];
+                }
+            }
+            const bool touch = cnt > 0u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, touch);
+            if (touch) {
+                const int at = mt + __popc(bal & lt_mask);
+                st_o[at] = o0;
+                st_c[at] = cnt;
+                st_g[at] = (uint32_t)(e - (long long)ci * N);
+            }
+            mt += __popc(bal);
+        }
+        __syncwarp();
+        if (mt == 0) continue;
+        uint32_t cnt[kStage / 32];
+        uint32_t lsum = 0;
+#pragma unroll
+        for (int u = 0; u < kStage / 32; ++u) {
+            const int k = lane * (kStage / 32) + u;
+            cnt[u] = k < mt ? st_c[k] : 0u;
+            lsum += cnt[u];
+        }
+        uint32_t incl = lsum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t run = incl - lsum;
+#pragma unroll
+        for (int u = 0; u < kStage / 32; ++u) {
+            st_p[lane * (kStage / 32) + u] = run;
+            run += cnt[u];
+        }
+        __syncwarp();
+        for (uint32_t i0 = 0; i0 < total; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            const bool act = i < total;
+            int lo = 0, hi = mt - 1;  // the staged Gaussian of pair i: the last k with prefix[k] <= i
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (st_p[mid] <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            const uint32_t x = act ? olist[st_o[lo] + (i - st_p[lo])] : 0u;
+            const uint32_t same = __match_any_sync(0xffffffffu, act ? x : (0x80000000u | (uint32_t)lane));
+            const uint32_t rank = __popc(same & lt_mask);
+            const uint32_t base = act ? ctr[x] : 0u;
+            __syncwarp();
+            if (act) {
+                const uint32_t pos = base + rank;
+                if (pos < capacity) gids[pos] = st_g[lo];
+                if (rank == 0) ctr[x] = base + (uint32_t)__popc(same);
+            }
+            __syncwarp();
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_table_ranges(const uint32_t *__restrict__ table, int S, int total_tiles,
                                                       const int64_t *total, long long capacity, uint32_t *ranges,
                                                       unsigned *status) {
@@ -509,8 +762,8 @@ size_t bin_scratch_bytes(long long N, int n_cams, int total_tiles, int sm_count)
     const long long S = (N + SEG - 1) / SEG;
     const long long tab = (long long)total_tiles * (S > 0 ? S : 1);
     const int G = 2 * sm_count;
-    return 4 * align_up(sizeof(uint32_t) * (cn + 1), 256) + align_up(sizeof(int4) * (cn + 1), 256) +
-           align_up(sizeof(uint32_t) * (tab + 1), 256) +
+    return 5 * align_up(sizeof(uint32_t) * (cn + 1), 256) + 2 * align_up(sizeof(int4) * (cn + 1), 256) +
+           2 * align_up(sizeof(uint32_t) * (tab + 1), 256) + align_up(sizeof(int) * (total_tiles + 1), 256) +
            align_up(sizeof(uint32_t) * ((tab + kScanTile - 1) / kScanTile + 1), 256) +
            align_up(sizeof(uint32_t) * kBuckets * (size_t)G, 256) + 256;
 }
@@ -532,7 +785,11 @@ BinScratch bin_scratch_view(void *base, long long N, int n_cams, int total_tiles
     s.dk_b = take(sizeof(uint32_t) * (cn + 1));
     s.dv_b = take(sizeof(uint32_t) * (cn + 1));
     s.rect = reinterpret_cast<int4 *>(take(sizeof(int4) * (cn + 1)));
+    s.inner = reinterpret_cast<int4 *>(take(sizeof(int4) * (cn + 1)));
+    s.imass = take(sizeof(uint32_t) * (cn + 1));
     s.table = take(sizeof(uint32_t) * (tab + 1));
+    s.mass = take(sizeof(uint32_t) * (tab + 1));
+    s.close = reinterpret_cast<int *>(take(sizeof(int) * (total_tiles + 1)));
     s.partials = take(sizeof(uint32_t) * ((tab + kScanTile - 1) / kScanTile + 1));
     s.hist = take(sizeof(uint32_t) * kBuckets * (size_t)(2 * sm_count));
     s.seg = SEG;
@@ -541,13 +798,19 @@ BinScratch bin_scratch_view(void *base, long long N, int n_cams, int total_tiles
     return s;
 }
 
-void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, const fhgs_bins &bins, BinScratch sc,
-                     unsigned *status, cudaStream_t st) {
+bool bin_cut_fits(const CamSet &cs) {
+    for (int c = 0; c < cs.n; ++c)
+        if (2ll * (cs.c[c].tiles_x + 1) * (cs.c[c].tiles_y + 1) > FHGS_MAX_TILE_CELLS) return false;
+    return true;
+}
+
+namespace {
+
+// 1. depth order of all (camera, Gaussian) entries, grouped by camera, and
+// the tile rectangles (with the cut: the nested boxes) in that order.
+uint32_t *sort_entries(long long N, int n_cams, ProjView pv, const BinScratch &sc, const Params *cut,
+                       cudaStream_t st) {
     const long long cn = (long long)n_cams * N;
-    cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)cs.total_tiles, st);
-    cudaMemsetAsync(bins.n_instances, 0, sizeof(int64_t), st);
-    if (cn == 0) return;
-    // 1. depth order of all (camera, Gaussian) entries, then grouped by camera
     const int G = radix_blocks(cn, sc.sm_count);
     note_launch(1);
     k_iota_keys<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(pv.dkey, cn, sc.dk_a, sc.dv_a);
@@ -562,52 +825,125 @@ void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, con
         while ((1 << bits) < n_cams) ++bits;
         if (radix_sort_pairs(ck, order, ok2, ov2, cn, bits, sc.hist, G, st)) order = ov2;
     }
+    Params q;
+    memset(&q, 0, sizeof(q));
+    if (cut) q = *cut;
     note_launch(1);
-    k_gather_rects<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(order, pv, cn, sc.rect);
-    // 2. per-segment tile counts
-    const int SEG = sc.seg, S = sc.nseg;
+    k_gather_rects<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(order, pv, cn, sc.rect, cut ? sc.inner : nullptr,
+                                                                 sc.imass, q);
+    return order;
+}
+
+// 2. per-segment tile counts (and, with the cut, opacity masses)
+void count_tiles(long long N, int n_cams, const CamSet &cs, const BinScratch &sc, bool cut, cudaStream_t st) {
     int max_cells = 0;
     for (int c = 0; c < n_cams; ++c) max_cells = max(max_cells, (cs.c[c].tiles_x + 1) * (cs.c[c].tiles_y + 1));
-    const int count_smem = max_cells * (int)sizeof(int);
-    static std::atomic<unsigned long long> count_done{0};
-    allow_max_smem(count_done, k_seg_count);
+    const int count_smem = (cut ? 2 : 1) * max_cells * (int)sizeof(int);
     note_launch(1);
-    k_seg_count<<<dim3(S, n_cams), 256, count_smem, st>>>(sc.rect, N, SEG, S, cs, sc.table);
-    // 3. scan of the (tile, segment) table: segment offsets and the total
-    const long long tab = (long long)cs.total_tiles * S;
+    if (cut) {
+        static std::atomic<unsigned long long> count_done{0};
+        allow_max_smem(count_done, k_seg_count<true>);
+        k_seg_count<true><<<dim3(sc.nseg, n_cams), 256, count_smem, st>>>(sc.rect, sc.inner, sc.imass, N, sc.seg,
+                                                                          sc.nseg, cs, sc.table, sc.mass);
+    } else {
+        static std::atomic<unsigned long long> count_done{0};
+        allow_max_smem(count_done, k_seg_count<false>);
+        k_seg_count<false><<<dim3(sc.nseg, n_cams), 256, count_smem, st>>>(sc.rect, nullptr, nullptr, N, sc.seg,
+                                                                           sc.nseg, cs, sc.table, nullptr);
+    }
+}
+
+// 3. exclusive scan of a (tile, segment) table in place, its total into *total
+void scan_table(uint32_t *table, long long tab, uint32_t *partials, int64_t *total, cudaStream_t st) {
     const unsigned nparts = (unsigned)((tab + kScanTile - 1) / kScanTile);
     note_launch(3);
-    k_scan_reduce<<<nparts, kScanThreads, 0, st>>>(sc.table, tab, sc.partials);
+    k_scan_reduce<<<nparts, kScanThreads, 0, st>>>(table, tab, partials);
     static std::atomic<unsigned long long> scan_done{0};
     allow_max_smem(scan_done, k_scan_small);
-    k_scan_small<<<1, 1024, kScanSmallSmem, st>>>(sc.partials, (int)nparts, bins.n_instances);
-    k_scan_down<<<nparts, kScanThreads, 0, st>>>(sc.table, tab, sc.partials);
+    k_scan_small<<<1, 1024, kScanSmallSmem, st>>>(partials, (int)nparts, total);
+    k_scan_down<<<nparts, kScanThreads, 0, st>>>(table, tab, partials);
+}
+
+void grid_extent(const CamSet &cs, int &max_tx, int &max_ty) {
+    max_tx = max_ty = 0;
+    for (int c = 0; c < cs.n; ++c) {
+        max_ty = max(max_ty, cs.c[c].tiles_y);
+        max_tx = max(max_tx, cs.c[c].tiles_x);
+    }
+}
+
+// 4b. the list cut's scatter: each segment into the tiles that close[] leaves
+// open, at the offsets of the scanned (tile, segment) table
+void scatter_cut(long long N, const CamSet &cs, const BinScratch &sc, const uint32_t *order, const fhgs_bins &bins,
+                 cudaStream_t st) {
+    int max_tx, max_ty;
+    grid_extent(cs, max_tx, max_ty);
+    if (max_ty == 0) return;
+    // one warp per (segment, tile row): counters, open prefix and open list
+    const int row_words = (max_tx + 1 + 3) & ~3;
+    const int scat_smem = kScatterWarps * (3 * row_words + kScatterStageWords) * (int)sizeof(uint32_t);
+    static std::atomic<unsigned long long> scatter_done{0};
+    allow_max_smem(scatter_done, k_seg_scatter_cut);
+    note_launch(1);
+    const long long items = (long long)sc.nseg * max_ty;
+    k_seg_scatter_cut<<<dim3((unsigned)((items + kScatterWarps - 1) / kScatterWarps), cs.n), kScatterWarps * 32,
+                        scat_smem, st>>>(order, sc.rect, N, sc.seg, sc.nseg, max_ty, row_words, cs, sc.close,
+                                         sc.table, bins.gids, bins.capacity);
+}
+
+}  // namespace
+
+void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, const fhgs_bins &bins, BinScratch sc,
+                     const Params *cutp, unsigned *status, cudaStream_t st) {
+    const long long cn = (long long)n_cams * N;
+    cudaMemsetAsync(bins.ranges, 0, sizeof(uint32_t) * 2 * (size_t)cs.total_tiles, st);
+    cudaMemsetAsync(bins.n_instances, 0, sizeof(int64_t), st);
+    if (cn == 0) return;
+    // the list cut needs the EWA records, a stop threshold in (0, 1) and room
+    // for two difference arrays per camera grid
+    const bool cut = cutp != nullptr && cutp->geom == FHGS_GEOM_EWA && cutp->teps > 0.f && cutp->teps < 1.f &&
+                     bin_cut_fits(cs);
+    const uint32_t *order = sort_entries(N, n_cams, pv, sc, cut ? cutp : nullptr, st);
+    const int S = sc.nseg;
+    count_tiles(N, n_cams, cs, sc, cut, st);
+    if (cut) {
+        // tiles close once their mass passes -ln(t_eps) (one unit of margin
+        // above the FP32 products of T)
+        const uint32_t thr = (uint32_t)ceil(-log((double)cutp->teps) * kCutUnits) + 1u;
+        note_launch(1);
+        k_close_tiles<<<(cs.total_tiles + 7) / 8, 256, 0, st>>>(sc.mass, S, cs.total_tiles, thr, sc.table,
+                                                                sc.close);
+    }
+    // 3. scan of the (tile, segment) table: segment offsets and the total
+    const long long tab = (long long)cs.total_tiles * S;
+    scan_table(sc.table, tab, sc.partials, bins.n_instances, st);
     // 4. tile ranges, then the scatter of Gaussian indices
     note_launch(1);
     k_table_ranges<<<(cs.total_tiles + 255) / 256, 256, 0, st>>>(sc.table, S, cs.total_tiles, bins.n_instances,
                                                                  bins.capacity, bins.ranges, status);
-    // bands of tile rows: enough (segment, band) warps to fill the GPU, at
-    // most a few thousand counters each
-    int max_ty = 0, max_tx = 0;
-    for (int c = 0; c < n_cams; ++c) {
-        max_ty = max(max_ty, cs.c[c].tiles_y);
-        max_tx = max(max_tx, cs.c[c].tiles_x);
+    if (cut) {
+        scatter_cut(N, cs, sc, order, bins, st);
+    } else {
+        int max_tx, max_ty;
+        grid_extent(cs, max_tx, max_ty);
+        // bands of tile rows: enough (segment, band) warps to fill the GPU, at
+        // most a few thousand counters each
+        const long long want = 128ll * sc.sm_count;  // warps
+        int nband = (int)min((long long)max_ty, (want + (long long)S * n_cams - 1) / ((long long)S * n_cams));
+        nband = max(nband, 1);
+        // at most kScatterCtr counters per warp (tiles_x <= 4096 keeps one row)
+        const int band_rows = max(1, min((max_ty + nband - 1) / nband, kScatterCtr / max(max_tx, 1)));
+        nband = (max_ty + band_rows - 1) / band_rows;
+        const int ctr_words = (band_rows * max_tx + 3) & ~3;
+        const int scat_smem = kScatterWarps * (ctr_words + kScatterStageWords) * (int)sizeof(uint32_t);
+        static std::atomic<unsigned long long> scatter_done{0};
+        allow_max_smem(scatter_done, k_seg_scatter);
+        note_launch(1);
+        const long long items = (long long)S * nband;
+        k_seg_scatter<<<dim3((unsigned)((items + kScatterWarps - 1) / kScatterWarps), n_cams), kScatterWarps * 32,
+                        scat_smem, st>>>(order, sc.rect, N, sc.seg, S, nband, band_rows, cs, sc.table, bins.gids,
+                                         bins.capacity);
     }
-    const long long want = 128ll * sc.sm_count;  // warps
-    int nband = (int)min((long long)max_ty, (want + (long long)S * n_cams - 1) / ((long long)S * n_cams));
-    nband = max(nband, 1);
-    // at most kScatterCtr counters per warp (tiles_x <= 4096 keeps one row)
-    const int band_rows = max(1, min((max_ty + nband - 1) / nband, kScatterCtr / max(max_tx, 1)));
-    nband = (max_ty + band_rows - 1) / band_rows;
-    const int ctr_words = (band_rows * max_tx + 3) & ~3;
-    const int scat_smem = kScatterWarps * (ctr_words + kScatterStageWords) * (int)sizeof(uint32_t);
-    static std::atomic<unsigned long long> scatter_done{0};
-    allow_max_smem(scatter_done, k_seg_scatter);
-    note_launch(1);
-    const long long items = (long long)S * nband;
-    k_seg_scatter<<<dim3((unsigned)((items + kScatterWarps - 1) / kScatterWarps), n_cams), kScatterWarps * 32,
-                    scat_smem, st>>>(order, sc.rect, N, SEG, S, nband, band_rows, cs, sc.table, bins.gids,
-                                     bins.capacity);
     if (bins.keys) {
         note_launch(1);
         k_keys64<<<cs.total_tiles, 256, 0, st>>>(bins.ranges, bins.gids, pv, N, cs, bins.keys);

@@ -195,15 +195,24 @@ void launch_project_bwd(const fhgs_gaussians &g, const CamSet &cs, const Params 
 struct BinScratch {
     uint32_t *dk_a, *dv_a, *dk_b, *dv_b;  // depth sort [C*N]
     int4 *rect;                           // tile rectangles in sorted order [C*N]
+    int4 *inner;                          // list cut: the nested boxes' tile ranges in sorted order [C*N]
+    uint32_t *imass;                      // list cut: their opacity-mass units [C*N]
     uint32_t *table;                      // per (tile, segment) counts, then offsets
+    uint32_t *mass;                       // list cut: per (tile, segment) opacity mass
+    int *close;                           // list cut: per tile, the last segment it takes
     uint32_t *partials;                   // scan partials of the table
     uint32_t *hist;                       // radix histogram [256][G]
     int seg, nseg, sm_count;              // segment size, segments per camera
 };
 size_t bin_scratch_bytes(long long N, int n_cams, int total_tiles, int sm_count);
 BinScratch bin_scratch_view(void *base, long long N, int n_cams, int total_tiles, int sm_count);
+// cut: the render rules of the list cut (EWA geometry), or nullptr for the
+// full lists of the (tile, depth) sort.
 void launch_bin_sort(long long N, int n_cams, const CamSet &cs, ProjView pv, const fhgs_bins &bins,
-                     BinScratch sc, unsigned *status, cudaStream_t st);
+                     BinScratch sc, const Params *cut, unsigned *status, cudaStream_t st);
+// Whether launch_bin_sort can cut the lists of these cameras (the count pass
+// keeps two difference arrays of each camera's tile grid in shared memory).
+bool bin_cut_fits(const CamSet &cs);
 
 // render, FP32 CUDA-core path (render_fp32.cu)
 void launch_render_fwd_fp32(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,

@@ -63,7 +63,7 @@ def test_host_helpers(L):
     assert L.fhgs_total_tiles(cams, 0) == -1
     assert L.fhgs_proj_bytes(1000, 2) >= 2000 * (48 + 16 + 8)
     assert L.fhgs_proj_bytes(-1, 1) == -1
-    assert L.fhgs_abi_version() == 1
+    assert L.fhgs_abi_version() == 2
     assert L.fhgs_status_string(api.ERR_CAPACITY) == b"instance buffer overflow"
 
 

@@ -34,13 +34,18 @@ def test_config5_one_full_view_against_oracle():
     D = 256
     fmap = synth.smooth_feature_map(0, 0, view["height"], view["width"], D)
     g = _upload(scene, dev)
-    rast = api.Rasterizer(0, sh_degree=3)
-    out, num, den = rast.fuse(*g, [view], [torch.from_numpy(fmap.reshape(-1, D)).to(dev)])
-    torch.cuda.synchronize()
-    assert rast.ctx.sync_status() == api.OK
     # decisions on the FP32 specification's footprints, as the kernels take them
     prep = oracle.prepare(scene, [view], dict(sh_degree=3), geometry="fp32")
     ref = oracle.fuse(scene, [view], [fmap], dict(sh_degree=3), prep=prep)
+    for cut in (0, 1):  # full lists, then the rounds over depth segments
+        rast = api.Rasterizer(0, sh_degree=3, list_cut=cut)
+        out, num, den = rast.fuse(*g, [view], [torch.from_numpy(fmap.reshape(-1, D)).to(dev)])
+        torch.cuda.synchronize()
+        assert rast.ctx.sync_status() == api.OK
+        _check_view(out, den, ref)
+
+
+def _check_view(out, den, ref):
     den_g, den_r = den.cpu().numpy().astype(np.float64), ref["den"]
     seen = den_r > 1e-6
     assert seen.sum() > 2_000, seen.sum()  # the dense ball saturates within its outer shell
@@ -79,7 +84,7 @@ def test_config5_all_views_constant_map():
     P = views[0]["width"] * views[0]["height"]
     cmap = c.to(dev).expand(P, D).contiguous()   # 944 MB, shared by the 64 views
     g = _upload(scene, dev)
-    rast = api.Rasterizer(0, sh_degree=3)
+    rast = api.Rasterizer(0, sh_degree=3, list_cut=1)
     out, num, den = rast.fuse(*g, views, [cmap] * len(views))
     torch.cuda.synchronize()
     assert rast.ctx.sync_status() == api.OK

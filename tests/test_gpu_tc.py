@@ -133,15 +133,15 @@ def test_tc_fusion_small_against_oracle_and_fp32_path(D):
     t = {k: _t(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
     dmaps = [_t(m).view(-1, D) for m in maps]
     outs = {}
-    for path in (api.PATH_TC, api.PATH_FP32):
-        rast = api.Rasterizer(0, sh_degree=1, path=path)
+    for path, cut in ((api.PATH_TC, 0), (api.PATH_TC, 1), (api.PATH_FP32, 0)):
+        rast = api.Rasterizer(0, sh_degree=1, path=path, list_cut=cut)
         rast.ctx.profile(True)
         o, n_, d_ = rast.fuse(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], views, dmaps)
         torch.cuda.synchronize()
         assert rast.ctx.sync_status() == api.OK
         prof = rast.ctx.profile_read()
         assert ("fuse_tc" if path == api.PATH_TC else "fuse_fp32") in prof, prof
-        outs[path] = (o.cpu().numpy().astype(np.float64), d_.cpu().numpy().astype(np.float64))
+        outs[(path, cut)] = (o.cpu().numpy().astype(np.float64), d_.cpu().numpy().astype(np.float64))
     seen = ref["den"] > 1e-6
     assert seen.sum() > 300
     fn = np.maximum(np.linalg.norm(ref["out"], axis=1), 1e-30)
