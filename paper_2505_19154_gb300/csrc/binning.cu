@@ -38,9 +38,18 @@ constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;  // 2048
 
 // ---------------------------------------------------------------- radix
+// A pass may be skipped when every key that matters shares its digit: kb
+// (nullable) holds the AND and the OR of those keys' bits, and a skipped
+// pass copies the keys in order (the sort stays stable).
+__device__ __forceinline__ bool radix_skip(const uint32_t *kb, int shift, uint32_t mask) {
+    return kb != nullptr && (((kb[0] ^ kb[1]) >> shift) & mask) == 0u;
+}
+
 // Per-block digit histogram of the block's contiguous segment.
 __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t *__restrict__ keys, long long n,
-                                                                 int shift, uint32_t mask, uint32_t *hist) {
+                                                                 int shift, uint32_t mask, uint32_t *hist,
+                                                                 const uint32_t *__restrict__ kb) {
+    if (radix_skip(kb, shift, mask)) return;
     __shared__ uint32_t h[kRadixWarps][kBuckets];
     for (int i = threadIdx.x; i < kRadixWarps * kBuckets; i += kRadixThreads) (&h[0][0])[i] = 0;
     __syncthreads();
@@ -72,7 +81,10 @@ constexpr int kScanSmallItems = 16;
 constexpr int kScanSmallStep = 1024 * kScanSmallItems;
 constexpr int kScanSmallSmem = kScanSmallStep * 4 + kScanSmallStep / 32 * 4;  // values, then one pad word per 32
 __device__ __forceinline__ int scan_small_slot(int i) { return i + (i >> 5); }  // pad: conflict-free per-thread rows
-__global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, int total, int64_t *total_out) {
+__global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, int total, int64_t *total_out,
+                                                    const uint32_t *__restrict__ kb = nullptr, int shift = 0,
+                                                    uint32_t mask = 0u) {
+    if (radix_skip(kb, shift, mask)) return;
     extern __shared__ uint32_t sv[];
     __shared__ uint32_t carry;
     __shared__ uint32_t wsum[32];
@@ -134,13 +146,21 @@ __global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, int total, int
 // computed in that order keep the sort stable.
 __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, long long n, int shift, uint32_t mask, const uint32_t *__restrict__ hist) {
+    uint32_t *__restrict__ vout, long long n, int shift, uint32_t mask, const uint32_t *__restrict__ hist,
+    const uint32_t *__restrict__ kb) {
     __shared__ uint32_t run[kBuckets];                // next output slot per digit
     __shared__ uint32_t tot[kBuckets];                // this tile's count per digit
     __shared__ uint32_t wcnt[kRadixWarps][kBuckets];  // per-warp counts, then prefixes
     const long long G = gridDim.x;
     const long long seg = (n + G - 1) / G;
     const long long s = blockIdx.x * seg, e = min(n, s + seg);
+    if (radix_skip(kb, shift, mask)) {  // every key that matters has this digit: keep the order
+        for (long long i = s + threadIdx.x; i < e; i += kRadixThreads) {
+            kout[i] = kin[i];
+            vout[i] = vin[i];
+        }
+        return;
+    }
     for (int d = threadIdx.x; d < kBuckets; d += kRadixThreads) run[d] = hist[(long long)d * G + blockIdx.x];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -194,11 +214,38 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
     }
 }
 
-__global__ void k_iota_keys(const uint32_t *__restrict__ dkey, long long n, uint32_t *k, uint32_t *v) {
+// Keys and indices of the depth sort, and the AND / OR of the keys of the
+// entries that are not culled (culled entries, key 0xFFFFFFFF, have empty
+// rectangles, so their place in the order does not matter).
+__global__ void k_iota_keys(const uint32_t *__restrict__ dkey, long long n, uint32_t *k, uint32_t *v,
+                            uint32_t *kb) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t key = 0xFFFFFFFFu;
     if (i < n) {
-        k[i] = dkey[i];
+        key = dkey[i];
+        k[i] = key;
         v[i] = (uint32_t)i;
+    }
+    const bool live = key != 0xFFFFFFFFu;
+    __shared__ uint32_t ra[8], ro[8];  // one AND / OR per warp, then one pair of atomics per block
+    const uint32_t a = __reduce_and_sync(0xffffffffu, live ? key : 0xFFFFFFFFu);
+    const uint32_t o = __reduce_or_sync(0xffffffffu, live ? key : 0u);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        ra[w] = a;
+        ro[w] = o;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t ba = 0xFFFFFFFFu, bo = 0u;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            ba &= ra[k];
+            bo |= ro[k];
+        }
+        if (ba != 0xFFFFFFFFu || bo != 0u) {  // the block holds a live key
+            atomicAnd(&kb[0], ba);
+            atomicOr(&kb[1], bo);
+        }
     }
 }
 
@@ -216,7 +263,7 @@ int radix_blocks(long long n, int sm_count) {
 // Sorts (kA, vA) by the low `bits` bits of kA; returns true if the result is
 // in (kB, vB) (odd number of passes), false if back in (kA, vA).
 bool radix_sort_pairs(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, long long n, int bits,
-                      uint32_t *hist, int G, cudaStream_t st) {
+                      uint32_t *hist, int G, cudaStream_t st, const uint32_t *kb = nullptr) {
     int shift = 0;
     bool a_to_b = true;
     while (shift < bits) {
@@ -227,11 +274,11 @@ bool radix_sort_pairs(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, lo
         uint32_t *ko = a_to_b ? kB : kA;
         uint32_t *vo = a_to_b ? vB : vA;
         note_launch(3);
-        k_radix_upsweep<<<G, kRadixThreads, 0, st>>>(ki, n, shift, mask, hist);
+        k_radix_upsweep<<<G, kRadixThreads, 0, st>>>(ki, n, shift, mask, hist, kb);
         static std::atomic<unsigned long long> scan_done{0};
         allow_max_smem(scan_done, k_scan_small);
-        k_scan_small<<<1, 1024, kScanSmallSmem, st>>>(hist, kBuckets * G, nullptr);
-        k_radix_downsweep<<<G, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n, shift, mask, hist);
+        k_scan_small<<<1, 1024, kScanSmallSmem, st>>>(hist, kBuckets * G, nullptr, kb, shift, mask);
+        k_radix_downsweep<<<G, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n, shift, mask, hist, kb);
         shift += nb;
         a_to_b = !a_to_b;
     }
@@ -765,7 +812,7 @@ size_t bin_scratch_bytes(long long N, int n_cams, int total_tiles, int sm_count)
     return 5 * align_up(sizeof(uint32_t) * (cn + 1), 256) + 2 * align_up(sizeof(int4) * (cn + 1), 256) +
            2 * align_up(sizeof(uint32_t) * (tab + 1), 256) + align_up(sizeof(int) * (total_tiles + 1), 256) +
            align_up(sizeof(uint32_t) * ((tab + kScanTile - 1) / kScanTile + 1), 256) +
-           align_up(sizeof(uint32_t) * kBuckets * (size_t)G, 256) + 256;
+           align_up(sizeof(uint32_t) * kBuckets * (size_t)G, 256) + 256 + 256;
 }
 
 BinScratch bin_scratch_view(void *base, long long N, int n_cams, int total_tiles, int sm_count) {
@@ -792,6 +839,7 @@ BinScratch bin_scratch_view(void *base, long long N, int n_cams, int total_tiles
     s.close = reinterpret_cast<int *>(take(sizeof(int) * (total_tiles + 1)));
     s.partials = take(sizeof(uint32_t) * ((tab + kScanTile - 1) / kScanTile + 1));
     s.hist = take(sizeof(uint32_t) * kBuckets * (size_t)(2 * sm_count));
+    s.kbits = take(2 * sizeof(uint32_t));
     s.seg = SEG;
     s.nseg = (int)S;
     s.sm_count = sm_count;
@@ -812,9 +860,11 @@ uint32_t *sort_entries(long long N, int n_cams, ProjView pv, const BinScratch &s
                        cudaStream_t st) {
     const long long cn = (long long)n_cams * N;
     const int G = radix_blocks(cn, sc.sm_count);
+    cudaMemsetAsync(sc.kbits, 0xFF, sizeof(uint32_t), st);
+    cudaMemsetAsync(sc.kbits + 1, 0, sizeof(uint32_t), st);
     note_launch(1);
-    k_iota_keys<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(pv.dkey, cn, sc.dk_a, sc.dv_a);
-    const bool in_b = radix_sort_pairs(sc.dk_a, sc.dv_a, sc.dk_b, sc.dv_b, cn, 32, sc.hist, G, st);
+    k_iota_keys<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(pv.dkey, cn, sc.dk_a, sc.dv_a, sc.kbits);
+    const bool in_b = radix_sort_pairs(sc.dk_a, sc.dv_a, sc.dk_b, sc.dv_b, cn, 32, sc.hist, G, st, sc.kbits);
     uint32_t *order = in_b ? sc.dv_b : sc.dv_a;
     if (n_cams > 1) {
         uint32_t *ck = in_b ? sc.dk_b : sc.dk_a;  // reuse the key buffer for camera ids

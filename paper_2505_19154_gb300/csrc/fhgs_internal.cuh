@@ -202,6 +202,7 @@ struct BinScratch {
     int *close;                           // list cut: per tile, the last segment it takes
     uint32_t *partials;                   // scan partials of the table
     uint32_t *hist;                       // radix histogram [256][G]
+    uint32_t *kbits;                      // AND and OR of the live depth keys (passes that can be skipped)
     int seg, nseg, sm_count;              // segment size, segments per camera
 };
 size_t bin_scratch_bytes(long long N, int n_cams, int total_tiles, int sm_count);
