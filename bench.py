@@ -188,10 +188,10 @@ def composited_pairs(st, cams, tile=16):
 # source file at capture time: a changed source reports null.
 _CROP_SCALE = (1920 * 1080) / (960 * 544)
 TRAFFIC = {
-    "render_bwd_tc": {"bytes": int((1102.7e6 + 7.6e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "85cbe8ce1091a39704b17f2ef8bf70e7bdab44a620471f6410bea418bf1403df"},
-    "render_fwd_tc": {"bytes": int((7.7e6 + 1022.9e6) * _CROP_SCALE), "file": "render_tc.cu",
-                      "sha256": "85cbe8ce1091a39704b17f2ef8bf70e7bdab44a620471f6410bea418bf1403df"},
+    "render_bwd_tc": {"bytes": int((1102.9e6 + 4.4e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "c88f555d2cb5d4e5fd98c657635ffc014556065435a7ed9bc11683facf6a2135"},
+    "render_fwd_tc": {"bytes": int((7.6e6 + 1021.6e6) * _CROP_SCALE), "file": "render_tc.cu",
+                      "sha256": "c88f555d2cb5d4e5fd98c657635ffc014556065435a7ed9bc11683facf6a2135"},
 }
 
 
