@@ -328,13 +328,13 @@ __device__ __forceinline__ uint32_t cut_units(float op, float q, float amin, flo
 }
 
 __global__ void __launch_bounds__(256) k_gather_rects(const uint32_t *__restrict__ order, ProjView pv, long long cn,
-                                                      int4 *rect, int4 *inner, uint32_t *imass, Params p) {
+                                                      short4 *rect, int4 *inner, uint32_t *imass, Params p) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cn) return;
     const uint32_t e = order[i];
     const bool live = pv.ntiles[e] != 0u;
     const int4 r = live ? pv.trect[e] : make_int4(0, 0, -1, -1);
-    rect[i] = r;
+    rect[i] = make_short4((short)r.x, (short)r.y, (short)r.z, (short)r.w);  // tile coordinates fit in 16 bits
     if (inner == nullptr) return;
     // the two boxes |dx| <= a, |dy| <= b with b = a sqrt(A/C): their corners
     // give q2 = 2 a^2 (A + |B| sqrt(A/C)) = q
@@ -380,7 +380,7 @@ __device__ __forceinline__ void add_box(int *d, int pitch, uint32_t rx, uint32_t
 // With the list cut (CUT) the same pass sums the segment's opacity mass per
 // tile (a second difference array over the nested boxes) into mass[].
 template <bool CUT>
-__global__ void __launch_bounds__(256) k_seg_count(const int4 *__restrict__ rect, const int4 *__restrict__ inner,
+__global__ void __launch_bounds__(256) k_seg_count(const short4 *__restrict__ rect, const int4 *__restrict__ inner,
                                                    const uint32_t *__restrict__ imass, long long N, int SEG, int S,
                                                    CamSet cs, uint32_t *table, uint32_t *mass) {
     extern __shared__ int diff[];
@@ -397,7 +397,8 @@ __global__ void __launch_bounds__(256) k_seg_count(const int4 *__restrict__ rect
     const long long b0 = (long long)ci * N + (long long)seg * SEG;
     const long long b1 = min((long long)(ci + 1) * N, b0 + SEG);
     for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-        const int4 r = rect[i];
+        const short4 sr = rect[i];
+        const int4 r = make_int4(sr.x, sr.y, sr.z, sr.w);
         if (r.w < r.y) continue;
         atomicAdd(&diff[r.y * pitch + r.x], 1);
         atomicAdd(&diff[r.y * pitch + r.z + 1], -1);
@@ -540,7 +541,7 @@ constexpr int kScatterStageWords = kStage * 7;  // staged rectangles, indices an
 // sectors per write burst); bands restore the parallelism.  Within one
 // Gaussian all tiles differ, so the 32 lanes update distinct counters.
 __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32_t *__restrict__ order,
-                                                                     const int4 *__restrict__ rect,
+                                                                     const short4 *__restrict__ rect,
                                                                      long long N, int SEG, int S, int nband,
                                                                      int band_rows, CamSet cs,
                                                                      const uint32_t *__restrict__ table, uint32_t *gids,
@@ -574,7 +575,8 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32
             int4 r = make_int4(0, 0, -1, -1);
             uint32_t e = 0;
             if (k < m) {
-                r = rect[c0 + k];
+                const short4 sr = rect[c0 + k];
+                r = make_int4(sr.x, sr.y, sr.z, sr.w);
                 e = order[c0 + k];
                 r.y = max(r.y, by0);
                 r.w = min(r.w, by1 - 1);
@@ -656,7 +658,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32
 // left of x), a staged Gaussian's pairs are the open tiles of its x range in
 // order, and a warp whose row has no open tile leaves at once.
 __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter_cut(const uint32_t *__restrict__ order,
-                                                                         const int4 *__restrict__ rect, long long N,
+                                                                         const short4 *__restrict__ rect, long long N,
                                                                          int SEG, int S, int max_ty, int row_words,
                                                                          CamSet cs, const int *__restrict__ close,
                                                                          const uint32_t *__restrict__ table,
@@ -705,7 +707,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter_cut(const ui
             const int k = k0 + lane;
             uint32_t o0 = 0, cnt = 0, e = 0;
             if (k < m) {
-                const int4 r = rect[c0 + k];
+                const short4 r = rect[c0 + k];
                 if (r.y <= row && row <= r.w) {
                     o0 = opre[r.x];
                     cnt = opre[r.z + 1] - o0;
@@ -809,7 +811,8 @@ size_t bin_scratch_bytes(long long N, int n_cams, int total_tiles, int sm_count)
     const long long S = (N + SEG - 1) / SEG;
     const long long tab = (long long)total_tiles * (S > 0 ? S : 1);
     const int G = 2 * sm_count;
-    return 5 * align_up(sizeof(uint32_t) * (cn + 1), 256) + 2 * align_up(sizeof(int4) * (cn + 1), 256) +
+    return 5 * align_up(sizeof(uint32_t) * (cn + 1), 256) + align_up(sizeof(int4) * (cn + 1), 256) +
+           align_up(sizeof(short4) * (cn + 1), 256) +
            2 * align_up(sizeof(uint32_t) * (tab + 1), 256) + align_up(sizeof(int) * (total_tiles + 1), 256) +
            align_up(sizeof(uint32_t) * ((tab + kScanTile - 1) / kScanTile + 1), 256) +
            align_up(sizeof(uint32_t) * kBuckets * (size_t)G, 256) + 256 + 256;
@@ -831,7 +834,7 @@ BinScratch bin_scratch_view(void *base, long long N, int n_cams, int total_tiles
     s.dv_a = take(sizeof(uint32_t) * (cn + 1));
     s.dk_b = take(sizeof(uint32_t) * (cn + 1));
     s.dv_b = take(sizeof(uint32_t) * (cn + 1));
-    s.rect = reinterpret_cast<int4 *>(take(sizeof(int4) * (cn + 1)));
+    s.rect = reinterpret_cast<short4 *>(take(sizeof(short4) * (cn + 1)));
     s.inner = reinterpret_cast<int4 *>(take(sizeof(int4) * (cn + 1)));
     s.imass = take(sizeof(uint32_t) * (cn + 1));
     s.table = take(sizeof(uint32_t) * (tab + 1));

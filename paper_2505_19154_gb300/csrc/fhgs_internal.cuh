@@ -194,7 +194,7 @@ void launch_project_bwd(const fhgs_gaussians &g, const CamSet &cs, const Params 
 // binning (binning.cu)
 struct BinScratch {
     uint32_t *dk_a, *dv_a, *dk_b, *dv_b;  // depth sort [C*N]
-    int4 *rect;                           // tile rectangles in sorted order [C*N]
+    short4 *rect;                         // tile rectangles in sorted order [C*N]
     int4 *inner;                          // list cut: the nested boxes' tile ranges in sorted order [C*N]
     uint32_t *imass;                      // list cut: their opacity-mass units [C*N]
     uint32_t *table;                      // per (tile, segment) counts, then offsets
