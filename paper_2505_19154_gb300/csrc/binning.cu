@@ -570,17 +570,21 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter(const uint32
         __syncwarp();
         // stage only the Gaussians that touch the band, in order (ballot compaction)
         int mt = 0;
-        for (int k0 = 0; k0 < m; k0 += 32) {
-            const int k = k0 + lane;
-            int4 r = make_int4(0, 0, -1, -1);
-            uint32_t e = 0;
-            if (k < m) {
-                const short4 sr = rect[c0 + k];
-                r = make_int4(sr.x, sr.y, sr.z, sr.w);
-                e = order[c0 + k];
-                r.y = max(r.y, by0);
-                r.w = min(r.w, by1 - 1);
-            }
+        // the stage's rectangles and indices are requested together
+        short4 rs[kStage / 32];
+        uint32_t es[kStage / 32];
+#pragma unroll
+        for (int u = 0; u < kStage / 32; ++u) {
+            const int k = u * 32 + lane;
+            rs[u] = k < m ? rect[c0 + k] : make_short4(0, 0, -1, -1);
+            es[u] = k < m ? order[c0 + k] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kStage / 32; ++u) {
+            int4 r = make_int4(rs[u].x, rs[u].y, rs[u].z, rs[u].w);
+            const uint32_t e = es[u];
+            r.y = max(r.y, by0);
+            r.w = min(r.w, by1 - 1);
             const bool touch = r.w >= r.y;
             const uint32_t bal = __ballot_sync(0xffffffffu, touch);
             if (touch) {
@@ -703,16 +707,22 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter_cut(const ui
         const int m = (int)min((long long)kStage, b1 - c0);
         __syncwarp();
         int mt = 0;
-        for (int k0 = 0; k0 < m; k0 += 32) {
-            const int k = k0 + lane;
+        // the stage's rectangles are requested together: four loads in flight
+        short4 rs[kStage / 32];
+#pragma unroll
+        for (int u = 0; u < kStage / 32; ++u) {
+            const int k = u * 32 + lane;
+            rs[u] = k < m ? rect[c0 + k] : make_short4(0, 0, -1, -1);
+        }
+#pragma unroll
+        for (int u = 0; u < kStage / 32; ++u) {
+            const int k = u * 32 + lane;
             uint32_t o0 = 0, cnt = 0, e = 0;
-            if (k < m) {
-                const short4 r = rect[c0 + k];
-                if (r.y <= row && row <= r.w) {
-                    o0 = opre[r.x];
-                    cnt = opre[r.z + 1] - o0;
-                    e = order[c0 + k];
-                }
+            const short4 r = rs[u];
+            if (r.y <= row && row <= r.w) {
+                o0 = opre[r.x];
+                cnt = opre[r.z + 1] - o0;
+                e = order[c0 + k];
             }
             const bool touch = cnt > 0u;
             const uint32_t bal = __ballot_sync(0xffffffffu, touch);
