@@ -58,11 +58,20 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t 
     const long long s = blockIdx.x * seg, e = min(n, s + seg);
     const int w = threadIdx.x >> 5;
     const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
-    for (long long i0 = s; i0 < e; i0 += kRadixThreads) {
-        const long long i = i0 + threadIdx.x;
-        const int d = i < e ? (int)((keys[i] >> shift) & mask) : (kBuckets + (int)(threadIdx.x & 31));
-        const unsigned peers = __match_any_sync(0xffffffffu, d);  // one shared add per distinct digit
-        if (d < kBuckets && (peers & lt) == 0) atomicAdd(&h[w][d], (uint32_t)__popc(peers));
+    for (long long i0 = s; i0 < e; i0 += kRadixTile) {
+        uint32_t kk[kRadixRounds];  // the tile's keys requested together
+#pragma unroll
+        for (int r = 0; r < kRadixRounds; ++r) {
+            const long long i = i0 + r * kRadixThreads + threadIdx.x;
+            kk[r] = i < e ? keys[i] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kRadixRounds; ++r) {
+            const long long i = i0 + r * kRadixThreads + threadIdx.x;
+            const int d = i < e ? (int)((kk[r] >> shift) & mask) : (kBuckets + (int)(threadIdx.x & 31));
+            const unsigned peers = __match_any_sync(0xffffffffu, d);  // one shared add per distinct digit
+            if (d < kBuckets && (peers & lt) == 0) atomicAdd(&h[w][d], (uint32_t)__popc(peers));
+        }
     }
     __syncthreads();
     for (int d = threadIdx.x; d < kBuckets; d += kRadixThreads) {
