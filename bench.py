@@ -845,7 +845,7 @@ def run_ndfd(args):
 
     def step():
         st = rast.prepare(*g, cams, check=False)
-        rast.ndfd_forward(st, feats, fgt)
+        rast.ndfd_forward(st, feats, fgt, save_state=True)  # the backward reads the walk's end state
         rast.ndfd_backward(st, feats, fgt, dLgt, dLcf)
 
     W_ = max(3, args.warmup)

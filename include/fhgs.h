@@ -365,10 +365,25 @@ fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void 
  * (the ray-plane solve of Sec. 3.1, the paper's own combination); the
  * tensor-core kernels then take BF16 features at D = 512 only (FHGS_PATH_TC
  * with any other D is FHGS_ERR_UNSUPPORTED). */
+/* The walk's end state of an NDFD forward, which the backward can read
+ * instead of rebuilding it front to back (App. A records F_{N-1} and W_{N-1}
+ * for the same purpose): per pixel the feature sum F_N = sum_i w_i f_i over
+ * all contributors [P][D] float32 (16-byte aligned), T after the walk [P]
+ * float32 and the last contributor's list position + 1 [P] int32.  All
+ * device, caller-owned.  Only the tensor-core NDFD kernels write and read it
+ * (BF16 features, EWA at D = 256 or 512, surfels at D = 512); the CUDA-core
+ * kernels ignore it.  fhgs_ndfd_bwd may be given it only after fhgs_ndfd_fwd
+ * wrote it for the same Gaussians, lists, features, cameras and parameters. */
+typedef struct fhgs_ndfd_state {
+    float *F;
+    float *T;
+    int32_t *last;
+} fhgs_ndfd_state;
+
 fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_bins *bins, const void *features,
                           const void *feat_gt, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
                           const fhgs_params *p, float k, float lambda, float *L_gt, float *L_cf, int32_t *n_contrib,
-                          void *stream);
+                          const fhgs_ndfd_state *save, void *stream);
 
 /* Derivative of L = sum_p grad_Lgt[p] L_gt(p) + grad_Lcf[p] L_cf(p) with
  * respect to the Gaussian parameters, through the weights w only (features
@@ -390,7 +405,8 @@ fhgs_status fhgs_ndfd_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *pr
                           const void *features, const void *feat_gt, fhgs_dtype ftype, int D,
                           const fhgs_camera *cams, int n_cams, const fhgs_params *p, float k, float lambda,
                           const float *grad_Lgt, const float *grad_Lcf, float *grad_means, float *grad_scales,
-                          float *grad_quats, float *grad_opac, float *grad_sh, void *stream);
+                          float *grad_quats, float *grad_opac, float *grad_sh, const fhgs_ndfd_state *saved,
+                          void *stream);
 
 /* ----------------------------------------------------- allocation-free -- */
 /* Largest n_cams * n accepted by fhgs_render_bwd_noalloc.  Its scratch is

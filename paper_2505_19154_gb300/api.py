@@ -70,6 +70,11 @@ class Bins(ctypes.Structure):
                 ("n_instances", ctypes.c_void_p), ("capacity", ctypes.c_int64)]
 
 
+class NdfdState(ctypes.Structure):
+    """fhgs_ndfd_state: the NDFD forward's end state (F_N, T, last contributor) for its backward."""
+    _fields_ = [("F", ctypes.c_void_p), ("T", ctypes.c_void_p), ("last", ctypes.c_void_p)]
+
+
 class FhgsError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"fhgs status {status}: {msg}")
@@ -128,10 +133,10 @@ def lib():
         L.fhgs_debug_wait_probe.restype = i32
         f32 = ctypes.c_float
         L.fhgs_ndfd_fwd.argtypes = [vp, i64, vp, ctypes.POINTER(Bins), vp, vp, i32, i32, ctypes.POINTER(Camera), i32,
-                                    ctypes.POINTER(Params), f32, f32, f32p, f32p, vp, vp]
+                                    ctypes.POINTER(Params), f32, f32, f32p, f32p, vp, ctypes.POINTER(NdfdState), vp]
         L.fhgs_ndfd_bwd.argtypes = [vp, ctypes.POINTER(Gaussians), vp, ctypes.POINTER(Bins), vp, vp, i32, i32,
                                     ctypes.POINTER(Camera), i32, ctypes.POINTER(Params), f32, f32, f32p, f32p,
-                                    f32p, f32p, f32p, f32p, f32p, vp]
+                                    f32p, f32p, f32p, f32p, f32p, ctypes.POINTER(NdfdState), vp]
         L.fhgs_point_features.argtypes = [vp, i64, f32p, ctypes.POINTER(Camera), i32, ctypes.POINTER(ctypes.c_void_p),
                                           i32, f32p, ctypes.POINTER(Params), f32p, vp, vp, vp]
         L.fhgs_l1_loss.argtypes = [vp, i64, f32p, f32p, f32, f32p, f32p, vp]
@@ -276,20 +281,28 @@ class Context:
 
 
     def ndfd_fwd(self, n, proj, bins, features, feat_gt, D, cams, params, k, lam, Lgt, Lcf, ncontrib=None,
-                 stream=None):
+                 state=None, stream=None):
+        """state: optional dict of F [P, D], T [P], last [P] tensors that
+        receive the walk's end state (tensor-core kernels only)."""
         ft = BF16 if features.dtype == torch.bfloat16 else F32
+        sv = None if state is None else ctypes.byref(_ndfd_state(state))
         self.check(lib().fhgs_ndfd_fwd(self.h, int(n), _ptr(proj), ctypes.byref(bins), _ptr(features), _ptr(feat_gt),
                                        ft, int(D), cams, len(cams), ctypes.byref(params), float(k), float(lam),
-                                       _ptr(Lgt), _ptr(Lcf), _ptr(ncontrib), self.stream_ptr(stream)))
+                                       _ptr(Lgt), _ptr(Lcf), _ptr(ncontrib), sv, self.stream_ptr(stream)))
 
     def ndfd_bwd(self, g, proj, bins, features, feat_gt, D, cams, params, k, lam, dLgt, dLcf, out: dict,
-                 stream=None):
+                 state=None, stream=None):
         ft = BF16 if features.dtype == torch.bfloat16 else F32
+        sv = None if state is None else ctypes.byref(_ndfd_state(state))
         self.check(lib().fhgs_ndfd_bwd(self.h, ctypes.byref(g), _ptr(proj), ctypes.byref(bins), _ptr(features),
                                        _ptr(feat_gt), ft, int(D), cams, len(cams), ctypes.byref(params), float(k),
                                        float(lam), _ptr(dLgt), _ptr(dLcf), _ptr(out["means"]), _ptr(out["scales"]),
-                                       _ptr(out["quats"]), _ptr(out["opacities"]), _ptr(out["sh"]),
+                                       _ptr(out["quats"]), _ptr(out["opacities"]), _ptr(out["sh"]), sv,
                                        self.stream_ptr(stream)))
+
+
+def _ndfd_state(state: dict) -> NdfdState:
+    return NdfdState(state["F"].data_ptr(), state["T"].data_ptr(), state["last"].data_ptr())
 
 
 def point_features(ctx: "Context", means, views: Sequence[dict], maps: Sequence[torch.Tensor], u, params: Params,
@@ -492,16 +505,27 @@ class Rasterizer:
         return out
 
     def ndfd_forward(self, st: dict, features, feat_gt, k: float = NDFD_K, lam: float = NDFD_LAMBDA,
-                     ncontrib=None):
+                     ncontrib=None, save_state: bool = False):
         """Per-pixel NDFD losses (L_gt, L_cf), each [P] float32, over the
         prepared views; feat_gt is [P, D] in the features' dtype.  ncontrib,
-        an optional [P] int32 tensor, receives each pixel's contributor count."""
+        an optional [P] int32 tensor, receives each pixel's contributor count.
+        save_state keeps the walk's end state (F_N [P, D] FP32, T, last) in
+        st, where ndfd_backward reads it instead of rebuilding it; the
+        CUDA-core kernels neither write nor read it."""
         P = sum(int(c.width) * int(c.height) for c in st["cams"])
         D = int(features.shape[1])
         Lgt = torch.empty(P, dtype=torch.float32, device=self.dev)
         Lcf = torch.empty(P, dtype=torch.float32, device=self.dev)
+        state = None
+        st.pop("ndfd_state", None)
+        if save_state:
+            state = dict(F=torch.empty((P, D), dtype=torch.float32, device=self.dev),
+                         T=torch.empty(P, dtype=torch.float32, device=self.dev),
+                         last=torch.empty(P, dtype=torch.int32, device=self.dev))
         self.ctx.ndfd_fwd(st["n"], st["proj"], st["bins"], features, feat_gt.contiguous(), D, st["cams"], self.params,
-                          k, lam, Lgt, Lcf, ncontrib)
+                          k, lam, Lgt, Lcf, ncontrib, state)
+        if state is not None:
+            st["ndfd_state"] = state
         return Lgt, Lcf
 
     def ndfd_backward(self, st: dict, features, feat_gt, grad_Lgt, grad_Lcf, k: float = NDFD_K,
@@ -514,7 +538,8 @@ class Rasterizer:
                    quats=torch.empty((n, 4), device=self.dev), opacities=torch.empty(n, device=self.dev),
                    sh=torch.empty((n, K, 3), device=self.dev))
         self.ctx.ndfd_bwd(st["g"], st["proj"], st["bins"], features, feat_gt.contiguous(), D, st["cams"],
-                          self.params, k, lam, grad_Lgt.contiguous(), grad_Lcf.contiguous(), out)
+                          self.params, k, lam, grad_Lgt.contiguous(), grad_Lcf.contiguous(), out,
+                          st.get("ndfd_state"))
         return out
 
     def fuse(self, means, scales, quats, opacities, sh, views: Sequence[dict], maps: Sequence[torch.Tensor],

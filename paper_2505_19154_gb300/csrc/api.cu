@@ -703,13 +703,28 @@ static fhgs_status check_ndfd(fhgs_ctx *ctx, long long n, const void *proj, cons
     return FHGS_OK;
 }
 
+// An NDFD end state: NULL, or all three buffers (F 16-byte aligned).
+static fhgs_status check_ndfd_state(fhgs_ctx *ctx, const fhgs_ndfd_state *st) {
+    if (!st) return FHGS_OK;
+    if (!st->F || !st->T || !st->last) return fail(ctx, FHGS_ERR_INVALID_ARG, "NDFD state has a NULL buffer");
+    if (!aligned16(st->F)) return fail(ctx, FHGS_ERR_ALIGNMENT, "NDFD state F must be 16-byte aligned");
+    return FHGS_OK;
+}
+
+static NdfdState ndfd_state(const fhgs_ndfd_state *st) {
+    NdfdState r{nullptr, nullptr, nullptr};
+    if (st) r = NdfdState{st->F, st->T, st->last};
+    return r;
+}
+
 fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_bins *bins, const void *features,
                           const void *feat_gt, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
                           const fhgs_params *p, float k, float lambda, float *L_gt, float *L_cf, int32_t *n_contrib,
-                          void *stream) {
+                          const fhgs_ndfd_state *save, void *stream) {
     if (!ctx) return FHGS_ERR_INVALID_ARG;
     if (n < 0 || n >= (1ll << 31)) return fail(ctx, FHGS_ERR_INVALID_ARG, "bad Gaussian count");
     fhgs_status s = check_ndfd(ctx, n, proj, bins, features, feat_gt, ftype, D, p, k, lambda);
+    if (s == FHGS_OK) s = check_ndfd_state(ctx, save);
     if (s != FHGS_OK) return s;
     if (!L_gt || !L_cf) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL output buffer");
     CamSet cs;
@@ -721,7 +736,7 @@ fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs
     if (ndfd_use_tc(p, ftype, D)) {
         Prof pr(ctx, p->geometry == FHGS_GEOM_SURFEL ? "ndfd_fwd_tc_surfel" : "ndfd_fwd_tc", st);
         launch_ndfd_fwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, (const __nv_bfloat16 *)feat_gt, D, k,
-                           lambda, L_gt, L_cf, n_contrib, ctx->status, st);
+                           lambda, L_gt, L_cf, n_contrib, ndfd_state(save), ctx->status, st);
     } else {
         Prof pr(ctx, p->geometry == FHGS_GEOM_SURFEL ? "ndfd_fwd_surfel" : "ndfd_fwd", st);
         launch_ndfd_fwd(n, cs, q, pv, *bins, features, feat_gt, ftype == FHGS_BF16, D, k, lambda, L_gt, L_cf, n_contrib, st);
@@ -734,10 +749,12 @@ fhgs_status fhgs_ndfd_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *pr
                           const void *features, const void *feat_gt, fhgs_dtype ftype, int D,
                           const fhgs_camera *cams, int n_cams, const fhgs_params *p, float k, float lambda,
                           const float *grad_Lgt, const float *grad_Lcf, float *grad_means, float *grad_scales,
-                          float *grad_quats, float *grad_opac, float *grad_sh, void *stream) {
+                          float *grad_quats, float *grad_opac, float *grad_sh, const fhgs_ndfd_state *saved,
+                          void *stream) {
     if (!ctx) return FHGS_ERR_INVALID_ARG;
     fhgs_status s = check_gaussians(ctx, g, true);
     if (s == FHGS_OK) s = check_ndfd(ctx, g->n, proj, bins, features, feat_gt, ftype, D, p, k, lambda);
+    if (s == FHGS_OK) s = check_ndfd_state(ctx, saved);
     if (s != FHGS_OK) return s;
     if (!grad_Lgt || !grad_Lcf) return fail(ctx, FHGS_ERR_INVALID_ARG, "NULL input buffer");
     if (g->n > 0 && (!grad_means || !grad_scales || !grad_quats || !grad_opac || !grad_sh))
@@ -758,7 +775,7 @@ fhgs_status fhgs_ndfd_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *pr
     if (ndfd_use_tc(p, ftype, D)) {
         Prof pr(ctx, surfel ? "ndfd_bwd_tc_surfel" : "ndfd_bwd_tc", st);
         launch_ndfd_bwd_tc(n, cs, q, pv, *bins, (const __nv_bfloat16 *)features, (const __nv_bfloat16 *)feat_gt, D, k,
-                           lambda, grad_Lgt, grad_Lcf, g2d, ctx->status, st);
+                           lambda, grad_Lgt, grad_Lcf, g2d, ndfd_state(saved), ctx->status, st);
     } else {
         Prof pr(ctx, surfel ? "ndfd_bwd_surfel" : "ndfd_bwd", st);
         launch_ndfd_bwd(n, cs, q, pv, *bins, features, feat_gt, ftype == FHGS_BF16, D, k, lambda, grad_Lgt,

@@ -301,12 +301,21 @@ void launch_ndfd_bwd(long long N, const CamSet &cs, const Params &p, ProjView pv
 // in {256, 512} (EWA) or 512 (surfels), split over a cluster of D / 128 CTAs;
 // g2d has 12 (EWA) or kSurfelG2d (surfel) floats per (camera, primitive)
 bool ndfd_tc_supported(int D, int geom);
+// The walk's end state of the tensor-core NDFD forward (F == nullptr: none):
+// F_N [P][D], T after the walk [P], last contributor + 1 [P].
+struct NdfdState {
+    float *F;
+    float *T;
+    int32_t *last;
+};
 void launch_ndfd_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                         const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam, float *Lgt,
-                        float *Lcf, int32_t *nc, unsigned *status, cudaStream_t st);
-// g2d: 12 floats per (camera, Gaussian), accumulated (zero it first)
+                        float *Lcf, int32_t *nc, NdfdState save, unsigned *status, cudaStream_t st);
+// g2d: 12 floats per (camera, Gaussian), accumulated (zero it first);
+// saved.F != nullptr: the forward's end state replaces the front-to-back rebuild
 void launch_ndfd_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                         const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam,
-                        const float *dLgt, const float *dLcf, float *g2d, unsigned *status, cudaStream_t st);
+                        const float *dLgt, const float *dLcf, float *g2d, NdfdState saved, unsigned *status,
+                        cudaStream_t st);
 
 }  // namespace fhgs

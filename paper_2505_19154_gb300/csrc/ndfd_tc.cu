@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(256, 1)
     k_ndfd_fwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                   const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats,
                   const __nv_bfloat16 *__restrict__ fgt, float ks, float lam, float *Lgt_out, float *Lcf_out,
-                  int32_t *nc_out, unsigned *status) {
+                  int32_t *nc_out, NdfdState save, unsigned *status) {
     using C = NCfg<NC, GEOM>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
@@ -833,6 +833,30 @@ __global__ void __launch_bounds__(256, 1)
             Lgt_out[opix] = S.acc(0)[tid];
             Lcf_out[opix] = S.acc(1)[tid];
             if (nc_out) nc_out[opix] = (int32_t)S.acc(2)[tid];
+        }
+    }
+    if (save.F != nullptr && !timeout && !skip) {
+        // the walk's end state for the backward: F_N of this CTA's 128
+        // channels (TMEM lane = pixel; group g takes columns 64 g ..), and T
+        // and the last contributor, which every CTA of the cluster holds alike
+        tc_after();
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+        const int c0 = grp * 64;
+        float *dst = save.F + pix * (long long)(NC * 128) + q * 128 + c0;
+#pragma unroll 1
+        for (int j = 0; j < 2; ++j) {
+            float v[32];
+            tmem_ld32(taddr + C::kColF + lanes + c0 + 32 * j, v);
+            if (inside) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    reinterpret_cast<float4 *>(dst + 32 * j)[k] =
+                        make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            }
+        }
+        if (q == 0 && grp == 0 && inside) {
+            save.T[pix] = ps.T[pidx];
+            save.last[pix] = ps.last[pidx];
         }
     }
     tc_before();
@@ -1158,7 +1182,7 @@ __global__ void __launch_bounds__(256, 1)
     k_ndfd_bwd_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
                   const uint32_t *__restrict__ ranges, const __nv_bfloat16 *__restrict__ feats,
                   const __nv_bfloat16 *__restrict__ fgt, float ks, float lam, const float *__restrict__ dLgt,
-                  const float *__restrict__ dLcf, float *g2d, unsigned *status) {
+                  const float *__restrict__ dLcf, float *g2d, NdfdState saved, unsigned *status) {
     using C = NBCfg<NC, GEOM>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align_smem_1024(smem_raw);
@@ -1241,8 +1265,35 @@ __global__ void __launch_bounds__(256, 1)
     bool timeout = false;
     int pend = -1;  // a commit barrier whose phase `pend_ph` may still be in flight
     uint32_t pend_ph = 0;
-    // ---- pass A: F_N, T after the walk and the last contributors, front to back
-    for (int b = 0; b < nlist; ++b) {
+    // ---- pass A: F_N, T after the walk and the last contributors, front to
+    // back; or, when the forward saved them, read back
+    if (saved.F != nullptr && !skip) {
+        if (grp == 0) {
+            ps.T[pidx] = inside ? saved.T[pix] : 1.f;
+            ps.last[pidx] = inside ? saved.last[pix] : 0;
+        }
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+        const int c0 = grp * 64;
+        const float4 *src = reinterpret_cast<const float4 *>(saved.F + pix * (long long)(NC * 128) + q * 128 + c0);
+        float4 x[16];  // the pixel's 64 channels, all requested before the first TMEM store
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = inside ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t v[16];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[4 * k] = __float_as_uint(x[4 * j + k].x);
+                v[4 * k + 1] = __float_as_uint(x[4 * j + k].y);
+                v[4 * k + 2] = __float_as_uint(x[4 * j + k].z);
+                v[4 * k + 3] = __float_as_uint(x[4 * j + k].w);
+            }
+            tmem_st16(tF + lanes + c0 + 16 * j, v);
+        }
+        tmem_st_wait();
+        tc_before();  // the stores precede the MMAs on F after the barrier below
+    }
+    for (int b = 0; b < ((saved.F != nullptr) ? 0 : nlist); ++b) {
         const uint32_t base = it.s + (uint32_t)b * kC;
         const int nb = (int)min((uint32_t)kC, it.e - base);
         L.features(b);  // its stage was last read by the previous chunk's update, complete
@@ -1457,23 +1508,23 @@ void launch_cluster(void (*kernel)(Args...), int smem, unsigned n_items, cudaStr
 template <int NC, int GEOM>
 void launch_fwd_tc_t(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                      const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, float ks, float lam, float *Lgt,
-                     float *Lcf, int32_t *nc, unsigned *status, cudaStream_t st) {
+                     float *Lcf, int32_t *nc, NdfdState save, unsigned *status, cudaStream_t st) {
     static std::atomic<unsigned long long> smem_set{0};
     allow_max_smem(smem_set, k_ndfd_fwd_tc<NC, GEOM>);
     launch_cluster<NC>(k_ndfd_fwd_tc<NC, GEOM>, NCfg<NC, GEOM>::kSmem, (unsigned)cs.total_tiles * 2u, st, N, cs, p, pv,
                        (const uint32_t *)bins.gids, (const uint32_t *)bins.ranges, feats, fgt, ks, lam, Lgt, Lcf, nc,
-                       status);
+                       save, status);
 }
 
 template <int NC, int GEOM>
 void launch_bwd_tc_t(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                      const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, float ks, float lam, const float *dLgt,
-                     const float *dLcf, float *g2d, unsigned *status, cudaStream_t st) {
+                     const float *dLcf, float *g2d, NdfdState saved, unsigned *status, cudaStream_t st) {
     static std::atomic<unsigned long long> smem_set{0};
     allow_max_smem(smem_set, k_ndfd_bwd_tc<NC, GEOM>);
     launch_cluster<NC>(k_ndfd_bwd_tc<NC, GEOM>, NBCfg<NC, GEOM>::kSmem, (unsigned)cs.total_tiles * 2u, st, N, cs, p, pv,
                        (const uint32_t *)bins.gids, (const uint32_t *)bins.ranges, feats, fgt, ks, lam, dLgt, dLcf,
-                       g2d, status);
+                       g2d, saved, status);
 }
 
 }  // namespace
@@ -1484,29 +1535,32 @@ bool ndfd_tc_supported(int D, int geom) {
 
 void launch_ndfd_bwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                         const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam,
-                        const float *dLgt, const float *dLcf, float *g2d, unsigned *status, cudaStream_t st) {
+                        const float *dLgt, const float *dLcf, float *g2d, NdfdState saved, unsigned *status,
+                        cudaStream_t st) {
     if (cs.total_tiles == 0) return;
     if (p.geom == FHGS_GEOM_SURFEL) {
         if (D == 512)
-            launch_bwd_tc_t<4, FHGS_GEOM_SURFEL>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, status, st);
+            launch_bwd_tc_t<4, FHGS_GEOM_SURFEL>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, saved,
+                                                 status, st);
     } else if (D == 512) {
-        launch_bwd_tc_t<4, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, status, st);
+        launch_bwd_tc_t<4, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, saved, status, st);
     } else if (D == 256) {
-        launch_bwd_tc_t<2, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, status, st);
+        launch_bwd_tc_t<2, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, dLgt, dLcf, g2d, saved, status, st);
     }
 }
 
 void launch_ndfd_fwd_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
                         const __nv_bfloat16 *feats, const __nv_bfloat16 *fgt, int D, float ks, float lam, float *Lgt,
-                        float *Lcf, int32_t *nc, unsigned *status, cudaStream_t st) {
+                        float *Lcf, int32_t *nc, NdfdState save, unsigned *status, cudaStream_t st) {
     if (cs.total_tiles == 0) return;
     if (p.geom == FHGS_GEOM_SURFEL) {
         if (D == 512)
-            launch_fwd_tc_t<4, FHGS_GEOM_SURFEL>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, status, st);
+            launch_fwd_tc_t<4, FHGS_GEOM_SURFEL>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, save, status,
+                                                 st);
     } else if (D == 512) {
-        launch_fwd_tc_t<4, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, status, st);
+        launch_fwd_tc_t<4, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, save, status, st);
     } else if (D == 256) {
-        launch_fwd_tc_t<2, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, status, st);
+        launch_fwd_tc_t<2, FHGS_GEOM_EWA>(N, cs, p, pv, bins, feats, fgt, ks, lam, Lgt, Lcf, nc, save, status, st);
     }
 }
 

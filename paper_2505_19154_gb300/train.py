@@ -98,7 +98,8 @@ class LibraryBackend:
         return loss, grad
 
     def ndfd(self, st, features, feat_gt):
-        return self.rast.ndfd_forward(st, features, feat_gt)
+        # keep the walk's end state for ndfd_backward of the same iteration
+        return self.rast.ndfd_forward(st, features, feat_gt, save_state=True)
 
     def total(self, x):
         return self.api.sum_f32(self.rast.ctx, x)

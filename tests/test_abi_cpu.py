@@ -80,9 +80,9 @@ def test_null_context_is_rejected(L):
     assert L.fhgs_reserve(None, 1, None, 1) == api.ERR_INVALID_ARG
     assert L.fhgs_project(None, None, None, 0, ctypes.byref(p), None, None) == api.ERR_INVALID_ARG
     assert L.fhgs_ndfd_fwd(None, 0, None, None, None, None, 0, 64, None, 1, ctypes.byref(p), 20.0, 0.5, None, None,
-                           None, None) == api.ERR_INVALID_ARG
+                           None, None, None) == api.ERR_INVALID_ARG
     assert L.fhgs_ndfd_bwd(None, None, None, None, None, None, 0, 64, None, 1, ctypes.byref(p), 20.0, 0.5, None, None,
-                           None, None, None, None, None, None) == api.ERR_INVALID_ARG
+                           None, None, None, None, None, None, None) == api.ERR_INVALID_ARG
 
 
 def test_new_calls_reject_a_null_context_and_size_the_adam_state(L):

@@ -45,7 +45,7 @@ def tc_expected(D, bf16, path):
     return bf16 and D in (256, 512) and path != api.PATH_FP32
 
 
-def run_ndfd(sc, cams, prm, fg, bf16=True, grads=None, path=api.PATH_AUTO):
+def run_ndfd(sc, cams, prm, fg, bf16=True, grads=None, path=api.PATH_AUTO, save_state=False):
     dt = torch.bfloat16 if bf16 else torch.float32
     rast = api.Rasterizer(0, sh_degree=prm.get("sh_degree", 0), path=path)
     t = {k: _t(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
@@ -54,8 +54,10 @@ def run_ndfd(sc, cams, prm, fg, bf16=True, grads=None, path=api.PATH_AUTO):
     rast.ctx.profile(True)
     st = rast.prepare(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cams)
     nc = torch.empty(gt.shape[0], dtype=torch.int32, device=gt.device)
-    Lgt, Lcf = rast.ndfd_forward(st, feats, gt, ncontrib=nc)
+    Lgt, Lcf = rast.ndfd_forward(st, feats, gt, ncontrib=nc, save_state=save_state)
     out = dict(Lgt=Lgt.cpu().numpy(), Lcf=Lcf.cpu().numpy(), nc=nc.cpu().numpy())
+    if save_state:
+        out["state"] = {k: v.cpu().numpy() for k, v in st["ndfd_state"].items()}
     if grads is not None:
         g = rast.ndfd_backward(st, feats, gt, _t(grads[0]), _t(grads[1]))
         out["grads"] = {k: v.cpu().numpy() for k, v in g.items()}
@@ -173,6 +175,45 @@ def test_ndfd_backward_tensor_core_ragged_multicamera_long_lists(D):
     ref = oracle.ndfd_backward(sc, cams, prm, sc["features"], fg, [a[offs[i]:offs[i + 1]] for i in range(3)],
                                [b[offs[i]:offs[i + 1]] for i in range(3)], prep=prep)
     check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities"), tol=1e-3)
+
+
+@pytest.mark.parametrize("D", [256, 512])
+def test_ndfd_backward_from_saved_state(D):
+    """The forward's saved end state (F_N, T after the walk, last
+    contributor) in place of the backward's front-to-back rebuild: the state
+    against the oracle's render of the same scene (F_N = sum w f, T_final,
+    last) outside its margin pixels, and the gradients against the oracle
+    and against the backward that rebuilds the state itself."""
+    cams = [synth.look_at_camera(synth.ring_position(2.4, a, e), w, h)
+            for a, e, w, h in [(10, 5, 70, 50), (140, 25, 33, 47), (260, -20, 96, 64)]]
+    sc, fg = ndfd_case(9000, 65 + D, D, cams, sh_degree=1, spread=0.45)
+    prm = dict(sh_degree=1)
+    P = [c["width"] * c["height"] for c in cams]
+    offs = np.cumsum([0] + P)
+    g = synth.rng(8, 4)
+    a = g.standard_normal(offs[-1]).astype(np.float32)
+    b = g.standard_normal(offs[-1]).astype(np.float32)
+    prep = oracle.prepare(sc, cams, prm)
+    out = run_ndfd(sc, cams, prm, fg, grads=(a, b), path=api.PATH_TC, save_state=True)
+    rebuilt = run_ndfd(sc, cams, prm, fg, grads=(a, b), path=api.PATH_TC)
+    refs = oracle.forward(sc, cams, prm, sc["features"], prep=prep)
+    state = out["state"]
+    n_margin = 0
+    for i, (cam, ref) in enumerate(zip(cams, refs)):
+        sl = slice(offs[i], offs[i + 1])
+        ok = ref["margin"].reshape(-1) > MARGIN_TOL
+        n_margin += int((~ok).sum())
+        np.testing.assert_array_equal(state["last"][sl][ok], ref["last"].reshape(-1)[ok])
+        assert np.abs(state["T"][sl] - ref["T"].reshape(-1))[ok].max(initial=0) <= 1e-5
+        F_ref = ref["feat"].reshape(-1, D)
+        assert np.abs(state["F"][sl] - F_ref)[ok].max(initial=0) <= 1e-4 * max(1.0, np.abs(F_ref).max())
+    check_margin_count(n_margin, int(offs[-1]), "NDFD state")
+    ref = oracle.ndfd_backward(sc, cams, prm, sc["features"], fg, [a[offs[i]:offs[i + 1]] for i in range(3)],
+                               [b[offs[i]:offs[i + 1]] for i in range(3)], prep=prep)
+    check_grads(out["grads"], ref, keys=("means", "scales", "quats", "opacities"), tol=1e-3)
+    for k in ("means", "scales", "quats", "opacities"):
+        x, y = out["grads"][k].astype(np.float64), rebuilt["grads"][k].astype(np.float64)
+        assert np.linalg.norm(x - y) <= 1e-5 * np.linalg.norm(y), k
 
 
 def test_ndfd_backward_multicamera():

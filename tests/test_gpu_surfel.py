@@ -265,3 +265,11 @@ def test_surfel_ndfd_losses_and_gradients(D, bf16):
     assert np.all(got["scales"][:, 2] == 0.0) and np.all(got["sh"] == 0.0)
     got["scales2"] = got["scales"][:, :2]
     check_grads(got, gr, keys=("means", "scales2", "quats", "opacities"), tol=1e-3)
+    if tc:  # the backward from the forward's saved end state gives the same gradients
+        rast.ndfd_forward(st, feats, gt, save_state=True)
+        g2 = rast.ndfd_backward(st, feats, gt, _t(a), _t(b))
+        torch.cuda.synchronize()
+        assert rast.ctx.sync_status() == api.OK
+        for k in ("means", "scales", "quats", "opacities"):
+            x, y = g2[k].cpu().numpy().astype(np.float64), got[k].astype(np.float64)
+            assert np.linalg.norm(x - y) <= 1e-5 * np.linalg.norm(y), k
