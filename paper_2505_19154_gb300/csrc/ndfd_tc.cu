@@ -169,6 +169,7 @@ struct NCfg {
     static constexpr int kSmem = 1024 + kOffBar + 64;  // 6 barriers and the TMEM slot
     static_assert(kSmem <= 232448, "NDFD CTA exceeds the opt-in shared memory");
     static_assert(8 * 32 * 20 * 4 <= kOffGh - kOffWh, "the row staging must fit in the weight operands");
+    static_assert(8 * 32 * 36 * 4 <= kOffGh, "the saved state's tiles must fit in the operand stages");
     static constexpr uint32_t kColF = 0, kColFh = 128, kColFl = 192, kColPhi = 256, kColX = 320, kColGam = 384;
 };
 
@@ -839,20 +840,35 @@ __global__ void __launch_bounds__(256, 1)
         // the walk's end state for the backward: F_N of this CTA's 128
         // channels (TMEM lane = pixel; group g takes columns 64 g ..), and T
         // and the last contributor, which every CTA of the cluster holds alike
+        // Each 32 x 32 block goes through the warp's padded tile in the operand
+        // stages (free after the walk), so that lane l then stores 16 bytes of
+        // pixel 4 i + l / 8: 128 contiguous bytes per pixel and store.
         tc_after();
         const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-        const int c0 = grp * 64;
-        float *dst = save.F + pix * (long long)(NC * 128) + q * 128 + c0;
+        const int c0 = grp * 64, sub = lane >> 3, c4 = (lane & 7) * 4;
+        float *tileb = reinterpret_cast<float *>(sm) + warp * (32 * 36);
+        long long opix[8];
+        bool oin[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float fx, fy;
+            oin[i] = item_pixel(it, (warp & 3) * 32 + 4 * i + sub, opix[i], fx, fy);
+        }
 #pragma unroll 1
         for (int j = 0; j < 2; ++j) {
             float v[32];
             tmem_ld32(taddr + C::kColF + lanes + c0 + 32 * j, v);
-            if (inside) {
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    reinterpret_cast<float4 *>(dst + 32 * j)[k] =
-                        make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-            }
+            for (int i = 0; i < 8; ++i)
+                *reinterpret_cast<float4 *>(tileb + lane * 36 + 4 * i) =
+                    make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (oin[i])
+                    *reinterpret_cast<float4 *>(save.F + opix[i] * (long long)(NC * 128) + q * 128 + c0 + 32 * j +
+                                                c4) = *reinterpret_cast<const float4 *>(tileb + (4 * i + sub) * 36 + c4);
+            __syncwarp();
         }
         if (q == 0 && grp == 0 && inside) {
             save.T[pix] = ps.T[pidx];
@@ -910,6 +926,7 @@ struct NBCfg {
     static constexpr int kOffBar = cal(kOffAcc + kC * kAcc * 4, 8);
     static constexpr int kSmem = 1024 + kOffBar + 128;      // 11 barriers, the TMEM slot, Lmax
     static_assert(kSmem <= 232448, "NDFD backward CTA exceeds the opt-in shared memory");
+    static_assert(8 * 32 * 36 * 4 <= kOffRecv - kOffF, "the saved state's tiles must fit in the free stages");
     static constexpr uint32_t kColF = 0, kColG = 128, kColA = 256, kColB = 320, kColH = 384, kColL = 448;
 };
 
@@ -1272,23 +1289,45 @@ __global__ void __launch_bounds__(256, 1)
             ps.T[pidx] = inside ? saved.T[pix] : 1.f;
             ps.last[pidx] = inside ? saved.last[pix] : 0;
         }
+        // Each 32 x 32 block of the warp's pixels and channels comes in as 128
+        // contiguous bytes per pixel and load (lane l: 16 bytes of pixel
+        // 4 i + l / 8), through the warp's padded tile in the feature, weight
+        // and Gram stages (free until pass B), then row by row into TMEM.
         const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-        const int c0 = grp * 64;
-        const float4 *src = reinterpret_cast<const float4 *>(saved.F + pix * (long long)(NC * 128) + q * 128 + c0);
-        float4 x[16];  // the pixel's 64 channels, all requested before the first TMEM store
+        const int c0 = grp * 64, sub = lane >> 3, c4 = (lane & 7) * 4;
+        float *tileb = reinterpret_cast<float *>(sm + C::kOffF) + warp * (32 * 36);
+        long long ipix[8];
+        bool iin[8];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) x[k] = inside ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = 0; i < 8; ++i) {
+            float fx, fy;
+            iin[i] = item_pixel(it, (warp & 3) * 32 + 4 * i + sub, ipix[i], fx, fy);
+        }
+#pragma unroll 1
+        for (int j = 0; j < 2; ++j) {
+            float4 x[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            uint32_t v[16];
+            for (int i = 0; i < 8; ++i)
+                x[i] = iin[i] ? *reinterpret_cast<const float4 *>(saved.F + ipix[i] * (long long)(NC * 128) + q * 128 +
+                                                                  c0 + 32 * j + c4)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                v[4 * k] = __float_as_uint(x[4 * j + k].x);
-                v[4 * k + 1] = __float_as_uint(x[4 * j + k].y);
-                v[4 * k + 2] = __float_as_uint(x[4 * j + k].z);
-                v[4 * k + 3] = __float_as_uint(x[4 * j + k].w);
+            for (int i = 0; i < 8; ++i) *reinterpret_cast<float4 *>(tileb + (4 * i + sub) * 36 + c4) = x[i];
+            __syncwarp();
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t v[16];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float4 y = *reinterpret_cast<const float4 *>(tileb + lane * 36 + 16 * h + 4 * k);
+                    v[4 * k] = __float_as_uint(y.x);
+                    v[4 * k + 1] = __float_as_uint(y.y);
+                    v[4 * k + 2] = __float_as_uint(y.z);
+                    v[4 * k + 3] = __float_as_uint(y.w);
+                }
+                tmem_st16(tF + lanes + c0 + 32 * j + 16 * h, v);
             }
-            tmem_st16(tF + lanes + c0 + 16 * j, v);
+            __syncwarp();
         }
         tmem_st_wait();
         tc_before();  // the stores precede the MMAs on F after the barrier below
