@@ -712,26 +712,38 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_seg_scatter_cut(const ui
     __syncwarp();
     const long long b0 = (long long)ci * N + (long long)seg * SEG;
     const long long b1 = min((long long)(ci + 1) * N, b0 + SEG);
+    // a stage's rectangles and indices are requested together, and the next
+    // stage's while this one's pairs are written: eight loads in flight
+    short4 rs[kStage / 32];
+    uint32_t es[kStage / 32];
+    auto fetch = [&](long long c) {
+#pragma unroll
+        for (int u = 0; u < kStage / 32; ++u) {
+            const long long k = c + u * 32 + lane;
+            rs[u] = k < b1 ? rect[k] : make_short4(0, 0, -1, -1);
+            es[u] = k < b1 ? order[k] : 0u;
+        }
+    };
+    fetch(b0);
     for (long long c0 = b0; c0 < b1; c0 += kStage) {
-        const int m = (int)min((long long)kStage, b1 - c0);
         __syncwarp();
         int mt = 0;
-        // the stage's rectangles are requested together: four loads in flight
-        short4 rs[kStage / 32];
+        short4 rn[kStage / 32];
+        uint32_t en[kStage / 32];
 #pragma unroll
         for (int u = 0; u < kStage / 32; ++u) {
-            const int k = u * 32 + lane;
-            rs[u] = k < m ? rect[c0 + k] : make_short4(0, 0, -1, -1);
+            rn[u] = rs[u];
+            en[u] = es[u];
         }
+        if (c0 + kStage < b1) fetch(c0 + kStage);
 #pragma unroll
         for (int u = 0; u < kStage / 32; ++u) {
-            const int k = u * 32 + lane;
-            uint32_t o0 = 0, cnt = 0, e = 0;
-            const short4 r = rs[u];
+            uint32_t o0 = 0, cnt = 0;
+            const short4 r = rn[u];
+            const uint32_t e = en[u];
             if (r.y <= row && row <= r.w) {
                 o0 = opre[r.x];
                 cnt = opre[r.z + 1] - o0;
-                e = order[c0 + k];
             }
             const bool touch = cnt > 0u;
             const uint32_t bal = __ballot_sync(0xffffffffu, touch);
