@@ -192,3 +192,19 @@ def test_config4_sixteen_cameras_autotuned_graph():
             g = _grads_np(o2["grads"])
             check_grads(g, ref, keys=("means", "scales", "quats", "opacities", "sh"), tol=1e-3)
             check_grads(g, ref, keys=("features",), tol=1e-2)
+
+    # the list cut inside the captured step (the bench's configuration): the
+    # same forward bit for bit and the same gradients, from fewer instances
+    rast_c = api.Rasterizer(0, sh_degree=3, path=api.PATH_TC, list_cut=1)
+    rast_c.set_splits(tuned["fwd"], tuned["bwd"])
+    step_c = api.CapturedStep(rast_c, t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], t["features"],
+                              dC, dF, cams)
+    oc = step_c.replay()
+    torch.cuda.synchronize()
+    assert rast_c.ctx.sync_status() == api.OK
+    for k in ("rgb", "feat", "T", "last"):
+        assert torch.equal(oc[k], o2[k]), k
+    for k, v in o2["grads"].items():
+        if v is not None:
+            assert torch.linalg.norm((v - oc["grads"][k]).double()) <= 1e-5 * torch.linalg.norm(v.double()), k
+    assert int(oc["count"].item()) < n_inst
