@@ -333,6 +333,21 @@ fhgs_status fhgs_activate_gaussians(fhgs_ctx *ctx, int64_t n, const float *log_s
 fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void *stream);
 
 /* ------------------------------------------------------------------ NDFD -- */
+/* The walk's end state of an NDFD forward, which the backward can read
+ * instead of rebuilding it front to back (App. A records F_{N-1} and W_{N-1}
+ * for the same purpose): per pixel the feature sum F_N = sum_i w_i f_i over
+ * all contributors [P][D] float32 (16-byte aligned), T after the walk [P]
+ * float32 and the last contributor's list position + 1 [P] int32.  All
+ * device, caller-owned.  Only the tensor-core NDFD kernels write and read it
+ * (BF16 features, EWA at D = 256 or 512, surfels at D = 512); the CUDA-core
+ * kernels ignore it.  fhgs_ndfd_bwd may be given it only after fhgs_ndfd_fwd
+ * wrote it for the same Gaussians, lists, features, cameras and parameters. */
+typedef struct fhgs_ndfd_state {
+    float *F;
+    float *T;
+    int32_t *last;
+} fhgs_ndfd_state;
+
 /* Non-differentiable feature driving (Sec. 3.2; App. A "NDFD"): per pixel,
  * over the same depth-sorted tile lists, contributors and Eq. 4 weights
  * w_i = alpha_i T_i as fhgs_render_fwd (i = 1 nearest), with the pixel's
@@ -364,22 +379,8 @@ fhgs_status fhgs_sum(fhgs_ctx *ctx, int64_t m, const float *x, float *out, void 
  * p->geometry = FHGS_GEOM_SURFEL the weights are the 2DGS surfel render's
  * (the ray-plane solve of Sec. 3.1, the paper's own combination); the
  * tensor-core kernels then take BF16 features at D = 512 only (FHGS_PATH_TC
- * with any other D is FHGS_ERR_UNSUPPORTED). */
-/* The walk's end state of an NDFD forward, which the backward can read
- * instead of rebuilding it front to back (App. A records F_{N-1} and W_{N-1}
- * for the same purpose): per pixel the feature sum F_N = sum_i w_i f_i over
- * all contributors [P][D] float32 (16-byte aligned), T after the walk [P]
- * float32 and the last contributor's list position + 1 [P] int32.  All
- * device, caller-owned.  Only the tensor-core NDFD kernels write and read it
- * (BF16 features, EWA at D = 256 or 512, surfels at D = 512); the CUDA-core
- * kernels ignore it.  fhgs_ndfd_bwd may be given it only after fhgs_ndfd_fwd
- * wrote it for the same Gaussians, lists, features, cameras and parameters. */
-typedef struct fhgs_ndfd_state {
-    float *F;
-    float *T;
-    int32_t *last;
-} fhgs_ndfd_state;
-
+ * with any other D is FHGS_ERR_UNSUPPORTED).  save (nullable) receives the
+ * walk's end state when the tensor-core kernels run (fhgs_ndfd_state). */
 fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs_bins *bins, const void *features,
                           const void *feat_gt, fhgs_dtype ftype, int D, const fhgs_camera *cams, int n_cams,
                           const fhgs_params *p, float k, float lambda, float *L_gt, float *L_cf, int32_t *n_contrib,
@@ -392,7 +393,11 @@ fhgs_status fhgs_ndfd_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fhgs
  *             + sum_{i>k} sigma_i w_i (1 - f_i . f_k))            (Sec. 3.3),
  *   dL/dalpha_k = T_k dL/dw_k - (1/(1-alpha_k)) sum_{i>k} w_i dL/dw_i (App. A.2).
  * The walk recomputes F_N front to back, then goes back to front; nothing
- * from a forward call is needed.  grad_Lgt, grad_Lcf [P] device float32.  All
+ * from a forward call is needed, unless `saved` (nullable) holds the end
+ * state fhgs_ndfd_fwd wrote with `save` for the same inputs: the tensor-core
+ * kernels then read F_N, T and the last contributors instead of the front-to-
+ * back walk (the gradients agree to the order of their float atomics).
+ * grad_Lgt, grad_Lcf [P] device float32.  All
  * gradient outputs are OVERWRITTEN, device float32 with the shapes of
  * fhgs_render_bwd's: grad_means [n][3], grad_scales [n][3], grad_quats [n][4]
  * (16-byte aligned), grad_opac [n], grad_sh [n][K][3] (all zero: colour
