@@ -241,7 +241,9 @@ fhgs_status fhgs_render_bwd(fhgs_ctx *ctx, const fhgs_gaussians *g, const void *
  * FHGS_FUSE_FINALIZE then writes out[g][c] = num/den where den > 0, else 0;
  * FHGS_FUSE_NORMALIZE additionally L2-normalises each non-zero out row.
  * out may be NULL unless FINALIZE is set.  Uses context scratch; views are
- * processed one at a time.  p->path: FHGS_PATH_FP32 sums on the CUDA cores;
+ * processed in groups of up to 8 (fewer when the group's projection records
+ * would pass 4 GiB), each group projected, binned and fused by one launch of
+ * each kernel, with one host read of its instance count.  p->path: FHGS_PATH_FP32 sums on the CUDA cores;
  * FHGS_PATH_AUTO and FHGS_PATH_TC use the tensor cores when D % 64 == 0
  * (weights and maps as BF16 hi + lo, ~16-bit products, FP32 accumulation;
  * FHGS_PATH_TC with another D returns FHGS_ERR_UNSUPPORTED).  Each view's

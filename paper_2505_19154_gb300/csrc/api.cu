@@ -1,5 +1,6 @@
 // C ABI of libfhgs.so (declared in include/fhgs.h): argument checks, context
 // scratch, camera/parameter marshalling and kernel dispatch.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -12,6 +13,9 @@
 #include "fhgs_internal.cuh"
 
 using namespace fhgs;
+
+// Most views a fusion call projects, bins and fuses together.
+constexpr int kFuseGroup = 8;
 
 struct DevBuf {
     void *p = nullptr;
@@ -828,25 +832,37 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
     Params qp = q;
     qp.sh_deg = 0;
     qp.K = 0;
-    if ((s = ensure(ctx, ctx->fuse_proj, proj_bytes(n))) != FHGS_OK) return s;
+    // Views go through in groups: one projection, one binning pass and one
+    // fusion launch per group.  The group shares the binning's fixed costs
+    // (the depth sort's passes, the scans, the host read of the instance
+    // count) and gives its latency-bound scatter several views' warps at
+    // once.  The group is capped by the projection records it needs.
+    int group = (int)std::max<long long>(1, std::min<long long>(kFuseGroup, (4ll << 30) / (long long)proj_bytes(n)));
+    group = std::min(group, std::max(1, n_views));
+    if ((s = ensure(ctx, ctx->fuse_proj, proj_bytes(n * group))) != FHGS_OK) return s;
     if ((s = ensure(ctx, ctx->fuse_count, 256)) != FHGS_OK) return s;
-    for (int v = 0; v < n_views && n > 0; ++v) {
+    for (int v0 = 0; v0 < n_views && n > 0;) {
+        const int nv = std::min(group, n_views - v0);
         CamSet cs;
-        make_cams(ctx, views + v, 1, cs);
+        make_cams(ctx, views + v0, nv, cs);
+        FuseMaps fm{};
+        for (int i = 0; i < nv; ++i) fm.m[i] = maps[v0 + i];
         if ((s = ensure(ctx, ctx->fuse_ranges, sizeof(uint32_t) * 2 * (size_t)cs.total_tiles)) != FHGS_OK) return s;
-        ProjView pv = proj_view(ctx->fuse_proj.p, n);
+        ProjView pv = proj_view(ctx->fuse_proj.p, n * nv);
         {
             Prof pr(ctx, "fuse_project", st);
             launch_project(*g, cs, qp, pv, ctx->status, st);
         }
-        if ((s = ensure_bin_scratch(ctx, n, 1, cs.total_tiles)) != FHGS_OK) return s;
-        BinScratch sc = bin_scratch_view(ctx->bin.p, n, 1, cs.total_tiles, ctx->sm_count);
+        if ((s = ensure_bin_scratch(ctx, n, nv, cs.total_tiles)) != FHGS_OK) return s;
+        BinScratch sc = bin_scratch_view(ctx->bin.p, n, nv, cs.total_tiles, ctx->sm_count);
         fhgs_bins b;
         b.keys = nullptr;
         b.ranges = (uint32_t *)ctx->fuse_ranges.p;
         b.n_instances = (int64_t *)ctx->fuse_count.p;
-        // instance capacity: grow until this view's instances fit (reads
-        // the count on the host, so fusion is not meant for stream capture)
+        // instance capacity: grow until the group's instances fit (reads the
+        // count on the host, so fusion is not meant for stream capture); a
+        // group whose instances overflow 32-bit offsets is split
+        bool split = false;
         for (int tries = 0;; ++tries) {
             if (tries > 3) return fail(ctx, FHGS_ERR_CAPACITY, "instance buffer did not converge");
             if ((s = ensure(ctx, ctx->fuse_gids, sizeof(uint32_t) * 1024)) != FHGS_OK) return s;
@@ -854,7 +870,7 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
             b.capacity = (long long)(ctx->fuse_gids.bytes / sizeof(uint32_t));
             {
                 Prof pr(ctx, "fuse_bin_sort", st);
-                launch_bin_sort(n, 1, cs, pv, b, sc, p->list_cut ? &q : nullptr, nullptr, st);
+                launch_bin_sort(n, nv, cs, pv, b, sc, p->list_cut ? &q : nullptr, nullptr, st);
             }
             int64_t count = 0;
             FHGS_CUDA(ctx, cudaMemcpyAsync(&count, b.n_instances, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -862,19 +878,25 @@ fhgs_status fhgs_fuse_features(fhgs_ctx *ctx, const fhgs_gaussians *g, const fhg
             if (count <= b.capacity) {
                 if (fuse_tc) {
                     Prof pr(ctx, "fuse_tc", st);
-                    launch_fuse_tc(n, cs, q, pv, b, maps[v], D, num, den, ctx->status, st);
+                    launch_fuse_tc(n, cs, q, pv, b, fm, D, num, den, ctx->status, st);
                 } else {
                     Prof pr(ctx, "fuse_fp32", st);
-                    launch_fuse_fp32(n, cs, q, pv, b, maps[v], D, num, den, st);
+                    launch_fuse_fp32(n, cs, q, pv, b, fm, D, num, den, st);
                 }
                 break;
             }
-            if (count > 0xFFFFFFFFll) return fail(ctx, FHGS_ERR_CAPACITY, "too many instances in one view");
+            if (count > 0xFFFFFFFFll) {
+                if (nv == 1) return fail(ctx, FHGS_ERR_CAPACITY, "too many instances in one view");
+                group = nv / 2;
+                split = true;
+                break;
+            }
             if ((s = ensure(ctx, ctx->fuse_gids, sizeof(uint32_t) * (size_t)(count + count / 8 + 1024))) !=
                 FHGS_OK)
                 return s;
         }
         FHGS_CUDA(ctx, cudaGetLastError());
+        if (!split) v0 += nv;
     }
     if (flags & FHGS_FUSE_FINALIZE) {
         Prof pr(ctx, "fuse_finalize", st);

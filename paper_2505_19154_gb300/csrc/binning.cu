@@ -32,6 +32,7 @@ constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kRadixRounds = 8;
 constexpr int kRadixTile = kRadixThreads * kRadixRounds;  // 2048
 constexpr int kBuckets = 256;
+constexpr int kRadixBlocksPerSM = 2;  // grid cap of the radix passes (the digit table is 256 x grid)
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
@@ -152,14 +153,20 @@ __global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, int total, int
 // Stable scatter.  The block walks its segment in tiles of kRadixTile items;
 // inside a tile, warp w owns items [w*256, w*256+256) visited in 8 rounds of
 // 32 consecutive items, so (warp, round, lane) is memory order and ranks
-// computed in that order keep the sort stable.
+// computed in that order keep the sort stable.  The tile is first reordered
+// by digit in shared memory, then written out in that order: consecutive
+// threads store consecutive slots of one digit's run, so each store
+// instruction touches a few sectors instead of one per lane.
 __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, long long n, int shift, uint32_t mask, const uint32_t *__restrict__ hist,
     const uint32_t *__restrict__ kb) {
     __shared__ uint32_t run[kBuckets];                // next output slot per digit
     __shared__ uint32_t tot[kBuckets];                // this tile's count per digit
+    __shared__ uint32_t tstart[kBuckets];             // first tile-local slot per digit
     __shared__ uint32_t wcnt[kRadixWarps][kBuckets];  // per-warp counts, then prefixes
+    __shared__ uint32_t wsum[kRadixWarps];
+    __shared__ uint32_t sk[kRadixTile], sv[kRadixTile];  // the tile in digit order
     const long long G = gridDim.x;
     const long long seg = (n + G - 1) / G;
     const long long s = blockIdx.x * seg, e = min(n, s + seg);
@@ -198,7 +205,9 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
             rank[r] = before + __popc(peers & lt);
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < kBuckets; d += kRadixThreads) {
+        static_assert(kBuckets == kRadixThreads, "one thread per digit");
+        {
+            const int d = threadIdx.x;
             uint32_t acc = 0;
 #pragma unroll
             for (int k = 0; k < kRadixWarps; ++k) {
@@ -207,18 +216,44 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
                 acc += c;
             }
             tot[d] = acc;
+            // exclusive scan of the digit totals over the block
+            uint32_t x = acc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[w] = x;
+            __syncthreads();
+            uint32_t before = 0;
+#pragma unroll
+            for (int k = 0; k < kRadixWarps; ++k) before += k < w ? wsum[k] : 0u;
+            tstart[d] = before + x - acc;
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kRadixRounds; ++r) {
             if (dig[r] < kBuckets) {
-                const uint32_t pos = run[dig[r]] + wcnt[w][dig[r]] + rank[r];
-                kout[pos] = key[r];
-                vout[pos] = val[r];
+                const uint32_t q = tstart[dig[r]] + wcnt[w][dig[r]] + rank[r];
+                sk[q] = key[r];
+                sv[q] = val[r];
             }
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < kBuckets; d += kRadixThreads) run[d] += tot[d];
+        const int tn = (int)min((long long)kRadixTile, e - t0);
+#pragma unroll
+        for (int r = 0; r < kRadixRounds; ++r) {
+            const int q = r * kRadixThreads + threadIdx.x;
+            if (q < tn) {
+                const uint32_t k2 = sk[q];
+                const int d = (int)((k2 >> shift) & mask);
+                const uint32_t pos = run[d] + (uint32_t)q - tstart[d];
+                kout[pos] = k2;
+                vout[pos] = sv[q];
+            }
+        }
+        __syncthreads();
+        run[threadIdx.x] += tot[threadIdx.x];
         __syncthreads();
     }
 }
@@ -265,7 +300,7 @@ __global__ void k_cam_keys(const uint32_t *__restrict__ order, long long n, long
 
 int radix_blocks(long long n, int sm_count) {
     long long g = (n + 4095) / 4096;
-    if (g > 2ll * sm_count) g = 2ll * sm_count;
+    if (g > (long long)kRadixBlocksPerSM * sm_count) g = (long long)kRadixBlocksPerSM * sm_count;
     return (int)(g < 1 ? 1 : g);
 }
 
@@ -841,7 +876,7 @@ size_t bin_scratch_bytes(long long N, int n_cams, int total_tiles, int sm_count)
     const int SEG = seg_size(N, total_tiles);
     const long long S = (N + SEG - 1) / SEG;
     const long long tab = (long long)total_tiles * (S > 0 ? S : 1);
-    const int G = 2 * sm_count;
+    const int G = kRadixBlocksPerSM * sm_count;
     return 5 * align_up(sizeof(uint32_t) * (cn + 1), 256) + align_up(sizeof(int4) * (cn + 1), 256) +
            align_up(sizeof(short4) * (cn + 1), 256) +
            2 * align_up(sizeof(uint32_t) * (tab + 1), 256) + align_up(sizeof(int) * (total_tiles + 1), 256) +
@@ -872,7 +907,7 @@ BinScratch bin_scratch_view(void *base, long long N, int n_cams, int total_tiles
     s.mass = take(sizeof(uint32_t) * (tab + 1));
     s.close = reinterpret_cast<int *>(take(sizeof(int) * (total_tiles + 1)));
     s.partials = take(sizeof(uint32_t) * ((tab + kScanTile - 1) / kScanTile + 1));
-    s.hist = take(sizeof(uint32_t) * kBuckets * (size_t)(2 * sm_count));
+    s.hist = take(sizeof(uint32_t) * kBuckets * (size_t)(kRadixBlocksPerSM * sm_count));
     s.kbits = take(2 * sizeof(uint32_t));
     s.seg = SEG;
     s.nseg = (int)S;

@@ -223,14 +223,18 @@ void launch_render_bwd_fp32(long long N, const CamSet &cs, const Params &p, Proj
                             const void *feats, int bf16, int D, const float *T, const int32_t *last,
                             const float *grgb, const float *gfeat, float *g2d, float *gfeatures,
                             cudaStream_t st);
+// The feature map of each camera of a fusion launch: [H*W, D] float32.
+struct FuseMaps {
+    const float *m[FHGS_MAX_CAMS];
+};
 void launch_fuse_fp32(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
-                      const float *fmap, int D, float *num, float *den, cudaStream_t st);
+                      const FuseMaps &maps, int D, float *num, float *den, cudaStream_t st);
 void launch_fuse_finalize(long long N, int D, const float *num, const float *den, float *out, int normalize,
                           cudaStream_t st);
 // fusion on the tensor cores (render_tc.cu): D a multiple of 64
 int fuse_tc_dn(int D);
 void launch_fuse_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
-                    const float *fmap, int D, float *num, float *den, unsigned *status, cudaStream_t st);
+                    const FuseMaps &maps, int D, float *num, float *den, unsigned *status, cudaStream_t st);
 
 // render, tcgen05 tensor-core path (render_tc.cu)
 int tc_supported(int D, int d_split);

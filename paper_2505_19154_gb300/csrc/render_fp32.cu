@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(256) k_render_bwd_fp32(long long N, CamSet cs,
 __global__ void __launch_bounds__(256) k_fuse_fp32(long long N, CamSet cs, Params p, ProjView pv,
                                                    const uint32_t *__restrict__ gids,
                                                    const uint32_t *__restrict__ ranges,
-                                                   const float *__restrict__ fmap, int D, float *num, float *den) {
+                                                   const FuseMaps maps, int D, float *num, float *den) {
     __shared__ float4 sa[kB], sb[kB];
     __shared__ uint32_t sg[kB];
     const TileCtx tc = tile_ctx(cs, ranges);
@@ -312,7 +312,9 @@ __global__ void __launch_bounds__(256) k_fuse_fp32(long long N, CamSet cs, Param
 #pragma unroll
     for (int c = 0; c < kDC; ++c) F[c] = 0.f;
     if (tc.inside) {
-        const float4 *src = reinterpret_cast<const float4 *>(fmap + tc.pix * D + c0);
+        // each camera's map is its own [H*W, D] array
+        const long long mp = (long long)tc.py * cs.c[tc.ci].W + tc.px;
+        const float4 *src = reinterpret_cast<const float4 *>(maps.m[tc.ci] + mp * D + c0);
 #pragma unroll
         for (int c = 0; c < kDC; c += 4)
             if (c0 + c < D) {
@@ -419,10 +421,10 @@ void launch_render_bwd_fp32(long long N, const CamSet &cs, const Params &p, Proj
 }
 
 void launch_fuse_fp32(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
-                      const float *fmap, int D, float *num, float *den, cudaStream_t st) {
+                      const FuseMaps &maps, int D, float *num, float *den, cudaStream_t st) {
     dim3 grid(cs.total_tiles, (D + kDC - 1) / kDC);
     note_launch(1);
-    k_fuse_fp32<<<grid, 256, 0, st>>>(N, cs, p, pv, bins.gids, bins.ranges, fmap, D, num, den);
+    k_fuse_fp32<<<grid, 256, 0, st>>>(N, cs, p, pv, bins.gids, bins.ranges, maps, D, num, den);
 }
 
 void launch_fuse_finalize(long long N, int D, const float *num, const float *den, float *out, int normalize,

@@ -1356,7 +1356,7 @@ struct FuseCfg {
 template <int DN>
 __global__ void __launch_bounds__(256, 1)
     k_fuse_tc(long long N, CamSet cs, Params p, ProjView pv, const uint32_t *__restrict__ gids,
-              const uint32_t *__restrict__ ranges, const float *__restrict__ fmap, int D, float *num, float *den,
+              const uint32_t *__restrict__ ranges, const FuseMaps maps, int D, float *num, float *den,
               unsigned *status) {
     using C = FuseCfg<DN>;
     extern __shared__ uint8_t smem_raw[];
@@ -1388,6 +1388,7 @@ __global__ void __launch_bounds__(256, 1)
     const int nbatches = (int)((e - s + kFB - 1) / kFB);
     const int d0 = chunk * DN;
     const GRec *rec = pv.rec + (long long)ci * N;
+    const float *__restrict__ fmap = maps.m[ci];
     if (nbatches == 0) return;  // uniform over the CTA: nothing to fuse
 
     if (warp == 0) tmem_alloc(tslot, C::kTmemCols);
@@ -1798,7 +1799,7 @@ int fuse_tc_dn(int D) {
 }
 
 void launch_fuse_tc(long long N, const CamSet &cs, const Params &p, ProjView pv, const fhgs_bins &bins,
-                    const float *fmap, int D, float *num, float *den, unsigned *status, cudaStream_t st) {
+                    const FuseMaps &maps, int D, float *num, float *den, unsigned *status, cudaStream_t st) {
     const int dn = fuse_tc_dn(D);
     dim3 grid(cs.total_tiles * 2, D / dn);
     note_launch(1);
@@ -1806,7 +1807,7 @@ void launch_fuse_tc(long long N, const CamSet &cs, const Params &p, ProjView pv,
     case DNV: {                                                                                                \
         static std::atomic<unsigned long long> smem_done{0};                                                 \
         allow_max_smem(smem_done, k_fuse_tc<DNV>);                                                           \
-        k_fuse_tc<DNV><<<grid, 256, FuseCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, fmap, D,  \
+        k_fuse_tc<DNV><<<grid, 256, FuseCfg<DNV>::kSmem, st>>>(N, cs, p, pv, bins.gids, bins.ranges, maps, D,  \
                                                                num, den, status);                            \
         break;                                                                                                 \
     }
