@@ -120,14 +120,16 @@ def test_tc_config2_forward_backward():
 def test_tc_fusion_small_against_oracle_and_fp32_path(D):
     """Tensor-core fusion (one D slice at 128, three at 192) against the
     oracle composited over the FP32 specification's footprints, with the
-    fusion margin rule; and against the FP32 CUDA-core fusion."""
+    fusion margin rule; and against the FP32 CUDA-core fusion.  The maps are
+    unit-norm per pixel (the workload's recipe): a weight change d at pixel p
+    moves num/den by d (f_p - out) / den, at most 2 d / den when |f_p| = 1,
+    which is what the margin rule's allowance 2 wflip / (den |out|) assumes."""
     sc = small_random_scene(2500, seed=33, sh_degree=1, D=0, spread=0.5)
     sc = {k: (np.asarray(v, np.float32) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
     views = [synth.look_at_camera(synth.ring_position(3.0, a, e), w, h)
              for a, e, w, h in [(10, 5, 80, 48), (130, -10, 64, 72), (250, 20, 50, 40)]]
     prm = dict(sh_degree=1)
-    g = np.random.default_rng(4)
-    maps = [g.normal(size=(v["height"], v["width"], D)).astype(np.float32) for v in views]
+    maps = [synth.smooth_feature_map(4, i, v["height"], v["width"], D) for i, v in enumerate(views)]
     prep = oracle.prepare(sc, views, prm, geometry="fp32")
     ref = oracle.fuse(sc, views, maps, prm, prep=prep)
     t = {k: _t(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
@@ -155,6 +157,60 @@ def test_tc_fusion_small_against_oracle_and_fp32_path(D):
         assert np.all(rel[seen] <= 1e-4 + risk[seen]), path
         assert np.abs(d_ - ref["den"]).max() <= 1e-4 * max(1.0, ref["den"].max()), path
         assert np.all(o[ref["den"] == 0] == 0), path
+
+
+def test_fusion_view_groups_against_oracle_and_single_views():
+    """Eleven ragged views fuse in two groups (8 + 3 views, one projection,
+    binning and fusion launch each): against the oracle with the fusion
+    margin rule, and against the same views fused one call per view (the
+    same weights, so num and den differ only by the order of their float
+    additions).  Unit-norm smooth maps, as in the small fusion test above."""
+    D = 64
+    sc = small_random_scene(2500, seed=35, sh_degree=1, D=0, spread=0.5)
+    sc = {k: (np.asarray(v, np.float32) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+    spec = [(33 * i, (-20, 0, 15, 25)[i % 4], (48, 64, 40, 72)[i % 4], (40, 56, 64, 36)[i % 3]) for i in range(11)]
+    views = [synth.look_at_camera(synth.ring_position(3.0, a, e), w, h) for a, e, w, h in spec]
+    prm = dict(sh_degree=1)
+    maps = [synth.smooth_feature_map(5, i, v["height"], v["width"], D) for i, v in enumerate(views)]
+    prep = oracle.prepare(sc, views, prm, geometry="fp32")
+    ref = oracle.fuse(sc, views, maps, prm, prep=prep)
+    t = {k: _t(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    gs = tuple(t[k] for k in ("means", "scales", "quats", "opacities", "sh"))
+    dmaps = [_t(m).view(-1, D) for m in maps]
+    seen = ref["den"] > 1e-6
+    assert seen.sum() > 300
+    fn = np.maximum(np.linalg.norm(ref["out"], axis=1), 1e-30)
+    risk = 2.0 * ref["wflip"] / np.maximum(ref["den"], 1e-30) / fn
+    for path, cut in ((api.PATH_TC, 1), (api.PATH_FP32, 0)):
+        rast = api.Rasterizer(0, sh_degree=1, path=path, list_cut=cut)
+        rast.ctx.profile(True)
+        o, num, den = rast.fuse(*gs, views, dmaps)
+        torch.cuda.synchronize()
+        assert rast.ctx.sync_status() == api.OK
+        prof = rast.ctx.profile_read()
+        name = "fuse_tc" if path == api.PATH_TC else "fuse_fp32"
+        assert prof[name][0] == 2 and prof["fuse_bin_sort"][0] >= 2, prof  # two groups
+        o = o.cpu().numpy().astype(np.float64)
+        d_ = den.cpu().numpy().astype(np.float64)
+        rel = np.linalg.norm(o - ref["out"], axis=1) / fn
+        chk = seen & (risk <= 1e-4)
+        assert (seen & ~chk).sum() <= 0.06 * seen.sum()
+        assert rel[chk].max() <= 1e-4, (path, rel[chk].max())
+        assert np.all(rel[seen] <= 1e-4 + risk[seen]), path
+        assert np.abs(d_ - ref["den"]).max() <= 1e-4 * max(1.0, ref["den"].max()), path
+        assert np.all(o[ref["den"] == 0] == 0), path
+        # one call per view into the same accumulators
+        num1 = torch.zeros_like(num)
+        den1 = torch.zeros_like(den)
+        for v, m in zip(views, dmaps):
+            rast.fuse_accumulate(gs, [v], [m], num1, den1)
+        torch.cuda.synchronize()
+        n0, n1 = num.cpu().numpy().astype(np.float64), num1.cpu().numpy().astype(np.float64)
+        d0, d1 = den.cpu().numpy().astype(np.float64), den1.cpu().numpy().astype(np.float64)
+        assert np.array_equal(d0 > 0, d1 > 0), path
+        assert np.abs(d0 - d1).max() <= 1e-5 * max(1.0, d0.max()), path
+        nrm = np.maximum(np.linalg.norm(n0, axis=1), 1e-30)
+        assert (np.linalg.norm(n0 - n1, axis=1) / nrm)[d0 > 0].max() <= 1e-5, path
 
 
 @pytest.mark.parametrize("D,cams_spec", [(256, [(30, 10, 64, 48)]),
