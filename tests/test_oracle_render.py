@@ -312,7 +312,8 @@ def test_fusion_flip_bound_covers_threshold_perturbations():
     near-threshold decision moves: moving alpha_min, the q^2 cutoff or t_eps
     by 0.5 % flips exactly the decisions within 0.5 % of their threshold, and
     every Gaussian's change of sum w (and of sum w F, unit-norm F) stays
-    within its wflip computed with a 1 % tolerance."""
+    within its wflip computed with a 1 % tolerance; the fused feature then
+    moves by at most 2 wflip / (den - wflip)."""
     sc = small_random_scene(500, seed=61, sh_degree=0, D=0, spread=0.45)
     views = [synth.look_at_camera(synth.ring_position(2.2, a, e), 48, 40) for a, e in [(10, 5), (150, -20)]]
     g = np.random.default_rng(9)
@@ -333,6 +334,12 @@ def test_fusion_flip_bound_covers_threshold_perturbations():
             d_num = np.linalg.norm(alt["num"] - ref["num"], axis=1)
             assert np.all(d_den <= ref["wflip"] * (1 + 1e-9) + 1e-15), (key, f)
             assert np.all(d_num <= ref["wflip"] * (1 + 1e-9) + 1e-15), (key, f)
+            # the fused feature num/den moves by at most 2 wflip / (den - wflip)
+            # (|F| = 1 >= |out|): the allowance the GPU fusion tests grant
+            both = (ref["den"] > 1e-6) & (alt["den"] > 1e-6) & (ref["wflip"] < 0.5 * ref["den"])
+            d_out = np.linalg.norm(alt["out"] - ref["out"], axis=1)
+            allow = 2.0 * ref["wflip"] / np.maximum(ref["den"] - ref["wflip"], 1e-30)
+            assert np.all(d_out[both] <= allow[both] * (1 + 1e-9) + 1e-15), (key, f)
             moved += int((d_den > 1e-12).sum())
     assert moved > 10  # the perturbations do flip decisions
     assert np.all(oracle.fuse(sc, views, maps, base, prep=prep, margin_tol=0.0)["wflip"] == 0.0)
