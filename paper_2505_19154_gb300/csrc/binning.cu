@@ -58,7 +58,6 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t 
     const long long seg = (n + G - 1) / G;
     const long long s = blockIdx.x * seg, e = min(n, s + seg);
     const int w = threadIdx.x >> 5;
-    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
     for (long long i0 = s; i0 < e; i0 += kRadixTile) {
         uint32_t kk[kRadixRounds];  // the tile's keys requested together
 #pragma unroll
@@ -69,9 +68,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t 
 #pragma unroll
         for (int r = 0; r < kRadixRounds; ++r) {
             const long long i = i0 + r * kRadixThreads + threadIdx.x;
-            const int d = i < e ? (int)((kk[r] >> shift) & mask) : (kBuckets + (int)(threadIdx.x & 31));
-            const unsigned peers = __match_any_sync(0xffffffffu, d);  // one shared add per distinct digit
-            if (d < kBuckets && (peers & lt) == 0) atomicAdd(&h[w][d], (uint32_t)__popc(peers));
+            if (i < e) atomicAdd(&h[w][(kk[r] >> shift) & mask], 1u);
         }
     }
     __syncthreads();
@@ -261,19 +258,24 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
 // Keys and indices of the depth sort, and the AND / OR of the keys of the
 // entries that are not culled (culled entries, key 0xFFFFFFFF, have empty
 // rectangles, so their place in the order does not matter).
+// Grid-stride: each thread folds its entries' keys, so the block issues one
+// pair of global atomics however many entries it covers.
 __global__ void k_iota_keys(const uint32_t *__restrict__ dkey, long long n, uint32_t *k, uint32_t *v,
                             uint32_t *kb) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t key = 0xFFFFFFFFu;
-    if (i < n) {
-        key = dkey[i];
+    uint32_t ta = 0xFFFFFFFFu, to = 0u;  // AND / OR of this thread's live keys
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t key = dkey[i];
         k[i] = key;
         v[i] = (uint32_t)i;
+        if (key != 0xFFFFFFFFu) {
+            ta &= key;
+            to |= key;
+        }
     }
-    const bool live = key != 0xFFFFFFFFu;
     __shared__ uint32_t ra[8], ro[8];  // one AND / OR per warp, then one pair of atomics per block
-    const uint32_t a = __reduce_and_sync(0xffffffffu, live ? key : 0xFFFFFFFFu);
-    const uint32_t o = __reduce_or_sync(0xffffffffu, live ? key : 0u);
+    const uint32_t a = __reduce_and_sync(0xffffffffu, ta);
+    const uint32_t o = __reduce_or_sync(0xffffffffu, to);
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         ra[w] = a;
@@ -932,7 +934,8 @@ uint32_t *sort_entries(long long N, int n_cams, ProjView pv, const BinScratch &s
     cudaMemsetAsync(sc.kbits, 0xFF, sizeof(uint32_t), st);
     cudaMemsetAsync(sc.kbits + 1, 0, sizeof(uint32_t), st);
     note_launch(1);
-    k_iota_keys<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(pv.dkey, cn, sc.dk_a, sc.dv_a, sc.kbits);
+    const long long iota_blocks = min((cn + 255) / 256, 8ll * sc.sm_count);
+    k_iota_keys<<<(unsigned)iota_blocks, 256, 0, st>>>(pv.dkey, cn, sc.dk_a, sc.dv_a, sc.kbits);
     const bool in_b = radix_sort_pairs(sc.dk_a, sc.dv_a, sc.dk_b, sc.dv_b, cn, 32, sc.hist, G, st, sc.kbits);
     uint32_t *order = in_b ? sc.dv_b : sc.dv_a;
     if (n_cams > 1) {
