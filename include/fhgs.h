@@ -217,7 +217,10 @@ fhgs_status fhgs_render_fwd(fhgs_ctx *ctx, int64_t n, const void *proj, const fh
 /* Derivative of L = sum_p grad_rgb[p] . rgb[p] + grad_feat[p] . feat[p]
  * (App. A.2: dL/dalpha_k = T_k dL/dw_k - (1/(1-alpha_k)) sum_{i>k} w_i
  * dL/dw_i, plus the background term), walking each tile back to front and
- * recovering T by division from T_final.  All gradient outputs are
+ * recovering each contributor's T from T_final: the FP32 path divides by
+ * (1 - alpha) per contributor; the tensor-core path divides once per group
+ * of Gaussians by the group's product of (1 - alpha) and rebuilds the T
+ * inside the group from prefix products.  All gradient outputs are
  * OVERWRITTEN (not accumulated), device float32 with the shapes of the
  * inputs: grad_means [n][3], grad_scales [n][3], grad_quats [n][4],
  * grad_opac [n], grad_sh [n][K][3], grad_features [n][D] (nullable: skips
