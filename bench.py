@@ -571,11 +571,11 @@ def run_fusion(args):
     P = sum(v["width"] * v["height"] for v in views)
     N = len(scene["means"])
     algo = P * 4 * D + 2 * N * (4 * D + 4)  # maps read once, accumulators written once
-    line = {"metric": "feature fusion Mpix/s (3M Gaussians, 64 views 1280x720, D=256 FP32 maps)",
+    line = {"metric": f"feature fusion Mpix/s (3M Gaussians, {len(views)} views 1280x720, D=256 FP32 maps)",
             "value": round(P / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s", "n_gpus": 1, "steps": K,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (maps generated on the device)",
-            "config": {"workload": "fusion: 3M Gaussians, 64 views 1280x720, D=256", "views": len(views), "list_cut": bool(args.list_cut),
+            "config": {"workload": f"fusion: 3M Gaussians, {len(views)} views 1280x720, D=256", "views": len(views), "list_cut": bool(args.list_cut),
                        "gaussians": N, "seen": int((den > 0).sum().item())},
             "roofline": {"bound": "hbm", "achieved": round(algo / (ms * 1e-3) / 1e9, 1),
                          "peak": load_peaks()["hbm"], "unit": "GB/s",
